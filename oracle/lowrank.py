@@ -1,0 +1,147 @@
+"""The subset Newton step as a matrix equation, solved densely (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+* ``rhs``          -- B_k of Sec. 3.4, Eq. (rhs_matrix1), written with the
+                      affine pieces: B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T).
+* ``apply_F``      -- F(S_k) of Eq. (newton_matrix1) in the affine notation
+                      J0 S + Jmu' S D_mu + Jnu' S D_nu (the reference values
+                      mu_s, nu_f of Eq. (pardep_matrix1) cancel).
+* ``brute_force``  -- the vector notation, Eq. (newtonstep_vectornot1): one
+                      sparse solve J(x~; mu_i, nu_i) s_i = -R(x~; mu_i, nu_i)
+                      per column, with J and R assembled directly (not through
+                      the affine pieces).
+* ``truncate``     -- the truncation operator T onto rank <= R (Sec. 5,
+                      htucker's truncation; for an order-2 tensor this is the
+                      truncated SVD, Eckart-Young): keep the smallest rank r
+                      with sqrt(sum_{i>r} s_i^2) <= tol ||s||_2, r <= rank_cap.
+* ``chebyshev_T``  -- the truncated, preconditioned Chebyshev iteration.  The
+                      paper cites it ([WeiBR20, Alg. 3]) without restating it;
+                      this is the textbook Chebyshev acceleration (centre d,
+                      half-width c of the spectrum of P^{-1} A, Sec. 5.1.1)
+                      with left preconditioning by the mean-based P_T^k
+                      (Sec. 4.2) and T applied after every update of the
+                      iterate, the residual (before preconditioning) and the
+                      search direction; the true residual B - F(S) is formed
+                      every step; a cycle of ``iters`` steps is restarted
+                      ``cycles - 1`` times from the current iterate (Sec. 5.1:
+                      "restarted once after 6 iterations" = 2 cycles of 6).
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse.linalg as spla
+
+from . import fsi
+
+
+def rhs(R0, Rmu, Rnu, mu_k, nu_k):
+    """B_k (M x m_k), Eq. (rhs_matrix1)."""
+    mu_k, nu_k = np.asarray(mu_k, float), np.asarray(nu_k, float)
+    return -(np.outer(R0, np.ones_like(mu_k)) + np.outer(Rmu, mu_k) + np.outer(Rnu, nu_k))
+
+
+def apply_F(J0, Jmu, Jnu, S, mu_k, nu_k):
+    """F(S) = J0 S + Jmu' S D_mu + Jnu' S D_nu (Eq. (newton_matrix1))."""
+    return J0 @ S + (Jmu @ S) * np.asarray(mu_k)[None, :] + (Jnu @ S) * np.asarray(nu_k)[None, :]
+
+
+def brute_force(mesh, xt, mu_k, nu_k):
+    """Exact S_k column by column (Eq. (newtonstep_vectornot1))."""
+    S = np.zeros((mesh.M, len(mu_k)))
+    for i, (mu, nu) in enumerate(zip(mu_k, nu_k)):
+        J = fsi.jacobian(mesh, xt, mu, nu)
+        S[:, i] = spla.splu(J.tocsc()).solve(-fsi.residual(mesh, xt, mu, nu))
+    return S
+
+
+def truncation_rank(s, tol, rank_cap):
+    """Smallest r with sqrt(sum_{i >= r} s_i^2) <= tol * ||s||_2, capped."""
+    s = np.asarray(s, float)
+    if s.size == 0 or s[0] == 0.0:
+        return 0
+    tail = np.sqrt(np.cumsum((s ** 2)[::-1])[::-1])          # tail[r] = ||s[r:]||
+    tail = np.append(tail, 0.0)
+    total = tail[0]
+    r = int(np.argmax(tail <= tol * total))
+    return min(r, rank_cap)
+
+
+def truncate(X, tol, rank_cap):
+    """Best approximation of rank <= r (truncated SVD)."""
+    U, s, Vt = np.linalg.svd(X, full_matrices=False)
+    r = truncation_rank(s, tol, rank_cap)
+    return (U[:, :r] * s[:r]) @ Vt[:r]
+
+
+def preconditioner(J0, Jmu, Jnu, mu_bar, nu_bar):
+    """LU of P_T^k = J(x~; mu_bar, nu_bar) = J0 + mu_bar Jmu' + nu_bar Jnu' (Sec. 4.2)."""
+    P = (J0 + mu_bar * Jmu + nu_bar * Jnu).tocsc()
+    return spla.splu(P)
+
+
+def chebyshev_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, c, d, iters=6, cycles=2,
+                tol=1e-8, rank_cap=None, truncated=True, eta=None, history=None):
+    """Truncated preconditioned Chebyshev iteration for F(S) = B, S0 = 0.
+
+    One step j (centre d, half-width c, sigma = d / c, rho_0 = 1 / sigma):
+        S_{j+1}   = T(S_j + Delta_j)
+        Res_{j+1} = T(B - F(S_{j+1}))
+        Z_{j+1}   = P^{-1} Res_{j+1}
+        rho_{j+1} = 1 / (2 sigma - rho_j)
+        Delta_{j+1} = T(rho_{j+1} rho_j Delta_j + (2 rho_{j+1} / c) Z_{j+1})
+    and each cycle starts with Res = T(B - F(S)), Delta = P^{-1} Res / d.
+    The last step of a cycle stops after the update of S.  With ``eta`` the
+    iteration also stops once ||B - F(S)||_F <= eta ||B||_F (checked whenever
+    the true residual is formed).  ``history`` receives ||B - F(S)||_F / ||B||_F.
+    """
+    m = B.shape[1]
+    rank_cap = m if rank_cap is None else rank_cap
+    T = (lambda X: truncate(X, tol, rank_cap)) if truncated else (lambda X: X)
+    F = lambda S: apply_F(J0, Jmu, Jnu, S, mu_k, nu_k)
+    sigma = d / c
+    nB = np.linalg.norm(B)
+    S = np.zeros_like(B)
+    for _ in range(cycles):
+        Res = B - F(S)
+        if history is not None:
+            history.append(np.linalg.norm(Res) / nB)
+        if eta is not None and np.linalg.norm(Res) <= eta * nB:
+            return S
+        Delta = P_lu.solve(T(Res)) / d
+        rho = 1.0 / sigma
+        for j in range(iters):
+            S = T(S + Delta)
+            if j == iters - 1:
+                break
+            Res = B - F(S)
+            if history is not None:
+                history.append(np.linalg.norm(Res) / nB)
+            if eta is not None and np.linalg.norm(Res) <= eta * nB:
+                return S
+            Z = P_lu.solve(T(Res))
+            rho_new = 1.0 / (2.0 * sigma - rho)
+            Delta = T(rho_new * rho * Delta + (2.0 * rho_new / c) * Z)
+            rho = rho_new
+    if history is not None:
+        history.append(np.linalg.norm(B - F(S)) / nB)
+    return S
+
+
+def spectrum_interval(J0, Jmu, Jnu, P_lu, mu_pts, nu_pts):
+    """Smallest and largest |lambda| of P^{-1} A(mu, nu) over the given
+    parameters (Sec. 5.1.1), by dense eigenvalues (small M only)."""
+    M = J0.shape[0]
+    Pinv = P_lu.solve(np.eye(M))
+    lo, hi = np.inf, 0.0
+    for mu, nu in zip(mu_pts, nu_pts):
+        A = (J0 + mu * Jmu + nu * Jnu).toarray()
+        lam = np.abs(np.linalg.eigvals(Pinv @ A))
+        lo, hi = min(lo, lam.min()), max(hi, lam.max())
+    return lo, hi
+
+
+def chebyshev_cd(lam_min, lam_max):
+    """Centre d and half-width c of the interval [lam_min, lam_max]
+    (reading of Sec. 5.1.1: c = 0.1, d = 1 for the spectrum in [0.9, 1.1])."""
+    return 0.5 * (lam_max - lam_min), 0.5 * (lam_max + lam_min)
