@@ -1,0 +1,250 @@
+/*
+ * lrfsi -- low-rank solver for parameter-dependent stationary FSI on GB300.
+ *
+ * C ABI of the library built from paper_2008_10275_gb300/csrc.  It implements
+ * the hot path of Benner, Richter & Weinhandl, "A Low-rank Method for
+ * Parameter-dependent Fluid-structure Interaction Discretizations with
+ * Hyperelasticity": the per-subset Newton step written as one matrix equation
+ * (Sec. 3.4, Eq. (newton_matrix1))
+ *
+ *     J0 S + Jmu' S D_mu + Jnu' S D_nu = B,    S = U V^T,
+ *
+ * solved on the factors by the truncated, mean-preconditioned Chebyshev
+ * iteration (ChebyshevT, Sec. 4 and Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an int status: LRFSI_OK (0) or a negative code
+ *   below.  lrfsi_last_error() returns a message for the calling thread's last
+ *   failure.  No function aborts, traps or prints.
+ * - Vectors x in R^M use the library's DOF order (slab-major, see
+ *   lrfsi_mesh_dofmap).  Tall matrices (M x r, "U factors", residual blocks)
+ *   are ROW-MAJOR with a leading dimension ld >= r (element (i, j) at
+ *   p[i * ld + j]).  Small parameter-side matrices (m x r, "V factors") are
+ *   row-major with leading dimension ldv >= r.
+ * - Pointers named *_dev are device pointers owned by the caller; pointers
+ *   named *_host are host pointers owned by the caller.  The library never
+ *   frees caller memory and keeps no reference to it after the call returns.
+ * - Handles are created and destroyed by the library; they own their device
+ *   workspace.
+ * - Work is enqueued on the given stream; entry points that return host
+ *   values (norms, ranks, iteration counts) synchronize that stream.
+ * - All arithmetic named FP64 is IEEE binary64; the mixed mode runs the inner
+ *   Chebyshev correction in binary32 inside an FP64 refinement loop.
+ */
+#ifndef LRFSI_H
+#define LRFSI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LRFSI_OK 0
+#define LRFSI_EINVAL (-1)      /* bad argument (null pointer, size, option) */
+#define LRFSI_ENOMEM (-2)      /* device or host allocation failed */
+#define LRFSI_ECUDA (-3)       /* a CUDA runtime call failed */
+#define LRFSI_ESINGULAR (-4)   /* LU pivot below threshold (reported, not trapped) */
+#define LRFSI_ENOCONV (-5)     /* Newton / Chebyshev hit its iteration limit */
+#define LRFSI_EBREAKDOWN (-6)  /* Cholesky-QR breakdown that the shifted retry could not fix */
+#define LRFSI_ETIMEOUT (-7)    /* a bounded device wait expired */
+
+typedef void* lrfsi_stream_t;  /* a cudaStream_t; NULL = the legacy default stream */
+
+/* Geometry and constants of the 2D channel-with-flap problem (Sec. 2,
+ * Eq. (fsi_problem_weak1); the 2D stand-in for the 3D test case of Sec. 5). */
+typedef struct {
+  int nx, ny;            /* cells along x and y (structured quadrilaterals) */
+  double Lx, Ly;         /* channel [0, Lx] x [0, Ly] */
+  double flap[4];        /* solid S = (x0, x1) x (y0, y1); x1 <= x0 means no solid */
+  double rho_f;          /* fluid density */
+  double lam_s;          /* first Lame parameter of the solid */
+  double v_mean;         /* mean velocity of the parabolic inflow at x = 0 */
+} lrfsi_problem;
+
+typedef struct lrfsi_mesh_s* lrfsi_mesh_h;
+
+typedef struct {
+  int64_t M;             /* number of unknowns, 4 * (#Q2 nodes) + #Q1 vertices */
+  int64_t nnz;           /* nonzeros of the union pattern of J0, Jmu', Jnu' */
+  int nslab;             /* diagonal blocks of the block-tridiagonal ordering */
+  int nmax;              /* largest slab size */
+  int ncell, nsolid;     /* cells, solid cells */
+} lrfsi_mesh_info_t;
+
+/* lrfsi_mesh: build the Q2/Q2/Q1 DOF layout of the channel, the Dirichlet
+ * data b_D (parabolic inflow, no-slip walls, v = 0 on the closed solid,
+ * u = 0 on the outer boundary), the CSR union pattern of the affine operators
+ * (Sec. 3, Eq. (pardep_matrix1)), the cell -> CSR scatter map and the slab
+ * structure of the preconditioner LU; upload them to the current device.
+ * Errors: LRFSI_EINVAL for nx < 1, ny < 1 or non-positive lengths;
+ * LRFSI_ENOMEM / LRFSI_ECUDA on allocation failure. */
+int lrfsi_mesh_create(const lrfsi_problem* prob, lrfsi_mesh_h* out);
+int lrfsi_mesh_destroy(lrfsi_mesh_h mesh);
+int lrfsi_mesh_info(lrfsi_mesh_h mesh, lrfsi_mesh_info_t* info);
+
+/* DOF description (host arrays of length M): field (0 v_x, 1 v_y, 2 u_x,
+ * 3 u_y, 4 p) and position of the DOF on the Q2 node grid (ix in [0, 2 nx],
+ * iy in [0, 2 ny]; a Q1 vertex (a, b) sits at (2a, 2b)). */
+int lrfsi_mesh_dofmap(lrfsi_mesh_h mesh, int32_t* field_host, int32_t* ix_host, int32_t* iy_host);
+/* Dirichlet data b_D (host array of length M). */
+int lrfsi_mesh_dirichlet(lrfsi_mesh_h mesh, double* bD_host);
+/* CSR pattern copies (host; rowptr has M + 1 entries, colidx nnz). */
+int lrfsi_mesh_pattern(lrfsi_mesh_h mesh, int32_t* rowptr_host, int32_t* colidx_host);
+
+/* lrfsi_assemble_affine: at the state x, the values of J0(x), Jmu'(x), Jnu'
+ * on the union pattern and the residual pieces R0(x), Rmu(x), Rnu(x) with
+ *   R(x; mu, nu) = R0 + mu Rmu + nu Rnu,  J(x; mu, nu) = J0 + mu Jmu' + nu Jnu'
+ * (Sec. 3, Eq. (pardep_matrix1) with the reference values mu_s = nu_f = 0;
+ * Sec. 3.4, Eq. (rhs_matrix1): Rmu = A1 x + g_mu(x), Rnu = rho_f A2 x).
+ * FP64, 3 x 3 Gauss quadrature per cell.
+ *   x_dev    : M state (device)
+ *   J3_dev   : nnz x 3 interleaved values (J0, Jmu', Jnu') per CSR entry, or NULL
+ *   R3_dev   : M x 3 row-major (R0, Rmu, Rnu) per row, or NULL
+ * Deterministic (cell colouring, no atomics). */
+int lrfsi_assemble_affine(lrfsi_mesh_h mesh, const double* x_dev, double* J3_dev, double* R3_dev,
+                          lrfsi_stream_t stream);
+
+/* lrfsi_residual_batch: R(X_i; mu_i, nu_i) for m columns (Sec. 2,
+ * Eq. (fsi_problem_weak1); Dirichlet rows X_i - b_D).
+ *   X_dev   : M x m row-major states, leading dimension ldx >= m
+ *   mu_dev, nu_dev : m parameters (device)
+ *   R_dev   : M x m row-major output (ldr >= m), or NULL
+ *   norm2_dev : m squared Euclidean norms of the columns of R, or NULL */
+int lrfsi_residual_batch(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
+                         const double* mu_dev, const double* nu_dev, double* R_dev, int ldr,
+                         double* norm2_dev, lrfsi_stream_t stream);
+
+/* lrfsi_residual: relative residuals of the low-rank approximation
+ * X = x~ 1^T + U V^T (Sec. 5.1.2): ||R(X_i; mu_i, nu_i)||_2 / ||R(b_D; mu_i, nu_i)||_2
+ * for the m columns.
+ *   xt_dev : M;  U_dev : M x r (ldu);  V_dev : m x r (ldv); r may be 0
+ *   relres_host : m outputs (host).  Synchronizes the stream. */
+int lrfsi_residual(lrfsi_mesh_h mesh, const double* xt_dev, const double* U_dev, int ldu,
+                   const double* V_dev, int ldv, int r, const double* mu_dev, const double* nu_dev,
+                   int m, double* relres_host, lrfsi_stream_t stream);
+
+/* lrfsi_newton_median: Newton iteration for K independent problems
+ * (Sec. 3.2, Eq. (newton_step_indiv1)), batched: every iteration assembles
+ * J(x_k; mu_k, nu_k), R(x_k; mu_k, nu_k), factors all K Jacobians with the
+ * block-tridiagonal FP64 LU and solves.  Stops a problem when ||R||_2 <= eps
+ * (absolute, as in Algorithm 1).  If the full step raises the residual norm the
+ * step is halved (up to 8 times).
+ *   X_dev   : K x M states (problem k at X_dev + k*M); in: start, out: result
+ *   mu_host, nu_host : K parameters
+ *   iters_host, res_host : K outputs (iterations, final residual norm), or NULL
+ * Returns LRFSI_ENOCONV if a problem did not reach eps in max_it iterations
+ * (its best iterate is left in X). */
+int lrfsi_newton_median(lrfsi_mesh_h mesh, int K, double* X_dev, const double* mu_host,
+                        const double* nu_host, double eps, int max_it, int* iters_host,
+                        double* res_host, lrfsi_stream_t stream);
+
+/* Options of the truncated Chebyshev iteration. */
+typedef struct {
+  double c, d;        /* half-width and centre of the spectrum of P^{-1} A (Sec. 5.1.1) */
+  int iters;          /* steps per cycle (paper: 6) */
+  int cycles;         /* 1 + restarts (paper: 2) */
+  int rank_cap;       /* R: maximal rank kept by the truncation */
+  double tol;         /* truncation: keep the smallest r with ||s_{>r}|| <= tol ||s|| */
+  double eta;         /* stop when ||B - F(S)||_F <= eta ||B||_F (0: run all steps) */
+  int precision;      /* 0: FP64; 1: mixed (FP32 SpMM and updates, FP64 truncation/LU) */
+} lrfsi_cheb_options;
+
+typedef struct {
+  int steps;              /* Chebyshev steps taken */
+  int rank;               /* rank of the returned S */
+  double rel_lin_res;     /* ||B - F(S)||_F / ||B||_F at the last evaluation */
+  int max_concat_rank;    /* largest rank fed to a truncation */
+} lrfsi_cheb_stats;
+
+typedef struct lrfsi_subset_s* lrfsi_subset_h;
+
+/* A subset handle holds K >= 1 subsets I_1..I_K (Sec. 3.3, Eq. (clustering1));
+ * every operation below advances all K subsets together in batched kernels.
+ * Subset k owns m_k consecutive entries of the concatenated parameter arrays
+ * (offset o_k = m_1 + ... + m_{k-1}).  Per-subset tall outputs are stacked:
+ * subset k's M x ld block starts at ptr + k * M * ld; per-subset V blocks are
+ * stacked by rows: subset k's m_k x ldv block starts at ptr + o_k * ldv. */
+
+/* lrfsi_subset_create: operators and preconditioners of K subsets (Sec. 3.4
+ * and Sec. 4.2) at their linearisation points xt_k (the upper-median Newton
+ * solutions): assembles J0, Jmu', Jnu', R0, Rmu, Rnu at xt_k and factors
+ * P_k = J(xt_k; mu_bar_k, nu_bar_k) with the block-tridiagonal FP64 LU,
+ * mu_bar_k / nu_bar_k the midpoints of the subset's parameter ranges.
+ *   xt_dev        : K x M linearisation points (device, row k at xt_dev + k*M)
+ *   mu_host, nu_host : sum m_k parameters, subsets consecutive
+ *   m_host        : K subset sizes (m_k >= 1)
+ *   rank_cap_host : K rank capacities R_k (1 <= R_k)
+ * Errors: LRFSI_EINVAL on bad sizes, LRFSI_ESINGULAR if an LU pivot is zero. */
+int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt_dev, const double* mu_host,
+                        const double* nu_host, const int* m_host, const int* rank_cap_host,
+                        lrfsi_subset_h* out, lrfsi_stream_t stream);
+int lrfsi_subset_destroy(lrfsi_subset_h sub);
+
+/* lrfsi_chebyshevT: solve F_k(S_k) = B_k for every subset on the factors
+ * (B_k = UB_k VB_k^T) with the truncated preconditioned Chebyshev iteration
+ * (the paper's ChebyshevT; recurrence: centre d, half-width c, left
+ * preconditioning by P_k, truncation after every update of the iterate, the
+ * residual before preconditioning and the direction; restart = new cycle).
+ *   UB_dev : K stacked M x lduB blocks;  VB_dev : stacked m_k x ldvB blocks
+ *   rB_host: K right-hand-side ranks (1 <= rB_k <= lduB, ldvB)
+ *   U_dev  : K stacked M x ldu output blocks (ldu >= R_k)
+ *   V_dev  : stacked m_k x ldv output blocks (ldv >= R_k)
+ *   rank_host : K output ranks r_k (S_k = U_k[:, :r_k] V_k[:, :r_k]^T)
+ *   stats  : K entries or NULL */
+int lrfsi_chebyshevT(lrfsi_subset_h sub, const double* UB_dev, int lduB, const double* VB_dev,
+                     int ldvB, const int* rB_host, const lrfsi_cheb_options* opt, double* U_dev,
+                     int ldu, double* V_dev, int ldv, int* rank_host, lrfsi_cheb_stats* stats,
+                     lrfsi_stream_t stream);
+
+/* lrfsi_subset_step: one Newton step on every subset (Sec. 3.4,
+ * Eq. (rhs_matrix1), Eq. (newton_matrix1)): B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T),
+ * S_k = ChebyshevT(B_k); then, while some column's relative residual exceeds
+ * target and fewer than max_outer corrections were taken, a correction in the
+ * same matrix form whose right-hand side is -R(X_i; mu_i, nu_i) evaluated
+ * column by column (operators and preconditioners kept at xt_k; the sum of
+ * corrections is truncated with the same rule).  Result per subset:
+ * X_k = xt_k 1^T + U_k V_k^T of rank r_k.
+ *   relres_host : sum m_k final relative residuals (Sec. 5.1.2), or NULL
+ *   outer_host  : K correction counts, or NULL
+ * Returns LRFSI_ENOCONV if target > 0 was not reached by every column. */
+int lrfsi_subset_step(lrfsi_subset_h sub, const lrfsi_cheb_options* opt, double target,
+                      int max_outer, double* U_dev, int ldu, double* V_dev, int ldv,
+                      int* rank_host, double* relres_host, int* outer_host,
+                      lrfsi_stream_t stream);
+
+/* lrfsi_precond_apply: Y_k = P_k^{-1} X_k with the factored mean-based
+ * preconditioner of subset k (Sec. 4.2), for r_k columns.
+ *   X_dev : K stacked M x ldx blocks (not modified);  Y_dev : K stacked M x ldy
+ *   r_host: K column counts (0 <= r_k <= min(ldx, ldy, rank capacity + m_k)) */
+int lrfsi_precond_apply(lrfsi_subset_h sub, const double* X_dev, int ldx, const int* r_host,
+                        double* Y_dev, int ldy, lrfsi_stream_t stream);
+
+/* lrfsi_truncate: the truncation operator T (Sec. 5: for an order-2 tensor
+ * the best rank-<=R approximation in the Frobenius norm, Eckart-Young) of
+ * X_k V_k^T for every subset: keep the smallest rank r with
+ * ||s_{>r}||_2 <= tol ||s||_2, at most cap_k; returns U_k (orthonormal columns)
+ * and V_k (carrying the singular values) with X_k V_k^T ~ U_k V_k^T.  The
+ * inputs are used as given (no equilibration).
+ *   X_dev : K stacked M x ldx blocks;  V_dev : stacked m_k x ldv blocks
+ *   p_host: K input ranks (1 <= p_k <= ldx, ldv, internal capacity)
+ *   U_dev : K stacked M x ldu;  Vo_dev : stacked m_k x ldvo;  rank_host: K */
+int lrfsi_truncate(lrfsi_subset_h sub, const double* X_dev, int ldx, const double* V_dev, int ldv,
+                   const int* p_host, double tol, const int* cap_host, double* U_dev, int ldu,
+                   double* Vo_dev, int ldvo, int* rank_host, lrfsi_stream_t stream);
+
+/* Device memory held by a handle (bytes). */
+size_t lrfsi_mesh_bytes(lrfsi_mesh_h mesh);
+size_t lrfsi_subset_bytes(lrfsi_subset_h sub);
+
+/* Number of kernels this library has launched in the calling process. */
+uint64_t lrfsi_kernel_launches(void);
+
+const char* lrfsi_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRFSI_H */

@@ -56,11 +56,11 @@ def subset_step(mesh, xt, mu_k, nu_k, opt: Options, X0=None, history=None):
     J0, Jmu, Jnu = fsi.affine_jacobian(mesh, xt)
     R0, Rmu, Rnu = fsi.affine_residual(mesh, xt)
     mu_bar, nu_bar = params.midpoint_parameters(mu_k, nu_k)
-    P = lowrank.preconditioner(J0, Jmu, Jnu, mu_bar, nu_bar)
     B = lowrank.rhs(R0, Rmu, Rnu, mu_k, nu_k)
-    run = lambda B_: lowrank.chebyshev_T(J0, Jmu, Jnu, P, B_, mu_k, nu_k, opt.c, opt.d,
-                                         opt.iters, opt.cycles, opt.tol, opt.rank_cap,
-                                         opt.truncated, opt.eta, history)
+    run = lambda B_: lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B_, mu_k, nu_k, mu_bar, nu_bar, opt.c, opt.d,
+                                                iters=opt.iters, cycles=opt.cycles, tol=opt.tol,
+                                                rank_cap=opt.rank_cap, truncated=opt.truncated,
+                                                eta=opt.eta, history=history)
     X = xt[:, None] + run(B)
     for _ in range(opt.chord_steps):
         Bc = -np.stack([fsi.residual(mesh, X[:, i], mu_k[i], nu_k[i]) for i in range(len(mu_k))], axis=1)

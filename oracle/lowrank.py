@@ -30,6 +30,7 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 from __future__ import annotations
 
 import numpy as np
+import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from . import fsi
@@ -126,6 +127,36 @@ def chebyshev_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, c, d, iters=6, cycles=2,
     if history is not None:
         history.append(np.linalg.norm(B - F(S)) / nB)
     return S
+
+
+def equilibration(J0, Jmu, Jnu, mu_bar, nu_bar):
+    """Row and column scales (r, c) of the max-norm equilibration of the
+    preconditioner matrix P = J0 + mu_bar Jmu' + nu_bar Jnu':
+        r_i = 1 / max_j |P_ij|,   c_j = 1 / max_i r_i |P_ij|
+    so that diag(r) P diag(c) has unit max-norm in every row and column.
+    Reading (not in the paper): the truncation operator is applied to the
+    equilibrated quantities -- the unknowns mix m/s, m and Pa and the
+    equations mix fluid and solid (mu ~ 1e6) scales, so an unscaled Euclidean
+    truncation discards the deformation components that dominate F(S)."""
+    P = (J0 + mu_bar * Jmu + nu_bar * Jnu).tocsr()
+    A = abs(P)
+    rmax = A.max(axis=1).toarray().ravel()
+    r = np.where(rmax > 0, 1.0 / np.where(rmax > 0, rmax, 1.0), 1.0)
+    cmax = (sp.diags(r) @ A).max(axis=0).toarray().ravel()
+    c = np.where(cmax > 0, 1.0 / np.where(cmax > 0, cmax, 1.0), 1.0)
+    return r, c
+
+
+def chebyshev_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, c, d, **kw):
+    """ChebyshevT on the equilibrated equation diag(r) F(diag(c) S~) = diag(r) B
+    with the equilibrated preconditioner; returns S = diag(c) S~.  The
+    spectrum of P^{-1} A is unchanged (similarity), so c and d are too."""
+    r, cc = equilibration(J0, Jmu, Jnu, mu_bar, nu_bar)
+    Dr, Dc = sp.diags(r), sp.diags(cc)
+    J0s, Jmus, Jnus = (Dr @ J0 @ Dc).tocsr(), (Dr @ Jmu @ Dc).tocsr(), (Dr @ Jnu @ Dc).tocsr()
+    P = preconditioner(J0s, Jmus, Jnus, mu_bar, nu_bar)
+    Ss = chebyshev_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, c, d, **kw)
+    return cc[:, None] * Ss
 
 
 def spectrum_interval(J0, Jmu, Jnu, P_lu, mu_pts, nu_pts):

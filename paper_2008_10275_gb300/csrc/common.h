@@ -1,0 +1,76 @@
+// Internal helpers shared by the lrfsi translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/lrfsi.h"
+
+namespace lrfsi {
+
+// ---- error reporting -------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define LRFSI_CUDA(call)                                        \
+  do {                                                          \
+    cudaError_t e_ = (call);                                    \
+    if (e_ != cudaSuccess) return ::lrfsi::cuda_fail(e_, #call); \
+  } while (0)
+
+#define LRFSI_TRY(call)              \
+  do {                               \
+    int s_ = (call);                 \
+    if (s_ != LRFSI_OK) return s_;   \
+  } while (0)
+
+// every kernel launch goes through count_launch() so that the process-wide
+// launch counter (lrfsi_kernel_launches) is exact
+void count_launch(uint64_t n = 1);
+inline int check_launch(const char* name) {
+  count_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, name);
+  return LRFSI_OK;
+}
+
+// ---- device buffers --------------------------------------------------------
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count) {
+    release();
+    if (count == 0) return LRFSI_OK;
+    cudaError_t e = cudaMalloc((void**)&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return fail(LRFSI_ENOMEM, std::string("cudaMalloc failed: ") + cudaGetErrorString(e));
+    }
+    n = count;
+    return LRFSI_OK;
+  }
+  int upload(const std::vector<T>& h, cudaStream_t s = 0) {
+    LRFSI_TRY(alloc(h.size()));
+    if (!h.empty()) LRFSI_CUDA(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+    return LRFSI_OK;
+  }
+  size_t bytes() const { return n * sizeof(T); }
+};
+
+inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace lrfsi

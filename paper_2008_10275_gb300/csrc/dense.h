@@ -1,0 +1,60 @@
+// Dense linear algebra building blocks (FP64 unless templated).
+#pragma once
+
+#include "common.h"
+
+namespace lrfsi {
+
+// C(i,j) = alpha * sum_l A(i,l) B(l,j) + beta * C(i,j), element (i,j) of X at
+// X.p[i * X.rs + j * X.cs].  beta == 0 never reads C.
+template <class T>
+struct GemmDesc {
+  int m, n, k;
+  const T* A; long a_rs, a_cs;
+  const T* B; long b_rs, b_cs;
+  T* C; long c_rs, c_cs;
+  T alpha, beta;
+};
+constexpr int kMaxGemmDescs = 32;
+template <class T>
+int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s);
+
+// Batched tall Gram G_b = A_b^T B_b (p_b x q_b, row-major ldg) with
+// A_b: M x p_b (row-major, lda), B_b: M x q_b (ldb); split over rows and
+// reduced in fixed order.  work must hold nbatch * nsplit * pmax * qmax doubles.
+struct GramDesc {
+  const double* A; int lda, p;
+  const double* B; int ldb, q;
+  double* G; int ldg;
+};
+int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t work_len, cudaStream_t s);
+size_t gram_work_len(int nbatch, long M, int pmax, int qmax);
+
+// Truncation helpers, one CTA per problem (see dense.cu for the algorithm).
+struct TruncDesc {
+  // inputs
+  int p;             // concatenated rank
+  int m;             // parameter-side rows
+  const double* Vc;  // m x p row-major (ldv)
+  int ldv;
+  double* G;         // p x p Gram of the tall factor (in: X^T X), workspace afterwards
+  double* G2;        // p x p Gram of Q1 (filled between the two passes)
+  double* T1;        // p x p: Q1 = X T1 after pass 1; final tall coefficients after the SVD (ld p)
+  double* T2;        // p x p: inverse Cholesky factor of the latest QR pass (ld p)
+  double* Vout;      // m x rank output (row-major, ldvo)
+  int ldvo;
+  double* work;      // scratch for the small SVD (>= trunc_small_work(p, m) doubles)
+  int* iwork;        // >= 2 p ints
+  int* info;         // [0] k (kept after pass 1), [1] rank, [2] status, [3] sweeps, [4] needs another QR pass
+  double* sv;        // >= p singular values (descending)
+  double* frob2;     // output: squared Frobenius norm of the input product (sum of s^2)
+  double tol;        // relative Frobenius truncation tolerance
+  int rank_cap;
+  double drop;       // pass-1 pivot threshold on the unit-diagonal Gram
+};
+size_t trunc_small_work(int p, int m);
+int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev);
+int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev);
+int trunc_svd(int n, cudaStream_t s, TruncDesc* d_dev);
+
+}  // namespace lrfsi

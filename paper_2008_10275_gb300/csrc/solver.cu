@@ -1,0 +1,1158 @@
+// The C ABI: mesh handles, assembly, batched residuals, the batched median
+// Newton iteration (Sec. 3.2), and the subset Newton step solved on factors by
+// the truncated preconditioned Chebyshev iteration (Sec. 3.4, Sec. 4.2,
+// Algorithm 1).
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+
+#include "dense.h"
+#include "mesh.h"
+#include "sparse_lu.h"
+
+namespace lrfsi {
+
+// ---------------------------------------------------------------------------
+// errors and launch counting
+// ---------------------------------------------------------------------------
+static thread_local std::string g_err;
+static std::atomic<uint64_t> g_launches{0};
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  g_err = std::string(what) + ": " + cudaGetErrorString(e);
+  return LRFSI_ECUDA;
+}
+void count_launch(uint64_t n) { g_launches += n; }
+
+// ---------------------------------------------------------------------------
+// small helper kernels
+// ---------------------------------------------------------------------------
+struct CopyDesc {
+  const double* src;  // mode 0
+  long lds;
+  double* dst;
+  long ldd;
+  long rows;
+  int ncols;
+  int mode;            // 0: copy, 1: fill alpha * rowscale, 2: alpha * identity
+  const double* rowscale;
+  double alpha;
+};
+struct CopyBatch {
+  CopyDesc d[kMaxGemmDescs];
+};
+
+__global__ void k_blockcopy(CopyBatch cb) {
+  const CopyDesc& d = cb.d[blockIdx.y];
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.rows * d.ncols) return;
+  const long i = e / d.ncols;
+  const int j = (int)(e % d.ncols);
+  double v;
+  if (d.mode == 0) v = d.src[i * d.lds + j];
+  else if (d.mode == 1) v = 1.0;
+  else v = (i == j) ? 1.0 : 0.0;
+  if (d.rowscale) v *= d.rowscale[i];
+  d.dst[i * d.ldd + j] = d.alpha * v;
+}
+
+static int copy_batched(const std::vector<CopyDesc>& v, cudaStream_t s) {
+  for (size_t base = 0; base < v.size(); base += kMaxGemmDescs) {
+    CopyBatch cb;
+    int cnt = 0;
+    long mx = 0;
+    for (size_t i = base; i < v.size() && cnt < kMaxGemmDescs; ++i) {
+      if (v[i].rows <= 0 || v[i].ncols <= 0) continue;
+      cb.d[cnt++] = v[i];
+      mx = std::max(mx, v[i].rows * v[i].ncols);
+    }
+    if (!cnt) continue;
+    k_blockcopy<<<dim3(ceil_div(mx, 256), cnt), 256, 0, s>>>(cb);
+    LRFSI_TRY(check_launch("k_blockcopy"));
+  }
+  return LRFSI_OK;
+}
+
+// problem-major (K x M) <-> column-major states (M x K row-major)
+__global__ void k_transpose(const double* __restrict__ A, long rows, int cols, double* __restrict__ B) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= rows * cols) return;
+  const long i = e / cols;
+  const int j = (int)(e % cols);
+  B[(size_t)j * rows + i] = A[e];
+}
+
+// X[:, j] = Xold[:, j] + t[j] * dX[:, j]  (M x K row-major)
+__global__ void k_newton_update(const double* __restrict__ Xold, const double* __restrict__ dX,
+                                const double* __restrict__ t, long M, int K, double* __restrict__ X) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * K) return;
+  const int j = (int)(e % K);
+  X[e] = Xold[e] + t[j] * dX[e];
+}
+
+// Jacobian values at column j of an M x K state matrix: gather to a vector first
+__global__ void k_gather_col(const double* __restrict__ X, long M, int K, int j, double* __restrict__ x) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) x[i] = X[i * K + j];
+}
+
+// Max-norm equilibration of P = J0 + a Jmu' + b Jnu' (values nnz x 3):
+// r_i = 1 / max_j |P_ij|, c_j = 1 / max_i r_i |P_ij|.
+__global__ void k_equil_rows(const double* __restrict__ J3, const int* __restrict__ rowptr, long M, double a,
+                             double b, double* __restrict__ r) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double mx = 0;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k)
+    mx = fmax(mx, fabs(J3[3 * (size_t)k] + a * J3[3 * (size_t)k + 1] + b * J3[3 * (size_t)k + 2]));
+  r[i] = mx > 0 ? 1.0 / mx : 1.0;
+}
+__global__ void k_equil_colmax(const double* __restrict__ J3, const int* __restrict__ rowptr,
+                               const int* __restrict__ colidx, long M, double a, double b,
+                               const double* __restrict__ r, unsigned long long* __restrict__ cmax) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+    const double v = r[i] * fabs(J3[3 * (size_t)k] + a * J3[3 * (size_t)k + 1] + b * J3[3 * (size_t)k + 2]);
+    atomicMax(cmax + colidx[k], (unsigned long long)__double_as_longlong(v));  // v >= 0: bit order = value order
+  }
+}
+__global__ void k_equil_cols(const unsigned long long* __restrict__ cmax, long M, double* __restrict__ c) {
+  const long j = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= M) return;
+  const double v = __longlong_as_double((long long)cmax[j]);
+  c[j] = v > 0 ? 1.0 / v : 1.0;
+}
+__global__ void k_scale_vals(double* __restrict__ J3, const int* __restrict__ rowptr, const int* __restrict__ colidx,
+                             long M, const double* __restrict__ r, const double* __restrict__ c) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  for (int k = rowptr[i]; k < rowptr[i + 1]; ++k) {
+    const double sc = r[i] * c[colidx[k]];
+    J3[3 * (size_t)k] *= sc;
+    J3[3 * (size_t)k + 1] *= sc;
+    J3[3 * (size_t)k + 2] *= sc;
+  }
+}
+// X[i, o + j] = x0[i] + s[i] * X[i, o + j]
+__global__ void k_affine_cols(double* __restrict__ X, long ld, int o, int ncols, const double* __restrict__ x0,
+                              const double* __restrict__ sc, long M) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * ncols) return;
+  const long i = e / ncols;
+  const int j = (int)(e % ncols);
+  double* p = X + i * ld + o + j;
+  *p = x0[i] + sc[i] * *p;
+}
+
+}  // namespace lrfsi
+
+using namespace lrfsi;
+
+// ---------------------------------------------------------------------------
+// mesh API
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char* lrfsi_last_error(void) { return g_err.c_str(); }
+uint64_t lrfsi_kernel_launches(void) { return g_launches.load(); }
+
+int lrfsi_mesh_create(const lrfsi_problem* prob, lrfsi_mesh_h* out) {
+  if (!prob || !out) return fail(LRFSI_EINVAL, "lrfsi_mesh_create: null argument");
+  *out = nullptr;
+  lrfsi_mesh_s* m = new (std::nothrow) lrfsi_mesh_s();
+  if (!m) return fail(LRFSI_ENOMEM, "lrfsi_mesh_create: host allocation");
+  int st = build_mesh(*prob, m->h);
+  if (st == LRFSI_OK) st = m->rowptr.upload(m->h.rowptr);
+  if (st == LRFSI_OK) st = m->colidx.upload(m->h.colidx);
+  if (st == LRFSI_OK) st = m->cell_dof.upload(m->h.cell_dof);
+  if (st == LRFSI_OK) st = m->cell_row.upload(m->h.cell_row);
+  if (st == LRFSI_OK) st = m->slot.upload(m->h.slot);
+  if (st == LRFSI_OK) st = m->color_cells.upload(m->h.color_cells);
+  if (st == LRFSI_OK) st = m->ident_rows.upload(m->h.ident_rows);
+  if (st == LRFSI_OK) st = m->ident_diag.upload(m->h.ident_diag);
+  if (st == LRFSI_OK) st = m->cell_solid.upload(m->h.cell_solid);
+  if (st == LRFSI_OK) st = m->bD.upload(m->h.bD);
+  if (st == LRFSI_OK) st = m->dense_off.upload(m->h.dense_off);
+  if (st == LRFSI_OK) {
+    std::vector<long long> so(m->h.slab_off.begin(), m->h.slab_off.end());
+    st = m->slab_off.upload(so);
+  }
+  if (st == LRFSI_OK) {
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) st = cuda_fail(e, "lrfsi_mesh_create upload");
+  }
+  if (st != LRFSI_OK) {
+    delete m;
+    return st;
+  }
+  // the slot map is only needed on the device
+  std::vector<int>().swap(m->h.slot);
+  *out = m;
+  return LRFSI_OK;
+}
+
+int lrfsi_mesh_destroy(lrfsi_mesh_h m) {
+  delete m;
+  return LRFSI_OK;
+}
+
+int lrfsi_mesh_info(lrfsi_mesh_h m, lrfsi_mesh_info_t* info) {
+  if (!m || !info) return fail(LRFSI_EINVAL, "lrfsi_mesh_info: null argument");
+  info->M = m->h.M;
+  info->nnz = (int64_t)m->h.colidx.size();
+  info->nslab = m->h.nslab;
+  info->nmax = m->h.nmax;
+  info->ncell = m->h.ncell;
+  info->nsolid = m->h.nsolid;
+  return LRFSI_OK;
+}
+
+int lrfsi_mesh_dofmap(lrfsi_mesh_h m, int32_t* field, int32_t* ix, int32_t* iy) {
+  if (!m) return fail(LRFSI_EINVAL, "lrfsi_mesh_dofmap: null mesh");
+  if (field) std::memcpy(field, m->h.dof_field.data(), sizeof(int32_t) * m->h.M);
+  if (ix) std::memcpy(ix, m->h.dof_ix.data(), sizeof(int32_t) * m->h.M);
+  if (iy) std::memcpy(iy, m->h.dof_iy.data(), sizeof(int32_t) * m->h.M);
+  return LRFSI_OK;
+}
+
+int lrfsi_mesh_dirichlet(lrfsi_mesh_h m, double* bD) {
+  if (!m || !bD) return fail(LRFSI_EINVAL, "lrfsi_mesh_dirichlet: null argument");
+  std::memcpy(bD, m->h.bD.data(), sizeof(double) * m->h.M);
+  return LRFSI_OK;
+}
+
+int lrfsi_mesh_pattern(lrfsi_mesh_h m, int32_t* rowptr, int32_t* colidx) {
+  if (!m) return fail(LRFSI_EINVAL, "lrfsi_mesh_pattern: null mesh");
+  if (rowptr) std::memcpy(rowptr, m->h.rowptr.data(), sizeof(int32_t) * (m->h.M + 1));
+  if (colidx) std::memcpy(colidx, m->h.colidx.data(), sizeof(int32_t) * m->h.colidx.size());
+  return LRFSI_OK;
+}
+
+size_t lrfsi_mesh_bytes(lrfsi_mesh_h m) {
+  if (!m) return 0;
+  return m->rowptr.bytes() + m->colidx.bytes() + m->cell_dof.bytes() + m->cell_row.bytes() + m->slot.bytes() +
+         m->color_cells.bytes() + m->ident_rows.bytes() + m->ident_diag.bytes() + m->cell_solid.bytes() +
+         m->bD.bytes() + m->dense_off.bytes() + m->slab_off.bytes();
+}
+
+int lrfsi_assemble_affine(lrfsi_mesh_h m, const double* x, double* J3, double* R3, lrfsi_stream_t stream) {
+  if (!m || !x) return fail(LRFSI_EINVAL, "lrfsi_assemble_affine: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (J3) LRFSI_TRY(launch_jacobian(m, x, J3, s));
+  if (R3) {
+    // columns (rest, mu, nu) = (1,0,0), (0,1,0), (0,0,1)
+    static const double h_coef[9] = {1, 0, 0, 0, 1, 0, 0, 0, 1};
+    DevBuf<double> coef;
+    LRFSI_TRY(coef.alloc(9));
+    LRFSI_CUDA(cudaMemcpyAsync(coef.p, h_coef, sizeof(h_coef), cudaMemcpyHostToDevice, s));
+    LRFSI_TRY(launch_residual(m, x, 0, 3, coef.p, coef.p + 3, coef.p + 6, R3, 3, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));  // coef is freed on return
+  }
+  return LRFSI_OK;
+}
+
+int lrfsi_residual_batch(lrfsi_mesh_h m, const double* X, int ldx, int ncol, const double* mu, const double* nu,
+                         double* R, int ldr, double* norm2, lrfsi_stream_t stream) {
+  if (!m || !X || !mu || !nu || ncol < 0 || ldx < ncol) return fail(LRFSI_EINVAL, "lrfsi_residual_batch: bad argument");
+  if (ncol == 0) return LRFSI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf<double> tmp, work;
+  double* Rp = R;
+  int ld = ldr;
+  if (!Rp) {
+    LRFSI_TRY(tmp.alloc((size_t)m->h.M * ncol));
+    Rp = tmp.p;
+    ld = ncol;
+  } else if (ldr < ncol) {
+    return fail(LRFSI_EINVAL, "lrfsi_residual_batch: ldr < ncol");
+  }
+  LRFSI_TRY(launch_residual(m, X, ldx, ncol, nullptr, mu, nu, Rp, ld, s));
+  if (norm2) {
+    size_t wl = (size_t)ceil_div(m->h.M, 256) * ncol;
+    LRFSI_TRY(work.alloc(wl));
+    LRFSI_TRY(launch_colnorm2(Rp, m->h.M, ncol, ld, norm2, work.p, wl, s));
+  }
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// internal: relative residuals of dense columns
+// ---------------------------------------------------------------------------
+namespace lrfsi {
+
+struct ResidualCtx {
+  DevBuf<double> R, norm2, norm2_bD, work;
+  long M = 0;
+  int ncol = 0;
+  int init(long M_, int ncol_) {
+    M = M_;
+    ncol = ncol_;
+    LRFSI_TRY(R.alloc((size_t)M * ncol));
+    LRFSI_TRY(norm2.alloc(ncol));
+    LRFSI_TRY(norm2_bD.alloc(ncol));
+    LRFSI_TRY(work.alloc((size_t)ceil_div(M, 256) * ncol));
+    return LRFSI_OK;
+  }
+};
+
+// ||R(b_D; mu, nu)||^2 per column (denominator of the relative residual)
+static int residual_bD_norms(lrfsi_mesh_s* m, ResidualCtx& c, const double* mu, const double* nu, cudaStream_t s) {
+  LRFSI_TRY(launch_residual(m, m->bD.p, 0, c.ncol, nullptr, mu, nu, c.R.p, c.ncol, s));
+  return launch_colnorm2(c.R.p, m->h.M, c.ncol, c.ncol, c.norm2_bD.p, c.work.p, c.work.n, s);
+}
+
+}  // namespace lrfsi
+
+extern "C" int lrfsi_residual(lrfsi_mesh_h m, const double* xt, const double* U, int ldu, const double* V, int ldv,
+                              int r, const double* mu, const double* nu, int ncol, double* relres,
+                              lrfsi_stream_t stream) {
+  if (!m || !xt || !mu || !nu || !relres || ncol < 1 || r < 0 || (r > 0 && (!U || !V || ldu < r || ldv < r)))
+    return fail(LRFSI_EINVAL, "lrfsi_residual: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long M = m->h.M;
+  DevBuf<double> X;
+  LRFSI_TRY(X.alloc((size_t)M * ncol));
+  std::vector<CopyDesc> cd(1);
+  cd[0] = CopyDesc{xt, 1, X.p, ncol, M, 1, 0, nullptr, 1.0};
+  // broadcast xt into every column: copy column 0 then use ldx trick per column
+  for (int j = 0; j < ncol; ++j) {
+    cd[0].dst = X.p + j;
+    LRFSI_TRY(copy_batched(cd, s));
+  }
+  if (r > 0) {
+    GemmDesc<double> g{(int)M, ncol, r, U, ldu, 1, V, 1, ldv, X.p, ncol, 1, 1.0, 1.0};
+    LRFSI_TRY(gemm_grouped<double>(&g, 1, s));
+  }
+  ResidualCtx c;
+  LRFSI_TRY(c.init(M, ncol));
+  LRFSI_TRY(residual_bD_norms(m, c, mu, nu, s));
+  LRFSI_TRY(launch_residual(m, X.p, ncol, ncol, nullptr, mu, nu, c.R.p, ncol, s));
+  LRFSI_TRY(launch_colnorm2(c.R.p, M, ncol, ncol, c.norm2.p, c.work.p, c.work.n, s));
+  std::vector<double> a(ncol), b(ncol);
+  LRFSI_CUDA(cudaMemcpyAsync(a.data(), c.norm2.p, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaMemcpyAsync(b.data(), c.norm2_bD.p, sizeof(double) * ncol, cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  for (int j = 0; j < ncol; ++j) relres[j] = b[j] > 0 ? std::sqrt(a[j] / b[j]) : std::sqrt(a[j]);
+  return LRFSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batched Newton iteration for independent problems (median solutions)
+// ---------------------------------------------------------------------------
+extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h,
+                                   double eps, int max_it, int* iters_h, double* res_h, lrfsi_stream_t stream) {
+  if (!m || !Xpm || !mu_h || !nu_h || K < 1 || K > kMaxGemmDescs || max_it < 0)
+    return fail(LRFSI_EINVAL, "lrfsi_newton_median: bad argument (1 <= K <= 32)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long M = m->h.M;
+  const long nnz = (long)m->h.colidx.size();
+  DevBuf<double> X, Xold, dX, Rb, J3, xcol, tdev, mu, nu, work, norm2;
+  LRFSI_TRY(X.alloc((size_t)M * K));
+  LRFSI_TRY(Xold.alloc((size_t)M * K));
+  LRFSI_TRY(dX.alloc((size_t)M * K));
+  LRFSI_TRY(Rb.alloc((size_t)M * K));
+  LRFSI_TRY(J3.alloc((size_t)3 * nnz * K));
+  LRFSI_TRY(xcol.alloc(M));
+  LRFSI_TRY(tdev.alloc(K));
+  LRFSI_TRY(mu.alloc(K));
+  LRFSI_TRY(nu.alloc(K));
+  LRFSI_TRY(norm2.alloc(K));
+  LRFSI_TRY(work.alloc((size_t)ceil_div(M, 256) * K));
+  LRFSI_CUDA(cudaMemcpyAsync(mu.p, mu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  LRFSI_CUDA(cudaMemcpyAsync(nu.p, nu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  k_transpose<<<ceil_div(M * K, 256), 256, 0, s>>>(Xpm, K, (int)M, X.p);  // (K x M) -> (M x K)
+  LRFSI_TRY(check_launch("k_transpose"));
+  BlockLU lu;
+  LRFSI_TRY(blocklu_alloc(m, K, lu));
+  auto norms = [&](const double* Xs, std::vector<double>& out) -> int {
+    LRFSI_TRY(launch_residual(m, Xs, K, K, nullptr, mu.p, nu.p, Rb.p, K, s));
+    LRFSI_TRY(launch_colnorm2(Rb.p, M, K, K, norm2.p, work.p, work.n, s));
+    out.resize(K);
+    LRFSI_CUDA(cudaMemcpyAsync(out.data(), norm2.p, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    for (auto& v : out) v = std::sqrt(v);
+    return LRFSI_OK;
+  };
+  std::vector<double> r, rn, t(K, 1.0);
+  std::vector<int> it(K, 0);
+  LRFSI_TRY(norms(X.p, r));
+  int status = LRFSI_OK;
+  for (int iter = 0; iter < max_it; ++iter) {
+    std::vector<int> act;
+    for (int k = 0; k < K; ++k)
+      if (!(r[k] <= eps)) act.push_back(k);
+    if (act.empty()) break;
+    // residual at the current iterate (Rb holds it for every column after norms())
+    LRFSI_TRY(launch_residual(m, X.p, K, K, nullptr, mu.p, nu.p, Rb.p, K, s));
+    std::vector<const double*> J3p;
+    std::vector<double> al, be;
+    for (int k : act) {
+      k_gather_col<<<ceil_div(M, 256), 256, 0, s>>>(X.p, M, K, k, xcol.p);
+      LRFSI_TRY(check_launch("k_gather_col"));
+      double* Jk = J3.p + (size_t)3 * nnz * J3p.size();
+      LRFSI_TRY(launch_jacobian(m, xcol.p, Jk, s));
+      J3p.push_back(Jk);
+      al.push_back(mu_h[k]);
+      be.push_back(nu_h[k]);
+    }
+    const int na = (int)act.size();
+    LRFSI_TRY(blocklu_factor(m, lu, J3p.data(), al.data(), be.data(), na, s));
+    std::vector<int> lst;
+    LRFSI_TRY(blocklu_status(lu, na, lst, s));
+    for (int a = 0; a < na; ++a)
+      if (lst[a] != 0) status = LRFSI_ESINGULAR;
+    // dX = -J^{-1} R  (negate the residual in place, solve column by column of the M x K block)
+    {
+      std::vector<CopyDesc> cd;
+      cd.push_back(CopyDesc{Rb.p, K, Rb.p, K, M, K, 0, nullptr, -1.0});
+      LRFSI_TRY(copy_batched(cd, s));
+    }
+    LRFSI_CUDA(cudaMemsetAsync(dX.p, 0, sizeof(double) * M * K, s));
+    std::vector<double*> Xs(na), Ys(na);
+    std::vector<int> rr(na, 1);
+    for (int a = 0; a < na; ++a) {
+      Xs[a] = Rb.p + act[a];
+      Ys[a] = dX.p + act[a];
+    }
+    LRFSI_TRY(blocklu_solve(lu, Xs.data(), Ys.data(), rr.data(), K, na, s));
+    LRFSI_CUDA(cudaMemcpyAsync(Xold.p, X.p, sizeof(double) * M * K, cudaMemcpyDeviceToDevice, s));
+    // step with halving while the residual grows
+    std::fill(t.begin(), t.end(), 0.0);
+    for (int k : act) t[k] = 1.0;
+    for (int h = 0; h < 9; ++h) {
+      LRFSI_CUDA(cudaMemcpyAsync(tdev.p, t.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
+      k_newton_update<<<ceil_div(M * K, 256), 256, 0, s>>>(Xold.p, dX.p, tdev.p, M, K, X.p);
+      LRFSI_TRY(check_launch("k_newton_update"));
+      LRFSI_TRY(norms(X.p, rn));
+      bool again = false;
+      for (int k : act) {
+        if (t[k] > 0 && !(rn[k] < r[k]) && h < 8) {
+          t[k] *= 0.5;
+          again = true;
+        }
+      }
+      if (!again) break;
+    }
+    for (int k : act) {
+      r[k] = rn[k];
+      it[k] += 1;
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    if (iters_h) iters_h[k] = it[k];
+    if (res_h) res_h[k] = r[k];
+    if (!(r[k] <= eps) && status == LRFSI_OK) status = LRFSI_ENOCONV;
+  }
+  k_transpose<<<ceil_div(M * K, 256), 256, 0, s>>>(X.p, M, K, Xpm);
+  LRFSI_TRY(check_launch("k_transpose"));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  if (status == LRFSI_ENOCONV) return fail(status, "lrfsi_newton_median: eps not reached within max_it");
+  if (status == LRFSI_ESINGULAR) return fail(status, "lrfsi_newton_median: zero pivot in the block LU");
+  return LRFSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Subsets
+// ---------------------------------------------------------------------------
+struct lrfsi_subset_s {
+  lrfsi_mesh_s* mesh = nullptr;
+  int K = 0;
+  long M = 0;
+  std::vector<int> m, off, cap;
+  int mtot = 0, mmax = 0, Rmax = 0, ldP = 0, ldR = 0;
+  std::vector<double> mu_h, nu_h, mubar, nubar;
+  DevBuf<double> mu, nu, xt, J3, R3;
+  DevBuf<double> rsc, csc;  // K x M equilibration scales (rows, columns)
+  BlockLU lu;
+  DevBuf<double> Xcat, Q1, US, UD, UR, UZ, UB, Ytmp, UC;  // K x M x ld
+  DevBuf<double> Vcat, VS, VD, VR, VB, VC;                // mtot x ld
+  DevBuf<double> G, G2, T1, T2, swork, sv, frob2, gramwork;
+  DevBuf<int> iwork, info;
+  DevBuf<TruncDesc> tdesc;
+  size_t swork_per = 0;
+  // dense columns for the nonlinear residual (M x mtot)
+  DevBuf<double> Xd;
+  ResidualCtx rc;
+  double* tall(DevBuf<double>& b, int k, int ld) { return b.p + (size_t)k * M * ld; }
+  double* vside(DevBuf<double>& b, int k, int ld) { return b.p + (size_t)off[k] * ld; }
+};
+
+namespace lrfsi {
+
+// T([X | ...], [V | ...]) for the listed subsets.  Inputs in Xcat (ld ldP) and
+// Vcat (ld ldP) with p[k] columns; outputs U (tall, ld ldR) and V (ld ldR).
+static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
+                          const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
+                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s) {
+  const int na = (int)act.size();
+  rank.assign(S->K, 0);
+  frob2.assign(S->K, 0.0);
+  if (!na) return LRFSI_OK;
+  const int ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<GramDesc> gd;
+  std::vector<TruncDesc> td(na);
+  for (int a = 0; a < na; ++a) {
+    const int k = act[a];
+    gd.push_back(GramDesc{S->tall(S->Xcat, k, ldP), ldP, p[k], S->tall(S->Xcat, k, ldP), ldP, p[k],
+                          S->G.p + (size_t)k * ldP * ldP, p[k]});
+    TruncDesc& d = td[a];
+    d.p = p[k];
+    d.m = S->m[k];
+    d.Vc = S->vside(S->Vcat, k, ldP);
+    d.ldv = ldP;
+    d.G = S->G.p + (size_t)k * ldP * ldP;
+    d.G2 = S->G2.p + (size_t)k * ldP * ldP;
+    d.T1 = S->T1.p + (size_t)k * ldP * ldP;
+    d.T2 = S->T2.p + (size_t)k * ldP * ldP;
+    d.Vout = Vout[k];
+    d.ldvo = ldR;
+    d.work = S->swork.p + S->swork_per * k;
+    d.iwork = S->iwork.p + (size_t)2 * ldP * k;
+    d.info = S->info.p + 5 * k;
+    d.sv = S->sv.p + (size_t)ldP * k;
+    d.frob2 = S->frob2.p + k;
+    d.tol = tol;
+    d.rank_cap = cap[k];
+    d.drop = 1e-14;
+  }
+  LRFSI_TRY(gram_batched(gd.data(), na, M, S->gramwork.p, S->gramwork.n, s));
+  LRFSI_TRY(trunc_pass1(td.data(), na, s, S->tdesc.p));
+  std::vector<GemmDesc<double>> gm(na);
+  for (int a = 0; a < na; ++a) {
+    const int k = act[a];
+    gm[a] = GemmDesc<double>{(int)M, p[k], p[k], S->tall(S->Xcat, k, ldP), ldP, 1, td[a].T1, p[k], 1,
+                             S->tall(S->Q1, k, ldP), ldP, 1, 1.0, 0.0};
+  }
+  LRFSI_TRY(gemm_grouped<double>(gm.data(), na, s));
+  for (int a = 0; a < na; ++a) {
+    const int k = act[a];
+    gd[a] = GramDesc{S->tall(S->Q1, k, ldP), ldP, p[k], S->tall(S->Q1, k, ldP), ldP, p[k], td[a].G2, p[k]};
+  }
+  LRFSI_TRY(gram_batched(gd.data(), na, M, S->gramwork.p, S->gramwork.n, s));
+  LRFSI_TRY(trunc_qr(na, s, S->tdesc.p));
+  std::vector<int> info((size_t)5 * S->K);
+  auto read_info = [&]() -> int {
+    LRFSI_CUDA(cudaMemcpyAsync(info.data(), S->info.p, sizeof(int) * 5 * S->K, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    return LRFSI_OK;
+  };
+  LRFSI_TRY(read_info());
+  // a third Cholesky-QR pass where the pass-1 basis was far from orthonormal:
+  // Q2 = Q1 R2^{-1} (into Xcat, no longer needed), G3 = Q2^T Q2, R3, Y <- R3 Y
+  std::vector<char> third(S->K, 0);
+  std::vector<TruncDesc> td2;
+  std::vector<GemmDesc<double>> g2;
+  std::vector<GramDesc> gd2;
+  for (int a = 0; a < na; ++a) {
+    const int k = act[a];
+    if (info[5 * k + 2] != 0) return fail(LRFSI_EBREAKDOWN, "truncation: Cholesky-QR breakdown");
+    if (info[5 * k + 4]) {
+      third[k] = 1;
+      const int kk = info[5 * k];
+      g2.push_back(GemmDesc<double>{(int)M, kk, kk, S->tall(S->Q1, k, ldP), ldP, 1, td[a].T2, p[k], 1,
+                                    S->tall(S->Xcat, k, ldP), ldP, 1, 1.0, 0.0});
+      gd2.push_back(GramDesc{S->tall(S->Xcat, k, ldP), ldP, kk, S->tall(S->Xcat, k, ldP), ldP, kk, td[a].G2, p[k]});
+      td2.push_back(td[a]);
+    }
+  }
+  if (!td2.empty()) {
+    LRFSI_TRY(gemm_grouped<double>(g2.data(), (int)g2.size(), s));
+    LRFSI_TRY(gram_batched(gd2.data(), (int)gd2.size(), M, S->gramwork.p, S->gramwork.n, s));
+    LRFSI_CUDA(cudaMemcpyAsync(S->tdesc.p + S->K, td2.data(), sizeof(TruncDesc) * td2.size(), cudaMemcpyHostToDevice, s));
+    LRFSI_TRY(trunc_qr((int)td2.size(), s, S->tdesc.p + S->K));
+  }
+  LRFSI_TRY(trunc_svd(na, s, S->tdesc.p));
+  std::vector<double> f2(S->K);
+  LRFSI_CUDA(cudaMemcpyAsync(f2.data(), S->frob2.p, sizeof(double) * S->K, cudaMemcpyDeviceToHost, s));
+  LRFSI_TRY(read_info());
+  for (int a = 0; a < na; ++a) {
+    const int k = act[a];
+    rank[k] = info[5 * k + 1];
+    frob2[k] = f2[k];
+    if (info[5 * k + 2] == LRFSI_EBREAKDOWN) return fail(LRFSI_EBREAKDOWN, "truncation: Cholesky-QR breakdown");
+    const double* Qlast = third[k] ? S->tall(S->Xcat, k, ldP) : S->tall(S->Q1, k, ldP);
+    gm[a] = GemmDesc<double>{(int)M, rank[k], info[5 * k], Qlast, ldP, 1, td[a].T1, p[k], 1, Uout[k], ldR, 1, 1.0,
+                             0.0};
+  }
+  LRFSI_TRY(gemm_grouped<double>(gm.data(), na, s));
+  return LRFSI_OK;
+}
+
+}  // namespace lrfsi
+
+extern "C" int lrfsi_subset_destroy(lrfsi_subset_h S) {
+  delete S;
+  return LRFSI_OK;
+}
+
+extern "C" size_t lrfsi_subset_bytes(lrfsi_subset_h S) {
+  if (!S) return 0;
+  size_t b = 0;
+  for (DevBuf<double>* p : {&S->mu, &S->nu, &S->xt, &S->J3, &S->R3, &S->rsc, &S->csc, &S->Xcat, &S->Q1, &S->US, &S->UD, &S->UR, &S->UZ,
+                            &S->UB, &S->Ytmp, &S->UC, &S->Vcat, &S->VS, &S->VD, &S->VR, &S->VB, &S->VC, &S->G, &S->G2,
+                            &S->T1, &S->T2, &S->swork, &S->sv, &S->frob2, &S->gramwork, &S->Xd, &S->rc.R,
+                            &S->rc.norm2, &S->rc.norm2_bD, &S->rc.work})
+    b += p->bytes();
+  return b + S->iwork.bytes() + S->info.bytes() + S->tdesc.bytes() + S->lu.bytes();
+}
+
+extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
+                                   const int* m_h, const int* cap_h, lrfsi_subset_h* out, lrfsi_stream_t stream) {
+  if (!mesh || !xt || !mu_h || !nu_h || !m_h || !cap_h || !out || K < 1 || K > kMaxGemmDescs)
+    return fail(LRFSI_EINVAL, "lrfsi_subset_create: bad argument (1 <= K <= 32)");
+  *out = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  lrfsi_subset_s* S = new (std::nothrow) lrfsi_subset_s();
+  if (!S) return fail(LRFSI_ENOMEM, "lrfsi_subset_create: host allocation");
+  std::unique_ptr<lrfsi_subset_s> guard(S);
+  S->mesh = mesh;
+  S->K = K;
+  S->M = mesh->h.M;
+  const long M = S->M;
+  S->m.assign(m_h, m_h + K);
+  S->cap.assign(cap_h, cap_h + K);
+  S->off.assign(K, 0);
+  for (int k = 0; k < K; ++k) {
+    if (S->m[k] < 1 || S->cap[k] < 1) return fail(LRFSI_EINVAL, "lrfsi_subset_create: m_k and R_k must be >= 1");
+    S->off[k] = S->mtot;
+    S->mtot += S->m[k];
+    S->mmax = std::max(S->mmax, S->m[k]);
+    S->Rmax = std::max(S->Rmax, S->cap[k]);
+  }
+  // largest concatenation: residual [B | J0 U | Jmu U | Jnu U] with rank(B) <= max(R, m)
+  S->ldR = std::max(S->Rmax, S->mmax);
+  S->ldP = S->ldR + 3 * S->Rmax + 4;
+  S->mu_h.assign(mu_h, mu_h + S->mtot);
+  S->nu_h.assign(nu_h, nu_h + S->mtot);
+  const long nnz = (long)mesh->h.colidx.size();
+  const int ldP = S->ldP, ldR = S->ldR;
+  LRFSI_TRY(S->mu.upload(S->mu_h, s));
+  LRFSI_TRY(S->nu.upload(S->nu_h, s));
+  LRFSI_TRY(S->xt.alloc((size_t)K * M));
+  LRFSI_CUDA(cudaMemcpyAsync(S->xt.p, xt, sizeof(double) * K * M, cudaMemcpyDeviceToDevice, s));
+  LRFSI_TRY(S->J3.alloc((size_t)K * 3 * nnz));
+  LRFSI_TRY(S->R3.alloc((size_t)K * 3 * M));
+  for (DevBuf<double>* b : {&S->Xcat, &S->Q1}) LRFSI_TRY(b->alloc((size_t)K * M * ldP));
+  for (DevBuf<double>* b : {&S->US, &S->UD, &S->UR, &S->UZ, &S->UB, &S->Ytmp, &S->UC})
+    LRFSI_TRY(b->alloc((size_t)K * M * ldR));
+  LRFSI_TRY(S->Vcat.alloc((size_t)S->mtot * ldP));
+  for (DevBuf<double>* b : {&S->VS, &S->VD, &S->VR, &S->VB, &S->VC}) LRFSI_TRY(b->alloc((size_t)S->mtot * ldR));
+  for (DevBuf<double>* b : {&S->G, &S->G2, &S->T1, &S->T2}) LRFSI_TRY(b->alloc((size_t)K * ldP * ldP));
+  S->swork_per = trunc_small_work(ldP, S->mmax);
+  LRFSI_TRY(S->swork.alloc(S->swork_per * K));
+  LRFSI_TRY(S->sv.alloc((size_t)K * ldP));
+  LRFSI_TRY(S->frob2.alloc(K));
+  LRFSI_TRY(S->iwork.alloc((size_t)2 * ldP * K));
+  LRFSI_TRY(S->info.alloc((size_t)5 * K));
+  LRFSI_TRY(S->tdesc.alloc(2 * K));
+  LRFSI_TRY(S->gramwork.alloc(gram_work_len(K, M, ldP, ldP)));
+  LRFSI_TRY(S->Xd.alloc((size_t)M * S->mtot));
+  LRFSI_TRY(S->rc.init(M, S->mtot));
+  // operators at xt_k and the preconditioners at the midpoint parameters
+  std::vector<const double*> J3p(K);
+  for (int k = 0; k < K; ++k) {
+    double* Jk = S->J3.p + (size_t)k * 3 * nnz;
+    J3p[k] = Jk;
+    LRFSI_TRY(lrfsi_assemble_affine(mesh, S->xt.p + (size_t)k * M, Jk, S->R3.p + (size_t)k * 3 * M, stream));
+    double mlo = 1e300, mhi = -1e300, nlo = 1e300, nhi = -1e300;
+    for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) {
+      mlo = std::min(mlo, S->mu_h[i]); mhi = std::max(mhi, S->mu_h[i]);
+      nlo = std::min(nlo, S->nu_h[i]); nhi = std::max(nhi, S->nu_h[i]);
+    }
+    S->mubar.push_back(0.5 * (mlo + mhi));
+    S->nubar.push_back(0.5 * (nlo + nhi));
+  }
+  // equilibrate P_k and scale the operator values: the iteration and the
+  // truncation run on diag(r) F(diag(c) S~) = diag(r) B
+  LRFSI_TRY(S->rsc.alloc((size_t)K * M));
+  LRFSI_TRY(S->csc.alloc((size_t)K * M));
+  {
+    DevBuf<unsigned long long> cmax;
+    LRFSI_TRY(cmax.alloc(M));
+    for (int k = 0; k < K; ++k) {
+      double* Jk = S->J3.p + (size_t)k * 3 * nnz;
+      double* rk = S->rsc.p + (size_t)k * M;
+      double* ck = S->csc.p + (size_t)k * M;
+      k_equil_rows<<<ceil_div(M, 256), 256, 0, s>>>(Jk, mesh->rowptr.p, M, S->mubar[k], S->nubar[k], rk);
+      LRFSI_TRY(check_launch("k_equil_rows"));
+      LRFSI_CUDA(cudaMemsetAsync(cmax.p, 0, sizeof(unsigned long long) * M, s));
+      k_equil_colmax<<<ceil_div(M, 256), 256, 0, s>>>(Jk, mesh->rowptr.p, mesh->colidx.p, M, S->mubar[k], S->nubar[k],
+                                                       rk, cmax.p);
+      LRFSI_TRY(check_launch("k_equil_colmax"));
+      k_equil_cols<<<ceil_div(M, 256), 256, 0, s>>>(cmax.p, M, ck);
+      LRFSI_TRY(check_launch("k_equil_cols"));
+      k_scale_vals<<<ceil_div(M, 256), 256, 0, s>>>(Jk, mesh->rowptr.p, mesh->colidx.p, M, rk, ck);
+      LRFSI_TRY(check_launch("k_scale_vals"));
+    }
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+  }
+  LRFSI_TRY(blocklu_alloc(mesh, K, S->lu));
+  LRFSI_TRY(blocklu_factor(mesh, S->lu, J3p.data(), S->mubar.data(), S->nubar.data(), K, s));
+  std::vector<int> st;
+  LRFSI_TRY(blocklu_status(S->lu, K, st, s));
+  for (int k = 0; k < K; ++k)
+    if (st[k]) return fail(LRFSI_ESINGULAR, "lrfsi_subset_create: zero pivot in a preconditioner LU");
+  LRFSI_TRY(residual_bD_norms(mesh, S->rc, S->mu.p, S->nu.p, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  *out = guard.release();
+  return LRFSI_OK;
+}
+
+namespace lrfsi {
+
+// Chebyshev on factors for the subsets in `act`; B given in UB/VB (rank rB[k]).
+// Results in US/VS with rank rS[k].
+static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<int> act, std::vector<int> rB,
+                    std::vector<int>& rS, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  const long nnz = (long)S->mesh->h.colidx.size();
+  rS.assign(K, 0);
+  st.assign(K, lrfsi_cheb_stats{0, 0, 1.0, 0});
+  std::vector<int> rD(K, 0), rR(K, 0), p(K, 0);
+  std::vector<double> nB(K, 0.0), rho(K, 0.0);
+  std::vector<double*> Uo(K), Vo(K);
+  std::vector<int> rk;
+  std::vector<double> f2;
+  const double sigma = o.d / o.c;
+  // B is dense in UB (M x m_k): ||B||_F from its column norms
+  {
+    for (int k : act) {
+      LRFSI_TRY(launch_colnorm2(S->tall(S->UB, k, ldR), M, S->m[k], ldR, S->rc.norm2.p + S->off[k], S->rc.work.p,
+                                S->rc.work.n, s));
+    }
+    std::vector<double> cn(S->mtot);
+    LRFSI_CUDA(cudaMemcpyAsync(cn.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    for (int k : act) {
+      double t = 0;
+      for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) t += cn[i];
+      nB[k] = std::sqrt(t);
+    }
+  }
+  std::vector<int> live;
+  for (int k : act)
+    if (nB[k] > 0) live.push_back(k);
+  // residual Res = B - F(S) formed densely in Xcat (M x m_k), then truncated
+  // into UR/VR; the dense form avoids cancellation between the factors of B
+  // and F(S).  Returns ||Res||_F.
+  auto residual = [&](const std::vector<int>& L, std::vector<double>& nres) -> int {
+    std::vector<CopyDesc> cd, cd2;
+    std::vector<SpmmDesc<double>> sd;
+    std::vector<GemmDesc<double>> gm;
+    for (int k : L) {
+      double* X = S->tall(S->Xcat, k, ldP);
+      double* Vc = S->vside(S->Vcat, k, ldP);
+      const int m = S->m[k];
+      cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, X, ldP, M, m, 0, nullptr, 1.0});
+      const int r = rS[k];
+      if (r > 0) {
+        const double* mu = S->mu.p + S->off[k];
+        const double* nu = S->nu.p + S->off[k];
+        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc, ldP, m, r, 0, nullptr, 1.0});
+        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + r, ldP, m, r, 0, mu, 1.0});
+        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + 2 * r, ldP, m, r, 0, nu, 1.0});
+        SpmmDesc<double> d;
+        d.J3 = S->J3.p + (size_t)k * 3 * nnz;
+        d.U = S->tall(S->US, k, ldR);
+        d.ldu = ldR;
+        d.r = r;
+        d.Y = S->tall(S->Q1, k, ldP);
+        d.ldy = ldP;
+        d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+        d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
+        d.a1 = d.a2 = 0.0;
+        sd.push_back(d);
+        gm.push_back(GemmDesc<double>{(int)M, m, 3 * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0,
+                                      1.0});
+      }
+      cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0});
+      p[k] = m;
+      Uo[k] = S->tall(S->UR, k, ldR);
+      Vo[k] = S->vside(S->VR, k, ldR);
+    }
+    LRFSI_TRY(copy_batched(cd, s));
+    if (!sd.empty()) {
+      LRFSI_TRY(spmm_batched<double>(S->mesh, sd.data(), (int)sd.size(), s));
+      LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+    }
+    LRFSI_TRY(copy_batched(cd2, s));
+    LRFSI_TRY(truncate_batch(S, L, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
+    nres.assign(K, 0.0);
+    for (int k : L) {
+      rR[k] = rk[k];
+      nres[k] = std::sqrt(f2[k]);
+      st[k].rel_lin_res = nres[k] / nB[k];
+      st[k].max_concat_rank = std::max(st[k].max_concat_rank, 3 * rS[k]);
+    }
+    return LRFSI_OK;
+  };
+  // Z = P^{-1} U_R  (into UZ; UR copied to Ytmp as the destroyed input)
+  auto precond = [&](const std::vector<int>& L) -> int {
+    std::vector<CopyDesc> cd;
+    std::vector<double*> Xs, Ys;
+    std::vector<int> rr;
+    for (int k : L) {
+      if (rR[k] == 0) continue;
+      cd.push_back(CopyDesc{S->tall(S->UR, k, ldR), ldR, S->tall(S->Ytmp, k, ldR), ldR, M, rR[k], 0, nullptr, 1.0});
+      Xs.push_back(S->tall(S->Ytmp, k, ldR));
+      Ys.push_back(S->tall(S->UZ, k, ldR));
+      rr.push_back(rR[k]);
+    }
+    LRFSI_TRY(copy_batched(cd, s));
+    // the LU batch is indexed by subset: solve subset by subset position
+    // (problems of the factorisation are the K subsets in order)
+    if (Xs.empty()) return LRFSI_OK;
+    std::vector<double*> X2(K, nullptr), Y2(K, nullptr);
+    std::vector<int> r2(K, 0);
+    size_t q = 0;
+    for (int k : L) {
+      if (rR[k] == 0) continue;
+      X2[k] = Xs[q]; Y2[k] = Ys[q]; r2[k] = rr[q]; ++q;
+    }
+    // subsets without work get r = 0 (their GEMMs are skipped)
+    for (int k = 0; k < K; ++k)
+      if (!X2[k]) { X2[k] = S->tall(S->Ytmp, k, ldR); Y2[k] = S->tall(S->UZ, k, ldR); }
+    return blocklu_solve(S->lu, X2.data(), Y2.data(), r2.data(), ldR, K, s);
+  };
+  for (int cyc = 0; cyc < o.cycles && !live.empty(); ++cyc) {
+    std::vector<double> nres;
+    LRFSI_TRY(residual(live, nres));
+    std::vector<int> next;
+    for (int k : live) {
+      if (o.eta > 0 && nres[k] <= o.eta * nB[k]) continue;
+      next.push_back(k);
+    }
+    live.swap(next);
+    if (live.empty()) break;
+    LRFSI_TRY(precond(live));
+    {  // Delta = Z / d
+      std::vector<CopyDesc> cd;
+      for (int k : live) {
+        cd.push_back(CopyDesc{S->tall(S->UZ, k, ldR), ldR, S->tall(S->UD, k, ldR), ldR, M, rR[k], 0, nullptr, 1.0});
+        cd.push_back(CopyDesc{S->vside(S->VR, k, ldR), ldR, S->vside(S->VD, k, ldR), ldR, S->m[k], rR[k], 0, nullptr,
+                              1.0 / o.d});
+        rD[k] = rR[k];
+        rho[k] = 1.0 / sigma;
+      }
+      LRFSI_TRY(copy_batched(cd, s));
+    }
+    for (int j = 0; j < o.iters && !live.empty(); ++j) {
+      // S <- T([U_S | U_D], [V_S | V_D])
+      {
+        std::vector<CopyDesc> cd;
+        for (int k : live) {
+          cd.push_back(CopyDesc{S->tall(S->US, k, ldR), ldR, S->tall(S->Xcat, k, ldP), ldP, M, rS[k], 0, nullptr, 1.0});
+          cd.push_back(CopyDesc{S->tall(S->UD, k, ldR), ldR, S->tall(S->Xcat, k, ldP) + rS[k], ldP, M, rD[k], 0, nullptr,
+                                1.0});
+          cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, S->vside(S->Vcat, k, ldP), ldP, S->m[k], rS[k], 0, nullptr,
+                                1.0});
+          cd.push_back(CopyDesc{S->vside(S->VD, k, ldR), ldR, S->vside(S->Vcat, k, ldP) + rS[k], ldP, S->m[k], rD[k], 0,
+                                nullptr, 1.0});
+          p[k] = rS[k] + rD[k];
+          Uo[k] = S->tall(S->US, k, ldR);
+          Vo[k] = S->vside(S->VS, k, ldR);
+        }
+        LRFSI_TRY(copy_batched(cd, s));
+        LRFSI_TRY(truncate_batch(S, live, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
+        for (int k : live) {
+          rS[k] = rk[k];
+          st[k].steps += 1;
+        }
+      }
+      if (j == o.iters - 1) break;
+      std::vector<double> nres2;
+      LRFSI_TRY(residual(live, nres2));
+      std::vector<int> next2;
+      for (int k : live)
+        if (!(o.eta > 0 && nres2[k] <= o.eta * nB[k])) next2.push_back(k);
+      live.swap(next2);
+      if (live.empty()) break;
+      LRFSI_TRY(precond(live));
+      // Delta <- T([U_D | U_Z], [rho' rho V_D | (2 rho' / c) V_R])
+      {
+        std::vector<CopyDesc> cd;
+        for (int k : live) {
+          const double rn = 1.0 / (2.0 * sigma - rho[k]);
+          cd.push_back(CopyDesc{S->tall(S->UD, k, ldR), ldR, S->tall(S->Xcat, k, ldP), ldP, M, rD[k], 0, nullptr, 1.0});
+          cd.push_back(CopyDesc{S->tall(S->UZ, k, ldR), ldR, S->tall(S->Xcat, k, ldP) + rD[k], ldP, M, rR[k], 0, nullptr,
+                                1.0});
+          cd.push_back(CopyDesc{S->vside(S->VD, k, ldR), ldR, S->vside(S->Vcat, k, ldP), ldP, S->m[k], rD[k], 0, nullptr,
+                                rn * rho[k]});
+          cd.push_back(CopyDesc{S->vside(S->VR, k, ldR), ldR, S->vside(S->Vcat, k, ldP) + rD[k], ldP, S->m[k], rR[k], 0,
+                                nullptr, 2.0 * rn / o.c});
+          p[k] = rD[k] + rR[k];
+          Uo[k] = S->tall(S->UD, k, ldR);
+          Vo[k] = S->vside(S->VD, k, ldR);
+          rho[k] = rn;
+        }
+        LRFSI_TRY(copy_batched(cd, s));
+        LRFSI_TRY(truncate_batch(S, live, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
+        for (int k : live) rD[k] = rk[k];
+      }
+    }
+  }
+  for (int k : act) st[k].rank = rS[k];
+  return LRFSI_OK;
+}
+
+static int check_opts(const lrfsi_cheb_options* o) {
+  if (!o || !(o->c > 0) || !(o->d > o->c) || o->iters < 1 || o->cycles < 1 || o->rank_cap < 1 || !(o->tol >= 0) ||
+      o->precision < 0 || o->precision > 1)
+    return fail(LRFSI_EINVAL, "lrfsi_cheb_options: need 0 < c < d, iters, cycles, rank_cap >= 1, tol >= 0");
+  return LRFSI_OK;
+}
+
+}  // namespace lrfsi
+
+extern "C" int lrfsi_chebyshevT(lrfsi_subset_h S, const double* UB, int lduB, const double* VB, int ldvB,
+                                const int* rB_h, const lrfsi_cheb_options* opt, double* U, int ldu, double* V, int ldv,
+                                int* rank_h, lrfsi_cheb_stats* stats, lrfsi_stream_t stream) {
+  if (!S || !UB || !VB || !rB_h || !U || !V || !rank_h) return fail(LRFSI_EINVAL, "lrfsi_chebyshevT: null argument");
+  LRFSI_TRY(check_opts(opt));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<int> act, rB(K);
+  std::vector<GemmDesc<double>> gm;
+  for (int k = 0; k < K; ++k) {
+    rB[k] = rB_h[k];
+    if (rB[k] < 1 || rB[k] > lduB || rB[k] > ldvB || ldu < S->cap[k] || ldv < S->cap[k])
+      return fail(LRFSI_EINVAL, "lrfsi_chebyshevT: rank / leading dimension mismatch");
+    act.push_back(k);
+    // dense B_k = UB_k VB_k^T (M x m_k)
+    gm.push_back(GemmDesc<double>{(int)M, S->m[k], rB[k], UB + (size_t)k * M * lduB, lduB, 1,
+                                  VB + (size_t)S->off[k] * ldvB, 1, ldvB, S->tall(S->UB, k, ldR), ldR, 1, 1.0, 0.0});
+  }
+  LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+  {
+    std::vector<CopyDesc> sc;
+    for (int k = 0; k < K; ++k)
+      sc.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, S->tall(S->UB, k, ldR), ldR, M, S->m[k], 0,
+                            S->rsc.p + (size_t)k * M, 1.0});
+    LRFSI_TRY(copy_batched(sc, s));
+  }
+  std::vector<int> rS;
+  std::vector<lrfsi_cheb_stats> st;
+  LRFSI_TRY(cheb_run(S, *opt, act, rB, rS, st, s));
+  std::vector<CopyDesc> cd;
+  for (int k = 0; k < K; ++k) {
+    rank_h[k] = rS[k];
+    if (stats) stats[k] = st[k];
+    cd.push_back(CopyDesc{S->tall(S->US, k, ldR), ldR, U + (size_t)k * M * ldu, ldu, M, rS[k], 0,
+                          S->csc.p + (size_t)k * M, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, V + (size_t)S->off[k] * ldv, ldv, S->m[k], rS[k], 0, nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt, double target, int max_outer,
+                                 double* U, int ldu, double* V, int ldv, int* rank_h, double* relres_h, int* outer_h,
+                                 lrfsi_stream_t stream) {
+  if (!S || !U || !V || !rank_h || max_outer < 0) return fail(LRFSI_EINVAL, "lrfsi_subset_step: bad argument");
+  LRFSI_TRY(check_opts(opt));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldR = S->ldR, ldP = S->ldP;
+  const long M = S->M;
+  for (int k = 0; k < K; ++k)
+    if (ldu < S->cap[k] || ldv < S->cap[k]) return fail(LRFSI_EINVAL, "lrfsi_subset_step: ldu/ldv < rank cap");
+  // B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T), dense M x m_k in UB
+  std::vector<CopyDesc> cd;
+  std::vector<GemmDesc<double>> gb;
+  std::vector<int> act, rB(K, 3);
+  for (int k = 0; k < K; ++k) {
+    act.push_back(k);
+    double* vb = S->vside(S->VB, k, ldR);
+    cd.push_back(CopyDesc{nullptr, 0, vb, ldR, S->m[k], 1, 1, nullptr, -1.0});
+    cd.push_back(CopyDesc{nullptr, 0, vb + 1, ldR, S->m[k], 1, 1, S->mu.p + S->off[k], -1.0});
+    cd.push_back(CopyDesc{nullptr, 0, vb + 2, ldR, S->m[k], 1, 1, S->nu.p + S->off[k], -1.0});
+    gb.push_back(GemmDesc<double>{(int)M, S->m[k], 3, S->R3.p + (size_t)k * 3 * M, 3, 1, vb, 1, ldR,
+                                  S->tall(S->UB, k, ldR), ldR, 1, 1.0, 0.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_TRY(gemm_grouped<double>(gb.data(), (int)gb.size(), s));
+  cd.clear();
+  for (int k = 0; k < K; ++k)
+    cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, S->tall(S->UB, k, ldR), ldR, M, S->m[k], 0,
+                          S->rsc.p + (size_t)k * M, 1.0});
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<int> rS;
+  std::vector<lrfsi_cheb_stats> st;
+  LRFSI_TRY(cheb_run(S, *opt, act, rB, rS, st, s));
+  // keep the accumulated update in UC/VC
+  std::vector<int> rC = rS;
+  cd.clear();
+  for (int k = 0; k < K; ++k) {
+    cd.push_back(CopyDesc{S->tall(S->US, k, ldR), ldR, S->tall(S->UC, k, ldR), ldR, M, rC[k], 0, nullptr, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, S->vside(S->VC, k, ldR), ldR, S->m[k], rC[k], 0, nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<int> outer(K, 0);
+  std::vector<double> rel(S->mtot, 0.0);
+  int status = LRFSI_OK;
+  for (int it = 0;; ++it) {
+    // X = xt 1^T + diag(c) U_C V_C^T (dense columns, M x mtot) and its nonlinear residual
+    std::vector<GemmDesc<double>> gm;
+    for (int k = 0; k < K; ++k) {
+      if (rC[k] > 0)
+        gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
+                                      S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
+      else
+        LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
+    }
+    if (!gm.empty()) LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+    for (int k = 0; k < K; ++k) {
+      k_affine_cols<<<ceil_div(M * S->m[k], 256), 256, 0, s>>>(S->Xd.p, S->mtot, S->off[k], S->m[k],
+                                                              S->xt.p + (size_t)k * M, S->csc.p + (size_t)k * M, M);
+      LRFSI_TRY(check_launch("k_affine_cols"));
+    }
+    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->rc.R.p, S->mtot, s));
+    LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
+    std::vector<double> a(S->mtot), b(S->mtot);
+    LRFSI_CUDA(cudaMemcpyAsync(a.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaMemcpyAsync(b.data(), S->rc.norm2_bD.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    for (int i = 0; i < S->mtot; ++i) rel[i] = b[i] > 0 ? std::sqrt(a[i] / b[i]) : std::sqrt(a[i]);
+    if (target <= 0) break;
+    std::vector<int> need;
+    for (int k = 0; k < K; ++k) {
+      double mx = 0;
+      for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) mx = std::max(mx, rel[i]);
+      if (mx > target) need.push_back(k);
+    }
+    if (need.empty()) break;
+    if (it >= max_outer) {
+      status = LRFSI_ENOCONV;
+      break;
+    }
+    // correction: B = -R(X) (dense, rank <= m_k as factors (R_k, I))
+    cd.clear();
+    std::vector<int> rBc(K, 0);
+    for (int k : need) {
+      const int m = S->m[k];
+      // UB must hold m columns: ldR >= mmax by construction
+      cd.push_back(CopyDesc{S->rc.R.p + S->off[k], S->mtot, S->tall(S->UB, k, ldR), ldR, M, m, 0,
+                            S->rsc.p + (size_t)k * M, -1.0});
+      rBc[k] = m;
+    }
+    LRFSI_TRY(copy_batched(cd, s));
+    LRFSI_TRY(cheb_run(S, *opt, need, rBc, rS, st, s));
+    // accumulate: C <- T([U_C | U_S], [V_C | V_S])
+    cd.clear();
+    std::vector<int> p(K, 0);
+    std::vector<double*> Uo(K), Vo(K);
+    for (int k : need) {
+      cd.push_back(CopyDesc{S->tall(S->UC, k, ldR), ldR, S->tall(S->Xcat, k, ldP), ldP, M, rC[k], 0, nullptr, 1.0});
+      cd.push_back(CopyDesc{S->tall(S->US, k, ldR), ldR, S->tall(S->Xcat, k, ldP) + rC[k], ldP, M, rS[k], 0, nullptr, 1.0});
+      cd.push_back(CopyDesc{S->vside(S->VC, k, ldR), ldR, S->vside(S->Vcat, k, ldP), ldP, S->m[k], rC[k], 0, nullptr, 1.0});
+      cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, S->vside(S->Vcat, k, ldP) + rC[k], ldP, S->m[k], rS[k], 0,
+                            nullptr, 1.0});
+      p[k] = rC[k] + rS[k];
+      Uo[k] = S->tall(S->UC, k, ldR);
+      Vo[k] = S->vside(S->VC, k, ldR);
+      outer[k] += 1;
+    }
+    LRFSI_TRY(copy_batched(cd, s));
+    std::vector<int> rk;
+    std::vector<double> f2;
+    LRFSI_TRY(truncate_batch(S, need, p, opt->tol, S->cap, Uo, Vo, rk, f2, s));
+    for (int k : need) rC[k] = rk[k];
+  }
+  cd.clear();
+  for (int k = 0; k < K; ++k) {
+    rank_h[k] = rC[k];
+    if (outer_h) outer_h[k] = outer[k];
+    cd.push_back(CopyDesc{S->tall(S->UC, k, ldR), ldR, U + (size_t)k * M * ldu, ldu, M, rC[k], 0,
+                          S->csc.p + (size_t)k * M, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VC, k, ldR), ldR, V + (size_t)S->off[k] * ldv, ldv, S->m[k], rC[k], 0, nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  if (relres_h) std::memcpy(relres_h, rel.data(), sizeof(double) * S->mtot);
+  if (status != LRFSI_OK) return fail(status, "lrfsi_subset_step: target not reached within max_outer corrections");
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_precond_apply(lrfsi_subset_h S, const double* X, int ldx, const int* r_h, double* Y, int ldy,
+                                   lrfsi_stream_t stream) {
+  if (!S || !X || !Y || !r_h) return fail(LRFSI_EINVAL, "lrfsi_precond_apply: null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldP = S->ldP;
+  const long M = S->M;
+  std::vector<CopyDesc> cd;
+  std::vector<double*> Xs(K), Ys(K);
+  std::vector<int> rr(K);
+  for (int k = 0; k < K; ++k) {
+    rr[k] = r_h[k];
+    if (rr[k] < 0 || rr[k] > ldx || rr[k] > ldy || rr[k] > ldP) return fail(LRFSI_EINVAL, "lrfsi_precond_apply: r_k");
+    // scaled right-hand side diag(r) X into Xcat, solve into Q1, unscale by c
+    cd.push_back(CopyDesc{X + (size_t)k * M * ldx, ldx, S->tall(S->Xcat, k, ldP), ldP, M, rr[k], 0,
+                          S->rsc.p + (size_t)k * M, 1.0});
+    Xs[k] = S->tall(S->Xcat, k, ldP);
+    Ys[k] = S->tall(S->Q1, k, ldP);
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_TRY(blocklu_solve(S->lu, Xs.data(), Ys.data(), rr.data(), ldP, K, s));
+  cd.clear();
+  for (int k = 0; k < K; ++k)
+    cd.push_back(CopyDesc{S->tall(S->Q1, k, ldP), ldP, Y + (size_t)k * M * ldy, ldy, M, rr[k], 0,
+                          S->csc.p + (size_t)k * M, 1.0});
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_truncate(lrfsi_subset_h S, const double* X, int ldx, const double* V, int ldv, const int* p_h,
+                              double tol, const int* cap_h, double* U, int ldu, double* Vo, int ldvo, int* rank_h,
+                              lrfsi_stream_t stream) {
+  if (!S || !X || !V || !p_h || !cap_h || !U || !Vo || !rank_h || !(tol >= 0))
+    return fail(LRFSI_EINVAL, "lrfsi_truncate: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<CopyDesc> cd;
+  std::vector<int> act, p(K), cap(K);
+  std::vector<double*> Uo(K), Vout(K);
+  for (int k = 0; k < K; ++k) {
+    p[k] = p_h[k];
+    cap[k] = std::min(cap_h[k], ldR);
+    if (p[k] < 1 || p[k] > ldx || p[k] > ldv || p[k] > ldP || cap[k] < 1 || ldu < cap[k] || ldvo < cap[k])
+      return fail(LRFSI_EINVAL, "lrfsi_truncate: rank / leading dimension mismatch");
+    act.push_back(k);
+    cd.push_back(CopyDesc{X + (size_t)k * M * ldx, ldx, S->tall(S->Xcat, k, ldP), ldP, M, p[k], 0, nullptr, 1.0});
+    cd.push_back(CopyDesc{V + (size_t)S->off[k] * ldv, ldv, S->vside(S->Vcat, k, ldP), ldP, S->m[k], p[k], 0, nullptr,
+                          1.0});
+    Uo[k] = S->tall(S->UR, k, ldR);
+    Vout[k] = S->vside(S->VR, k, ldR);
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<int> rk;
+  std::vector<double> f2;
+  LRFSI_TRY(truncate_batch(S, act, p, tol, cap, Uo, Vout, rk, f2, s));
+  cd.clear();
+  for (int k = 0; k < K; ++k) {
+    rank_h[k] = rk[k];
+    cd.push_back(CopyDesc{S->tall(S->UR, k, ldR), ldR, U + (size_t)k * M * ldu, ldu, M, rk[k], 0, nullptr, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VR, k, ldR), ldR, Vo + (size_t)S->off[k] * ldvo, ldvo, S->m[k], rk[k], 0,
+                          nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}

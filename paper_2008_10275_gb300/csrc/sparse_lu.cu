@@ -1,0 +1,409 @@
+// SpMM of the affine operators and the block-tridiagonal FP64 LU used for the
+// mean-based preconditioner P_T^k = J(x~; mu_bar, nu_bar) (Sec. 4.2; the
+// paper factors it with a permuted LU) and for the median Newton solves
+// (Sec. 3.2).
+//
+// Fill-reducing ordering: the slab-major DOF order makes every operator block
+// tridiagonal over the nx + 1 slabs of the channel, so the LU fills only the
+// diagonal, first super- and first sub-diagonal blocks (block Thomas
+// elimination).  Pivoting is partial pivoting inside each diagonal Schur
+// block; its pivot threshold is reported through the status word.
+#include <cmath>
+
+#include "sparse_lu.h"
+
+namespace lrfsi {
+
+// ---------------------------------------------------------------------------
+// SpMM: one warp per row, lanes over the columns of U
+// ---------------------------------------------------------------------------
+template <class T>
+struct SpmmBatch {
+  SpmmDesc<T> d[kMaxGemmDescs];
+};
+
+template <class T, int CPL>
+__global__ void __launch_bounds__(256) k_spmm(SpmmBatch<T> sb, const int* __restrict__ rowptr,
+                                               const int* __restrict__ colidx, long M) {
+  const SpmmDesc<T>& dref = sb.d[blockIdx.y];
+  const long row = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= M) return;
+  const int r = dref.r;
+  const T* __restrict__ U = dref.U;
+  const T* __restrict__ J3 = dref.J3;
+  const int ldu = dref.ldu;
+  const bool combined = dref.o[1] < 0;
+  const T a1 = dref.a1, a2 = dref.a2;
+  const int k0 = rowptr[row], k1 = rowptr[row + 1];
+  for (int c0 = 0; c0 < r; c0 += 32 * CPL) {
+    T acc0[CPL], acc1[CPL], acc2[CPL];
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) acc0[q] = acc1[q] = acc2[q] = T(0);
+    for (int k = k0; k < k1; ++k) {
+      const int col = colidx[k];
+      const T v0 = J3[3 * (size_t)k], v1 = J3[3 * (size_t)k + 1], v2 = J3[3 * (size_t)k + 2];
+      const T* ur = U + (size_t)col * ldu;
+#pragma unroll
+      for (int q = 0; q < CPL; ++q) {
+        const int j = c0 + lane + 32 * q;
+        if (j < r) {
+          const T u = ur[j];
+          if (combined) {
+            acc0[q] += (v0 + a1 * v1 + a2 * v2) * u;
+          } else {
+            acc0[q] += v0 * u; acc1[q] += v1 * u; acc2[q] += v2 * u;
+          }
+        }
+      }
+    }
+    T* yr = dref.Y + (size_t)row * dref.ldy;
+#pragma unroll
+    for (int q = 0; q < CPL; ++q) {
+      const int j = c0 + lane + 32 * q;
+      if (j < r) {
+        yr[dref.o[0] + j] = dref.sc[0] * acc0[q];
+        if (!combined) {
+          yr[dref.o[1] + j] = dref.sc[1] * acc1[q];
+          yr[dref.o[2] + j] = dref.sc[2] * acc2[q];
+        }
+      }
+    }
+  }
+}
+
+template <class T>
+int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_t s) {
+  const long M = m->h.M;
+  for (int base = 0; base < n; base += kMaxGemmDescs) {
+    SpmmBatch<T> sb;
+    int cnt = 0, rmax = 0;
+    for (int i = base; i < n && cnt < kMaxGemmDescs; ++i) {
+      if (d[i].r <= 0) continue;
+      sb.d[cnt++] = d[i];
+      rmax = rmax > d[i].r ? rmax : d[i].r;
+    }
+    if (!cnt) continue;
+    dim3 grid(ceil_div(M, 8), cnt);
+    if (rmax <= 32) k_spmm<T, 1><<<grid, 256, 0, s>>>(sb, m->rowptr.p, m->colidx.p, M);
+    else k_spmm<T, 2><<<grid, 256, 0, s>>>(sb, m->rowptr.p, m->colidx.p, M);
+    LRFSI_TRY(check_launch("k_spmm"));
+  }
+  return LRFSI_OK;
+}
+template int spmm_batched<double>(const lrfsi_mesh_s*, const SpmmDesc<double>*, int, cudaStream_t);
+template int spmm_batched<float>(const lrfsi_mesh_s*, const SpmmDesc<float>*, int, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Block LU
+// ---------------------------------------------------------------------------
+constexpr int kNb = 32;  // panel width
+
+struct ProbPtrs {
+  double* ws[kMaxGemmDescs];
+  const double* J3[kMaxGemmDescs];
+  int* piv[kMaxGemmDescs];
+  int* status[kMaxGemmDescs];
+  double alpha[kMaxGemmDescs], beta[kMaxGemmDescs];
+};
+
+__global__ void k_lu_extract(ProbPtrs pp, const long long* __restrict__ dense_off, long nnz) {
+  const long k = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nnz) return;
+  const int b = blockIdx.y;
+  const double* J = pp.J3[b];
+  pp.ws[b][dense_off[k]] = J[3 * k] + pp.alpha[b] * J[3 * k + 1] + pp.beta[b] * J[3 * k + 2];
+}
+
+// Identity right-hand side next to Up: RHS = [Up_s | I] (n x (n_next + n)).
+__global__ void k_lu_rhs(ProbPtrs pp, size_t off_up_s, size_t off_rhs, int n, int nnext, int nmax) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ldr = 2 * nmax;
+  if (e >= (long)n * ldr) return;
+  const int i = (int)(e / ldr), j = (int)(e % ldr);
+  double* R = pp.ws[blockIdx.y] + off_rhs;
+  double v;
+  if (j < nmax) v = j < nnext ? pp.ws[blockIdx.y][off_up_s + (size_t)i * nmax + j] : 0.0;
+  else v = (j - nmax == i) ? 1.0 : 0.0;
+  R[(size_t)i * ldr + j] = v;
+}
+
+// Panel factorization with partial pivoting of columns [j0, j0 + nb) of the
+// n x n block A (ld) (rows j0..n-1); pivots are absolute row indices.
+__global__ void __launch_bounds__(512) k_lu_panel(ProbPtrs pp, size_t off_blk, int piv_off, int n, int ld, int j0,
+                                                  int nb) {
+  const int b = blockIdx.x;
+  double* A = pp.ws[b] + off_blk;
+  int* piv = pp.piv[b] + piv_off;
+  __shared__ double s_val[512];
+  __shared__ int s_idx[512];
+  const int j1 = j0 + nb < n ? j0 + nb : n;
+  for (int j = j0; j < j1; ++j) {
+    double best = -1.0;
+    int bi = j;
+    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
+      const double v = fabs(A[(size_t)i * ld + j]);
+      if (v > best) { best = v; bi = i; }
+    }
+    s_val[threadIdx.x] = best;
+    s_idx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if (threadIdx.x < o) {
+        const double v2 = s_val[threadIdx.x + o];
+        const int i2 = s_idx[threadIdx.x + o];
+        if (v2 > s_val[threadIdx.x] || (v2 == s_val[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
+          s_val[threadIdx.x] = v2;
+          s_idx[threadIdx.x] = i2;
+        }
+      }
+      __syncthreads();
+    }
+    const int p = s_idx[0];
+    const double pv = s_val[0];
+    if (threadIdx.x == 0) {
+      piv[j] = p;
+      if (!(pv > 0.0)) *pp.status[b] = LRFSI_ESINGULAR;
+    }
+    if (p != j)
+      for (int c = j0 + threadIdx.x; c < j1; c += blockDim.x) {
+        const double t = A[(size_t)j * ld + c];
+        A[(size_t)j * ld + c] = A[(size_t)p * ld + c];
+        A[(size_t)p * ld + c] = t;
+      }
+    __syncthreads();
+    double d = A[(size_t)j * ld + j];
+    if (d == 0.0) d = 1e-300;  // singular: flagged above, keep going without NaNs
+    const double inv = 1.0 / d;
+    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * ld + j] *= inv;
+    __syncthreads();
+    const int w = j1 - j - 1;
+    for (long e = threadIdx.x; e < (long)(n - j - 1) * w; e += blockDim.x) {
+      const int i = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
+      A[(size_t)i * ld + c] -= A[(size_t)i * ld + j] * A[(size_t)j * ld + c];
+    }
+    __syncthreads();
+  }
+}
+
+// Apply the row interchanges piv[j0..j1) to columns [c0, c1) of a matrix with
+// ld (one thread per column).
+__global__ void k_lu_laswp(ProbPtrs pp, size_t off_mat, int ld, int piv_off, int j0, int j1, int c0, int c1,
+                           int skip0, int skip1) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1 || (c >= skip0 && c < skip1)) return;
+  double* A = pp.ws[blockIdx.y] + off_mat;
+  const int* piv = pp.piv[blockIdx.y] + piv_off;
+  for (int j = j0; j < j1; ++j) {
+    const int p = piv[j];
+    if (p != j) {
+      const double t = A[(size_t)j * ld + c];
+      A[(size_t)j * ld + c] = A[(size_t)p * ld + c];
+      A[(size_t)p * ld + c] = t;
+    }
+  }
+}
+
+// Triangular solve of a diagonal nb x nb block for columns [c0, c1) of B:
+// lower (unit) forward or upper backward substitution, thread per column.
+__global__ void k_lu_trsm_diag(ProbPtrs pp, size_t off_L, int ldl, size_t off_B, int ldb, int i0, int nb, int c0,
+                               int c1, int upper) {
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
+  const double* L = pp.ws[blockIdx.y] + off_L;
+  double* B = pp.ws[blockIdx.y] + off_B;
+  if (!upper) {
+    for (int i = i0; i < i0 + nb; ++i) {
+      double s = B[(size_t)i * ldb + c];
+      for (int l = i0; l < i; ++l) s -= L[(size_t)i * ldl + l] * B[(size_t)l * ldb + c];
+      B[(size_t)i * ldb + c] = s;
+    }
+  } else {
+    for (int i = i0 + nb - 1; i >= i0; --i) {
+      double s = B[(size_t)i * ldb + c];
+      for (int l = i + 1; l < i0 + nb; ++l) s -= L[(size_t)i * ldl + l] * B[(size_t)l * ldb + c];
+      double d = L[(size_t)i * ldl + i];
+      B[(size_t)i * ldb + c] = s / (d == 0.0 ? 1e-300 : d);
+    }
+  }
+}
+
+__global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t off_inv, int n, int nnext, int nmax) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)n * nmax) return;
+  const int i = (int)(e / nmax), j = (int)(e % nmax);
+  double* ws = pp.ws[blockIdx.y];
+  const double* R = ws + off_rhs + (size_t)i * 2 * nmax;
+  if (j < nnext) ws[off_w + (size_t)i * nmax + j] = R[j];
+  if (j < n) ws[off_inv + (size_t)i * nmax + j] = R[nmax + j];
+}
+
+int blocklu_alloc(const lrfsi_mesh_s* m, int nprob, BlockLU& lu) {
+  if (nprob < 1 || nprob > kMaxGemmDescs) return fail(LRFSI_EINVAL, "block LU: 1..32 problems per batch");
+  lu.nslab = m->h.nslab;
+  lu.nmax = m->h.nmax;
+  lu.nprob = nprob;
+  lu.off = m->h.slab_off;
+  const size_t nb2 = (size_t)lu.nmax * lu.nmax;
+  lu.off_up = nb2 * lu.nslab;
+  lu.off_lo = lu.off_up + nb2 * (lu.nslab - 1);
+  lu.off_inv = lu.off_lo + nb2 * (lu.nslab - 1);
+  lu.off_rhs = lu.off_inv + nb2 * lu.nslab;
+  lu.per_prob = lu.off_rhs + 2 * nb2;
+  LRFSI_TRY(lu.ws.alloc(lu.per_prob * nprob));
+  LRFSI_TRY(lu.piv.alloc((size_t)lu.nslab * lu.nmax * nprob));
+  LRFSI_TRY(lu.status.alloc(nprob));
+  return LRFSI_OK;
+}
+
+static ProbPtrs make_ptrs(BlockLU& lu, int nprob) {
+  ProbPtrs pp;
+  for (int b = 0; b < nprob; ++b) {
+    pp.ws[b] = lu.ws.p + lu.per_prob * b;
+    pp.piv[b] = lu.piv.p + (size_t)lu.nslab * lu.nmax * b;
+    pp.status[b] = lu.status.p + b;
+    pp.J3[b] = nullptr;
+    pp.alpha[b] = pp.beta[b] = 0;
+  }
+  return pp;
+}
+
+int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, const double* alpha,
+                   const double* beta, int nprob, cudaStream_t s) {
+  if (nprob > lu.nprob) return fail(LRFSI_EINVAL, "block LU: more problems than allocated");
+  ProbPtrs pp = make_ptrs(lu, nprob);
+  for (int b = 0; b < nprob; ++b) {
+    pp.J3[b] = J3[b];
+    pp.alpha[b] = alpha[b];
+    pp.beta[b] = beta[b];
+  }
+  const int nmax = lu.nmax;
+  const size_t nb2 = (size_t)nmax * nmax;
+  for (int b = 0; b < nprob; ++b) LRFSI_CUDA(cudaMemsetAsync(pp.ws[b], 0, sizeof(double) * lu.off_inv, s));
+  LRFSI_CUDA(cudaMemsetAsync(lu.status.p, 0, sizeof(int) * nprob, s));
+  const long nnz = (long)m->h.colidx.size();
+  k_lu_extract<<<dim3(ceil_div(nnz, 256), nprob), 256, 0, s>>>(pp, m->dense_off.p, nnz);
+  LRFSI_TRY(check_launch("k_lu_extract"));
+  std::vector<GemmDesc<double>> gd(nprob);
+  for (int sl = 0; sl < lu.nslab; ++sl) {
+    const int n = (int)(lu.off[sl + 1] - lu.off[sl]);
+    const int nnext = sl + 1 < lu.nslab ? (int)(lu.off[sl + 2] - lu.off[sl + 1]) : 0;
+    const size_t offD = nb2 * sl;
+    const int poff = sl * nmax;
+    // blocked right-looking LU of the Schur block S_s
+    for (int j0 = 0; j0 < n; j0 += kNb) {
+      const int nb = j0 + kNb < n ? kNb : n - j0;
+      k_lu_panel<<<nprob, 512, 0, s>>>(pp, offD, poff, n, nmax, j0, nb);
+      LRFSI_TRY(check_launch("k_lu_panel"));
+      // interchanges to the left and right of the panel
+      k_lu_laswp<<<dim3(ceil_div(n, 128), nprob), 128, 0, s>>>(pp, offD, nmax, poff, j0, j0 + nb, 0, n, j0, j0 + nb);
+      LRFSI_TRY(check_launch("k_lu_laswp"));
+      if (j0 + nb < n) {
+        k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, 128), nprob), 128, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
+                                                                              j0 + nb, n, 0);
+        LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+        for (int b = 0; b < nprob; ++b) {
+          double* A = pp.ws[b] + offD;
+          gd[b] = GemmDesc<double>{n - j0 - nb, n - j0 - nb, nb,
+                                   A + (size_t)(j0 + nb) * nmax + j0, nmax, 1,
+                                   A + (size_t)j0 * nmax + j0 + nb, nmax, 1,
+                                   A + (size_t)(j0 + nb) * nmax + j0 + nb, nmax, 1, -1.0, 1.0};
+        }
+        LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+      }
+    }
+    // RHS = P [Up_s | I];  L solve;  U solve  ->  [W_s | S_s^{-1}]
+    const int ldr = 2 * nmax;
+    k_lu_rhs<<<dim3(ceil_div((long)n * ldr, 256), nprob), 256, 0, s>>>(pp, lu.off_up + nb2 * sl, lu.off_rhs, n, nnext,
+                                                                       nmax);
+    LRFSI_TRY(check_launch("k_lu_rhs"));
+    k_lu_laswp<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, lu.off_rhs, ldr, poff, 0, n, 0, ldr, 0, 0);
+    LRFSI_TRY(check_launch("k_lu_laswp"));
+    for (int i0 = 0; i0 < n; i0 += kNb) {
+      const int nb = i0 + kNb < n ? kNb : n - i0;
+      k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
+      LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+      if (i0 + nb < n) {
+        for (int b = 0; b < nprob; ++b) {
+          double* A = pp.ws[b] + offD;
+          double* R = pp.ws[b] + lu.off_rhs;
+          gd[b] = GemmDesc<double>{n - i0 - nb, ldr, nb, A + (size_t)(i0 + nb) * nmax + i0, nmax, 1,
+                                   R + (size_t)i0 * ldr, ldr, 1, R + (size_t)(i0 + nb) * ldr, ldr, 1, -1.0, 1.0};
+        }
+        LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+      }
+    }
+    for (int i0 = ((n - 1) / kNb) * kNb; i0 >= 0; i0 -= kNb) {
+      const int nb = i0 + kNb < n ? kNb : n - i0;
+      k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
+      LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+      if (i0 > 0) {
+        for (int b = 0; b < nprob; ++b) {
+          double* A = pp.ws[b] + offD;
+          double* R = pp.ws[b] + lu.off_rhs;
+          gd[b] = GemmDesc<double>{i0, ldr, nb, A + i0, nmax, 1, R + (size_t)i0 * ldr, ldr, 1, R, ldr, 1, -1.0, 1.0};
+        }
+        LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+      }
+    }
+    k_lu_copy_out<<<dim3(ceil_div((long)n * nmax, 256), nprob), 256, 0, s>>>(pp, lu.off_rhs, lu.off_up + nb2 * sl,
+                                                                            lu.off_inv + nb2 * sl, n, nnext, nmax);
+    LRFSI_TRY(check_launch("k_lu_copy_out"));
+    // Schur complement of the next slab: D_{s+1} -= Lo_s W_s
+    if (nnext > 0) {
+      for (int b = 0; b < nprob; ++b) {
+        double* ws = pp.ws[b];
+        gd[b] = GemmDesc<double>{nnext, nnext, n, ws + lu.off_lo + nb2 * sl, nmax, 1, ws + lu.off_up + nb2 * sl, nmax,
+                                 1, ws + nb2 * (sl + 1), nmax, 1, -1.0, 1.0};
+      }
+      LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+    }
+  }
+  return LRFSI_OK;
+}
+
+int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r, int ld, int nprob, cudaStream_t s) {
+  const int nmax = lu.nmax;
+  const size_t nb2 = (size_t)nmax * nmax;
+  std::vector<GemmDesc<double>> gd(nprob);
+  for (int sl = 0; sl < lu.nslab; ++sl) {
+    const long o = lu.off[sl];
+    const int n = (int)(lu.off[sl + 1] - o);
+    if (sl > 0) {  // X_s -= Lo_{s-1} Y_{s-1}
+      const long op = lu.off[sl - 1];
+      const int np = (int)(o - op);
+      for (int b = 0; b < nprob; ++b) {
+        double* ws = lu.ws.p + lu.per_prob * b;
+        gd[b] = GemmDesc<double>{n, r[b], np, ws + lu.off_lo + nb2 * (sl - 1), nmax, 1, Y[b] + op * ld, ld, 1,
+                                 X[b] + o * ld, ld, 1, -1.0, 1.0};
+      }
+      LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+    }
+    for (int b = 0; b < nprob; ++b) {  // Y_s = S_s^{-1} X_s
+      double* ws = lu.ws.p + lu.per_prob * b;
+      gd[b] = GemmDesc<double>{n, r[b], n, ws + lu.off_inv + nb2 * sl, nmax, 1, X[b] + o * ld, ld, 1, Y[b] + o * ld,
+                               ld, 1, 1.0, 0.0};
+    }
+    LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+  }
+  for (int sl = lu.nslab - 2; sl >= 0; --sl) {  // Y_s -= W_s Y_{s+1}
+    const long o = lu.off[sl], on = lu.off[sl + 1];
+    const int n = (int)(on - o), nn = (int)(lu.off[sl + 2] - on);
+    for (int b = 0; b < nprob; ++b) {
+      double* ws = lu.ws.p + lu.per_prob * b;
+      gd[b] = GemmDesc<double>{n, r[b], nn, ws + lu.off_up + nb2 * sl, nmax, 1, Y[b] + on * ld, ld, 1, Y[b] + o * ld,
+                               ld, 1, -1.0, 1.0};
+    }
+    LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+  }
+  return LRFSI_OK;
+}
+
+int blocklu_status(BlockLU& lu, int nprob, std::vector<int>& out, cudaStream_t s) {
+  out.assign(nprob, 0);
+  LRFSI_CUDA(cudaMemcpyAsync(out.data(), lu.status.p, sizeof(int) * nprob, cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+}  // namespace lrfsi

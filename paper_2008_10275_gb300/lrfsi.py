@@ -1,0 +1,269 @@
+"""Python binding of the lrfsi C ABI (include/lrfsi.h): argument marshalling only.
+
+Every computation runs in the CUDA library ``liblrfsi.so`` built from
+``csrc/``; this module converts torch tensors (device memory) and numpy arrays
+(host memory) to pointers and checks status codes.  There is no fallback: if
+the library is missing, importing the binding raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrfsi.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "lrfsi.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ESINGULAR, ENOCONV, EBREAKDOWN, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+
+
+class LrfsiError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"lrfsi error {code}: {msg}")
+        self.code = code
+
+
+class lrfsi_problem(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("Lx", C.c_double), ("Ly", C.c_double),
+                ("flap", C.c_double * 4), ("rho_f", C.c_double), ("lam_s", C.c_double), ("v_mean", C.c_double)]
+
+
+class lrfsi_mesh_info_t(C.Structure):
+    _fields_ = [("M", C.c_int64), ("nnz", C.c_int64), ("nslab", C.c_int), ("nmax", C.c_int),
+                ("ncell", C.c_int), ("nsolid", C.c_int)]
+
+
+class lrfsi_cheb_options(C.Structure):
+    _fields_ = [("c", C.c_double), ("d", C.c_double), ("iters", C.c_int), ("cycles", C.c_int),
+                ("rank_cap", C.c_int), ("tol", C.c_double), ("eta", C.c_double), ("precision", C.c_int)]
+
+
+class lrfsi_cheb_stats(C.Structure):
+    _fields_ = [("steps", C.c_int), ("rank", C.c_int), ("rel_lin_res", C.c_double), ("max_concat_rank", C.c_int)]
+
+
+_lib = None
+
+
+def load():
+    """Load liblrfsi.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"liblrfsi.so not built ({LIB_PATH}); run paper_2008_10275_gb300.build.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp, i, d, i64p = C.c_void_p, C.c_int, C.c_double, C.POINTER(C.c_int64)
+    sig = {
+        "lrfsi_mesh_create": [C.POINTER(lrfsi_problem), C.POINTER(vp)],
+        "lrfsi_mesh_destroy": [vp],
+        "lrfsi_mesh_info": [vp, C.POINTER(lrfsi_mesh_info_t)],
+        "lrfsi_mesh_dofmap": [vp, vp, vp, vp],
+        "lrfsi_mesh_dirichlet": [vp, vp],
+        "lrfsi_mesh_pattern": [vp, vp, vp],
+        "lrfsi_assemble_affine": [vp, vp, vp, vp, vp],
+        "lrfsi_residual_batch": [vp, vp, i, i, vp, vp, vp, i, vp, vp],
+        "lrfsi_residual": [vp, vp, vp, i, vp, i, i, vp, vp, i, vp, vp],
+        "lrfsi_newton_median": [vp, i, vp, vp, vp, d, i, vp, vp, vp],
+        "lrfsi_subset_create": [vp, i, vp, vp, vp, vp, vp, C.POINTER(vp), vp],
+        "lrfsi_subset_destroy": [vp],
+        "lrfsi_chebyshevT": [vp, vp, i, vp, i, vp, C.POINTER(lrfsi_cheb_options), vp, i, vp, i, vp, vp, vp],
+        "lrfsi_subset_step": [vp, C.POINTER(lrfsi_cheb_options), d, i, vp, i, vp, i, vp, vp, vp, vp],
+        "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
+        "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = C.c_int
+    lib.lrfsi_last_error.restype = C.c_char_p
+    lib.lrfsi_kernel_launches.restype = C.c_uint64
+    lib.lrfsi_mesh_bytes.restype = C.c_size_t
+    lib.lrfsi_mesh_bytes.argtypes = [vp]
+    lib.lrfsi_subset_bytes.restype = C.c_size_t
+    lib.lrfsi_subset_bytes.argtypes = [vp]
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    """Names of the functions declared in include/lrfsi.h."""
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lrfsi_[a-zA-Z0-9_]+)\s*\(", txt)))
+
+
+def _check(code, allow=()):
+    if code != OK and code not in allow:
+        raise LrfsiError(code, load().lrfsi_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        return t.ctypes.data
+    return t.data_ptr()
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def kernel_launches():
+    return int(load().lrfsi_kernel_launches())
+
+
+class Mesh:
+    """A mesh handle (lrfsi_mesh)."""
+
+    def __init__(self, nx, ny, Lx=2.0, Ly=0.4, flap=(0.6, 0.7, 0.0, 0.2), rho_f=1e3, lam_s=2e6, v_mean=0.2):
+        lib = load()
+        p = lrfsi_problem(nx, ny, Lx, Ly, (C.c_double * 4)(*(flap if flap is not None else (0, 0, 0, 0))),
+                          rho_f, lam_s, v_mean)
+        self.h = C.c_void_p()
+        _check(lib.lrfsi_mesh_create(C.byref(p), C.byref(self.h)))
+        info = lrfsi_mesh_info_t()
+        _check(lib.lrfsi_mesh_info(self.h, C.byref(info)))
+        self.M, self.nnz, self.nslab, self.nmax = int(info.M), int(info.nnz), info.nslab, info.nmax
+        self.ncell, self.nsolid = info.ncell, info.nsolid
+        self.nx, self.ny = nx, ny
+
+    def close(self):
+        if self.h:
+            load().lrfsi_mesh_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def dofmap(self):
+        f = np.zeros(self.M, np.int32); ix = np.zeros(self.M, np.int32); iy = np.zeros(self.M, np.int32)
+        _check(load().lrfsi_mesh_dofmap(self.h, _ptr(f), _ptr(ix), _ptr(iy)))
+        return f, ix, iy
+
+    def dirichlet(self):
+        b = np.zeros(self.M)
+        _check(load().lrfsi_mesh_dirichlet(self.h, _ptr(b)))
+        return b
+
+    def pattern(self):
+        rp = np.zeros(self.M + 1, np.int32); ci = np.zeros(self.nnz, np.int32)
+        _check(load().lrfsi_mesh_pattern(self.h, _ptr(rp), _ptr(ci)))
+        return rp, ci
+
+    def device_bytes(self):
+        return int(load().lrfsi_mesh_bytes(self.h))
+
+
+def lrfsi_mesh(nx, ny, **kw):
+    return Mesh(nx, ny, **kw)
+
+
+def lrfsi_assemble_affine(mesh, x, J3=None, R3=None, stream=None):
+    _check(load().lrfsi_assemble_affine(mesh.h, _ptr(x), _ptr(J3), _ptr(R3), _stream(stream)))
+
+
+def lrfsi_residual_batch(mesh, X, ldx, m, mu, nu, R=None, ldr=0, norm2=None, stream=None):
+    _check(load().lrfsi_residual_batch(mesh.h, _ptr(X), ldx, m, _ptr(mu), _ptr(nu), _ptr(R), ldr, _ptr(norm2),
+                                       _stream(stream)))
+
+
+def lrfsi_residual(mesh, xt, U, ldu, V, ldv, r, mu, nu, m, stream=None):
+    out = np.zeros(m)
+    _check(load().lrfsi_residual(mesh.h, _ptr(xt), _ptr(U), ldu, _ptr(V), ldv, r, _ptr(mu), _ptr(nu), m,
+                                 _ptr(out), _stream(stream)))
+    return out
+
+
+def lrfsi_newton_median(mesh, X, mu, nu, eps, max_it, stream=None, allow_noconv=False):
+    """X: K x M device tensor (in: start, out: solution).  Returns (iters, res, status)."""
+    K = len(mu)
+    mu = np.ascontiguousarray(mu, np.float64); nu = np.ascontiguousarray(nu, np.float64)
+    it = np.zeros(K, np.int32); res = np.zeros(K)
+    st = load().lrfsi_newton_median(mesh.h, K, _ptr(X), _ptr(mu), _ptr(nu), eps, max_it, _ptr(it), _ptr(res),
+                                    _stream(stream))
+    _check(st, (ENOCONV,) if allow_noconv else ())
+    return it, res, st
+
+
+def cheb_options(c, d, iters=6, cycles=2, rank_cap=20, tol=1e-8, eta=0.0, precision=0):
+    return lrfsi_cheb_options(c, d, iters, cycles, rank_cap, tol, eta, precision)
+
+
+class Subsets:
+    """K subsets sharing one mesh (lrfsi_subset_create)."""
+
+    def __init__(self, mesh, xt, mu, nu, sizes, caps, stream=None):
+        self.mesh = mesh
+        self.K = len(sizes)
+        self.mu = np.ascontiguousarray(mu, np.float64)
+        self.nu = np.ascontiguousarray(nu, np.float64)
+        self.sizes = np.ascontiguousarray(sizes, np.int32)
+        self.caps = np.ascontiguousarray(caps, np.int32)
+        self.offsets = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
+        self.h = C.c_void_p()
+        _check(load().lrfsi_subset_create(mesh.h, self.K, _ptr(xt), _ptr(self.mu), _ptr(self.nu), _ptr(self.sizes),
+                                          _ptr(self.caps), C.byref(self.h), _stream(stream)))
+
+    def close(self):
+        if self.h:
+            load().lrfsi_subset_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_bytes(self):
+        return int(load().lrfsi_subset_bytes(self.h))
+
+
+def lrfsi_subset_create(mesh, xt, mu, nu, sizes, caps, stream=None):
+    return Subsets(mesh, xt, mu, nu, sizes, caps, stream)
+
+
+def lrfsi_chebyshevT(sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream=None):
+    rB = np.ascontiguousarray(rB, np.int32)
+    ranks = np.zeros(sub.K, np.int32)
+    stats = (lrfsi_cheb_stats * sub.K)()
+    _check(load().lrfsi_chebyshevT(sub.h, _ptr(UB), lduB, _ptr(VB), ldvB, _ptr(rB), C.byref(opt), _ptr(U), ldu,
+                                   _ptr(V), ldv, _ptr(ranks), C.cast(stats, C.c_void_p), _stream(stream)))
+    return ranks, [dict(steps=s.steps, rank=s.rank, rel_lin_res=s.rel_lin_res, max_concat_rank=s.max_concat_rank)
+                   for s in stats]
+
+
+def lrfsi_subset_step(sub, opt, target, max_outer, U, ldu, V, ldv, stream=None, allow_noconv=True):
+    ranks = np.zeros(sub.K, np.int32)
+    rel = np.zeros(int(sub.sizes.sum()))
+    outer = np.zeros(sub.K, np.int32)
+    st = load().lrfsi_subset_step(sub.h, C.byref(opt), target, max_outer, _ptr(U), ldu, _ptr(V), ldv, _ptr(ranks),
+                                  _ptr(rel), _ptr(outer), _stream(stream))
+    _check(st, (ENOCONV,) if allow_noconv else ())
+    return ranks, rel, outer, st
+
+
+def lrfsi_precond_apply(sub, X, ldx, r, Y, ldy, stream=None):
+    r = np.ascontiguousarray(np.broadcast_to(r, (sub.K,)), np.int32)
+    _check(load().lrfsi_precond_apply(sub.h, _ptr(X), ldx, _ptr(r), _ptr(Y), ldy, _stream(stream)))
+
+
+def lrfsi_truncate(sub, X, ldx, V, ldv, p, tol, cap, U, ldu, Vo, ldvo, stream=None):
+    p = np.ascontiguousarray(np.broadcast_to(p, (sub.K,)), np.int32)
+    cap = np.ascontiguousarray(np.broadcast_to(cap, (sub.K,)), np.int32)
+    ranks = np.zeros(sub.K, np.int32)
+    _check(load().lrfsi_truncate(sub.h, _ptr(X), ldx, _ptr(V), ldv, _ptr(p), tol, _ptr(cap), _ptr(U), ldu, _ptr(Vo),
+                                 ldvo, _ptr(ranks), _stream(stream)))
+    return ranks

@@ -115,3 +115,22 @@ def test_relative_residual_definition_and_subset_step(small_subset):
     X = algorithm1.subset_step(m, xt, mu_k, nu_k, opt)
     rr = algorithm1.relative_residuals(m, X, mu_k, nu_k)
     assert rr.max() < 1e-8
+
+
+def test_equilibration_unit_max_norms_and_scaling_invariance(small_subset):
+    m, xt, mu_k, nu_k = small_subset
+    J0, Jmu, Jnu = fsi.affine_jacobian(m, xt)
+    mb, nb = params.midpoint_parameters(mu_k, nu_k)
+    r, c = lowrank.equilibration(J0, Jmu, Jnu, mb, nb)
+    P = (J0 + mb * Jmu + nb * Jnu).toarray()
+    Ps = np.abs(r[:, None] * P * c[None, :])
+    assert np.allclose(Ps.max(axis=0), 1.0, rtol=1e-14)          # every column max is 1
+    assert np.all(Ps.max(axis=1) <= 1.0 + 1e-14)
+    # untruncated Chebyshev is invariant under the two-sided scaling (similarity)
+    R0, Rmu, Rnu = fsi.affine_residual(m, xt)
+    B = lowrank.rhs(R0, Rmu, Rnu, mu_k, nu_k)
+    Pl = lowrank.preconditioner(J0, Jmu, Jnu, mb, nb)
+    S1 = lowrank.chebyshev_T(J0, Jmu, Jnu, Pl, B, mu_k, nu_k, 0.5, 1.0, iters=5, cycles=2, truncated=False)
+    S2 = lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mb, nb, 0.5, 1.0, iters=5, cycles=2,
+                                    truncated=False)
+    assert np.linalg.norm(S1 - S2) <= 1e-10 * np.linalg.norm(S1)
