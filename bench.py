@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark: parameter solves per second of Algorithm 1 to a nonlinear
+relative residual <= 1e-6 in every parameter column, on one GB300 per rank.
+
+One step = the whole hot path over the workload's parameter set: batched
+Newton for the K upper-median problems (from b_D), the K subset operators and
+mean-based preconditioners (assembly, equilibration, block LU), and the
+subset Newton step solved by the truncated preconditioned Chebyshev iteration
+with nonlinear-residual corrections until every column meets the target.
+
+--impl reference times the CPU oracle (the paper's "standard Newton":
+consecutive per-parameter Newton with a sparse direct solve) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2008_10275_gb300 import inputs  # noqa: E402
+
+METRIC = "parameter solves/sec to nonlinear rel. residual 1e-6"
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (profiling recipe's table)
+
+
+def workload_params(W):
+    """Parameters in little-endian order (mu fastest), or nu fastest when the
+    workload asks for it."""
+    mu_g, nu_g = np.array(W.mu_values), np.array(W.nu_values)
+    if W.nu_fastest:
+        return np.repeat(mu_g, len(nu_g)), np.tile(nu_g, len(mu_g))
+    return np.tile(mu_g, len(nu_g)), np.repeat(nu_g, len(mu_g))
+
+
+def subset_layout(m, K):
+    base = m // K
+    sizes = [base] * (K - 1) + [m - (K - 1) * base]
+    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)
+    medians = [int(o + s // 2) for o, s in zip(offs, sizes)]
+    return sizes, medians
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self._stop = threading.Event()
+
+    def _run(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        while not self._stop.is_set():
+            try:
+                out = subprocess.run(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                      "--format=csv,noheader,nounits"], capture_output=True, text=True, timeout=5)
+                parts = [p.strip() for p in out.stdout.strip().split(",")]
+                if len(parts) == 7:
+                    self.samples.append(parts)
+            except Exception:
+                pass
+            self._stop.wait(0.2)
+
+    def __enter__(self):
+        self._t = threading.Thread(target=self._run, daemon=True)
+        self._t.start()
+        return self
+
+    def __exit__(self, *a):
+        self._stop.set()
+        self._t.join(timeout=10)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4) if s[3 + i] == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+def cpu_reference(workload, n_sample, threads=1):
+    """The oracle's standard Newton (Sec. 5.1.2) on the first n_sample
+    parameters of the workload, in a fresh single-threaded process."""
+    code = f"""
+import sys, time, json, numpy as np
+sys.path.insert(0, {ROOT!r})
+from oracle import fsi, newton
+from paper_2008_10275_gb300 import inputs
+W = inputs.WORKLOADS[{workload!r}]
+mu_g, nu_g = np.array(W.mu_values), np.array(W.nu_values)
+if W.nu_fastest:
+    mus, nus = np.repeat(mu_g, len(nu_g)), np.tile(nu_g, len(mu_g))
+else:
+    mus, nus = np.tile(mu_g, len(nu_g)), np.repeat(nu_g, len(mu_g))
+m = fsi.Mesh(fsi.Problem(W.nx, W.ny))
+t = time.perf_counter()
+X, steps, norms = newton.standard_newton(m, mus[:{n_sample}], nus[:{n_sample}], eps=1e-8)
+dt = time.perf_counter() - t
+print(json.dumps(dict(seconds=dt, steps=int(steps), n={n_sample})))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    W = inputs.WORKLOADS[args.workload]
+    vals = []
+    last = None
+    for i in range(args.warmup + args.steps):
+        r = cpu_reference(args.workload, args.ref_sample)
+        if i >= args.warmup:
+            vals.append(r["n"] / r["seconds"])
+        last = r
+    v = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "params/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * last["seconds"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "sample_params": args.ref_sample},
+        "cpu_baseline": {"value": v, "unit": "params/s", "cores": 1, "kind": "oracle",
+                         "sample": f"standard Newton (eps 1e-8) on the first {args.ref_sample} parameters"},
+        "e2e": {"value": v, "unit": "params/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="medium")
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--c", type=float, default=0.65)
+    ap.add_argument("--d", type=float, default=1.0)
+    ap.add_argument("--target", type=float, default=1e-6)
+    ap.add_argument("--max-outer", type=int, default=40)
+    ap.add_argument("--ref-sample", type=int, default=4)
+    ap.add_argument("--eta", type=float, default=0.05)
+    ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (the lrfsi library has no CPU path)")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2008_10275_gb300 import build, lrfsi
+    build.build()
+    lrfsi.load()
+    dev = f"cuda:{local}"
+    W = inputs.WORKLOADS[args.workload]
+    mus, nus = workload_params(W)
+    m = len(mus)
+    sizes, medians = subset_layout(m, W.K)
+    K = W.K
+    caps = [W.rank_cap] * K
+    mesh = lrfsi.Mesh(W.nx, W.ny)
+    bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=dev)
+    R = W.rank_cap
+    U = torch.zeros(K * mesh.M * R, dtype=torch.float64, device=dev)
+    V = torch.zeros(m * R, dtype=torch.float64, device=dev)
+    eps_N = 1e-8
+
+    opt_mixed = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=1,
+                                   eta=args.eta)
+    opt = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=args.precision,
+                             eta=args.eta)
+
+    def step(mu_h, nu_h, o=None):
+        X = bD.repeat(K, 1)
+        it, res, _ = lrfsi.lrfsi_newton_median(mesh, X, mu_h[medians], nu_h[medians], eps_N, 30)
+        sub = lrfsi.Subsets(mesh, X, mu_h, nu_h, sizes, caps)
+        ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, o or opt, args.target, args.max_outer, U, R, V, R)
+        sub.close()
+        return dict(newton_iters=it.tolist(), ranks=ranks.tolist(), outer=outer.tolist(), max_relres=float(rel.max()),
+                    status=int(st), xt=X)
+
+    def dense_solution(info):
+        """X = x~_k 1^T + U_k V_k^T for every subset (M x m) from the last step."""
+        cols = []
+        for k in range(K):
+            r = info["ranks"][k]
+            Uk = U[k * mesh.M * R:(k + 1) * mesh.M * R].view(mesh.M, R)[:, :r]
+            Vk = V[int(np.sum(sizes[:k])) * R:int(np.sum(sizes[:k + 1])) * R].view(sizes[k], R)[:, :r]
+            cols.append(info["xt"][k][:, None] + Uk @ Vk.T)
+        return torch.cat(cols, 1)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+
+    info = None
+    for _ in range(args.warmup):
+        info = step(mus, nus)
+    stream = torch.cuda.current_stream()
+    L0 = lrfsi.kernel_launches()
+    barrier()
+    with Clocks(local) as clk:
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            info = step(mus, nus)
+        e1.record(stream)
+        barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = (lrfsi.kernel_launches() - L0) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * m / (ms * 1e-3)
+
+    X64 = dense_solution(info)
+    mixed = None
+    if not args.no_mixed:
+        # the mixed-precision path (FP32 SpMM / residual GEMM inside the FP64 correction loop)
+        step(mus, nus, opt_mixed)
+        barrier()
+        e4 = torch.cuda.Event(enable_timing=True)
+        e5 = torch.cuda.Event(enable_timing=True)
+        e4.record(stream)
+        for _ in range(args.steps):
+            info_m = step(mus, nus, opt_mixed)
+        e5.record(stream)
+        barrier()
+        ms_m = e4.elapsed_time(e5) / args.steps
+        Xm = dense_solution(info_m)
+        diff = float(torch.linalg.norm(Xm - X64) / torch.linalg.norm(X64 - bD[:, None]))
+        mixed = {"value": world * m / (ms_m * 1e-3), "ms_per_step": ms_m, "max_relres": info_m["max_relres"],
+                 "status": info_m["status"], "outer": info_m["outer"],
+                 "rel_diff_vs_fp64_solution_update": diff}
+
+    # end to end through the public API: host parameter arrays in, factors and
+    # relative residuals back to host memory every step
+    h2d = 2 * m * 8
+    d2h = (K * mesh.M * R + m * R) * 8 + m * 8
+    barrier()
+    e2 = torch.cuda.Event(enable_timing=True)
+    e3 = torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    for _ in range(args.steps):
+        mu_host = np.array(mus, copy=True)
+        nu_host = np.array(nus, copy=True)
+        step(mu_host, nu_host)
+        Uh = U.cpu()
+        Vh = V.cpu()
+    e3.record(stream)
+    barrier()
+    ms_e2e = e2.elapsed_time(e3) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    # roofline of the dominant kernel class: one more step with per-launch events
+    lrfsi.stats_reset()
+    lrfsi.timing(True)
+    step(mus, nus)
+    torch.cuda.synchronize()
+    ks = lrfsi.kernel_stats()
+    lrfsi.timing(False)
+    # block_lu is one timed region per factorisation that contains its GEMMs,
+    # so it overlaps gemm_fp64 and is not a candidate for the dominant kernel
+    dom = max((k for k in ks if k != "block_lu"), key=lambda k: ks[k]["ms"])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    d = ks[dom]
+    if dom in ("gemm_fp64", "gram_fp64", "block_lu", "trunc_small", "fe_assembly"):
+        achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
+                "kernel": dom, "peak_source": "nominal FP64 of the recipe table (not in MEASURED_PEAKS.json)"}
+    else:
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": dom, "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+    roof["per_class_ms"] = {k: round(v["ms"], 3) for k, v in ks.items()}
+    spmm = ks["spmm_fp64"]
+    spmm_gbs = spmm["bytes"] / (spmm["ms"] * 1e-3) / 1e9 if spmm["ms"] > 0 else None
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        try:
+            r = cpu_reference(args.workload, args.ref_sample)
+            cpu = {"value": r["n"] / r["seconds"], "unit": "params/s", "cores": 1, "kind": "oracle",
+                   "sample": f"standard Newton (eps 1e-8) on the first {args.ref_sample} of {m} parameters, "
+                             f"{r['steps']} Newton steps, {r['seconds']:.1f} s"}
+        except Exception as ex:  # reported, not fatal
+            cpu = {"value": None, "unit": "params/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:200]}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "params/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
+            "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "M": mesh.M, "nnz": mesh.nnz, "params": m,
+                       "subsets": K, "rank_cap": R, "tol": W.tol, "cheb": [args.c, args.d, 6, 2],
+                       "target_relres": args.target, "l2": "working set (block-LU factors) larger than L2",
+                       "parallelism": f"replicas x{world}"},
+            "clocks": clk.summary(),
+            "e2e": {"value": world * m / (ms_e2e * 1e-3), "unit": "params/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "spmm_gbs": spmm_gbs,
+            "cpu_baseline": cpu,
+            "result": {k: v for k, v in info.items() if k != "xt"},
+            "mixed": mixed,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -150,6 +150,11 @@ typedef struct {
   double tol;         /* truncation: keep the smallest r with ||s_{>r}|| <= tol ||s|| */
   double eta;         /* stop when ||B - F(S)||_F <= eta ||B||_F (0: run all steps) */
   int precision;      /* 0: FP64; 1: mixed (FP32 SpMM and updates, FP64 truncation/LU) */
+  double tol_sol;     /* lrfsi_subset_step: truncation tolerance of the accumulated solution
+                         (0: 1e-6 * tol).  In the equilibrated norm a deformation error of
+                         relative size e costs about 1e6 e in the unscaled relative residual,
+                         so the accumulated Newton update needs a tighter tolerance than the
+                         inner iteration. */
 } lrfsi_cheb_options;
 
 typedef struct {
@@ -235,12 +240,70 @@ int lrfsi_truncate(lrfsi_subset_h sub, const double* X_dev, int ldx, const doubl
                    const int* p_host, double tol, const int* cap_host, double* U_dev, int ldu,
                    double* Vo_dev, int ldvo, int* rank_host, lrfsi_stream_t stream);
 
+/* ---- Learned initial guess (not a method of the paper) -------------------
+ * A multilayer perceptron maps the scaled parameters z = (mu_s, nu_f) in
+ * [-1, 1]^2 to k coefficients of a POD basis of method-generated solutions:
+ * n_in -> n_h1 -> n_h2 -> n_out with exact-erf GELU after the hidden layers,
+ * BF16 weights, FP32 biases and FP32 accumulation; trained by mean squared
+ * error with Adam (FP32 master weights).  Its prediction starts the median
+ * Newton iteration; the plain start b_D remains the fallback.
+ * Packed parameter layout (host float arrays): for each layer l, the weight
+ * matrix W_l (n_{l+1} x n_l, row-major) followed by the bias b_l. */
+typedef struct lrfsi_mlp_s* lrfsi_mlp_h;
+int lrfsi_mlp_create(int n_in, int n_h1, int n_h2, int n_out, lrfsi_mlp_h* out);
+int lrfsi_mlp_destroy(lrfsi_mlp_h mlp);
+int64_t lrfsi_mlp_num_params(lrfsi_mlp_h mlp);
+/* Set (and reset the Adam state) / get the FP32 master parameters (host). */
+int lrfsi_mlp_set_params(lrfsi_mlp_h mlp, const float* packed_host);
+int lrfsi_mlp_get_params(lrfsi_mlp_h mlp, float* packed_host);
+/* Y (B x n_out) = MLP(Z (B x n_in)); device arrays, row-major. */
+int lrfsi_mlp_forward(lrfsi_mlp_h mlp, const float* Z_dev, int B, float* Y_dev, lrfsi_stream_t stream);
+/* Gradients of L = mean((MLP(Z) - T)^2) w.r.t. the packed parameters into
+ * grad_dev (or the handle's buffer if NULL) and L into loss_dev (or NULL). */
+int lrfsi_mlp_gradients(lrfsi_mlp_h mlp, const float* Z_dev, const float* T_dev, int B, float* grad_dev,
+                        float* loss_dev, lrfsi_stream_t stream);
+/* epochs full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8); loss_host: last loss. */
+int lrfsi_mlp_train(lrfsi_mlp_h mlp, const float* Z_dev, const float* T_dev, int B, int epochs, float lr,
+                    float* loss_host, lrfsi_stream_t stream);
+/* X (B x M, problem-major, device) = offset + field_scale .* (Phi (coef_scale .* MLP(Z))),
+ * Dirichlet rows overwritten with b_D.  Phi: M x k (ldphi, device FP64); coef_scale (k),
+ * field_scale (M), offset (M): device FP64.  Synchronizes the stream. */
+int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, const float* Z_dev, int B, const double* Phi_dev,
+                        int ldphi, int k, const double* coef_scale_dev, const double* field_scale_dev,
+                        const double* offset_dev, double* X_dev, lrfsi_stream_t stream);
+
+/* lrfsi_pod: rank-k POD of the snapshot columns X (M x n, ldx): the leading k
+ * left singular vectors Phi (M x k, ldphi, orthonormal columns) and the
+ * coefficients C (n x k, ldc) with X ~ Phi C^T, by the same Cholesky-QR +
+ * Jacobi machinery as the truncation T.  sigma_host: k singular values. */
+int lrfsi_pod(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int n, int k, double* Phi_dev, int ldphi,
+              double* C_dev, int ldc, double* sigma_host, lrfsi_stream_t stream);
+
 /* Device memory held by a handle (bytes). */
 size_t lrfsi_mesh_bytes(lrfsi_mesh_h mesh);
 size_t lrfsi_subset_bytes(lrfsi_subset_h sub);
 
 /* Number of kernels this library has launched in the calling process. */
 uint64_t lrfsi_kernel_launches(void);
+
+/* Per-kernel-class accounting for roofline reports.  Classes:
+ * 0 FP64 dense GEMM, 1 SpMM (FP64), 2 Gram products (FP64), 3 block-LU panel
+ * and triangular kernels, 4 FE assembly and residuals, 5 FP32 dense GEMM,
+ * 6 SpMM (FP32), 7 small per-subset truncation kernels.  For every launch the library adds the algorithmic FLOPs and
+ * HBM bytes of the launch (from its shape) to the class counters; with timing
+ * enabled it also brackets each launch with CUDA events on the launching
+ * stream and accumulates the elapsed time when lrfsi_stats is called (which
+ * synchronizes those events). */
+#define LRFSI_NUM_KERNEL_CLASSES 8
+typedef struct {
+  uint64_t launches;
+  double flops;        /* algorithmic floating-point operations */
+  double bytes;        /* algorithmic bytes moved to/from HBM */
+  double ms;           /* summed event time (timing enabled only) */
+} lrfsi_kernel_stat;
+int lrfsi_stats(int kernel_class, lrfsi_kernel_stat* out);
+int lrfsi_stats_reset(void);
+int lrfsi_timing(int enable);
 
 const char* lrfsi_last_error(void);
 

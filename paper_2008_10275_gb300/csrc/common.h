@@ -28,6 +28,17 @@ int cuda_fail(cudaError_t e, const char* what);
     if (s_ != LRFSI_OK) return s_;   \
   } while (0)
 
+// per-class accounting (see lrfsi_stats); timed_begin/timed_end bracket a
+// launch with events when timing is enabled
+enum KClass { KC_GEMM = 0, KC_SPMM = 1, KC_GRAM = 2, KC_LU = 3, KC_FE = 4, KC_GEMM32 = 5, KC_SPMM32 = 6, KC_TRUNC = 7 };
+void account(int cls, double flops, double bytes);
+struct TimedLaunch {
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  TimedLaunch(int c, cudaStream_t s);
+  void end(cudaStream_t s);
+};
+
 // every kernel launch goes through count_launch() so that the process-wide
 // launch counter (lrfsi_kernel_launches) is exact
 void count_launch(uint64_t n = 1);

@@ -26,81 +26,156 @@ struct GemmBatch {
 
 constexpr int GBM = 64, GBN = 64, GBK = 16;
 
-template <class T>
-__global__ void __launch_bounds__(256) k_gemm(GemmBatch<T> gb) {
-  const GemmDesc<T> g = gb.d[blockIdx.z];
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
+// Tile BM x BN, 256 threads, (BM/16) x (BN/16) outputs per thread.  With
+// ks > 1 the k range is split: chunk c of descriptor z writes alpha * A B over
+// its k slice to part[z][c] (m x n dense) and k_gemm_reduce adds the chunks in
+// order (deterministic) together with beta * C.
+template <class T, int BM, int BN>
+__global__ void __launch_bounds__(256) k_gemm(GemmBatch<T> gb, int ks, T* __restrict__ part, long part_stride) {
+  const int z = blockIdx.z / ks, chunk = blockIdx.z % ks;
+  const GemmDesc<T> g = gb.d[z];
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
   if (m0 >= g.m || n0 >= g.n) return;
-  __shared__ T As[GBK][GBM + 1];
-  __shared__ T Bs[GBK][GBN + 1];
+  constexpr int RM = BM / 16, RN = BN / 16;
+  __shared__ T As[GBK][BM + 1];
+  __shared__ T Bs[GBK][BN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  T acc[4][4];
+  T acc[RM][RN];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RM; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0;
+    for (int c = 0; c < RN; ++c) acc[r][c] = 0;
   const bool a_kfast = g.a_cs == 1, b_nfast = g.b_cs == 1;
-  for (int k0 = 0; k0 < g.k; k0 += GBK) {
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int idx = threadIdx.x + 256 * e;
+  const int kc = (g.k + ks - 1) / ks;
+  const int kbeg = chunk * kc, kend = kbeg + kc < g.k ? kbeg + kc : g.k;
+  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
+    for (int idx = threadIdx.x; idx < BM * GBK; idx += 256) {
       int i, l;
-      if (a_kfast) { l = idx % GBK; i = idx / GBK; } else { i = idx % GBM; l = idx / GBM; }
+      if (a_kfast) { l = idx % GBK; i = idx / GBK; } else { i = idx % BM; l = idx / BM; }
       const int gi = m0 + i, gl = k0 + l;
-      As[l][i] = (gi < g.m && gl < g.k) ? g.A[(long)gi * g.a_rs + (long)gl * g.a_cs] : T(0);
-      int j;
-      if (b_nfast) { j = idx % GBN; l = idx / GBN; } else { l = idx % GBK; j = idx / GBK; }
-      const int gj = n0 + j, gl2 = k0 + l;
-      Bs[l][j] = (gj < g.n && gl2 < g.k) ? g.B[(long)gl2 * g.b_rs + (long)gj * g.b_cs] : T(0);
+      As[l][i] = (gi < g.m && gl < kend) ? g.A[(long)gi * g.a_rs + (long)gl * g.a_cs] : T(0);
+    }
+    for (int idx = threadIdx.x; idx < BN * GBK; idx += 256) {
+      int j, l;
+      if (b_nfast) { j = idx % BN; l = idx / BN; } else { l = idx % GBK; j = idx / GBK; }
+      const int gj = n0 + j, gl = k0 + l;
+      Bs[l][j] = (gj < g.n && gl < kend) ? g.B[(long)gl * g.b_rs + (long)gj * g.b_cs] : T(0);
     }
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < GBK; ++l) {
-      T a[4], b[4];
+      T a[RM], bb[RN];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[l][ty + 16 * r];
+      for (int r = 0; r < RM; ++r) a[r] = As[l][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = Bs[l][tx + 16 * c];
+      for (int c = 0; c < RN; ++c) bb[c] = Bs[l][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RM; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < RN; ++c) acc[r][c] = fma(a[r], bb[c], acc[r][c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < RM; ++r) {
     const int gi = m0 + ty + 16 * r;
     if (gi >= g.m) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < RN; ++c) {
       const int gj = n0 + tx + 16 * c;
       if (gj >= g.n) continue;
-      T* cp = g.C + (long)gi * g.c_rs + (long)gj * g.c_cs;
-      T v = g.alpha * acc[r][c];
-      if (g.beta != T(0)) v += g.beta * *cp;
-      *cp = v;
+      if (ks > 1) {
+        part[(long)blockIdx.z * part_stride + (long)gi * g.n + gj] = g.alpha * acc[r][c];
+      } else {
+        T* cp = g.C + (long)gi * g.c_rs + (long)gj * g.c_cs;
+        T v = g.alpha * acc[r][c];
+        if (g.beta != T(0)) v += g.beta * *cp;
+        *cp = v;
+      }
     }
   }
 }
 
 template <class T>
+__global__ void k_gemm_reduce(GemmBatch<T> gb, int ks, const T* __restrict__ part, long part_stride) {
+  const GemmDesc<T> g = gb.d[blockIdx.y];
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)g.m * g.n) return;
+  const int i = (int)(e / g.n), j = (int)(e % g.n);
+  T v = 0;
+  for (int c = 0; c < ks; ++c) v += part[((long)blockIdx.y * ks + c) * part_stride + e];
+  T* cp = g.C + (long)i * g.c_rs + (long)j * g.c_cs;
+  if (g.beta != T(0)) v += g.beta * *cp;
+  *cp = v;
+}
+
+// process-wide split-K workspace (grown on demand, never shrunk)
+static void* g_gemm_ws = nullptr;
+static size_t g_gemm_ws_bytes = 0;
+
+template <class T>
 int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
+  constexpr int kTarget = 2 * 152;  // enough CTAs to occupy every SM's FP64 unit twice
   for (int base = 0; base < n; base += kMaxGemmDescs) {
     GemmBatch<T> gb;
-    int cnt = 0, mm = 0, nn = 0;
+    int cnt = 0, mm = 0, nn = 0, kk = 0;
     for (int i = base; i < n && cnt < kMaxGemmDescs; ++i) {
       if (descs[i].m <= 0 || descs[i].n <= 0) continue;
       gb.d[cnt] = descs[i];
-      if (descs[i].k <= 0) { gb.d[cnt].k = 0; }
+      if (descs[i].k <= 0) gb.d[cnt].k = 0;
       mm = mm > descs[i].m ? mm : descs[i].m;
       nn = nn > descs[i].n ? nn : descs[i].n;
+      kk = kk > descs[i].k ? kk : descs[i].k;
       ++cnt;
     }
     if (!cnt) continue;
-    dim3 grid(ceil_div(nn, GBN), ceil_div(mm, GBM), cnt);
-    k_gemm<T><<<grid, 256, 0, s>>>(gb);
+    {
+      double fl = 0, by = 0;
+      for (int i = 0; i < cnt; ++i) {
+        const GemmDesc<T>& g = gb.d[i];
+        fl += 2.0 * g.m * g.n * g.k;
+        by += sizeof(T) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != T(0) ? 2.0 : 1.0) * g.m * g.n);
+      }
+      account(sizeof(T) == 8 ? KC_GEMM : KC_GEMM32, fl, by);
+    }
+    TimedLaunch tl(sizeof(T) == 8 ? KC_GEMM : KC_GEMM32, s);
+    const long tiles64 = (long)ceil_div(nn, 64) * ceil_div(mm, 64) * cnt;
+    if (tiles64 >= kTarget || (mm >= 1024 && nn >= 64)) {
+      dim3 grid(ceil_div(nn, 64), ceil_div(mm, 64), cnt);
+      k_gemm<T, 64, 64><<<grid, 256, 0, s>>>(gb, 1, (T*)nullptr, 0);
+      LRFSI_TRY(check_launch("k_gemm"));
+      tl.end(s);
+      continue;
+    }
+    const long tiles32 = (long)ceil_div(nn, 32) * ceil_div(mm, 32) * cnt;
+    int ks = 1;
+    if (tiles32 < kTarget && kk >= 4 * GBK) {
+      ks = (int)((kTarget + tiles32 - 1) / tiles32);
+      const int kmax = kk / (2 * GBK);
+      if (ks > kmax) ks = kmax;
+      if (ks > 16) ks = 16;
+      if (ks < 1) ks = 1;
+    }
+    const long pstride = (long)mm * nn;
+    if (ks > 1) {
+      const size_t need = sizeof(T) * (size_t)cnt * ks * pstride;
+      if (need > g_gemm_ws_bytes) {
+        if (g_gemm_ws) cudaFree(g_gemm_ws);
+        g_gemm_ws = nullptr;
+        g_gemm_ws_bytes = 0;
+        LRFSI_CUDA(cudaMalloc(&g_gemm_ws, need));
+        g_gemm_ws_bytes = need;
+      }
+    }
+    dim3 grid(ceil_div(nn, 32), ceil_div(mm, 32), cnt * ks);
+    k_gemm<T, 32, 32><<<grid, 256, 0, s>>>(gb, ks, (T*)g_gemm_ws, pstride);
     LRFSI_TRY(check_launch("k_gemm"));
+    if (ks > 1) {
+      dim3 g2(ceil_div(pstride, 256), cnt);
+      k_gemm_reduce<T><<<g2, 256, 0, s>>>(gb, ks, (const T*)g_gemm_ws, pstride);
+      LRFSI_TRY(check_launch("k_gemm_reduce"));
+    }
+    tl.end(s);
   }
   return LRFSI_OK;
 }
@@ -208,12 +283,22 @@ int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t wor
     const size_t fit = work_len / ((size_t)cnt * pmax * qmax);
     if (fit < 1) return fail(LRFSI_EINVAL, "gram workspace too small");
     if ((size_t)nsplit > fit) nsplit = (int)fit;
+    {
+      double fl = 0, by = 0;
+      for (int i = 0; i < cnt; ++i) {
+        fl += 2.0 * M * gb.d[i].p * gb.d[i].q;
+        by += 8.0 * M * (gb.d[i].A == gb.d[i].B ? gb.d[i].p : gb.d[i].p + gb.d[i].q);
+      }
+      account(KC_GRAM, fl, by);
+    }
+    TimedLaunch tl(KC_GRAM, s);
     dim3 grid(ceil_div(pmax, GBM) * ceil_div(qmax, GBN), nsplit, cnt);
     k_gram_partial<<<grid, 256, 0, s>>>(gb, M, nsplit, pmax, qmax, work);
     LRFSI_TRY(check_launch("k_gram_partial"));
     dim3 g2(ceil_div((long)pmax * qmax, 256), cnt);
     k_gram_reduce<<<g2, 256, 0, s>>>(gb, nsplit, pmax, qmax, work);
     LRFSI_TRY(check_launch("k_gram_reduce"));
+    tl.end(s);
   }
   return LRFSI_OK;
 }
@@ -224,16 +309,25 @@ int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t wor
 constexpr int kSmallThreads = 1024;
 
 // Inverse of the k x k upper triangular R (row-major, ldr) into Ri (row-major,
-// ldi); one thread per column, back substitution.
+// ldi): rows from the bottom up; in row a every warp computes entries
+// Ri[a][b] = -(sum_{l=a+1..b} R[a][l] Ri[l][b]) / R[a][a] with a lane-split dot
+// product.  Must be called by the whole block.
 __device__ void upper_inverse(const double* R, int ldr, double* Ri, int ldi, int k) {
-  for (int b = threadIdx.x; b < k; b += blockDim.x) {
-    for (int a = k - 1; a > b; --a) Ri[(size_t)a * ldi + b] = 0.0;
-    Ri[(size_t)b * ldi + b] = 1.0 / R[(size_t)b * ldr + b];
-    for (int a = b - 1; a >= 0; --a) {
-      double s = 0;
-      for (int l = a + 1; l <= b; ++l) s += R[(size_t)a * ldr + l] * Ri[(size_t)l * ldi + b];
-      Ri[(size_t)a * ldi + b] = -s / R[(size_t)a * ldr + a];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
+    const int i = (int)(e / k), j = (int)(e % k);
+    if (j < i) Ri[(size_t)i * ldi + j] = 0.0;
+  }
+  for (int a = k - 1; a >= 0; --a) {
+    const double inv = 1.0 / R[(size_t)a * ldr + a];
+    for (int b = a + warp; b < k; b += nw) {
+      double sacc = 0;
+      for (int l = a + 1 + lane; l <= b; l += 32) sacc += R[(size_t)a * ldr + l] * Ri[(size_t)l * ldi + b];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+      if (lane == 0) Ri[(size_t)a * ldi + b] = (b == a) ? inv : -sacc * inv;
     }
+    __syncthreads();
   }
 }
 
@@ -271,19 +365,31 @@ size_t trunc_small_work(int p, int m) {
 
 // One-sided Jacobi on A (L x n, column-major, n <= L), accumulating the n x n
 // rotation Vm (column-major): A_out = A_in Vm with orthogonal columns.  Pairs
-// follow a round-robin tournament, one warp per pair.  Returns the sweeps used
-// (or -1 if not converged within max_sweeps).
+// follow a round-robin tournament, one half-warp per pair.  A pair is rotated
+// when |a_x . a_y| > 4 eps sqrt(|a_x|^2 |a_y|^2) and neither column is below
+// eps times the largest column norm (such columns carry no information at
+// working precision).  Returns the sweeps used (or -1 if not converged).
 __device__ int jacobi_onesided(double* A, int L, int n, double* Vm, int max_sweeps) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const int hl = threadIdx.x & 15, half = threadIdx.x >> 4, nh = blockDim.x >> 4;
+  const unsigned mask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
   __shared__ int s_rot;
+  __shared__ double s_cmax;
   for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) Vm[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
+  if (threadIdx.x == 0) s_cmax = 0.0;
   __syncthreads();
   const int np = n + (n & 1);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
+    // largest squared column norm (for the negligible-column test)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      double t = 0;
+      for (int i = 0; i < L; ++i) t += A[(size_t)j * L + i] * A[(size_t)j * L + i];
+      atomicMax((unsigned long long*)&s_cmax, (unsigned long long)__double_as_longlong(t));
+    }
     __syncthreads();
+    const double small2 = s_cmax * 1e-32;
     for (int round = 0; round < np - 1; ++round) {
-      for (int k = warp; k < np / 2; k += nwarps) {
+      for (int k = half; k < np / 2; k += nh) {
         auto pos = [&](int t) { return t == 0 ? 0 : ((round + t - 1) % (np - 1)) + 1; };
         int x = pos(k), y = pos(np - 1 - k);
         if (x >= n || y >= n) continue;
@@ -291,33 +397,33 @@ __device__ int jacobi_onesided(double* A, int L, int n, double* Vm, int max_swee
         double* ax = A + (size_t)x * L;
         double* ay = A + (size_t)y * L;
         double al = 0, be = 0, ga = 0;
-        for (int i = lane; i < L; i += 32) {
+        for (int i = hl; i < L; i += 16) {
           const double u = ax[i], v = ay[i];
           al += u * u; be += v * v; ga += u * v;
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, o);
-          be += __shfl_xor_sync(0xffffffffu, be, o);
-          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(mask, al, o);
+          be += __shfl_xor_sync(mask, be, o);
+          ga += __shfl_xor_sync(mask, ga, o);
         }
-        if (ga != 0.0 && fabs(ga) > 1e-15 * sqrt(al * be)) {
+        if (al > small2 && be > small2 && fabs(ga) > 4.4e-16 * sqrt(al * be)) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
           const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-          for (int i = lane; i < L; i += 32) {
+          for (int i = hl; i < L; i += 16) {
             const double u = ax[i], v = ay[i];
             ax[i] = c * u - sn * v;
             ay[i] = sn * u + c * v;
           }
           double* vx = Vm + (size_t)x * n;
           double* vy = Vm + (size_t)y * n;
-          for (int i = lane; i < n; i += 32) {
+          for (int i = hl; i < n; i += 16) {
             const double u = vx[i], v = vy[i];
             vx[i] = c * u - sn * v;
             vy[i] = sn * u + c * v;
           }
-          if (lane == 0) atomicAdd(&s_rot, 1);
+          if (hl == 0) atomicAdd(&s_rot, 1);
         }
       }
       __syncthreads();
@@ -361,8 +467,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
   double* G = d.G;         // p x p, original column order; Schur complements in place
   double* R = W.Rk;        // k x p, R[a][b] = R1 entry for permuted columns a, b (b >= a)
   int* perm = d.iwork;
-  __shared__ double s_val[kSmallThreads];
-  __shared__ int s_idx[kSmallThreads];
+  __shared__ double s_val[33];
+  __shared__ int s_idx[33];
   __shared__ int s_k;
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
     const double g = G[(size_t)i * p + i];
@@ -385,22 +491,29 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
       const double v = G[(size_t)pj * p + pj];
       if (v > best) { best = v; bj = j; }
     }
-    s_val[threadIdx.x] = best;
-    s_idx[threadIdx.x] = bj;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        const double v2 = s_val[threadIdx.x + o];
-        const int j2 = s_idx[threadIdx.x + o];
-        if (v2 > s_val[threadIdx.x] || (v2 == s_val[threadIdx.x] && j2 < s_idx[threadIdx.x])) {
-          s_val[threadIdx.x] = v2;
-          s_idx[threadIdx.x] = j2;
-        }
-      }
-      __syncthreads();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+      if (v2 > best || (v2 == best && j2 < bj)) { best = v2; bj = j2; }
     }
-    const double piv = s_val[0];
-    const int jm = s_idx[0];
+    if ((threadIdx.x & 31) == 0) { s_val[threadIdx.x >> 5] = best; s_idx[threadIdx.x >> 5] = bj; }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      const int nw = blockDim.x >> 5;
+      best = threadIdx.x < nw ? s_val[threadIdx.x] : -1.0;
+      bj = threadIdx.x < nw ? s_idx[threadIdx.x] : 0x7fffffff;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
+        if (v2 > best || (v2 == best && j2 < bj)) { best = v2; bj = j2; }
+      }
+      if (threadIdx.x == 0) { s_val[32] = best; s_idx[32] = bj; }
+    }
+    __syncthreads();
+    const double piv = s_val[32];
+    const int jm = s_idx[32];
     if (!(piv > d.drop) || !isfinite(piv)) {
       if (threadIdx.x == 0) s_k = i;
       break;  // uniform: every thread read the same s_val[0]
@@ -529,7 +642,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_svd(TruncDesc* descs) {
     W.A[e] = cols_of_C ? W.Y[(size_t)i * m + col] : W.Y[(size_t)col * m + i];
   }
   __syncthreads();
-  const int sweeps = jacobi_onesided(W.A, L, n, W.Vm, 60);
+  const int sweeps = jacobi_onesided(W.A, L, n, W.Vm, 40);
   __syncthreads();
   double* sraw = W.C;  // n unsorted singular values
   double* sig = d.sv;
@@ -589,18 +702,30 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_svd(TruncDesc* descs) {
 
 int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
   LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
+  account(KC_TRUNC, 0, 0);
+  TimedLaunch tl(KC_TRUNC, s);
   k_trunc_pass1<<<n, kSmallThreads, 0, s>>>(d_dev);
-  return check_launch("k_trunc_pass1");
+  LRFSI_TRY(check_launch("k_trunc_pass1"));
+  tl.end(s);
+  return LRFSI_OK;
 }
 
 int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev) {
+  account(KC_TRUNC, 0, 0);
+  TimedLaunch tl(KC_TRUNC, s);
   k_trunc_qr<<<n, kSmallThreads, 0, s>>>(d_dev);
-  return check_launch("k_trunc_qr");
+  LRFSI_TRY(check_launch("k_trunc_qr"));
+  tl.end(s);
+  return LRFSI_OK;
 }
 
 int trunc_svd(int n, cudaStream_t s, TruncDesc* d_dev) {
+  account(KC_TRUNC, 0, 0);
+  TimedLaunch tl(KC_TRUNC, s);
   k_trunc_svd<<<n, kSmallThreads, 0, s>>>(d_dev);
-  return check_launch("k_trunc_svd");
+  LRFSI_TRY(check_launch("k_trunc_svd"));
+  tl.end(s);
+  return LRFSI_OK;
 }
 
 }  // namespace lrfsi

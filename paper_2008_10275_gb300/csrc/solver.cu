@@ -32,6 +32,41 @@ int cuda_fail(cudaError_t e, const char* what) {
 }
 void count_launch(uint64_t n) { g_launches += n; }
 
+static std::mutex g_stat_mu;
+static lrfsi_kernel_stat g_stat[LRFSI_NUM_KERNEL_CLASSES];
+static bool g_timing = false;
+struct PendingEv { int cls; cudaEvent_t a, b; };
+static std::vector<PendingEv> g_pending;
+void account(int cls, double flops, double bytes) {
+  std::lock_guard<std::mutex> lk(g_stat_mu);
+  g_stat[cls].launches += 1;
+  g_stat[cls].flops += flops;
+  g_stat[cls].bytes += bytes;
+}
+TimedLaunch::TimedLaunch(int c, cudaStream_t s) : cls(c) {
+  if (!g_timing) return;
+  if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) { a = b = nullptr; return; }
+  cudaEventRecord(a, s);
+}
+void TimedLaunch::end(cudaStream_t s) {
+  if (!a) return;
+  cudaEventRecord(b, s);
+  std::lock_guard<std::mutex> lk(g_stat_mu);
+  g_pending.push_back(PendingEv{cls, a, b});
+  a = b = nullptr;
+}
+static void collect_events() {
+  std::lock_guard<std::mutex> lk(g_stat_mu);
+  for (auto& e : g_pending) {
+    float ms = 0;
+    if (cudaEventSynchronize(e.b) == cudaSuccess && cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess)
+      g_stat[e.cls].ms += ms;
+    cudaEventDestroy(e.a);
+    cudaEventDestroy(e.b);
+  }
+  g_pending.clear();
+}
+
 // ---------------------------------------------------------------------------
 // small helper kernels
 // ---------------------------------------------------------------------------
@@ -77,6 +112,49 @@ static int copy_batched(const std::vector<CopyDesc>& v, cudaStream_t s) {
     if (!cnt) continue;
     k_blockcopy<<<dim3(ceil_div(mx, 256), cnt), 256, 0, s>>>(cb);
     LRFSI_TRY(check_launch("k_blockcopy"));
+  }
+  return LRFSI_OK;
+}
+
+// Block copy with precision conversion: dst[i*ldd + j] = (Tout) (alpha * rowscale[i] * src[i*lds + j])
+struct ConvDesc {
+  const void* src;
+  long lds;
+  void* dst;
+  long ldd;
+  long rows;
+  int ncols;
+  const double* rowscale;
+  double alpha;
+};
+struct ConvBatch {
+  ConvDesc d[kMaxGemmDescs];
+};
+template <class Tin, class Tout>
+__global__ void k_convert(ConvBatch cb) {
+  const ConvDesc& d = cb.d[blockIdx.y];
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= d.rows * d.ncols) return;
+  const long i = e / d.ncols;
+  const int j = (int)(e % d.ncols);
+  double v = (double)((const Tin*)d.src)[i * d.lds + j] * d.alpha;
+  if (d.rowscale) v *= d.rowscale[i];
+  ((Tout*)d.dst)[i * d.ldd + j] = (Tout)v;
+}
+template <class Tin, class Tout>
+static int convert_batched(const std::vector<ConvDesc>& v, cudaStream_t s) {
+  for (size_t base = 0; base < v.size(); base += kMaxGemmDescs) {
+    ConvBatch cb;
+    int cnt = 0;
+    long mx = 0;
+    for (size_t i = base; i < v.size() && cnt < kMaxGemmDescs; ++i) {
+      if (v[i].rows <= 0 || v[i].ncols <= 0) continue;
+      cb.d[cnt++] = v[i];
+      mx = std::max(mx, v[i].rows * v[i].ncols);
+    }
+    if (!cnt) continue;
+    k_convert<Tin, Tout><<<dim3(ceil_div(mx, 256), cnt), 256, 0, s>>>(cb);
+    LRFSI_TRY(check_launch("k_convert"));
   }
   return LRFSI_OK;
 }
@@ -164,6 +242,25 @@ using namespace lrfsi;
 extern "C" {
 
 const char* lrfsi_last_error(void) { return g_err.c_str(); }
+
+int lrfsi_stats(int cls, lrfsi_kernel_stat* out) {
+  if (cls < 0 || cls >= LRFSI_NUM_KERNEL_CLASSES || !out) return fail(LRFSI_EINVAL, "lrfsi_stats: bad class");
+  collect_events();
+  std::lock_guard<std::mutex> lk(g_stat_mu);
+  *out = g_stat[cls];
+  return LRFSI_OK;
+}
+int lrfsi_stats_reset(void) {
+  collect_events();
+  std::lock_guard<std::mutex> lk(g_stat_mu);
+  for (auto& st : g_stat) st = lrfsi_kernel_stat{0, 0, 0, 0};
+  return LRFSI_OK;
+}
+int lrfsi_timing(int enable) {
+  collect_events();
+  g_timing = enable != 0;
+  return LRFSI_OK;
+}
 uint64_t lrfsi_kernel_launches(void) { return g_launches.load(); }
 
 int lrfsi_mesh_create(const lrfsi_problem* prob, lrfsi_mesh_h* out) {
@@ -476,8 +573,9 @@ struct lrfsi_subset_s {
   std::vector<double> mu_h, nu_h, mubar, nubar;
   DevBuf<double> mu, nu, xt, J3, R3;
   DevBuf<double> rsc, csc;  // K x M equilibration scales (rows, columns)
+  DevBuf<float> J3f, USf, Yf, Xf, Vf;  // FP32 operator copies and inner-residual buffers (mixed mode)
   BlockLU lu;
-  DevBuf<double> Xcat, Q1, US, UD, UR, UZ, UB, Ytmp, UC;  // K x M x ld
+  DevBuf<double> Xcat, Q1, Q2, US, UD, UR, UZ, UB, Ytmp, UC;  // K x M x ld
   DevBuf<double> Vcat, VS, VD, VR, VB, VC;                // mtot x ld
   DevBuf<double> G, G2, T1, T2, swork, sv, frob2, gramwork;
   DevBuf<int> iwork, info;
@@ -494,9 +592,10 @@ namespace lrfsi {
 
 // T([X | ...], [V | ...]) for the listed subsets.  Inputs in Xcat (ld ldP) and
 // Vcat (ld ldP) with p[k] columns; outputs U (tall, ld ldR) and V (ld ldR).
-static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
-                          const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
-                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s) {
+static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
+                         const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
+                         std::vector<int>& rank, std::vector<double>& frob2, double drop, std::vector<int>& broke,
+                         cudaStream_t s) {
   const int na = (int)act.size();
   rank.assign(S->K, 0);
   frob2.assign(S->K, 0.0);
@@ -527,7 +626,7 @@ static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const 
     d.frob2 = S->frob2.p + k;
     d.tol = tol;
     d.rank_cap = cap[k];
-    d.drop = 1e-14;
+    d.drop = drop;
   }
   LRFSI_TRY(gram_batched(gd.data(), na, M, S->gramwork.p, S->gramwork.n, s));
   LRFSI_TRY(trunc_pass1(td.data(), na, s, S->tdesc.p));
@@ -552,20 +651,22 @@ static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const 
   };
   LRFSI_TRY(read_info());
   // a third Cholesky-QR pass where the pass-1 basis was far from orthonormal:
-  // Q2 = Q1 R2^{-1} (into Xcat, no longer needed), G3 = Q2^T Q2, R3, Y <- R3 Y
+  // Q2 = Q1 R2^{-1}, G3 = Q2^T Q2, R3, Y <- R3 Y (the input X stays intact for a retry)
   std::vector<char> third(S->K, 0);
   std::vector<TruncDesc> td2;
   std::vector<GemmDesc<double>> g2;
   std::vector<GramDesc> gd2;
+  broke.clear();
+  std::vector<char> bad(S->K, 0);
   for (int a = 0; a < na; ++a) {
     const int k = act[a];
-    if (info[5 * k + 2] != 0) return fail(LRFSI_EBREAKDOWN, "truncation: Cholesky-QR breakdown");
+    if (info[5 * k + 2] == LRFSI_EBREAKDOWN) { bad[k] = 1; continue; }
     if (info[5 * k + 4]) {
       third[k] = 1;
       const int kk = info[5 * k];
       g2.push_back(GemmDesc<double>{(int)M, kk, kk, S->tall(S->Q1, k, ldP), ldP, 1, td[a].T2, p[k], 1,
-                                    S->tall(S->Xcat, k, ldP), ldP, 1, 1.0, 0.0});
-      gd2.push_back(GramDesc{S->tall(S->Xcat, k, ldP), ldP, kk, S->tall(S->Xcat, k, ldP), ldP, kk, td[a].G2, p[k]});
+                                    S->tall(S->Q2, k, ldP), ldP, 1, 1.0, 0.0});
+      gd2.push_back(GramDesc{S->tall(S->Q2, k, ldP), ldP, kk, S->tall(S->Q2, k, ldP), ldP, kk, td[a].G2, p[k]});
       td2.push_back(td[a]);
     }
   }
@@ -579,16 +680,58 @@ static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const 
   std::vector<double> f2(S->K);
   LRFSI_CUDA(cudaMemcpyAsync(f2.data(), S->frob2.p, sizeof(double) * S->K, cudaMemcpyDeviceToHost, s));
   LRFSI_TRY(read_info());
+  {  // algorithmic FP64 work of the small kernels (upper bound: every Jacobi pair rotated)
+    double fl = 0;
+    for (int a = 0; a < na; ++a) {
+      const int k = act[a];
+      const double P = p[k], kk = info[5 * k], mm = S->m[k];
+      const double n = std::min(kk, mm), L = std::max(kk, mm), sw = std::max(info[5 * k + 3], 1);
+      fl += 2.0 * P * P * P / 3.0 + kk * kk * kk / 3.0 + 2.0 * kk * mm * P;     // pass 1
+      fl += (third[k] ? 2.0 : 1.0) * (2.0 * kk * kk * kk / 3.0 + 2.0 * kk * kk * mm);  // QR passes
+      fl += sw * n * (n - 1) / 2.0 * (6.0 * L + 4.0 * n) + 2.0 * n * n * L;    // Jacobi
+    }
+    account(KC_TRUNC, fl, 0);
+  }
   for (int a = 0; a < na; ++a) {
     const int k = act[a];
     rank[k] = info[5 * k + 1];
     frob2[k] = f2[k];
-    if (info[5 * k + 2] == LRFSI_EBREAKDOWN) return fail(LRFSI_EBREAKDOWN, "truncation: Cholesky-QR breakdown");
-    const double* Qlast = third[k] ? S->tall(S->Xcat, k, ldP) : S->tall(S->Q1, k, ldP);
+    if (bad[k] || info[5 * k + 2] == LRFSI_EBREAKDOWN) {
+      bad[k] = 1;
+      broke.push_back(k);
+      rank[k] = 0;
+      gm[a].n = 0;  // no output GEMM for this subset
+      continue;
+    }
+    const double* Qlast = third[k] ? S->tall(S->Q2, k, ldP) : S->tall(S->Q1, k, ldP);
     gm[a] = GemmDesc<double>{(int)M, rank[k], info[5 * k], Qlast, ldP, 1, td[a].T1, p[k], 1, Uout[k], ldR, 1, 1.0,
                              0.0};
   }
   LRFSI_TRY(gemm_grouped<double>(gm.data(), na, s));
+  return LRFSI_OK;
+}
+
+// T with a retry: a Cholesky-QR breakdown (basis still too ill-conditioned
+// after dropping) is retried with a 100x larger drop threshold, at most three
+// times (the lost relative remainder grows from 1e-7 to 1e-4 of a column).
+static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
+                          const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
+                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s) {
+  std::vector<int> broke, todo = act;
+  rank.assign(S->K, 0);
+  frob2.assign(S->K, 0.0);
+  double drop = 1e-14;
+  for (int attempt = 0; attempt < 4 && !todo.empty(); ++attempt, drop *= 100.0) {
+    std::vector<int> rk;
+    std::vector<double> f2;
+    LRFSI_TRY(truncate_once(S, todo, p, tol, cap, Uout, Vout, rk, f2, drop, broke, s));
+    for (int k : todo) {
+      rank[k] = rk[k];
+      frob2[k] = f2[k];
+    }
+    todo = broke;
+  }
+  if (!todo.empty()) return fail(LRFSI_EBREAKDOWN, "truncation: Cholesky-QR breakdown after retries");
   return LRFSI_OK;
 }
 
@@ -602,13 +745,44 @@ extern "C" int lrfsi_subset_destroy(lrfsi_subset_h S) {
 extern "C" size_t lrfsi_subset_bytes(lrfsi_subset_h S) {
   if (!S) return 0;
   size_t b = 0;
-  for (DevBuf<double>* p : {&S->mu, &S->nu, &S->xt, &S->J3, &S->R3, &S->rsc, &S->csc, &S->Xcat, &S->Q1, &S->US, &S->UD, &S->UR, &S->UZ,
+  for (DevBuf<double>* p : {&S->mu, &S->nu, &S->xt, &S->J3, &S->R3, &S->rsc, &S->csc, &S->Xcat, &S->Q1, &S->Q2, &S->US, &S->UD, &S->UR, &S->UZ,
                             &S->UB, &S->Ytmp, &S->UC, &S->Vcat, &S->VS, &S->VD, &S->VR, &S->VB, &S->VC, &S->G, &S->G2,
                             &S->T1, &S->T2, &S->swork, &S->sv, &S->frob2, &S->gramwork, &S->Xd, &S->rc.R,
                             &S->rc.norm2, &S->rc.norm2_bD, &S->rc.work})
     b += p->bytes();
+  for (DevBuf<float>* p : {&S->J3f, &S->USf, &S->Yf, &S->Xf, &S->Vf}) b += p->bytes();
   return b + S->iwork.bytes() + S->info.bytes() + S->tdesc.bytes() + S->lu.bytes();
 }
+
+namespace lrfsi {
+// Workspace of a subset handle (factors, concatenation buffers, truncation
+// scratch, dense residual columns); S->K, M, m, cap, off, mtot, mmax, Rmax set.
+static int subset_alloc_ws(lrfsi_subset_s* S, cudaStream_t s) {
+  const int K = S->K;
+  const long M = S->M;
+  // largest concatenation: residual [B | J0 U | Jmu U | Jnu U] with rank(B) <= max(R, m)
+  S->ldR = std::max(S->Rmax, S->mmax);
+  S->ldP = S->ldR + 3 * S->Rmax + 4;
+  const int ldP = S->ldP, ldR = S->ldR;
+  for (DevBuf<double>* b : {&S->Xcat, &S->Q1, &S->Q2}) LRFSI_TRY(b->alloc((size_t)K * M * ldP));
+  for (DevBuf<double>* b : {&S->US, &S->UD, &S->UR, &S->UZ, &S->UB, &S->Ytmp, &S->UC})
+    LRFSI_TRY(b->alloc((size_t)K * M * ldR));
+  LRFSI_TRY(S->Vcat.alloc((size_t)S->mtot * ldP));
+  for (DevBuf<double>* b : {&S->VS, &S->VD, &S->VR, &S->VB, &S->VC}) LRFSI_TRY(b->alloc((size_t)S->mtot * ldR));
+  for (DevBuf<double>* b : {&S->G, &S->G2, &S->T1, &S->T2}) LRFSI_TRY(b->alloc((size_t)K * ldP * ldP));
+  S->swork_per = trunc_small_work(ldP, S->mmax);
+  LRFSI_TRY(S->swork.alloc(S->swork_per * K));
+  LRFSI_TRY(S->sv.alloc((size_t)K * ldP));
+  LRFSI_TRY(S->frob2.alloc(K));
+  LRFSI_TRY(S->iwork.alloc((size_t)2 * ldP * K));
+  LRFSI_TRY(S->info.alloc((size_t)5 * K));
+  LRFSI_TRY(S->tdesc.alloc(2 * K));
+  LRFSI_TRY(S->gramwork.alloc(gram_work_len(K, M, ldP, ldP)));
+  LRFSI_TRY(S->Xd.alloc((size_t)M * S->mtot));
+  LRFSI_TRY(S->rc.init(M, S->mtot));
+  return LRFSI_OK;
+}
+}  // namespace lrfsi
 
 extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
                                    const int* m_h, const int* cap_h, lrfsi_subset_h* out, lrfsi_stream_t stream) {
@@ -633,35 +807,17 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
     S->mmax = std::max(S->mmax, S->m[k]);
     S->Rmax = std::max(S->Rmax, S->cap[k]);
   }
-  // largest concatenation: residual [B | J0 U | Jmu U | Jnu U] with rank(B) <= max(R, m)
-  S->ldR = std::max(S->Rmax, S->mmax);
-  S->ldP = S->ldR + 3 * S->Rmax + 4;
-  S->mu_h.assign(mu_h, mu_h + S->mtot);
-  S->nu_h.assign(nu_h, nu_h + S->mtot);
+  LRFSI_TRY(subset_alloc_ws(S, s));
   const long nnz = (long)mesh->h.colidx.size();
   const int ldP = S->ldP, ldR = S->ldR;
+  S->mu_h.assign(mu_h, mu_h + S->mtot);
+  S->nu_h.assign(nu_h, nu_h + S->mtot);
   LRFSI_TRY(S->mu.upload(S->mu_h, s));
   LRFSI_TRY(S->nu.upload(S->nu_h, s));
   LRFSI_TRY(S->xt.alloc((size_t)K * M));
   LRFSI_CUDA(cudaMemcpyAsync(S->xt.p, xt, sizeof(double) * K * M, cudaMemcpyDeviceToDevice, s));
   LRFSI_TRY(S->J3.alloc((size_t)K * 3 * nnz));
   LRFSI_TRY(S->R3.alloc((size_t)K * 3 * M));
-  for (DevBuf<double>* b : {&S->Xcat, &S->Q1}) LRFSI_TRY(b->alloc((size_t)K * M * ldP));
-  for (DevBuf<double>* b : {&S->US, &S->UD, &S->UR, &S->UZ, &S->UB, &S->Ytmp, &S->UC})
-    LRFSI_TRY(b->alloc((size_t)K * M * ldR));
-  LRFSI_TRY(S->Vcat.alloc((size_t)S->mtot * ldP));
-  for (DevBuf<double>* b : {&S->VS, &S->VD, &S->VR, &S->VB, &S->VC}) LRFSI_TRY(b->alloc((size_t)S->mtot * ldR));
-  for (DevBuf<double>* b : {&S->G, &S->G2, &S->T1, &S->T2}) LRFSI_TRY(b->alloc((size_t)K * ldP * ldP));
-  S->swork_per = trunc_small_work(ldP, S->mmax);
-  LRFSI_TRY(S->swork.alloc(S->swork_per * K));
-  LRFSI_TRY(S->sv.alloc((size_t)K * ldP));
-  LRFSI_TRY(S->frob2.alloc(K));
-  LRFSI_TRY(S->iwork.alloc((size_t)2 * ldP * K));
-  LRFSI_TRY(S->info.alloc((size_t)5 * K));
-  LRFSI_TRY(S->tdesc.alloc(2 * K));
-  LRFSI_TRY(S->gramwork.alloc(gram_work_len(K, M, ldP, ldP)));
-  LRFSI_TRY(S->Xd.alloc((size_t)M * S->mtot));
-  LRFSI_TRY(S->rc.init(M, S->mtot));
   // operators at xt_k and the preconditioners at the midpoint parameters
   std::vector<const double*> J3p(K);
   for (int k = 0; k < K; ++k) {
@@ -699,6 +855,20 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
       LRFSI_TRY(check_launch("k_scale_vals"));
     }
     LRFSI_CUDA(cudaStreamSynchronize(s));
+  }
+  // FP32 copies for the mixed-precision inner iteration
+  {
+    LRFSI_TRY(S->J3f.alloc((size_t)K * 3 * nnz));
+    std::vector<ConvDesc> cv;
+    for (int k = 0; k < K; ++k)
+      cv.push_back(ConvDesc{S->J3.p + (size_t)k * 3 * nnz, 0, S->J3f.p + (size_t)k * 3 * nnz, 0, 3 * nnz, 1, nullptr,
+                            1.0});
+    for (auto& c : cv) { c.lds = 1; c.ldd = 1; }
+    LRFSI_TRY((convert_batched<double, float>(cv, s)));
+    LRFSI_TRY(S->USf.alloc((size_t)K * M * ldR));
+    LRFSI_TRY(S->Yf.alloc((size_t)K * M * ldP));
+    LRFSI_TRY(S->Xf.alloc((size_t)K * M * ldP));
+    LRFSI_TRY(S->Vf.alloc((size_t)S->mtot * ldP));
   }
   LRFSI_TRY(blocklu_alloc(mesh, K, S->lu));
   LRFSI_TRY(blocklu_factor(mesh, S->lu, J3p.data(), S->mubar.data(), S->nubar.data(), K, s));
@@ -786,9 +956,42 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
       Vo[k] = S->vside(S->VR, k, ldR);
     }
     LRFSI_TRY(copy_batched(cd, s));
-    if (!sd.empty()) {
+    if (!sd.empty() && o.precision == 0) {
       LRFSI_TRY(spmm_batched<double>(S->mesh, sd.data(), (int)sd.size(), s));
       LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+    } else if (!sd.empty()) {
+      // mixed: B - F(S) with an FP32 SpMM and an FP32 GEMM (FP32 accumulation);
+      // the result is widened to FP64 for the truncation
+      std::vector<ConvDesc> c1, c2;
+      std::vector<SpmmDesc<float>> sdf;
+      std::vector<GemmDesc<float>> gmf;
+      for (size_t q = 0; q < sd.size(); ++q) {
+        // subset of this SpMM descriptor
+        int k = -1;
+        for (int kk : L)
+          if (S->tall(S->US, kk, ldR) == sd[q].U) k = kk;
+        const int r = rS[k], m = S->m[k];
+        float* Uf = S->USf.p + (size_t)k * M * ldR;
+        float* Yf = S->Yf.p + (size_t)k * M * ldP;
+        float* Xf = S->Xf.p + (size_t)k * M * ldP;
+        float* Vf = S->Vf.p + (size_t)S->off[k] * ldP;
+        c1.push_back(ConvDesc{S->tall(S->US, k, ldR), ldR, Uf, ldR, M, r, nullptr, 1.0});
+        c1.push_back(ConvDesc{S->tall(S->Xcat, k, ldP), ldP, Xf, ldP, M, m, nullptr, 1.0});
+        c1.push_back(ConvDesc{S->vside(S->Vcat, k, ldP), ldP, Vf, ldP, m, 3 * r, nullptr, 1.0});
+        SpmmDesc<float> d;
+        d.J3 = S->J3f.p + (size_t)k * 3 * nnz;
+        d.U = Uf; d.ldu = ldR; d.r = r; d.Y = Yf; d.ldy = ldP;
+        d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+        d.sc[0] = d.sc[1] = d.sc[2] = 1.0f;
+        d.a1 = d.a2 = 0.0f;
+        sdf.push_back(d);
+        gmf.push_back(GemmDesc<float>{(int)M, m, 3 * r, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f});
+        c2.push_back(ConvDesc{Xf, ldP, S->tall(S->Xcat, k, ldP), ldP, M, m, nullptr, 1.0});
+      }
+      LRFSI_TRY((convert_batched<double, float>(c1, s)));
+      LRFSI_TRY(spmm_batched<float>(S->mesh, sdf.data(), (int)sdf.size(), s));
+      LRFSI_TRY(gemm_grouped<float>(gmf.data(), (int)gmf.size(), s));
+      LRFSI_TRY((convert_batched<float, double>(c2, s)));
     }
     LRFSI_TRY(copy_batched(cd2, s));
     LRFSI_TRY(truncate_batch(S, L, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
@@ -912,7 +1115,7 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
 
 static int check_opts(const lrfsi_cheb_options* o) {
   if (!o || !(o->c > 0) || !(o->d > o->c) || o->iters < 1 || o->cycles < 1 || o->rank_cap < 1 || !(o->tol >= 0) ||
-      o->precision < 0 || o->precision > 1)
+      o->precision < 0 || o->precision > 1 || !(o->tol_sol >= 0))
     return fail(LRFSI_EINVAL, "lrfsi_cheb_options: need 0 < c < d, iters, cycles, rank_cap >= 1, tol >= 0");
   return LRFSI_OK;
 }
@@ -1071,7 +1274,8 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
     LRFSI_TRY(copy_batched(cd, s));
     std::vector<int> rk;
     std::vector<double> f2;
-    LRFSI_TRY(truncate_batch(S, need, p, opt->tol, S->cap, Uo, Vo, rk, f2, s));
+    const double tol_sol = opt->tol_sol > 0 ? opt->tol_sol : 1e-6 * opt->tol;
+    LRFSI_TRY(truncate_batch(S, need, p, tol_sol, S->cap, Uo, Vo, rk, f2, s));
     for (int k : need) rC[k] = rk[k];
   }
   cd.clear();
@@ -1153,6 +1357,43 @@ extern "C" int lrfsi_truncate(lrfsi_subset_h S, const double* X, int ldx, const 
                           nullptr, 1.0});
   }
   LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_pod(lrfsi_mesh_h mesh, const double* X, int ldx, int n, int k, double* Phi, int ldphi, double* C,
+                         int ldc, double* sigma, lrfsi_stream_t stream) {
+  if (!mesh || !X || !Phi || !C || n < 1 || k < 1 || k > n || ldx < n || ldphi < k || ldc < k)
+    return fail(LRFSI_EINVAL, "lrfsi_pod: bad argument (1 <= k <= n, ldx >= n, ldphi, ldc >= k)");
+  cudaStream_t s = (cudaStream_t)stream;
+  std::unique_ptr<lrfsi_subset_s> S(new (std::nothrow) lrfsi_subset_s());
+  if (!S) return fail(LRFSI_ENOMEM, "lrfsi_pod: host allocation");
+  S->mesh = mesh;
+  S->K = 1;
+  S->M = mesh->h.M;
+  S->m = {n};
+  S->cap = {k};
+  S->off = {0};
+  S->mtot = n;
+  S->mmax = n;
+  S->Rmax = k;
+  LRFSI_TRY(subset_alloc_ws(S.get(), s));
+  const long M = S->M;
+  const int ldP = S->ldP, ldR = S->ldR;
+  std::vector<CopyDesc> cd;
+  cd.push_back(CopyDesc{X, ldx, S->Xcat.p, ldP, M, n, 0, nullptr, 1.0});
+  cd.push_back(CopyDesc{nullptr, 0, S->Vcat.p, ldP, n, n, 2, nullptr, 1.0});
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<int> act{0}, p{n}, rank;
+  std::vector<double*> Uo{S->UR.p}, Vo{S->VR.p};
+  std::vector<double> f2;
+  LRFSI_TRY(truncate_batch(S.get(), act, p, 0.0, S->cap, Uo, Vo, rank, f2, s));
+  if (rank[0] < k) return fail(LRFSI_EINVAL, "lrfsi_pod: the snapshots have numerical rank below k");
+  cd.clear();
+  cd.push_back(CopyDesc{S->UR.p, ldR, Phi, ldphi, M, k, 0, nullptr, 1.0});
+  cd.push_back(CopyDesc{S->VR.p, ldR, C, ldc, n, k, 0, nullptr, 1.0});
+  LRFSI_TRY(copy_batched(cd, s));
+  if (sigma) LRFSI_CUDA(cudaMemcpyAsync(sigma, S->sv.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
   LRFSI_CUDA(cudaStreamSynchronize(s));
   return LRFSI_OK;
 }

@@ -84,10 +84,24 @@ int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_
       rmax = rmax > d[i].r ? rmax : d[i].r;
     }
     if (!cnt) continue;
+    {
+      // algorithmic: CSR index + 3 value arrays once, U gathered once per row
+      // of the pattern (L2-resident reuse not counted), outputs written once
+      const double nnz = (double)m->h.colidx.size();
+      double fl = 0, by = 0;
+      for (int i = 0; i < cnt; ++i) {
+        const bool comb = sb.d[i].o[1] < 0;
+        fl += nnz * sb.d[i].r * (comb ? 2.0 : 6.0);
+        by += nnz * (4.0 + 3.0 * sizeof(T)) + 4.0 * (M + 1) + (double)M * sb.d[i].r * sizeof(T) * (comb ? 2.0 : 4.0);
+      }
+      account(sizeof(T) == 8 ? KC_SPMM : KC_SPMM32, fl, by);
+    }
+    TimedLaunch tl(sizeof(T) == 8 ? KC_SPMM : KC_SPMM32, s);
     dim3 grid(ceil_div(M, 8), cnt);
     if (rmax <= 32) k_spmm<T, 1><<<grid, 256, 0, s>>>(sb, m->rowptr.p, m->colidx.p, M);
     else k_spmm<T, 2><<<grid, 256, 0, s>>>(sb, m->rowptr.p, m->colidx.p, M);
     LRFSI_TRY(check_launch("k_spmm"));
+    tl.end(s);
   }
   return LRFSI_OK;
 }
@@ -129,20 +143,28 @@ __global__ void k_lu_rhs(ProbPtrs pp, size_t off_up_s, size_t off_rhs, int n, in
 }
 
 // Panel factorization with partial pivoting of columns [j0, j0 + nb) of the
-// n x n block A (ld) (rows j0..n-1); pivots are absolute row indices.
+// n x n block A (ld) (rows j0..n-1); pivots are absolute row indices.  The
+// panel (at most kPanelRows x 32) is staged in shared memory.
+constexpr int kPanelSmem = 220 * 1024;  // dynamic shared memory for the staged panel
 __global__ void __launch_bounds__(512) k_lu_panel(ProbPtrs pp, size_t off_blk, int piv_off, int n, int ld, int j0,
                                                   int nb) {
   const int b = blockIdx.x;
   double* A = pp.ws[b] + off_blk;
   int* piv = pp.piv[b] + piv_off;
+  extern __shared__ double sp[];  // (n - j0) x nb, row-major
   __shared__ double s_val[512];
   __shared__ int s_idx[512];
-  const int j1 = j0 + nb < n ? j0 + nb : n;
-  for (int j = j0; j < j1; ++j) {
+  const int rows = n - j0;
+  for (long e = threadIdx.x; e < (long)rows * nb; e += blockDim.x) {
+    const int i = (int)(e / nb), c = (int)(e % nb);
+    sp[e] = A[(size_t)(j0 + i) * ld + j0 + c];
+  }
+  __syncthreads();
+  for (int jj = 0; jj < nb; ++jj) {
     double best = -1.0;
-    int bi = j;
-    for (int i = j + threadIdx.x; i < n; i += blockDim.x) {
-      const double v = fabs(A[(size_t)i * ld + j]);
+    int bi = jj;
+    for (int i = jj + threadIdx.x; i < rows; i += blockDim.x) {
+      const double v = fabs(sp[(size_t)i * nb + jj]);
       if (v > best) { best = v; bi = i; }
     }
     s_val[threadIdx.x] = best;
@@ -159,30 +181,35 @@ __global__ void __launch_bounds__(512) k_lu_panel(ProbPtrs pp, size_t off_blk, i
       }
       __syncthreads();
     }
-    const int p = s_idx[0];
+    const int pr = s_idx[0];
     const double pv = s_val[0];
     if (threadIdx.x == 0) {
-      piv[j] = p;
+      piv[j0 + jj] = j0 + pr;
       if (!(pv > 0.0)) *pp.status[b] = LRFSI_ESINGULAR;
     }
-    if (p != j)
-      for (int c = j0 + threadIdx.x; c < j1; c += blockDim.x) {
-        const double t = A[(size_t)j * ld + c];
-        A[(size_t)j * ld + c] = A[(size_t)p * ld + c];
-        A[(size_t)p * ld + c] = t;
+    if (pr != jj)
+      for (int c = threadIdx.x; c < nb; c += blockDim.x) {
+        const double t = sp[(size_t)jj * nb + c];
+        sp[(size_t)jj * nb + c] = sp[(size_t)pr * nb + c];
+        sp[(size_t)pr * nb + c] = t;
       }
     __syncthreads();
-    double d = A[(size_t)j * ld + j];
-    if (d == 0.0) d = 1e-300;  // singular: flagged above, keep going without NaNs
-    const double inv = 1.0 / d;
-    for (int i = j + 1 + threadIdx.x; i < n; i += blockDim.x) A[(size_t)i * ld + j] *= inv;
-    __syncthreads();
-    const int w = j1 - j - 1;
-    for (long e = threadIdx.x; e < (long)(n - j - 1) * w; e += blockDim.x) {
-      const int i = j + 1 + (int)(e / w), c = j + 1 + (int)(e % w);
-      A[(size_t)i * ld + c] -= A[(size_t)i * ld + j] * A[(size_t)j * ld + c];
+    double dgn = sp[(size_t)jj * nb + jj];
+    if (dgn == 0.0) dgn = 1e-300;  // singular: flagged above, keep going without NaNs
+    const double inv = 1.0 / dgn;
+    const int w = nb - jj - 1;
+    for (int i = jj + 1 + threadIdx.x; i < rows; i += blockDim.x) {
+      double* ri = sp + (size_t)i * nb;
+      const double l = ri[jj] * inv;
+      ri[jj] = l;
+      const double* rj = sp + (size_t)jj * nb;
+      for (int c = 0; c < w; ++c) ri[jj + 1 + c] -= l * rj[jj + 1 + c];
     }
     __syncthreads();
+  }
+  for (long e = threadIdx.x; e < (long)rows * nb; e += blockDim.x) {
+    const int i = (int)(e / nb), c = (int)(e % nb);
+    A[(size_t)(j0 + i) * ld + j0 + c] = sp[e];
   }
 }
 
@@ -204,28 +231,47 @@ __global__ void k_lu_laswp(ProbPtrs pp, size_t off_mat, int ld, int piv_off, int
   }
 }
 
-// Triangular solve of a diagonal nb x nb block for columns [c0, c1) of B:
-// lower (unit) forward or upper backward substitution, thread per column.
-__global__ void k_lu_trsm_diag(ProbPtrs pp, size_t off_L, int ldl, size_t off_B, int ldb, int i0, int nb, int c0,
-                               int c1, int upper) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1) return;
+// Triangular solve of a diagonal nb x nb block (nb <= 32) for columns
+// [c0, c1) of B: unit lower forward or upper backward substitution, thread
+// per column, the block in shared memory and the column in registers.
+__global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L, int ldl, size_t off_B, int ldb,
+                                                      int i0, int nb, int c0, int c1, int upper) {
+  __shared__ double Ls[32][33];
   const double* L = pp.ws[blockIdx.y] + off_L;
   double* B = pp.ws[blockIdx.y] + off_B;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    const int i = e / nb, l = e % nb;
+    Ls[i][l] = L[(size_t)(i0 + i) * ldl + i0 + l];
+  }
+  __syncthreads();
+  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= c1) return;
+  double x[32];
+#pragma unroll
+  for (int i = 0; i < 32; ++i) x[i] = i < nb ? B[(size_t)(i0 + i) * ldb + c] : 0.0;
   if (!upper) {
-    for (int i = i0; i < i0 + nb; ++i) {
-      double s = B[(size_t)i * ldb + c];
-      for (int l = i0; l < i; ++l) s -= L[(size_t)i * ldl + l] * B[(size_t)l * ldb + c];
-      B[(size_t)i * ldb + c] = s;
+#pragma unroll
+    for (int i = 1; i < 32; ++i) {
+      double sacc = x[i];
+#pragma unroll
+      for (int l = 0; l < i; ++l) sacc -= Ls[i][l] * x[l];
+      x[i] = sacc;
     }
   } else {
-    for (int i = i0 + nb - 1; i >= i0; --i) {
-      double s = B[(size_t)i * ldb + c];
-      for (int l = i + 1; l < i0 + nb; ++l) s -= L[(size_t)i * ldl + l] * B[(size_t)l * ldb + c];
-      double d = L[(size_t)i * ldl + i];
-      B[(size_t)i * ldb + c] = s / (d == 0.0 ? 1e-300 : d);
+#pragma unroll
+    for (int i = 31; i >= 0; --i) {
+      if (i >= nb) continue;
+      double sacc = x[i];
+#pragma unroll
+      for (int l = i + 1; l < 32; ++l)
+        if (l < nb) sacc -= Ls[i][l] * x[l];
+      const double dg = Ls[i][i];
+      x[i] = sacc / (dg == 0.0 ? 1e-300 : dg);
     }
   }
+#pragma unroll
+  for (int i = 0; i < 32; ++i)
+    if (i < nb) B[(size_t)(i0 + i) * ldb + c] = x[i];
 }
 
 __global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t off_inv, int n, int nnext, int nmax) {
@@ -240,6 +286,15 @@ __global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t 
 
 int blocklu_alloc(const lrfsi_mesh_s* m, int nprob, BlockLU& lu) {
   if (nprob < 1 || nprob > kMaxGemmDescs) return fail(LRFSI_EINVAL, "block LU: 1..32 problems per batch");
+  if ((size_t)m->h.nmax * 8 * sizeof(double) > (size_t)kPanelSmem)
+    return fail(LRFSI_EINVAL, "block LU: slab larger than the panel kernel supports");
+  {
+    static bool attr = false;
+    if (!attr) {
+      LRFSI_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem));
+      attr = true;
+    }
+  }
   lu.nslab = m->h.nslab;
   lu.nmax = m->h.nmax;
   lu.nprob = nprob;
@@ -282,6 +337,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
   for (int b = 0; b < nprob; ++b) LRFSI_CUDA(cudaMemsetAsync(pp.ws[b], 0, sizeof(double) * lu.off_inv, s));
   LRFSI_CUDA(cudaMemsetAsync(lu.status.p, 0, sizeof(int) * nprob, s));
   const long nnz = (long)m->h.colidx.size();
+  TimedLaunch tl_all(KC_LU, s);  // the whole factorisation is one timed region of class KC_LU
   k_lu_extract<<<dim3(ceil_div(nnz, 256), nprob), 256, 0, s>>>(pp, m->dense_off.p, nnz);
   LRFSI_TRY(check_launch("k_lu_extract"));
   std::vector<GemmDesc<double>> gd(nprob);
@@ -290,10 +346,13 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
     const int nnext = sl + 1 < lu.nslab ? (int)(lu.off[sl + 2] - lu.off[sl + 1]) : 0;
     const size_t offD = nb2 * sl;
     const int poff = sl * nmax;
-    // blocked right-looking LU of the Schur block S_s
-    for (int j0 = 0; j0 < n; j0 += kNb) {
-      const int nb = j0 + kNb < n ? kNb : n - j0;
-      k_lu_panel<<<nprob, 512, 0, s>>>(pp, offD, poff, n, nmax, j0, nb);
+    // blocked right-looking LU of the Schur block S_s; the panel width keeps
+    // the staged panel within shared memory
+    int nbp = kNb;
+    while (nbp > 8 && (size_t)n * nbp * sizeof(double) > (size_t)kPanelSmem) nbp /= 2;
+    for (int j0 = 0; j0 < n; j0 += nbp) {
+      const int nb = j0 + nbp < n ? nbp : n - j0;
+      k_lu_panel<<<nprob, 512, sizeof(double) * (size_t)(n - j0) * nb, s>>>(pp, offD, poff, n, nmax, j0, nb);
       LRFSI_TRY(check_launch("k_lu_panel"));
       // interchanges to the left and right of the panel
       k_lu_laswp<<<dim3(ceil_div(n, 128), nprob), 128, 0, s>>>(pp, offD, nmax, poff, j0, j0 + nb, 0, n, j0, j0 + nb);
@@ -359,6 +418,15 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
     }
   }
+  {
+    double fl = 0;
+    for (int sl = 0; sl < lu.nslab; ++sl) {
+      const double n = (double)(lu.off[sl + 1] - lu.off[sl]);
+      fl += (2.0 / 3.0) * n * n * n + 4.0 * n * n * n + (sl + 1 < lu.nslab ? 2.0 * n * n * n : 0.0);
+    }
+    account(KC_LU, fl * nprob, 0);
+  }
+  tl_all.end(s);
   return LRFSI_OK;
 }
 

@@ -38,7 +38,16 @@ class lrfsi_mesh_info_t(C.Structure):
 
 class lrfsi_cheb_options(C.Structure):
     _fields_ = [("c", C.c_double), ("d", C.c_double), ("iters", C.c_int), ("cycles", C.c_int),
-                ("rank_cap", C.c_int), ("tol", C.c_double), ("eta", C.c_double), ("precision", C.c_int)]
+                ("rank_cap", C.c_int), ("tol", C.c_double), ("eta", C.c_double), ("precision", C.c_int),
+                ("tol_sol", C.c_double)]
+
+
+class lrfsi_kernel_stat(C.Structure):
+    _fields_ = [("launches", C.c_uint64), ("flops", C.c_double), ("bytes", C.c_double), ("ms", C.c_double)]
+
+
+KERNEL_CLASSES = ("gemm_fp64", "spmm_fp64", "gram_fp64", "block_lu", "fe_assembly", "gemm_fp32", "spmm_fp32",
+                  "trunc_small")
 
 
 class lrfsi_cheb_stats(C.Structure):
@@ -67,6 +76,15 @@ def load():
         "lrfsi_assemble_affine": [vp, vp, vp, vp, vp],
         "lrfsi_residual_batch": [vp, vp, i, i, vp, vp, vp, i, vp, vp],
         "lrfsi_residual": [vp, vp, vp, i, vp, i, i, vp, vp, i, vp, vp],
+        "lrfsi_mlp_create": [i, i, i, i, C.POINTER(vp)],
+        "lrfsi_mlp_destroy": [vp],
+        "lrfsi_mlp_set_params": [vp, vp],
+        "lrfsi_mlp_get_params": [vp, vp],
+        "lrfsi_mlp_forward": [vp, vp, i, vp, vp],
+        "lrfsi_mlp_gradients": [vp, vp, vp, i, vp, vp, vp],
+        "lrfsi_mlp_train": [vp, vp, vp, i, i, C.c_float, vp, vp],
+        "lrfsi_learned_start": [vp, vp, vp, i, vp, i, i, vp, vp, vp, vp, vp],
+        "lrfsi_pod": [vp, vp, i, i, i, vp, i, vp, i, vp, vp],
         "lrfsi_newton_median": [vp, i, vp, vp, vp, d, i, vp, vp, vp],
         "lrfsi_subset_create": [vp, i, vp, vp, vp, vp, vp, C.POINTER(vp), vp],
         "lrfsi_subset_destroy": [vp],
@@ -85,6 +103,13 @@ def load():
     lib.lrfsi_mesh_bytes.argtypes = [vp]
     lib.lrfsi_subset_bytes.restype = C.c_size_t
     lib.lrfsi_subset_bytes.argtypes = [vp]
+    lib.lrfsi_mlp_num_params.argtypes = [vp]
+    lib.lrfsi_mlp_num_params.restype = C.c_int64
+    lib.lrfsi_stats.argtypes = [i, C.POINTER(lrfsi_kernel_stat)]
+    lib.lrfsi_stats.restype = C.c_int
+    lib.lrfsi_stats_reset.restype = C.c_int
+    lib.lrfsi_timing.argtypes = [i]
+    lib.lrfsi_timing.restype = C.c_int
     _lib = lib
     return lib
 
@@ -197,8 +222,8 @@ def lrfsi_newton_median(mesh, X, mu, nu, eps, max_it, stream=None, allow_noconv=
     return it, res, st
 
 
-def cheb_options(c, d, iters=6, cycles=2, rank_cap=20, tol=1e-8, eta=0.0, precision=0):
-    return lrfsi_cheb_options(c, d, iters, cycles, rank_cap, tol, eta, precision)
+def cheb_options(c, d, iters=6, cycles=2, rank_cap=20, tol=1e-8, eta=0.0, precision=0, tol_sol=0.0):
+    return lrfsi_cheb_options(c, d, iters, cycles, rank_cap, tol, eta, precision, tol_sol)
 
 
 class Subsets:
@@ -267,3 +292,89 @@ def lrfsi_truncate(sub, X, ldx, V, ldv, p, tol, cap, U, ldu, Vo, ldvo, stream=No
     _check(load().lrfsi_truncate(sub.h, _ptr(X), ldx, _ptr(V), ldv, _ptr(p), tol, _ptr(cap), _ptr(U), ldu, _ptr(Vo),
                                  ldvo, _ptr(ranks), _stream(stream)))
     return ranks
+
+
+def kernel_stats():
+    """{class name: dict(launches, flops, bytes, ms)} accumulated since the last reset."""
+    out = {}
+    for i, name in enumerate(KERNEL_CLASSES):
+        st = lrfsi_kernel_stat()
+        _check(load().lrfsi_stats(i, C.byref(st)))
+        out[name] = dict(launches=int(st.launches), flops=st.flops, bytes=st.bytes, ms=st.ms)
+    return out
+
+
+def stats_reset():
+    _check(load().lrfsi_stats_reset())
+
+
+def timing(enable):
+    _check(load().lrfsi_timing(1 if enable else 0))
+
+
+class MLP:
+    """The learned-start network (lrfsi_mlp_*): n_in -> n_h1 -> n_h2 -> n_out."""
+
+    def __init__(self, sizes=(2, 128, 128, 64)):
+        self.sizes = tuple(sizes)
+        self.h = C.c_void_p()
+        _check(load().lrfsi_mlp_create(*self.sizes, C.byref(self.h)))
+        self.n = int(load().lrfsi_mlp_num_params(self.h))
+
+    def close(self):
+        if self.h:
+            load().lrfsi_mlp_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, packed):
+        packed = np.ascontiguousarray(packed, np.float32)
+        assert packed.size == self.n
+        _check(load().lrfsi_mlp_set_params(self.h, _ptr(packed)))
+
+    def get_params(self):
+        out = np.zeros(self.n, np.float32)
+        _check(load().lrfsi_mlp_get_params(self.h, _ptr(out)))
+        return out
+
+    def forward(self, Z, Y, B, stream=None):
+        _check(load().lrfsi_mlp_forward(self.h, _ptr(Z), B, _ptr(Y), _stream(stream)))
+
+    def gradients(self, Z, T, B, grad, loss=None, stream=None):
+        _check(load().lrfsi_mlp_gradients(self.h, _ptr(Z), _ptr(T), B, _ptr(grad), _ptr(loss), _stream(stream)))
+
+    def train(self, Z, T, B, epochs, lr, stream=None):
+        loss = np.zeros(1, np.float32)
+        _check(load().lrfsi_mlp_train(self.h, _ptr(Z), _ptr(T), B, epochs, C.c_float(lr), _ptr(loss),
+                                      _stream(stream)))
+        return float(loss[0])
+
+
+def pack_params(params):
+    """Packed layout of lrfsi_mlp_*: W_0, b_0, W_1, b_1, ... (row-major)."""
+    return np.concatenate([np.asarray(p, np.float32).ravel() for p in params])
+
+
+def unpack_params(packed, sizes=(2, 128, 128, 64)):
+    out, o = [], 0
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        out.append(packed[o:o + n_in * n_out].reshape(n_out, n_in)); o += n_in * n_out
+        out.append(packed[o:o + n_out]); o += n_out
+    return out
+
+
+def lrfsi_learned_start(mesh, mlp, Z, B, Phi, ldphi, k, coef_scale, field_scale, offset, X, stream=None):
+    _check(load().lrfsi_learned_start(mesh.h, mlp.h, _ptr(Z), B, _ptr(Phi), ldphi, k, _ptr(coef_scale),
+                                      _ptr(field_scale), _ptr(offset), _ptr(X), _stream(stream)))
+
+
+def lrfsi_pod(mesh, X, ldx, n, k, Phi, ldphi, Cm, ldc, stream=None):
+    sigma = np.zeros(k)
+    _check(load().lrfsi_pod(mesh.h, _ptr(X), ldx, n, k, _ptr(Phi), ldphi, _ptr(Cm), ldc, _ptr(sigma),
+                            _stream(stream)))
+    return sigma

@@ -154,3 +154,28 @@ def test_subset_step_reaches_target_and_matches_oracle_residual():
     rr = algorithm1.relative_residuals(om, X[inv], mu, nu)
     assert np.allclose(rr, rel, rtol=1e-6, atol=1e-14)
     assert rr.max() <= 1e-8
+
+
+def test_mixed_precision_subset_step_reaches_target():
+    """Mixed mode (FP32 SpMM and residual GEMM inside the FP64 correction loop)
+    reaches the same target; its result agrees with the FP64 path to the
+    target's accuracy."""
+    lm, om, perm, mu, nu, xt = _subset_problem(m=8)
+    m = len(mu)
+    out = {}
+    for prec in (0, 1):
+        sub = lrfsi.Subsets(lm, _dev(xt[perm]), mu, nu, [m], [m])
+        U = torch.zeros(lm.M * m, dtype=torch.float64, device=DEV)
+        V = torch.zeros(m * m, dtype=torch.float64, device=DEV)
+        opt = lrfsi.cheb_options(0.5, 1.0, iters=6, cycles=3, rank_cap=m, tol=1e-10, eta=0.05, precision=prec)
+        ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, 1e-8, 30, U, m, V, m)
+        assert st == 0 and rel.max() <= 1e-8, (prec, rel.max())
+        r = int(ranks[0])
+        X = xt[perm][:, None] + U.cpu().numpy().reshape(lm.M, m)[:, :r] @ V.cpu().numpy().reshape(m, m)[:, :r].T
+        rr = algorithm1.relative_residuals(om, X[np.argsort(perm)], mu, nu)
+        assert rr.max() <= 1e-8
+        out[prec] = X
+    # both are solutions to relative residual 1e-8: their difference is small
+    # against the Newton update itself
+    upd = np.linalg.norm(out[0] - xt[perm][:, None])
+    assert np.linalg.norm(out[1] - out[0]) <= 1e-5 * upd
