@@ -27,19 +27,10 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2008_10275_gb300 import inputs  # noqa: E402
+from paper_2008_10275_gb300 import inputs, multi  # noqa: E402
 
 METRIC = "parameter solves/sec to nonlinear rel. residual 1e-6"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (profiling recipe's table)
-
-
-def workload_params(W):
-    """Parameters in little-endian order (mu fastest), or nu fastest when the
-    workload asks for it."""
-    mu_g, nu_g = np.array(W.mu_values), np.array(W.nu_values)
-    if W.nu_fastest:
-        return np.repeat(mu_g, len(nu_g)), np.tile(nu_g, len(mu_g))
-    return np.tile(mu_g, len(nu_g)), np.repeat(nu_g, len(mu_g))
 
 
 def subset_layout(m, K):
@@ -102,11 +93,7 @@ sys.path.insert(0, {ROOT!r})
 from oracle import fsi, newton
 from paper_2008_10275_gb300 import inputs
 W = inputs.WORKLOADS[{workload!r}]
-mu_g, nu_g = np.array(W.mu_values), np.array(W.nu_values)
-if W.nu_fastest:
-    mus, nus = np.repeat(mu_g, len(nu_g)), np.tile(nu_g, len(mu_g))
-else:
-    mus, nus = np.tile(mu_g, len(nu_g)), np.repeat(nu_g, len(mu_g))
+mus, nus = inputs.workload_parameters(W)
 m = fsi.Mesh(fsi.Problem(W.nx, W.ny))
 t = time.perf_counter()
 X, steps, norms = newton.standard_newton(m, mus[:{n_sample}], nus[:{n_sample}], eps=1e-8)
@@ -164,9 +151,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = multi.rank_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
 
@@ -183,7 +168,7 @@ def main():
     lrfsi.load()
     dev = f"cuda:{local}"
     W = inputs.WORKLOADS[args.workload]
-    mus, nus = workload_params(W)
+    mus, nus = inputs.workload_parameters(W, rank, world)
     m = len(mus)
     sizes, medians = subset_layout(m, W.K)
     K = W.K
@@ -240,10 +225,7 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
     launches = (lrfsi.kernel_launches() - L0) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = multi.max_over_ranks(ms, dist, dev)
     value = world * m / (ms * 1e-3)
 
     X64 = dense_solution(info)
@@ -283,10 +265,7 @@ def main():
     e3.record(stream)
     barrier()
     ms_e2e = e2.elapsed_time(e3) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = multi.max_over_ranks(ms_e2e, dist, dev)
 
     # roofline of the dominant kernel class: one more step with per-launch events
     lrfsi.stats_reset()

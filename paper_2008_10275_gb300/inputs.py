@@ -89,3 +89,42 @@ def random_state(M, seed, scales=(0.3, 1e-3, 50.0), nq2=None):
         x[2 * nq2:4 * nq2] *= scales[1]
         x[4 * nq2:] *= scales[2]
     return x
+
+
+def mlp_init(sizes=(2, 128, 128, 64), seed=0):
+    """Seeded initial parameters of the learned-start MLP, packed as the
+    library expects (per layer: W_l (n_{l+1} x n_l, row-major), then b_l):
+    He-normal weights, zero biases, FP32."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for n_in, n_out in zip(sizes[:-1], sizes[1:]):
+        parts.append((rng.standard_normal((n_out, n_in)) * np.sqrt(2.0 / n_in)).astype(np.float32).ravel())
+        parts.append(np.zeros(n_out, np.float32))
+    return np.concatenate(parts)
+
+
+def rank_strip(rank=0, world=1):
+    """Shear-modulus strip of rank ``rank`` out of ``world`` processes: the box
+    is cut into ``world`` equal strips along mu_s, so that every process solves a
+    workload of the same shape on its own parameters (weak scaling)."""
+    w = (MU_RANGE[1] - MU_RANGE[0]) / world
+    return MU_RANGE[0] + rank * w, MU_RANGE[0] + (rank + 1) * w
+
+
+def workload_parameters(W, rank=0, world=1):
+    """The parameters of workload ``W`` for process ``rank`` of ``world``, in
+    the workload's grid order (little endian: mu fastest; or nu fastest).  The
+    grid's shear moduli are mapped affinely from the full box onto the rank's
+    strip (the identity for one process).  Random workloads draw from the
+    strip with a rank-dependent seed."""
+    lo, hi = rank_strip(rank, world)
+    if W.seed is not None:
+        rng = np.random.default_rng(W.seed + 7919 * rank)
+        return rng.uniform(lo, hi, W.n_random), rng.uniform(*NU_RANGE, W.n_random)
+    a = (np.array(W.mu_values) - MU_RANGE[0]) / (MU_RANGE[1] - MU_RANGE[0])
+    mu_g, nu_g = lo + a * (hi - lo), np.array(W.nu_values)
+    if world == 1:
+        mu_g = np.array(W.mu_values)
+    if W.nu_fastest:
+        return np.repeat(mu_g, len(nu_g)), np.tile(nu_g, len(mu_g))
+    return np.tile(mu_g, len(nu_g)), np.repeat(nu_g, len(mu_g))
