@@ -265,12 +265,32 @@ int lrfsi_mlp_gradients(lrfsi_mlp_h mlp, const float* Z_dev, const float* T_dev,
 /* epochs full-batch Adam steps (beta 0.9 / 0.999, eps 1e-8); loss_host: last loss. */
 int lrfsi_mlp_train(lrfsi_mlp_h mlp, const float* Z_dev, const float* T_dev, int B, int epochs, float lr,
                     float* loss_host, lrfsi_stream_t stream);
-/* X (B x M, problem-major, device) = offset + field_scale .* (Phi (coef_scale .* MLP(Z))),
- * Dirichlet rows overwritten with b_D.  Phi: M x k (ldphi, device FP64); coef_scale (k),
- * field_scale (M), offset (M): device FP64.  Synchronizes the stream. */
-int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, const float* Z_dev, int B, const double* Phi_dev,
-                        int ldphi, int k, const double* coef_scale_dev, const double* field_scale_dev,
-                        const double* offset_dev, double* X_dev, lrfsi_stream_t stream);
+/* lrfsi_learned_fit: build the start model from n method-generated solutions.
+ *   X_dev : n solutions, problem-major (row j = solution j, length M, stride
+ *           ldx >= M), e.g. the output of lrfsi_newton_median.
+ *   mu_host, nu_host : their n parameters;  box = {mu_lo, mu_hi, nu_lo, nu_hi}
+ *           maps the parameters to z in [-1, 1]^2.
+ *   Steps (all on the device): offset = mean snapshot; field_scale = RMS of the
+ *   centred snapshots per field (v_x, v_y, u_x, u_y, p); POD of the centred,
+ *   field-scaled snapshots (lrfsi_pod) into Phi (M x k, ldphi); coef_scale[l] =
+ *   RMS of coefficient l; then epochs Adam steps (learning rate lr) fitting
+ *   MLP(z_j) to the scaled coefficients.  The MLP must be 2 -> .. -> k and
+ *   hold its initial parameters.  Outputs are caller-owned device arrays
+ *   (coef_scale: k, field_scale and offset: M); loss_host / sigma_host (k) may
+ *   be NULL.  Synchronizes the stream. */
+int lrfsi_learned_fit(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, const double* mu_host, const double* nu_host, int n,
+                      const double* box, const double* X_dev, int ldx, int k, int epochs, float lr,
+                      double* Phi_dev, int ldphi, double* coef_scale_dev, double* field_scale_dev,
+                      double* offset_dev, float* loss_host, double* sigma_host, lrfsi_stream_t stream);
+/* lrfsi_learned_start: X (B x M, problem-major, device) = offset + field_scale
+ * .* (Phi (coef_scale .* MLP(z))) with Dirichlet rows set to b_D, for the B
+ * parameters (host arrays, box as above).  Every column whose residual norm is
+ * not below that of b_D falls back to b_D; fallback_host (B ints, or NULL)
+ * receives 1 for those columns.  Synchronizes the stream. */
+int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, const double* mu_host, const double* nu_host, int B,
+                        const double* box, const double* Phi_dev, int ldphi, int k, const double* coef_scale_dev,
+                        const double* field_scale_dev, const double* offset_dev, double* X_dev,
+                        int* fallback_host, lrfsi_stream_t stream);
 
 /* lrfsi_pod: rank-k POD of the snapshot columns X (M x n, ldx): the leading k
  * left singular vectors Phi (M x k, ldphi, orthonormal columns) and the
@@ -287,14 +307,18 @@ size_t lrfsi_subset_bytes(lrfsi_subset_h sub);
 uint64_t lrfsi_kernel_launches(void);
 
 /* Per-kernel-class accounting for roofline reports.  Classes:
- * 0 FP64 dense GEMM, 1 SpMM (FP64), 2 Gram products (FP64), 3 block-LU panel
- * and triangular kernels, 4 FE assembly and residuals, 5 FP32 dense GEMM,
- * 6 SpMM (FP32), 7 small per-subset truncation kernels.  For every launch the library adds the algorithmic FLOPs and
+ * 0 FP64 dense GEMM, 1 SpMM (FP64), 2 Gram products (FP64), 3 block-LU
+ * factorisations (whole region, contains launches of classes 0, 8 and 9),
+ * 4 FE assembly and residuals, 5 FP32 dense GEMM, 6 SpMM (FP32), 7 small
+ * per-subset factorisation kernels of the truncation, 8 LU panel kernels
+ * (panel factorisation and row interchanges), 9 LU diagonal-block triangular
+ * solves, 10 block-LU solves (whole region, contains class-0 launches),
+ * 11 the cluster SVD of the truncation.  For every launch the library adds the algorithmic FLOPs and
  * HBM bytes of the launch (from its shape) to the class counters; with timing
  * enabled it also brackets each launch with CUDA events on the launching
  * stream and accumulates the elapsed time when lrfsi_stats is called (which
  * synchronizes those events). */
-#define LRFSI_NUM_KERNEL_CLASSES 8
+#define LRFSI_NUM_KERNEL_CLASSES 12
 typedef struct {
   uint64_t launches;
   double flops;        /* algorithmic floating-point operations */
@@ -303,6 +327,10 @@ typedef struct {
 } lrfsi_kernel_stat;
 int lrfsi_stats(int kernel_class, lrfsi_kernel_stat* out);
 int lrfsi_stats_reset(void);
+/* Truncation counters of this process: out6 = {truncations, SVD sweeps (sum),
+ * SVD sweeps (max), SVDs stopped at the sweep limit, Cholesky-QR breakdowns,
+ * retries}; reset != 0 zeroes them after reading. */
+int lrfsi_truncation_counters(int64_t* out6, int reset);
 int lrfsi_timing(int enable);
 
 const char* lrfsi_last_error(void);

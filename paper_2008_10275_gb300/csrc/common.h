@@ -30,7 +30,13 @@ int cuda_fail(cudaError_t e, const char* what);
 
 // per-class accounting (see lrfsi_stats); timed_begin/timed_end bracket a
 // launch with events when timing is enabled
-enum KClass { KC_GEMM = 0, KC_SPMM = 1, KC_GRAM = 2, KC_LU = 3, KC_FE = 4, KC_GEMM32 = 5, KC_SPMM32 = 6, KC_TRUNC = 7 };
+// KC_LU, KC_LUSOLVE and KC_SVD time whole regions that contain launches of
+// other classes (they overlap those classes); the rest time single launches.
+enum KClass {
+  KC_GEMM = 0, KC_SPMM = 1, KC_GRAM = 2, KC_LU = 3, KC_FE = 4, KC_GEMM32 = 5, KC_SPMM32 = 6, KC_TRUNC = 7,
+  KC_LUPANEL = 8, KC_LUTRSM = 9, KC_LUSOLVE = 10, KC_SVD = 11
+};
+constexpr int kNumKClasses = 12;
 void account(int cls, double flops, double bytes);
 struct TimedLaunch {
   int cls;

@@ -10,6 +10,11 @@
 //   pass 2: G2 = Q1^T Q1 = R2^T R2, C = R2 R1 D^{-1} Vc^T (k x m),
 //           C = W diag(s) Z^T (one-sided Jacobi), rank r by the tolerance rule,
 //           U' = Q1 R2^{-1} W_r (orthonormal), V' = Z_r diag(s_r).
+// The factorisations run in one CTA per problem, the SVD on a thread-block
+// cluster per problem, and every product with O(p^2 m) or more work (the core
+// products, T2 W_r) in the grouped GEMM.
+#include <cooperative_groups.h>
+
 #include <cmath>
 
 #include "dense.h"
@@ -363,99 +368,13 @@ size_t trunc_small_work(int p, int m) {
   return 4 * (size_t)p * p + 3 * n * n + 2 * (size_t)p * m + 4 * n + 64;
 }
 
-// One-sided Jacobi on A (L x n, column-major, n <= L), accumulating the n x n
-// rotation Vm (column-major): A_out = A_in Vm with orthogonal columns.  Pairs
-// follow a round-robin tournament, one half-warp per pair.  A pair is rotated
-// when |a_x . a_y| > 4 eps sqrt(|a_x|^2 |a_y|^2) and neither column is below
-// eps times the largest column norm (such columns carry no information at
-// working precision).  Returns the sweeps used (or -1 if not converged).
-__device__ int jacobi_onesided(double* A, int L, int n, double* Vm, int max_sweeps) {
-  const int hl = threadIdx.x & 15, half = threadIdx.x >> 4, nh = blockDim.x >> 4;
-  const unsigned mask = (threadIdx.x & 16) ? 0xffff0000u : 0x0000ffffu;
-  __shared__ int s_rot;
-  __shared__ double s_cmax;
-  for (long e = threadIdx.x; e < (long)n * n; e += blockDim.x) Vm[e] = ((e / n) == (e % n)) ? 1.0 : 0.0;
-  if (threadIdx.x == 0) s_cmax = 0.0;
-  __syncthreads();
-  const int np = n + (n & 1);
-  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) s_rot = 0;
-    // largest squared column norm (for the negligible-column test)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      double t = 0;
-      for (int i = 0; i < L; ++i) t += A[(size_t)j * L + i] * A[(size_t)j * L + i];
-      atomicMax((unsigned long long*)&s_cmax, (unsigned long long)__double_as_longlong(t));
-    }
-    __syncthreads();
-    const double small2 = s_cmax * 1e-32;
-    for (int round = 0; round < np - 1; ++round) {
-      for (int k = half; k < np / 2; k += nh) {
-        auto pos = [&](int t) { return t == 0 ? 0 : ((round + t - 1) % (np - 1)) + 1; };
-        int x = pos(k), y = pos(np - 1 - k);
-        if (x >= n || y >= n) continue;
-        if (x > y) { const int t = x; x = y; y = t; }
-        double* ax = A + (size_t)x * L;
-        double* ay = A + (size_t)y * L;
-        double al = 0, be = 0, ga = 0;
-        for (int i = hl; i < L; i += 16) {
-          const double u = ax[i], v = ay[i];
-          al += u * u; be += v * v; ga += u * v;
-        }
-#pragma unroll
-        for (int o = 8; o > 0; o >>= 1) {
-          al += __shfl_xor_sync(mask, al, o);
-          be += __shfl_xor_sync(mask, be, o);
-          ga += __shfl_xor_sync(mask, ga, o);
-        }
-        if (al > small2 && be > small2 && fabs(ga) > 4.4e-16 * sqrt(al * be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-          const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
-          for (int i = hl; i < L; i += 16) {
-            const double u = ax[i], v = ay[i];
-            ax[i] = c * u - sn * v;
-            ay[i] = sn * u + c * v;
-          }
-          double* vx = Vm + (size_t)x * n;
-          double* vy = Vm + (size_t)y * n;
-          for (int i = hl; i < n; i += 16) {
-            const double u = vx[i], v = vy[i];
-            vx[i] = c * u - sn * v;
-            vy[i] = sn * u + c * v;
-          }
-          if (hl == 0) atomicAdd(&s_rot, 1);
-        }
-      }
-      __syncthreads();
-    }
-    if (s_rot == 0) return sweep + 1;
-    __syncthreads();
-  }
-  return -1;
-}
-
-// Work layout per problem (doubles): Dsc (p) | Rk (p*p) | Rki (p*p) | Y (p*m) |
-// C (p*m) | A (n'*n') | Vm (n'*n'), n' = max(p, m).
-struct TruncWork {
-  double *Dsc, *Rk, *Rki, *Y, *C, *A, *Vm;
-  __device__ TruncWork(double* w, int p, int m) {
-    const size_t n = (size_t)(p > m ? p : m);
-    Dsc = w;
-    Rk = Dsc + p;
-    Rki = Rk + (size_t)p * p;
-    Y = Rki + (size_t)p * p;
-    C = Y + (size_t)p * m;
-    A = C + (size_t)p * m;
-    Vm = A + n * n;
-  }
-};
-
 // Pass 1: unit-diagonal scaling and a diagonally pivoted (rank-revealing)
 // Cholesky of the Gram: at every step the column with the largest remaining
 // Schur diagonal is taken; the factorisation stops when that diagonal is
 // <= drop (the remaining columns lie in the span of the chosen ones up to a
 // relative remainder sqrt(drop)).  Outputs T1 (Q1 = X T1, k columns), the
-// core Y = R1 D^{-1} Vc^T (k x m) and info[0] = k.
+// scaled factor Rs = R1 D^{-1} (p x p in work Rk, rows >= k zero; the core
+// Y = Rs Vc^T is a GEMM after this kernel) and info[0] = k.
 __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs) {
   const TruncDesc d = descs[blockIdx.x];
   const int p = d.p, m = d.m;
@@ -542,7 +461,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
   }
   __syncthreads();
   const int k = s_k;
-  if (threadIdx.x == 0) { d.info[0] = k; d.info[4] = 0; }
+  if (threadIdx.x == 0) { d.info[0] = k; d.info[1] = 0; d.info[2] = 0; d.info[3] = 0; d.info[4] = 0; }
   // R_kk[a][b] = R[a][perm[b]] (upper triangular in pivot order) into T2 (ld k), inverse into Rki (ld k)
   for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
     const int a = (int)(e / k), b = (int)(e % k);
@@ -557,20 +476,19 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
     const int a = (int)(e / k), b = (int)(e % k);
     d.T1[(size_t)perm[a] * p + b] = W.Dsc[perm[a]] * W.Rki[(size_t)a * k + b];
   }
-  // Y[a, c] = sum_o R[a][o] ||x_o|| Vc[c, o]   (k x m; R[a][o] = 0 before a in pivot order)
-  for (long e = threadIdx.x; e < (long)k * m; e += blockDim.x) {
-    const int a = (int)(e / m), c = (int)(e % m);
-    double sacc = 0;
-    for (int o = 0; o < p; ++o) {
-      const double db = W.Dsc[o];
-      if (db > 0) sacc += R[(size_t)a * p + o] / db * d.Vc[(size_t)c * d.ldv + o];
-    }
-    W.Y[(size_t)a * m + c] = sacc;
+  // Rs = R D^{-1} (p x p, rows >= k zero): the core Y = Rs Vc^T is formed by
+  // a grouped GEMM after this kernel.  (R[a][o] = 0 before a in pivot order.)
+  __syncthreads();
+  for (long e = threadIdx.x; e < (long)p * p; e += blockDim.x) {
+    const int a = (int)(e / p), o = (int)(e % p);
+    const double db = W.Dsc[o];
+    R[e] = (a < k && db > 0) ? R[e] / db : 0.0;
   }
 }
 
 // One Cholesky-QR pass on the k x k Gram Gq (ld p) of the current basis:
-// Gq = R^T R, T2 = R^{-1} (k x k, ld p), Y <- R Y.  info[4] = 1 when the
+// Gq = R^T R, T2 = R^{-1} (k x k, ld p), R zero-padded to p x p in work Rki
+// (the core update Y <- R Y is a GEMM after this kernel).  info[4] = 1 when the
 // basis was far from orthonormal (max |Gq_ij - delta_ij| > 0.1), so that one
 // more pass is needed before the SVD.
 __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs) {
@@ -609,58 +527,232 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs) {
     const int a = (int)(e / k), b = (int)(e % k);
     d.T2[(size_t)a * p + b] = W.Rki[e];
   }
-  // Y <- R Y (k x m), via C
-  for (long e = threadIdx.x; e < (long)k * m; e += blockDim.x) {
-    const int a = (int)(e / m), c = (int)(e % m);
-    double sacc = 0;
-    for (int l = a; l < k; ++l) sacc += R[(size_t)a * k + l] * W.Y[(size_t)l * m + c];
-    W.C[e] = sacc;
-  }
   __syncthreads();
-  for (long e = threadIdx.x; e < (long)k * m; e += blockDim.x) W.Y[e] = W.C[e];
+  // R (upper triangle of the k x k factor) zero-padded to p x p into Rki: the
+  // core update Y <- R Y is a grouped GEMM after this kernel
+  for (long e = threadIdx.x; e < (long)p * p; e += blockDim.x) {
+    const int a = (int)(e / p), b = (int)(e % p);
+    W.Rki[e] = (a < k && b < k && b >= a) ? R[(size_t)a * k + b] : 0.0;
+  }
 }
 
-// SVD of the core C = Y (k x m) by one-sided Jacobi, rank rule, output
-// T1 <- T2 W_r (k x r, ld p; the tall result is Q_last T1) and
-// Vout = Z_r diag(s_r).
-__global__ void __launch_bounds__(kSmallThreads) k_trunc_svd(TruncDesc* descs) {
-  const TruncDesc d = descs[blockIdx.x];
-  const int p = d.p, m = d.m;
-  __shared__ int s_k, s_r;
-  if (threadIdx.x == 0) s_k = p > 0 ? d.info[0] : 0;
+// ---------------------------------------------------------------------------
+// SVD of the core by one-sided Jacobi on a thread-block cluster
+// ---------------------------------------------------------------------------
+// The core C (k x m, rows of d.core, ld m) is orthogonalised as A = C
+// (L = k, n = m columns) if m < k, else A = C^T (L = m, n = k): A V = A'
+// with orthogonal columns, V accumulated.  Every column is stored with its V
+// column appended (length LV = L + n), so one rotation updates both.
+//
+// Parallel block ordering: the n columns form nb = 2 C blocks of b columns; CTA
+// c of the cluster owns blocks 2c, 2c+1 in its shared memory.  A sweep is
+//   (i) every CTA orthogonalises all pairs inside its own 2b columns, then
+//  (ii) nb - 1 rounds of the round-robin tournament on blocks: in each round
+//       CTA c copies its pair of blocks (from the owners, through distributed
+//       shared memory) into local memory, rotates all b^2 cross pairs (b
+//       sub-rounds of b disjoint pairs, one warp per pair), and writes them
+//       back, followed by a cluster barrier.
+// Every block pair meets once per sweep, so every column pair is visited; the
+// pairing and the order of rotations are fixed, so the result does not depend
+// on timing.  A pair is rotated when |a_x . a_y| > 4 eps sqrt(|a_x|^2
+// |a_y|^2) and neither column is below eps times the largest column norm.
+// Stops after a sweep without rotations (info[3] = sweeps) or at 40 sweeps
+// (info[2] = LRFSI_ENOCONV).  The FP64 rate of one SM is the bound here, hence
+// the cluster: the rotations of one problem run on C SMs.
+constexpr int kSvdThreads = 256;
+constexpr int kSvdWarps = kSvdThreads / 32;
+
+__device__ __forceinline__ bool jacobi_pair(double* __restrict__ cx, double* __restrict__ cy, int L, int LV,
+                                            double small2, int lane) {
+  double al = 0, be = 0, ga = 0;
+  for (int i = lane; i < L; i += 32) {
+    const double u = cx[i], v = cy[i];
+    al = fma(u, u, al);
+    be = fma(v, v, be);
+    ga = fma(u, v, ga);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
+  if (!(al > small2 && be > small2 && fabs(ga) > 4.4e-16 * sqrt(al * be))) return false;
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+  for (int i = lane; i < LV; i += 32) {
+    const double u = cx[i], v = cy[i];
+    cx[i] = c * u - sn * v;
+    cy[i] = sn * u + c * v;
+  }
+  return true;
+}
+
+// largest squared column norm (A part) of the 2b columns at cols (global
+// column index of slot 0 = j0; columns >= n are padding)
+__device__ double local_cmax(const double* cols, int nslot, int j0, int n, int L, int LV) {
+  __shared__ double s_red[kSvdWarps];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double mx = 0;
+  for (int h = warp; h < nslot; h += kSvdWarps) {
+    if (j0 + h >= n) continue;
+    double t = 0;
+    for (int i = lane; i < L; i += 32) t = fma(cols[(size_t)h * LV + i], cols[(size_t)h * LV + i], t);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    mx = fmax(mx, t);
+  }
+  if (lane == 0) s_red[warp] = mx;
   __syncthreads();
-  const int k = s_k;
+  double r = 0;
+  for (int w = 0; w < kSvdWarps; ++w) r = fmax(r, s_red[w]);
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
+  const TruncDesc d = descs[blockIdx.y];
+  const int p = d.p, m = d.m;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ double s_ex[2][2];  // per sweep parity: {rotations, max column norm^2}
+  __shared__ double s_tot, s_cm;
+  __shared__ int s_rot, s_r;
+  // uniform across the cluster: every CTA reads the same descriptor and info
+  const int k = p > 0 ? d.info[0] : 0;
   if (k <= 0 || m <= 0 || d.info[2] != 0) {
-    if (threadIdx.x == 0) { d.info[1] = 0; d.info[3] = 0; *d.frob2 = 0.0; }
+    if (crank == 0 && tid == 0) { d.info[1] = 0; d.info[3] = 0; *d.frob2 = 0.0; }
     return;
   }
   TruncWork W(d.work, p, m);
-  const int n = k < m ? k : m, L = k < m ? m : k;
-  const bool cols_of_C = m <= k;  // A = C (L = k, n = m) else A = C^T (L = m, n = k)
-  for (long e = threadIdx.x; e < (long)L * n; e += blockDim.x) {
-    const int col = (int)(e / L), i = (int)(e % L);
-    W.A[e] = cols_of_C ? W.Y[(size_t)i * m + col] : W.Y[(size_t)col * m + i];
+  // A = C^T whenever k <= m: the rows of the core are graded by the pivoted
+  // Cholesky, and Jacobi converges in fewer sweeps on graded columns
+  const bool cols_of_C = m < k;
+  const int n = cols_of_C ? m : k, L = cols_of_C ? k : m, LV = L + n;
+  const int nb = 2 * C, b = (n + nb - 1) / nb;
+  extern __shared__ double sm[];
+  double* home = sm;                    // 2b columns: global columns 2 crank b + h
+  double* work = sm + (size_t)2 * b * LV;  // the two blocks of a tournament round
+  const int j0 = 2 * crank * b;
+  const double* core = d.core;
+  for (long e = tid; e < (long)2 * b * LV; e += kSvdThreads) {
+    const int h = (int)(e / LV), i = (int)(e % LV), j = j0 + h;
+    double v = 0;
+    if (j < n) {
+      if (i < L) v = cols_of_C ? core[(size_t)i * m + j] : core[(size_t)j * m + i];
+      else v = (i - L == j) ? 1.0 : 0.0;
+    }
+    home[e] = v;
   }
   __syncthreads();
-  const int sweeps = jacobi_onesided(W.A, L, n, W.Vm, 40);
-  __syncthreads();
-  double* sraw = W.C;  // n unsorted singular values
-  double* sig = d.sv;
-  int* order = d.iwork;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    double sacc = 0;
-    for (int i = 0; i < L; ++i) sacc += W.A[(size_t)j * L + i] * W.A[(size_t)j * L + i];
-    sraw[j] = sqrt(sacc);
+  // exchange of {rotations, largest column norm} over the cluster
+  auto exchange = [&](int slot, double rot, double cm) {
+    if (tid == 0) { s_ex[slot][0] = rot; s_ex[slot][1] = cm; }
+    cl.sync();
+    if (tid == 0) {
+      double tr = 0, tc = 0;
+      for (int r = 0; r < C; ++r) {
+        const double* ex = cl.map_shared_rank(&s_ex[slot][0], r);
+        tr += ex[0];
+        tc = fmax(tc, ex[1]);
+      }
+      s_tot = tr;
+      s_cm = tc;
+    }
+    __syncthreads();
+  };
+  exchange(1, 0.0, local_cmax(home, 2 * b, j0, n, L, LV));
+  double small2 = s_cm * 1e-32;
+  int sweeps = -1;
+  for (int t = 0; t < 40; ++t) {
+    if (tid == 0) s_rot = 0;
+    __syncthreads();
+    int nrot = 0;
+    {  // (i) all pairs inside this CTA's 2b columns: tournament on 2b slots
+      const int np = 2 * b;
+      for (int round = 0; round < np - 1; ++round) {
+        for (int q = warp; q < b; q += kSvdWarps) {
+          auto pos = [&](int u) { return u == 0 ? 0 : ((round + u - 1) % (np - 1)) + 1; };
+          int x = pos(q), y = pos(np - 1 - q);
+          if (x > y) { const int tt = x; x = y; y = tt; }
+          if (j0 + y >= n) continue;
+          if (jacobi_pair(home + (size_t)x * LV, home + (size_t)y * LV, L, LV, small2, lane)) ++nrot;
+        }
+        __syncthreads();
+      }
+    }
+    cl.sync();
+    for (int round = 0; round < nb - 1; ++round) {  // (ii) cross pairs of the block tournament
+      auto bpos = [&](int u) { return u == 0 ? 0 : ((round + u - 1) % (nb - 1)) + 1; };
+      int X = bpos(crank), Y = bpos(nb - 1 - crank);
+      if (X > Y) { const int tt = X; X = Y; Y = tt; }
+      double* hx = cl.map_shared_rank(sm, X >> 1) + (size_t)(X & 1) * b * LV;
+      double* hy = cl.map_shared_rank(sm, Y >> 1) + (size_t)(Y & 1) * b * LV;
+      const bool any = X * b < n && Y * b < n;
+      if (any) {
+        for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
+          work[e] = hx[e];
+          work[(size_t)b * LV + e] = hy[e];
+        }
+        __syncthreads();
+        for (int sr = 0; sr < b; ++sr) {
+          for (int q = warp; q < b; q += kSvdWarps) {
+            const int xi = q, yi = (q + sr) % b;
+            if (X * b + xi >= n || Y * b + yi >= n) continue;
+            if (jacobi_pair(work + (size_t)xi * LV, work + (size_t)(b + yi) * LV, L, LV, small2, lane)) ++nrot;
+          }
+          __syncthreads();
+        }
+        for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
+          hx[e] = work[e];
+          hy[e] = work[(size_t)b * LV + e];
+        }
+      }
+      cl.sync();
+    }
+    if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
+    __syncthreads();
+    exchange(t & 1, (double)s_rot, local_cmax(home, 2 * b, j0, n, L, LV));
+    small2 = s_cm * 1e-32;
+    if (s_tot == 0.0) { sweeps = t + 1; break; }
+  }
+  // final columns to global memory: A (L x n) and V (n x n), column-major;
+  // unsorted singular values into Dsc
+  for (int h = warp; h < 2 * b; h += kSvdWarps) {
+    const int j = j0 + h;
+    if (j >= n) continue;
+    const double* col = home + (size_t)h * LV;
+    double t = 0;
+    for (int i = lane; i < L; i += 32) {
+      W.A[(size_t)j * L + i] = col[i];
+      t = fma(col[i], col[i], t);
+    }
+    for (int i = lane; i < n; i += 32) W.Vm[(size_t)j * n + i] = col[L + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) W.Dsc[j] = sqrt(t);
+  }
+  __threadfence();
+  cl.sync();
+  // every CTA: descending order (ties by index), rank rule (identical results)
+  double* sig = work;
+  int* order = (int*)(work + n);
+  const double* sraw = W.Dsc;
+  for (int j = tid; j < n; j += kSvdThreads) {
+    const double v = sraw[j];
+    int rk = 0;
+    for (int l = 0; l < n; ++l) {
+      const double w = sraw[l];
+      rk += (w > v) || (w == v && l < j);
+    }
+    order[rk] = j;
+    sig[rk] = v;
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    int rank = 0;
-    for (int l = 0; l < n; ++l) rank += (sraw[l] > sraw[j]) || (sraw[l] == sraw[j] && l < j);
-    order[rank] = j;
-    sig[rank] = sraw[j];
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
+  if (tid == 0) {
     double tot = 0;
     for (int j = 0; j < n; ++j) tot += sig[j] * sig[j];
     double tail = 0;
@@ -672,31 +764,29 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_svd(TruncDesc* descs) {
     if (tot == 0.0) r = 0;
     if (r > d.rank_cap) r = d.rank_cap;
     s_r = r;
-    d.info[1] = r;
-    d.info[3] = sweeps;
-    if (sweeps < 0) d.info[2] = LRFSI_ENOCONV;
-    *d.frob2 = tot;
+    if (crank == 0) {
+      d.info[1] = r;
+      d.info[3] = sweeps;
+      if (sweeps < 0) d.info[2] = LRFSI_ENOCONV;
+      *d.frob2 = tot;
+    }
   }
   __syncthreads();
+  if (crank == 0)
+    for (int j = tid; j < n; j += kSvdThreads) d.sv[j] = sig[j];
   const int r = s_r;
-  double* Wr = W.Rk;  // k x r
-  for (long e = threadIdx.x; e < (long)k * r; e += blockDim.x) {
+  // W_r (k x r, ld p) into Rk; the tall coefficients T2 W_r follow as a GEMM
+  const long stride = (long)C * kSvdThreads;
+  for (long e = (long)crank * kSvdThreads + tid; e < (long)k * r; e += stride) {
     const int a = (int)(e / r), j = (int)(e % r);
     const int col = order[j];
-    Wr[e] = cols_of_C ? (sig[j] > 0 ? W.A[(size_t)col * L + a] / sig[j] : 0.0) : W.Vm[(size_t)col * n + a];
+    W.Rk[(size_t)a * p + j] =
+        cols_of_C ? (sig[j] > 0 ? W.A[(size_t)col * L + a] / sig[j] : 0.0) : W.Vm[(size_t)col * n + a];
   }
-  for (long e = threadIdx.x; e < (long)m * r; e += blockDim.x) {
+  for (long e = (long)crank * kSvdThreads + tid; e < (long)m * r; e += stride) {
     const int c = (int)(e / r), j = (int)(e % r);
     const int col = order[j];
     d.Vout[(size_t)c * d.ldvo + j] = cols_of_C ? W.Vm[(size_t)col * n + c] * sig[j] : W.A[(size_t)col * L + c];
-  }
-  __syncthreads();
-  // T1 = T2 W_r with T2 upper triangular (k x k, ld p)
-  for (long e = threadIdx.x; e < (long)k * r; e += blockDim.x) {
-    const int a = (int)(e / r), j = (int)(e % r);
-    double sacc = 0;
-    for (int l = a; l < k; ++l) sacc += d.T2[(size_t)a * p + l] * Wr[(size_t)l * r + j];
-    d.T1[(size_t)a * p + j] = sacc;
   }
 }
 
@@ -719,10 +809,75 @@ int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev) {
   return LRFSI_OK;
 }
 
-int trunc_svd(int n, cudaStream_t s, TruncDesc* d_dev) {
-  account(KC_TRUNC, 0, 0);
-  TimedLaunch tl(KC_TRUNC, s);
-  k_trunc_svd<<<n, kSmallThreads, 0, s>>>(d_dev);
+// Cluster size for the SVD: the problems' clusters together should cover the
+// SMs about once (16 needs the non-portable cluster size; fall back to 8 if
+// the device cannot co-schedule it).
+static int svd_cluster_size(int nprob, size_t smem) {
+  static int max16 = -1;
+  if (max16 < 0) {
+    max16 = 0;
+    if (cudaFuncSetAttribute(k_trunc_svd, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeClusterDimension;
+      at[0].val.clusterDim.x = 16;
+      at[0].val.clusterDim.y = 1;
+      at[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(16, 1, 1);
+      cfg.blockDim = dim3(kSvdThreads, 1, 1);
+      cfg.dynamicSmemBytes = 64 * 1024;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      int ncl = 0;
+      if (cudaOccupancyMaxActiveClusters(&ncl, k_trunc_svd, &cfg) == cudaSuccess && ncl > 0) max16 = 1;
+    }
+    cudaGetLastError();
+  }
+  (void)smem;
+  if (nprob <= 9 && max16) return 16;
+  if (nprob <= 19) return 8;
+  if (nprob <= 38) return 4;
+  return 2;
+}
+
+int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
+  if (n <= 0) return LRFSI_OK;
+  LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
+  int nmax = 1, Lmax = 1;
+  for (int i = 0; i < n; ++i) {
+    const int lo = d[i].p < d[i].m ? d[i].p : d[i].m, hi = d[i].p < d[i].m ? d[i].m : d[i].p;
+    nmax = nmax > lo ? nmax : lo;
+    Lmax = Lmax > hi ? Lmax : hi;
+  }
+  int C = svd_cluster_size(n, 0);
+  size_t smem = 0;
+  for (;;) {
+    const int b = (nmax + 2 * C - 1) / (2 * C);
+    smem = sizeof(double) * (size_t)4 * b * (Lmax + nmax);
+    if (smem <= 200 * 1024 || C >= 16) break;
+    C *= 2;  // more CTAs per problem: smaller blocks
+  }
+  if (smem > 200 * 1024) return fail(LRFSI_EINVAL, "trunc_svd: core too large for the cluster SVD");
+  static size_t smem_set = 0;
+  if (smem > 48 * 1024 && smem > smem_set) {
+    LRFSI_CUDA(cudaFuncSetAttribute(k_trunc_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
+    smem_set = 200 * 1024;
+  }
+  account(KC_SVD, 0, 0);
+  TimedLaunch tl(KC_SVD, s);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = C;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C, n, 1);
+  cfg.blockDim = dim3(kSvdThreads, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  LRFSI_CUDA(cudaLaunchKernelEx(&cfg, k_trunc_svd, d_dev));
   LRFSI_TRY(check_launch("k_trunc_svd"));
   tl.end(s);
   return LRFSI_OK;

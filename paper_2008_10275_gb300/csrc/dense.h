@@ -44,6 +44,7 @@ struct TruncDesc {
   double* Vout;      // m x rank output (row-major, ldvo)
   int ldvo;
   double* work;      // scratch for the small SVD (>= trunc_small_work(p, m) doubles)
+  const double* core;  // k x m core for the SVD (ld m): one of the two core buffers of work
   int* iwork;        // >= 2 p ints
   int* info;         // [0] k (kept after pass 1), [1] rank, [2] status, [3] sweeps, [4] needs another QR pass
   double* sv;        // >= p singular values (descending)
@@ -55,6 +56,24 @@ struct TruncDesc {
 size_t trunc_small_work(int p, int m);
 int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev);
 int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev);
-int trunc_svd(int n, cudaStream_t s, TruncDesc* d_dev);
+int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev);
+
+// Offsets of the per-problem scratch (doubles): Dsc (p) | Rk (p*p) | Rki (p*p) |
+// Y (p*m) | C (p*m) | A (n'*n') | Vm (n'*n'), n' = max(p, m).  Rk holds the
+// scaled pass-1 factor, later W_r; Rki the zero-padded factor of the latest QR
+// pass; Y and C the two core buffers.
+struct TruncWork {
+  double *Dsc, *Rk, *Rki, *Y, *C, *A, *Vm;
+  __host__ __device__ TruncWork(double* w, int p, int m) {
+    const size_t n = (size_t)(p > m ? p : m);
+    Dsc = w;
+    Rk = Dsc + p;
+    Rki = Rk + (size_t)p * p;
+    Y = Rki + (size_t)p * p;
+    C = Y + (size_t)p * m;
+    A = C + (size_t)p * m;
+    Vm = A + n * n;
+  }
+};
 
 }  // namespace lrfsi

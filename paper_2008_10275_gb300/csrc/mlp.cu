@@ -131,15 +131,105 @@ __global__ void k_to_bf16(const float* __restrict__ p, long n, __nv_bfloat16* __
   if (e < n) pbf[e] = __float2bfloat16_rn(p[e]);
 }
 
-// x0[b][i] = offset[i] + s[i] * sum_l Phi[i][l] c[b][l] * cs[l]; Dirichlet rows -> b_D
+// Box scaling of the parameters: z = 2 (p - lo) / (hi - lo) - 1 per coordinate.
+__global__ void k_scale_params(const double* __restrict__ mu, const double* __restrict__ nu, int B, double mlo,
+                               double mhi, double nlo, double nhi, float* __restrict__ Z) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  Z[2 * b] = (float)(2.0 * (mu[b] - mlo) / (mhi - mlo) - 1.0);
+  Z[2 * b + 1] = (float)(2.0 * (nu[b] - nlo) / (nhi - nlo) - 1.0);
+}
+
+// Snapshot statistics per DOF: off[i] = mean_j X_j[i], ss[i] = sum_j (X_j[i] - off[i])^2.
+// X: n problem-major rows of length ldx.
+__global__ void k_snap_mean(const double* __restrict__ X, int ldx, int n, long M, double* __restrict__ off,
+                            double* __restrict__ ss) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  double s = 0;
+  for (int j = 0; j < n; ++j) s += X[(long)j * ldx + i];
+  const double mean = s / n;
+  double q = 0;
+  for (int j = 0; j < n; ++j) {
+    const double d = X[(long)j * ldx + i] - mean;
+    q += d * d;
+  }
+  off[i] = mean;
+  ss[i] = q;
+}
+
+// One block per field f: scale[f] = RMS of the centred snapshot values of that
+// field (1 where the field does not vary), then fs[i] = scale[field[i]].
+__global__ void k_field_scale(const double* __restrict__ ss, const int* __restrict__ field, long M, int n,
+                              double* __restrict__ fscale) {
+  const int f = blockIdx.x;
+  double s = 0;
+  long c = 0;
+  for (long i = threadIdx.x; i < M; i += blockDim.x)
+    if (field[i] == f) {
+      s += ss[i];
+      ++c;
+    }
+  __shared__ double rs[256];
+  __shared__ long rc[256];
+  rs[threadIdx.x] = s;
+  rc[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      rs[threadIdx.x] += rs[threadIdx.x + o];
+      rc[threadIdx.x] += rc[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double v = rc[0] > 0 ? sqrt(rs[0] / ((double)rc[0] * n)) : 0.0;
+    fscale[f] = v > 0 ? v : 1.0;
+  }
+}
+
+__global__ void k_fill_field(const double* __restrict__ fscale, const int* __restrict__ field, long M,
+                             double* __restrict__ fs) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < M) fs[i] = fscale[field[i]];
+}
+
+// Y (M x n, row-major) = (X_j[i] - off[i]) / fs[i]
+__global__ void k_scale_snap(const double* __restrict__ X, int ldx, int n, long M, const double* __restrict__ off,
+                             const double* __restrict__ fs, double* __restrict__ Y) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * n) return;
+  const long i = e / n;
+  const int j = (int)(e % n);
+  Y[e] = (X[(long)j * ldx + i] - off[i]) / fs[i];
+}
+
+// Regression targets: cs[l] = RMS over snapshots of coefficient l (1 if zero),
+// T[j][l] = C[j][l] / cs[l] in FP32.
+__global__ void k_coef_targets(const double* __restrict__ Cc, int ldc, int n, int k, double* __restrict__ cs,
+                               float* __restrict__ T) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= k) return;
+  double q = 0;
+  for (int j = 0; j < n; ++j) q += Cc[(long)j * ldc + l] * Cc[(long)j * ldc + l];
+  double r = sqrt(q / n);
+  if (!(r > 0)) r = 1.0;
+  cs[l] = r;
+  for (int j = 0; j < n; ++j) T[(long)j * k + l] = (float)(Cc[(long)j * ldc + l] / r);
+}
+
+// x0 = offset + fs .* (Phi (cs .* c_b)), Dirichlet rows -> b_D.  Writes the
+// problem-major start X (B x M) and its column-major copy Xt (M x B) for the
+// residual check.
 __global__ void k_learned_start(const double* __restrict__ Phi, int ldphi, int k, const float* __restrict__ C,
                                 const double* __restrict__ cs, const double* __restrict__ fs,
                                 const double* __restrict__ off, const char* __restrict__ ident,
-                                const double* __restrict__ bD, long M, int B, double* __restrict__ X) {
+                                const double* __restrict__ bD, long M, int B, double* __restrict__ X,
+                                double* __restrict__ Xt) {
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= M * B) return;
-  const int b = (int)(e / M);
-  const long i = e % M;
+  const long i = e / B;
+  const int b = (int)(e % B);
   double v;
   if (ident[i]) {
     v = bD[i];
@@ -148,7 +238,22 @@ __global__ void k_learned_start(const double* __restrict__ Phi, int ldphi, int k
     for (int l = 0; l < k; ++l) s += Phi[i * ldphi + l] * (double)C[(long)b * k + l] * cs[l];
     v = off[i] + fs[i] * s;
   }
+  Xt[e] = v;
   X[(long)b * M + i] = v;
+}
+
+// Columns whose start does not reduce the residual below that of b_D fall
+// back to b_D: flag[b] = n2[b] >= n2D[b].
+__global__ void k_start_fallback(const double* __restrict__ n2, const double* __restrict__ n2D,
+                                 const double* __restrict__ bD, long M, int B, double* __restrict__ X,
+                                 int* __restrict__ flag) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * B) return;
+  const int b = (int)(e / M);
+  const long i = e % M;
+  const bool fb = !(n2[b] < n2D[b]);
+  if (fb) X[e] = bD[i];
+  if (i == 0) flag[b] = fb ? 1 : 0;
 }
 
 }  // namespace lrfsi
@@ -316,23 +421,87 @@ int lrfsi_mlp_train(lrfsi_mlp_h h, const float* Z, const float* T, int B, int ep
   return LRFSI_OK;
 }
 
-int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h h, const float* Z, int B, const double* Phi, int ldphi, int k,
-                        const double* coef_scale, const double* field_scale, const double* offset, double* X,
+int lrfsi_learned_fit(lrfsi_mesh_h mesh, lrfsi_mlp_h h, const double* mu_h, const double* nu_h, int n,
+                      const double* box, const double* X, int ldx, int k, int epochs, float lr, double* Phi,
+                      int ldphi, double* coef_scale, double* field_scale, double* offset, float* loss_host,
+                      double* sigma_host, lrfsi_stream_t stream) {
+  if (!mesh || !h || !mu_h || !nu_h || !box || !X || !Phi || !coef_scale || !field_scale || !offset || n < 1 ||
+      k < 1 || k > n || ldx < mesh->h.M || ldphi < k || epochs < 0 || !(lr > 0) || h->d.n[0] != 2 ||
+      h->d.n[kMlpLayers] != k || !(box[1] > box[0]) || !(box[3] > box[2]))
+    return fail(LRFSI_EINVAL, "lrfsi_learned_fit: bad argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long M = mesh->h.M;
+  DevBuf<double> ss, fsc, Y, Cc, mu, nu;
+  DevBuf<int> field;
+  DevBuf<float> Z, T;
+  LRFSI_TRY(ss.alloc(M));
+  LRFSI_TRY(fsc.alloc(8));
+  LRFSI_TRY(Y.alloc((size_t)M * n));
+  LRFSI_TRY(Cc.alloc((size_t)n * k));
+  LRFSI_TRY(Z.alloc((size_t)2 * n));
+  LRFSI_TRY(T.alloc((size_t)n * k));
+  LRFSI_TRY(field.upload(mesh->h.dof_field, s));
+  std::vector<double> muv(mu_h, mu_h + n), nuv(nu_h, nu_h + n);
+  LRFSI_TRY(mu.upload(muv, s));
+  LRFSI_TRY(nu.upload(nuv, s));
+  k_snap_mean<<<ceil_div(M, 256), 256, 0, s>>>(X, ldx, n, M, offset, ss.p);
+  LRFSI_TRY(check_launch("k_snap_mean"));
+  k_field_scale<<<5, 256, 0, s>>>(ss.p, field.p, M, n, fsc.p);
+  LRFSI_TRY(check_launch("k_field_scale"));
+  k_fill_field<<<ceil_div(M, 256), 256, 0, s>>>(fsc.p, field.p, M, field_scale);
+  LRFSI_TRY(check_launch("k_fill_field"));
+  k_scale_snap<<<ceil_div(M * n, 256), 256, 0, s>>>(X, ldx, n, M, offset, field_scale, Y.p);
+  LRFSI_TRY(check_launch("k_scale_snap"));
+  LRFSI_TRY(lrfsi_pod(mesh, Y.p, n, n, k, Phi, ldphi, Cc.p, k, sigma_host, stream));
+  k_coef_targets<<<ceil_div(k, 64), 64, 0, s>>>(Cc.p, k, n, k, coef_scale, T.p);
+  LRFSI_TRY(check_launch("k_coef_targets"));
+  k_scale_params<<<ceil_div(n, 128), 128, 0, s>>>(mu.p, nu.p, n, box[0], box[1], box[2], box[3], Z.p);
+  LRFSI_TRY(check_launch("k_scale_params"));
+  LRFSI_TRY(lrfsi_mlp_train(h, Z.p, T.p, n, epochs, lr, loss_host, stream));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h h, const double* mu_h, const double* nu_h, int B,
+                        const double* box, const double* Phi, int ldphi, int k, const double* coef_scale,
+                        const double* field_scale, const double* offset, double* X, int* fallback_host,
                         lrfsi_stream_t stream) {
-  if (!mesh || !h || !Z || !Phi || !coef_scale || !field_scale || !offset || !X || B < 1 || k < 1 || ldphi < k ||
-      h->d.n[kMlpLayers] != k)
+  if (!mesh || !h || !mu_h || !nu_h || !box || !Phi || !coef_scale || !field_scale || !offset || !X || B < 1 ||
+      k < 1 || ldphi < k || h->d.n[0] != 2 || h->d.n[kMlpLayers] != k || !(box[1] > box[0]) || !(box[3] > box[2]))
     return fail(LRFSI_EINVAL, "lrfsi_learned_start: bad argument");
   cudaStream_t s = (cudaStream_t)stream;
-  DevBuf<float> C;
+  const long M = mesh->h.M;
+  DevBuf<float> Z, C;
   DevBuf<char> ident;
+  DevBuf<double> mu, nu, Xt, R, n2, n2D, work;
+  DevBuf<int> flag;
+  LRFSI_TRY(Z.alloc((size_t)2 * B));
   LRFSI_TRY(C.alloc((size_t)B * k));
-  LRFSI_TRY(mlp_forward_impl(h, Z, B, C.p, s, false));
+  LRFSI_TRY(Xt.alloc((size_t)M * B));
+  LRFSI_TRY(R.alloc((size_t)M * B));
+  LRFSI_TRY(n2.alloc(B));
+  LRFSI_TRY(n2D.alloc(B));
+  LRFSI_TRY(flag.alloc(B));
+  LRFSI_TRY(work.alloc((size_t)ceil_div(M, 256) * B));
+  std::vector<double> muv(mu_h, mu_h + B), nuv(nu_h, nu_h + B);
+  LRFSI_TRY(mu.upload(muv, s));
+  LRFSI_TRY(nu.upload(nuv, s));
   std::vector<char> id(mesh->h.ident.begin(), mesh->h.ident.end());
   LRFSI_TRY(ident.upload(id, s));
-  const long M = mesh->h.M;
+  k_scale_params<<<ceil_div(B, 128), 128, 0, s>>>(mu.p, nu.p, B, box[0], box[1], box[2], box[3], Z.p);
+  LRFSI_TRY(check_launch("k_scale_params"));
+  LRFSI_TRY(mlp_forward_impl(h, Z.p, B, C.p, s, false));
   k_learned_start<<<ceil_div(M * B, 256), 256, 0, s>>>(Phi, ldphi, k, C.p, coef_scale, field_scale, offset, ident.p,
-                                                       mesh->bD.p, M, B, X);
+                                                       mesh->bD.p, M, B, X, Xt.p);
   LRFSI_TRY(check_launch("k_learned_start"));
+  // fallback test: residual of the learned start against that of b_D, per column
+  LRFSI_TRY(launch_residual(mesh, Xt.p, B, B, nullptr, mu.p, nu.p, R.p, B, s));
+  LRFSI_TRY(launch_colnorm2(R.p, M, B, B, n2.p, work.p, work.n, s));
+  LRFSI_TRY(launch_residual(mesh, mesh->bD.p, 0, B, nullptr, mu.p, nu.p, R.p, B, s));
+  LRFSI_TRY(launch_colnorm2(R.p, M, B, B, n2D.p, work.p, work.n, s));
+  k_start_fallback<<<ceil_div(M * B, 256), 256, 0, s>>>(n2.p, n2D.p, mesh->bD.p, M, B, X, flag.p);
+  LRFSI_TRY(check_launch("k_start_fallback"));
+  if (fallback_host) LRFSI_CUDA(cudaMemcpyAsync(fallback_host, flag.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
   LRFSI_CUDA(cudaStreamSynchronize(s));
   return LRFSI_OK;
 }

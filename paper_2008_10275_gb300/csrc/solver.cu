@@ -592,6 +592,11 @@ namespace lrfsi {
 
 // T([X | ...], [V | ...]) for the listed subsets.  Inputs in Xcat (ld ldP) and
 // Vcat (ld ldP) with p[k] columns; outputs U (tall, ld ldR) and V (ld ldR).
+// Truncation counters (process-wide): calls, SVD sweeps (sum, max), SVDs that
+// hit the sweep limit, Cholesky-QR breakdowns, retries.
+static std::atomic<long long> g_tr_calls{0}, g_tr_sweeps{0}, g_tr_maxsweeps{0}, g_tr_noconv{0}, g_tr_breakdown{0},
+    g_tr_retry{0};
+
 static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
                          const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
                          std::vector<int>& rank, std::vector<double>& frob2, double drop, std::vector<int>& broke,
@@ -630,19 +635,34 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
   }
   LRFSI_TRY(gram_batched(gd.data(), na, M, S->gramwork.p, S->gramwork.n, s));
   LRFSI_TRY(trunc_pass1(td.data(), na, s, S->tdesc.p));
-  std::vector<GemmDesc<double>> gm(na);
+  // Q1 = X T1 (tall) and the core Y = Rs Vc^T (p x m; rows >= k are zero)
+  std::vector<GemmDesc<double>> gm(na), gy;
   for (int a = 0; a < na; ++a) {
     const int k = act[a];
+    const TruncWork W(td[a].work, p[k], S->m[k]);
     gm[a] = GemmDesc<double>{(int)M, p[k], p[k], S->tall(S->Xcat, k, ldP), ldP, 1, td[a].T1, p[k], 1,
                              S->tall(S->Q1, k, ldP), ldP, 1, 1.0, 0.0};
+    gy.push_back(gm[a]);
+    gy.push_back(GemmDesc<double>{p[k], S->m[k], p[k], W.Rk, p[k], 1, td[a].Vc, 1, td[a].ldv, W.Y, S->m[k], 1, 1.0,
+                                  0.0});
   }
-  LRFSI_TRY(gemm_grouped<double>(gm.data(), na, s));
+  LRFSI_TRY(gemm_grouped<double>(gy.data(), (int)gy.size(), s));
   for (int a = 0; a < na; ++a) {
     const int k = act[a];
     gd[a] = GramDesc{S->tall(S->Q1, k, ldP), ldP, p[k], S->tall(S->Q1, k, ldP), ldP, p[k], td[a].G2, p[k]};
   }
   LRFSI_TRY(gram_batched(gd.data(), na, M, S->gramwork.p, S->gramwork.n, s));
   LRFSI_TRY(trunc_qr(na, s, S->tdesc.p));
+  {  // core C = R2 Y
+    std::vector<GemmDesc<double>> gc;
+    for (int a = 0; a < na; ++a) {
+      const int k = act[a];
+      const TruncWork W(td[a].work, p[k], S->m[k]);
+      gc.push_back(GemmDesc<double>{p[k], S->m[k], p[k], W.Rki, p[k], 1, W.Y, S->m[k], 1, W.C, S->m[k], 1, 1.0, 0.0});
+      td[a].core = W.C;
+    }
+    LRFSI_TRY(gemm_grouped<double>(gc.data(), (int)gc.size(), s));
+  }
   std::vector<int> info((size_t)5 * S->K);
   auto read_info = [&]() -> int {
     LRFSI_CUDA(cudaMemcpyAsync(info.data(), S->info.p, sizeof(int) * 5 * S->K, cudaMemcpyDeviceToHost, s));
@@ -651,10 +671,10 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
   };
   LRFSI_TRY(read_info());
   // a third Cholesky-QR pass where the pass-1 basis was far from orthonormal:
-  // Q2 = Q1 R2^{-1}, G3 = Q2^T Q2, R3, Y <- R3 Y (the input X stays intact for a retry)
+  // Q2 = Q1 R2^{-1}, G3 = Q2^T Q2, R3, Y <- R3 C (the input X stays intact for a retry)
   std::vector<char> third(S->K, 0);
   std::vector<TruncDesc> td2;
-  std::vector<GemmDesc<double>> g2;
+  std::vector<GemmDesc<double>> g2, g3;
   std::vector<GramDesc> gd2;
   broke.clear();
   std::vector<char> bad(S->K, 0);
@@ -664,9 +684,12 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     if (info[5 * k + 4]) {
       third[k] = 1;
       const int kk = info[5 * k];
+      const TruncWork W(td[a].work, p[k], S->m[k]);
       g2.push_back(GemmDesc<double>{(int)M, kk, kk, S->tall(S->Q1, k, ldP), ldP, 1, td[a].T2, p[k], 1,
                                     S->tall(S->Q2, k, ldP), ldP, 1, 1.0, 0.0});
       gd2.push_back(GramDesc{S->tall(S->Q2, k, ldP), ldP, kk, S->tall(S->Q2, k, ldP), ldP, kk, td[a].G2, p[k]});
+      g3.push_back(GemmDesc<double>{p[k], S->m[k], p[k], W.Rki, p[k], 1, W.C, S->m[k], 1, W.Y, S->m[k], 1, 1.0, 0.0});
+      td[a].core = W.Y;
       td2.push_back(td[a]);
     }
   }
@@ -675,25 +698,50 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     LRFSI_TRY(gram_batched(gd2.data(), (int)gd2.size(), M, S->gramwork.p, S->gramwork.n, s));
     LRFSI_CUDA(cudaMemcpyAsync(S->tdesc.p + S->K, td2.data(), sizeof(TruncDesc) * td2.size(), cudaMemcpyHostToDevice, s));
     LRFSI_TRY(trunc_qr((int)td2.size(), s, S->tdesc.p + S->K));
+    LRFSI_TRY(gemm_grouped<double>(g3.data(), (int)g3.size(), s));
   }
-  LRFSI_TRY(trunc_svd(na, s, S->tdesc.p));
+  LRFSI_TRY(trunc_svd(td.data(), na, s, S->tdesc.p));
   std::vector<double> f2(S->K);
   LRFSI_CUDA(cudaMemcpyAsync(f2.data(), S->frob2.p, sizeof(double) * S->K, cudaMemcpyDeviceToHost, s));
   LRFSI_TRY(read_info());
   {  // algorithmic FP64 work of the small kernels (upper bound: every Jacobi pair rotated)
-    double fl = 0;
+    double fl = 0, fj = 0;
     for (int a = 0; a < na; ++a) {
       const int k = act[a];
-      const double P = p[k], kk = info[5 * k], mm = S->m[k];
+      const double P = p[k], kk = info[5 * k];
+      const double mm = S->m[k];
       const double n = std::min(kk, mm), L = std::max(kk, mm), sw = std::max(info[5 * k + 3], 1);
-      fl += 2.0 * P * P * P / 3.0 + kk * kk * kk / 3.0 + 2.0 * kk * mm * P;     // pass 1
-      fl += (third[k] ? 2.0 : 1.0) * (2.0 * kk * kk * kk / 3.0 + 2.0 * kk * kk * mm);  // QR passes
-      fl += sw * n * (n - 1) / 2.0 * (6.0 * L + 4.0 * n) + 2.0 * n * n * L;    // Jacobi
+      fl += 2.0 * P * P * P / 3.0 + kk * kk * kk / 3.0;                 // pass 1
+      fl += (third[k] ? 2.0 : 1.0) * (2.0 * kk * kk * kk / 3.0);         // QR passes
+      fj += sw * n * (n - 1) / 2.0 * (6.0 * L + 4.0 * (L + n));         // Jacobi
     }
     account(KC_TRUNC, fl, 0);
+    account(KC_SVD, fj, 0);
+  }
+  // tall coefficients T1 = T2_last W_r (k x r)
+  {
+    std::vector<GemmDesc<double>> gt;
+    for (int a = 0; a < na; ++a) {
+      const int k = act[a];
+      const int r = info[5 * k + 1], kk = info[5 * k];
+      if (bad[k] || info[5 * k + 2] == LRFSI_EBREAKDOWN || r <= 0) continue;
+      const TruncWork W(td[a].work, p[k], S->m[k]);
+      gt.push_back(GemmDesc<double>{kk, r, kk, td[a].T2, p[k], 1, W.Rk, p[k], 1, td[a].T1, p[k], 1, 1.0, 0.0});
+    }
+    LRFSI_TRY(gemm_grouped<double>(gt.data(), (int)gt.size(), s));
   }
   for (int a = 0; a < na; ++a) {
     const int k = act[a];
+    g_tr_calls += 1;
+    const int sw = info[5 * k + 3];
+    if (sw > 0) {
+      g_tr_sweeps += sw;
+      long long cur = g_tr_maxsweeps.load();
+      while (sw > cur && !g_tr_maxsweeps.compare_exchange_weak(cur, sw)) {
+      }
+    }
+    if (info[5 * k + 2] == LRFSI_ENOCONV) g_tr_noconv += 1;
+    if (bad[k] || info[5 * k + 2] == LRFSI_EBREAKDOWN) g_tr_breakdown += 1;
     rank[k] = info[5 * k + 1];
     frob2[k] = f2[k];
     if (bad[k] || info[5 * k + 2] == LRFSI_EBREAKDOWN) {
@@ -730,12 +778,27 @@ static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const 
       frob2[k] = f2[k];
     }
     todo = broke;
+    g_tr_retry += (long long)broke.size();
   }
   if (!todo.empty()) return fail(LRFSI_EBREAKDOWN, "truncation: Cholesky-QR breakdown after retries");
   return LRFSI_OK;
 }
 
 }  // namespace lrfsi
+
+extern "C" int lrfsi_truncation_counters(int64_t* out6, int reset) {
+  if (!out6) return fail(LRFSI_EINVAL, "lrfsi_truncation_counters: null argument");
+  out6[0] = g_tr_calls.load();
+  out6[1] = g_tr_sweeps.load();
+  out6[2] = g_tr_maxsweeps.load();
+  out6[3] = g_tr_noconv.load();
+  out6[4] = g_tr_breakdown.load();
+  out6[5] = g_tr_retry.load();
+  if (reset) {
+    g_tr_calls = 0; g_tr_sweeps = 0; g_tr_maxsweeps = 0; g_tr_noconv = 0; g_tr_breakdown = 0; g_tr_retry = 0;
+  }
+  return LRFSI_OK;
+}
 
 extern "C" int lrfsi_subset_destroy(lrfsi_subset_h S) {
   delete S;

@@ -352,15 +352,29 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
     while (nbp > 8 && (size_t)n * nbp * sizeof(double) > (size_t)kPanelSmem) nbp /= 2;
     for (int j0 = 0; j0 < n; j0 += nbp) {
       const int nb = j0 + nbp < n ? nbp : n - j0;
-      k_lu_panel<<<nprob, 512, sizeof(double) * (size_t)(n - j0) * nb, s>>>(pp, offD, poff, n, nmax, j0, nb);
-      LRFSI_TRY(check_launch("k_lu_panel"));
+      {
+        account(KC_LUPANEL, (double)nprob * ((double)(n - j0) * nb * nb - (double)nb * nb * nb / 3.0), 0);
+        TimedLaunch tk(KC_LUPANEL, s);
+        k_lu_panel<<<nprob, 512, sizeof(double) * (size_t)(n - j0) * nb, s>>>(pp, offD, poff, n, nmax, j0, nb);
+        LRFSI_TRY(check_launch("k_lu_panel"));
+        tk.end(s);
+      }
       // interchanges to the left and right of the panel
-      k_lu_laswp<<<dim3(ceil_div(n, 128), nprob), 128, 0, s>>>(pp, offD, nmax, poff, j0, j0 + nb, 0, n, j0, j0 + nb);
-      LRFSI_TRY(check_launch("k_lu_laswp"));
+      {
+        TimedLaunch tk(KC_LUPANEL, s);
+        k_lu_laswp<<<dim3(ceil_div(n, 128), nprob), 128, 0, s>>>(pp, offD, nmax, poff, j0, j0 + nb, 0, n, j0, j0 + nb);
+        LRFSI_TRY(check_launch("k_lu_laswp"));
+        tk.end(s);
+      }
       if (j0 + nb < n) {
-        k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, 128), nprob), 128, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
-                                                                              j0 + nb, n, 0);
-        LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+        {
+          account(KC_LUTRSM, (double)nprob * nb * nb * (n - j0 - nb), 0);
+          TimedLaunch tk(KC_LUTRSM, s);
+          k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, 128), nprob), 128, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
+                                                                                j0 + nb, n, 0);
+          LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+          tk.end(s);
+        }
         for (int b = 0; b < nprob; ++b) {
           double* A = pp.ws[b] + offD;
           gd[b] = GemmDesc<double>{n - j0 - nb, n - j0 - nb, nb,
@@ -376,12 +390,21 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
     k_lu_rhs<<<dim3(ceil_div((long)n * ldr, 256), nprob), 256, 0, s>>>(pp, lu.off_up + nb2 * sl, lu.off_rhs, n, nnext,
                                                                        nmax);
     LRFSI_TRY(check_launch("k_lu_rhs"));
-    k_lu_laswp<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, lu.off_rhs, ldr, poff, 0, n, 0, ldr, 0, 0);
-    LRFSI_TRY(check_launch("k_lu_laswp"));
+    {
+      TimedLaunch tk(KC_LUPANEL, s);
+      k_lu_laswp<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, lu.off_rhs, ldr, poff, 0, n, 0, ldr, 0, 0);
+      LRFSI_TRY(check_launch("k_lu_laswp"));
+      tk.end(s);
+    }
     for (int i0 = 0; i0 < n; i0 += kNb) {
       const int nb = i0 + kNb < n ? kNb : n - i0;
-      k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
-      LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+      {
+        account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
+        TimedLaunch tk(KC_LUTRSM, s);
+        k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
+        LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+        tk.end(s);
+      }
       if (i0 + nb < n) {
         for (int b = 0; b < nprob; ++b) {
           double* A = pp.ws[b] + offD;
@@ -394,8 +417,13 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
     }
     for (int i0 = ((n - 1) / kNb) * kNb; i0 >= 0; i0 -= kNb) {
       const int nb = i0 + kNb < n ? kNb : n - i0;
-      k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
-      LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+      {
+        account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
+        TimedLaunch tk(KC_LUTRSM, s);
+        k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
+        LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+        tk.end(s);
+      }
       if (i0 > 0) {
         for (int b = 0; b < nprob; ++b) {
           double* A = pp.ws[b] + offD;
@@ -431,6 +459,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
 }
 
 int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r, int ld, int nprob, cudaStream_t s) {
+  TimedLaunch tl_all(KC_LUSOLVE, s);  // the whole solve is one timed region (its GEMMs are class KC_GEMM)
   const int nmax = lu.nmax;
   const size_t nb2 = (size_t)nmax * nmax;
   std::vector<GemmDesc<double>> gd(nprob);
@@ -464,6 +493,7 @@ int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r,
     }
     LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
   }
+  tl_all.end(s);
   return LRFSI_OK;
 }
 

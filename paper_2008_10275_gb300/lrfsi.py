@@ -47,7 +47,9 @@ class lrfsi_kernel_stat(C.Structure):
 
 
 KERNEL_CLASSES = ("gemm_fp64", "spmm_fp64", "gram_fp64", "block_lu", "fe_assembly", "gemm_fp32", "spmm_fp32",
-                  "trunc_small")
+                  "trunc_small", "lu_panel", "lu_trsm", "lu_solve", "trunc_svd")
+# classes that time whole regions containing launches of other classes
+REGION_CLASSES = ("block_lu", "lu_solve")
 
 
 class lrfsi_cheb_stats(C.Structure):
@@ -83,7 +85,9 @@ def load():
         "lrfsi_mlp_forward": [vp, vp, i, vp, vp],
         "lrfsi_mlp_gradients": [vp, vp, vp, i, vp, vp, vp],
         "lrfsi_mlp_train": [vp, vp, vp, i, i, C.c_float, vp, vp],
-        "lrfsi_learned_start": [vp, vp, vp, i, vp, i, i, vp, vp, vp, vp, vp],
+        "lrfsi_learned_fit": [vp, vp, vp, vp, i, vp, vp, i, i, i, C.c_float, vp, i, vp, vp, vp, vp, vp, vp],
+        "lrfsi_learned_start": [vp, vp, vp, vp, i, vp, vp, i, i, vp, vp, vp, vp, vp, vp],
+        "lrfsi_truncation_counters": [vp, i],
         "lrfsi_pod": [vp, vp, i, i, i, vp, i, vp, i, vp, vp],
         "lrfsi_newton_median": [vp, i, vp, vp, vp, d, i, vp, vp, vp],
         "lrfsi_subset_create": [vp, i, vp, vp, vp, vp, vp, C.POINTER(vp), vp],
@@ -304,6 +308,12 @@ def kernel_stats():
     return out
 
 
+def truncation_counters(reset=False):
+    out = np.zeros(6, np.int64)
+    _check(load().lrfsi_truncation_counters(_ptr(out), int(reset)))
+    return dict(zip(("calls", "sweeps_sum", "sweeps_max", "svd_noconv", "breakdowns", "retries"), out.tolist()))
+
+
 def stats_reset():
     _check(load().lrfsi_stats_reset())
 
@@ -368,9 +378,48 @@ def unpack_params(packed, sizes=(2, 128, 128, 64)):
     return out
 
 
-def lrfsi_learned_start(mesh, mlp, Z, B, Phi, ldphi, k, coef_scale, field_scale, offset, X, stream=None):
-    _check(load().lrfsi_learned_start(mesh.h, mlp.h, _ptr(Z), B, _ptr(Phi), ldphi, k, _ptr(coef_scale),
-                                      _ptr(field_scale), _ptr(offset), _ptr(X), _stream(stream)))
+class LearnedStart:
+    """Device state of the learned start: the MLP, Phi, the scales and offset
+    (torch tensors on the mesh's device)."""
+
+    def __init__(self, mesh, k=64, hidden=(128, 128), box=None, seed=0, init=None):
+        import torch
+        from . import inputs
+        self.mesh, self.k = mesh, k
+        self.box = np.array(box if box is not None else (*inputs.MU_RANGE, *inputs.NU_RANGE), np.float64)
+        self.mlp = MLP((2, hidden[0], hidden[1], k))
+        if init is None:
+            init = inputs.mlp_init((2, hidden[0], hidden[1], k), seed)
+        self.mlp.set_params(init)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.Phi = torch.zeros(mesh.M, k, dtype=torch.float64, device=dev)
+        self.cs = torch.zeros(k, dtype=torch.float64, device=dev)
+        self.fs = torch.zeros(mesh.M, dtype=torch.float64, device=dev)
+        self.off = torch.zeros(mesh.M, dtype=torch.float64, device=dev)
+        self.loss = None
+        self.sigma = None
+
+    def fit(self, X, mu, nu, epochs=500, lr=1e-3, stream=None):
+        """X: n x M device tensor of solutions (problem-major)."""
+        n = len(mu)
+        mu = np.ascontiguousarray(mu, np.float64); nu = np.ascontiguousarray(nu, np.float64)
+        loss = np.zeros(1, np.float32); sigma = np.zeros(self.k)
+        _check(load().lrfsi_learned_fit(self.mesh.h, self.mlp.h, _ptr(mu), _ptr(nu), n, _ptr(self.box), _ptr(X),
+                                        X.stride(0), self.k, epochs, C.c_float(lr), _ptr(self.Phi), self.k,
+                                        _ptr(self.cs), _ptr(self.fs), _ptr(self.off), _ptr(loss), _ptr(sigma),
+                                        _stream(stream)))
+        self.loss, self.sigma = float(loss[0]), sigma
+        return self.loss
+
+    def start(self, mu, nu, X, stream=None):
+        """Fill X (B x M device tensor) with the start; returns the fallback flags."""
+        B = len(mu)
+        mu = np.ascontiguousarray(mu, np.float64); nu = np.ascontiguousarray(nu, np.float64)
+        fb = np.zeros(B, np.int32)
+        _check(load().lrfsi_learned_start(self.mesh.h, self.mlp.h, _ptr(mu), _ptr(nu), B, _ptr(self.box),
+                                          _ptr(self.Phi), self.k, self.k, _ptr(self.cs), _ptr(self.fs),
+                                          _ptr(self.off), _ptr(X), _ptr(fb), _stream(stream)))
+        return fb
 
 
 def lrfsi_pod(mesh, X, ldx, n, k, Phi, ldphi, Cm, ldc, stream=None):
