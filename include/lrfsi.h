@@ -117,6 +117,25 @@ int lrfsi_residual_batch(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
                          const double* mu_dev, const double* nu_dev, double* R_dev, int ldr,
                          double* norm2_dev, lrfsi_stream_t stream);
 
+/* lrfsi_residual_batch_noalloc: the same residual block and column norms as
+ * lrfsi_residual_batch, computed without allocating device memory.  (No
+ * counterpart in the paper: an interface for callers that cannot let a library
+ * allocate -- work recorded into a CUDA graph by stream capture, where a
+ * cudaMalloc breaks the capture, and processes whose device memory belongs to
+ * their own pool allocator.)
+ *   R_dev is required (M x m, ldr >= m).  The partial sums of the norms live in
+ *   a library-owned device array of 2^21 doubles (16 MiB, held by every GPU
+ *   that loads the library until the process exits); ceil(M / 256) * m must not
+ *   exceed 2^21, else LRFSI_EINVAL.  Calls share that array: calls that
+ *   overlap on the GPU (e.g. on two streams) race.  Each call overwrites every
+ *   partial it reads, so no clearing is needed between calls.
+ *   The first call on a device looks up the array's device address (set-up
+ *   once per device, with that device current); make that first call before
+ *   any stream capture.  Enqueues work on the stream and does not synchronize. */
+int lrfsi_residual_batch_noalloc(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
+                                 const double* mu_dev, const double* nu_dev, double* R_dev, int ldr,
+                                 double* norm2_dev, lrfsi_stream_t stream);
+
 /* lrfsi_residual: relative residuals of the low-rank approximation
  * X = x~ 1^T + U V^T (Sec. 5.1.2): ||R(X_i; mu_i, nu_i)||_2 / ||R(b_D; mu_i, nu_i)||_2
  * for the m columns.

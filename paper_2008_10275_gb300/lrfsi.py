@@ -78,6 +78,7 @@ def load():
         "lrfsi_assemble_affine": [vp, vp, vp, vp, vp],
         "lrfsi_residual_batch": [vp, vp, i, i, vp, vp, vp, i, vp, vp],
         "lrfsi_residual": [vp, vp, vp, i, vp, i, i, vp, vp, i, vp, vp],
+        "lrfsi_residual_batch_noalloc": [vp, vp, i, i, vp, vp, vp, i, vp, vp],
         "lrfsi_mlp_create": [i, i, i, i, C.POINTER(vp)],
         "lrfsi_mlp_destroy": [vp],
         "lrfsi_mlp_set_params": [vp, vp],
@@ -206,6 +207,12 @@ def lrfsi_assemble_affine(mesh, x, J3=None, R3=None, stream=None):
 def lrfsi_residual_batch(mesh, X, ldx, m, mu, nu, R=None, ldr=0, norm2=None, stream=None):
     _check(load().lrfsi_residual_batch(mesh.h, _ptr(X), ldx, m, _ptr(mu), _ptr(nu), _ptr(R), ldr, _ptr(norm2),
                                        _stream(stream)))
+
+
+def lrfsi_residual_batch_noalloc(mesh, X, ldx, m, mu, nu, R, ldr, norm2=None, stream=None):
+    """lrfsi_residual_batch without device allocation (R is required)."""
+    _check(load().lrfsi_residual_batch_noalloc(mesh.h, _ptr(X), ldx, m, _ptr(mu), _ptr(nu), _ptr(R), ldr,
+                                               _ptr(norm2), _stream(stream)))
 
 
 def lrfsi_residual(mesh, xt, U, ldu, V, ldv, r, mu, nu, m, stream=None):
