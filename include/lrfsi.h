@@ -136,6 +136,25 @@ int lrfsi_residual_batch_noalloc(lrfsi_mesh_h mesh, const double* X_dev, int ldx
                                  const double* mu_dev, const double* nu_dev, double* R_dev, int ldr,
                                  double* norm2_dev, lrfsi_stream_t stream);
 
+/* lrfsi_spmm: the affine operator applied to a tall factor (the SpMM of the
+ * ChebyshevT residual, Sec. 4: F(U V^T) = [J0 U | Jmu' U | Jnu' U] [V | D_mu V | D_nu V]^T):
+ *   Y (M x 3r, row-major, ldy >= 3r) = [J0 U | Jmu' U | Jnu' U]
+ *   J3_dev : operator values, nnz x 3 interleaved on the mesh's CSR pattern
+ *            (as written by lrfsi_assemble_affine)
+ *   U_dev  : M x r row-major (ldu >= r)
+ *   precision 0: all arrays FP64; 1: all arrays FP32 (FP32 accumulation).
+ * The row/column shape of the kernel is chosen per precision and rank by
+ * timing all shapes on first use (see lrfsi_spmm_tuning).  Asynchronous on the
+ * stream except for that first timed use. */
+int lrfsi_spmm(lrfsi_mesh_h mesh, const void* J3_dev, const void* U_dev, int ldu, int r, void* Y_dev, int ldy,
+               int precision, lrfsi_stream_t stream);
+/* The SpMM autotuner's table for (precision 0/1, rank bucket ceil(r / 16)
+ * capped at 8): chosen shape index (-1 before the first use) and the measured
+ * milliseconds of the 9 shapes (lanes per row x columns per lane: 32x1, 32x2,
+ * 16x2, 16x4, 8x4, 8x8 gathering U from L2; 32x2, 16x4, 8x8 gathering from a
+ * shared-memory window of U staged per block of 128 rows; 0 = not applicable). */
+int lrfsi_spmm_tuning(int precision, int bucket, int* variant, float* ms9);
+
 /* lrfsi_residual: relative residuals of the low-rank approximation
  * X = x~ 1^T + U V^T (Sec. 5.1.2): ||R(X_i; mu_i, nu_i)||_2 / ||R(b_D; mu_i, nu_i)||_2
  * for the m columns.
@@ -239,6 +258,21 @@ int lrfsi_subset_step(lrfsi_subset_h sub, const lrfsi_cheb_options* opt, double 
                       int* rank_host, double* relres_host, int* outer_host,
                       lrfsi_stream_t stream);
 
+/* lrfsi_subset_step_init: lrfsi_subset_step from a given start instead of the
+ * first Newton step: X0_k = x~_k 1^T + U0_k V0_k^T (e.g. the learned start,
+ * lrfsi_learned_factors).  The start is truncated to the rank cap (tolerance
+ * tol_sol); every column whose residual norm at X0 is not below that of the
+ * median solution x~_k falls back to x~_k (fallback_host, sum(m_k) ints, 1 for
+ * those columns; may be NULL).  Then the chord corrections of
+ * lrfsi_subset_step run until every column reaches target.
+ *   U0_dev: K stacked M x ldu0 blocks; V0_dev: sum(m_k) x ldv0; r0_host (K):
+ *   columns of the start factors (0 = start at x~_k).  Outputs as
+ *   lrfsi_subset_step. */
+int lrfsi_subset_step_init(lrfsi_subset_h sub, const lrfsi_cheb_options* opt, double target, int max_outer,
+                           const double* U0_dev, int ldu0, const double* V0_dev, int ldv0, const int* r0_host,
+                           double* U_dev, int ldu, double* V_dev, int ldv, int* rank_host, double* relres_host,
+                           int* outer_host, int* fallback_host, lrfsi_stream_t stream);
+
 /* lrfsi_precond_apply: Y_k = P_k^{-1} X_k with the factored mean-based
  * preconditioner of subset k (Sec. 4.2), for r_k columns.
  *   X_dev : K stacked M x ldx blocks (not modified);  Y_dev : K stacked M x ldy
@@ -310,6 +344,20 @@ int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, const double* mu_hos
                         const double* box, const double* Phi_dev, int ldphi, int k, const double* coef_scale_dev,
                         const double* field_scale_dev, const double* offset_dev, double* X_dev,
                         int* fallback_host, lrfsi_stream_t stream);
+
+/* lrfsi_learned_factors: the learned start of K subsets as factors relative
+ * to their median solutions, X0_k - x~_k 1^T = U0_k V0_k^T with
+ *   U0_k = [offset - x~_k | diag(field_scale) Phi]  (M x (k+1), Dirichlet rows 0)
+ *   V0   = [1 | MLP(z) diag(coef_scale)]            (one row per parameter)
+ * sizes_h (K): parameters per subset; mu_host, nu_host: all parameters in
+ * subset order; xt_dev: the K median solutions (K x M, problem-major); U0_dev:
+ * K stacked M x ldu0 blocks; V0_dev: sum(sizes) x ldv0 (ldu0, ldv0 >= k + 1).
+ * Feed to lrfsi_subset_step_init.  Synchronizes the stream. */
+int lrfsi_learned_factors(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, int K, const int* sizes_h, const double* mu_host,
+                          const double* nu_host, const double* box, const double* Phi_dev, int ldphi, int k,
+                          const double* coef_scale_dev, const double* field_scale_dev, const double* offset_dev,
+                          const double* xt_dev, double* U0_dev, int ldu0, double* V0_dev, int ldv0,
+                          lrfsi_stream_t stream);
 
 /* lrfsi_pod: rank-k POD of the snapshot columns X (M x n, ldx): the leading k
  * left singular vectors Phi (M x k, ldphi, orthonormal columns) and the

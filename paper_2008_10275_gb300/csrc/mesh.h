@@ -45,7 +45,15 @@ struct lrfsi_mesh_s {
   lrfsi::DevBuf<double> bD;
   lrfsi::DevBuf<long long> dense_off;
   lrfsi::DevBuf<long long> slab_off;
+  // SpMM windows: for row block b (kSpmmRowBlock rows) the column range
+  // [win[2b], win[2b+1]) its nonzeros touch; winmax = the widest window
+  lrfsi::DevBuf<int> spmm_win;
+  int spmm_winmax = 0;
 };
+
+namespace lrfsi {
+constexpr int kSpmmRowBlock = 128;
+}
 
 namespace lrfsi {
 int build_mesh(const lrfsi_problem& prob, MeshHost& h);

@@ -256,6 +256,29 @@ __global__ void k_start_fallback(const double* __restrict__ n2, const double* __
   if (i == 0) flag[b] = fb ? 1 : 0;
 }
 
+// Factors of the learned start relative to the median solution of subset k:
+// X0 - x~_k 1^T = U0 V0^T with U0 = [offset - x~_k | diag(fs) Phi] (M x (k+1))
+// and V0 = [1 | C diag(cs)] (m x (k+1)); Dirichlet rows of U0 are zero.
+__global__ void k_learned_u0(const double* __restrict__ Phi, int ldphi, int k, const double* __restrict__ fs,
+                             const double* __restrict__ off, const double* __restrict__ xt,
+                             const char* __restrict__ ident, long M, double* __restrict__ U0, int ldu0) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= M * (k + 1)) return;
+  const long i = e / (k + 1);
+  const int l = (int)(e % (k + 1));
+  double v = 0.0;
+  if (!ident[i]) v = l == 0 ? off[i] - xt[i] : fs[i] * Phi[i * ldphi + l - 1];
+  U0[i * ldu0 + l] = v;
+}
+
+__global__ void k_learned_v0(const float* __restrict__ C, int k, const double* __restrict__ cs, int B,
+                             double* __restrict__ V0, int ldv0) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)B * (k + 1)) return;
+  const int b = (int)(e / (k + 1)), l = (int)(e % (k + 1));
+  V0[(size_t)b * ldv0 + l] = l == 0 ? 1.0 : cs[l - 1] * (double)C[(size_t)b * k + l - 1];
+}
+
 }  // namespace lrfsi
 
 struct lrfsi_mlp_s {
@@ -502,6 +525,45 @@ int lrfsi_learned_start(lrfsi_mesh_h mesh, lrfsi_mlp_h h, const double* mu_h, co
   k_start_fallback<<<ceil_div(M * B, 256), 256, 0, s>>>(n2.p, n2D.p, mesh->bD.p, M, B, X, flag.p);
   LRFSI_TRY(check_launch("k_start_fallback"));
   if (fallback_host) LRFSI_CUDA(cudaMemcpyAsync(fallback_host, flag.p, sizeof(int) * B, cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+int lrfsi_learned_factors(lrfsi_mesh_h mesh, lrfsi_mlp_h h, int K, const int* sizes_h, const double* mu_h,
+                          const double* nu_h, const double* box, const double* Phi, int ldphi, int k,
+                          const double* coef_scale, const double* field_scale, const double* offset,
+                          const double* xt, double* U0, int ldu0, double* V0, int ldv0, lrfsi_stream_t stream) {
+  if (!mesh || !h || K < 1 || !sizes_h || !mu_h || !nu_h || !box || !Phi || !coef_scale || !field_scale || !offset ||
+      !xt || !U0 || !V0 || k < 1 || ldphi < k || ldu0 < k + 1 || ldv0 < k + 1 || h->d.n[0] != 2 ||
+      h->d.n[kMlpLayers] != k || !(box[1] > box[0]) || !(box[3] > box[2]))
+    return fail(LRFSI_EINVAL, "lrfsi_learned_factors: bad argument");
+  int B = 0;
+  for (int q = 0; q < K; ++q) {
+    if (sizes_h[q] < 1) return fail(LRFSI_EINVAL, "lrfsi_learned_factors: empty subset");
+    B += sizes_h[q];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const long M = mesh->h.M;
+  DevBuf<float> Z, C;
+  DevBuf<char> ident;
+  DevBuf<double> mu, nu;
+  LRFSI_TRY(Z.alloc((size_t)2 * B));
+  LRFSI_TRY(C.alloc((size_t)B * k));
+  std::vector<double> muv(mu_h, mu_h + B), nuv(nu_h, nu_h + B);
+  LRFSI_TRY(mu.upload(muv, s));
+  LRFSI_TRY(nu.upload(nuv, s));
+  std::vector<char> id(mesh->h.ident.begin(), mesh->h.ident.end());
+  LRFSI_TRY(ident.upload(id, s));
+  k_scale_params<<<ceil_div(B, 128), 128, 0, s>>>(mu.p, nu.p, B, box[0], box[1], box[2], box[3], Z.p);
+  LRFSI_TRY(check_launch("k_scale_params"));
+  LRFSI_TRY(mlp_forward_impl(h, Z.p, B, C.p, s, false));
+  k_learned_v0<<<ceil_div((long)B * (k + 1), 256), 256, 0, s>>>(C.p, k, coef_scale, B, V0, ldv0);
+  LRFSI_TRY(check_launch("k_learned_v0"));
+  for (int q = 0; q < K; ++q) {
+    k_learned_u0<<<ceil_div(M * (k + 1), 256), 256, 0, s>>>(Phi, ldphi, k, field_scale, offset, xt + (size_t)q * M,
+                                                            ident.p, M, U0 + (size_t)q * M * ldu0, ldu0);
+    LRFSI_TRY(check_launch("k_learned_u0"));
+  }
   LRFSI_CUDA(cudaStreamSynchronize(s));
   return LRFSI_OK;
 }

@@ -3,6 +3,8 @@
 // the truncated preconditioned Chebyshev iteration (Sec. 3.4, Sec. 4.2,
 // Algorithm 1).
 #include <algorithm>
+#include <climits>
+#include <cstdint>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -283,6 +285,24 @@ int lrfsi_mesh_create(const lrfsi_problem* prob, lrfsi_mesh_h* out) {
   if (st == LRFSI_OK) {
     std::vector<long long> so(m->h.slab_off.begin(), m->h.slab_off.end());
     st = m->slab_off.upload(so);
+  }
+  if (st == LRFSI_OK) {  // SpMM column windows of the row blocks
+    const long M = m->h.M;
+    const long nb = (M + kSpmmRowBlock - 1) / kSpmmRowBlock;
+    std::vector<int> win(2 * nb);
+    for (long b = 0; b < nb; ++b) {
+      int lo = INT32_MAX, hi = -1;
+      for (long r = b * kSpmmRowBlock; r < std::min(M, (b + 1) * kSpmmRowBlock); ++r)
+        for (int q = m->h.rowptr[r]; q < m->h.rowptr[r + 1]; ++q) {
+          lo = std::min(lo, m->h.colidx[q]);
+          hi = std::max(hi, m->h.colidx[q]);
+        }
+      if (hi < 0) { lo = 0; hi = -1; }
+      win[2 * b] = lo;
+      win[2 * b + 1] = hi + 1;
+      m->spmm_winmax = std::max(m->spmm_winmax, hi + 1 - lo);
+    }
+    st = m->spmm_win.upload(win);
   }
   if (st == LRFSI_OK) {
     cudaError_t e = cudaDeviceSynchronize();
@@ -573,6 +593,7 @@ struct lrfsi_subset_s {
   std::vector<double> mu_h, nu_h, mubar, nubar;
   DevBuf<double> mu, nu, xt, J3, R3;
   DevBuf<double> rsc, csc;  // K x M equilibration scales (rows, columns)
+  DevBuf<double> cinv;      // K x M reciprocal column scales (allocated on first use)
   DevBuf<float> J3f, USf, Yf, Xf, Vf;  // FP32 operator copies and inner-residual buffers (mixed mode)
   BlockLU lu;
   DevBuf<double> Xcat, Q1, Q2, US, UD, UR, UZ, UB, Ytmp, UC;  // K x M x ld
@@ -590,12 +611,13 @@ struct lrfsi_subset_s {
 
 namespace lrfsi {
 
-// T([X | ...], [V | ...]) for the listed subsets.  Inputs in Xcat (ld ldP) and
-// Vcat (ld ldP) with p[k] columns; outputs U (tall, ld ldR) and V (ld ldR).
 // Truncation counters (process-wide): calls, SVD sweeps (sum, max), SVDs that
 // hit the sweep limit, Cholesky-QR breakdowns, retries.
 static std::atomic<long long> g_tr_calls{0}, g_tr_sweeps{0}, g_tr_maxsweeps{0}, g_tr_noconv{0}, g_tr_breakdown{0},
     g_tr_retry{0};
+
+// T([X | ...], [V | ...]) for the listed subsets.  Inputs in Xcat (ld ldP) and
+// Vcat (ld ldP) with p[k] columns; outputs U (tall, ld ldR) and V (ld ldR).
 
 static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
                          const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
@@ -786,6 +808,35 @@ static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const 
 
 }  // namespace lrfsi
 
+extern "C" int lrfsi_spmm(lrfsi_mesh_h m, const void* J3, const void* U, int ldu, int r, void* Y, int ldy,
+                          int precision, lrfsi_stream_t stream) {
+  if (!m || !J3 || !U || !Y || r < 0 || ldu < r || ldy < 3 * r || (precision != 0 && precision != 1))
+    return fail(LRFSI_EINVAL, "lrfsi_spmm: bad argument (ldu >= r, ldy >= 3 r, precision 0 or 1)");
+  if (r == 0) return LRFSI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (precision == 0) {
+    SpmmDesc<double> d;
+    d.J3 = (const double*)J3; d.U = (const double*)U; d.ldu = ldu; d.r = r; d.Y = (double*)Y; d.ldy = ldy;
+    d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+    d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
+    d.a1 = d.a2 = 0.0;
+    return spmm_batched<double>(m, &d, 1, s);
+  }
+  SpmmDesc<float> d;
+  d.J3 = (const float*)J3; d.U = (const float*)U; d.ldu = ldu; d.r = r; d.Y = (float*)Y; d.ldy = ldy;
+  d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+  d.sc[0] = d.sc[1] = d.sc[2] = 1.0f;
+  d.a1 = d.a2 = 0.0f;
+  return spmm_batched<float>(m, &d, 1, s);
+}
+
+extern "C" int lrfsi_spmm_tuning(int precision, int bucket, int* variant, float* ms9) {
+  if (!variant || !ms9) return fail(LRFSI_EINVAL, "lrfsi_spmm_tuning: null argument");
+  if (spmm_autotune_table(precision, bucket, variant, ms9) != LRFSI_OK)
+    return fail(LRFSI_EINVAL, "lrfsi_spmm_tuning: precision 0/1, bucket 0..8");
+  return LRFSI_OK;
+}
+
 extern "C" int lrfsi_truncation_counters(int64_t* out6, int reset) {
   if (!out6) return fail(LRFSI_EINVAL, "lrfsi_truncation_counters: null argument");
   out6[0] = g_tr_calls.load();
@@ -808,7 +859,7 @@ extern "C" int lrfsi_subset_destroy(lrfsi_subset_h S) {
 extern "C" size_t lrfsi_subset_bytes(lrfsi_subset_h S) {
   if (!S) return 0;
   size_t b = 0;
-  for (DevBuf<double>* p : {&S->mu, &S->nu, &S->xt, &S->J3, &S->R3, &S->rsc, &S->csc, &S->Xcat, &S->Q1, &S->Q2, &S->US, &S->UD, &S->UR, &S->UZ,
+  for (DevBuf<double>* p : {&S->mu, &S->nu, &S->xt, &S->J3, &S->R3, &S->rsc, &S->csc, &S->cinv, &S->Xcat, &S->Q1, &S->Q2, &S->US, &S->UD, &S->UR, &S->UZ,
                             &S->UB, &S->Ytmp, &S->UC, &S->Vcat, &S->VS, &S->VD, &S->VR, &S->VB, &S->VC, &S->G, &S->G2,
                             &S->T1, &S->T2, &S->swork, &S->sv, &S->frob2, &S->gramwork, &S->Xd, &S->rc.R,
                             &S->rc.norm2, &S->rc.norm2_bD, &S->rc.work})
@@ -1228,49 +1279,31 @@ extern "C" int lrfsi_chebyshevT(lrfsi_subset_h S, const double* UB, int lduB, co
   return LRFSI_OK;
 }
 
-extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt, double target, int max_outer,
-                                 double* U, int ldu, double* V, int ldv, int* rank_h, double* relres_h, int* outer_h,
-                                 lrfsi_stream_t stream) {
-  if (!S || !U || !V || !rank_h || max_outer < 0) return fail(LRFSI_EINVAL, "lrfsi_subset_step: bad argument");
-  LRFSI_TRY(check_opts(opt));
-  cudaStream_t s = (cudaStream_t)stream;
+__global__ void k_recip(const double* __restrict__ x, long n, double* __restrict__ y) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = x[e] != 0.0 ? 1.0 / x[e] : 0.0;
+}
+
+// rows i of V (ld) with flag[i] != 0 set to zero (columns 0..r-1)
+__global__ void k_zero_flagged_rows(double* __restrict__ V, int ld, int r, const int* __restrict__ flag, int n) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)n * r) return;
+  const int i = (int)(e / r), j = (int)(e % r);
+  if (flag[i]) V[(size_t)i * ld + j] = 0.0;
+}
+
+// Nonlinear residuals of X = xt 1^T + diag(c) U_C V_C^T (UC/VC, ranks rC) and
+// chord corrections (right-hand side -R(X_i) per column, operators and
+// preconditioner kept at xt) until every column's relative residual is <=
+// target or max_outer corrections were made (LRFSI_ENOCONV).  rel receives the
+// last relative residuals, outer the corrections per subset.
+static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, double target, int max_outer,
+                             std::vector<int>& rC, std::vector<int>& outer, std::vector<double>& rel, cudaStream_t s) {
   const int K = S->K, ldR = S->ldR, ldP = S->ldP;
   const long M = S->M;
-  for (int k = 0; k < K; ++k)
-    if (ldu < S->cap[k] || ldv < S->cap[k]) return fail(LRFSI_EINVAL, "lrfsi_subset_step: ldu/ldv < rank cap");
-  // B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T), dense M x m_k in UB
   std::vector<CopyDesc> cd;
-  std::vector<GemmDesc<double>> gb;
-  std::vector<int> act, rB(K, 3);
-  for (int k = 0; k < K; ++k) {
-    act.push_back(k);
-    double* vb = S->vside(S->VB, k, ldR);
-    cd.push_back(CopyDesc{nullptr, 0, vb, ldR, S->m[k], 1, 1, nullptr, -1.0});
-    cd.push_back(CopyDesc{nullptr, 0, vb + 1, ldR, S->m[k], 1, 1, S->mu.p + S->off[k], -1.0});
-    cd.push_back(CopyDesc{nullptr, 0, vb + 2, ldR, S->m[k], 1, 1, S->nu.p + S->off[k], -1.0});
-    gb.push_back(GemmDesc<double>{(int)M, S->m[k], 3, S->R3.p + (size_t)k * 3 * M, 3, 1, vb, 1, ldR,
-                                  S->tall(S->UB, k, ldR), ldR, 1, 1.0, 0.0});
-  }
-  LRFSI_TRY(copy_batched(cd, s));
-  LRFSI_TRY(gemm_grouped<double>(gb.data(), (int)gb.size(), s));
-  cd.clear();
-  for (int k = 0; k < K; ++k)
-    cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, S->tall(S->UB, k, ldR), ldR, M, S->m[k], 0,
-                          S->rsc.p + (size_t)k * M, 1.0});
-  LRFSI_TRY(copy_batched(cd, s));
   std::vector<int> rS;
   std::vector<lrfsi_cheb_stats> st;
-  LRFSI_TRY(cheb_run(S, *opt, act, rB, rS, st, s));
-  // keep the accumulated update in UC/VC
-  std::vector<int> rC = rS;
-  cd.clear();
-  for (int k = 0; k < K; ++k) {
-    cd.push_back(CopyDesc{S->tall(S->US, k, ldR), ldR, S->tall(S->UC, k, ldR), ldR, M, rC[k], 0, nullptr, 1.0});
-    cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, S->vside(S->VC, k, ldR), ldR, S->m[k], rC[k], 0, nullptr, 1.0});
-  }
-  LRFSI_TRY(copy_batched(cd, s));
-  std::vector<int> outer(K, 0);
-  std::vector<double> rel(S->mtot, 0.0);
   int status = LRFSI_OK;
   for (int it = 0;; ++it) {
     // X = xt 1^T + diag(c) U_C V_C^T (dense columns, M x mtot) and its nonlinear residual
@@ -1318,7 +1351,7 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
       rBc[k] = m;
     }
     LRFSI_TRY(copy_batched(cd, s));
-    LRFSI_TRY(cheb_run(S, *opt, need, rBc, rS, st, s));
+    LRFSI_TRY(cheb_run(S, o, need, rBc, rS, st, s));
     // accumulate: C <- T([U_C | U_S], [V_C | V_S])
     cd.clear();
     std::vector<int> p(K, 0);
@@ -1337,10 +1370,58 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
     LRFSI_TRY(copy_batched(cd, s));
     std::vector<int> rk;
     std::vector<double> f2;
-    const double tol_sol = opt->tol_sol > 0 ? opt->tol_sol : 1e-6 * opt->tol;
+    const double tol_sol = o.tol_sol > 0 ? o.tol_sol : 1e-6 * o.tol;
     LRFSI_TRY(truncate_batch(S, need, p, tol_sol, S->cap, Uo, Vo, rk, f2, s));
     for (int k : need) rC[k] = rk[k];
   }
+  return status;
+}
+
+extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt, double target, int max_outer,
+                                 double* U, int ldu, double* V, int ldv, int* rank_h, double* relres_h, int* outer_h,
+                                 lrfsi_stream_t stream) {
+  if (!S || !U || !V || !rank_h || max_outer < 0) return fail(LRFSI_EINVAL, "lrfsi_subset_step: bad argument");
+  LRFSI_TRY(check_opts(opt));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldR = S->ldR, ldP = S->ldP;
+  const long M = S->M;
+  for (int k = 0; k < K; ++k)
+    if (ldu < S->cap[k] || ldv < S->cap[k]) return fail(LRFSI_EINVAL, "lrfsi_subset_step: ldu/ldv < rank cap");
+  // B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T), dense M x m_k in UB
+  std::vector<CopyDesc> cd;
+  std::vector<GemmDesc<double>> gb;
+  std::vector<int> act, rB(K, 3);
+  for (int k = 0; k < K; ++k) {
+    act.push_back(k);
+    double* vb = S->vside(S->VB, k, ldR);
+    cd.push_back(CopyDesc{nullptr, 0, vb, ldR, S->m[k], 1, 1, nullptr, -1.0});
+    cd.push_back(CopyDesc{nullptr, 0, vb + 1, ldR, S->m[k], 1, 1, S->mu.p + S->off[k], -1.0});
+    cd.push_back(CopyDesc{nullptr, 0, vb + 2, ldR, S->m[k], 1, 1, S->nu.p + S->off[k], -1.0});
+    gb.push_back(GemmDesc<double>{(int)M, S->m[k], 3, S->R3.p + (size_t)k * 3 * M, 3, 1, vb, 1, ldR,
+                                  S->tall(S->UB, k, ldR), ldR, 1, 1.0, 0.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_TRY(gemm_grouped<double>(gb.data(), (int)gb.size(), s));
+  cd.clear();
+  for (int k = 0; k < K; ++k)
+    cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, S->tall(S->UB, k, ldR), ldR, M, S->m[k], 0,
+                          S->rsc.p + (size_t)k * M, 1.0});
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<int> rS;
+  std::vector<lrfsi_cheb_stats> st;
+  LRFSI_TRY(cheb_run(S, *opt, act, rB, rS, st, s));
+  // keep the accumulated update in UC/VC
+  std::vector<int> rC = rS;
+  cd.clear();
+  for (int k = 0; k < K; ++k) {
+    cd.push_back(CopyDesc{S->tall(S->US, k, ldR), ldR, S->tall(S->UC, k, ldR), ldR, M, rC[k], 0, nullptr, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, S->vside(S->VC, k, ldR), ldR, S->m[k], rC[k], 0, nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<int> outer(K, 0);
+  std::vector<double> rel(S->mtot, 0.0);
+  const int status = outer_corrections(S, *opt, target, max_outer, rC, outer, rel, s);
+  if (status != LRFSI_OK && status != LRFSI_ENOCONV) return status;
   cd.clear();
   for (int k = 0; k < K; ++k) {
     rank_h[k] = rC[k];
@@ -1353,6 +1434,119 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
   LRFSI_CUDA(cudaStreamSynchronize(s));
   if (relres_h) std::memcpy(relres_h, rel.data(), sizeof(double) * S->mtot);
   if (status != LRFSI_OK) return fail(status, "lrfsi_subset_step: target not reached within max_outer corrections");
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options* opt, double target,
+                                      int max_outer, const double* U0, int ldu0, const double* V0, int ldv0,
+                                      const int* r0_h, double* U, int ldu, double* V, int ldv, int* rank_h,
+                                      double* relres_h, int* outer_h, int* fallback_h, lrfsi_stream_t stream) {
+  if (!S || !U0 || !V0 || !r0_h || !U || !V || !rank_h || max_outer < 0)
+    return fail(LRFSI_EINVAL, "lrfsi_subset_step_init: bad argument");
+  LRFSI_TRY(check_opts(opt));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldR = S->ldR, ldP = S->ldP;
+  const long M = S->M;
+  for (int k = 0; k < K; ++k) {
+    if (ldu < S->cap[k] || ldv < S->cap[k]) return fail(LRFSI_EINVAL, "lrfsi_subset_step_init: ldu/ldv < rank cap");
+    if (r0_h[k] < 0 || r0_h[k] > ldu0 || r0_h[k] > ldv0 || r0_h[k] > ldP)
+      return fail(LRFSI_EINVAL, "lrfsi_subset_step_init: initial rank r0_k out of range");
+  }
+  if (!S->cinv.p) {
+    LRFSI_TRY(S->cinv.alloc((size_t)K * M));
+    k_recip<<<ceil_div((long)K * M, 256), 256, 0, s>>>(S->csc.p, (long)K * M, S->cinv.p);
+    LRFSI_TRY(check_launch("k_recip"));
+  }
+  // C = T(diag(c)^{-1} U0, V0): the start in the scaled coordinates, at most cap_k
+  std::vector<CopyDesc> cd;
+  std::vector<int> act, p(K, 0), rC(K, 0);
+  std::vector<double*> Uo(K), Vo(K);
+  for (int k = 0; k < K; ++k) {
+    if (r0_h[k] == 0) continue;
+    act.push_back(k);
+    cd.push_back(CopyDesc{U0 + (size_t)k * M * ldu0, ldu0, S->tall(S->Xcat, k, ldP), ldP, M, r0_h[k], 0,
+                          S->cinv.p + (size_t)k * M, 1.0});
+    cd.push_back(CopyDesc{V0 + (size_t)S->off[k] * ldv0, ldv0, S->vside(S->Vcat, k, ldP), ldP, S->m[k], r0_h[k], 0,
+                          nullptr, 1.0});
+    p[k] = r0_h[k];
+    Uo[k] = S->tall(S->UC, k, ldR);
+    Vo[k] = S->vside(S->VC, k, ldR);
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  if (!act.empty()) {
+    std::vector<int> rk;
+    std::vector<double> f2;
+    const double tol_sol = opt->tol_sol > 0 ? opt->tol_sol : 1e-6 * opt->tol;
+    LRFSI_TRY(truncate_batch(S, act, p, tol_sol, S->cap, Uo, Vo, rk, f2, s));
+    for (int k : act) rC[k] = rk[k];
+  }
+  // fallback: columns whose start does not cut the residual of the median
+  // solution x~_k restart from x~_k (their row of V_C is zeroed)
+  std::vector<int> fb(S->mtot, 0);
+  {
+    std::vector<GemmDesc<double>> gm;
+    for (int k = 0; k < K; ++k) {
+      if (rC[k] > 0)
+        gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
+                                      S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
+      else
+        LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
+    }
+    if (!gm.empty()) LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+    for (int k = 0; k < K; ++k) {
+      k_affine_cols<<<ceil_div(M * S->m[k], 256), 256, 0, s>>>(S->Xd.p, S->mtot, S->off[k], S->m[k],
+                                                              S->xt.p + (size_t)k * M, S->csc.p + (size_t)k * M, M);
+      LRFSI_TRY(check_launch("k_affine_cols"));
+    }
+    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->rc.R.p, S->mtot, s));
+    LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
+    std::vector<double> a(S->mtot), b(S->mtot);
+    LRFSI_CUDA(cudaMemcpyAsync(a.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
+    // the median solutions themselves: Xd columns = x~_k
+    LRFSI_CUDA(cudaMemsetAsync(S->Xd.p, 0, sizeof(double) * (size_t)M * S->mtot, s));
+    for (int k = 0; k < K; ++k) {
+      k_affine_cols<<<ceil_div(M * S->m[k], 256), 256, 0, s>>>(S->Xd.p, S->mtot, S->off[k], S->m[k],
+                                                              S->xt.p + (size_t)k * M, S->csc.p + (size_t)k * M, M);
+      LRFSI_TRY(check_launch("k_affine_cols"));
+    }
+    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->rc.R.p, S->mtot, s));
+    LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
+    LRFSI_CUDA(cudaMemcpyAsync(b.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int i = 0; i < S->mtot; ++i) {
+      fb[i] = !(a[i] < b[i]);
+      any = any || fb[i];
+    }
+    if (any) {
+      DevBuf<int> fdev;
+      LRFSI_TRY(fdev.upload(fb, s));
+      for (int k = 0; k < K; ++k) {
+        if (rC[k] <= 0) continue;
+        k_zero_flagged_rows<<<ceil_div((long)S->m[k] * rC[k], 256), 256, 0, s>>>(
+            S->vside(S->VC, k, ldR), ldR, rC[k], fdev.p + S->off[k], S->m[k]);
+        LRFSI_TRY(check_launch("k_zero_flagged_rows"));
+      }
+      LRFSI_CUDA(cudaStreamSynchronize(s));
+    }
+  }
+  std::vector<int> outer(K, 0);
+  std::vector<double> rel(S->mtot, 0.0);
+  const int status = outer_corrections(S, *opt, target, max_outer, rC, outer, rel, s);
+  if (status != LRFSI_OK && status != LRFSI_ENOCONV) return status;
+  cd.clear();
+  for (int k = 0; k < K; ++k) {
+    rank_h[k] = rC[k];
+    if (outer_h) outer_h[k] = outer[k];
+    cd.push_back(CopyDesc{S->tall(S->UC, k, ldR), ldR, U + (size_t)k * M * ldu, ldu, M, rC[k], 0,
+                          S->csc.p + (size_t)k * M, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VC, k, ldR), ldR, V + (size_t)S->off[k] * ldv, ldv, S->m[k], rC[k], 0, nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  if (relres_h) std::memcpy(relres_h, rel.data(), sizeof(double) * S->mtot);
+  if (fallback_h) std::memcpy(fallback_h, fb.data(), sizeof(int) * S->mtot);
+  if (status != LRFSI_OK) return fail(status, "lrfsi_subset_step_init: target not reached within max_outer corrections");
   return LRFSI_OK;
 }
 

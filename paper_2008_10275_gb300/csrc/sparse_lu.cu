@@ -9,67 +9,274 @@
 // elimination).  Pivoting is partial pivoting inside each diagonal Schur
 // block; its pivot threshold is reported through the status word.
 #include <cmath>
+#include <mutex>
 
 #include "sparse_lu.h"
 
 namespace lrfsi {
 
 // ---------------------------------------------------------------------------
-// SpMM: one warp per row, lanes over the columns of U
+// SpMM: LPR lanes per row (256 / LPR rows per CTA), each lane CPL columns of
+// U per pass; the (LPR, CPL) shape per precision and rank is picked by timing
+// (spmm_variant below)
 // ---------------------------------------------------------------------------
 template <class T>
 struct SpmmBatch {
   SpmmDesc<T> d[kMaxGemmDescs];
 };
 
-template <class T, int CPL>
+template <class T, int LPR, int CPL>
 __global__ void __launch_bounds__(256) k_spmm(SpmmBatch<T> sb, const int* __restrict__ rowptr,
                                                const int* __restrict__ colidx, long M) {
+  // The LPR lanes of a row load up to LPR nonzeros (index and the three
+  // values) with one coalesced access and pass them around with shuffles, so
+  // that the gathers of U rows for several nonzeros are in flight at once.
+  // Trip counts are made uniform over the warp (rows of one warp differ in
+  // length); lanes past their row's end only skip the arithmetic.
   const SpmmDesc<T>& dref = sb.d[blockIdx.y];
-  const long row = (long)blockIdx.x * 8 + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= M) return;
+  constexpr int RPB = 256 / LPR;
+  const long row0 = (long)blockIdx.x * RPB + (threadIdx.x / LPR);
+  const int lane = threadIdx.x % LPR;
+  const bool valid = row0 < M;
+  const long row = valid ? row0 : M - 1;
   const int r = dref.r;
   const T* __restrict__ U = dref.U;
   const T* __restrict__ J3 = dref.J3;
   const int ldu = dref.ldu;
   const bool combined = dref.o[1] < 0;
   const T a1 = dref.a1, a2 = dref.a2;
-  const int k0 = rowptr[row], k1 = rowptr[row + 1];
-  for (int c0 = 0; c0 < r; c0 += 32 * CPL) {
+  const int k0 = rowptr[row], k1 = valid ? rowptr[row + 1] : k0;
+  int nch = (k1 - k0 + LPR - 1) / LPR;
+#pragma unroll
+  for (int o = LPR; o < 32; o <<= 1) nch = max(nch, __shfl_xor_sync(0xffffffffu, nch, o));
+  for (int c0 = 0; c0 < r; c0 += LPR * CPL) {
     T acc0[CPL], acc1[CPL], acc2[CPL];
 #pragma unroll
     for (int q = 0; q < CPL; ++q) acc0[q] = acc1[q] = acc2[q] = T(0);
-    for (int k = k0; k < k1; ++k) {
-      const int col = colidx[k];
-      const T v0 = J3[3 * (size_t)k], v1 = J3[3 * (size_t)k + 1], v2 = J3[3 * (size_t)k + 2];
-      const T* ur = U + (size_t)col * ldu;
+    for (int ch = 0; ch < nch; ++ch) {
+      const int kb = k0 + ch * LPR, kk = kb + lane;
+      const bool have = kk < k1;
+      const int mc = have ? colidx[kk] : 0;
+      const T w0 = have ? J3[3 * (size_t)kk] : T(0);
+      const T w1 = have ? J3[3 * (size_t)kk + 1] : T(0);
+      const T w2 = have ? J3[3 * (size_t)kk + 2] : T(0);
+      const int nk = k1 - kb;
+#pragma unroll 8
+      for (int t = 0; t < LPR; ++t) {
+        const int col = __shfl_sync(0xffffffffu, mc, t, LPR);
+        const T v0 = __shfl_sync(0xffffffffu, w0, t, LPR);
+        const T v1 = __shfl_sync(0xffffffffu, w1, t, LPR);
+        const T v2 = __shfl_sync(0xffffffffu, w2, t, LPR);
+        if (t < nk) {
+          const T* ur = U + (size_t)col * ldu;
 #pragma unroll
-      for (int q = 0; q < CPL; ++q) {
-        const int j = c0 + lane + 32 * q;
-        if (j < r) {
-          const T u = ur[j];
-          if (combined) {
-            acc0[q] += (v0 + a1 * v1 + a2 * v2) * u;
-          } else {
-            acc0[q] += v0 * u; acc1[q] += v1 * u; acc2[q] += v2 * u;
+          for (int q = 0; q < CPL; ++q) {
+            const int j = c0 + lane + LPR * q;
+            if (j < r) {
+              const T u = ur[j];
+              if (combined) {
+                acc0[q] += (v0 + a1 * v1 + a2 * v2) * u;
+              } else {
+                acc0[q] += v0 * u; acc1[q] += v1 * u; acc2[q] += v2 * u;
+              }
+            }
           }
         }
       }
     }
-    T* yr = dref.Y + (size_t)row * dref.ldy;
+    if (valid) {
+      T* yr = dref.Y + (size_t)row * dref.ldy;
 #pragma unroll
-    for (int q = 0; q < CPL; ++q) {
-      const int j = c0 + lane + 32 * q;
-      if (j < r) {
-        yr[dref.o[0] + j] = dref.sc[0] * acc0[q];
-        if (!combined) {
-          yr[dref.o[1] + j] = dref.sc[1] * acc1[q];
-          yr[dref.o[2] + j] = dref.sc[2] * acc2[q];
+      for (int q = 0; q < CPL; ++q) {
+        const int j = c0 + lane + LPR * q;
+        if (j < r) {
+          yr[dref.o[0] + j] = dref.sc[0] * acc0[q];
+          if (!combined) {
+            yr[dref.o[1] + j] = dref.sc[1] * acc1[q];
+            yr[dref.o[2] + j] = dref.sc[2] * acc2[q];
+          }
         }
       }
     }
   }
+}
+
+// Windowed SpMM: CTA b takes rows [128 b, 128 b + 128) and first stages the
+// rows of U its nonzeros touch (the column window of the row block; the slab
+// ordering keeps it to about three slabs) in shared memory, in chunks of rc
+// columns; the gathers then read shared memory.  LPR lanes per row, CPL
+// columns per lane per pass.
+template <class T, int LPR, int CPL>
+__global__ void __launch_bounds__(256) k_spmm_win(SpmmBatch<T> sb, const int* __restrict__ rowptr,
+                                                   const int* __restrict__ colidx, const int* __restrict__ win,
+                                                   long M, int rc) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  T* Us = reinterpret_cast<T*>(smraw);
+  const SpmmDesc<T>& dref = sb.d[blockIdx.y];
+  const long rb0 = (long)blockIdx.x * kSpmmRowBlock;
+  const int w0 = win[2 * blockIdx.x], w1 = win[2 * blockIdx.x + 1];
+  const int wl = w1 - w0;
+  const int r = dref.r, ldu = dref.ldu;
+  const T* __restrict__ U = dref.U;
+  const T* __restrict__ J3 = dref.J3;
+  const bool combined = dref.o[1] < 0;
+  const T a1 = dref.a1, a2 = dref.a2;
+  const int lane = threadIdx.x % LPR, grp = threadIdx.x / LPR;
+  constexpr int GROUPS = 256 / LPR;
+  for (int cb = 0; cb < r; cb += rc) {
+    const int nc = r - cb < rc ? r - cb : rc;
+    __syncthreads();  // the previous chunk's gathers are done
+    for (long e = threadIdx.x; e < (long)wl * nc; e += 256) {
+      const int i = (int)(e / nc), c = (int)(e % nc);
+      Us[e] = U[(size_t)(w0 + i) * ldu + cb + c];
+    }
+    __syncthreads();
+    for (int rr = grp; rr < kSpmmRowBlock; rr += GROUPS) {
+      const long row = rb0 + rr;
+      if (row >= M) break;
+      const int k0 = rowptr[row], k1 = rowptr[row + 1];
+      for (int c0 = 0; c0 < nc; c0 += LPR * CPL) {
+        T acc0[CPL], acc1[CPL], acc2[CPL];
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) acc0[q] = acc1[q] = acc2[q] = T(0);
+        for (int k = k0; k < k1; ++k) {
+          const T* ur = Us + (size_t)(colidx[k] - w0) * nc;
+          const T v0 = J3[3 * (size_t)k], v1 = J3[3 * (size_t)k + 1], v2 = J3[3 * (size_t)k + 2];
+#pragma unroll
+          for (int q = 0; q < CPL; ++q) {
+            const int j = c0 + lane + LPR * q;
+            if (j < nc) {
+              const T u = ur[j];
+              if (combined) {
+                acc0[q] += (v0 + a1 * v1 + a2 * v2) * u;
+              } else {
+                acc0[q] += v0 * u; acc1[q] += v1 * u; acc2[q] += v2 * u;
+              }
+            }
+          }
+        }
+        T* yr = dref.Y + (size_t)row * dref.ldy + cb;
+#pragma unroll
+        for (int q = 0; q < CPL; ++q) {
+          const int j = c0 + lane + LPR * q;
+          if (j < nc) {
+            yr[dref.o[0] + j] = dref.sc[0] * acc0[q];
+            if (!combined) {
+              yr[dref.o[1] + j] = dref.sc[1] * acc1[q];
+              yr[dref.o[2] + j] = dref.sc[2] * acc2[q];
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// The candidate shapes: lanes per row x columns per lane, U gathered from
+// L2 (0-5) or from the shared-memory window (6-8).
+constexpr int kSpmmVariants = 9;
+constexpr size_t kSpmmWinSmem = 200 * 1024;
+template <class T>
+static int spmm_window_cols(const lrfsi_mesh_s* m, int rmax) {
+  const long per_col = (long)m->spmm_winmax * (long)sizeof(T);
+  if (per_col <= 0) return 0;
+  int rc = (int)((long)kSpmmWinSmem / per_col);
+  return rc < rmax ? rc : rmax;
+}
+template <class T>
+static void spmm_launch(int v, const lrfsi_mesh_s* m, int cnt, int rmax, const SpmmBatch<T>& sb, cudaStream_t s) {
+  const int* rp = m->rowptr.p;
+  const int* ci = m->colidx.p;
+  const long M = m->h.M;
+  auto g = [&](int rpb) { return dim3(ceil_div(M, rpb), cnt); };
+  if (v >= 6) {
+    const int rc = spmm_window_cols<T>(m, rmax);
+    const size_t smem = (size_t)m->spmm_winmax * rc * sizeof(T);
+    const dim3 gw(ceil_div(M, kSpmmRowBlock), cnt);
+    switch (v) {
+      case 6: k_spmm_win<T, 32, 2><<<gw, 256, smem, s>>>(sb, rp, ci, m->spmm_win.p, M, rc); break;
+      case 7: k_spmm_win<T, 16, 4><<<gw, 256, smem, s>>>(sb, rp, ci, m->spmm_win.p, M, rc); break;
+      default: k_spmm_win<T, 8, 8><<<gw, 256, smem, s>>>(sb, rp, ci, m->spmm_win.p, M, rc); break;
+    }
+    return;
+  }
+  switch (v) {
+    case 0: k_spmm<T, 32, 1><<<g(8), 256, 0, s>>>(sb, rp, ci, M); break;
+    case 1: k_spmm<T, 32, 2><<<g(8), 256, 0, s>>>(sb, rp, ci, M); break;
+    case 2: k_spmm<T, 16, 2><<<g(16), 256, 0, s>>>(sb, rp, ci, M); break;
+    case 3: k_spmm<T, 16, 4><<<g(16), 256, 0, s>>>(sb, rp, ci, M); break;
+    case 4: k_spmm<T, 8, 4><<<g(32), 256, 0, s>>>(sb, rp, ci, M); break;
+    default: k_spmm<T, 8, 8><<<g(32), 256, 0, s>>>(sb, rp, ci, M); break;
+  }
+}
+
+static int spmm_win_attrs() {
+  static bool done = false;
+  if (done) return LRFSI_OK;
+  LRFSI_CUDA(cudaFuncSetAttribute(k_spmm_win<double, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmWinSmem));
+  LRFSI_CUDA(cudaFuncSetAttribute(k_spmm_win<double, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmWinSmem));
+  LRFSI_CUDA(cudaFuncSetAttribute(k_spmm_win<double, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmWinSmem));
+  LRFSI_CUDA(cudaFuncSetAttribute(k_spmm_win<float, 32, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmWinSmem));
+  LRFSI_CUDA(cudaFuncSetAttribute(k_spmm_win<float, 16, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmWinSmem));
+  LRFSI_CUDA(cudaFuncSetAttribute(k_spmm_win<float, 8, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSpmmWinSmem));
+  done = true;
+  return LRFSI_OK;
+}
+
+// Autotuner: on the first batch of a given (precision, rank bucket) every
+// shape is timed (CUDA events on the launching stream, best of 3 after one
+// warm-up run) and the fastest is kept for the process.  The timed runs
+// compute the same outputs, so the batch's result is unaffected.
+struct SpmmChoice {
+  int v = -1;
+  float ms[kSpmmVariants] = {0};
+};
+static std::mutex g_spmm_mu;
+static SpmmChoice g_spmm_choice[2][9];  // [FP64, FP32][rank bucket: ceil(rmax / 16), capped]
+
+static int spmm_bucket(int rmax) {
+  const int b = (rmax + 15) / 16;
+  return b < 8 ? b : 8;
+}
+
+template <class T>
+static int spmm_variant(const SpmmBatch<T>& sb, int cnt, int rmax, const lrfsi_mesh_s* m, cudaStream_t s) {
+  const int pi = sizeof(T) == 8 ? 0 : 1, bk = spmm_bucket(rmax);
+  {
+    std::lock_guard<std::mutex> lk(g_spmm_mu);
+    if (g_spmm_choice[pi][bk].v >= 0) return g_spmm_choice[pi][bk].v;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+    return rmax <= 32 ? 0 : 1;  // no timing while a stream is being captured
+  cudaEvent_t e0, e1;
+  LRFSI_CUDA(cudaEventCreate(&e0));
+  LRFSI_CUDA(cudaEventCreate(&e1));
+  SpmmChoice ch;
+  float best = 1e30f;
+  LRFSI_TRY(spmm_win_attrs());
+  const bool win_ok = spmm_window_cols<T>(m, rmax) >= 1;
+  for (int v = 0; v < kSpmmVariants; ++v) {
+    float bv = 1e30f;
+    if (v >= 6 && !win_ok) { ch.ms[v] = 0; continue; }
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0, s);
+      spmm_launch<T>(v, m, cnt, rmax, sb, s);
+      cudaEventRecord(e1, s);
+      LRFSI_TRY(check_launch("k_spmm (autotune)"));
+      LRFSI_CUDA(cudaEventSynchronize(e1));
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep > 0 && ms < bv) bv = ms;
+    }
+    ch.ms[v] = bv;
+    if (bv < best) { best = bv; ch.v = v; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  std::lock_guard<std::mutex> lk(g_spmm_mu);
+  g_spmm_choice[pi][bk] = ch;
+  return ch.v;
 }
 
 template <class T>
@@ -84,6 +291,7 @@ int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_
       rmax = rmax > d[i].r ? rmax : d[i].r;
     }
     if (!cnt) continue;
+    const int v = spmm_variant<T>(sb, cnt, rmax, m, s);
     {
       // algorithmic: CSR index + 3 value arrays once, U gathered once per row
       // of the pattern (L2-resident reuse not counted), outputs written once
@@ -97,12 +305,18 @@ int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_
       account(sizeof(T) == 8 ? KC_SPMM : KC_SPMM32, fl, by);
     }
     TimedLaunch tl(sizeof(T) == 8 ? KC_SPMM : KC_SPMM32, s);
-    dim3 grid(ceil_div(M, 8), cnt);
-    if (rmax <= 32) k_spmm<T, 1><<<grid, 256, 0, s>>>(sb, m->rowptr.p, m->colidx.p, M);
-    else k_spmm<T, 2><<<grid, 256, 0, s>>>(sb, m->rowptr.p, m->colidx.p, M);
+    spmm_launch<T>(v, m, cnt, rmax, sb, s);
     LRFSI_TRY(check_launch("k_spmm"));
     tl.end(s);
   }
+  return LRFSI_OK;
+}
+
+int spmm_autotune_table(int precision, int bucket, int* variant, float* ms) {
+  if (precision < 0 || precision > 1 || bucket < 0 || bucket > 8) return LRFSI_EINVAL;
+  std::lock_guard<std::mutex> lk(g_spmm_mu);
+  *variant = g_spmm_choice[precision][bucket].v;
+  for (int v = 0; v < kSpmmVariants; ++v) ms[v] = g_spmm_choice[precision][bucket].ms[v];
   return LRFSI_OK;
 }
 template int spmm_batched<double>(const lrfsi_mesh_s*, const SpmmDesc<double>*, int, cudaStream_t);
@@ -144,72 +358,85 @@ __global__ void k_lu_rhs(ProbPtrs pp, size_t off_up_s, size_t off_rhs, int n, in
 
 // Panel factorization with partial pivoting of columns [j0, j0 + nb) of the
 // n x n block A (ld) (rows j0..n-1); pivots are absolute row indices.  The
-// panel (at most kPanelRows x 32) is staged in shared memory.
+// panel ((n - j0) x nb) is staged in shared memory.  Two barriers per column:
+// the search for the next pivot is fused into the rank-1 update (each thread
+// tracks the largest |entry| of the next column among its rows, warps reduce
+// with shuffles), and every thread finishes the reduction over the warps'
+// candidates itself.  Ties go to the smallest row.
 constexpr int kPanelSmem = 220 * 1024;  // dynamic shared memory for the staged panel
-__global__ void __launch_bounds__(512) k_lu_panel(ProbPtrs pp, size_t off_blk, int piv_off, int n, int ld, int j0,
-                                                  int nb) {
+constexpr int kPanelThreads = 256;
+__device__ __forceinline__ void argmax_merge(double& v, int& i, double v2, int i2) {
+  if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
+}
+__global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t off_blk, int piv_off, int n, int ld,
+                                                            int j0, int nb) {
+  constexpr int kWarps = kPanelThreads / 32;
   const int b = blockIdx.x;
   double* A = pp.ws[b] + off_blk;
   int* piv = pp.piv[b] + piv_off;
-  extern __shared__ double sp[];  // (n - j0) x nb, row-major
-  __shared__ double s_val[512];
-  __shared__ int s_idx[512];
-  const int rows = n - j0;
-  for (long e = threadIdx.x; e < (long)rows * nb; e += blockDim.x) {
+  extern __shared__ double sp[];  // (n - j0) x nb, row-major with stride nb + 1 (no bank conflicts)
+  __shared__ double s_val[kWarps];
+  __shared__ int s_idx[kWarps];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int rows = n - j0, sl = nb + 1;
+  for (long e = tid; e < (long)rows * nb; e += kPanelThreads) {
     const int i = (int)(e / nb), c = (int)(e % nb);
-    sp[e] = A[(size_t)(j0 + i) * ld + j0 + c];
+    sp[(size_t)i * sl + c] = A[(size_t)(j0 + i) * ld + j0 + c];
+  }
+  __syncthreads();
+  auto warp_argmax = [&](double best, int bi) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
+      argmax_merge(best, bi, v2, i2);
+    }
+    if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
+  };
+  {  // candidates for column 0
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = tid; i < rows; i += kPanelThreads) argmax_merge(best, bi, fabs(sp[(size_t)i * sl]), i);
+    warp_argmax(best, bi);
   }
   __syncthreads();
   for (int jj = 0; jj < nb; ++jj) {
-    double best = -1.0;
-    int bi = jj;
-    for (int i = jj + threadIdx.x; i < rows; i += blockDim.x) {
-      const double v = fabs(sp[(size_t)i * nb + jj]);
-      if (v > best) { best = v; bi = i; }
-    }
-    s_val[threadIdx.x] = best;
-    s_idx[threadIdx.x] = bi;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if (threadIdx.x < o) {
-        const double v2 = s_val[threadIdx.x + o];
-        const int i2 = s_idx[threadIdx.x + o];
-        if (v2 > s_val[threadIdx.x] || (v2 == s_val[threadIdx.x] && i2 < s_idx[threadIdx.x])) {
-          s_val[threadIdx.x] = v2;
-          s_idx[threadIdx.x] = i2;
-        }
-      }
-      __syncthreads();
-    }
-    const int pr = s_idx[0];
-    const double pv = s_val[0];
-    if (threadIdx.x == 0) {
+    double pv = -1.0;
+    int pr = 0x7fffffff;
+#pragma unroll
+    for (int w = 0; w < kWarps; ++w) argmax_merge(pv, pr, s_val[w], s_idx[w]);
+    if (pr >= rows) { pr = jj; pv = 0.0; }
+    if (tid == 0) {
       piv[j0 + jj] = j0 + pr;
       if (!(pv > 0.0)) *pp.status[b] = LRFSI_ESINGULAR;
     }
     if (pr != jj)
-      for (int c = threadIdx.x; c < nb; c += blockDim.x) {
-        const double t = sp[(size_t)jj * nb + c];
-        sp[(size_t)jj * nb + c] = sp[(size_t)pr * nb + c];
-        sp[(size_t)pr * nb + c] = t;
+      for (int c = tid; c < nb; c += kPanelThreads) {
+        const double t = sp[(size_t)jj * sl + c];
+        sp[(size_t)jj * sl + c] = sp[(size_t)pr * sl + c];
+        sp[(size_t)pr * sl + c] = t;
       }
     __syncthreads();
-    double dgn = sp[(size_t)jj * nb + jj];
+    const double* rj = sp + (size_t)jj * sl;
+    double dgn = rj[jj];
     if (dgn == 0.0) dgn = 1e-300;  // singular: flagged above, keep going without NaNs
     const double inv = 1.0 / dgn;
     const int w = nb - jj - 1;
-    for (int i = jj + 1 + threadIdx.x; i < rows; i += blockDim.x) {
-      double* ri = sp + (size_t)i * nb;
+    double best = -1.0;
+    int bi = 0x7fffffff;
+    for (int i = jj + 1 + tid; i < rows; i += kPanelThreads) {
+      double* ri = sp + (size_t)i * sl;
       const double l = ri[jj] * inv;
       ri[jj] = l;
-      const double* rj = sp + (size_t)jj * nb;
-      for (int c = 0; c < w; ++c) ri[jj + 1 + c] -= l * rj[jj + 1 + c];
+      for (int c = 0; c < w; ++c) ri[jj + 1 + c] = fma(-l, rj[jj + 1 + c], ri[jj + 1 + c]);
+      if (w > 0) argmax_merge(best, bi, fabs(ri[jj + 1]), i);
     }
+    warp_argmax(best, bi);
     __syncthreads();
   }
-  for (long e = threadIdx.x; e < (long)rows * nb; e += blockDim.x) {
+  for (long e = tid; e < (long)rows * nb; e += kPanelThreads) {
     const int i = (int)(e / nb), c = (int)(e % nb);
-    A[(size_t)(j0 + i) * ld + j0 + c] = sp[e];
+    A[(size_t)(j0 + i) * ld + j0 + c] = sp[(size_t)i * sl + c];
   }
 }
 
@@ -232,46 +459,64 @@ __global__ void k_lu_laswp(ProbPtrs pp, size_t off_mat, int ld, int piv_off, int
 }
 
 // Triangular solve of a diagonal nb x nb block (nb <= 32) for columns
-// [c0, c1) of B: unit lower forward or upper backward substitution, thread
-// per column, the block in shared memory and the column in registers.
+// [c0, c1) of B: unit lower forward or upper backward substitution.  Four
+// lanes share a column (lane q holds rows q, q+4, ...); the substitution is
+// column-oriented: once x_l is final its owner broadcasts it within the
+// four lanes and each lane updates its own rows, so no lane runs a long
+// dependent chain.  32 columns per CTA of 128 threads; the block is staged in
+// shared memory.
+constexpr int kTrsmCols = 32;
 __global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L, int ldl, size_t off_B, int ldb,
                                                       int i0, int nb, int c0, int c1, int upper) {
   __shared__ double Ls[32][33];
   const double* L = pp.ws[blockIdx.y] + off_L;
   double* B = pp.ws[blockIdx.y] + off_B;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    const int i = e / nb, l = e % nb;
-    Ls[i][l] = L[(size_t)(i0 + i) * ldl + i0 + l];
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    const int i = e >> 5, l = e & 31;
+    Ls[i][l] = (i < nb && l < nb) ? L[(size_t)(i0 + i) * ldl + i0 + l] : 0.0;
   }
   __syncthreads();
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1) return;
-  double x[32];
+  const int lane = threadIdx.x & 31, q = lane & 3, base = lane & ~3;
+  const int c = c0 + blockIdx.x * kTrsmCols + (threadIdx.x >> 2);
+  const bool active = c < c1;
+  double x[8];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) x[i] = i < nb ? B[(size_t)(i0 + i) * ldb + c] : 0.0;
+  for (int k = 0; k < 8; ++k) {
+    const int i = q + 4 * k;
+    x[k] = (active && i < nb) ? B[(size_t)(i0 + i) * ldb + c] : 0.0;
+  }
   if (!upper) {
 #pragma unroll
-    for (int i = 1; i < 32; ++i) {
-      double sacc = x[i];
+    for (int l = 0; l < 32; ++l) {
+      const double xl = __shfl_sync(0xffffffffu, x[l >> 2], base + (l & 3));
 #pragma unroll
-      for (int l = 0; l < i; ++l) sacc -= Ls[i][l] * x[l];
-      x[i] = sacc;
+      for (int k = 0; k < 8; ++k) {
+        const int i = q + 4 * k;
+        if (i > l) x[k] = fma(-Ls[i][l], xl, x[k]);
+      }
     }
   } else {
 #pragma unroll
-    for (int i = 31; i >= 0; --i) {
-      if (i >= nb) continue;
-      double sacc = x[i];
+    for (int l = 31; l >= 0; --l) {
+      if (q == (l & 3)) {
+        const double dg = Ls[l][l];
+        x[l >> 2] = (l < nb) ? x[l >> 2] / (dg == 0.0 ? 1e-300 : dg) : 0.0;
+      }
+      const double xl = __shfl_sync(0xffffffffu, x[l >> 2], base + (l & 3));
 #pragma unroll
-      for (int l = i + 1; l < 32; ++l)
-        if (l < nb) sacc -= Ls[i][l] * x[l];
-      const double dg = Ls[i][i];
-      x[i] = sacc / (dg == 0.0 ? 1e-300 : dg);
+      for (int k = 0; k < 8; ++k) {
+        const int i = q + 4 * k;
+        if (i < l) x[k] = fma(-Ls[i][l], xl, x[k]);
+      }
     }
   }
+  if (active) {
 #pragma unroll
-  for (int i = 0; i < 32; ++i)
-    if (i < nb) B[(size_t)(i0 + i) * ldb + c] = x[i];
+    for (int k = 0; k < 8; ++k) {
+      const int i = q + 4 * k;
+      if (i < nb) B[(size_t)(i0 + i) * ldb + c] = x[k];
+    }
+  }
 }
 
 __global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t off_inv, int n, int nnext, int nmax) {
@@ -284,9 +529,15 @@ __global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t 
   if (j < n) ws[off_inv + (size_t)i * nmax + j] = R[nmax + j];
 }
 
+static int launch_panel(const ProbPtrs& pp, size_t offD, int poff, int n, int nmax, int j0, int nb, int nprob,
+                        cudaStream_t s) {
+  k_lu_panel<<<nprob, kPanelThreads, sizeof(double) * (size_t)(n - j0) * (nb + 1), s>>>(pp, offD, poff, n, nmax, j0, nb);
+  return check_launch("k_lu_panel");
+}
+
 int blocklu_alloc(const lrfsi_mesh_s* m, int nprob, BlockLU& lu) {
   if (nprob < 1 || nprob > kMaxGemmDescs) return fail(LRFSI_EINVAL, "block LU: 1..32 problems per batch");
-  if ((size_t)m->h.nmax * 8 * sizeof(double) > (size_t)kPanelSmem)
+  if ((size_t)m->h.nmax * 9 * sizeof(double) > (size_t)kPanelSmem)
     return fail(LRFSI_EINVAL, "block LU: slab larger than the panel kernel supports");
   {
     static bool attr = false;
@@ -349,14 +600,13 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
     // blocked right-looking LU of the Schur block S_s; the panel width keeps
     // the staged panel within shared memory
     int nbp = kNb;
-    while (nbp > 8 && (size_t)n * nbp * sizeof(double) > (size_t)kPanelSmem) nbp /= 2;
+    while (nbp > 8 && (size_t)n * (nbp + 1) * sizeof(double) > (size_t)kPanelSmem) nbp /= 2;
     for (int j0 = 0; j0 < n; j0 += nbp) {
       const int nb = j0 + nbp < n ? nbp : n - j0;
       {
         account(KC_LUPANEL, (double)nprob * ((double)(n - j0) * nb * nb - (double)nb * nb * nb / 3.0), 0);
         TimedLaunch tk(KC_LUPANEL, s);
-        k_lu_panel<<<nprob, 512, sizeof(double) * (size_t)(n - j0) * nb, s>>>(pp, offD, poff, n, nmax, j0, nb);
-        LRFSI_TRY(check_launch("k_lu_panel"));
+        LRFSI_TRY(launch_panel(pp, offD, poff, n, nmax, j0, nb, nprob, s));
         tk.end(s);
       }
       // interchanges to the left and right of the panel
@@ -370,7 +620,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
         {
           account(KC_LUTRSM, (double)nprob * nb * nb * (n - j0 - nb), 0);
           TimedLaunch tk(KC_LUTRSM, s);
-          k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, 128), nprob), 128, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
+          k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, kTrsmCols), nprob), 128, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
                                                                                 j0 + nb, n, 0);
           LRFSI_TRY(check_launch("k_lu_trsm_diag"));
           tk.end(s);
@@ -401,7 +651,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       {
         account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
         TimedLaunch tk(KC_LUTRSM, s);
-        k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
+        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
         LRFSI_TRY(check_launch("k_lu_trsm_diag"));
         tk.end(s);
       }
@@ -420,7 +670,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       {
         account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
         TimedLaunch tk(KC_LUTRSM, s);
-        k_lu_trsm_diag<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
+        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
         LRFSI_TRY(check_launch("k_lu_trsm_diag"));
         tk.end(s);
       }

@@ -20,6 +20,8 @@ struct SpmmDesc {
 };
 template <class T>
 int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_t s);
+// The autotuner's table: chosen shape (-1: not tuned) and timed ms of the shapes.
+int spmm_autotune_table(int precision, int bucket, int* variant, float* ms);
 
 // Block-tridiagonal LU of A_b = J0_b + alpha_b Jmu'_b + beta_b Jnu'_b over
 // the slab ordering: per slab s, S_s = D_s - Lo_{s-1} W_{s-1} (dense, FP64)

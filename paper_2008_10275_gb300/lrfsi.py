@@ -89,12 +89,17 @@ def load():
         "lrfsi_learned_fit": [vp, vp, vp, vp, i, vp, vp, i, i, i, C.c_float, vp, i, vp, vp, vp, vp, vp, vp],
         "lrfsi_learned_start": [vp, vp, vp, vp, i, vp, vp, i, i, vp, vp, vp, vp, vp, vp],
         "lrfsi_truncation_counters": [vp, i],
+        "lrfsi_spmm": [vp, vp, vp, i, i, vp, i, i, vp],
+        "lrfsi_spmm_tuning": [i, i, vp, vp],
         "lrfsi_pod": [vp, vp, i, i, i, vp, i, vp, i, vp, vp],
         "lrfsi_newton_median": [vp, i, vp, vp, vp, d, i, vp, vp, vp],
         "lrfsi_subset_create": [vp, i, vp, vp, vp, vp, vp, C.POINTER(vp), vp],
         "lrfsi_subset_destroy": [vp],
         "lrfsi_chebyshevT": [vp, vp, i, vp, i, vp, C.POINTER(lrfsi_cheb_options), vp, i, vp, i, vp, vp, vp],
         "lrfsi_subset_step": [vp, C.POINTER(lrfsi_cheb_options), d, i, vp, i, vp, i, vp, vp, vp, vp],
+        "lrfsi_subset_step_init": [vp, C.POINTER(lrfsi_cheb_options), d, i, vp, i, vp, i, vp, vp, i, vp, i, vp, vp,
+                                   vp, vp, vp],
+        "lrfsi_learned_factors": [vp, vp, i, vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp, vp, i, vp, i, vp],
         "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
         "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
     }
@@ -291,6 +296,22 @@ def lrfsi_subset_step(sub, opt, target, max_outer, U, ldu, V, ldv, stream=None, 
     return ranks, rel, outer, st
 
 
+def lrfsi_subset_step_init(sub, opt, target, max_outer, U0, ldu0, V0, ldv0, r0, U, ldu, V, ldv, stream=None,
+                           allow_noconv=True):
+    """lrfsi_subset_step from X0_k = x~_k 1^T + U0_k V0_k^T.  Returns
+    (ranks, relres, outer, fallback flags, status)."""
+    ranks = np.zeros(sub.K, np.int32)
+    rel = np.zeros(int(sub.sizes.sum()))
+    outer = np.zeros(sub.K, np.int32)
+    fb = np.zeros(int(sub.sizes.sum()), np.int32)
+    r0 = np.ascontiguousarray(np.broadcast_to(r0, (sub.K,)), np.int32)
+    st = load().lrfsi_subset_step_init(sub.h, C.byref(opt), target, max_outer, _ptr(U0), ldu0, _ptr(V0), ldv0,
+                                       _ptr(r0), _ptr(U), ldu, _ptr(V), ldv, _ptr(ranks), _ptr(rel), _ptr(outer),
+                                       _ptr(fb), _stream(stream))
+    _check(st, (ENOCONV,) if allow_noconv else ())
+    return ranks, rel, outer, fb, st
+
+
 def lrfsi_precond_apply(sub, X, ldx, r, Y, ldy, stream=None):
     r = np.ascontiguousarray(np.broadcast_to(r, (sub.K,)), np.int32)
     _check(load().lrfsi_precond_apply(sub.h, _ptr(X), ldx, _ptr(r), _ptr(Y), ldy, _stream(stream)))
@@ -313,6 +334,20 @@ def kernel_stats():
         _check(load().lrfsi_stats(i, C.byref(st)))
         out[name] = dict(launches=int(st.launches), flops=st.flops, bytes=st.bytes, ms=st.ms)
     return out
+
+
+def lrfsi_spmm(mesh, J3, U, ldu, r, Y, ldy, stream=None):
+    """Y = [J0 U | Jmu' U | Jnu' U]; FP64 or FP32 tensors (all the same dtype)."""
+    import torch
+    prec = {torch.float64: 0, torch.float32: 1}[U.dtype]
+    _check(load().lrfsi_spmm(mesh.h, _ptr(J3), _ptr(U), ldu, r, _ptr(Y), ldy, prec, _stream(stream)))
+
+
+def spmm_tuning(precision, bucket):
+    v = np.zeros(1, np.int32)
+    ms = np.zeros(9, np.float32)
+    _check(load().lrfsi_spmm_tuning(precision, bucket, _ptr(v), _ptr(ms)))
+    return int(v[0]), ms
 
 
 def truncation_counters(reset=False):
@@ -417,6 +452,16 @@ class LearnedStart:
                                         _stream(stream)))
         self.loss, self.sigma = float(loss[0]), sigma
         return self.loss
+
+    def factors(self, sizes, mu, nu, xt, U0, V0, stream=None):
+        """Start factors relative to the K median solutions xt (K x M tensor):
+        U0 (K*M x (k+1)) and V0 (sum(sizes) x (k+1)) device tensors."""
+        sizes = np.ascontiguousarray(sizes, np.int32)
+        mu = np.ascontiguousarray(mu, np.float64); nu = np.ascontiguousarray(nu, np.float64)
+        _check(load().lrfsi_learned_factors(self.mesh.h, self.mlp.h, len(sizes), _ptr(sizes), _ptr(mu), _ptr(nu),
+                                            _ptr(self.box), _ptr(self.Phi), self.k, self.k, _ptr(self.cs),
+                                            _ptr(self.fs), _ptr(self.off), _ptr(xt), _ptr(U0), self.k + 1,
+                                            _ptr(V0), self.k + 1, _stream(stream)))
 
     def start(self, mu, nu, X, stream=None):
         """Fill X (B x M device tensor) with the start; returns the fallback flags."""

@@ -205,3 +205,66 @@ def test_learned_start_fit_and_start():
     assert np.all(it_l <= it_b)
     # Newton's solution does not depend on the start
     assert _rel(Xl.cpu().numpy(), Xb.cpu().numpy()) <= 1e-7
+
+
+def test_learned_start_of_the_subset_step_saves_corrections():
+    """What the trained network gains: the subset step started from the
+    learned start (lrfsi_subset_step_init) needs fewer correction steps than
+    the plain step from the median solution, reaches the same target in every
+    column and lands on the same solutions."""
+    mesh = lrfsi.Mesh(20, 4)
+    M = mesh.M
+    bD = torch.as_tensor(mesh.dirichlet(), device=DEV)
+    mu_t, nu_t = inputs.latin_hypercube(96, seed=21)
+    Xs, _ = _newton(mesh, mu_t, nu_t, bD.repeat(96, 1))
+    k = 16
+    ls = lrfsi.LearnedStart(mesh, k=k, seed=1)
+    ls.fit(Xs, mu_t, nu_t, epochs=2000, lr=2e-3)
+    # evaluation: 3 subsets of 16 held-out parameters (ordered by mu_s) in the
+    # middle of the box, where the chord corrections of the plain step
+    # converge in a few steps
+    mu_e, nu_e = inputs.uniform_parameters(48, seed=22)
+    mu_e = 8e5 + (mu_e - inputs.MU_RANGE[0]) / (inputs.MU_RANGE[1] - inputs.MU_RANGE[0]) * 6e5
+    nu_e = 2.5e-3 + (nu_e - inputs.NU_RANGE[0]) / (inputs.NU_RANGE[1] - inputs.NU_RANGE[0]) * 1e-3
+    o = np.argsort(mu_e)
+    mu_e, nu_e = mu_e[o], nu_e[o]
+    K, m, R = 3, 16, 20
+    sizes = [m] * K
+    med = [q * m + m // 2 for q in range(K)]
+    X = bD.repeat(K, 1)
+    lrfsi.lrfsi_newton_median(mesh, X, mu_e[med], nu_e[med], 1e-10, 30)
+    opt = lrfsi.cheb_options(0.65, 1.0, iters=6, cycles=2, rank_cap=R, tol=1e-8, eta=0.05)
+    target = 1e-6
+    res = {}
+    for mode in ("plain", "learned"):
+        sub = lrfsi.Subsets(mesh, X, mu_e, nu_e, sizes, [R] * K)
+        U = torch.zeros(K * M * R, dtype=torch.float64, device=DEV)
+        V = torch.zeros(K * m * R, dtype=torch.float64, device=DEV)
+        if mode == "plain":
+            ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, target, 40, U, R, V, R)
+            fb = None
+        else:
+            U0 = torch.zeros(K * M * (k + 1), dtype=torch.float64, device=DEV)
+            V0 = torch.zeros(K * m * (k + 1), dtype=torch.float64, device=DEV)
+            ls.factors(sizes, mu_e, nu_e, X, U0, V0)
+            ranks, rel, outer, fb, st = lrfsi.lrfsi_subset_step_init(sub, opt, target, 40, U0, k + 1, V0, k + 1,
+                                                                     k + 1, U, R, V, R)
+        assert st == 0 and np.all(rel <= target), (mode, outer, rel.max())
+        cols = []
+        for q in range(K):
+            Uq = U[q * M * R:(q + 1) * M * R].view(M, R)[:, :ranks[q]]
+            Vq = V[q * m * R:(q + 1) * m * R].view(m, R)[:, :ranks[q]]
+            cols.append(X[q][:, None] + Uq @ Vq.T)
+        res[mode] = (outer.copy(), torch.cat(cols, 1).cpu().numpy(), fb)
+        sub.close()
+    # the plain step counts its first Newton step as a ChebyshevT solve plus
+    # the corrections; the learned step replaces that first step
+    plain_solves = res["plain"][0].sum() + K
+    learned_solves = res["learned"][0].sum()
+    assert learned_solves < plain_solves, (res["plain"][0], res["learned"][0])
+    assert res["learned"][2].sum() <= len(mu_e) // 4
+    Xp, Xl = res["plain"][1], res["learned"][1]
+    # both solve R(x_i) = 0 to a relative residual of 1e-6; the solutions agree
+    # to that order relative to the size of the correction from b_D
+    d = np.abs(Xp - Xl).max() / np.abs(Xp - mesh.dirichlet()[:, None]).max()
+    assert d <= 1e-4

@@ -179,3 +179,30 @@ def test_mixed_precision_subset_step_reaches_target():
     # against the Newton update itself
     upd = np.linalg.norm(out[0] - xt[perm][:, None])
     assert np.linalg.norm(out[1] - out[0]) <= 1e-5 * upd
+
+
+@pytest.mark.parametrize("r", [1, 7, 40, 80])
+def test_spmm_parity_fp64_and_fp32(r):
+    """lrfsi_spmm against the oracle's affine operators times U: FP64 to 1e-12
+    of the largest entry (same products, different order); FP32 (FP32 values,
+    FP32 accumulation over <= ~50 terms per row) to 1e-5."""
+    lm, om, perm = _meshes(20, 4)
+    x = om.bD + inputs.random_state(om.M, 3, nq2=om.NQ2)
+    J3 = torch.zeros(lm.nnz * 3, dtype=torch.float64, device=DEV)
+    lrfsi.lrfsi_assemble_affine(lm, _dev(x[perm]), J3, None)
+    oJ = fsi.affine_jacobian(om, x)
+    Uh = np.random.default_rng(r).standard_normal((lm.M, r))
+    ref = np.concatenate([(oJ[t][perm][:, perm] @ Uh) for t in range(3)], 1)
+    for dt, tol in ((torch.float64, 1e-12), (torch.float32, 1e-5)):
+        U = torch.tensor(Uh, dtype=dt, device=DEV)
+        Y = torch.full((lm.M, 3 * r), float("nan"), dtype=dt, device=DEV)
+        J = J3 if dt == torch.float64 else J3.to(torch.float32)
+        for _ in range(2):  # the first call of a rank bucket runs the autotuner
+            lrfsi.lrfsi_spmm(lm, J, U, r, r, Y, 3 * r)
+            torch.cuda.synchronize()
+            got = Y.double().cpu().numpy()
+            for t in range(3):
+                blk = slice(t * r, (t + 1) * r)
+                assert rel_max(got[:, blk], ref[:, blk]) <= tol, (str(dt), t)
+    v, ms = lrfsi.spmm_tuning(0, (r + 15) // 16 if r < 128 else 8)
+    assert 0 <= v < 9 and ms[v] > 0
