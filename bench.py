@@ -133,6 +133,108 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_learned(args, rank, world):
+    """The learned-start workload: an MLP trained on 500 method-generated
+    solutions (Latin hypercube parameters, 5 subsets of 100) starts both the
+    median Newton iterations and the subset steps for 2000 held-out uniform
+    parameters (20 subsets of 100, nu_f-major order); compared with the plain
+    method (median Newton from b_D, subset step from the median solution)."""
+    import torch
+    from paper_2008_10275_gb300 import build, lrfsi
+    build.build()
+    lrfsi.load()
+    dev = "cuda:0"
+    W = inputs.WORKLOADS["learned"]
+    mesh = lrfsi.Mesh(W.nx, W.ny)
+    M, R = mesh.M, W.rank_cap
+    bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=dev)
+    opt = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=args.precision,
+                             eta=args.eta)
+
+    def layout(mus, nus, K):
+        o = np.lexsort((mus, nus))  # nu_f-major, as the grids' little-endian order
+        mus, nus = mus[o], nus[o]
+        sizes, medians = subset_layout(len(mus), K)
+        return mus, nus, sizes, medians
+
+    def solve(mus, nus, K, ls=None):
+        """Method on (mus, nus): returns dense solutions (M x m) and stats."""
+        mus, nus, sizes, medians = layout(mus, nus, K)
+        m = len(mus)
+        X = bD.repeat(K, 1)
+        if ls is not None:  # learned start of the median Newton iterations
+            ls.start(mus[medians], nus[medians], X)
+        it, res, _ = lrfsi.lrfsi_newton_median(mesh, X, mus[medians], nus[medians], 1e-8, 30)
+        sub = lrfsi.Subsets(mesh, X, mus, nus, sizes, [R] * K)
+        U = torch.zeros(K * M * R, dtype=torch.float64, device=dev)
+        V = torch.zeros(m * R, dtype=torch.float64, device=dev)
+        fb = np.zeros(m, np.int32)
+        if ls is None:
+            ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, args.target, args.max_outer, U, R, V, R)
+        else:
+            k = ls.k
+            U0 = torch.zeros(K * M * (k + 1), dtype=torch.float64, device=dev)
+            V0 = torch.zeros(m * (k + 1), dtype=torch.float64, device=dev)
+            ls.factors(sizes, mus, nus, X, U0, V0)
+            ranks, rel, outer, fb, st = lrfsi.lrfsi_subset_step_init(sub, opt, args.target, args.max_outer, U0, k + 1,
+                                                                     V0, k + 1, k + 1, U, R, V, R)
+        sub.close()
+        cols, o = [], 0
+        for q in range(K):
+            r = int(ranks[q])
+            Uq = U[q * M * R:(q + 1) * M * R].view(M, R)[:, :r]
+            Vq = V[o * R:(o + sizes[q]) * R].view(sizes[q], R)[:, :r]
+            cols.append(X[q][:, None] + Uq @ Vq.T)
+            o += sizes[q]
+        return torch.cat(cols, 1), dict(newton_steps=int(it.sum()), newton_max=int(it.max()),
+                                        outer=outer.tolist(), max_relres=float(rel.max()), status=int(st),
+                                        fallbacks=int(fb.sum()))
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        out = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), out
+
+    # training data: the method itself on 500 Latin-hypercube parameters
+    mu_t, nu_t = inputs.latin_hypercube(500, seed=W.seed + 1)
+    ms_gen, (Xt, st_t) = timed(lambda: solve(mu_t, nu_t, 5))
+    mu_ts, nu_ts, _, _ = layout(mu_t, nu_t, 5)
+    k = 64
+    ls = lrfsi.LearnedStart(mesh, k=k, seed=W.seed)
+    Xtrain = Xt.T.contiguous()  # problem-major
+    ms_fit, loss = timed(lambda: ls.fit(Xtrain, mu_ts, nu_ts, epochs=3000, lr=2e-3))
+    # evaluation on 2000 held-out parameters
+    mu_e, nu_e = inputs.workload_parameters(W)
+    for _ in range(max(1, args.warmup)):
+        solve(mu_e[:200], nu_e[:200], 2)
+        solve(mu_e[:200], nu_e[:200], 2, ls)
+    ms_plain, (Xp, st_p) = timed(lambda: solve(mu_e, nu_e, W.K))
+    ms_learn, (Xl, st_l) = timed(lambda: solve(mu_e, nu_e, W.K, ls))
+    diff = float(torch.linalg.norm(Xl - Xp) / torch.linalg.norm(Xp - bD[:, None]))
+    m = len(mu_e)
+    line = {
+        "metric": METRIC, "value": m / (ms_learn * 1e-3), "unit": "params/s", "n_gpus": 1, "steps": 1,
+        "warmup": args.warmup, "ms_per_step": ms_learn, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
+        "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "M": M, "params": m, "subsets": W.K, "rank_cap": R,
+                   "train": "500 method solutions at Latin-hypercube parameters", "pod_rank": k,
+                   "mlp": "2-128-128-64 GELU, BF16 weights"},
+        "learned": {**st_l, "ms": ms_learn, "params_per_s": m / (ms_learn * 1e-3)},
+        "plain": {**st_p, "ms": ms_plain, "params_per_s": m / (ms_plain * 1e-3)},
+        "speedup_vs_plain": ms_plain / ms_learn,
+        "rel_diff_learned_vs_plain_solution_update": diff,
+        "train": {"generate_ms": ms_gen, "fit_ms": ms_fit, "final_loss": loss, "epochs": 3000,
+                  "generate_status": st_t["status"], "generate_max_relres": st_t["max_relres"]},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -154,6 +256,10 @@ def main():
     rank, world, local = multi.rank_env()
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "learned":
+        if rank != 0:
+            return 0
+        return run_learned(args, rank, world)
 
     import torch
     if not torch.cuda.is_available():
@@ -169,13 +275,22 @@ def main():
     dev = f"cuda:{local}"
     W = inputs.WORKLOADS[args.workload]
     mus, nus = inputs.workload_parameters(W, rank, world)
+    if W.seed is not None:  # random parameters: nu_f-major order, as the grids' little-endian order
+        o = np.lexsort((mus, nus))
+        mus, nus = mus[o], nus[o]
     m = len(mus)
-    sizes, medians = subset_layout(m, W.K)
     K = W.K
-    caps = [W.rank_cap] * K
+    if W.subset_sizes:  # uneven subsets with their own rank caps
+        sizes = list(W.subset_sizes)
+        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)
+        medians = [int(o + q // 2) for o, q in zip(offs, sizes)]
+        caps = list(W.rank_caps)
+    else:
+        sizes, medians = subset_layout(m, K)
+        caps = [W.rank_cap] * K
     mesh = lrfsi.Mesh(W.nx, W.ny)
     bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=dev)
-    R = W.rank_cap
+    R = max(caps)
     U = torch.zeros(K * mesh.M * R, dtype=torch.float64, device=dev)
     V = torch.zeros(m * R, dtype=torch.float64, device=dev)
     eps_N = 1e-8

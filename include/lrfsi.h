@@ -362,7 +362,9 @@ int lrfsi_learned_factors(lrfsi_mesh_h mesh, lrfsi_mlp_h mlp, int K, const int* 
 /* lrfsi_pod: rank-k POD of the snapshot columns X (M x n, ldx): the leading k
  * left singular vectors Phi (M x k, ldphi, orthonormal columns) and the
  * coefficients C (n x k, ldc) with X ~ Phi C^T, by the same Cholesky-QR +
- * Jacobi machinery as the truncation T.  sigma_host: k singular values. */
+ * Jacobi machinery as the truncation T.  sigma_host: k singular values.
+ * Directions beyond the numerical rank of X (pivoted-Cholesky remainder below
+ * 1e-7 of the column norm) come back as zero columns with zero sigma. */
 int lrfsi_pod(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int n, int k, double* Phi_dev, int ldphi,
               double* C_dev, int ldc, double* sigma_host, lrfsi_stream_t stream);
 

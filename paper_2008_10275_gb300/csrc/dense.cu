@@ -365,7 +365,7 @@ __device__ void chol_drop(double* G, int ld, int p, double drop, int* keep) {
 
 size_t trunc_small_work(int p, int m) {
   const size_t n = (size_t)(p > m ? p : m);
-  return 4 * (size_t)p * p + 3 * n * n + 2 * (size_t)p * m + 4 * n + 64;
+  return 4 * (size_t)p * p + 3 * n * n + 2 * (size_t)p * m + 4 * n + 64 + trunc_svd_global_len(p, m, 16);
 }
 
 // Pass 1: unit-diagonal scaling and a diagonally pivoted (rank-revealing)
@@ -611,7 +611,7 @@ __device__ double local_cmax(const double* cols, int nslot, int j0, int n, int L
   return r;
 }
 
-__global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs) {
+__global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int global_blocks) {
   namespace cg = cooperative_groups;
   cg::cluster_group cl = cg::this_cluster();
   const int C = (int)cl.num_blocks(), crank = (int)cl.block_rank();
@@ -633,7 +633,14 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs) {
   const bool cols_of_C = m < k;
   const int n = cols_of_C ? m : k, L = cols_of_C ? k : m, LV = L + n;
   const int nb = 2 * C, b = (n + nb - 1) / nb;
-  extern __shared__ double sm[];
+  // the CTA's column blocks and round buffers: shared memory, or (problems
+  // too large for it) a slice of the global work array per CTA
+  extern __shared__ double smd[];
+  const size_t per_cta = (size_t)4 * b * LV;
+  double* sm = global_blocks ? W.Jg + (size_t)crank * per_cta : smd;
+  auto owner_blocks = [&](int r) -> double* {
+    return global_blocks ? W.Jg + (size_t)r * per_cta : cl.map_shared_rank(smd, r);
+  };
   double* home = sm;                    // 2b columns: global columns 2 crank b + h
   double* work = sm + (size_t)2 * b * LV;  // the two blocks of a tournament round
   const int j0 = 2 * crank * b;
@@ -649,9 +656,13 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs) {
   }
   __syncthreads();
   // exchange of {rotations, largest column norm} over the cluster
+  auto csync = [&]() {
+    if (global_blocks) __threadfence();
+    cl.sync();
+  };
   auto exchange = [&](int slot, double rot, double cm) {
     if (tid == 0) { s_ex[slot][0] = rot; s_ex[slot][1] = cm; }
-    cl.sync();
+    csync();
     if (tid == 0) {
       double tr = 0, tc = 0;
       for (int r = 0; r < C; ++r) {
@@ -684,13 +695,13 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs) {
         __syncthreads();
       }
     }
-    cl.sync();
+    csync();
     for (int round = 0; round < nb - 1; ++round) {  // (ii) cross pairs of the block tournament
       auto bpos = [&](int u) { return u == 0 ? 0 : ((round + u - 1) % (nb - 1)) + 1; };
       int X = bpos(crank), Y = bpos(nb - 1 - crank);
       if (X > Y) { const int tt = X; X = Y; Y = tt; }
-      double* hx = cl.map_shared_rank(sm, X >> 1) + (size_t)(X & 1) * b * LV;
-      double* hy = cl.map_shared_rank(sm, Y >> 1) + (size_t)(Y & 1) * b * LV;
+      double* hx = owner_blocks(X >> 1) + (size_t)(X & 1) * b * LV;
+      double* hy = owner_blocks(Y >> 1) + (size_t)(Y & 1) * b * LV;
       const bool any = X * b < n && Y * b < n;
       if (any) {
         for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
@@ -711,7 +722,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs) {
           hy[e] = work[(size_t)b * LV + e];
         }
       }
-      cl.sync();
+      csync();
     }
     if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
@@ -857,7 +868,13 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
     if (smem <= 200 * 1024 || C >= 16) break;
     C *= 2;  // more CTAs per problem: smaller blocks
   }
-  if (smem > 200 * 1024) return fail(LRFSI_EINVAL, "trunc_svd: core too large for the cluster SVD");
+  // beyond shared memory the column blocks live in the problem's global work
+  // array (sized for 16 CTAs by trunc_small_work)
+  const int global_blocks = smem > 200 * 1024 ? 1 : 0;
+  if (global_blocks) {
+    if (C < 16 && svd_cluster_size(1, 0) == 16) C = 16;
+    smem = 0;
+  }
   static size_t smem_set = 0;
   if (smem > 48 * 1024 && smem > smem_set) {
     LRFSI_CUDA(cudaFuncSetAttribute(k_trunc_svd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(200 * 1024)));
@@ -877,7 +894,7 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
   cfg.stream = s;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  LRFSI_CUDA(cudaLaunchKernelEx(&cfg, k_trunc_svd, d_dev));
+  LRFSI_CUDA(cudaLaunchKernelEx(&cfg, k_trunc_svd, d_dev, global_blocks));
   LRFSI_TRY(check_launch("k_trunc_svd"));
   tl.end(s);
   return LRFSI_OK;

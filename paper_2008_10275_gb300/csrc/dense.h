@@ -63,7 +63,7 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev);
 // scaled pass-1 factor, later W_r; Rki the zero-padded factor of the latest QR
 // pass; Y and C the two core buffers.
 struct TruncWork {
-  double *Dsc, *Rk, *Rki, *Y, *C, *A, *Vm;
+  double *Dsc, *Rk, *Rki, *Y, *C, *A, *Vm, *Jg;
   __host__ __device__ TruncWork(double* w, int p, int m) {
     const size_t n = (size_t)(p > m ? p : m);
     Dsc = w;
@@ -73,7 +73,14 @@ struct TruncWork {
     C = Y + (size_t)p * m;
     A = C + (size_t)p * m;
     Vm = A + n * n;
+    Jg = Vm + n * n;  // column blocks of the cluster SVD when they exceed shared memory
   }
 };
+// Doubles of Jg per problem for a cluster of C CTAs: C x 4 b (L + n), b = ceil(n / 2C).
+__host__ __device__ inline size_t trunc_svd_global_len(int p, int m, int C) {
+  const int n = p < m ? p : m, L = p < m ? m : p;
+  const int b = (n + 2 * C - 1) / (2 * C);
+  return (size_t)C * 4 * b * (size_t)(L + n);
+}
 
 }  // namespace lrfsi

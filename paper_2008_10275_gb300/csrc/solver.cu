@@ -1645,12 +1645,24 @@ extern "C" int lrfsi_pod(lrfsi_mesh_h mesh, const double* X, int ldx, int n, int
   std::vector<double*> Uo{S->UR.p}, Vo{S->VR.p};
   std::vector<double> f2;
   LRFSI_TRY(truncate_batch(S.get(), act, p, 0.0, S->cap, Uo, Vo, rank, f2, s));
-  if (rank[0] < k) return fail(LRFSI_EINVAL, "lrfsi_pod: the snapshots have numerical rank below k");
+  // below the numerical rank the basis and coefficients are zero-filled
+  const int kr = rank[0] < k ? rank[0] : k;
   cd.clear();
-  cd.push_back(CopyDesc{S->UR.p, ldR, Phi, ldphi, M, k, 0, nullptr, 1.0});
-  cd.push_back(CopyDesc{S->VR.p, ldR, C, ldc, n, k, 0, nullptr, 1.0});
+  if (kr > 0) {
+    cd.push_back(CopyDesc{S->UR.p, ldR, Phi, ldphi, M, kr, 0, nullptr, 1.0});
+    cd.push_back(CopyDesc{S->VR.p, ldR, C, ldc, n, kr, 0, nullptr, 1.0});
+  }
+  if (kr < k) {
+    cd.push_back(CopyDesc{nullptr, 0, Phi + kr, ldphi, M, k - kr, 1, nullptr, 0.0});
+    cd.push_back(CopyDesc{nullptr, 0, C + kr, ldc, n, k - kr, 1, nullptr, 0.0});
+  }
   LRFSI_TRY(copy_batched(cd, s));
-  if (sigma) LRFSI_CUDA(cudaMemcpyAsync(sigma, S->sv.p, sizeof(double) * k, cudaMemcpyDeviceToHost, s));
+  if (sigma) {
+    std::vector<double> sv(k, 0.0);
+    if (kr > 0) LRFSI_CUDA(cudaMemcpyAsync(sv.data(), S->sv.p, sizeof(double) * kr, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(sigma, sv.data(), sizeof(double) * k);
+  }
   LRFSI_CUDA(cudaStreamSynchronize(s));
   return LRFSI_OK;
 }

@@ -54,10 +54,10 @@ WORKLOADS = {
     "medium": Workload("channel80x16_400", 80, 16, _lin(MU_RANGE, 20), _lin(NU_RANGE, 20),
                        K=4, rank_cap=40),
     "batched": Workload("channel80x16_random1000_16uneven", 80, 16, K=16, seed=0, n_random=1000,
-                        subset_sizes=uneven_sizes(), rank_caps=tuple(int(round(10 + 50 * j / 15)) for j in range(16))),
+                        subset_sizes=uneven_sizes(), rank_caps=tuple(int(round(60 - 40 * j / 15)) for j in range(16))),
     "large": Workload("channel320x64_2500", 320, 64, _lin(MU_RANGE, 50), _lin(NU_RANGE, 50),
                       K=25, rank_cap=80),
-    "learned": Workload("channel80x16_learned", 80, 16, seed=1, n_random=2000, K=4, rank_cap=40),
+    "learned": Workload("channel80x16_learned2000", 80, 16, seed=1, n_random=2000, K=20, rank_cap=40),
 }
 
 
