@@ -411,6 +411,10 @@ def main():
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom, "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback"}
     roof["per_class_ms"] = {k: round(v["ms"], 3) for k, v in ks.items()}
+    # algorithmic FP rate per class (TFLOP/s over its own launch time) and launches
+    roof["per_class_tflops"] = {k: round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4)
+                                for k, v in ks.items() if v["ms"] > 0 and v["flops"] > 0}
+    roof["per_class_launches"] = {k: int(v["launches"]) for k, v in ks.items() if v["launches"] > 0}
     spmm = ks["spmm_fp64"]
     spmm_gbs = spmm["bytes"] / (spmm["ms"] * 1e-3) / 1e9 if spmm["ms"] > 0 else None
 

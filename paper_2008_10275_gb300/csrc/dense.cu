@@ -196,10 +196,16 @@ struct GramBatch {
 constexpr int kGramRowsMin = 256;
 
 __global__ void __launch_bounds__(256) k_gram_partial(GramBatch gb, long M, int nsplit, int pmax, int qmax,
-                                                     double* __restrict__ work) {
+                                                     double* __restrict__ work, int upper) {
   const GramDesc g = gb.d[blockIdx.z];
   const int tiles_q = (qmax + GBN - 1) / GBN;
-  const int ti = blockIdx.x / tiles_q, tj = blockIdx.x % tiles_q;
+  int ti = blockIdx.x / tiles_q, tj = blockIdx.x % tiles_q;
+  if (upper) {  // blockIdx.x enumerates the tiles ti <= tj row by row
+    int t = blockIdx.x;
+    ti = 0;
+    while (t >= tiles_q - ti) { t -= tiles_q - ti; ++ti; }
+    tj = ti + t;
+  }
   const int i0 = ti * GBM, j0 = tj * GBN;
   const int split = blockIdx.y;
   double* out = work + ((size_t)blockIdx.z * nsplit + split) * (size_t)pmax * qmax;
@@ -250,15 +256,19 @@ __global__ void __launch_bounds__(256) k_gram_partial(GramBatch gb, long M, int 
   }
 }
 
-__global__ void k_gram_reduce(GramBatch gb, int nsplit, int pmax, int qmax, const double* __restrict__ work) {
+__global__ void k_gram_reduce(GramBatch gb, int nsplit, int pmax, int qmax, const double* __restrict__ work,
+                              int upper) {
   const GramDesc g = gb.d[blockIdx.y];
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (idx >= (long)g.p * g.q) return;
-  const int i = (int)(idx / g.q), j = (int)(idx % g.q);
+  int i = (int)(idx / g.q), j = (int)(idx % g.q);
+  const int oi = i, oj = j;
+  // symmetric products: tiles below the diagonal were not computed, read the mirror
+  if (upper && i / GBM > j / GBN) { const int t = i; i = j; j = t; }
   const double* w = work + (size_t)blockIdx.y * nsplit * (size_t)pmax * qmax + (size_t)i * qmax + j;
   double s = 0;
   for (int t = 0; t < nsplit; ++t) s += w[(size_t)t * pmax * qmax];
-  g.G[(size_t)i * g.ldg + j] = s;
+  g.G[(size_t)oi * g.ldg + oj] = s;
 }
 
 static int gram_nsplit(int nbatch, long M, int pmax, int qmax) {
@@ -284,24 +294,40 @@ int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t wor
       pmax = pmax > d[i].p ? pmax : d[i].p;
       qmax = qmax > d[i].q ? qmax : d[i].q;
     }
+    // all products symmetric (A^T A): only the tiles on and above the diagonal
+    bool upper = pmax == qmax;
+    for (int i = 0; i < cnt; ++i)
+      upper = upper && gb.d[i].A == gb.d[i].B && gb.d[i].lda == gb.d[i].ldb && gb.d[i].p == gb.d[i].q;
+    const int T = ceil_div(pmax, GBM);
+    const int ntiles = upper ? T * (T + 1) / 2 : ceil_div(pmax, GBM) * ceil_div(qmax, GBN);
     int nsplit = gram_nsplit(cnt, M, pmax, qmax);
+    if (upper) {  // the same number of CTAs for fewer tiles: more row splits
+      long want = 4L * 152 / ((long)ntiles * cnt);
+      const long maxs = (M + kGramRowsMin - 1) / kGramRowsMin;
+      if (want < 1) want = 1;
+      if (want > maxs) want = maxs;
+      if (want > 256) want = 256;
+      nsplit = (int)want;
+    }
     const size_t fit = work_len / ((size_t)cnt * pmax * qmax);
     if (fit < 1) return fail(LRFSI_EINVAL, "gram workspace too small");
     if ((size_t)nsplit > fit) nsplit = (int)fit;
     {
       double fl = 0, by = 0;
       for (int i = 0; i < cnt; ++i) {
-        fl += 2.0 * M * gb.d[i].p * gb.d[i].q;
+        // symmetric products: the algorithmic work is the upper triangle
+        const bool sym = gb.d[i].A == gb.d[i].B && gb.d[i].p == gb.d[i].q;
+        fl += sym ? 1.0 * M * gb.d[i].p * (gb.d[i].p + 1) : 2.0 * M * gb.d[i].p * gb.d[i].q;
         by += 8.0 * M * (gb.d[i].A == gb.d[i].B ? gb.d[i].p : gb.d[i].p + gb.d[i].q);
       }
       account(KC_GRAM, fl, by);
     }
     TimedLaunch tl(KC_GRAM, s);
-    dim3 grid(ceil_div(pmax, GBM) * ceil_div(qmax, GBN), nsplit, cnt);
-    k_gram_partial<<<grid, 256, 0, s>>>(gb, M, nsplit, pmax, qmax, work);
+    dim3 grid(ntiles, nsplit, cnt);
+    k_gram_partial<<<grid, 256, 0, s>>>(gb, M, nsplit, pmax, qmax, work, upper ? 1 : 0);
     LRFSI_TRY(check_launch("k_gram_partial"));
     dim3 g2(ceil_div((long)pmax * qmax, 256), cnt);
-    k_gram_reduce<<<g2, 256, 0, s>>>(gb, nsplit, pmax, qmax, work);
+    k_gram_reduce<<<g2, 256, 0, s>>>(gb, nsplit, pmax, qmax, work, upper ? 1 : 0);
     LRFSI_TRY(check_launch("k_gram_reduce"));
     tl.end(s);
   }

@@ -526,25 +526,25 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
       be.push_back(nu_h[k]);
     }
     const int na = (int)act.size();
-    LRFSI_TRY(blocklu_factor(m, lu, J3p.data(), al.data(), be.data(), na, s));
-    std::vector<int> lst;
-    LRFSI_TRY(blocklu_status(lu, na, lst, s));
-    for (int a = 0; a < na; ++a)
-      if (lst[a] != 0) status = LRFSI_ESINGULAR;
-    // dX = -J^{-1} R  (negate the residual in place, solve column by column of the M x K block)
+    // dX = -J^{-1} R: the residual is negated in place and its forward sweep
+    // runs inside the factorisation (single-solve mode: no explicit inverses)
     {
       std::vector<CopyDesc> cd;
       cd.push_back(CopyDesc{Rb.p, K, Rb.p, K, M, K, 0, nullptr, -1.0});
       LRFSI_TRY(copy_batched(cd, s));
     }
     LRFSI_CUDA(cudaMemsetAsync(dX.p, 0, sizeof(double) * M * K, s));
-    std::vector<double*> Xs(na), Ys(na);
-    std::vector<int> rr(na, 1);
+    std::vector<const double*> bs(na);
+    std::vector<double*> ys(na);
     for (int a = 0; a < na; ++a) {
-      Xs[a] = Rb.p + act[a];
-      Ys[a] = dX.p + act[a];
+      bs[a] = Rb.p + act[a];
+      ys[a] = dX.p + act[a];
     }
-    LRFSI_TRY(blocklu_solve(lu, Xs.data(), Ys.data(), rr.data(), K, na, s));
+    LRFSI_TRY(blocklu_factor(m, lu, J3p.data(), al.data(), be.data(), na, s, bs.data(), ys.data(), K));
+    std::vector<int> lst;
+    LRFSI_TRY(blocklu_status(lu, na, lst, s));
+    for (int a = 0; a < na; ++a)
+      if (lst[a] != 0) status = LRFSI_ESINGULAR;
     LRFSI_CUDA(cudaMemcpyAsync(Xold.p, X.p, sizeof(double) * M * K, cudaMemcpyDeviceToDevice, s));
     // step with halving while the residual grows
     std::fill(t.begin(), t.end(), 0.0);

@@ -333,6 +333,9 @@ struct ProbPtrs {
   int* piv[kMaxGemmDescs];
   int* status[kMaxGemmDescs];
   double alpha[kMaxGemmDescs], beta[kMaxGemmDescs];
+  const double* b[kMaxGemmDescs];  // single-solve mode: right-hand side (stride ldb)
+  double* y[kMaxGemmDescs];        // single-solve mode: solution (stride ldb)
+  int ldb;
 };
 
 __global__ void k_lu_extract(ProbPtrs pp, const long long* __restrict__ dense_off, long nnz) {
@@ -343,17 +346,19 @@ __global__ void k_lu_extract(ProbPtrs pp, const long long* __restrict__ dense_of
   pp.ws[b][dense_off[k]] = J[3 * k] + pp.alpha[b] * J[3 * k + 1] + pp.beta[b] * J[3 * k + 2];
 }
 
-// Identity right-hand side next to Up: RHS = [Up_s | I] (n x (n_next + n)).
-__global__ void k_lu_rhs(ProbPtrs pp, size_t off_up_s, size_t off_rhs, int n, int nnext, int nmax) {
+// Right-hand side of slab s (n rows, width w): RHS = [Up_s | I] (w = n_next + n,
+// the inverse is kept) or, in single-solve mode, [Up_s | b_s] (w = n_next + 1).
+__global__ void k_lu_rhs(ProbPtrs pp, size_t off_up_s, size_t off_rhs, int n, int nnext, int nmax, int w, long o,
+                         int single) {
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int ldr = 2 * nmax;
-  if (e >= (long)n * ldr) return;
-  const int i = (int)(e / ldr), j = (int)(e % ldr);
+  if (e >= (long)n * w) return;
+  const int i = (int)(e / w), j = (int)(e % w);
   double* R = pp.ws[blockIdx.y] + off_rhs;
   double v;
-  if (j < nmax) v = j < nnext ? pp.ws[blockIdx.y][off_up_s + (size_t)i * nmax + j] : 0.0;
-  else v = (j - nmax == i) ? 1.0 : 0.0;
-  R[(size_t)i * ldr + j] = v;
+  if (j < nnext) v = pp.ws[blockIdx.y][off_up_s + (size_t)i * nmax + j];
+  else if (single) v = pp.b[blockIdx.y][(size_t)(o + i) * pp.ldb];
+  else v = (j - nnext == i) ? 1.0 : 0.0;
+  R[(size_t)i * w + j] = v;
 }
 
 // Panel factorization with partial pivoting of columns [j0, j0 + nb) of the
@@ -365,7 +370,13 @@ __global__ void k_lu_rhs(ProbPtrs pp, size_t off_up_s, size_t off_rhs, int n, in
 // candidates itself.  Ties go to the smallest row.
 constexpr int kPanelSmem = 220 * 1024;  // dynamic shared memory for the staged panel
 constexpr int kPanelThreads = 256;
-__device__ __forceinline__ void argmax_merge(double& v, int& i, double v2, int i2) {
+// Candidates are compared as the bit patterns of |x| (unsigned integers order
+// non-negative doubles like their values), which keeps the search off the
+// FP64 pipe; a NaN compares above every number and is flagged as singular.
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ void argmax_merge(unsigned long long& v, int& i, unsigned long long v2, int i2) {
   if (v2 > v || (v2 == v && i2 < i)) { v = v2; i = i2; }
 }
 __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t off_blk, int piv_off, int n, int ld,
@@ -375,7 +386,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t 
   double* A = pp.ws[b] + off_blk;
   int* piv = pp.piv[b] + piv_off;
   extern __shared__ double sp[];  // (n - j0) x nb, row-major with stride nb + 1 (no bank conflicts)
-  __shared__ double s_val[kWarps];
+  __shared__ unsigned long long s_val[kWarps];
   __shared__ int s_idx[kWarps];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int rows = n - j0, sl = nb + 1;
@@ -384,27 +395,28 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t 
     sp[(size_t)i * sl + c] = A[(size_t)(j0 + i) * ld + j0 + c];
   }
   __syncthreads();
-  auto warp_argmax = [&](double best, int bi) {
+  auto warp_argmax = [&](unsigned long long best, int bi) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+      const unsigned long long v2 = __shfl_xor_sync(0xffffffffu, best, o);
       const int i2 = __shfl_xor_sync(0xffffffffu, bi, o);
       argmax_merge(best, bi, v2, i2);
     }
     if (lane == 0) { s_val[warp] = best; s_idx[warp] = bi; }
   };
   {  // candidates for column 0
-    double best = -1.0;
+    unsigned long long best = 0;
     int bi = 0x7fffffff;
-    for (int i = tid; i < rows; i += kPanelThreads) argmax_merge(best, bi, fabs(sp[(size_t)i * sl]), i);
+    for (int i = tid; i < rows; i += kPanelThreads) argmax_merge(best, bi, abs_key(sp[(size_t)i * sl]), i);
     warp_argmax(best, bi);
   }
   __syncthreads();
   for (int jj = 0; jj < nb; ++jj) {
-    double pv = -1.0;
+    unsigned long long pk = 0;
     int pr = 0x7fffffff;
 #pragma unroll
-    for (int w = 0; w < kWarps; ++w) argmax_merge(pv, pr, s_val[w], s_idx[w]);
+    for (int w = 0; w < kWarps; ++w) argmax_merge(pk, pr, s_val[w], s_idx[w]);
+    double pv = __longlong_as_double((long long)pk);
     if (pr >= rows) { pr = jj; pv = 0.0; }
     if (tid == 0) {
       piv[j0 + jj] = j0 + pr;
@@ -422,14 +434,14 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t 
     if (dgn == 0.0) dgn = 1e-300;  // singular: flagged above, keep going without NaNs
     const double inv = 1.0 / dgn;
     const int w = nb - jj - 1;
-    double best = -1.0;
+    unsigned long long best = 0;
     int bi = 0x7fffffff;
     for (int i = jj + 1 + tid; i < rows; i += kPanelThreads) {
       double* ri = sp + (size_t)i * sl;
       const double l = ri[jj] * inv;
       ri[jj] = l;
       for (int c = 0; c < w; ++c) ri[jj + 1 + c] = fma(-l, rj[jj + 1 + c], ri[jj + 1 + c]);
-      if (w > 0) argmax_merge(best, bi, fabs(ri[jj + 1]), i);
+      if (w > 0) argmax_merge(best, bi, abs_key(ri[jj + 1]), i);
     }
     warp_argmax(best, bi);
     __syncthreads();
@@ -519,14 +531,21 @@ __global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L,
   }
 }
 
-__global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t off_inv, int n, int nnext, int nmax) {
+// W_s (first n_next columns) to the Up slot; then either S_s^{-1} to the
+// inverse slot or, in single-solve mode, y_s to the solution vector.
+__global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t off_inv, int n, int nnext, int nmax,
+                              int w, long o, int single) {
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= (long)n * nmax) return;
   const int i = (int)(e / nmax), j = (int)(e % nmax);
   double* ws = pp.ws[blockIdx.y];
-  const double* R = ws + off_rhs + (size_t)i * 2 * nmax;
+  const double* R = ws + off_rhs + (size_t)i * w;
   if (j < nnext) ws[off_w + (size_t)i * nmax + j] = R[j];
-  if (j < n) ws[off_inv + (size_t)i * nmax + j] = R[nmax + j];
+  if (single) {
+    if (j == 0) pp.y[blockIdx.y][(size_t)(o + i) * pp.ldb] = R[nnext];
+  } else if (j < n) {
+    ws[off_inv + (size_t)i * nmax + j] = R[nnext + j];
+  }
 }
 
 static int launch_panel(const ProbPtrs& pp, size_t offD, int poff, int n, int nmax, int j0, int nb, int nprob,
@@ -575,9 +594,15 @@ static ProbPtrs make_ptrs(BlockLU& lu, int nprob) {
 }
 
 int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, const double* alpha,
-                   const double* beta, int nprob, cudaStream_t s) {
+                   const double* beta, int nprob, cudaStream_t s, const double* const* b, double* const* y, int ldb) {
   if (nprob > lu.nprob) return fail(LRFSI_EINVAL, "block LU: more problems than allocated");
   ProbPtrs pp = make_ptrs(lu, nprob);
+  const int single = b != nullptr;
+  pp.ldb = ldb;
+  for (int q = 0; q < nprob; ++q) {
+    pp.b[q] = single ? b[q] : nullptr;
+    pp.y[q] = single ? y[q] : nullptr;
+  }
   for (int b = 0; b < nprob; ++b) {
     pp.J3[b] = J3[b];
     pp.alpha[b] = alpha[b];
@@ -635,11 +660,23 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
         LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
       }
     }
-    // RHS = P [Up_s | I];  L solve;  U solve  ->  [W_s | S_s^{-1}]
-    const int ldr = 2 * nmax;
+    // RHS = P [Up_s | I];  L solve;  U solve  ->  [W_s | S_s^{-1}]; in
+    // single-solve mode RHS = P [Up_s | b_s - Lo_{s-1} y_{s-1}] -> [W_s | y_s]
+    const int ldr = nnext + (single ? 1 : n);
+    const long o = lu.off[sl];
     k_lu_rhs<<<dim3(ceil_div((long)n * ldr, 256), nprob), 256, 0, s>>>(pp, lu.off_up + nb2 * sl, lu.off_rhs, n, nnext,
-                                                                       nmax);
+                                                                       nmax, ldr, o, single);
     LRFSI_TRY(check_launch("k_lu_rhs"));
+    if (single && sl > 0) {
+      const long op = lu.off[sl - 1];
+      const int np = (int)(o - op);
+      for (int q = 0; q < nprob; ++q) {
+        double* ws = pp.ws[q];
+        gd[q] = GemmDesc<double>{n, 1, np, ws + lu.off_lo + nb2 * (sl - 1), nmax, 1, y[q] + op * ldb, ldb, 1,
+                                 ws + lu.off_rhs + nnext, ldr, 1, -1.0, 1.0};
+      }
+      LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+    }
     {
       TimedLaunch tk(KC_LUPANEL, s);
       k_lu_laswp<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, lu.off_rhs, ldr, poff, 0, n, 0, ldr, 0, 0);
@@ -684,7 +721,8 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       }
     }
     k_lu_copy_out<<<dim3(ceil_div((long)n * nmax, 256), nprob), 256, 0, s>>>(pp, lu.off_rhs, lu.off_up + nb2 * sl,
-                                                                            lu.off_inv + nb2 * sl, n, nnext, nmax);
+                                                                            lu.off_inv + nb2 * sl, n, nnext, nmax,
+                                                                            ldr, o, single);
     LRFSI_TRY(check_launch("k_lu_copy_out"));
     // Schur complement of the next slab: D_{s+1} -= Lo_s W_s
     if (nnext > 0) {
@@ -696,11 +734,25 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
     }
   }
+  if (single) {  // backward sweep: x_s = y_s - W_s x_{s+1}
+    for (int sl = lu.nslab - 2; sl >= 0; --sl) {
+      const long o = lu.off[sl], on = lu.off[sl + 1];
+      const int n = (int)(on - o), nn = (int)(lu.off[sl + 2] - on);
+      for (int q = 0; q < nprob; ++q) {
+        double* ws = pp.ws[q];
+        gd[q] = GemmDesc<double>{n, 1, nn, ws + lu.off_up + nb2 * sl, nmax, 1, y[q] + on * ldb, ldb, 1,
+                                 y[q] + o * ldb, ldb, 1, -1.0, 1.0};
+      }
+      LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
+    }
+  }
   {
     double fl = 0;
     for (int sl = 0; sl < lu.nslab; ++sl) {
       const double n = (double)(lu.off[sl + 1] - lu.off[sl]);
-      fl += (2.0 / 3.0) * n * n * n + 4.0 * n * n * n + (sl + 1 < lu.nslab ? 2.0 * n * n * n : 0.0);
+      const double nn = sl + 1 < lu.nslab ? (double)(lu.off[sl + 2] - lu.off[sl + 1]) : 0.0;
+      // LU, the triangular solves on the right-hand side, the Schur update
+      fl += (2.0 / 3.0) * n * n * n + 2.0 * n * n * (nn + (single ? 1.0 : n)) + 2.0 * nn * nn * n;
     }
     account(KC_LU, fl * nprob, 0);
   }

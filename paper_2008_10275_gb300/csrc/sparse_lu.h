@@ -39,8 +39,14 @@ struct BlockLU {
 };
 int blocklu_alloc(const lrfsi_mesh_s* m, int nprob, BlockLU& lu);
 // J3[b] (device, nnz x 3) and the coefficients per problem.
+// Single-solve mode (b != nullptr): instead of keeping S_s^{-1}, the forward
+// sweep of one right-hand side per problem (b[q], stride ldb) is carried
+// through the factorisation and the backward sweep follows it, so that y[q]
+// (stride ldb) receives A_q^{-1} b[q]; the factors cannot be reused for
+// blocklu_solve afterwards.
 int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, const double* alpha,
-                   const double* beta, int nprob, cudaStream_t s);
+                   const double* beta, int nprob, cudaStream_t s, const double* const* b = nullptr,
+                   double* const* y = nullptr, int ldb = 0);
 // Y_b = A_b^{-1} X_b for r columns; X_b is overwritten (scratch).  X, Y: M x r, ld.
 int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r, int ld, int nprob,
                   cudaStream_t s);
