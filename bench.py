@@ -207,7 +207,7 @@ def run_learned(args, rank, world):
     k = 64
     ls = lrfsi.LearnedStart(mesh, k=k, seed=W.seed)
     Xtrain = Xt.T.contiguous()  # problem-major
-    ms_fit, loss = timed(lambda: ls.fit(Xtrain, mu_ts, nu_ts, epochs=3000, lr=2e-3))
+    ms_fit, loss = timed(lambda: ls.fit(Xtrain, mu_ts, nu_ts, epochs=12000, lr=2e-3))
     # evaluation on 2000 held-out parameters
     mu_e, nu_e = inputs.workload_parameters(W)
     for _ in range(max(1, args.warmup)):
@@ -228,7 +228,7 @@ def run_learned(args, rank, world):
         "plain": {**st_p, "ms": ms_plain, "params_per_s": m / (ms_plain * 1e-3)},
         "speedup_vs_plain": ms_plain / ms_learn,
         "rel_diff_learned_vs_plain_solution_update": diff,
-        "train": {"generate_ms": ms_gen, "fit_ms": ms_fit, "final_loss": loss, "epochs": 3000,
+        "train": {"generate_ms": ms_gen, "fit_ms": ms_fit, "final_loss": loss, "epochs": 12000,
                   "generate_status": st_t["status"], "generate_max_relres": st_t["max_relres"]},
     }
     print(json.dumps(line), flush=True)

@@ -326,8 +326,8 @@ int lrfsi_mlp_train(lrfsi_mlp_h mlp, const float* Z_dev, const float* T_dev, int
  *   Steps (all on the device): offset = mean snapshot; field_scale = RMS of the
  *   centred snapshots per field (v_x, v_y, u_x, u_y, p); POD of the centred,
  *   field-scaled snapshots (lrfsi_pod) into Phi (M x k, ldphi); coef_scale[l] =
- *   RMS of coefficient l; then epochs Adam steps (learning rate lr) fitting
- *   MLP(z_j) to the scaled coefficients.  The MLP must be 2 -> .. -> k and
+ *   RMS of coefficient l; then epochs Adam steps fitting MLP(z_j) to the scaled
+ *   coefficients, a third each at learning rate lr, lr / 4 and lr / 16.  The MLP must be 2 -> .. -> k and
  *   hold its initial parameters.  Outputs are caller-owned device arrays
  *   (coef_scale: k, field_scale and offset: M); loss_host / sigma_host (k) may
  *   be NULL.  Synchronizes the stream. */

@@ -145,7 +145,7 @@ int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
     }
     TimedLaunch tl(sizeof(T) == 8 ? KC_GEMM : KC_GEMM32, s);
     const long tiles64 = (long)ceil_div(nn, 64) * ceil_div(mm, 64) * cnt;
-    if (tiles64 >= kTarget || (mm >= 1024 && nn >= 64)) {
+    if (tiles64 >= kTarget) {  // enough 64x64 tiles to fill the GPU; else 32x32 tiles with split-K
       dim3 grid(ceil_div(nn, 64), ceil_div(mm, 64), cnt);
       k_gemm<T, 64, 64><<<grid, 256, 0, s>>>(gb, 1, (T*)nullptr, 0);
       LRFSI_TRY(check_launch("k_gemm"));

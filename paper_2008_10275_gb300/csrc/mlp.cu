@@ -480,7 +480,11 @@ int lrfsi_learned_fit(lrfsi_mesh_h mesh, lrfsi_mlp_h h, const double* mu_h, cons
   LRFSI_TRY(check_launch("k_coef_targets"));
   k_scale_params<<<ceil_div(n, 128), 128, 0, s>>>(mu.p, nu.p, n, box[0], box[1], box[2], box[3], Z.p);
   LRFSI_TRY(check_launch("k_scale_params"));
-  LRFSI_TRY(lrfsi_mlp_train(h, Z.p, T.p, n, epochs, lr, loss_host, stream));
+  // step schedule: a third of the epochs each at lr, lr / 4 and lr / 16
+  const int e1 = epochs / 3, e2 = epochs / 3, e3 = epochs - e1 - e2;
+  LRFSI_TRY(lrfsi_mlp_train(h, Z.p, T.p, n, e1, lr, nullptr, stream));
+  LRFSI_TRY(lrfsi_mlp_train(h, Z.p, T.p, n, e2, lr * 0.25f, nullptr, stream));
+  LRFSI_TRY(lrfsi_mlp_train(h, Z.p, T.p, n, e3, lr * 0.0625f, loss_host, stream));
   LRFSI_CUDA(cudaStreamSynchronize(s));
   return LRFSI_OK;
 }

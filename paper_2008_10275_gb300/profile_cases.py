@@ -4,10 +4,13 @@ timing outside the full step.
     python -m paper_2008_10275_gb300.profile_cases lu       # K block-LU factorisations (subset preconditioners)
     python -m paper_2008_10275_gb300.profile_cases trunc    # median Newton + two correction steps (truncations)
     python -m paper_2008_10275_gb300.profile_cases spmm     # FP64 and FP32 SpMM of the affine operators
+    python -m paper_2008_10275_gb300.profile_cases large    # 320 x 64 mesh: SpMM, block LU, solve, one ChebyshevT step
 
 Each case builds the 80 x 16 channel mesh (M = 22629) with the seeded
 parameters of the 400-parameter workload, runs the case twice (the first run
-warms up) and prints the CUDA-event time of the second run.
+warms up) and prints the CUDA-event time of the second run.  The large case
+uses the 320 x 64 mesh (M = 351621) and one subset of the first 100
+parameters of the 50 x 50 grid (rank cap 80), timed once each.
 """
 from __future__ import annotations
 
@@ -101,5 +104,79 @@ def case_spmm():
               f"(shape {v}, tuned ms {[round(float(t), 4) for t in tms]})")
 
 
+def case_large():
+    import json
+    import torch
+    from . import build, inputs, lrfsi
+    if not torch.cuda.is_available():
+        raise SystemExit("profile cases need a CUDA GPU")
+    build.build()
+    lrfsi.load()
+    dev = "cuda:0"
+    W = inputs.WORKLOADS["large"]
+    mesh = lrfsi.Mesh(W.nx, W.ny)
+    mus, nus = inputs.workload_parameters(W)
+    mus, nus = mus[:100], nus[:100]
+    R, m = W.rank_cap, 100
+    out = {"mesh": f"{W.nx}x{W.ny}", "M": mesh.M, "nnz": mesh.nnz, "slabs": mesh.nslab, "slab_max": mesh.nmax}
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    bD = torch.tensor(mesh.dirichlet(), device=dev)
+    # SpMM at r = R
+    J3 = torch.zeros(3 * mesh.nnz, dtype=torch.float64, device=dev)
+    lrfsi.lrfsi_assemble_affine(mesh, bD, J3, None)
+    Uh = np.random.default_rng(0).standard_normal((mesh.M, R))
+    for dt in (torch.float64, torch.float32):
+        U = torch.tensor(Uh, dtype=dt, device=dev)
+        Y = torch.zeros(mesh.M, 3 * R, dtype=dt, device=dev)
+        J = J3 if dt == torch.float64 else J3.to(torch.float32)
+        ms, _ = _timed(torch, lambda: lrfsi.lrfsi_spmm(mesh, J, U, R, R, Y, 3 * R), reps=10)
+        by = mesh.nnz * (3 * J.element_size() + 4) + (mesh.M + 1) * 4 + U.numel() * U.element_size() \
+            + Y.numel() * Y.element_size()
+        out[f"spmm_{str(dt)[6:]}"] = {"us": ms * 1e3, "GBs": by / (ms * 1e-3) / 1e9,
+                                       "TFLOPs": 6.0 * mesh.nnz * R / (ms * 1e-3) / 1e12}
+    del J3
+    # median Newton: two steps from b_D (two block-LU factorisations in single-solve mode)
+    med = m // 2
+    X = bD.repeat(1, 1)
+    e0, e1 = ev(), ev()
+    torch.cuda.synchronize(); e0.record()
+    it, res, st = lrfsi.lrfsi_newton_median(mesh, X, mus[med:med + 1], nus[med:med + 1], 1e-8, 2,
+                                            allow_noconv=True)
+    e1.record(); torch.cuda.synchronize()
+    out["newton_2_steps_ms"] = e0.elapsed_time(e1)
+    out["newton_residual_after_2"] = float(res[0])
+    # subset operators + preconditioner (assembly, equilibration, block LU keeping the inverses)
+    e0, e1 = ev(), ev()
+    e0.record()
+    sub = lrfsi.Subsets(mesh, X, mus, nus, [m], [R])
+    e1.record(); torch.cuda.synchronize()
+    out["subset_create_ms"] = e0.elapsed_time(e1)
+    # preconditioner solve with r = R right-hand sides (block-LU factors read once)
+    Xr = torch.tensor(np.random.default_rng(1).standard_normal((mesh.M, R)), device=dev)
+    Yr = torch.zeros(mesh.M, R, dtype=torch.float64, device=dev)
+    ms, _ = _timed(torch, lambda: lrfsi.lrfsi_precond_apply(sub, Xr.clone(), R, R, Yr, R), reps=3)
+    nb2 = mesh.nmax ** 2
+    lu_bytes = 8.0 * nb2 * (3 * mesh.nslab - 2)
+    out["precond_solve"] = {"ms": ms, "GBs": lu_bytes / (ms * 1e-3) / 1e9,
+                            "TFLOPs": 2.0 * R * nb2 * (3 * mesh.nslab - 2) / (ms * 1e-3) / 1e12}
+    # one ChebyshevT iteration on the subset's rank-3 Newton right-hand side
+    R3 = torch.zeros(mesh.M * 3, dtype=torch.float64, device=dev)
+    lrfsi.lrfsi_assemble_affine(mesh, X[0], None, R3)
+    VB = torch.tensor(-np.stack([np.ones(m), mus, nus], 1), device=dev)
+    U = torch.zeros(mesh.M * R, dtype=torch.float64, device=dev)
+    V = torch.zeros(m * R, dtype=torch.float64, device=dev)
+    for iters in (1, 3):
+        opt = lrfsi.cheb_options(0.65, 1.0, iters=iters, cycles=1, rank_cap=R, tol=W.tol)
+        e0, e1 = ev(), ev()
+        torch.cuda.synchronize(); e0.record()
+        ranks, st = lrfsi.lrfsi_chebyshevT(sub, R3, 3, VB, 3, [3], opt, U, R, V, R)
+        e1.record(); torch.cuda.synchronize()
+        out[f"chebyshevT_{iters}_iter_ms"] = e0.elapsed_time(e1)
+        out[f"chebyshevT_{iters}_iter_rel_lin_res"] = st[0]["rel_lin_res"]
+    out["chebyshevT_ms_per_step"] = (out["chebyshevT_3_iter_ms"] - out["chebyshevT_1_iter_ms"]) / 2
+    sub.close()
+    print(json.dumps(out))
+
+
 if __name__ == "__main__":
-    {"lu": case_lu, "trunc": case_trunc, "spmm": case_spmm}[sys.argv[1]]()
+    {"lu": case_lu, "trunc": case_trunc, "spmm": case_spmm, "large": case_large}[sys.argv[1]]()
