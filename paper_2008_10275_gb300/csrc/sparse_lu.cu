@@ -475,9 +475,10 @@ __global__ void k_lu_laswp(ProbPtrs pp, size_t off_mat, int ld, int piv_off, int
 // lanes share a column (lane q holds rows q, q+4, ...); the substitution is
 // column-oriented: once x_l is final its owner broadcasts it within the
 // four lanes and each lane updates its own rows, so no lane runs a long
-// dependent chain.  32 columns per CTA of 128 threads; the block is staged in
-// shared memory.
-constexpr int kTrsmCols = 32;
+// dependent chain.  16 columns per CTA of 64 threads (many CTAs: the FP64
+// pipes of more SMs); the block is staged in shared memory.
+constexpr int kTrsmCols = 16;
+constexpr int kTrsmThreads = 4 * kTrsmCols;
 __global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L, int ldl, size_t off_B, int ldb,
                                                       int i0, int nb, int c0, int c1, int upper) {
   __shared__ double Ls[32][33];
@@ -645,7 +646,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
         {
           account(KC_LUTRSM, (double)nprob * nb * nb * (n - j0 - nb), 0);
           TimedLaunch tk(KC_LUTRSM, s);
-          k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, kTrsmCols), nprob), 128, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
+          k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, kTrsmCols), nprob), kTrsmThreads, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
                                                                                 j0 + nb, n, 0);
           LRFSI_TRY(check_launch("k_lu_trsm_diag"));
           tk.end(s);
@@ -688,7 +689,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       {
         account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
         TimedLaunch tk(KC_LUTRSM, s);
-        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
+        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), kTrsmThreads, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
         LRFSI_TRY(check_launch("k_lu_trsm_diag"));
         tk.end(s);
       }
@@ -707,7 +708,7 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       {
         account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
         TimedLaunch tk(KC_LUTRSM, s);
-        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), 128, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
+        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), kTrsmThreads, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
         LRFSI_TRY(check_launch("k_lu_trsm_diag"));
         tk.end(s);
       }

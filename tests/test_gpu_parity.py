@@ -206,3 +206,54 @@ def test_spmm_parity_fp64_and_fp32(r):
                 assert rel_max(got[:, blk], ref[:, blk]) <= tol, (str(dt), t)
     v, ms = lrfsi.spmm_tuning(0, (r + 15) // 16 if r < 128 else 8)
     assert 0 <= v < 9 and ms[v] > 0
+
+
+def test_chebyshevT_parity_uneven_subsets_batched():
+    """Three subsets of uneven size and rank cap advance in the same launches;
+    each matches its own oracle solve (1e-10 per column, relative to the
+    subset's largest column)."""
+    lm, om, perm = _meshes(20, 4)
+    rng = np.random.default_rng(17)
+    sizes = [5, 12, 9]
+    K = len(sizes)
+    mus, nus, xts = [], [], []
+    for q, m in enumerate(sizes):
+        mu = np.sort(rng.uniform(6e5 + 2e5 * q, 8e5 + 2e5 * q, m))
+        nu = rng.uniform(2.5e-3, 3.5e-3, m)
+        med = params.upper_median_position(m)
+        xt, _, _ = newton.newton(om, mu[med], nu[med], eps=1e-11)
+        mus.append(mu); nus.append(nu); xts.append(xt)
+    mu_all, nu_all = np.concatenate(mus), np.concatenate(nus)
+    ld = max(sizes)
+    sub = lrfsi.Subsets(lm, _dev(np.stack([x[perm] for x in xts])), mu_all, nu_all, sizes, sizes)
+    UB = torch.zeros(K * lm.M * 3, dtype=torch.float64, device=DEV)
+    VB = torch.zeros(sum(sizes) * 3, dtype=torch.float64, device=DEV)
+    o = 0
+    for q, m in enumerate(sizes):
+        R0, Rmu, Rnu = fsi.affine_residual(om, xts[q])
+        UB[q * lm.M * 3:(q + 1) * lm.M * 3] = _dev(np.stack([R0, Rmu, Rnu], 1)[perm]).reshape(-1)
+        VB[o * 3:(o + m) * 3] = _dev(-np.stack([np.ones(m), mus[q], nus[q]], 1)).reshape(-1)
+        o += m
+    U = torch.zeros(K * lm.M * ld, dtype=torch.float64, device=DEV)
+    V = torch.zeros(sum(sizes) * ld, dtype=torch.float64, device=DEV)
+    c, d = 0.5, 1.0
+    opt = lrfsi.cheb_options(c, d, iters=6, cycles=2, rank_cap=ld, tol=1e-13)
+    ranks, _ = lrfsi.lrfsi_chebyshevT(sub, UB, 3, VB, 3, [3] * K, opt, U, ld, V, ld)
+    Uh, Vh = U.cpu().numpy(), V.cpu().numpy()
+    o = 0
+    for q, m in enumerate(sizes):
+        r = int(ranks[q])
+        Uq = Uh[q * lm.M * ld:(q + 1) * lm.M * ld].reshape(lm.M, ld)[:, :r]
+        Vq = Vh[o * ld:(o + m) * ld].reshape(m, ld)[:, :r]
+        S = Uq @ Vq.T
+        J0, Jmu, Jnu = fsi.affine_jacobian(om, xts[q])
+        R0, Rmu, Rnu = fsi.affine_residual(om, xts[q])
+        B = lowrank.rhs(R0, Rmu, Rnu, mus[q], nus[q])
+        mb, nb = params.midpoint_parameters(mus[q], nus[q])
+        So = lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B, mus[q], nus[q], mb, nb, c, d, iters=6, cycles=2, tol=1e-13,
+                                        rank_cap=m)[perm]
+        scale = np.linalg.norm(So, axis=0).max()
+        for j in range(m):
+            err = np.linalg.norm(S[:, j] - So[:, j]) / scale
+            assert err <= 1e-10, (q, j, err)
+        o += m
