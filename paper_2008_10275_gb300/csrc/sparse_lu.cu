@@ -532,22 +532,118 @@ __global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L,
   }
 }
 
-// W_s (first n_next columns) to the Up slot; then either S_s^{-1} to the
-// inverse slot or, in single-solve mode, y_s to the solution vector.
-__global__ void k_lu_copy_out(ProbPtrs pp, size_t off_rhs, size_t off_w, size_t off_inv, int n, int nnext, int nmax,
-                              int w, long o, int single) {
-  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long)n * nmax) return;
-  const int i = (int)(e / nmax), j = (int)(e % nmax);
-  double* ws = pp.ws[blockIdx.y];
-  const double* R = ws + off_rhs + (size_t)i * w;
-  if (j < nnext) ws[off_w + (size_t)i * nmax + j] = R[j];
-  if (single) {
-    if (j == 0) pp.y[blockIdx.y][(size_t)(o + i) * pp.ldb] = R[nnext];
-  } else if (j < n) {
-    ws[off_inv + (size_t)i * nmax + j] = R[nnext + j];
+// The right-hand-side phase of a slab in one launch: CTA (t, q) takes columns
+// [8t, 8t + 8) of problem q's right-hand side R (n x w), applies the row
+// interchanges, solves L (unit lower) then U (upper) of P S_s = L U, and
+// writes the columns to their destinations (W_s to the Up slot; S_s^{-1} to the
+// inverse slot or, in single-solve mode, y_s to the solution).  The columns
+// are independent, so the two triangular solves need no grid-wide step: per
+// 32-row block one warp solves the diagonal block (four lanes per column) and
+// then all threads update the remaining rows of the tile in shared memory.
+constexpr int kRhsCols = 8;
+constexpr int kRhsThreads = 128;
+__global__ void __launch_bounds__(kRhsThreads) k_lu_rhs_solve(ProbPtrs pp, size_t off_lu, int ld, int piv_off,
+                                                              size_t off_rhs, int w, int n, int nnext, size_t off_w,
+                                                              size_t off_inv, long o, int single) {
+  extern __shared__ double rsm[];
+  double* Bt = rsm;                                  // n x kRhsCols tile
+  double* Ls = rsm + (size_t)n * kRhsCols;           // 32 x 33 diagonal block
+  int* idx = reinterpret_cast<int*>(Ls + 32 * 33);   // row permutation (n)
+  const int q = blockIdx.y;
+  const double* A = pp.ws[q] + off_lu;
+  const double* R = pp.ws[q] + off_rhs;
+  const int* piv = pp.piv[q] + piv_off;
+  const int c0 = blockIdx.x * kRhsCols;
+  const int tid = threadIdx.x;
+  if (tid == 0) {  // the interchanges, applied in order, as one permutation
+    for (int i = 0; i < n; ++i) idx[i] = i;
+    for (int j = 0; j < n; ++j) {
+      const int p = piv[j];
+      if (p != j && p >= 0 && p < n) { const int t = idx[j]; idx[j] = idx[p]; idx[p] = t; }
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < n * kRhsCols; e += kRhsThreads) {
+    const int r = e / kRhsCols, c = e % kRhsCols;
+    Bt[e] = c0 + c < w ? R[(size_t)idx[r] * w + c0 + c] : 0.0;
+  }
+  const int lane = tid & 31, warp = tid >> 5;
+  const int lq = lane & 3, lbase = lane & ~3, lc = lane >> 2;  // diagonal solve: 4 lanes per column
+  for (int pass = 0; pass < 2; ++pass) {
+    const bool upper = pass == 1;
+    const int nblk = (n + 31) / 32;
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int blk = upper ? nblk - 1 - bb : bb;
+      const int i0 = blk * 32, nb = n - i0 < 32 ? n - i0 : 32;
+      __syncthreads();  // the tile rows of this block are final
+      for (int e = tid; e < 32 * 32; e += kRhsThreads) {
+        const int i = e >> 5, l = e & 31;
+        Ls[i * 33 + l] = (i < nb && l < nb) ? A[(size_t)(i0 + i) * ld + i0 + l] : 0.0;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        double x[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int i = lq + 4 * k;
+          x[k] = i < nb ? Bt[(size_t)(i0 + i) * kRhsCols + lc] : 0.0;
+        }
+        if (!upper) {
+#pragma unroll
+          for (int l = 0; l < 32; ++l) {
+            const double xl = __shfl_sync(0xffffffffu, x[l >> 2], lbase + (l & 3));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int i = lq + 4 * k;
+              if (i > l) x[k] = fma(-Ls[i * 33 + l], xl, x[k]);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int l = 31; l >= 0; --l) {
+            if (lq == (l & 3)) {
+              const double dg = Ls[l * 33 + l];
+              x[l >> 2] = (l < nb) ? x[l >> 2] / (dg == 0.0 ? 1e-300 : dg) : 0.0;
+            }
+            const double xl = __shfl_sync(0xffffffffu, x[l >> 2], lbase + (l & 3));
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+              const int i = lq + 4 * k;
+              if (i < l) x[k] = fma(-Ls[i * 33 + l], xl, x[k]);
+            }
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int i = lq + 4 * k;
+          if (i < nb) Bt[(size_t)(i0 + i) * kRhsCols + lc] = x[k];
+        }
+      }
+      __syncthreads();
+      // the rest of the tile: rows below (L) or above (U) the block
+      const int rlo = upper ? 0 : i0 + nb, rhi = upper ? i0 : n;
+      const int c = tid % kRhsCols;
+      for (int r = rlo + tid / kRhsCols; r < rhi; r += kRhsThreads / kRhsCols) {
+        const double* ar = A + (size_t)r * ld + i0;
+        double acc = Bt[(size_t)r * kRhsCols + c];
+#pragma unroll 8
+        for (int l = 0; l < nb; ++l) acc = fma(-ar[l], Bt[(size_t)(i0 + l) * kRhsCols + c], acc);
+        Bt[(size_t)r * kRhsCols + c] = acc;
+      }
+    }
+  }
+  __syncthreads();
+  double* ws = pp.ws[q];
+  for (int e = tid; e < n * kRhsCols; e += kRhsThreads) {
+    const int r = e / kRhsCols, c = e % kRhsCols, j = c0 + c;
+    if (j >= w) continue;
+    const double v = Bt[e];
+    if (j < nnext) ws[off_w + (size_t)r * ld + j] = v;
+    else if (single) pp.y[q][(size_t)(o + r) * pp.ldb] = v;
+    else ws[off_inv + (size_t)r * ld + (j - nnext)] = v;
   }
 }
+
 
 static int launch_panel(const ProbPtrs& pp, size_t offD, int poff, int n, int nmax, int j0, int nb, int nprob,
                         cudaStream_t s) {
@@ -557,12 +653,14 @@ static int launch_panel(const ProbPtrs& pp, size_t offD, int poff, int n, int nm
 
 int blocklu_alloc(const lrfsi_mesh_s* m, int nprob, BlockLU& lu) {
   if (nprob < 1 || nprob > kMaxGemmDescs) return fail(LRFSI_EINVAL, "block LU: 1..32 problems per batch");
-  if ((size_t)m->h.nmax * 9 * sizeof(double) > (size_t)kPanelSmem)
-    return fail(LRFSI_EINVAL, "block LU: slab larger than the panel kernel supports");
+  if ((size_t)m->h.nmax * 9 * sizeof(double) > (size_t)kPanelSmem ||
+      sizeof(double) * ((size_t)m->h.nmax * kRhsCols + 32 * 33) + sizeof(int) * (size_t)m->h.nmax > (size_t)kPanelSmem)
+    return fail(LRFSI_EINVAL, "block LU: slab larger than the panel kernels support");
   {
     static bool attr = false;
     if (!attr) {
       LRFSI_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem));
+      LRFSI_CUDA(cudaFuncSetAttribute(k_lu_rhs_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem));
       attr = true;
     }
   }
@@ -678,53 +776,15 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
       }
       LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
     }
-    {
-      TimedLaunch tk(KC_LUPANEL, s);
-      k_lu_laswp<<<dim3(ceil_div(ldr, 128), nprob), 128, 0, s>>>(pp, lu.off_rhs, ldr, poff, 0, n, 0, ldr, 0, 0);
-      LRFSI_TRY(check_launch("k_lu_laswp"));
+    {  // interchanges, L and U solves and the copy-out, columns in parallel
+      account(KC_LUTRSM, (double)nprob * n * n * ldr, 0);
+      TimedLaunch tk(KC_LUTRSM, s);
+      const size_t smem = sizeof(double) * ((size_t)n * kRhsCols + 32 * 33) + sizeof(int) * (size_t)n;
+      k_lu_rhs_solve<<<dim3(ceil_div(ldr, kRhsCols), nprob), kRhsThreads, smem, s>>>(
+          pp, offD, nmax, poff, lu.off_rhs, ldr, n, nnext, lu.off_up + nb2 * sl, lu.off_inv + nb2 * sl, o, single);
+      LRFSI_TRY(check_launch("k_lu_rhs_solve"));
       tk.end(s);
     }
-    for (int i0 = 0; i0 < n; i0 += kNb) {
-      const int nb = i0 + kNb < n ? kNb : n - i0;
-      {
-        account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
-        TimedLaunch tk(KC_LUTRSM, s);
-        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), kTrsmThreads, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 0);
-        LRFSI_TRY(check_launch("k_lu_trsm_diag"));
-        tk.end(s);
-      }
-      if (i0 + nb < n) {
-        for (int b = 0; b < nprob; ++b) {
-          double* A = pp.ws[b] + offD;
-          double* R = pp.ws[b] + lu.off_rhs;
-          gd[b] = GemmDesc<double>{n - i0 - nb, ldr, nb, A + (size_t)(i0 + nb) * nmax + i0, nmax, 1,
-                                   R + (size_t)i0 * ldr, ldr, 1, R + (size_t)(i0 + nb) * ldr, ldr, 1, -1.0, 1.0};
-        }
-        LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
-      }
-    }
-    for (int i0 = ((n - 1) / kNb) * kNb; i0 >= 0; i0 -= kNb) {
-      const int nb = i0 + kNb < n ? kNb : n - i0;
-      {
-        account(KC_LUTRSM, (double)nprob * nb * nb * ldr, 0);
-        TimedLaunch tk(KC_LUTRSM, s);
-        k_lu_trsm_diag<<<dim3(ceil_div(ldr, kTrsmCols), nprob), kTrsmThreads, 0, s>>>(pp, offD, nmax, lu.off_rhs, ldr, i0, nb, 0, ldr, 1);
-        LRFSI_TRY(check_launch("k_lu_trsm_diag"));
-        tk.end(s);
-      }
-      if (i0 > 0) {
-        for (int b = 0; b < nprob; ++b) {
-          double* A = pp.ws[b] + offD;
-          double* R = pp.ws[b] + lu.off_rhs;
-          gd[b] = GemmDesc<double>{i0, ldr, nb, A + i0, nmax, 1, R + (size_t)i0 * ldr, ldr, 1, R, ldr, 1, -1.0, 1.0};
-        }
-        LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
-      }
-    }
-    k_lu_copy_out<<<dim3(ceil_div((long)n * nmax, 256), nprob), 256, 0, s>>>(pp, lu.off_rhs, lu.off_up + nb2 * sl,
-                                                                            lu.off_inv + nb2 * sl, n, nnext, nmax,
-                                                                            ldr, o, single);
-    LRFSI_TRY(check_launch("k_lu_copy_out"));
     // Schur complement of the next slab: D_{s+1} -= Lo_s W_s
     if (nnext > 0) {
       for (int b = 0; b < nprob; ++b) {
