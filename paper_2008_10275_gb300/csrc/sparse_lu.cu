@@ -452,83 +452,102 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t 
   }
 }
 
-// Apply the row interchanges piv[j0..j1) to columns [c0, c1) of a matrix with
-// ld (one thread per column).
-__global__ void k_lu_laswp(ProbPtrs pp, size_t off_mat, int ld, int piv_off, int j0, int j1, int c0, int c1,
-                           int skip0, int skip1) {
-  const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= c1 || (c >= skip0 && c < skip1)) return;
-  double* A = pp.ws[blockIdx.y] + off_mat;
-  const int* piv = pp.piv[blockIdx.y] + piv_off;
-  for (int j = j0; j < j1; ++j) {
-    const int p = piv[j];
-    if (p != j) {
-      const double t = A[(size_t)j * ld + c];
-      A[(size_t)j * ld + c] = A[(size_t)p * ld + c];
-      A[(size_t)p * ld + c] = t;
+
+
+constexpr int kRhsCols = 8;      // columns per CTA of the column-parallel kernels
+constexpr int kRhsThreads = 128;
+// After the panel [j0, j0 + nb) of the slab block A (n x n, ld) is factored:
+// the row interchanges of the panel applied to every other column, then for
+// the columns right of the panel U12 = L11^{-1} A12 and A22 -= L21 U12.  The
+// columns are independent: CTA t takes 8 columns (the first ceil(j0 / 8) CTAs
+// the columns left of the panel, which only take the interchanges), stages
+// rows [j0, n) of its columns in shared memory, one warp solves the unit lower
+// diagonal block (four lanes per column) and all threads update the rows below.
+__global__ void __launch_bounds__(kRhsThreads) k_lu_panel_update(ProbPtrs pp, size_t off_lu, int ld, int piv_off, int n,
+                                                                 int j0, int nb) {
+  extern __shared__ double usm[];
+  const int q = blockIdx.y;
+  double* A = pp.ws[q] + off_lu;
+  const int* piv = pp.piv[q] + piv_off;
+  const int nleft = (j0 + kRhsCols - 1) / kRhsCols;
+  const bool left = (int)blockIdx.x < nleft;
+  const int cb = left ? blockIdx.x * kRhsCols : j0 + nb + (blockIdx.x - nleft) * kRhsCols;
+  const int ce = left ? min(cb + kRhsCols, j0) : min(cb + kRhsCols, n);
+  const int tid = threadIdx.x;
+  if (left) {  // interchanges only
+    if (tid < ce - cb) {
+      const int c = cb + tid;
+      for (int j = j0; j < j0 + nb; ++j) {
+        const int p = piv[j];
+        if (p != j && p >= 0 && p < n) {
+          const double t = A[(size_t)j * ld + c];
+          A[(size_t)j * ld + c] = A[(size_t)p * ld + c];
+          A[(size_t)p * ld + c] = t;
+        }
+      }
+    }
+    return;
+  }
+  const int rows = n - j0;
+  double* Bt = usm;                                  // rows x 8 tile (rows j0..n-1)
+  double* Ls = usm + (size_t)rows * kRhsCols;        // 32 x 33: L11
+  int* idx = reinterpret_cast<int*>(Ls + 32 * 33);   // row permutation of rows j0..n-1
+  if (tid == 0) {
+    for (int i = 0; i < rows; ++i) idx[i] = i;
+    for (int j = j0; j < j0 + nb; ++j) {
+      const int p = piv[j];
+      if (p != j && p >= j0 && p < n) { const int t = idx[j - j0]; idx[j - j0] = idx[p - j0]; idx[p - j0] = t; }
     }
   }
-}
-
-// Triangular solve of a diagonal nb x nb block (nb <= 32) for columns
-// [c0, c1) of B: unit lower forward or upper backward substitution.  Four
-// lanes share a column (lane q holds rows q, q+4, ...); the substitution is
-// column-oriented: once x_l is final its owner broadcasts it within the
-// four lanes and each lane updates its own rows, so no lane runs a long
-// dependent chain.  16 columns per CTA of 64 threads (many CTAs: the FP64
-// pipes of more SMs); the block is staged in shared memory.
-constexpr int kTrsmCols = 16;
-constexpr int kTrsmThreads = 4 * kTrsmCols;
-__global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L, int ldl, size_t off_B, int ldb,
-                                                      int i0, int nb, int c0, int c1, int upper) {
-  __shared__ double Ls[32][33];
-  const double* L = pp.ws[blockIdx.y] + off_L;
-  double* B = pp.ws[blockIdx.y] + off_B;
-  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+  for (int e = tid; e < 32 * 32; e += kRhsThreads) {
     const int i = e >> 5, l = e & 31;
-    Ls[i][l] = (i < nb && l < nb) ? L[(size_t)(i0 + i) * ldl + i0 + l] : 0.0;
+    Ls[i * 33 + l] = (i < nb && l < nb) ? A[(size_t)(j0 + i) * ld + j0 + l] : 0.0;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, q = lane & 3, base = lane & ~3;
-  const int c = c0 + blockIdx.x * kTrsmCols + (threadIdx.x >> 2);
-  const bool active = c < c1;
-  double x[8];
-#pragma unroll
-  for (int k = 0; k < 8; ++k) {
-    const int i = q + 4 * k;
-    x[k] = (active && i < nb) ? B[(size_t)(i0 + i) * ldb + c] : 0.0;
+  for (int e = tid; e < rows * kRhsCols; e += kRhsThreads) {
+    const int r = e / kRhsCols, c = e % kRhsCols;
+    Bt[e] = cb + c < ce ? A[(size_t)(j0 + idx[r]) * ld + cb + c] : 0.0;
   }
-  if (!upper) {
-#pragma unroll
-    for (int l = 0; l < 32; ++l) {
-      const double xl = __shfl_sync(0xffffffffu, x[l >> 2], base + (l & 3));
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int i = q + 4 * k;
-        if (i > l) x[k] = fma(-Ls[i][l], xl, x[k]);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int l = 31; l >= 0; --l) {
-      if (q == (l & 3)) {
-        const double dg = Ls[l][l];
-        x[l >> 2] = (l < nb) ? x[l >> 2] / (dg == 0.0 ? 1e-300 : dg) : 0.0;
-      }
-      const double xl = __shfl_sync(0xffffffffu, x[l >> 2], base + (l & 3));
-#pragma unroll
-      for (int k = 0; k < 8; ++k) {
-        const int i = q + 4 * k;
-        if (i < l) x[k] = fma(-Ls[i][l], xl, x[k]);
-      }
-    }
-  }
-  if (active) {
+  __syncthreads();
+  const int lane = tid & 31, warp = tid >> 5;
+  if (warp == 0) {  // U12 = L11^{-1} A12 (unit lower)
+    const int lq = lane & 3, lbase = lane & ~3, lc = lane >> 2;
+    double x[8];
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-      const int i = q + 4 * k;
-      if (i < nb) B[(size_t)(i0 + i) * ldb + c] = x[k];
+      const int i = lq + 4 * k;
+      x[k] = i < nb ? Bt[(size_t)i * kRhsCols + lc] : 0.0;
     }
+#pragma unroll
+    for (int l = 0; l < 32; ++l) {
+      const double xl = __shfl_sync(0xffffffffu, x[l >> 2], lbase + (l & 3));
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const int i = lq + 4 * k;
+        if (i > l) x[k] = fma(-Ls[i * 33 + l], xl, x[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const int i = lq + 4 * k;
+      if (i < nb) Bt[(size_t)i * kRhsCols + lc] = x[k];
+    }
+  }
+  __syncthreads();
+  {  // A22 -= L21 U12 on the tile (L21 = rows j0 + nb.. of the panel, already swapped by the panel kernel)
+    const int c = tid % kRhsCols;
+    for (int r = nb + tid / kRhsCols; r < rows; r += kRhsThreads / kRhsCols) {
+      const double* ar = A + (size_t)(j0 + r) * ld + j0;
+      double acc = Bt[(size_t)r * kRhsCols + c];
+#pragma unroll 8
+      for (int l = 0; l < nb; ++l) acc = fma(-ar[l], Bt[(size_t)l * kRhsCols + c], acc);
+      Bt[(size_t)r * kRhsCols + c] = acc;
+    }
+  }
+  __syncthreads();
+  for (int e = tid; e < rows * kRhsCols; e += kRhsThreads) {
+    const int r = e / kRhsCols, c = e % kRhsCols;
+    if (cb + c < ce) A[(size_t)(j0 + r) * ld + cb + c] = Bt[e];
   }
 }
 
@@ -540,8 +559,6 @@ __global__ void __launch_bounds__(128) k_lu_trsm_diag(ProbPtrs pp, size_t off_L,
 // are independent, so the two triangular solves need no grid-wide step: per
 // 32-row block one warp solves the diagonal block (four lanes per column) and
 // then all threads update the remaining rows of the tile in shared memory.
-constexpr int kRhsCols = 8;
-constexpr int kRhsThreads = 128;
 __global__ void __launch_bounds__(kRhsThreads) k_lu_rhs_solve(ProbPtrs pp, size_t off_lu, int ld, int piv_off,
                                                               size_t off_rhs, int w, int n, int nnext, size_t off_w,
                                                               size_t off_inv, long o, int single) {
@@ -661,6 +678,7 @@ int blocklu_alloc(const lrfsi_mesh_s* m, int nprob, BlockLU& lu) {
     if (!attr) {
       LRFSI_CUDA(cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem));
       LRFSI_CUDA(cudaFuncSetAttribute(k_lu_rhs_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem));
+      LRFSI_CUDA(cudaFuncSetAttribute(k_lu_panel_update, cudaFuncAttributeMaxDynamicSharedMemorySize, kPanelSmem));
       attr = true;
     }
   }
@@ -733,30 +751,18 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
         LRFSI_TRY(launch_panel(pp, offD, poff, n, nmax, j0, nb, nprob, s));
         tk.end(s);
       }
-      // interchanges to the left and right of the panel
+      // interchanges left and right of the panel, U12 and the trailing update, columns in parallel
       {
-        TimedLaunch tk(KC_LUPANEL, s);
-        k_lu_laswp<<<dim3(ceil_div(n, 128), nprob), 128, 0, s>>>(pp, offD, nmax, poff, j0, j0 + nb, 0, n, j0, j0 + nb);
-        LRFSI_TRY(check_launch("k_lu_laswp"));
-        tk.end(s);
-      }
-      if (j0 + nb < n) {
-        {
-          account(KC_LUTRSM, (double)nprob * nb * nb * (n - j0 - nb), 0);
+        const int ncols = ceil_div(j0, kRhsCols) + ceil_div(n - j0 - nb, kRhsCols);
+        if (ncols > 0) {
+          account(KC_LUTRSM, (double)nprob * ((double)nb * nb * (n - j0 - nb) +
+                                              2.0 * (double)(n - j0 - nb) * (n - j0 - nb) * nb), 0);
           TimedLaunch tk(KC_LUTRSM, s);
-          k_lu_trsm_diag<<<dim3(ceil_div(n - j0 - nb, kTrsmCols), nprob), kTrsmThreads, 0, s>>>(pp, offD, nmax, offD, nmax, j0, nb,
-                                                                                j0 + nb, n, 0);
-          LRFSI_TRY(check_launch("k_lu_trsm_diag"));
+          const size_t smem = sizeof(double) * ((size_t)(n - j0) * kRhsCols + 32 * 33) + sizeof(int) * (size_t)(n - j0);
+          k_lu_panel_update<<<dim3(ncols, nprob), kRhsThreads, smem, s>>>(pp, offD, nmax, poff, n, j0, nb);
+          LRFSI_TRY(check_launch("k_lu_panel_update"));
           tk.end(s);
         }
-        for (int b = 0; b < nprob; ++b) {
-          double* A = pp.ws[b] + offD;
-          gd[b] = GemmDesc<double>{n - j0 - nb, n - j0 - nb, nb,
-                                   A + (size_t)(j0 + nb) * nmax + j0, nmax, 1,
-                                   A + (size_t)j0 * nmax + j0 + nb, nmax, 1,
-                                   A + (size_t)(j0 + nb) * nmax + j0 + nb, nmax, 1, -1.0, 1.0};
-        }
-        LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
       }
     }
     // RHS = P [Up_s | I];  L solve;  U solve  ->  [W_s | S_s^{-1}]; in
