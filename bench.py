@@ -137,8 +137,10 @@ def run_learned(args, rank, world):
     """The learned-start workload: an MLP trained on 500 method-generated
     solutions (Latin hypercube parameters, 5 subsets of 100) starts both the
     median Newton iterations and the subset steps for 2000 held-out uniform
-    parameters (20 subsets of 100, nu_f-major order); compared with the plain
-    method (median Newton from b_D, subset step from the median solution)."""
+    parameters (20 subsets of 100, nu_f-major order).  Three arms on the same
+    parameters: the plain FP64 method (median Newton from b_D, subset step
+    from the median solution), the learned start in FP64, and the learned
+    start with the mixed-precision inner residual (the line's value)."""
     import torch
     from paper_2008_10275_gb300 import build, lrfsi
     build.build()
@@ -148,8 +150,8 @@ def run_learned(args, rank, world):
     mesh = lrfsi.Mesh(W.nx, W.ny)
     M, R = mesh.M, W.rank_cap
     bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=dev)
-    opt = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=args.precision,
-                             eta=args.eta)
+    opts = [lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=pr, eta=args.eta)
+            for pr in (0, 1)]
 
     def layout(mus, nus, K):
         o = np.lexsort((mus, nus))  # nu_f-major, as the grids' little-endian order
@@ -157,8 +159,9 @@ def run_learned(args, rank, world):
         sizes, medians = subset_layout(len(mus), K)
         return mus, nus, sizes, medians
 
-    def solve(mus, nus, K, ls=None):
+    def solve(mus, nus, K, ls=None, precision=0):
         """Method on (mus, nus): returns dense solutions (M x m) and stats."""
+        opt = opts[precision]
         mus, nus, sizes, medians = layout(mus, nus, K)
         m = len(mus)
         X = bD.repeat(K, 1)
@@ -213,21 +216,27 @@ def run_learned(args, rank, world):
     for _ in range(max(1, args.warmup)):
         solve(mu_e[:200], nu_e[:200], 2)
         solve(mu_e[:200], nu_e[:200], 2, ls)
+        solve(mu_e[:200], nu_e[:200], 2, ls, 1)
     ms_plain, (Xp, st_p) = timed(lambda: solve(mu_e, nu_e, W.K))
-    ms_learn, (Xl, st_l) = timed(lambda: solve(mu_e, nu_e, W.K, ls))
+    ms_l64, (Xl64, st_l64) = timed(lambda: solve(mu_e, nu_e, W.K, ls))
+    ms_learn, (Xl, st_l) = timed(lambda: solve(mu_e, nu_e, W.K, ls, 1))
     diff = float(torch.linalg.norm(Xl - Xp) / torch.linalg.norm(Xp - bD[:, None]))
+    diff64 = float(torch.linalg.norm(Xl64 - Xp) / torch.linalg.norm(Xp - bD[:, None]))
     m = len(mu_e)
     line = {
         "metric": METRIC, "value": m / (ms_learn * 1e-3), "unit": "params/s", "n_gpus": 1, "steps": 1,
         "warmup": args.warmup, "ms_per_step": ms_learn, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == 0 else "f64+f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "M": M, "params": m, "subsets": W.K, "rank_cap": R,
                    "train": "500 method solutions at Latin-hypercube parameters", "pod_rank": k,
                    "mlp": "2-128-128-64 GELU, BF16 weights"},
-        "learned": {**st_l, "ms": ms_learn, "params_per_s": m / (ms_learn * 1e-3)},
-        "plain": {**st_p, "ms": ms_plain, "params_per_s": m / (ms_plain * 1e-3)},
-        "speedup_vs_plain": ms_plain / ms_learn,
-        "rel_diff_learned_vs_plain_solution_update": diff,
+        "learned_mixed": {**st_l, "ms": ms_learn, "params_per_s": m / (ms_learn * 1e-3)},
+        "learned_fp64": {**st_l64, "ms": ms_l64, "params_per_s": m / (ms_l64 * 1e-3)},
+        "plain_fp64": {**st_p, "ms": ms_plain, "params_per_s": m / (ms_plain * 1e-3)},
+        "speedup_learned_mixed_vs_plain_fp64": ms_plain / ms_learn,
+        "speedup_learned_fp64_vs_plain_fp64": ms_plain / ms_l64,
+        "rel_diff_learned_mixed_vs_plain_fp64_solution_update": diff,
+        "rel_diff_learned_fp64_vs_plain_fp64_solution_update": diff64,
         "train": {"generate_ms": ms_gen, "fit_ms": ms_fit, "final_loss": loss, "epochs": 12000,
                   "generate_status": st_t["status"], "generate_max_relres": st_t["max_relres"]},
     }
@@ -361,9 +370,17 @@ def main():
         ms_m = e4.elapsed_time(e5) / args.steps
         Xm = dense_solution(info_m)
         diff = float(torch.linalg.norm(Xm - X64) / torch.linalg.norm(X64 - bD[:, None]))
+        # where the mixed step spends its time (one more step with per-launch events)
+        lrfsi.stats_reset()
+        lrfsi.timing(True)
+        step(mus, nus, opt_mixed)
+        torch.cuda.synchronize()
+        ksm = lrfsi.kernel_stats()
+        lrfsi.timing(False)
         mixed = {"value": world * m / (ms_m * 1e-3), "ms_per_step": ms_m, "max_relres": info_m["max_relres"],
                  "status": info_m["status"], "outer": info_m["outer"],
-                 "rel_diff_vs_fp64_solution_update": diff}
+                 "rel_diff_vs_fp64_solution_update": diff,
+                 "per_class_ms": {k: round(v["ms"], 3) for k, v in ksm.items() if v["ms"] > 0}}
 
     # end to end through the public API: host parameter arrays in, factors and
     # relative residuals back to host memory every step

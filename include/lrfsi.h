@@ -187,7 +187,9 @@ typedef struct {
   int rank_cap;       /* R: maximal rank kept by the truncation */
   double tol;         /* truncation: keep the smallest r with ||s_{>r}|| <= tol ||s|| */
   double eta;         /* stop when ||B - F(S)||_F <= eta ||B||_F (0: run all steps) */
-  int precision;      /* 0: FP64; 1: mixed (FP32 SpMM and updates, FP64 truncation/LU) */
+  int precision;      /* 0: FP64; 1: mixed: the inner residual B - F(S) in FP32 (SpMM
+                         and GEMM, FP32 accumulation), truncated at 1e-6 (its noise
+                         level); LU, Gram products, SVD and the outer loop in FP64 */
   double tol_sol;     /* lrfsi_subset_step: truncation tolerance of the accumulated solution
                          (0: 1e-6 * tol).  In the equilibrated norm a deformation error of
                          relative size e costs about 1e6 e in the unscaled relative residual,

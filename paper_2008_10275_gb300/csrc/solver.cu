@@ -786,11 +786,11 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
 // times (the lost relative remainder grows from 1e-7 to 1e-4 of a column).
 static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
                           const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
-                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s) {
+                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s, double drop0 = 1e-14) {
   std::vector<int> broke, todo = act;
   rank.assign(S->K, 0);
   frob2.assign(S->K, 0.0);
-  double drop = 1e-14;
+  double drop = drop0;
   for (int attempt = 0; attempt < 4 && !todo.empty(); ++attempt, drop *= 100.0) {
     std::vector<int> rk;
     std::vector<double> f2;
@@ -1108,7 +1108,14 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
       LRFSI_TRY((convert_batched<float, double>(c2, s)));
     }
     LRFSI_TRY(copy_batched(cd2, s));
-    LRFSI_TRY(truncate_batch(S, L, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
+    // a residual formed in FP32 carries rounding noise of ~1e-7 of its terms in
+    // every direction: it is truncated at that level (tolerance 1e-6, pivoted
+    // Cholesky remainder 1e-6) instead of resolving the noise
+    if (o.precision == 1) {
+      LRFSI_TRY(truncate_batch(S, L, p, std::max(o.tol, 1e-6), S->cap, Uo, Vo, rk, f2, s, 1e-12));
+    } else {
+      LRFSI_TRY(truncate_batch(S, L, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
+    }
     nres.assign(K, 0.0);
     for (int k : L) {
       rR[k] = rk[k];
