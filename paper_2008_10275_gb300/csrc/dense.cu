@@ -580,7 +580,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs) {
 //       back, followed by a cluster barrier.
 // Every block pair meets once per sweep, so every column pair is visited; the
 // pairing and the order of rotations are fixed, so the result does not depend
-// on timing.  A pair is rotated when |a_x . a_y| > 4 eps sqrt(|a_x|^2
+// on timing.  A pair is rotated when |a_x . a_y| > 2e-15 sqrt(|a_x|^2
 // |a_y|^2) and neither column is below eps times the largest column norm.
 // Stops after a sweep without rotations (info[3] = sweeps) or at 40 sweeps
 // (info[2] = LRFSI_ENOCONV).  The FP64 rate of one SM is the bound here, hence
@@ -603,10 +603,14 @@ __device__ __forceinline__ bool jacobi_pair(double* __restrict__ cx, double* __r
     be += __shfl_xor_sync(0xffffffffu, be, o);
     ga += __shfl_xor_sync(0xffffffffu, ga, o);
   }
-  if (!(al > small2 && be > small2 && fabs(ga) > 4.4e-16 * sqrt(al * be))) return false;
-  const double zeta = (be - al) / (2.0 * ga);
-  const double t = (zeta >= 0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  const double c = 1.0 / sqrt(1.0 + t * t), sn = c * t;
+  // rotate when |a_x . a_y| > 2e-15 |a_x| |a_y| (squared: no square root)
+  if (!(al > small2 && be > small2 && ga * ga > 4e-30 * al * be)) return false;
+  // t = tan of the rotation angle, the smaller root of t^2 + 2 zeta t - 1 = 0
+  // with zeta = (be - al) / (2 ga), written without dividing by ga:
+  // t = sign(tau) g2 / (|tau| + sqrt(tau^2 + g2^2)), tau = be - al, g2 = 2 ga
+  const double tau = be - al, g2 = 2.0 * ga;
+  const double t = (tau >= 0 ? g2 : -g2) / (fabs(tau) + sqrt(fma(tau, tau, g2 * g2)));
+  const double c = rsqrt(fma(t, t, 1.0)), sn = c * t;
   for (int i = lane; i < LV; i += 32) {
     const double u = cx[i], v = cy[i];
     cx[i] = c * u - sn * v;
