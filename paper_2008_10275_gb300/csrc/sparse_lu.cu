@@ -455,7 +455,7 @@ __global__ void __launch_bounds__(kPanelThreads) k_lu_panel(ProbPtrs pp, size_t 
 
 
 constexpr int kRhsCols = 8;      // columns per CTA of the column-parallel kernels
-constexpr int kRhsThreads = 256;
+constexpr int kRhsThreads = 512;
 // After the panel [j0, j0 + nb) of the slab block A (n x n, ld) is factored:
 // the row interchanges of the panel applied to every other column, then for
 // the columns right of the panel U12 = L11^{-1} A12 and A22 -= L21 U12.  The
