@@ -380,7 +380,9 @@ def main():
         mixed = {"value": world * m / (ms_m * 1e-3), "ms_per_step": ms_m, "max_relres": info_m["max_relres"],
                  "status": info_m["status"], "outer": info_m["outer"],
                  "rel_diff_vs_fp64_solution_update": diff,
-                 "per_class_ms": {k: round(v["ms"], 3) for k, v in ksm.items() if v["ms"] > 0}}
+                 "per_class_ms": {k: round(v["ms"], 3) for k, v in ksm.items() if v["ms"] > 0},
+                 "spmm_fp32_gbs": (ksm["spmm_fp32"]["bytes"] / (ksm["spmm_fp32"]["ms"] * 1e-3) / 1e9
+                                   if ksm["spmm_fp32"]["ms"] > 0 else None)}
 
     # end to end through the public API: host parameter arrays in, factors and
     # relative residuals back to host memory every step
