@@ -8,8 +8,8 @@ subset compute the Newton solution x~ of the upper-median problem (stop at
 matrix equation F(S_k) = B_k solved by the truncated Chebyshev iteration with
 the mean-based preconditioner; X^k = x~ 1^T + S_k.
 
-Reading for accuracy targets the paper does not reach in one step (listed in
-the design doc): ``chord_steps`` further subset corrections in the same matrix
+Reading for accuracy targets the paper does not reach in one step:
+``chord_steps`` further subset corrections in the same matrix
 form, the right-hand side being minus the per-column residuals
 R(X_i; mu_i, nu_i) and the operators and preconditioner kept at x~.
 

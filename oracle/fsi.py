@@ -9,7 +9,7 @@ deformation in Q2 (biquadratic), pressure in Q1 (bilinear) on a structured
 quadrilateral mesh of the channel [0, Lx] x [0, Ly] with the elastic flap S
 attached to the bottom wall.
 
-Readings of the paper that this file fixes (all listed in the design doc):
+Readings of the paper that this file fixes:
 
 * Gradient convention (grad u)_ij = d u_i / d x_j; the solid terms are taken
   literally from Eq. (fsi_problem_weak1): mu_s <G + G^T + G^T G, grad phi>_S and

@@ -5,7 +5,7 @@ x_j = x_{j-1} + dx_j, started at x_0 = b_D (or a given start), stopped when
 the Euclidean residual norm is <= eps_N (Algorithm 1, Sec. 5.1).  The linear
 solve is a sparse direct LU (SuperLU via scipy, a library primitive).
 
-Safeguard that the paper does not state (listed in the design doc): if the full
+Safeguard that the paper does not state: if the full
 step increases the residual norm, the step is halved up to 20 times.
 """
 from __future__ import annotations
