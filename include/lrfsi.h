@@ -31,6 +31,10 @@
  *   values (norms, ranks, iteration counts) synchronize that stream.
  * - All arithmetic named FP64 is IEEE binary64; the mixed mode runs the inner
  *   Chebyshev correction in binary32 inside an FP64 refinement loop.
+ * - Concurrency: calls on one handle must not overlap, and the library keeps
+ *   process-wide scratch (the split-K GEMM workspace, the SpMM autotuner
+ *   table), so calls from several host threads must be serialised by the
+ *   caller.  One device per process (the current device at each call).
  */
 #ifndef LRFSI_H
 #define LRFSI_H
