@@ -31,6 +31,7 @@ from paper_2008_10275_gb300 import inputs, multi  # noqa: E402
 
 METRIC = "parameter solves/sec to nonlinear rel. residual 1e-6"
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (profiling recipe's table)
+EPS_N = 1e-6                 # median Newton stopping tolerance ||R||_2 (the paper's epsilon_N, Sec. 5)
 
 
 def subset_layout(m, K):
@@ -96,7 +97,7 @@ W = inputs.WORKLOADS[{workload!r}]
 mus, nus = inputs.workload_parameters(W)
 m = fsi.Mesh(fsi.Problem(W.nx, W.ny))
 t = time.perf_counter()
-X, steps, norms = newton.standard_newton(m, mus[:{n_sample}], nus[:{n_sample}], eps=1e-8)
+X, steps, norms = newton.standard_newton(m, mus[:{n_sample}], nus[:{n_sample}], eps={EPS_N!r})
 dt = time.perf_counter() - t
 print(json.dumps(dict(seconds=dt, steps=int(steps), n={n_sample})))
 """
@@ -126,7 +127,7 @@ def run_reference(args, rank, world):
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "sample_params": args.ref_sample},
         "cpu_baseline": {"value": v, "unit": "params/s", "cores": 1, "kind": "oracle",
-                         "sample": f"standard Newton (eps 1e-8) on the first {args.ref_sample} parameters"},
+                         "sample": f"standard Newton (eps {EPS_N:g}) on the first {args.ref_sample} parameters"},
         "e2e": {"value": v, "unit": "params/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -167,7 +168,7 @@ def run_learned(args, rank, world):
         X = bD.repeat(K, 1)
         if ls is not None:  # learned start of the median Newton iterations
             ls.start(mus[medians], nus[medians], X)
-        it, res, _ = lrfsi.lrfsi_newton_median(mesh, X, mus[medians], nus[medians], 1e-8, 30)
+        it, res, _ = lrfsi.lrfsi_newton_median(mesh, X, mus[medians], nus[medians], EPS_N, 30)
         sub = lrfsi.Subsets(mesh, X, mus, nus, sizes, [R] * K)
         U = torch.zeros(K * M * R, dtype=torch.float64, device=dev)
         V = torch.zeros(m * R, dtype=torch.float64, device=dev)
@@ -302,7 +303,7 @@ def main():
     R = max(caps)
     U = torch.zeros(K * mesh.M * R, dtype=torch.float64, device=dev)
     V = torch.zeros(m * R, dtype=torch.float64, device=dev)
-    eps_N = 1e-8
+    eps_N = EPS_N
 
     opt_mixed = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=1,
                                    eta=args.eta)
@@ -442,7 +443,7 @@ def main():
         try:
             r = cpu_reference(args.workload, args.ref_sample)
             cpu = {"value": r["n"] / r["seconds"], "unit": "params/s", "cores": 1, "kind": "oracle",
-                   "sample": f"standard Newton (eps 1e-8) on the first {args.ref_sample} of {m} parameters, "
+                   "sample": f"standard Newton (eps {EPS_N:g}) on the first {args.ref_sample} of {m} parameters, "
                              f"{r['steps']} Newton steps, {r['seconds']:.1f} s"}
         except Exception as ex:  # reported, not fatal
             cpu = {"value": None, "unit": "params/s", "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"[:200]}
