@@ -581,7 +581,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs) {
 // Every block pair meets once per sweep, so every column pair is visited; the
 // pairing and the order of rotations are fixed, so the result does not depend
 // on timing.  A pair is rotated when |a_x . a_y| > 2e-15 sqrt(|a_x|^2
-// |a_y|^2) and neither column is below eps times the largest column norm.
+// |a_y|^2) and neither column is below max(1e-16, 1e-2 tol) times the largest
+// column norm (such columns lie below what the truncation keeps).
 // Stops after a sweep without rotations (info[3] = sweeps) or at 40 sweeps
 // (info[2] = LRFSI_ENOCONV).  The FP64 rate of one SM is the bound here, hence
 // the cluster: the rotations of one problem run on C SMs.
@@ -706,7 +707,10 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     __syncthreads();
   };
   exchange(1, 0.0, local_cmax(home, 2 * b, j0, n, L, LV));
-  double small2 = s_cm * 1e-32;
+  // columns below 1e-2 tol of the largest column norm cannot affect what the
+  // truncation keeps (its tail is measured at tol): they are not rotated
+  const double zfac = fmax(1e-32, (1e-2 * d.tol) * (1e-2 * d.tol));
+  double small2 = s_cm * zfac;
   int sweeps = -1;
   for (int t = 0; t < 40; ++t) {
     if (tid == 0) s_rot = 0;
@@ -757,7 +761,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
     exchange(t & 1, (double)s_rot, local_cmax(home, 2 * b, j0, n, L, LV));
-    small2 = s_cm * 1e-32;
+    small2 = s_cm * zfac;
     if (s_tot == 0.0) { sweeps = t + 1; break; }
   }
   // final columns to global memory: A (L x n) and V (n x n), column-major;
