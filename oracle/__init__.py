@@ -24,7 +24,8 @@ Contents (each function cites the passage of the paper it follows):
                    (rhs_matrix1), Eq. (newton_matrix1)), its brute-force
                    column-by-column solution (Eq. (newtonstep_vectornot1)), the
                    mean-based preconditioner (Sec. 4.2) and the truncated,
-                   preconditioned Chebyshev iteration on dense matrices.
+                   preconditioned Chebyshev iteration and GMRES on dense
+                   matrices.
 * ``algorithm1``-- Algorithm 1 and the relative residual of Sec. 5.1.2.
 
 Every floating-point computation is FP64.  Parity pins live in

@@ -5,8 +5,8 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Algorithm 1 (Sec. 4): split the ordered parameter set into K subsets; for each
 subset compute the Newton solution x~ of the upper-median problem (stop at
 ||residual||_2 <= eps_N); take one Newton step on the whole subset as the
-matrix equation F(S_k) = B_k solved by the truncated Chebyshev iteration with
-the mean-based preconditioner; X^k = x~ 1^T + S_k.
+matrix equation F(S_k) = B_k solved by the truncated Chebyshev iteration (or
+the truncated GMRES) with the mean-based preconditioner; X^k = x~ 1^T + S_k.
 
 Reading for accuracy targets the paper does not reach in one step:
 ``chord_steps`` further subset corrections in the same matrix
@@ -39,6 +39,7 @@ class Options:
     eta: float | None = None
     chord_steps: int = 0
     warm_start: bool = True        # x~^{k-1} starts the median Newton of subset k (Sec. 5.1)
+    solver: str = "chebyshev"      # "chebyshev" (ChebyshevT) or "gmres" (GMREST), Algorithm 1 step 3
 
 
 def relative_residuals(mesh, X, mus, nus):
@@ -57,10 +58,13 @@ def subset_step(mesh, xt, mu_k, nu_k, opt: Options, X0=None, history=None):
     R0, Rmu, Rnu = fsi.affine_residual(mesh, xt)
     mu_bar, nu_bar = params.midpoint_parameters(mu_k, nu_k)
     B = lowrank.rhs(R0, Rmu, Rnu, mu_k, nu_k)
-    run = lambda B_: lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B_, mu_k, nu_k, mu_bar, nu_bar, opt.c, opt.d,
-                                                iters=opt.iters, cycles=opt.cycles, tol=opt.tol,
-                                                rank_cap=opt.rank_cap, truncated=opt.truncated,
-                                                eta=opt.eta, history=history)
+    kw = dict(iters=opt.iters, cycles=opt.cycles, tol=opt.tol, rank_cap=opt.rank_cap,
+              truncated=opt.truncated, eta=opt.eta, history=history)
+    if opt.solver == "gmres":
+        run = lambda B_: lowrank.gmres_T_scaled(J0, Jmu, Jnu, B_, mu_k, nu_k, mu_bar, nu_bar, **kw)
+    else:
+        run = lambda B_: lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B_, mu_k, nu_k, mu_bar, nu_bar, opt.c, opt.d,
+                                                    **kw)
     X = xt[:, None] + run(B)
     for _ in range(opt.chord_steps):
         Bc = -np.stack([fsi.residual(mesh, X[:, i], mu_k[i], nu_k[i]) for i in range(len(mu_k))], axis=1)

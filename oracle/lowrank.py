@@ -26,6 +26,18 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
                       every step; a cycle of ``iters`` steps is restarted
                       ``cycles - 1`` times from the current iterate (Sec. 5.1:
                       "restarted once after 6 iterations" = 2 cycles of 6).
+* ``gmres_T``      -- the truncated GMRES (GMREST), the paper's other low-rank
+                      solver (Sec. 4, Algorithm 1 step 3; Sec. 5.1, Table 1),
+                      also cited ([WeiBR20, Alg. 1]) without being restated.
+                      Reading: the textbook restarted GMRES (Arnoldi with the
+                      Frobenius inner product <X, Y> = trace(X^T Y), least
+                      squares on the Hessenberg matrix) with right
+                      preconditioning by the mean-based P_T^k (Sec. 4.2), so
+                      that it minimises the true residual ||B - F(S)||_F, and T
+                      applied to the starting residual, to every operator
+                      application, to every Gram-Schmidt result and to every
+                      update of the iterate; classical Gram-Schmidt against
+                      the basis; the same restart rule as ChebyshevT.
 """
 from __future__ import annotations
 
@@ -129,6 +141,73 @@ def chebyshev_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, c, d, iters=6, cycles=2,
     return S
 
 
+def frobenius_inner(X, Y):
+    """<X, Y>_F = trace(X^T Y)."""
+    return float(np.sum(X * Y))
+
+
+def gmres_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, iters=6, cycles=2, tol=1e-8, rank_cap=None,
+            truncated=True, eta=None, history=None):
+    """Truncated right-preconditioned restarted GMRES for F(S) = B, S0 = 0.
+
+    One cycle from the current S:
+        Res = B - F(S);  V_0 = T(Res) / beta,  beta = ||T(Res)||_F
+        for j = 0 .. iters-1:
+            Z_j = P^{-1} V_j
+            W   = T(F(Z_j))
+            h_ij = <W, V_i>_F  (i <= j);  W = T(W - sum_i h_ij V_i)
+            h_{j+1,j} = ||W||_F;  V_{j+1} = W / h_{j+1,j}
+            stop early when h_{j+1,j} = 0 or the least-squares residual
+            min_y ||beta e_1 - H y|| is <= eta ||B||_F
+        y = argmin ||beta e_1 - H y||_2  (H: (n+1) x n upper Hessenberg)
+        S = T(S + sum_j y_j Z_j)
+    The true residual is checked against eta at the start of every cycle;
+    ``history`` receives ||B - F(S)||_F / ||B||_F there and at the end.
+    """
+    m = B.shape[1]
+    rank_cap = m if rank_cap is None else rank_cap
+    T = (lambda X: truncate(X, tol, rank_cap)) if truncated else (lambda X: X)
+    F = lambda S: apply_F(J0, Jmu, Jnu, S, mu_k, nu_k)
+    nB = np.linalg.norm(B)
+    S = np.zeros_like(B)
+    for _ in range(cycles):
+        Res = B - F(S)
+        if history is not None:
+            history.append(np.linalg.norm(Res) / nB)
+        if eta is not None and np.linalg.norm(Res) <= eta * nB:
+            return S
+        R = T(Res)
+        beta = np.linalg.norm(R)
+        if beta == 0.0:
+            return S
+        V = [R / beta]
+        Z = []
+        H = np.zeros((iters + 1, iters))
+        n = 0
+        for j in range(iters):
+            Z.append(P_lu.solve(V[j]))
+            W = T(F(Z[j]))
+            h = np.array([frobenius_inner(W, Vi) for Vi in V])
+            W = T(W - sum(hi * Vi for hi, Vi in zip(h, V)))
+            H[:j + 1, j] = h
+            H[j + 1, j] = np.linalg.norm(W)
+            n = j + 1
+            g = np.zeros(j + 2)
+            g[0] = beta
+            y = np.linalg.lstsq(H[:j + 2, :j + 1], g, rcond=None)[0]
+            est = np.linalg.norm(g - H[:j + 2, :j + 1] @ y)
+            if H[j + 1, j] == 0.0 or (eta is not None and est <= eta * nB):
+                break
+            V.append(W / H[j + 1, j])
+        g = np.zeros(n + 1)
+        g[0] = beta
+        y = np.linalg.lstsq(H[:n + 1, :n], g, rcond=None)[0]
+        S = T(S + sum(y[i] * Z[i] for i in range(n)))
+    if history is not None:
+        history.append(np.linalg.norm(B - F(S)) / nB)
+    return S
+
+
 def equilibration(J0, Jmu, Jnu, mu_bar, nu_bar):
     """Row and column scales (r, c) of the max-norm equilibration of the
     preconditioner matrix P = J0 + mu_bar Jmu' + nu_bar Jnu':
@@ -156,6 +235,18 @@ def chebyshev_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, c, d, **kw):
     J0s, Jmus, Jnus = (Dr @ J0 @ Dc).tocsr(), (Dr @ Jmu @ Dc).tocsr(), (Dr @ Jnu @ Dc).tocsr()
     P = preconditioner(J0s, Jmus, Jnus, mu_bar, nu_bar)
     Ss = chebyshev_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, c, d, **kw)
+    return cc[:, None] * Ss
+
+
+def gmres_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, **kw):
+    """GMREST on the equilibrated equation diag(r) F(diag(c) S~) = diag(r) B
+    with the equilibrated preconditioner; returns S = diag(c) S~.  GMRES
+    minimises the residual in the row-scaled norm ||diag(r) (B - F(S))||_F."""
+    r, cc = equilibration(J0, Jmu, Jnu, mu_bar, nu_bar)
+    Dr, Dc = sp.diags(r), sp.diags(cc)
+    J0s, Jmus, Jnus = (Dr @ J0 @ Dc).tocsr(), (Dr @ Jmu @ Dc).tocsr(), (Dr @ Jnu @ Dc).tocsr()
+    P = preconditioner(J0s, Jmus, Jnus, mu_bar, nu_bar)
+    Ss = gmres_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, **kw)
     return cc[:, None] * Ss
 
 
