@@ -183,10 +183,11 @@ int lrfsi_newton_median(lrfsi_mesh_h mesh, int K, double* X_dev, const double* m
                         const double* nu_host, double eps, int max_it, int* iters_host,
                         double* res_host, lrfsi_stream_t stream);
 
-/* Options of the truncated Chebyshev iteration. */
+/* Options of the low-rank solvers (truncated Chebyshev iteration and truncated GMRES). */
 typedef struct {
-  double c, d;        /* half-width and centre of the spectrum of P^{-1} A (Sec. 5.1.1) */
-  int iters;          /* steps per cycle (paper: 6) */
+  double c, d;        /* half-width and centre of the spectrum of P^{-1} A (Sec. 5.1.1);
+                         ChebyshevT only */
+  int iters;          /* steps per cycle (paper: 6; GMREST: Arnoldi steps before a restart) */
   int cycles;         /* 1 + restarts (paper: 2) */
   int rank_cap;       /* R: maximal rank kept by the truncation */
   double tol;         /* truncation: keep the smallest r with ||s_{>r}|| <= tol ||s|| */
@@ -199,10 +200,12 @@ typedef struct {
                          relative size e costs about 1e6 e in the unscaled relative residual,
                          so the accumulated Newton update needs a tighter tolerance than the
                          inner iteration. */
+  int solver;         /* lrfsi_subset_step / _init: 0 ChebyshevT, 1 GMREST (Algorithm 1 step 3
+                         allows either); lrfsi_chebyshevT and lrfsi_gmresT ignore it */
 } lrfsi_cheb_options;
 
 typedef struct {
-  int steps;              /* Chebyshev steps taken */
+  int steps;              /* Chebyshev steps (GMREST: Arnoldi steps) taken */
   int rank;               /* rank of the returned S */
   double rel_lin_res;     /* ||B - F(S)||_F / ||B||_F at the last evaluation */
   int max_concat_rank;    /* largest rank fed to a truncation */
@@ -248,9 +251,26 @@ int lrfsi_chebyshevT(lrfsi_subset_h sub, const double* UB_dev, int lduB, const d
                      int ldu, double* V_dev, int ldv, int* rank_host, lrfsi_cheb_stats* stats,
                      lrfsi_stream_t stream);
 
+/* lrfsi_gmresT: the same problem and arguments as lrfsi_chebyshevT, solved with
+ * the truncated GMRES (the paper's GMREST, Sec. 4 Algorithm 1 step 3 and
+ * Sec. 5.1, cited from [WeiBR20] without being restated; c and d are not used).
+ * Restarted GMRES with right preconditioning by P_k, so that it minimises the
+ * true residual ||B_k - F_k(S)||_F; Frobenius inner products computed from the
+ * Gram blocks of the factors (U_a^T U_b, V_a^T V_b); classical Gram-Schmidt;
+ * the truncation (tol, rank cap R_k) applied to the starting residual, to
+ * F(P^{-1} V_j), to the orthogonalised vector and to the updated iterate.  A
+ * cycle is `iters` Arnoldi steps; it ends early when h_{j+1,j} = 0 or the
+ * least-squares residual falls to eta ||B_k||_F.  Sums too wide for the
+ * concatenation buffer are truncated in parts.  stats[k].steps counts Arnoldi
+ * steps.  The Krylov basis (2 iters tall factors per subset) is allocated in
+ * the handle on first use.  Errors as lrfsi_chebyshevT. */
+int lrfsi_gmresT(lrfsi_subset_h sub, const double* UB_dev, int lduB, const double* VB_dev, int ldvB,
+                 const int* rB_host, const lrfsi_cheb_options* opt, double* U_dev, int ldu,
+                 double* V_dev, int ldv, int* rank_host, lrfsi_cheb_stats* stats, lrfsi_stream_t stream);
+
 /* lrfsi_subset_step: one Newton step on every subset (Sec. 3.4,
  * Eq. (rhs_matrix1), Eq. (newton_matrix1)): B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T),
- * S_k = ChebyshevT(B_k); then, while some column's relative residual exceeds
+ * S_k = ChebyshevT(B_k) (GMREST if opt->solver = 1); then, while some column's relative residual exceeds
  * target and fewer than max_outer corrections were taken, a correction in the
  * same matrix form whose right-hand side is -R(X_i; mu_i, nu_i) evaluated
  * column by column (operators and preconditioners kept at xt_k; the sum of

@@ -121,10 +121,10 @@ static size_t g_gemm_ws_bytes = 0;
 template <class T>
 int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
   constexpr int kTarget = 2 * 152;  // enough CTAs to occupy every SM's FP64 unit twice
-  for (int base = 0; base < n; base += kMaxGemmDescs) {
+  for (int i = 0; i < n;) {  // chunks of up to kMaxGemmDescs non-empty products
     GemmBatch<T> gb;
     int cnt = 0, mm = 0, nn = 0, kk = 0;
-    for (int i = base; i < n && cnt < kMaxGemmDescs; ++i) {
+    for (; i < n && cnt < kMaxGemmDescs; ++i) {
       if (descs[i].m <= 0 || descs[i].n <= 0) continue;
       gb.d[cnt] = descs[i];
       if (descs[i].k <= 0) gb.d[cnt].k = 0;
@@ -136,8 +136,8 @@ int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
     if (!cnt) continue;
     {
       double fl = 0, by = 0;
-      for (int i = 0; i < cnt; ++i) {
-        const GemmDesc<T>& g = gb.d[i];
+      for (int q = 0; q < cnt; ++q) {
+        const GemmDesc<T>& g = gb.d[q];
         fl += 2.0 * g.m * g.n * g.k;
         by += sizeof(T) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != T(0) ? 2.0 : 1.0) * g.m * g.n);
       }

@@ -102,11 +102,11 @@ __global__ void k_blockcopy(CopyBatch cb) {
 }
 
 static int copy_batched(const std::vector<CopyDesc>& v, cudaStream_t s) {
-  for (size_t base = 0; base < v.size(); base += kMaxGemmDescs) {
+  for (size_t i = 0; i < v.size();) {  // chunks of up to kMaxGemmDescs non-empty blocks
     CopyBatch cb;
     int cnt = 0;
     long mx = 0;
-    for (size_t i = base; i < v.size() && cnt < kMaxGemmDescs; ++i) {
+    for (; i < v.size() && cnt < kMaxGemmDescs; ++i) {
       if (v[i].rows <= 0 || v[i].ncols <= 0) continue;
       cb.d[cnt++] = v[i];
       mx = std::max(mx, v[i].rows * v[i].ncols);
@@ -145,11 +145,11 @@ __global__ void k_convert(ConvBatch cb) {
 }
 template <class Tin, class Tout>
 static int convert_batched(const std::vector<ConvDesc>& v, cudaStream_t s) {
-  for (size_t base = 0; base < v.size(); base += kMaxGemmDescs) {
+  for (size_t i = 0; i < v.size();) {  // chunks of up to kMaxGemmDescs non-empty blocks
     ConvBatch cb;
     int cnt = 0;
     long mx = 0;
-    for (size_t i = base; i < v.size() && cnt < kMaxGemmDescs; ++i) {
+    for (; i < v.size() && cnt < kMaxGemmDescs; ++i) {
       if (v[i].rows <= 0 || v[i].ncols <= 0) continue;
       cb.d[cnt++] = v[i];
       mx = std::max(mx, v[i].rows * v[i].ncols);
@@ -602,6 +602,10 @@ struct lrfsi_subset_s {
   DevBuf<int> iwork, info;
   DevBuf<TruncDesc> tdesc;
   size_t swork_per = 0;
+  // GMREST Krylov basis (allocated on first use for gm_iters steps per cycle)
+  DevBuf<double> GU, GZ, GV, Gu, Gv, Gh;
+  DevBuf<int> Gn;
+  int gm_iters = 0;
   // dense columns for the nonlinear residual (M x mtot)
   DevBuf<double> Xd;
   ResidualCtx rc;
@@ -622,10 +626,11 @@ static std::atomic<long long> g_tr_calls{0}, g_tr_sweeps{0}, g_tr_maxsweeps{0}, 
 static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
                          const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
                          std::vector<int>& rank, std::vector<double>& frob2, double drop, std::vector<int>& broke,
-                         cudaStream_t s) {
+                         cudaStream_t s, std::vector<double>* kept2 = nullptr) {
   const int na = (int)act.size();
   rank.assign(S->K, 0);
   frob2.assign(S->K, 0.0);
+  if (kept2) kept2->assign(S->K, 0.0);
   if (!na) return LRFSI_OK;
   const int ldP = S->ldP, ldR = S->ldR;
   const long M = S->M;
@@ -723,8 +728,12 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     LRFSI_TRY(gemm_grouped<double>(g3.data(), (int)g3.size(), s));
   }
   LRFSI_TRY(trunc_svd(td.data(), na, s, S->tdesc.p));
-  std::vector<double> f2(S->K);
+  std::vector<double> f2(S->K), svh;
   LRFSI_CUDA(cudaMemcpyAsync(f2.data(), S->frob2.p, sizeof(double) * S->K, cudaMemcpyDeviceToHost, s));
+  if (kept2) {  // singular values, for the norm of the kept part
+    svh.resize((size_t)S->K * ldP);
+    LRFSI_CUDA(cudaMemcpyAsync(svh.data(), S->sv.p, sizeof(double) * svh.size(), cudaMemcpyDeviceToHost, s));
+  }
   LRFSI_TRY(read_info());
   {  // algorithmic FP64 work of the small kernels (upper bound: every Jacobi pair rotated)
     double fl = 0, fj = 0;
@@ -766,6 +775,11 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     if (bad[k] || info[5 * k + 2] == LRFSI_EBREAKDOWN) g_tr_breakdown += 1;
     rank[k] = info[5 * k + 1];
     frob2[k] = f2[k];
+    if (kept2) {
+      double t = 0;
+      for (int j = 0; j < rank[k]; ++j) t += svh[(size_t)ldP * k + j] * svh[(size_t)ldP * k + j];
+      (*kept2)[k] = t;
+    }
     if (bad[k] || info[5 * k + 2] == LRFSI_EBREAKDOWN) {
       bad[k] = 1;
       broke.push_back(k);
@@ -786,18 +800,21 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
 // times (the lost relative remainder grows from 1e-7 to 1e-4 of a column).
 static int truncate_batch(lrfsi_subset_s* S, const std::vector<int>& act, const std::vector<int>& p, double tol,
                           const std::vector<int>& cap, const std::vector<double*>& Uout, const std::vector<double*>& Vout,
-                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s, double drop0 = 1e-14) {
+                          std::vector<int>& rank, std::vector<double>& frob2, cudaStream_t s, double drop0 = 1e-14,
+                          std::vector<double>* kept2 = nullptr) {
   std::vector<int> broke, todo = act;
   rank.assign(S->K, 0);
   frob2.assign(S->K, 0.0);
+  if (kept2) kept2->assign(S->K, 0.0);
   double drop = drop0;
   for (int attempt = 0; attempt < 4 && !todo.empty(); ++attempt, drop *= 100.0) {
     std::vector<int> rk;
-    std::vector<double> f2;
-    LRFSI_TRY(truncate_once(S, todo, p, tol, cap, Uout, Vout, rk, f2, drop, broke, s));
+    std::vector<double> f2, k2;
+    LRFSI_TRY(truncate_once(S, todo, p, tol, cap, Uout, Vout, rk, f2, drop, broke, s, kept2 ? &k2 : nullptr));
     for (int k : todo) {
       rank[k] = rk[k];
       frob2[k] = f2[k];
+      if (kept2) (*kept2)[k] = k2[k];
     }
     todo = broke;
     g_tr_retry += (long long)broke.size();
@@ -861,11 +878,12 @@ extern "C" size_t lrfsi_subset_bytes(lrfsi_subset_h S) {
   size_t b = 0;
   for (DevBuf<double>* p : {&S->mu, &S->nu, &S->xt, &S->J3, &S->R3, &S->rsc, &S->csc, &S->cinv, &S->Xcat, &S->Q1, &S->Q2, &S->US, &S->UD, &S->UR, &S->UZ,
                             &S->UB, &S->Ytmp, &S->UC, &S->Vcat, &S->VS, &S->VD, &S->VR, &S->VB, &S->VC, &S->G, &S->G2,
-                            &S->T1, &S->T2, &S->swork, &S->sv, &S->frob2, &S->gramwork, &S->Xd, &S->rc.R,
+                            &S->T1, &S->T2, &S->swork, &S->sv, &S->frob2, &S->gramwork, &S->GU, &S->GZ, &S->GV,
+                            &S->Gu, &S->Gv, &S->Gh, &S->Xd, &S->rc.R,
                             &S->rc.norm2, &S->rc.norm2_bD, &S->rc.work})
     b += p->bytes();
   for (DevBuf<float>* p : {&S->J3f, &S->USf, &S->Yf, &S->Xf, &S->Vf}) b += p->bytes();
-  return b + S->iwork.bytes() + S->info.bytes() + S->tdesc.bytes() + S->lu.bytes();
+  return b + S->iwork.bytes() + S->info.bytes() + S->tdesc.bytes() + S->Gn.bytes() + S->lu.bytes();
 }
 
 namespace lrfsi {
@@ -998,164 +1016,183 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
 
 namespace lrfsi {
 
-// Chebyshev on factors for the subsets in `act`; B given in UB/VB (rank rB[k]).
-// Results in US/VS with rank rS[k].
-static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<int> act, std::vector<int> rB,
-                    std::vector<int>& rS, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
+// ||B_k||_F of the dense right-hand sides in UB (M x m_k), from column norms.
+static int rhs_norms(lrfsi_subset_s* S, const std::vector<int>& act, std::vector<double>& nB, cudaStream_t s) {
+  const int ldR = S->ldR;
+  const long M = S->M;
+  nB.assign(S->K, 0.0);
+  for (int k : act)
+    LRFSI_TRY(launch_colnorm2(S->tall(S->UB, k, ldR), M, S->m[k], ldR, S->rc.norm2.p + S->off[k], S->rc.work.p,
+                              S->rc.work.n, s));
+  std::vector<double> cn(S->mtot);
+  LRFSI_CUDA(cudaMemcpyAsync(cn.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  for (int k : act) {
+    double t = 0;
+    for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) t += cn[i];
+    nB[k] = std::sqrt(t);
+  }
+  return LRFSI_OK;
+}
+
+// Residual Res = B - F(S) of the subsets in L (B dense in UB, S = US VS^T of
+// rank rS), formed densely in Xcat (M x m_k) and truncated into UR/VR (ranks
+// rR); the dense form avoids cancellation between the factors of B and F(S).
+// nres[k] = ||Res_k||_F; kept2[k] (optional) = ||T(Res_k)||_F^2.
+static int lr_residual(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std::vector<int>& L,
+                       const std::vector<int>& rS, const std::vector<double>& nB, std::vector<int>& rR,
+                       std::vector<double>& nres, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s,
+                       std::vector<double>* kept2 = nullptr) {
   const int K = S->K, ldP = S->ldP, ldR = S->ldR;
   const long M = S->M;
   const long nnz = (long)S->mesh->h.colidx.size();
+  std::vector<int> p(K, 0), rk;
+  std::vector<double*> Uo(K), Vo(K);
+  std::vector<double> f2;
+  std::vector<CopyDesc> cd, cd2;
+  std::vector<SpmmDesc<double>> sd;
+  std::vector<GemmDesc<double>> gm;
+  for (int k : L) {
+    double* X = S->tall(S->Xcat, k, ldP);
+    double* Vc = S->vside(S->Vcat, k, ldP);
+    const int m = S->m[k];
+    cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, X, ldP, M, m, 0, nullptr, 1.0});
+    const int r = rS[k];
+    if (r > 0) {
+      const double* mu = S->mu.p + S->off[k];
+      const double* nu = S->nu.p + S->off[k];
+      cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc, ldP, m, r, 0, nullptr, 1.0});
+      cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + r, ldP, m, r, 0, mu, 1.0});
+      cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + 2 * r, ldP, m, r, 0, nu, 1.0});
+      SpmmDesc<double> d;
+      d.J3 = S->J3.p + (size_t)k * 3 * nnz;
+      d.U = S->tall(S->US, k, ldR);
+      d.ldu = ldR;
+      d.r = r;
+      d.Y = S->tall(S->Q1, k, ldP);
+      d.ldy = ldP;
+      d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+      d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
+      d.a1 = d.a2 = 0.0;
+      sd.push_back(d);
+      gm.push_back(GemmDesc<double>{(int)M, m, 3 * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0,
+                                    1.0});
+    }
+    cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0});
+    p[k] = m;
+    Uo[k] = S->tall(S->UR, k, ldR);
+    Vo[k] = S->vside(S->VR, k, ldR);
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  if (!sd.empty() && o.precision == 0) {
+    LRFSI_TRY(spmm_batched<double>(S->mesh, sd.data(), (int)sd.size(), s));
+    LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+  } else if (!sd.empty()) {
+    // mixed: B - F(S) with an FP32 SpMM and an FP32 GEMM (FP32 accumulation);
+    // the result is widened to FP64 for the truncation
+    std::vector<ConvDesc> c1, c2;
+    std::vector<SpmmDesc<float>> sdf;
+    std::vector<GemmDesc<float>> gmf;
+    for (size_t q = 0; q < sd.size(); ++q) {
+      // subset of this SpMM descriptor
+      int k = -1;
+      for (int kk : L)
+        if (S->tall(S->US, kk, ldR) == sd[q].U) k = kk;
+      const int r = rS[k], m = S->m[k];
+      float* Uf = S->USf.p + (size_t)k * M * ldR;
+      float* Yf = S->Yf.p + (size_t)k * M * ldP;
+      float* Xf = S->Xf.p + (size_t)k * M * ldP;
+      float* Vf = S->Vf.p + (size_t)S->off[k] * ldP;
+      c1.push_back(ConvDesc{S->tall(S->US, k, ldR), ldR, Uf, ldR, M, r, nullptr, 1.0});
+      c1.push_back(ConvDesc{S->tall(S->Xcat, k, ldP), ldP, Xf, ldP, M, m, nullptr, 1.0});
+      c1.push_back(ConvDesc{S->vside(S->Vcat, k, ldP), ldP, Vf, ldP, m, 3 * r, nullptr, 1.0});
+      SpmmDesc<float> d;
+      d.J3 = S->J3f.p + (size_t)k * 3 * nnz;
+      d.U = Uf; d.ldu = ldR; d.r = r; d.Y = Yf; d.ldy = ldP;
+      d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+      d.sc[0] = d.sc[1] = d.sc[2] = 1.0f;
+      d.a1 = d.a2 = 0.0f;
+      sdf.push_back(d);
+      gmf.push_back(GemmDesc<float>{(int)M, m, 3 * r, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f});
+      c2.push_back(ConvDesc{Xf, ldP, S->tall(S->Xcat, k, ldP), ldP, M, m, nullptr, 1.0});
+    }
+    LRFSI_TRY((convert_batched<double, float>(c1, s)));
+    LRFSI_TRY(spmm_batched<float>(S->mesh, sdf.data(), (int)sdf.size(), s));
+    LRFSI_TRY(gemm_grouped<float>(gmf.data(), (int)gmf.size(), s));
+    LRFSI_TRY((convert_batched<float, double>(c2, s)));
+  }
+  LRFSI_TRY(copy_batched(cd2, s));
+  // a residual formed in FP32 carries rounding noise of ~1e-7 of its terms in
+  // every direction: it is truncated at that level (tolerance 1e-6, pivoted
+  // Cholesky remainder 1e-6) instead of resolving the noise
+  if (o.precision == 1) {
+    LRFSI_TRY(truncate_batch(S, L, p, std::max(o.tol, 1e-6), S->cap, Uo, Vo, rk, f2, s, 1e-12, kept2));
+  } else {
+    LRFSI_TRY(truncate_batch(S, L, p, o.tol, S->cap, Uo, Vo, rk, f2, s, 1e-14, kept2));
+  }
+  nres.assign(K, 0.0);
+  for (int k : L) {
+    rR[k] = rk[k];
+    nres[k] = std::sqrt(f2[k]);
+    st[k].rel_lin_res = nres[k] / nB[k];
+    st[k].max_concat_rank = std::max(st[k].max_concat_rank, 3 * rS[k]);
+  }
+  return LRFSI_OK;
+}
+
+// Y_k = P_k^{-1} X_k on tall factors (M x r[k], ld ldR) for the subsets in L
+// with r[k] > 0; X_k is first copied to Ytmp (the solve overwrites its input).
+static int lr_precond(lrfsi_subset_s* S, const std::vector<int>& L, const std::vector<double*>& X,
+                      const std::vector<double*>& Y, const std::vector<int>& r, cudaStream_t s) {
+  const int K = S->K, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<CopyDesc> cd;
+  // the LU batch is indexed by subset: problems of the factorisation are the
+  // K subsets in order; subsets without work get r = 0 (their GEMMs are skipped)
+  std::vector<double*> X2(K), Y2(K);
+  std::vector<int> r2(K, 0);
+  bool any = false;
+  for (int k = 0; k < K; ++k) {
+    X2[k] = S->tall(S->Ytmp, k, ldR);
+    Y2[k] = S->tall(S->UZ, k, ldR);
+  }
+  for (int k : L) {
+    if (r[k] == 0) continue;
+    cd.push_back(CopyDesc{X[k], ldR, S->tall(S->Ytmp, k, ldR), ldR, M, r[k], 0, nullptr, 1.0});
+    Y2[k] = Y[k];
+    r2[k] = r[k];
+    any = true;
+  }
+  if (!any) return LRFSI_OK;
+  LRFSI_TRY(copy_batched(cd, s));
+  return blocklu_solve(S->lu, X2.data(), Y2.data(), r2.data(), ldR, K, s);
+}
+
+// Chebyshev on factors for the subsets in `act`; B given densely in UB.
+// Results in US/VS with rank rS[k].
+static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<int> act, std::vector<int>& rS,
+                    std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
   rS.assign(K, 0);
   st.assign(K, lrfsi_cheb_stats{0, 0, 1.0, 0});
   std::vector<int> rD(K, 0), rR(K, 0), p(K, 0);
-  std::vector<double> nB(K, 0.0), rho(K, 0.0);
-  std::vector<double*> Uo(K), Vo(K);
+  std::vector<double> nB, rho(K, 0.0);
+  std::vector<double*> Uo(K), Vo(K), UR(K), UZ(K);
   std::vector<int> rk;
   std::vector<double> f2;
   const double sigma = o.d / o.c;
-  // B is dense in UB (M x m_k): ||B||_F from its column norms
-  {
-    for (int k : act) {
-      LRFSI_TRY(launch_colnorm2(S->tall(S->UB, k, ldR), M, S->m[k], ldR, S->rc.norm2.p + S->off[k], S->rc.work.p,
-                                S->rc.work.n, s));
-    }
-    std::vector<double> cn(S->mtot);
-    LRFSI_CUDA(cudaMemcpyAsync(cn.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
-    LRFSI_CUDA(cudaStreamSynchronize(s));
-    for (int k : act) {
-      double t = 0;
-      for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) t += cn[i];
-      nB[k] = std::sqrt(t);
-    }
+  for (int k = 0; k < K; ++k) {
+    UR[k] = S->tall(S->UR, k, ldR);
+    UZ[k] = S->tall(S->UZ, k, ldR);
   }
+  LRFSI_TRY(rhs_norms(S, act, nB, s));
   std::vector<int> live;
   for (int k : act)
     if (nB[k] > 0) live.push_back(k);
-  // residual Res = B - F(S) formed densely in Xcat (M x m_k), then truncated
-  // into UR/VR; the dense form avoids cancellation between the factors of B
-  // and F(S).  Returns ||Res||_F.
-  auto residual = [&](const std::vector<int>& L, std::vector<double>& nres) -> int {
-    std::vector<CopyDesc> cd, cd2;
-    std::vector<SpmmDesc<double>> sd;
-    std::vector<GemmDesc<double>> gm;
-    for (int k : L) {
-      double* X = S->tall(S->Xcat, k, ldP);
-      double* Vc = S->vside(S->Vcat, k, ldP);
-      const int m = S->m[k];
-      cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, X, ldP, M, m, 0, nullptr, 1.0});
-      const int r = rS[k];
-      if (r > 0) {
-        const double* mu = S->mu.p + S->off[k];
-        const double* nu = S->nu.p + S->off[k];
-        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc, ldP, m, r, 0, nullptr, 1.0});
-        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + r, ldP, m, r, 0, mu, 1.0});
-        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + 2 * r, ldP, m, r, 0, nu, 1.0});
-        SpmmDesc<double> d;
-        d.J3 = S->J3.p + (size_t)k * 3 * nnz;
-        d.U = S->tall(S->US, k, ldR);
-        d.ldu = ldR;
-        d.r = r;
-        d.Y = S->tall(S->Q1, k, ldP);
-        d.ldy = ldP;
-        d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
-        d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
-        d.a1 = d.a2 = 0.0;
-        sd.push_back(d);
-        gm.push_back(GemmDesc<double>{(int)M, m, 3 * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0,
-                                      1.0});
-      }
-      cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0});
-      p[k] = m;
-      Uo[k] = S->tall(S->UR, k, ldR);
-      Vo[k] = S->vside(S->VR, k, ldR);
-    }
-    LRFSI_TRY(copy_batched(cd, s));
-    if (!sd.empty() && o.precision == 0) {
-      LRFSI_TRY(spmm_batched<double>(S->mesh, sd.data(), (int)sd.size(), s));
-      LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
-    } else if (!sd.empty()) {
-      // mixed: B - F(S) with an FP32 SpMM and an FP32 GEMM (FP32 accumulation);
-      // the result is widened to FP64 for the truncation
-      std::vector<ConvDesc> c1, c2;
-      std::vector<SpmmDesc<float>> sdf;
-      std::vector<GemmDesc<float>> gmf;
-      for (size_t q = 0; q < sd.size(); ++q) {
-        // subset of this SpMM descriptor
-        int k = -1;
-        for (int kk : L)
-          if (S->tall(S->US, kk, ldR) == sd[q].U) k = kk;
-        const int r = rS[k], m = S->m[k];
-        float* Uf = S->USf.p + (size_t)k * M * ldR;
-        float* Yf = S->Yf.p + (size_t)k * M * ldP;
-        float* Xf = S->Xf.p + (size_t)k * M * ldP;
-        float* Vf = S->Vf.p + (size_t)S->off[k] * ldP;
-        c1.push_back(ConvDesc{S->tall(S->US, k, ldR), ldR, Uf, ldR, M, r, nullptr, 1.0});
-        c1.push_back(ConvDesc{S->tall(S->Xcat, k, ldP), ldP, Xf, ldP, M, m, nullptr, 1.0});
-        c1.push_back(ConvDesc{S->vside(S->Vcat, k, ldP), ldP, Vf, ldP, m, 3 * r, nullptr, 1.0});
-        SpmmDesc<float> d;
-        d.J3 = S->J3f.p + (size_t)k * 3 * nnz;
-        d.U = Uf; d.ldu = ldR; d.r = r; d.Y = Yf; d.ldy = ldP;
-        d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
-        d.sc[0] = d.sc[1] = d.sc[2] = 1.0f;
-        d.a1 = d.a2 = 0.0f;
-        sdf.push_back(d);
-        gmf.push_back(GemmDesc<float>{(int)M, m, 3 * r, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f});
-        c2.push_back(ConvDesc{Xf, ldP, S->tall(S->Xcat, k, ldP), ldP, M, m, nullptr, 1.0});
-      }
-      LRFSI_TRY((convert_batched<double, float>(c1, s)));
-      LRFSI_TRY(spmm_batched<float>(S->mesh, sdf.data(), (int)sdf.size(), s));
-      LRFSI_TRY(gemm_grouped<float>(gmf.data(), (int)gmf.size(), s));
-      LRFSI_TRY((convert_batched<float, double>(c2, s)));
-    }
-    LRFSI_TRY(copy_batched(cd2, s));
-    // a residual formed in FP32 carries rounding noise of ~1e-7 of its terms in
-    // every direction: it is truncated at that level (tolerance 1e-6, pivoted
-    // Cholesky remainder 1e-6) instead of resolving the noise
-    if (o.precision == 1) {
-      LRFSI_TRY(truncate_batch(S, L, p, std::max(o.tol, 1e-6), S->cap, Uo, Vo, rk, f2, s, 1e-12));
-    } else {
-      LRFSI_TRY(truncate_batch(S, L, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
-    }
-    nres.assign(K, 0.0);
-    for (int k : L) {
-      rR[k] = rk[k];
-      nres[k] = std::sqrt(f2[k]);
-      st[k].rel_lin_res = nres[k] / nB[k];
-      st[k].max_concat_rank = std::max(st[k].max_concat_rank, 3 * rS[k]);
-    }
-    return LRFSI_OK;
-  };
-  // Z = P^{-1} U_R  (into UZ; UR copied to Ytmp as the destroyed input)
-  auto precond = [&](const std::vector<int>& L) -> int {
-    std::vector<CopyDesc> cd;
-    std::vector<double*> Xs, Ys;
-    std::vector<int> rr;
-    for (int k : L) {
-      if (rR[k] == 0) continue;
-      cd.push_back(CopyDesc{S->tall(S->UR, k, ldR), ldR, S->tall(S->Ytmp, k, ldR), ldR, M, rR[k], 0, nullptr, 1.0});
-      Xs.push_back(S->tall(S->Ytmp, k, ldR));
-      Ys.push_back(S->tall(S->UZ, k, ldR));
-      rr.push_back(rR[k]);
-    }
-    LRFSI_TRY(copy_batched(cd, s));
-    // the LU batch is indexed by subset: solve subset by subset position
-    // (problems of the factorisation are the K subsets in order)
-    if (Xs.empty()) return LRFSI_OK;
-    std::vector<double*> X2(K, nullptr), Y2(K, nullptr);
-    std::vector<int> r2(K, 0);
-    size_t q = 0;
-    for (int k : L) {
-      if (rR[k] == 0) continue;
-      X2[k] = Xs[q]; Y2[k] = Ys[q]; r2[k] = rr[q]; ++q;
-    }
-    // subsets without work get r = 0 (their GEMMs are skipped)
-    for (int k = 0; k < K; ++k)
-      if (!X2[k]) { X2[k] = S->tall(S->Ytmp, k, ldR); Y2[k] = S->tall(S->UZ, k, ldR); }
-    return blocklu_solve(S->lu, X2.data(), Y2.data(), r2.data(), ldR, K, s);
-  };
   for (int cyc = 0; cyc < o.cycles && !live.empty(); ++cyc) {
     std::vector<double> nres;
-    LRFSI_TRY(residual(live, nres));
+    LRFSI_TRY(lr_residual(S, o, live, rS, nB, rR, nres, st, s));
     std::vector<int> next;
     for (int k : live) {
       if (o.eta > 0 && nres[k] <= o.eta * nB[k]) continue;
@@ -1163,7 +1200,7 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
     }
     live.swap(next);
     if (live.empty()) break;
-    LRFSI_TRY(precond(live));
+    LRFSI_TRY(lr_precond(S, live, UR, UZ, rR, s));  // Z = P^{-1} U_R
     {  // Delta = Z / d
       std::vector<CopyDesc> cd;
       for (int k : live) {
@@ -1200,13 +1237,13 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
       }
       if (j == o.iters - 1) break;
       std::vector<double> nres2;
-      LRFSI_TRY(residual(live, nres2));
+      LRFSI_TRY(lr_residual(S, o, live, rS, nB, rR, nres2, st, s));
       std::vector<int> next2;
       for (int k : live)
         if (!(o.eta > 0 && nres2[k] <= o.eta * nB[k])) next2.push_back(k);
       live.swap(next2);
       if (live.empty()) break;
-      LRFSI_TRY(precond(live));
+      LRFSI_TRY(lr_precond(S, live, UR, UZ, rR, s));
       // Delta <- T([U_D | U_Z], [rho' rho V_D | (2 rho' / c) V_R])
       {
         std::vector<CopyDesc> cd;
@@ -1234,20 +1271,361 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
   return LRFSI_OK;
 }
 
+// Krylov basis storage of GMREST for `iters` steps per cycle: the tall
+// factors of V_j and Z_j = P^{-1} V_j (K x M x ldR each), the parameter-side
+// factors of V_j (sum m_k x ldR), the two Gram blocks of the inner products
+// (K x iters blocks of ldR^2) and their sizes and results (K x iters).
+static int gmres_alloc(lrfsi_subset_s* S, int iters) {
+  if (S->gm_iters >= iters) return LRFSI_OK;
+  const size_t tall = (size_t)S->K * S->M * S->ldR, side = (size_t)S->mtot * S->ldR;
+  const size_t nblk = (size_t)S->K * iters;
+  LRFSI_TRY(S->GU.alloc(tall * iters));
+  LRFSI_TRY(S->GZ.alloc(tall * iters));
+  LRFSI_TRY(S->GV.alloc(side * iters));
+  LRFSI_TRY(S->Gu.alloc(nblk * S->ldR * S->ldR));
+  LRFSI_TRY(S->Gv.alloc(nblk * S->ldR * S->ldR));
+  LRFSI_TRY(S->Gh.alloc(nblk));
+  LRFSI_TRY(S->Gn.alloc(nblk));
+  S->gm_iters = iters;
+  return LRFSI_OK;
+}
+
+// h[q] = sum_e A_q[e] B_q[e] over the first n[q] entries of block q (blocks of
+// `blk` doubles): the Frobenius inner product <X, Y> = sum((U_X^T U_Y) .*
+// (V_X^T V_Y)) from its two Gram blocks.  One CTA per block, fixed-order
+// reduction.
+constexpr int kDotThreads = 256;
+__global__ void __launch_bounds__(kDotThreads) k_block_dot(const double* __restrict__ A, const double* __restrict__ B,
+                                                           const int* __restrict__ n, size_t blk,
+                                                           double* __restrict__ h) {
+  __shared__ double red[kDotThreads / 32];
+  const int q = blockIdx.x;
+  const int nq = n[q];
+  const double* a = A + (size_t)q * blk;
+  const double* b = B + (size_t)q * blk;
+  double t = 0.0;
+  for (int e = threadIdx.x; e < nq; e += kDotThreads) t = fma(a[e], b[e], t);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double u = 0.0;
+    for (int w = 0; w < kDotThreads / 32; ++w) u += red[w];
+    h[q] = u;
+  }
+}
+
+// Widens the concatenation buffers and the truncation scratch to `width`
+// columns (a GMREST sum has up to iters + 1 terms of rank <= R_k and is
+// truncated at once).  The widened buffers are scratch only: no state lives in
+// them between operations.
+static int widen_concat(lrfsi_subset_s* S, int width) {
+  if (width <= S->ldP) return LRFSI_OK;
+  const int K = S->K;
+  const long M = S->M;
+  const size_t w = (size_t)width;
+  for (DevBuf<double>* b : {&S->Xcat, &S->Q1, &S->Q2}) LRFSI_TRY(b->alloc((size_t)K * M * w));
+  LRFSI_TRY(S->Vcat.alloc((size_t)S->mtot * w));
+  for (DevBuf<double>* b : {&S->G, &S->G2, &S->T1, &S->T2}) LRFSI_TRY(b->alloc((size_t)K * w * w));
+  S->swork_per = trunc_small_work(width, S->mmax);
+  LRFSI_TRY(S->swork.alloc(S->swork_per * K));
+  LRFSI_TRY(S->sv.alloc((size_t)K * w));
+  LRFSI_TRY(S->iwork.alloc((size_t)2 * w * K));
+  LRFSI_TRY(S->gramwork.alloc(gram_work_len(K, M, width, width)));
+  LRFSI_TRY(S->Yf.alloc((size_t)K * M * w));
+  LRFSI_TRY(S->Xf.alloc((size_t)K * M * w));
+  LRFSI_TRY(S->Vf.alloc((size_t)S->mtot * w));
+  S->ldP = width;
+  return LRFSI_OK;
+}
+
+// T(sum of terms) for the subsets in L, one truncation per subset: per subset
+// a list of terms (tall factor, ld ldR; parameter-side factor, ld ldR; rank;
+// scale of the parameter side) concatenated in Xcat/Vcat; the result goes to
+// Uo/Vo (ld ldR; may be the first term's buffers).
+struct LrTerm {
+  const double* U;
+  const double* V;
+  int r;
+  double a;
+};
+static int truncate_sum(lrfsi_subset_s* S, const std::vector<int>& L, const std::vector<std::vector<LrTerm>>& terms,
+                        double tol, const std::vector<double*>& Uo, const std::vector<double*>& Vo,
+                        std::vector<int>& rank, std::vector<double>* kept2, cudaStream_t s) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<int> p(K, 0);
+  std::vector<CopyDesc> cd;
+  for (int k : L) {
+    int c = 0;
+    for (const LrTerm& t : terms[k]) {
+      if (c + t.r > ldP) return fail(LRFSI_EINVAL, "truncate_sum: concatenation wider than its buffer");
+      cd.push_back(CopyDesc{t.U, ldR, S->tall(S->Xcat, k, ldP) + c, ldP, M, t.r, 0, nullptr, 1.0});
+      cd.push_back(CopyDesc{t.V, ldR, S->vside(S->Vcat, k, ldP) + c, ldP, S->m[k], t.r, 0, nullptr, t.a});
+      c += t.r;
+    }
+    p[k] = c;
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  std::vector<double> f2;
+  return truncate_batch(S, L, p, tol, S->cap, Uo, Vo, rank, f2, s, 1e-14, kept2);
+}
+
+// GMREST on factors for the subsets in `act`: restarted GMRES with right
+// preconditioning by P_k, Frobenius inner products (<X, Y> from the Gram
+// blocks of the factors), classical Gram-Schmidt, and the truncation applied
+// to the starting residual, to F(Z_j), to the orthogonalised vector and to
+// the updated iterate (each sum truncated at once: the concatenation buffers
+// are widened to (iters + 1) R_max columns).  B given densely in UB; results
+// in US/VS (ranks rS).
+static int gmres_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<int> act, std::vector<int>& rS,
+                     std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
+  const int K = S->K, ldR = S->ldR, nit = o.iters;
+  const long M = S->M;
+  const long nnz = (long)S->mesh->h.colidx.size();
+  rS.assign(K, 0);
+  st.assign(K, lrfsi_cheb_stats{0, 0, 1.0, 0});
+  if (S->gm_iters < nit || S->ldP < (nit + 1) * S->Rmax)
+    return fail(LRFSI_EINVAL, "GMREST: workspace not prepared for this iteration count");
+  const int ldP = S->ldP;
+  const size_t tall = (size_t)K * M * ldR, side = (size_t)S->mtot * ldR, gblk = (size_t)ldR * ldR;
+  auto GU = [&](int j, int k) { return S->GU.p + tall * j + (size_t)k * M * ldR; };
+  auto GZ = [&](int j, int k) { return S->GZ.p + tall * j + (size_t)k * M * ldR; };
+  auto GV = [&](int j, int k) { return S->GV.p + side * j + (size_t)S->off[k] * ldR; };
+  std::vector<double> nB;
+  LRFSI_TRY(rhs_norms(S, act, nB, s));
+  std::vector<int> live;
+  for (int k : act)
+    if (nB[k] > 0) live.push_back(k);
+  std::vector<int> rR(K, 0), rW(K, 0), rk;
+  std::vector<double> f2;
+  std::vector<double*> Uo(K), Vo(K), Xb(K), Yb(K);
+  for (int k = 0; k < K; ++k) {
+    Uo[k] = S->tall(S->UD, k, ldR);
+    Vo[k] = S->vside(S->VD, k, ldR);
+  }
+  std::vector<int> hn((size_t)K * nit);    // Gram block sizes of the inner products
+  std::vector<double> hh((size_t)K * nit);  // the inner products
+  for (int cyc = 0; cyc < o.cycles && !live.empty(); ++cyc) {
+    std::vector<double> nres, beta;
+    LRFSI_TRY(lr_residual(S, o, live, rS, nB, rR, nres, st, s, &beta));
+    std::vector<int> arn;
+    for (int k : live) {
+      if (o.eta > 0 && nres[k] <= o.eta * nB[k]) continue;
+      beta[k] = std::sqrt(beta[k]);
+      if (rR[k] > 0 && beta[k] > 0) arn.push_back(k);
+    }
+    live = arn;
+    if (arn.empty()) break;
+    // V_0 = T(Res) / beta
+    std::vector<std::vector<int>> rb(K, std::vector<int>(nit, 0));
+    {
+      std::vector<CopyDesc> cd;
+      for (int k : arn) {
+        cd.push_back(CopyDesc{S->tall(S->UR, k, ldR), ldR, GU(0, k), ldR, M, rR[k], 0, nullptr, 1.0});
+        cd.push_back(CopyDesc{S->vside(S->VR, k, ldR), ldR, GV(0, k), ldR, S->m[k], rR[k], 0, nullptr, 1.0 / beta[k]});
+        rb[k][0] = rR[k];
+      }
+      LRFSI_TRY(copy_batched(cd, s));
+    }
+    // Hessenberg columns reduced by Givens rotations: Rh (upper triangle), g
+    std::vector<std::vector<double>> Rh(K, std::vector<double>((size_t)(nit + 1) * nit, 0.0));
+    std::vector<std::vector<double>> g(K, std::vector<double>(nit + 1, 0.0)), cs(K, std::vector<double>(nit, 1.0)),
+        sn(K, std::vector<double>(nit, 0.0));
+    std::vector<int> nstep(K, 0);
+    for (int k : arn) g[k][0] = beta[k];
+    for (int j = 0; j < nit && !arn.empty(); ++j) {
+      // Z_j = P^{-1} V_j (tall factor)
+      std::vector<int> rj(K, 0);
+      for (int k : arn) {
+        Xb[k] = GU(j, k);
+        Yb[k] = GZ(j, k);
+        rj[k] = rb[k][j];
+      }
+      LRFSI_TRY(lr_precond(S, arn, Xb, Yb, rj, s));
+      // W = T(F(Z_j)) = T([J0 Z | Jmu' Z | Jnu' Z] [V | D_mu V | D_nu V]^T)
+      {
+        std::vector<SpmmDesc<double>> sd;
+        std::vector<CopyDesc> cd;
+        std::vector<int> p(K, 0);
+        for (int k : arn) {
+          const int r = rj[k];
+          SpmmDesc<double> d;
+          d.J3 = S->J3.p + (size_t)k * 3 * nnz;
+          d.U = GZ(j, k);
+          d.ldu = ldR;
+          d.r = r;
+          d.Y = S->tall(S->Xcat, k, ldP);
+          d.ldy = ldP;
+          d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+          d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
+          d.a1 = d.a2 = 0.0;
+          sd.push_back(d);
+          double* Vc = S->vside(S->Vcat, k, ldP);
+          cd.push_back(CopyDesc{GV(j, k), ldR, Vc, ldP, S->m[k], r, 0, nullptr, 1.0});
+          cd.push_back(CopyDesc{GV(j, k), ldR, Vc + r, ldP, S->m[k], r, 0, S->mu.p + S->off[k], 1.0});
+          cd.push_back(CopyDesc{GV(j, k), ldR, Vc + 2 * r, ldP, S->m[k], r, 0, S->nu.p + S->off[k], 1.0});
+          p[k] = 3 * r;
+          st[k].max_concat_rank = std::max(st[k].max_concat_rank, 3 * r);
+        }
+        LRFSI_TRY(spmm_batched<double>(S->mesh, sd.data(), (int)sd.size(), s));
+        LRFSI_TRY(copy_batched(cd, s));
+        LRFSI_TRY(truncate_batch(S, arn, p, o.tol, S->cap, Uo, Vo, rk, f2, s));
+        for (int k : arn) rW[k] = rk[k];
+      }
+      // h_ij = <W, V_i>_F = sum((U_W^T U_i) .* (V_W^T V_i)), i <= j
+      std::vector<std::vector<double>> h(K, std::vector<double>(j + 1, 0.0));
+      {
+        std::vector<GramDesc> gd;
+        std::vector<GemmDesc<double>> gv;
+        for (int k : arn) {
+          if (rW[k] == 0) continue;
+          for (int i = 0; i <= j; ++i) {
+            double* Gu = S->Gu.p + ((size_t)k * nit + i) * gblk;
+            double* Gv = S->Gv.p + ((size_t)k * nit + i) * gblk;
+            gd.push_back(GramDesc{S->tall(S->UD, k, ldR), ldR, rW[k], GU(i, k), ldR, rb[k][i], Gu, rb[k][i]});
+            gv.push_back(GemmDesc<double>{rW[k], rb[k][i], S->m[k], S->vside(S->VD, k, ldR), 1, ldR, GV(i, k), ldR, 1,
+                                          Gv, rb[k][i], 1, 1.0, 0.0});
+          }
+        }
+        if (!gd.empty()) {
+          std::fill(hn.begin(), hn.end(), 0);
+          for (int k : arn)
+            if (rW[k] > 0)
+              for (int i = 0; i <= j; ++i) hn[(size_t)k * nit + i] = rW[k] * rb[k][i];
+          LRFSI_CUDA(cudaMemcpyAsync(S->Gn.p, hn.data(), sizeof(int) * hn.size(), cudaMemcpyHostToDevice, s));
+          LRFSI_TRY(gram_batched(gd.data(), (int)gd.size(), M, S->gramwork.p, S->gramwork.n, s));
+          LRFSI_TRY(gemm_grouped<double>(gv.data(), (int)gv.size(), s));
+          k_block_dot<<<(int)hn.size(), kDotThreads, 0, s>>>(S->Gu.p, S->Gv.p, S->Gn.p, gblk, S->Gh.p);
+          LRFSI_TRY(check_launch("k_block_dot"));
+          LRFSI_CUDA(cudaMemcpyAsync(hh.data(), S->Gh.p, sizeof(double) * hh.size(), cudaMemcpyDeviceToHost, s));
+          LRFSI_CUDA(cudaStreamSynchronize(s));
+        }
+        for (int k : arn)
+          if (rW[k] > 0)
+            for (int i = 0; i <= j; ++i) h[k][i] = hh[(size_t)k * nit + i];
+      }
+      // W <- T(W - sum_i h_ij V_i); h_{j+1,j} = ||W||_F
+      std::vector<double> hnext(K, 0.0);
+      {
+        std::vector<int> L;
+        std::vector<std::vector<LrTerm>> terms(K);
+        for (int k : arn) {
+          if (rW[k] == 0) continue;
+          terms[k].push_back(LrTerm{S->tall(S->UD, k, ldR), S->vside(S->VD, k, ldR), rW[k], 1.0});
+          for (int i = 0; i <= j; ++i) terms[k].push_back(LrTerm{GU(i, k), GV(i, k), rb[k][i], -h[k][i]});
+          L.push_back(k);
+        }
+        std::vector<double> kw;
+        LRFSI_TRY(truncate_sum(S, L, terms, o.tol, Uo, Vo, rk, &kw, s));
+        for (int k : L) {
+          rW[k] = rk[k];
+          hnext[k] = std::sqrt(kw[k]);
+        }
+      }
+      // Givens rotations on column j; g_{j+1} is the least-squares residual
+      std::vector<int> cont;
+      for (int k : arn) {
+        std::vector<double> col(j + 2, 0.0);
+        for (int i = 0; i <= j; ++i) col[i] = h[k][i];
+        col[j + 1] = hnext[k];
+        for (int i = 0; i < j; ++i) {
+          const double a = col[i], b = col[i + 1];
+          col[i] = cs[k][i] * a + sn[k][i] * b;
+          col[i + 1] = -sn[k][i] * a + cs[k][i] * b;
+        }
+        const double den = std::hypot(col[j], col[j + 1]);
+        cs[k][j] = den > 0 ? col[j] / den : 1.0;
+        sn[k][j] = den > 0 ? col[j + 1] / den : 0.0;
+        col[j] = den;
+        g[k][j + 1] = -sn[k][j] * g[k][j];
+        g[k][j] = cs[k][j] * g[k][j];
+        for (int i = 0; i <= j; ++i) Rh[k][(size_t)i * nit + j] = col[i];
+        nstep[k] = j + 1;
+        st[k].steps += 1;
+        const bool stop = hnext[k] == 0.0 || rW[k] == 0 || (o.eta > 0 && std::fabs(g[k][j + 1]) <= o.eta * nB[k]);
+        if (!stop && j + 1 < nit) {
+          cont.push_back(k);
+          rb[k][j + 1] = rW[k];
+        }
+      }
+      // V_{j+1} = W / h_{j+1,j}
+      {
+        std::vector<CopyDesc> cd;
+        for (int k : cont) {
+          cd.push_back(CopyDesc{S->tall(S->UD, k, ldR), ldR, GU(j + 1, k), ldR, M, rW[k], 0, nullptr, 1.0});
+          cd.push_back(CopyDesc{S->vside(S->VD, k, ldR), ldR, GV(j + 1, k), ldR, S->m[k], rW[k], 0, nullptr,
+                                1.0 / hnext[k]});
+        }
+        LRFSI_TRY(copy_batched(cd, s));
+      }
+      arn.swap(cont);
+    }
+    // y = Rh^{-1} g (n x n upper triangular), S <- T(S + sum_j y_j Z_j)
+    {
+      std::vector<int> L;
+      std::vector<std::vector<LrTerm>> terms(K);
+      std::vector<double*> Us(K), Vs(K);
+      for (int k : live) {
+        const int n = nstep[k];
+        std::vector<double> y(n, 0.0);
+        for (int i = n - 1; i >= 0; --i) {
+          double t = g[k][i];
+          for (int l = i + 1; l < n; ++l) t -= Rh[k][(size_t)i * nit + l] * y[l];
+          const double dg = Rh[k][(size_t)i * nit + i];
+          y[i] = dg != 0.0 ? t / dg : 0.0;
+        }
+        Us[k] = S->tall(S->US, k, ldR);
+        Vs[k] = S->vside(S->VS, k, ldR);
+        terms[k].push_back(LrTerm{Us[k], Vs[k], rS[k], 1.0});
+        for (int i = 0; i < n; ++i) terms[k].push_back(LrTerm{GZ(i, k), GV(i, k), rb[k][i], y[i]});
+        L.push_back(k);
+      }
+      LRFSI_TRY(truncate_sum(S, L, terms, o.tol, Us, Vs, rk, nullptr, s));
+      for (int k : L) rS[k] = rk[k];
+    }
+  }
+  for (int k : act) st[k].rank = rS[k];
+  return LRFSI_OK;
+}
+
+// Workspace of the selected solver, set up at an entry point before anything
+// takes the concatenation width (GMREST: Krylov basis, widened buffers).
+static int solver_prepare(lrfsi_subset_s* S, const lrfsi_cheb_options& o) {
+  if (o.solver != 1) return LRFSI_OK;
+  LRFSI_TRY(gmres_alloc(S, o.iters));
+  return widen_concat(S, (o.iters + 1) * S->Rmax);
+}
+
+// The low-rank solver the options select (0: ChebyshevT, 1: GMREST).
+static int lr_solve(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std::vector<int>& act,
+                    std::vector<int>& rS, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
+  return o.solver == 1 ? gmres_run(S, o, act, rS, st, s) : cheb_run(S, o, act, rS, st, s);
+}
+
 static int check_opts(const lrfsi_cheb_options* o) {
-  if (!o || !(o->c > 0) || !(o->d > o->c) || o->iters < 1 || o->cycles < 1 || o->rank_cap < 1 || !(o->tol >= 0) ||
+  if (!o || o->solver < 0 || o->solver > 1 || o->iters < 1 || o->cycles < 1 || o->rank_cap < 1 || !(o->tol >= 0) ||
       o->precision < 0 || o->precision > 1 || !(o->tol_sol >= 0))
-    return fail(LRFSI_EINVAL, "lrfsi_cheb_options: need 0 < c < d, iters, cycles, rank_cap >= 1, tol >= 0");
+    return fail(LRFSI_EINVAL, "lrfsi_cheb_options: need solver 0 or 1, iters, cycles, rank_cap >= 1, tol >= 0");
+  if (o->solver == 0 && !(o->c > 0 && o->d > o->c))
+    return fail(LRFSI_EINVAL, "lrfsi_cheb_options: ChebyshevT needs 0 < c < d");
   return LRFSI_OK;
 }
 
 }  // namespace lrfsi
 
-extern "C" int lrfsi_chebyshevT(lrfsi_subset_h S, const double* UB, int lduB, const double* VB, int ldvB,
-                                const int* rB_h, const lrfsi_cheb_options* opt, double* U, int ldu, double* V, int ldv,
-                                int* rank_h, lrfsi_cheb_stats* stats, lrfsi_stream_t stream) {
-  if (!S || !UB || !VB || !rB_h || !U || !V || !rank_h) return fail(LRFSI_EINVAL, "lrfsi_chebyshevT: null argument");
+// F_k(S_k) = UB_k VB_k^T by the given solver (0: ChebyshevT, 1: GMREST).
+static int lowrank_solve(lrfsi_subset_h S, const double* UB, int lduB, const double* VB, int ldvB, const int* rB_h,
+                         const lrfsi_cheb_options* opt_in, int solver, double* U, int ldu, double* V, int ldv,
+                         int* rank_h, lrfsi_cheb_stats* stats, lrfsi_stream_t stream) {
+  if (!S || !UB || !VB || !rB_h || !U || !V || !rank_h || !opt_in)
+    return fail(LRFSI_EINVAL, "lrfsi_chebyshevT / lrfsi_gmresT: null argument");
+  lrfsi_cheb_options o = *opt_in;
+  o.solver = solver;
+  const lrfsi_cheb_options* opt = &o;
   LRFSI_TRY(check_opts(opt));
+  LRFSI_TRY(solver_prepare(S, *opt));
   cudaStream_t s = (cudaStream_t)stream;
   const int K = S->K, ldR = S->ldR;
   const long M = S->M;
@@ -1272,7 +1650,7 @@ extern "C" int lrfsi_chebyshevT(lrfsi_subset_h S, const double* UB, int lduB, co
   }
   std::vector<int> rS;
   std::vector<lrfsi_cheb_stats> st;
-  LRFSI_TRY(cheb_run(S, *opt, act, rB, rS, st, s));
+  LRFSI_TRY(lr_solve(S, *opt, act, rS, st, s));
   std::vector<CopyDesc> cd;
   for (int k = 0; k < K; ++k) {
     rank_h[k] = rS[k];
@@ -1284,6 +1662,18 @@ extern "C" int lrfsi_chebyshevT(lrfsi_subset_h S, const double* UB, int lduB, co
   LRFSI_TRY(copy_batched(cd, s));
   LRFSI_CUDA(cudaStreamSynchronize(s));
   return LRFSI_OK;
+}
+
+extern "C" int lrfsi_chebyshevT(lrfsi_subset_h S, const double* UB, int lduB, const double* VB, int ldvB,
+                                const int* rB_h, const lrfsi_cheb_options* opt, double* U, int ldu, double* V, int ldv,
+                                int* rank_h, lrfsi_cheb_stats* stats, lrfsi_stream_t stream) {
+  return lowrank_solve(S, UB, lduB, VB, ldvB, rB_h, opt, 0, U, ldu, V, ldv, rank_h, stats, stream);
+}
+
+extern "C" int lrfsi_gmresT(lrfsi_subset_h S, const double* UB, int lduB, const double* VB, int ldvB, const int* rB_h,
+                            const lrfsi_cheb_options* opt, double* U, int ldu, double* V, int ldv, int* rank_h,
+                            lrfsi_cheb_stats* stats, lrfsi_stream_t stream) {
+  return lowrank_solve(S, UB, lduB, VB, ldvB, rB_h, opt, 1, U, ldu, V, ldv, rank_h, stats, stream);
 }
 
 __global__ void k_recip(const double* __restrict__ x, long n, double* __restrict__ y) {
@@ -1349,16 +1739,14 @@ static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, dou
     }
     // correction: B = -R(X) (dense, rank <= m_k as factors (R_k, I))
     cd.clear();
-    std::vector<int> rBc(K, 0);
     for (int k : need) {
       const int m = S->m[k];
       // UB must hold m columns: ldR >= mmax by construction
       cd.push_back(CopyDesc{S->rc.R.p + S->off[k], S->mtot, S->tall(S->UB, k, ldR), ldR, M, m, 0,
                             S->rsc.p + (size_t)k * M, -1.0});
-      rBc[k] = m;
     }
     LRFSI_TRY(copy_batched(cd, s));
-    LRFSI_TRY(cheb_run(S, o, need, rBc, rS, st, s));
+    LRFSI_TRY(lr_solve(S, o, need, rS, st, s));
     // accumulate: C <- T([U_C | U_S], [V_C | V_S])
     cd.clear();
     std::vector<int> p(K, 0);
@@ -1389,15 +1777,16 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
                                  lrfsi_stream_t stream) {
   if (!S || !U || !V || !rank_h || max_outer < 0) return fail(LRFSI_EINVAL, "lrfsi_subset_step: bad argument");
   LRFSI_TRY(check_opts(opt));
+  LRFSI_TRY(solver_prepare(S, *opt));
   cudaStream_t s = (cudaStream_t)stream;
-  const int K = S->K, ldR = S->ldR, ldP = S->ldP;
+  const int K = S->K, ldR = S->ldR;
   const long M = S->M;
   for (int k = 0; k < K; ++k)
     if (ldu < S->cap[k] || ldv < S->cap[k]) return fail(LRFSI_EINVAL, "lrfsi_subset_step: ldu/ldv < rank cap");
   // B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T), dense M x m_k in UB
   std::vector<CopyDesc> cd;
   std::vector<GemmDesc<double>> gb;
-  std::vector<int> act, rB(K, 3);
+  std::vector<int> act;
   for (int k = 0; k < K; ++k) {
     act.push_back(k);
     double* vb = S->vside(S->VB, k, ldR);
@@ -1416,7 +1805,7 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
   LRFSI_TRY(copy_batched(cd, s));
   std::vector<int> rS;
   std::vector<lrfsi_cheb_stats> st;
-  LRFSI_TRY(cheb_run(S, *opt, act, rB, rS, st, s));
+  LRFSI_TRY(lr_solve(S, *opt, act, rS, st, s));
   // keep the accumulated update in UC/VC
   std::vector<int> rC = rS;
   cd.clear();
@@ -1451,6 +1840,7 @@ extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options
   if (!S || !U0 || !V0 || !r0_h || !U || !V || !rank_h || max_outer < 0)
     return fail(LRFSI_EINVAL, "lrfsi_subset_step_init: bad argument");
   LRFSI_TRY(check_opts(opt));
+  LRFSI_TRY(solver_prepare(S, *opt));
   cudaStream_t s = (cudaStream_t)stream;
   const int K = S->K, ldR = S->ldR, ldP = S->ldP;
   const long M = S->M;

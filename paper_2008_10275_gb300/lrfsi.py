@@ -39,7 +39,7 @@ class lrfsi_mesh_info_t(C.Structure):
 class lrfsi_cheb_options(C.Structure):
     _fields_ = [("c", C.c_double), ("d", C.c_double), ("iters", C.c_int), ("cycles", C.c_int),
                 ("rank_cap", C.c_int), ("tol", C.c_double), ("eta", C.c_double), ("precision", C.c_int),
-                ("tol_sol", C.c_double)]
+                ("tol_sol", C.c_double), ("solver", C.c_int)]
 
 
 class lrfsi_kernel_stat(C.Structure):
@@ -96,6 +96,7 @@ def load():
         "lrfsi_subset_create": [vp, i, vp, vp, vp, vp, vp, C.POINTER(vp), vp],
         "lrfsi_subset_destroy": [vp],
         "lrfsi_chebyshevT": [vp, vp, i, vp, i, vp, C.POINTER(lrfsi_cheb_options), vp, i, vp, i, vp, vp, vp],
+        "lrfsi_gmresT": [vp, vp, i, vp, i, vp, C.POINTER(lrfsi_cheb_options), vp, i, vp, i, vp, vp, vp],
         "lrfsi_subset_step": [vp, C.POINTER(lrfsi_cheb_options), d, i, vp, i, vp, i, vp, vp, vp, vp],
         "lrfsi_subset_step_init": [vp, C.POINTER(lrfsi_cheb_options), d, i, vp, i, vp, i, vp, vp, i, vp, i, vp, vp,
                                    vp, vp, vp],
@@ -238,8 +239,12 @@ def lrfsi_newton_median(mesh, X, mu, nu, eps, max_it, stream=None, allow_noconv=
     return it, res, st
 
 
-def cheb_options(c, d, iters=6, cycles=2, rank_cap=20, tol=1e-8, eta=0.0, precision=0, tol_sol=0.0):
-    return lrfsi_cheb_options(c, d, iters, cycles, rank_cap, tol, eta, precision, tol_sol)
+SOLVERS = {"chebyshev": 0, "gmres": 1}
+
+
+def cheb_options(c, d, iters=6, cycles=2, rank_cap=20, tol=1e-8, eta=0.0, precision=0, tol_sol=0.0,
+                 solver="chebyshev"):
+    return lrfsi_cheb_options(c, d, iters, cycles, rank_cap, tol, eta, precision, tol_sol, SOLVERS[solver])
 
 
 class Subsets:
@@ -276,14 +281,22 @@ def lrfsi_subset_create(mesh, xt, mu, nu, sizes, caps, stream=None):
     return Subsets(mesh, xt, mu, nu, sizes, caps, stream)
 
 
-def lrfsi_chebyshevT(sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream=None):
+def _lowrank_solve(fn, sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream):
     rB = np.ascontiguousarray(rB, np.int32)
     ranks = np.zeros(sub.K, np.int32)
     stats = (lrfsi_cheb_stats * sub.K)()
-    _check(load().lrfsi_chebyshevT(sub.h, _ptr(UB), lduB, _ptr(VB), ldvB, _ptr(rB), C.byref(opt), _ptr(U), ldu,
-                                   _ptr(V), ldv, _ptr(ranks), C.cast(stats, C.c_void_p), _stream(stream)))
+    _check(fn(sub.h, _ptr(UB), lduB, _ptr(VB), ldvB, _ptr(rB), C.byref(opt), _ptr(U), ldu, _ptr(V), ldv,
+              _ptr(ranks), C.cast(stats, C.c_void_p), _stream(stream)))
     return ranks, [dict(steps=s.steps, rank=s.rank, rel_lin_res=s.rel_lin_res, max_concat_rank=s.max_concat_rank)
                    for s in stats]
+
+
+def lrfsi_chebyshevT(sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream=None):
+    return _lowrank_solve(load().lrfsi_chebyshevT, sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream)
+
+
+def lrfsi_gmresT(sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream=None):
+    return _lowrank_solve(load().lrfsi_gmresT, sub, UB, lduB, VB, ldvB, rB, opt, U, ldu, V, ldv, stream)
 
 
 def lrfsi_subset_step(sub, opt, target, max_outer, U, ldu, V, ldv, stream=None, allow_noconv=True):
