@@ -86,6 +86,10 @@ struct DevBuf {
     return LRFSI_OK;
   }
   size_t bytes() const { return n * sizeof(T); }
+  void swap(DevBuf& o) {
+    T* tp = p; p = o.p; o.p = tp;
+    size_t tn = n; n = o.n; o.n = tn;
+  }
 };
 
 inline int ceil_div(long a, long b) { return (int)((a + b - 1) / b); }

@@ -1277,6 +1277,7 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
 // (K x iters blocks of ldR^2) and their sizes and results (K x iters).
 static int gmres_alloc(lrfsi_subset_s* S, int iters) {
   if (S->gm_iters >= iters) return LRFSI_OK;
+  S->gm_iters = 0;  // nothing usable until every buffer below exists
   const size_t tall = (size_t)S->K * S->M * S->ldR, side = (size_t)S->mtot * S->ldR;
   const size_t nblk = (size_t)S->K * iters;
   LRFSI_TRY(S->GU.alloc(tall * iters));
@@ -1325,17 +1326,28 @@ static int widen_concat(lrfsi_subset_s* S, int width) {
   const int K = S->K;
   const long M = S->M;
   const size_t w = (size_t)width;
-  for (DevBuf<double>* b : {&S->Xcat, &S->Q1, &S->Q2}) LRFSI_TRY(b->alloc((size_t)K * M * w));
-  LRFSI_TRY(S->Vcat.alloc((size_t)S->mtot * w));
-  for (DevBuf<double>* b : {&S->G, &S->G2, &S->T1, &S->T2}) LRFSI_TRY(b->alloc((size_t)K * w * w));
-  S->swork_per = trunc_small_work(width, S->mmax);
-  LRFSI_TRY(S->swork.alloc(S->swork_per * K));
-  LRFSI_TRY(S->sv.alloc((size_t)K * w));
-  LRFSI_TRY(S->iwork.alloc((size_t)2 * w * K));
-  LRFSI_TRY(S->gramwork.alloc(gram_work_len(K, M, width, width)));
-  LRFSI_TRY(S->Yf.alloc((size_t)K * M * w));
-  LRFSI_TRY(S->Xf.alloc((size_t)K * M * w));
-  LRFSI_TRY(S->Vf.alloc((size_t)S->mtot * w));
+  // allocate everything first: on failure the handle keeps its old buffers
+  DevBuf<double> Xc, Q1, Q2, Vc, G, G2, T1, T2, sw, sv, gw;
+  DevBuf<int> iw;
+  DevBuf<float> Yf, Xf, Vf;
+  const size_t swork_per = trunc_small_work(width, S->mmax);
+  for (DevBuf<double>* b : {&Xc, &Q1, &Q2}) LRFSI_TRY(b->alloc((size_t)K * M * w));
+  LRFSI_TRY(Vc.alloc((size_t)S->mtot * w));
+  for (DevBuf<double>* b : {&G, &G2, &T1, &T2}) LRFSI_TRY(b->alloc((size_t)K * w * w));
+  LRFSI_TRY(sw.alloc(swork_per * K));
+  LRFSI_TRY(sv.alloc((size_t)K * w));
+  LRFSI_TRY(iw.alloc((size_t)2 * w * K));
+  LRFSI_TRY(gw.alloc(gram_work_len(K, M, width, width)));
+  LRFSI_TRY(Yf.alloc((size_t)K * M * w));
+  LRFSI_TRY(Xf.alloc((size_t)K * M * w));
+  LRFSI_TRY(Vf.alloc((size_t)S->mtot * w));
+  // the old buffers may still be read by queued work: swap, and let the
+  // destructors free them (cudaFree waits for the device)
+  S->Xcat.swap(Xc); S->Q1.swap(Q1); S->Q2.swap(Q2); S->Vcat.swap(Vc);
+  S->G.swap(G); S->G2.swap(G2); S->T1.swap(T1); S->T2.swap(T2);
+  S->swork.swap(sw); S->sv.swap(sv); S->gramwork.swap(gw); S->iwork.swap(iw);
+  S->Yf.swap(Yf); S->Xf.swap(Xf); S->Vf.swap(Vf);
+  S->swork_per = swork_per;
   S->ldP = width;
   return LRFSI_OK;
 }

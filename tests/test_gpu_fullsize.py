@@ -1,7 +1,8 @@
 """Full-size parity on sampled outputs: the 400-parameter workload on the 80x16
 mesh (M = 22629, 4 subsets of 100, rank cap 40) in the launch configuration
 the benchmark times (Chebyshev c = 0.65, d = 1, 6 steps x 2 cycles, eta 0.05,
-target 1e-6).  The oracle cannot run the whole method at this size in a test,
+target 1e-6; FP64, mixed, and FP64 with GMREST as the low-rank solver).  The
+oracle cannot run the whole method at this size in a test,
 so it checks what it can compute one by one: the Newton solution of one
 median parameter, and the nonlinear relative residual of sampled columns of
 the GPU result (the definition of the reported metric, Sec. 5.1.2), which must
@@ -42,14 +43,15 @@ def fullsize():
     it, res, st = lrfsi.lrfsi_newton_median(lm, X, mus[medians], nus[medians], 1e-8, 30)
     assert st == 0 and np.all(res <= 1e-8)
     out = {}
-    for precision in (0, 1):
+    for variant, precision, solver in (("fp64", 0, "chebyshev"), ("mixed", 1, "chebyshev"), ("gmrest", 0, "gmres")):
         sub = lrfsi.Subsets(lm, X, mus, nus, sizes, [R] * K)
         U = torch.zeros(K * lm.M * R, dtype=torch.float64, device=DEV)
         V = torch.zeros(m * R, dtype=torch.float64, device=DEV)
-        opt = lrfsi.cheb_options(0.65, 1.0, iters=6, cycles=2, rank_cap=R, tol=W.tol, eta=0.05, precision=precision)
+        opt = lrfsi.cheb_options(0.65, 1.0, iters=6, cycles=2, rank_cap=R, tol=W.tol, eta=0.05, precision=precision,
+                                 solver=solver)
         ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, 1e-6, 40, U, R, V, R)
         sub.close()
-        out[precision] = (ranks, rel, st, U.cpu().numpy(), V.cpu().numpy())
+        out[variant] = (ranks, rel, st, U.cpu().numpy(), V.cpu().numpy())
     return dict(W=W, lm=lm, om=om, perm=perm, mus=mus, nus=nus, K=K, R=R, m=m, sizes=sizes, medians=medians,
                 X=X.cpu().numpy(), out=out)
 
@@ -62,10 +64,10 @@ def test_fullsize_median_newton_matches_oracle(fullsize):
     assert rel_max(f["X"][q], xo[f["perm"]]) <= 1e-7
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-def test_fullsize_sampled_columns_residual_matches_oracle(fullsize, precision):
+@pytest.mark.parametrize("variant", ["fp64", "mixed", "gmrest"])
+def test_fullsize_sampled_columns_residual_matches_oracle(fullsize, variant):
     f = fullsize
-    ranks, rel, st, U, V = f["out"][precision]
+    ranks, rel, st, U, V = f["out"][variant]
     assert st == 0 and rel.max() <= 1e-6
     M, R, mloc = f["lm"].M, f["R"], f["m"] // f["K"]
     inv = np.argsort(f["perm"])
@@ -78,5 +80,5 @@ def test_fullsize_sampled_columns_residual_matches_oracle(fullsize, precision):
         vi = V[i * R:(i + 1) * R][:r]
         x = f["X"][q] + Uq @ vi
         ro = algorithm1.relative_residuals(f["om"], x[inv][:, None], f["mus"][i:i + 1], f["nus"][i:i + 1])[0]
-        assert ro <= 1e-6, (precision, i, ro)
-        assert ro == pytest.approx(rel[i], rel=1e-6, abs=1e-13), (precision, i, ro, rel[i])
+        assert ro <= 1e-6, (variant, i, ro)
+        assert ro == pytest.approx(rel[i], rel=1e-6, abs=1e-13), (variant, i, ro, rel[i])
