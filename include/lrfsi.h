@@ -260,18 +260,22 @@ int lrfsi_chebyshevT(lrfsi_subset_h sub, const double* UB_dev, int lduB, const d
  * the truncation (tol, rank cap R_k) applied to the starting residual, to
  * F(P^{-1} V_j), to the orthogonalised vector and to the updated iterate.  A
  * cycle is `iters` Arnoldi steps; it ends early when h_{j+1,j} = 0 or the
- * least-squares residual falls to eta ||B_k||_F.  Sums too wide for the
- * concatenation buffer are truncated in parts.  stats[k].steps counts Arnoldi
- * steps.  The Krylov basis (2 iters tall factors per subset) is allocated in
- * the handle on first use.  Errors as lrfsi_chebyshevT. */
+ * least-squares residual falls to eta ||B_k||_F.  stats[k].steps counts Arnoldi
+ * steps.  On first use the handle allocates the Krylov basis (2 iters tall
+ * factors per subset) and widens its concatenation buffers to
+ * (iters + 1) max_k R_k columns, so that every sum is truncated at once; the
+ * same happens in lrfsi_subset_step / _init with opt->solver = 1.  Errors as
+ * lrfsi_chebyshevT (LRFSI_ENOMEM if that allocation fails; the handle stays
+ * usable). */
 int lrfsi_gmresT(lrfsi_subset_h sub, const double* UB_dev, int lduB, const double* VB_dev, int ldvB,
                  const int* rB_host, const lrfsi_cheb_options* opt, double* U_dev, int ldu,
                  double* V_dev, int ldv, int* rank_host, lrfsi_cheb_stats* stats, lrfsi_stream_t stream);
 
 /* lrfsi_subset_step: one Newton step on every subset (Sec. 3.4,
  * Eq. (rhs_matrix1), Eq. (newton_matrix1)): B_k = -(R0 1^T + Rmu mu^T + Rnu nu^T),
- * S_k = ChebyshevT(B_k) (GMREST if opt->solver = 1); then, while some column's relative residual exceeds
- * target and fewer than max_outer corrections were taken, a correction in the
+ * S_k = ChebyshevT(B_k) (GMREST if opt->solver = 1); then, while some
+ * column's relative residual exceeds target and fewer than max_outer
+ * corrections were taken, a correction in the
  * same matrix form whose right-hand side is -R(X_i; mu_i, nu_i) evaluated
  * column by column (operators and preconditioners kept at xt_k; the sum of
  * corrections is truncated with the same rule).  Result per subset:
