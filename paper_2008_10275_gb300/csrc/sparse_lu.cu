@@ -282,10 +282,10 @@ static int spmm_variant(const SpmmBatch<T>& sb, int cnt, int rmax, const lrfsi_m
 template <class T>
 int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_t s) {
   const long M = m->h.M;
-  for (int base = 0; base < n; base += kMaxGemmDescs) {
+  for (int i = 0; i < n;) {  // chunks of up to kMaxGemmDescs non-empty products
     SpmmBatch<T> sb;
     int cnt = 0, rmax = 0;
-    for (int i = base; i < n && cnt < kMaxGemmDescs; ++i) {
+    for (; i < n && cnt < kMaxGemmDescs; ++i) {
       if (d[i].r <= 0) continue;
       sb.d[cnt++] = d[i];
       rmax = rmax > d[i].r ? rmax : d[i].r;
@@ -297,10 +297,10 @@ int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_
       // of the pattern (L2-resident reuse not counted), outputs written once
       const double nnz = (double)m->h.colidx.size();
       double fl = 0, by = 0;
-      for (int i = 0; i < cnt; ++i) {
-        const bool comb = sb.d[i].o[1] < 0;
-        fl += nnz * sb.d[i].r * (comb ? 2.0 : 6.0);
-        by += nnz * (4.0 + 3.0 * sizeof(T)) + 4.0 * (M + 1) + (double)M * sb.d[i].r * sizeof(T) * (comb ? 2.0 : 4.0);
+      for (int q = 0; q < cnt; ++q) {
+        const bool comb = sb.d[q].o[1] < 0;
+        fl += nnz * sb.d[q].r * (comb ? 2.0 : 6.0);
+        by += nnz * (4.0 + 3.0 * sizeof(T)) + 4.0 * (M + 1) + (double)M * sb.d[q].r * sizeof(T) * (comb ? 2.0 : 4.0);
       }
       account(sizeof(T) == 8 ? KC_SPMM : KC_SPMM32, fl, by);
     }
