@@ -244,8 +244,9 @@ def _qp_fields(mesh, x):
     return v, Gv, Gu, p
 
 
-def element_residual_terms(mesh, x):
-    """Element vectors of every term of Eq. (fsi_problem_weak1) on every cell.
+def element_residual_terms(mesh, x, rho=None, lam=None):
+    """Element vectors of every term of Eq. (fsi_problem_weak1) on every cell
+    (rho, lam: override the problem's rho_f, lambda_s; Sec. 4.4 varies them).
 
     Returns a dict of arrays over all cells (callers mask fluid / solid cells):
       conv[c,a,i]  = rho_f <(v . grad) v, phi_a e_i>
@@ -256,7 +257,8 @@ def element_residual_terms(mesh, x):
       smu[c,a,i]   = <G + G^T + G^T G, grad(phi_a e_i)>              (times mu)
       slam[c,a,i]  = lambda_s <tr(G + G^T G / 2), div(phi_a e_i)>
     """
-    rho, lam = mesh.prob.rho_f, mesh.prob.lam_s
+    rho = mesh.prob.rho_f if rho is None else rho
+    lam = mesh.prob.lam_s if lam is None else lam
     v, Gv, Gu, p = _qp_fields(mesh, x)
     w, N, dN, P = mesh.w, mesh.N, mesh.dN, mesh.P
     adv = np.einsum("cqj,cqij->cqi", v, Gv)                             # (v . grad) v
@@ -327,8 +329,9 @@ def affine_residual(mesh, x):
 # ----------------------------------------------------------------------------
 
 
-def element_jacobian_terms(mesh, x):
-    """Element matrices of the derivatives of every term, indexed
+def element_jacobian_terms(mesh, x, rho=None, lam=None):
+    """Element matrices of the derivatives of every term (rho, lam: override
+    the problem's rho_f, lambda_s), indexed
     [c, a, i, b, k] = d(term for test (a, i)) / d(trial dof (b, k)).
 
       conv_vv : rho_f * (phi_b d_k v_i + delta_ik v . grad phi_b) phi_a      (J_rho)
@@ -340,7 +343,8 @@ def element_jacobian_terms(mesh, x):
       slam_uu : lambda_s (d_k phi_b + G_k . grad phi_b) d_i phi_a            (J_lambda)
     with G = grad u, G_k the k-th row of G, ga = grad phi_a, gb = grad phi_b.
     """
-    rho, lam = mesh.prob.rho_f, mesh.prob.lam_s
+    rho = mesh.prob.rho_f if rho is None else rho
+    lam = mesh.prob.lam_s if lam is None else lam
     v, Gv, Gu, p = _qp_fields(mesh, x)
     w, N, dN, P = mesh.w, mesh.N, mesh.dN, mesh.P
     eye = np.eye(2)
@@ -444,6 +448,93 @@ def affine_jacobian(mesh, x):
     d = mesh.ident_rows
     J0.add(d, d, np.ones(len(d)))
     return J0.csr(), Jmu.csr(), Jnu.csr()
+
+
+# ----------------------------------------------------------------------------
+# Four parameters (Sec. 4.4, "Extension to further parameters"): mu_s, nu_f,
+# lambda_s and rho_f all vary; nu_f enters as the product nu_f rho_f.
+# ----------------------------------------------------------------------------
+
+
+def residual4(mesh, x, mu, nu, lam, rho):
+    """R(x; mu_s, nu_f, lambda_s, rho_f) assembled directly (Eq.
+    (fsi_problem_weak1) with all four constants given)."""
+    t = element_residual_terms(mesh, x, rho=rho, lam=lam)
+    F, S = ~mesh.cell_solid, mesh.cell_solid
+    mom = np.zeros_like(t["conv"])
+    mom[F] = t["conv"][F] + t["pres"][F] + nu * t["visc"][F]
+    mom[S] = mu * t["smu"][S] + t["slam"][S]
+    R = _scatter(mesh.M, mesh.momrow, mom)
+    R += _scatter(mesh.M, mesh.extrow[F], t["ext"][F])
+    R += _scatter(mesh.M, mesh.divrow[F], t["div"][F])
+    x = np.asarray(x, dtype=np.float64)
+    R[mesh.ident_rows] = x[mesh.ident_rows] - mesh.bD[mesh.ident_rows]
+    return R
+
+
+def jacobian4(mesh, x, mu, nu, lam, rho):
+    """J(x; mu_s, nu_f, lambda_s, rho_f) = dR/dx assembled directly (the
+    Jacobian of Sec. 4.4 with its reference values cancelled)."""
+    t = element_jacobian_terms(mesh, x, rho=rho, lam=lam)
+    F = np.flatnonzero(~mesh.cell_solid)
+    S = np.flatnonzero(mesh.cell_solid)
+    coo = _COO(mesh.M)
+    nf = len(F)
+    if nf:
+        _add_block(coo, mesh.momrow[F], mesh.vdof[F], t["conv"][F] + nu * _bcast(t["visc"], nf))
+        _add_block(coo, mesh.momrow[F], mesh.pdof[F], np.broadcast_to(t["pres"], (nf,) + t["pres"].shape))
+        _add_block(coo, mesh.divrow[F], mesh.vdof[F], np.broadcast_to(t["div"], (nf,) + t["div"].shape))
+        _add_block(coo, mesh.extrow[F], mesh.udof[F], np.broadcast_to(t["ext"], (nf,) + t["ext"].shape))
+    if len(S):
+        _add_block(coo, mesh.momrow[S], mesh.udof[S], mu * t["smu"][S] + t["slam"][S])
+    d = mesh.ident_rows
+    coo.add(d, d, np.ones(len(d)))
+    return coo.csr()
+
+
+def affine_residual4(mesh, x):
+    """(R0, Rmu, Rnurho, Rlam, Rrho) with R = R0 + mu Rmu + (nu rho) Rnurho +
+    lam Rlam + rho Rrho (Sec. 4.4, the right-hand side B_k^{mu,nu,lambda,rho}
+    with the reference values set to 0): Rmu = A1 x + g_mu(x), Rnurho = A2 x,
+    Rlam = A3 x + g_lambda(x), Rrho = g_rho(x) (convection), R0 the rest
+    (pressure, divergence, extension, Dirichlet rows x - b_D)."""
+    t1 = element_residual_terms(mesh, x, rho=1.0, lam=1.0)
+    F, S = ~mesh.cell_solid, mesh.cell_solid
+    M = mesh.M
+    R0 = _scatter(M, mesh.momrow[F], t1["pres"][F])
+    R0 += _scatter(M, mesh.extrow[F], t1["ext"][F])
+    R0 += _scatter(M, mesh.divrow[F], t1["div"][F])
+    x = np.asarray(x, dtype=np.float64)
+    R0[mesh.ident_rows] = x[mesh.ident_rows] - mesh.bD[mesh.ident_rows]
+    Rmu = _scatter(M, mesh.momrow[S], t1["smu"][S])
+    Rnurho = _scatter(M, mesh.momrow[F], t1["visc"][F])
+    Rlam = _scatter(M, mesh.momrow[S], t1["slam"][S])
+    Rrho = _scatter(M, mesh.momrow[F], t1["conv"][F])
+    return R0, Rmu, Rnurho, Rlam, Rrho
+
+
+def affine_jacobian4(mesh, x):
+    """(J0, Jmu', Jnurho', Jlam', Jrho') with J = J0 + mu Jmu' + (nu rho)
+    Jnurho' + lam Jlam' + rho Jrho' (Sec. 4.4, Eq. (matrix_fourpars1) with
+    the reference values set to 0): Jmu' = A1 + J_mu(x), Jnurho' = A2,
+    Jlam' = A3 + J_lambda(x), Jrho' = J_rho(x), J0 = A0."""
+    t1 = element_jacobian_terms(mesh, x, rho=1.0, lam=1.0)
+    F = np.flatnonzero(~mesh.cell_solid)
+    S = np.flatnonzero(mesh.cell_solid)
+    nf = len(F)
+    J0, Jmu, Jnr, Jlam, Jrho = (_COO(mesh.M) for _ in range(5))
+    if nf:
+        _add_block(J0, mesh.momrow[F], mesh.pdof[F], np.broadcast_to(t1["pres"], (nf,) + t1["pres"].shape))
+        _add_block(J0, mesh.divrow[F], mesh.vdof[F], np.broadcast_to(t1["div"], (nf,) + t1["div"].shape))
+        _add_block(J0, mesh.extrow[F], mesh.udof[F], np.broadcast_to(t1["ext"], (nf,) + t1["ext"].shape))
+        _add_block(Jnr, mesh.momrow[F], mesh.vdof[F], np.broadcast_to(t1["visc"], (nf,) + t1["visc"].shape))
+        _add_block(Jrho, mesh.momrow[F], mesh.vdof[F], t1["conv"][F])
+    if len(S):
+        _add_block(Jmu, mesh.momrow[S], mesh.udof[S], t1["smu"][S])
+        _add_block(Jlam, mesh.momrow[S], mesh.udof[S], t1["slam"][S])
+    d = mesh.ident_rows
+    J0.add(d, d, np.ones(len(d)))
+    return J0.csr(), Jmu.csr(), Jnr.csr(), Jlam.csr(), Jrho.csr()
 
 
 # ----------------------------------------------------------------------------

@@ -59,6 +59,31 @@ def apply_F(J0, Jmu, Jnu, S, mu_k, nu_k):
     return J0 @ S + (Jmu @ S) * np.asarray(mu_k)[None, :] + (Jnu @ S) * np.asarray(nu_k)[None, :]
 
 
+def apply_terms(terms, S):
+    """sum_t J_t S D_t for further affine terms [(J_t, diag(D_t))] (Sec. 4.4,
+    Eq. (matrix_fourpars1): the lambda and rho terms); 0 for none."""
+    return sum((J @ S) * np.asarray(c)[None, :] for J, c in terms)
+
+
+def rhs_terms(R_terms, coeffs):
+    """B_k = -(R0 1^T + sum_t R_t c_t^T) for the affine pieces [R0, R_1, ...]
+    and coefficient vectors [c_1, ...] (Sec. 4.4, B_k^{mu,nu,lambda,rho})."""
+    B = -np.outer(R_terms[0], np.ones(len(coeffs[0])))
+    for R, c in zip(R_terms[1:], coeffs):
+        B -= np.outer(R, np.asarray(c, float))
+    return B
+
+
+def brute_force4(mesh, xt, mu_k, nu_k, lam_k, rho_k):
+    """Exact four-parameter S_k column by column (the vector form of Eq.
+    (matrix_fourpars1)): J(x~; mu_i, nu_i, lam_i, rho_i) s_i = -R(x~; ...)."""
+    S = np.zeros((mesh.M, len(mu_k)))
+    for i in range(len(mu_k)):
+        J = fsi.jacobian4(mesh, xt, mu_k[i], nu_k[i], lam_k[i], rho_k[i])
+        S[:, i] = spla.splu(J.tocsc()).solve(-fsi.residual4(mesh, xt, mu_k[i], nu_k[i], lam_k[i], rho_k[i]))
+    return S
+
+
 def brute_force(mesh, xt, mu_k, nu_k):
     """Exact S_k column by column (Eq. (newtonstep_vectornot1))."""
     S = np.zeros((mesh.M, len(mu_k)))
@@ -87,14 +112,17 @@ def truncate(X, tol, rank_cap):
     return (U[:, :r] * s[:r]) @ Vt[:r]
 
 
-def preconditioner(J0, Jmu, Jnu, mu_bar, nu_bar):
-    """LU of P_T^k = J(x~; mu_bar, nu_bar) = J0 + mu_bar Jmu' + nu_bar Jnu' (Sec. 4.2)."""
-    P = (J0 + mu_bar * Jmu + nu_bar * Jnu).tocsc()
-    return spla.splu(P)
+def preconditioner(J0, Jmu, Jnu, mu_bar, nu_bar, extra=()):
+    """LU of P_T^k = J(x~; mu_bar, nu_bar) = J0 + mu_bar Jmu' + nu_bar Jnu' (Sec. 4.2)
+    (+ sum_t bar_t J_t for further affine terms extra = [(J_t, bar_t)], Sec. 4.4)."""
+    P = J0 + mu_bar * Jmu + nu_bar * Jnu
+    for J, b in extra:
+        P = P + b * J
+    return spla.splu(P.tocsc())
 
 
 def chebyshev_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, c, d, iters=6, cycles=2,
-                tol=1e-8, rank_cap=None, truncated=True, eta=None, history=None):
+                tol=1e-8, rank_cap=None, truncated=True, eta=None, history=None, extra_terms=()):
     """Truncated preconditioned Chebyshev iteration for F(S) = B, S0 = 0.
 
     One step j (centre d, half-width c, sigma = d / c, rho_0 = 1 / sigma):
@@ -107,11 +135,12 @@ def chebyshev_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, c, d, iters=6, cycles=2,
     The last step of a cycle stops after the update of S.  With ``eta`` the
     iteration also stops once ||B - F(S)||_F <= eta ||B||_F (checked whenever
     the true residual is formed).  ``history`` receives ||B - F(S)||_F / ||B||_F.
+    ``extra_terms`` [(J_t, diag(D_t))] adds further affine terms to F (Sec. 4.4).
     """
     m = B.shape[1]
     rank_cap = m if rank_cap is None else rank_cap
     T = (lambda X: truncate(X, tol, rank_cap)) if truncated else (lambda X: X)
-    F = lambda S: apply_F(J0, Jmu, Jnu, S, mu_k, nu_k)
+    F = lambda S: apply_F(J0, Jmu, Jnu, S, mu_k, nu_k) + apply_terms(extra_terms, S)
     sigma = d / c
     nB = np.linalg.norm(B)
     S = np.zeros_like(B)
@@ -147,7 +176,7 @@ def frobenius_inner(X, Y):
 
 
 def gmres_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, iters=6, cycles=2, tol=1e-8, rank_cap=None,
-            truncated=True, eta=None, history=None):
+            truncated=True, eta=None, history=None, extra_terms=()):
     """Truncated right-preconditioned restarted GMRES for F(S) = B, S0 = 0.
 
     One cycle from the current S:
@@ -163,11 +192,12 @@ def gmres_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, iters=6, cycles=2, tol=1e-8, rank
         S = T(S + sum_j y_j Z_j)
     The true residual is checked against eta at the start of every cycle;
     ``history`` receives ||B - F(S)||_F / ||B||_F there and at the end.
+    ``extra_terms`` [(J_t, diag(D_t))] adds further affine terms to F (Sec. 4.4).
     """
     m = B.shape[1]
     rank_cap = m if rank_cap is None else rank_cap
     T = (lambda X: truncate(X, tol, rank_cap)) if truncated else (lambda X: X)
-    F = lambda S: apply_F(J0, Jmu, Jnu, S, mu_k, nu_k)
+    F = lambda S: apply_F(J0, Jmu, Jnu, S, mu_k, nu_k) + apply_terms(extra_terms, S)
     nB = np.linalg.norm(B)
     S = np.zeros_like(B)
     for _ in range(cycles):
@@ -208,7 +238,7 @@ def gmres_T(J0, Jmu, Jnu, P_lu, B, mu_k, nu_k, iters=6, cycles=2, tol=1e-8, rank
     return S
 
 
-def equilibration(J0, Jmu, Jnu, mu_bar, nu_bar):
+def equilibration(J0, Jmu, Jnu, mu_bar, nu_bar, extra=()):
     """Row and column scales (r, c) of the max-norm equilibration of the
     preconditioner matrix P = J0 + mu_bar Jmu' + nu_bar Jnu':
         r_i = 1 / max_j |P_ij|,   c_j = 1 / max_i r_i |P_ij|
@@ -217,8 +247,10 @@ def equilibration(J0, Jmu, Jnu, mu_bar, nu_bar):
     equilibrated quantities -- the unknowns mix m/s, m and Pa and the
     equations mix fluid and solid (mu ~ 1e6) scales, so an unscaled Euclidean
     truncation discards the deformation components that dominate F(S)."""
-    P = (J0 + mu_bar * Jmu + nu_bar * Jnu).tocsr()
-    A = abs(P)
+    P = J0 + mu_bar * Jmu + nu_bar * Jnu
+    for J, b in extra:
+        P = P + b * J
+    A = abs(P.tocsr())
     rmax = A.max(axis=1).toarray().ravel()
     r = np.where(rmax > 0, 1.0 / np.where(rmax > 0, rmax, 1.0), 1.0)
     cmax = (sp.diags(r) @ A).max(axis=0).toarray().ravel()
@@ -226,27 +258,36 @@ def equilibration(J0, Jmu, Jnu, mu_bar, nu_bar):
     return r, c
 
 
-def chebyshev_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, c, d, **kw):
+def _scaled_system(J0, Jmu, Jnu, mu_bar, nu_bar, extra):
+    """The equilibrated operators, extra terms and preconditioner, and the
+    row and column scales (see ``equilibration``).  extra = [(J_t, diag(D_t),
+    bar_t)] for further affine terms (Sec. 4.4)."""
+    r, cc = equilibration(J0, Jmu, Jnu, mu_bar, nu_bar, [(J, b) for J, _, b in extra])
+    Dr, Dc = sp.diags(r), sp.diags(cc)
+    sc = lambda J: (Dr @ J @ Dc).tocsr()
+    J0s, Jmus, Jnus = sc(J0), sc(Jmu), sc(Jnu)
+    ext = [(sc(J), c, b) for J, c, b in extra]
+    P = preconditioner(J0s, Jmus, Jnus, mu_bar, nu_bar, [(J, b) for J, _, b in ext])
+    return J0s, Jmus, Jnus, [(J, c) for J, c, _ in ext], P, r, cc
+
+
+def chebyshev_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, c, d, extra=(), **kw):
     """ChebyshevT on the equilibrated equation diag(r) F(diag(c) S~) = diag(r) B
     with the equilibrated preconditioner; returns S = diag(c) S~.  The
-    spectrum of P^{-1} A is unchanged (similarity), so c and d are too."""
-    r, cc = equilibration(J0, Jmu, Jnu, mu_bar, nu_bar)
-    Dr, Dc = sp.diags(r), sp.diags(cc)
-    J0s, Jmus, Jnus = (Dr @ J0 @ Dc).tocsr(), (Dr @ Jmu @ Dc).tocsr(), (Dr @ Jnu @ Dc).tocsr()
-    P = preconditioner(J0s, Jmus, Jnus, mu_bar, nu_bar)
-    Ss = chebyshev_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, c, d, **kw)
+    spectrum of P^{-1} A is unchanged (similarity), so c and d are too.
+    extra = [(J_t, diag(D_t), bar_t)]: further affine terms (Sec. 4.4)."""
+    J0s, Jmus, Jnus, ext, P, r, cc = _scaled_system(J0, Jmu, Jnu, mu_bar, nu_bar, extra)
+    Ss = chebyshev_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, c, d, extra_terms=ext, **kw)
     return cc[:, None] * Ss
 
 
-def gmres_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, **kw):
+def gmres_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mu_bar, nu_bar, extra=(), **kw):
     """GMREST on the equilibrated equation diag(r) F(diag(c) S~) = diag(r) B
     with the equilibrated preconditioner; returns S = diag(c) S~.  GMRES
-    minimises the residual in the row-scaled norm ||diag(r) (B - F(S))||_F."""
-    r, cc = equilibration(J0, Jmu, Jnu, mu_bar, nu_bar)
-    Dr, Dc = sp.diags(r), sp.diags(cc)
-    J0s, Jmus, Jnus = (Dr @ J0 @ Dc).tocsr(), (Dr @ Jmu @ Dc).tocsr(), (Dr @ Jnu @ Dc).tocsr()
-    P = preconditioner(J0s, Jmus, Jnus, mu_bar, nu_bar)
-    Ss = gmres_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, **kw)
+    minimises the residual in the row-scaled norm ||diag(r) (B - F(S))||_F.
+    extra = [(J_t, diag(D_t), bar_t)]: further affine terms (Sec. 4.4)."""
+    J0s, Jmus, Jnus, ext, P, r, cc = _scaled_system(J0, Jmu, Jnu, mu_bar, nu_bar, extra)
+    Ss = gmres_T(J0s, Jmus, Jnus, P, r[:, None] * B, mu_k, nu_k, extra_terms=ext, **kw)
     return cc[:, None] * Ss
 
 

@@ -2,7 +2,8 @@
 
 Sec. 3.2, Eq. (newton_step_indiv1): A(x_{j-1}; mu, nu) dx_j = b_D - g(x_{j-1}),
 x_j = x_{j-1} + dx_j, started at x_0 = b_D (or a given start), stopped when
-the Euclidean residual norm is <= eps_N (Algorithm 1, Sec. 5.1).  The linear
+the Euclidean residual norm is <= eps_N (Algorithm 1, Sec. 5.1); ``newton4``
+is the same iteration for the four parameters of Sec. 4.4.  The linear
 solve is a sparse direct LU (SuperLU via scipy, a library primitive).
 
 Safeguard that the paper does not state: if the full
@@ -19,19 +20,31 @@ from . import fsi
 def newton(mesh, mu, nu, x0=None, eps=1e-8, max_it=30, source=None, history=None):
     """Returns (x, iterations, final residual norm).  ``history`` (a list)
     receives the residual norm of every iterate."""
+    return _iterate(mesh, lambda x: fsi.residual(mesh, x, mu, nu, source), lambda x: fsi.jacobian(mesh, x, mu, nu),
+                    x0, eps, max_it, history)
+
+
+def newton4(mesh, mu, nu, lam, rho, x0=None, eps=1e-8, max_it=30, history=None):
+    """The same iteration for the four-parameter problem of Sec. 4.4 (the
+    Jacobian A(x; mu_s, nu_f, lambda_s, rho_f) given there)."""
+    return _iterate(mesh, lambda x: fsi.residual4(mesh, x, mu, nu, lam, rho),
+                    lambda x: fsi.jacobian4(mesh, x, mu, nu, lam, rho), x0, eps, max_it, history)
+
+
+def _iterate(mesh, residual, jacobian, x0, eps, max_it, history):
     x = mesh.bD.copy() if x0 is None else np.array(x0, dtype=np.float64)
-    R = fsi.residual(mesh, x, mu, nu, source)
+    R = residual(x)
     r = np.linalg.norm(R)
     if history is not None:
         history.append(r)
     it = 0
     while r > eps and it < max_it:
-        J = fsi.jacobian(mesh, x, mu, nu)
+        J = jacobian(x)
         dx = spla.splu(J.tocsc()).solve(-R)
         t = 1.0
         for _ in range(20):
             xn = x + t * dx
-            Rn = fsi.residual(mesh, xn, mu, nu, source)
+            Rn = residual(xn)
             rn = np.linalg.norm(Rn)
             if rn < r or t < 1e-5:
                 break

@@ -3,7 +3,8 @@
 Sec. 3.3: little-endian order (Def. 1), clustering into K contiguous subsets
 (Eq. (clustering1)), upper median index (Def. "Upper Median Index", Ex. 2);
 Sec. 3.4: diagonal matrices D_mu^k, D_nu^k; Sec. 3.4 end: column p of the
-global approximation <-> (mu^{((p-1) mod m1)+1}, nu^{ceil(p/m1)}).
+global approximation <-> (mu^{((p-1) mod m1)+1}, nu^{ceil(p/m1)});
+Sec. 4.4: the four-parameter little-endian order.
 Indices in this module are 1-based where the paper's are, and say so.
 """
 from __future__ import annotations
@@ -16,6 +17,22 @@ def little_endian_order(m1, m2):
     (Def. 1): mu index runs fastest."""
     pairs = [(i1, i2) for i1 in range(1, m1 + 1) for i2 in range(1, m2 + 1)]
     return sorted(pairs, key=lambda t: t[0] + (t[1] - 1) * m1)
+
+
+def little_endian_order4(m1, m2, m3, m4):
+    """All multi-indices (i1, i2, i3, i4), 1-based, sorted by the key
+    i1 + (i2-1) m1 + (i3-1) m1 m2 + (i4-1) m1 m2 m3 (Sec. 4.4, "Clustering"):
+    the mu index runs fastest, then nu, lambda, rho."""
+    tuples = [(a, b, c, d) for a in range(1, m1 + 1) for b in range(1, m2 + 1)
+              for c in range(1, m3 + 1) for d in range(1, m4 + 1)]
+    return sorted(tuples, key=lambda t: t[0] + (t[1] - 1) * m1 + (t[2] - 1) * m1 * m2 + (t[3] - 1) * m1 * m2 * m3)
+
+
+def affine_midpoints(*coeffs):
+    """Midpoints of the ranges of the subset's affine coefficients (the
+    mean-based preconditioner's coefficients, reading of Sec. 4.2 applied to
+    every coefficient; for four parameters they are mu, nu rho, lambda, rho)."""
+    return tuple(0.5 * (np.min(c) + np.max(c)) for c in coeffs)
 
 
 def cluster_sizes(m, K):
