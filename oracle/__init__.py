@@ -14,12 +14,14 @@ Contents (each function cites the passage of the paper it follows):
                    element residual R(x; mu, nu) and Jacobian J(x; mu, nu) of the
                    stationary FSI weak form (Sec. 2, Eq. (fsi_problem_weak1)),
                    both assembled directly and as the affine pieces
-                   R0, Rmu, Rnu / J0, Jmu', Jnu' (Sec. 3, Eq. (pardep_matrix1)).
+                   R0, Rmu, Rnu / J0, Jmu', Jnu' (Sec. 3, Eq. (pardep_matrix1));
+                   the four-parameter forms of Sec. 4.4 (``*4``).
 * ``params``    -- little-endian ordering, clustering into K subsets, upper
                    median index, diagonal matrices (Sec. 3.3, Def. 1, Eq.
                    (clustering1), Ex. 1-2; Sec. 3.4 Def. "Diagonal Matrices").
 * ``newton``    -- per-parameter Newton iteration with a sparse direct solve
-                   (Sec. 3.2, Eq. (newton_step_indiv1)).
+                   (Sec. 3.2, Eq. (newton_step_indiv1); four parameters,
+                   Sec. 4.4).
 * ``lowrank``   -- the subset matrix equation F(S_k) = B_k (Sec. 3.4, Eq.
                    (rhs_matrix1), Eq. (newton_matrix1)), its brute-force
                    column-by-column solution (Eq. (newtonstep_vectornot1)), the
