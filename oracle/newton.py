@@ -69,3 +69,11 @@ def standard_newton(mesh, mus, nus, eps=1e-6, max_it=30, x0=None):
         steps += it
         norms.append(r)
     return X, steps, np.array(norms)
+
+
+def standard_newton_problem(nx, ny, mus, nus, eps=1e-6, max_it=30):
+    """standard_newton on a freshly built nx x ny channel mesh; returns the
+    Newton steps taken (a self-contained unit of work for a process pool)."""
+    mesh = fsi.Mesh(fsi.Problem(nx, ny))
+    X, steps, norms = standard_newton(mesh, mus, nus, eps=eps, max_it=max_it)
+    return int(steps)
