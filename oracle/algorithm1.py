@@ -15,6 +15,10 @@ R(X_i; mu_i, nu_i) and the operators and preconditioner kept at x~.
 
 Relative residual of a column (Sec. 5.1.2):
 ||R(x_i; mu_i, nu_i)||_2 / ||R(b_D; mu_i, nu_i)||_2.
+
+Four parameters (Sec. 4.4): the same algorithm over the little-endian order of
+(mu_s, nu_f, lambda_s, rho_f) with the matrix equation replaced by Eq.
+(matrix_fourpars1) (``*4`` functions).
 """
 from __future__ import annotations
 
@@ -88,6 +92,64 @@ def algorithm1(mesh, mus, nus, opt: Options):
         info["medians"].append(int(med))
         info["xt"].append(xt)
         X[:, idx] = subset_step(mesh, xt, mus[idx], nus[idx], opt)
+        if opt.warm_start:
+            x_prev = xt
+        start += size
+    return X, info
+
+
+def relative_residuals4(mesh, X, mus, nus, lams, rhos):
+    """Sec. 5.1.2's relative residual for the four-parameter problem."""
+    out = np.zeros(X.shape[1])
+    for i in range(X.shape[1]):
+        num = np.linalg.norm(fsi.residual4(mesh, X[:, i], mus[i], nus[i], lams[i], rhos[i]))
+        den = np.linalg.norm(fsi.residual4(mesh, mesh.bD, mus[i], nus[i], lams[i], rhos[i]))
+        out[i] = num / den
+    return out
+
+
+def subset_step4(mesh, xt, mu_k, nu_k, lam_k, rho_k, opt: Options, history=None):
+    """One Newton step on a four-parameter subset (Eq. (matrix_fourpars1):
+    affine coefficients mu, nu rho, lambda, rho; the mean-based
+    preconditioner at the midpoints of their ranges) plus ``opt.chord_steps``
+    chord corrections.  Returns X^k (M x m_k)."""
+    mu_k, nu_k, lam_k, rho_k = (np.asarray(a, float) for a in (mu_k, nu_k, lam_k, rho_k))
+    nr_k = nu_k * rho_k
+    J0, Jmu, Jnr, Jlam, Jrho = fsi.affine_jacobian4(mesh, xt)
+    B = lowrank.rhs_terms(fsi.affine_residual4(mesh, xt), [mu_k, nr_k, lam_k, rho_k])
+    mb, nrb, lb, rb = params.affine_midpoints(mu_k, nr_k, lam_k, rho_k)
+    extra = [(Jlam, lam_k, lb), (Jrho, rho_k, rb)]
+    kw = dict(iters=opt.iters, cycles=opt.cycles, tol=opt.tol, rank_cap=opt.rank_cap,
+              truncated=opt.truncated, eta=opt.eta, history=history, extra=extra)
+    if opt.solver == "gmres":
+        run = lambda B_: lowrank.gmres_T_scaled(J0, Jmu, Jnr, B_, mu_k, nr_k, mb, nrb, **kw)
+    else:
+        run = lambda B_: lowrank.chebyshev_T_scaled(J0, Jmu, Jnr, B_, mu_k, nr_k, mb, nrb, opt.c, opt.d, **kw)
+    X = xt[:, None] + run(B)
+    for _ in range(opt.chord_steps):
+        Bc = -np.stack([fsi.residual4(mesh, X[:, i], mu_k[i], nu_k[i], lam_k[i], rho_k[i])
+                        for i in range(len(mu_k))], axis=1)
+        X = X + run(Bc)
+    return X
+
+
+def algorithm1_4(mesh, mus, nus, lams, rhos, opt: Options):
+    """Algorithm 1 for four parameters over an already ordered parameter list
+    (Sec. 4.4).  Returns (X, info)."""
+    mus, nus, lams, rhos = (np.asarray(a, float) for a in (mus, nus, lams, rhos))
+    m = len(mus)
+    X = np.zeros((mesh.M, m))
+    info = dict(newton_steps=[], medians=[], xt=[])
+    start = 0
+    x_prev = None
+    for size in params.cluster_sizes(m, opt.K):
+        idx = np.arange(start, start + size)
+        med = idx[params.upper_median_position(size)]
+        xt, it, r = newton.newton4(mesh, mus[med], nus[med], lams[med], rhos[med], x0=x_prev, eps=opt.eps_N)
+        info["newton_steps"].append(it)
+        info["medians"].append(int(med))
+        info["xt"].append(xt)
+        X[:, idx] = subset_step4(mesh, xt, mus[idx], nus[idx], lams[idx], rhos[idx], opt)
         if opt.warm_start:
             x_prev = xt
         start += size

@@ -149,3 +149,23 @@ def test_untruncated_solvers_with_further_terms_converge(mesh, subset, solver):
         S = lowrank.chebyshev_T_scaled(J0, Jmu, Jnr, B, mu, nu * rho, mb, nrb, 0.5, 1.0, extra=extra, iters=6,
                                        cycles=6, truncated=False)
     assert np.linalg.norm(S - S_bf) <= 1e-8 * np.linalg.norm(S_bf)
+
+
+@pytest.mark.parametrize("solver", ["chebyshev", "gmres"])
+def test_algorithm1_four_parameters_reaches_the_target(mesh, solver):
+    """Algorithm 1 with Eq. (matrix_fourpars1) on a 2 x 2 x 2 x 2 set in
+    little-endian order, K = 2: untruncated subset steps plus chord
+    corrections bring every column below 1e-8; the column order is the
+    four-index order."""
+    from oracle import algorithm1
+    grid = (np.array([6e5, 9e5]), np.array([2.8e-3, 3.4e-3]), np.array([1.8e6, 2.3e6]), np.array([0.9e3, 1.1e3]))
+    order = params.little_endian_order4(2, 2, 2, 2)
+    mus, nus, lams, rhos = (np.array([g[t[q] - 1] for t in order]) for q, g in enumerate(grid))
+    assert list(mus[:2]) == [6e5, 9e5] and nus[1] == 2.8e-3 and nus[2] == 3.4e-3 and lams[4] == 2.3e6
+    # the chord corrections contract ~10x each (4e-2 after the subset step, 9e-11 after 7)
+    opt = algorithm1.Options(K=2, c=0.5, d=1.0, iters=6, cycles=3, truncated=False, chord_steps=7, solver=solver,
+                             eps_N=1e-10)
+    X, info = algorithm1.algorithm1_4(mesh, mus, nus, lams, rhos, opt)
+    rr = algorithm1.relative_residuals4(mesh, X, mus, nus, lams, rhos)
+    assert rr.max() < 1e-8, rr.max()
+    assert info["medians"] == [4, 12]
