@@ -55,9 +55,9 @@ def relative_residuals(mesh, X, mus, nus):
     return out
 
 
-def subset_step(mesh, xt, mu_k, nu_k, opt: Options, X0=None, history=None):
-    """One Newton step on a subset (Sec. 3.4) plus ``opt.chord_steps`` chord
-    corrections.  Returns X^k (M x m_k)."""
+def _subset_solver(mesh, xt, mu_k, nu_k, opt: Options, history=None):
+    """The subset's right-hand side B_k and the low-rank solve F_k(S) = B'
+    (operators and preconditioner at x~)."""
     J0, Jmu, Jnu = fsi.affine_jacobian(mesh, xt)
     R0, Rmu, Rnu = fsi.affine_residual(mesh, xt)
     mu_bar, nu_bar = params.midpoint_parameters(mu_k, nu_k)
@@ -69,11 +69,37 @@ def subset_step(mesh, xt, mu_k, nu_k, opt: Options, X0=None, history=None):
     else:
         run = lambda B_: lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B_, mu_k, nu_k, mu_bar, nu_bar, opt.c, opt.d,
                                                     **kw)
+    return B, run
+
+
+def _chord_rhs(mesh, X, mu_k, nu_k):
+    return -np.stack([fsi.residual(mesh, X[:, i], mu_k[i], nu_k[i]) for i in range(len(mu_k))], axis=1)
+
+
+def subset_step(mesh, xt, mu_k, nu_k, opt: Options, X0=None, history=None):
+    """One Newton step on a subset (Sec. 3.4) plus ``opt.chord_steps`` chord
+    corrections.  Returns X^k (M x m_k)."""
+    B, run = _subset_solver(mesh, xt, mu_k, nu_k, opt, history)
     X = xt[:, None] + run(B)
     for _ in range(opt.chord_steps):
-        Bc = -np.stack([fsi.residual(mesh, X[:, i], mu_k[i], nu_k[i]) for i in range(len(mu_k))], axis=1)
-        X = X + run(Bc)
+        X = X + run(_chord_rhs(mesh, X, mu_k, nu_k))
     return X
+
+
+def subset_step_to_target(mesh, xt, mu_k, nu_k, opt: Options, target, max_chord=40):
+    """The subset step followed by chord corrections until every column's
+    relative residual (Sec. 5.1.2) is <= target or max_chord corrections were
+    made (reading for targets beyond one step).  Returns (X, corrections,
+    relative residuals)."""
+    B, run = _subset_solver(mesh, xt, mu_k, nu_k, opt)
+    X = xt[:, None] + run(B)
+    k = 0
+    rr = relative_residuals(mesh, X, mu_k, nu_k)
+    while rr.max() > target and k < max_chord:
+        X = X + run(_chord_rhs(mesh, X, mu_k, nu_k))
+        k += 1
+        rr = relative_residuals(mesh, X, mu_k, nu_k)
+    return X, k, rr
 
 
 def algorithm1(mesh, mus, nus, opt: Options):

@@ -140,7 +140,7 @@ def test_eta_stops_at_the_first_cycle_that_meets_it():
 
 @pytest.fixture(scope="module")
 def small_subset():
-    m = fsi.Mesh(fsi.Problem(10, 2))
+    m = fsi.Mesh(fsi.Problem(20, 4))   # the flap is 1 x 2 cells: mu_s acts
     mu_k = np.repeat(np.linspace(6e5, 9e5, 3), 2)
     nu_k = np.tile(np.array([3.0e-3, 3.4e-3]), 3)
     med = params.upper_median_position(len(mu_k))
@@ -159,7 +159,9 @@ def test_untruncated_gmres_converges_to_brute_force(small_subset):
     for cycles in (1, 2, 3):
         S = lowrank.gmres_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mb, nb, iters=6, cycles=cycles, truncated=False)
         errs.append(np.linalg.norm(S - S_bf) / np.linalg.norm(S_bf))
-    assert errs[0] > errs[1] > errs[2] and errs[2] < 1e-9, errs
+    # the second cycle gains orders of magnitude; the third sits at the
+    # rounding floor of the comparison (~1e-11)
+    assert errs[0] > 10 * errs[1] and max(errs[1:]) < 1e-9, errs
     S_t = lowrank.gmres_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mb, nb, iters=6, cycles=3, tol=1e-12,
                                  rank_cap=len(mu_k))
     assert np.linalg.norm(S_t - S_bf) <= 1e-9 * np.linalg.norm(S_bf)

@@ -61,7 +61,8 @@ def test_truncation_closed_form():
 
 @pytest.fixture(scope="module")
 def small_subset():
-    m = fsi.Mesh(fsi.Problem(10, 2))
+    m = fsi.Mesh(fsi.Problem(20, 4))   # the flap is 1 x 2 cells: mu_s acts (the 10 x 2 mesh has no solid cell)
+    assert m.cell_solid.any()
     mu_k = np.repeat(np.linspace(6e5, 9e5, 3), 2)
     nu_k = np.tile(np.array([3.0e-3, 3.4e-3]), 3)
     med = params.upper_median_position(len(mu_k))
@@ -111,7 +112,8 @@ def test_relative_residual_definition_and_subset_step(small_subset):
     m, xt, mu_k, nu_k = small_subset
     rr0 = algorithm1.relative_residuals(m, np.repeat(m.bD[:, None], len(mu_k), 1), mu_k, nu_k)
     assert np.allclose(rr0, 1.0)
-    opt = algorithm1.Options(c=0.5, d=1.0, iters=6, cycles=3, truncated=False, chord_steps=3)
+    # the chord corrections contract ~15-30x each here (5.8e-7 after 3, 6.5e-11 after 6)
+    opt = algorithm1.Options(c=0.5, d=1.0, iters=6, cycles=3, truncated=False, chord_steps=6)
     X = algorithm1.subset_step(m, xt, mu_k, nu_k, opt)
     rr = algorithm1.relative_residuals(m, X, mu_k, nu_k)
     assert rr.max() < 1e-8
@@ -134,3 +136,19 @@ def test_equilibration_unit_max_norms_and_scaling_invariance(small_subset):
     S2 = lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B, mu_k, nu_k, mb, nb, 0.5, 1.0, iters=5, cycles=2,
                                     truncated=False)
     assert np.linalg.norm(S1 - S2) <= 1e-10 * np.linalg.norm(S1)
+
+
+def test_subset_step_to_target_stops_at_the_first_correction_that_meets_it(small_subset):
+    m, xt, mu_k, nu_k = small_subset
+    opt = algorithm1.Options(c=0.5, d=1.0, iters=6, cycles=1, truncated=False)
+    X, k, rr = algorithm1.subset_step_to_target(m, xt, mu_k, nu_k, opt, 1e-9)
+    assert rr.max() <= 1e-9 and k >= 1
+    # the same iterate as the fixed-count subset step with k corrections, and
+    # k - 1 corrections were not enough
+    opt.chord_steps = k
+    Xk = algorithm1.subset_step(m, xt, mu_k, nu_k, opt)
+    assert np.abs(Xk - X).max() <= 1e-12 * np.abs(X).max()
+    opt.chord_steps = k - 1
+    rr_prev = algorithm1.relative_residuals(m, algorithm1.subset_step(m, xt, mu_k, nu_k, opt), mu_k, nu_k)
+    assert rr_prev.max() > 1e-9
+    assert np.allclose(rr, algorithm1.relative_residuals(m, X, mu_k, nu_k))
