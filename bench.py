@@ -129,6 +129,35 @@ print(json.dumps(dict(seconds=dt, steps=int(steps), n=n, procs=p)))
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
+def cpu_algorithm1(workload, n_sample, c=0.65, d=1.0, eta=0.05, target=1e-6):
+    """The oracle's own Algorithm 1 (Sec. 4; dense truncated ChebyshevT with
+    the workload's rank cap and tolerance) on the first n_sample parameters as
+    one subset: the median's Newton solve, then the subset step with chord
+    corrections until every column is <= target; one thread, fresh process."""
+    code = f"""
+import sys, time, json, numpy as np
+sys.path.insert(0, {ROOT!r})
+from oracle import algorithm1, fsi, newton, params
+from paper_2008_10275_gb300 import inputs
+W = inputs.WORKLOADS[{workload!r}]
+mus, nus = inputs.workload_parameters(W)
+mu, nu = mus[:{n_sample}], nus[:{n_sample}]
+m = fsi.Mesh(fsi.Problem(W.nx, W.ny))
+opt = algorithm1.Options(K=1, rank_cap=W.rank_cap, tol=W.tol, c={c!r}, d={d!r}, iters=6, cycles=2, eta={eta!r})
+t = time.perf_counter()
+med = params.upper_median_position(len(mu))
+xt, it, r = newton.newton(m, mu[med], nu[med], eps={EPS_N!r})
+X, k, rr = algorithm1.subset_step_to_target(m, xt, mu, nu, opt, {target!r})
+dt = time.perf_counter() - t
+print(json.dumps(dict(seconds=dt, n=len(mu), newton=int(it), corrections=int(k), max_relres=float(rr.max()))))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
 def run_reference(args, rank, world):
     """The oracle's standard Newton on all host cores: every step solves a
     bounded sample of 2 parameters per core (consecutive chunks, one
@@ -501,6 +530,13 @@ def main():
             cpu = {"value": r["n"] / r["seconds"], "unit": "params/s", "cores": 1, "kind": "oracle",
                    "sample": f"standard Newton (eps {EPS_N:g}) on the first {args.ref_sample} of {m} parameters, "
                              f"{r['steps']} Newton steps, {r['seconds']:.1f} s"}
+            ra = cpu_algorithm1(args.workload, 20, c=args.c, d=args.d, eta=args.eta, target=args.target)
+            cpu["algorithm1"] = {"value": ra["n"] / ra["seconds"], "unit": "params/s", "cores": 1,
+                                 "sample": f"the oracle's Algorithm 1 (dense truncated ChebyshevT, rank cap "
+                                           f"{W.rank_cap}, tol {W.tol:g}) on the first {ra['n']} parameters as one "
+                                           f"subset: median Newton ({ra['newton']} steps), subset step and "
+                                           f"{ra['corrections']} chord corrections to max relres "
+                                           f"{ra['max_relres']:.1e}, {ra['seconds']:.1f} s"}
             cores = host_cores()
             if cores > 1:  # the same method on every host core, 2 parameters per core
                 ra = cpu_reference(args.workload, 2 * cores, procs=cores)

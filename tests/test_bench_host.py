@@ -1,7 +1,7 @@
 """The benchmark's host-side legs (CPU only): the oracle's standard Newton on
 one core and spread over spawned single-threaded processes, and the
-`--impl reference` JSON line.  Small 20 x 4 workload so that they take
-seconds."""
+`--impl reference` JSON line, and the oracle's Algorithm 1 on a bounded
+sample.  Small samples so that they take seconds."""
 import json
 import os
 import subprocess
@@ -45,3 +45,9 @@ def test_reference_arm_other_ranks_exit_without_work(rank):
                           "small", "--steps", "1", "--warmup", "0"], capture_output=True, text=True, timeout=600,
                          cwd=ROOT, env=env)
     assert out.returncode == 0 and not [l for l in out.stdout.splitlines() if l.startswith("{")]
+
+
+def test_cpu_algorithm1_reaches_the_target():
+    # the first parameters of the 80 x 16 grid share nu_f (mu_s runs fastest): one narrow subset
+    r = bench.cpu_algorithm1("medium", 4)
+    assert r["n"] == 4 and r["max_relres"] <= 1e-6 and r["seconds"] > 0 and r["newton"] >= 1
