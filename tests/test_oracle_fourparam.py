@@ -169,3 +169,26 @@ def test_algorithm1_four_parameters_reaches_the_target(mesh, solver):
     rr = algorithm1.relative_residuals4(mesh, X, mus, nus, lams, rhos)
     assert rr.max() < 1e-8, rr.max()
     assert info["medians"] == [4, 12]
+
+
+def test_five_operators_from_three_two_parameter_assemblies(mesh):
+    """The two-parameter affine assembly at (rho_f, lambda_s) = (0, 0), (1, 0),
+    (0, 1) yields the five four-parameter operators: the rho and lambda parts
+    live in element blocks of their own (fluid momentum x velocity, solid
+    momentum x deformation), so the differences below cancel nothing.  Here
+    they agree to the rounding of the sparse assembly's summation order (the
+    explicit zero entries of the rho = 0 pass reorder it)."""
+    import dataclasses
+    x = _state(mesh, 8)
+
+    def aff(rho, lam):
+        m = fsi.Mesh(dataclasses.replace(mesh.prob, rho_f=rho, lam_s=lam))
+        return [A.toarray() for A in fsi.affine_jacobian(m, x)]
+
+    a00, a10, a01 = aff(0.0, 0.0), aff(1.0, 0.0), aff(0.0, 1.0)
+    J0, Jmu, Jnr, Jlam, Jrho = (A.toarray() for A in fsi.affine_jacobian4(mesh, x))
+    close = lambda a, b: np.abs(a - b).max() <= 1e-15 * np.abs(b).max()
+    assert close(a00[0], J0) and close(a00[1], Jmu)
+    assert close(a10[2], Jnr)                               # Jnu' = rho_f A2
+    assert close(a10[0] - a00[0], Jrho)
+    assert close(a01[0] - a00[0], Jlam)
