@@ -32,16 +32,28 @@ sys.path.insert(0, ROOT)
 from paper_2008_10275_gb300 import inputs, multi  # noqa: E402
 
 METRIC = "parameter solves/sec to nonlinear rel. residual 1e-6"
-FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (profiling recipe's table)
 EPS_N = 1e-6                 # median Newton stopping tolerance ||R||_2 (the paper's epsilon_N, Sec. 5)
 
 
-def subset_layout(m, K):
-    base = m // K
-    sizes = [base] * (K - 1) + [m - (K - 1) * base]
-    offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)
-    medians = [int(o + s // 2) for o, s in zip(offs, sizes)]
-    return sizes, medians
+def fp64_peak(dev, n=4096, reps=10):
+    """Measured FP64 rate of this GPU: a cuBLAS DGEMM n^3 (torch.matmul on
+    float64), best of ``reps`` by CUDA events (the FP64 counterpart of the
+    bf16 GEMM peak measured for the pool)."""
+    import torch
+    a = torch.randn(n, n, dtype=torch.float64, device=dev)
+    b = torch.randn(n, n, dtype=torch.float64, device=dev)
+    c = a @ b
+    best = float("inf")
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12, f"cuBLAS DGEMM {n}^3 measured in this run (best of {reps})"
 
 
 class Clocks:
@@ -105,8 +117,14 @@ import sys, time, json, multiprocessing as mp, numpy as np
 sys.path.insert(0, {ROOT!r})
 from oracle import fsi, newton
 from paper_2008_10275_gb300 import inputs
+from oracle import params
 W = inputs.WORKLOADS[{workload!r}]
-mus, nus = inputs.workload_parameters(W)
+mu_v, nu_v = inputs.workload_values(W)
+if W.seed is None:
+    mus, nus = params.ordered_grid(mu_v, nu_v, W.nu_fastest)
+else:
+    o = params.order_set(mu_v, nu_v)
+    mus, nus = mu_v[o], nu_v[o]
 n, p = {n_sample}, {procs}
 if p == 1:
     m = fsi.Mesh(fsi.Problem(W.nx, W.ny))
@@ -140,7 +158,12 @@ sys.path.insert(0, {ROOT!r})
 from oracle import algorithm1, fsi, newton, params
 from paper_2008_10275_gb300 import inputs
 W = inputs.WORKLOADS[{workload!r}]
-mus, nus = inputs.workload_parameters(W)
+mu_v, nu_v = inputs.workload_values(W)
+if W.seed is None:
+    mus, nus = params.ordered_grid(mu_v, nu_v, W.nu_fastest)
+else:
+    o = params.order_set(mu_v, nu_v)
+    mus, nus = mu_v[o], nu_v[o]
 mu, nu = mus[:{n_sample}], nus[:{n_sample}]
 m = fsi.Mesh(fsi.Problem(W.nx, W.ny))
 opt = algorithm1.Options(K=1, rank_cap=W.rank_cap, tol=W.tol, c={c!r}, d={d!r}, iters=6, cycles=2, eta={eta!r})
@@ -199,7 +222,7 @@ def run_learned(args, rank, world):
     from the median solution), the learned start in FP64, and the learned
     start with the mixed-precision inner residual (the line's value)."""
     import torch
-    from paper_2008_10275_gb300 import build, lrfsi
+    from paper_2008_10275_gb300 import algorithm1, build, lrfsi
     build.build()
     lrfsi.load()
     dev = "cuda:0"
@@ -211,10 +234,8 @@ def run_learned(args, rank, world):
             for pr in (0, 1)]
 
     def layout(mus, nus, K):
-        o = np.lexsort((mus, nus))  # nu_f-major, as the grids' little-endian order
-        mus, nus = mus[o], nus[o]
-        sizes, medians = subset_layout(len(mus), K)
-        return mus, nus, sizes, medians
+        Ly = algorithm1.set_layout(mus, nus, K=K, rank_cap=R)  # nu_f-major, mu fastest
+        return Ly.mu, Ly.nu, Ly.sizes.tolist(), Ly.medians.tolist()
 
     def solve(mus, nus, K, ls=None, precision=0):
         """Method on (mus, nus): returns dense solutions (M x m) and stats."""
@@ -269,7 +290,7 @@ def run_learned(args, rank, world):
     Xtrain = Xt.T.contiguous()  # problem-major
     ms_fit, loss = timed(lambda: ls.fit(Xtrain, mu_ts, nu_ts, epochs=12000, lr=2e-3))
     # evaluation on 2000 held-out parameters
-    mu_e, nu_e = inputs.workload_parameters(W)
+    mu_e, nu_e = inputs.workload_values(W)
     for _ in range(max(1, args.warmup)):
         solve(mu_e[:200], nu_e[:200], 2)
         solve(mu_e[:200], nu_e[:200], 2, ls)
@@ -336,31 +357,21 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    from paper_2008_10275_gb300 import build, lrfsi
+    from paper_2008_10275_gb300 import algorithm1, build, lrfsi
     build.build()
     lrfsi.load()
     dev = f"cuda:{local}"
     W = inputs.WORKLOADS[args.workload]
-    mus, nus = inputs.workload_parameters(W, rank, world)
-    if W.seed is not None:  # random parameters: nu_f-major order, as the grids' little-endian order
-        o = np.lexsort((mus, nus))
-        mus, nus = mus[o], nus[o]
-    m = len(mus)
-    K = W.K
-    if W.subset_sizes:  # uneven subsets with their own rank caps
-        sizes = list(W.subset_sizes)
-        offs = np.concatenate([[0], np.cumsum(sizes)[:-1]]).astype(int)
-        medians = [int(o + q // 2) for o, q in zip(offs, sizes)]
-        caps = list(W.rank_caps)
-    else:
-        sizes, medians = subset_layout(m, K)
-        caps = [W.rank_cap] * K
+    # one workload for the whole job: `world` copies of the configuration's
+    # shape, its subsets dealt out to the processes in contiguous blocks
+    # balanced by m_k R_k; one gather of the results to process 0 per step
+    job = algorithm1.workload_layout(W, replicas=world)
+    first = algorithm1.partition(job, world)
+    L = job.part(int(first[rank]), int(first[rank + 1]))
+    m, K = L.m, L.K
     mesh = lrfsi.Mesh(W.nx, W.ny)
     bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=dev)
-    R = max(caps)
-    U = torch.zeros(K * mesh.M * R, dtype=torch.float64, device=dev)
-    V = torch.zeros(m * R, dtype=torch.float64, device=dev)
-    eps_N = EPS_N
+    R = int(job.caps.max())
 
     opt_mixed = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=1,
                                    eta=args.eta)
@@ -368,31 +379,28 @@ def main():
                              eta=args.eta)
     opt_gmres = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=0,
                                    eta=args.eta, solver="gmres")
+    run = algorithm1.Runner(mesh, L, opt, target=args.target, max_outer=args.max_outer, eps_N=EPS_N, device=dev)
+    U, V = run.U, run.V
+    mus, nus = L.mu, L.nu
 
     def step(mu_h, nu_h, o=None):
-        X = bD.repeat(K, 1)
-        it, res, _ = lrfsi.lrfsi_newton_median(mesh, X, mu_h[medians], nu_h[medians], eps_N, 30)
-        sub = lrfsi.Subsets(mesh, X, mu_h, nu_h, sizes, caps)
-        ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, o or opt, args.target, args.max_outer, U, R, V, R)
-        sub.close()
-        return dict(newton_iters=it.tolist(), ranks=ranks.tolist(), outer=outer.tolist(), max_relres=float(rel.max()),
-                    status=int(st), xt=X)
+        res = run.step(mu_h, nu_h, o)
+        if dist is not None:
+            packed = multi.pack(res["xt"], U, V, res["ranks"], res["relres"], mesh.M, R)
+            multi.gather_results(job, first, rank, world, packed, mesh.M, R, dist, device=dev)
+        return dict(newton_iters=res["newton_iters"].tolist(), ranks=res["ranks"].tolist(),
+                    outer=res["outer"].tolist(), max_relres=float(res["relres"].max()) if m else 0.0,
+                    status=res["status"], xt=res["xt"])
 
     def dense_solution(info):
-        """X = x~_k 1^T + U_k V_k^T for every subset (M x m) from the last step."""
-        cols = []
-        for k in range(K):
-            r = info["ranks"][k]
-            Uk = U[k * mesh.M * R:(k + 1) * mesh.M * R].view(mesh.M, R)[:, :r]
-            Vk = V[int(np.sum(sizes[:k])) * R:int(np.sum(sizes[:k + 1])) * R].view(sizes[k], R)[:, :r]
-            cols.append(info["xt"][k][:, None] + Uk @ Vk.T)
-        return torch.cat(cols, 1)
+        return run.dense(dict(xt=info["xt"], ranks=info["ranks"]))
 
     def barrier():
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
 
+    peak64, peak64_src = fp64_peak(dev)
     info = None
     for _ in range(args.warmup):
         info = step(mus, nus)
@@ -412,7 +420,7 @@ def main():
     launches = (lrfsi.kernel_launches() - L0) / args.steps
     trunc_counts = lrfsi.truncation_counters()
     ms = multi.max_over_ranks(ms, dist, dev)
-    value = world * m / (ms * 1e-3)
+    value = job.m / (ms * 1e-3)
 
     X64 = dense_solution(info)
     mixed = None
@@ -437,7 +445,7 @@ def main():
         torch.cuda.synchronize()
         ksm = lrfsi.kernel_stats()
         lrfsi.timing(False)
-        mixed = {"value": world * m / (ms_m * 1e-3), "ms_per_step": ms_m, "max_relres": info_m["max_relres"],
+        mixed = {"value": job.m / (ms_m * 1e-3), "ms_per_step": ms_m, "max_relres": info_m["max_relres"],
                  "status": info_m["status"], "outer": info_m["outer"],
                  "rel_diff_vs_fp64_solution_update": diff,
                  "per_class_ms": {k: round(v["ms"], 3) for k, v in ksm.items() if v["ms"] > 0},
@@ -465,7 +473,7 @@ def main():
         torch.cuda.synchronize()
         ksg = lrfsi.kernel_stats()
         lrfsi.timing(False)
-        gmres = {"value": world * m / (ms_g * 1e-3), "ms_per_step": ms_g, "max_relres": info_g["max_relres"],
+        gmres = {"value": job.m / (ms_g * 1e-3), "ms_per_step": ms_g, "max_relres": info_g["max_relres"],
                  "status": info_g["status"], "outer": info_g["outer"], "ranks": info_g["ranks"],
                  "rel_diff_vs_chebyshev_solution_update": diff_g,
                  "per_class_ms": {k: round(v["ms"], 3) for k, v in ksg.items() if v["ms"] > 0}}
@@ -507,9 +515,11 @@ def main():
     d = ks[dom]
     if dom in ("gemm_fp64", "gram_fp64", "trunc_small", "trunc_svd", "lu_panel", "lu_trsm", "fe_assembly"):
         achieved = d["flops"] / (d["ms"] * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_NOMINAL_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_NOMINAL_TFLOPS, "traffic": None,
-                "kernel": dom, "peak_source": "nominal FP64 of the recipe table (not in MEASURED_PEAKS.json)"}
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak64, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": None, "kernel": dom, "peak_source": peak64_src,
+                "peak_nominal_fp64": 1.25,
+                "peak_fp64_from_bf16": round(peaks["bf16_tflops"] * 1.25 / 2250.0, 4) if "bf16_tflops" in peaks
+                else None}
     else:
         hbm = peaks.get("hbm_gbs", 6800.0)
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
@@ -519,6 +529,8 @@ def main():
     # algorithmic FP rate per class (TFLOP/s over its own launch time) and launches
     roof["per_class_tflops"] = {k: round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4)
                                 for k, v in ks.items() if v["ms"] > 0 and v["flops"] > 0}
+    roof["per_class_frac_fp64"] = {k: round(v / peak64, 4) for k, v in roof["per_class_tflops"].items()
+                                   if not k.endswith("fp32")}
     roof["per_class_launches"] = {k: int(v["launches"]) for k, v in ks.items() if v["launches"] > 0}
     spmm = ks["spmm_fp64"]
     spmm_gbs = spmm["bytes"] / (spmm["ms"] * 1e-3) / 1e9 if spmm["ms"] > 0 else None
@@ -554,9 +566,11 @@ def main():
             "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "M": mesh.M, "nnz": mesh.nnz, "params": m,
                        "subsets": K, "rank_cap": R, "tol": W.tol, "cheb": [args.c, args.d, 6, 2],
                        "target_relres": args.target, "l2": "working set (block-LU factors) larger than L2",
-                       "parallelism": f"{world} rank(s), one parameter strip each"},
+                       "parallelism": (f"{world} rank(s); the job's {job.K} subsets in contiguous blocks "
+                                       f"balanced by m_k R_k, one gather of the results to rank 0 per step"
+                                       if world > 1 else "1 rank")},
             "clocks": clk.summary(),
-            "e2e": {"value": world * m / (ms_e2e * 1e-3), "unit": "params/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": job.m / (ms_e2e * 1e-3), "unit": "params/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": roof,

@@ -124,9 +124,10 @@ int lrfsi_residual_batch(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
 /* lrfsi_residual_batch_noalloc: the same residual block and column norms as
  * lrfsi_residual_batch, computed without allocating device memory.  (No
  * counterpart in the paper: an interface for callers that cannot let a library
- * allocate -- work recorded into a CUDA graph by stream capture, where a
- * cudaMalloc breaks the capture, and processes whose device memory belongs to
- * their own pool allocator.)
+ * allocate -- processes whose device memory belongs to their own pool
+ * allocator or fixed budget, where memory taken or returned behind that
+ * allocator's back, and the device synchronisation of a cudaMalloc/cudaFree,
+ * are not acceptable.)
  *   R_dev is required (M x m, ldr >= m).  The partial sums of the norms live in
  *   a library-owned device array of 2^21 doubles (16 MiB, held by every GPU
  *   that loads the library until the process exits); ceil(M / 256) * m must not
@@ -134,8 +135,11 @@ int lrfsi_residual_batch(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
  *   overlap on the GPU (e.g. on two streams) race.  Each call overwrites every
  *   partial it reads, so no clearing is needed between calls.
  *   The first call on a device looks up the array's device address (set-up
- *   once per device, with that device current); make that first call before
- *   any stream capture.  Enqueues work on the stream and does not synchronize. */
+ *   once per device, with that device current) and keeps it for the life of
+ *   the process: do not use the library across cudaDeviceReset.  Make that
+ *   first call before any stream capture.  R alone is computed when norm2_dev
+ *   is NULL (the array is then not touched).  Enqueues work on the stream and
+ *   does not synchronize. */
 int lrfsi_residual_batch_noalloc(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
                                  const double* mu_dev, const double* nu_dev, double* R_dev, int ldr,
                                  double* norm2_dev, lrfsi_stream_t stream);
@@ -167,6 +171,47 @@ int lrfsi_spmm_tuning(int precision, int bucket, int* variant, float* ms9);
 int lrfsi_residual(lrfsi_mesh_h mesh, const double* xt_dev, const double* U_dev, int ldu,
                    const double* V_dev, int ldv, int r, const double* mu_dev, const double* nu_dev,
                    int m, double* relres_host, lrfsi_stream_t stream);
+
+/* ---- Algorithm 1's parameter bookkeeping (host only: no device work, no GPU
+ * needed; every array is a caller-owned host array) ---------------------- */
+
+/* lrfsi_order_grid: the little-endian order of the grid mu_values x nu_values
+ * (Sec. 3.3, Def. 1): the parameter with 1-based indices (i1, i2) goes to
+ * position i1 + (i2 - 1) m1, i.e. the mu index runs fastest.  nu_fastest != 0
+ * swaps the axes (position i2 + (i1 - 1) m2; used where the split of two
+ * subsets must run along mu).  Outputs mu_out, nu_out have m1 m2 entries.
+ * Errors: LRFSI_EINVAL for m1 < 1, m2 < 1 or NULL arrays. */
+int lrfsi_order_grid(int m1, int m2, const double* mu_values_host, const double* nu_values_host,
+                     int nu_fastest, double* mu_out_host, double* nu_out_host);
+
+/* lrfsi_order_set: the order of an unstructured parameter set (the paper
+ * orders grids only; this carries Def. 1 over): by nu_f, then by mu_s, equal
+ * pairs in input order.  perm_host[p] = input index of the p-th parameter.
+ * Errors: LRFSI_EINVAL for m < 0, NULL arrays or a NaN parameter. */
+int lrfsi_order_set(int m, const double* mu_host, const double* nu_host, int32_t* perm_host);
+
+/* lrfsi_cluster: K contiguous subsets of m ordered parameters (Eq.
+ * (clustering1): |I_k| = floor(m / K) for k < K, the remainder for k = K),
+ * their first positions (offsets, 0-based) and the 0-based global position of
+ * each subset's upper median (Sec. 3.3: 1-based position floor(|I_k| / 2) + 1
+ * within the subset).  offsets_host and medians_host may be NULL.
+ * Errors: LRFSI_EINVAL unless 1 <= K <= m. */
+int lrfsi_cluster(int m, int K, int32_t* sizes_host, int32_t* offsets_host, int32_t* medians_host);
+
+/* lrfsi_medians: offsets and upper-median positions (as lrfsi_cluster) for
+ * given subset sizes (uneven subsets).  Errors: LRFSI_EINVAL for K < 1 or an
+ * empty subset. */
+int lrfsi_medians(int K, const int32_t* sizes_host, int32_t* offsets_host, int32_t* medians_host);
+
+/* lrfsi_partition: split K subsets into nproc contiguous blocks, balanced by
+ * the per-subset weights (e.g. m_k R_k, the work of a subset step).  The K
+ * subsets are independent (Sec. 2), so a process solves whole subsets.
+ * first_host (nproc + 1 entries): process p owns subsets
+ * [first[p], first[p + 1]); the largest block weight is the smallest possible
+ * for contiguous blocks (binary search on the bound, greedy fill), and no
+ * process is left without a subset while K >= nproc.
+ * Errors: LRFSI_EINVAL for K < 0, nproc < 1, NULL arrays or negative weights. */
+int lrfsi_partition(int K, const int64_t* weights_host, int nproc, int32_t* first_host);
 
 /* lrfsi_newton_median: Newton iteration for K independent problems
  * (Sec. 3.2, Eq. (newton_step_indiv1)), batched: every iteration assembles

@@ -28,6 +28,25 @@ def little_endian_order4(m1, m2, m3, m4):
     return sorted(tuples, key=lambda t: t[0] + (t[1] - 1) * m1 + (t[2] - 1) * m1 * m2 + (t[3] - 1) * m1 * m2 * m3)
 
 
+def order_set(mu, nu):
+    """Order of a scattered parameter set (reading: the little-endian order of
+    Def. 1 carried over from grids): sorted by nu, then by mu, equal pairs in
+    input order.  Returns the permutation (0-based)."""
+    return np.lexsort((np.asarray(mu, float), np.asarray(nu, float)))
+
+
+def ordered_grid(mu_values, nu_values, nu_fastest=False):
+    """The grid mu_values x nu_values as two arrays in Def. 1's order (mu
+    index fastest), or with the nu index fastest."""
+    if nu_fastest:
+        pairs = [(b, a) for a, b in little_endian_order(len(nu_values), len(mu_values))]
+    else:
+        pairs = little_endian_order(len(mu_values), len(nu_values))
+    mu = np.array([mu_values[i - 1] for i, _ in pairs], float)
+    nu = np.array([nu_values[j - 1] for _, j in pairs], float)
+    return mu, nu
+
+
 def affine_midpoints(*coeffs):
     """Midpoints of the ranges of the subset's affine coefficients (the
     mean-based preconditioner's coefficients, reading of Sec. 4.2 applied to

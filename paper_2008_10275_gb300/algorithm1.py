@@ -1,0 +1,153 @@
+"""Algorithm 1 (Sec. 4) driven through the C ABI.
+
+The parameter bookkeeping -- the little-endian order of a grid (Sec. 3.3,
+Def. 1), the contiguous subsets of Eq. (clustering1) and their upper medians
+-- is done by the library's host entry points (lrfsi_order_grid,
+lrfsi_order_set, lrfsi_cluster, lrfsi_medians); this module only holds the
+result (``Layout``) and sequences the device calls of one run (``Runner``):
+
+1. the K upper-median problems by the batched Newton iteration
+   (lrfsi_newton_median, from b_D; Sec. 3.2),
+2. the K subset operators and mean-based preconditioners at the median
+   solutions (lrfsi_subset_create; Sec. 3.4, Sec. 4.2),
+3. the subset Newton step on factors with corrections until every column's
+   relative residual (Sec. 5.1.2) meets the target (lrfsi_subset_step).
+
+Every arithmetic step runs in the library's kernels.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+
+from . import inputs, lrfsi
+
+
+@dataclasses.dataclass
+class Layout:
+    """An ordered parameter set split into subsets."""
+    mu: np.ndarray          # ordered shear moduli (m)
+    nu: np.ndarray          # ordered viscosities (m)
+    sizes: np.ndarray       # m_k (K)
+    offsets: np.ndarray     # first position of each subset (K)
+    medians: np.ndarray     # global position of each subset's upper median (K)
+    caps: np.ndarray        # rank cap R_k of each subset (K)
+
+    @property
+    def m(self):
+        return int(len(self.mu))
+
+    @property
+    def K(self):
+        return int(len(self.sizes))
+
+    def columns(self, k):
+        """Positions of subset k's parameters."""
+        return slice(int(self.offsets[k]), int(self.offsets[k] + self.sizes[k]))
+
+    def part(self, k0, k1):
+        """The layout of subsets k0 .. k1 - 1 alone (positions re-based)."""
+        a = int(self.offsets[k0]) if k0 < self.K else self.m
+        b = int(self.offsets[k1 - 1] + self.sizes[k1 - 1]) if k1 > k0 else a
+        sizes = self.sizes[k0:k1].copy()
+        offs, med = lrfsi.lrfsi_medians(sizes) if len(sizes) else (np.zeros(0, np.int32), np.zeros(0, np.int32))
+        return Layout(self.mu[a:b].copy(), self.nu[a:b].copy(), sizes, offs[:len(sizes)], med[:len(sizes)],
+                      self.caps[k0:k1].copy())
+
+    def weights(self):
+        """Work of each subset step, m_k R_k (the balance of a split over processes)."""
+        return self.sizes.astype(np.int64) * self.caps.astype(np.int64)
+
+
+def grid_layout(mu_values, nu_values, K, rank_cap, nu_fastest=False):
+    """Def. 1 order of the grid, Eq. (clustering1) subsets, upper medians."""
+    mu, nu = lrfsi.lrfsi_order_grid(mu_values, nu_values, nu_fastest)
+    sizes, offs, med = lrfsi.lrfsi_cluster(len(mu), K)
+    return Layout(mu, nu, sizes, offs, med, np.full(K, rank_cap, np.int32))
+
+
+def set_layout(mu, nu, K=None, rank_cap=None, sizes=None, caps=None):
+    """An unstructured set ordered by lrfsi_order_set, then split into K equal
+    subsets (Eq. (clustering1)) or into the given uneven sizes."""
+    perm = lrfsi.lrfsi_order_set(mu, nu)
+    mu, nu = np.asarray(mu, np.float64)[perm], np.asarray(nu, np.float64)[perm]
+    if sizes is None:
+        sizes, offs, med = lrfsi.lrfsi_cluster(len(mu), K)
+    else:
+        sizes = np.asarray(sizes, np.int32)
+        if int(sizes.sum()) != len(mu):
+            raise ValueError("subset sizes must add up to the number of parameters")
+        offs, med = lrfsi.lrfsi_medians(sizes)
+    caps = np.full(len(sizes), rank_cap, np.int32) if caps is None else np.asarray(caps, np.int32)
+    return Layout(mu, nu, np.asarray(sizes, np.int32), offs, med, caps)
+
+
+def workload_layout(W, replicas=1):
+    """The layout of a seeded workload (``inputs.WORKLOADS``); ``replicas``
+    copies of its shape for a job on several GPUs (grid: replicas x more shear
+    moduli and subsets; random: replicas x more draws and subsets)."""
+    mu, nu = inputs.workload_values(W, replicas)
+    if W.seed is None:
+        return grid_layout(mu, nu, W.K * replicas, W.rank_cap, W.nu_fastest)
+    if W.subset_sizes:
+        return set_layout(mu, nu, sizes=list(W.subset_sizes) * replicas, caps=list(W.rank_caps) * replicas)
+    return set_layout(mu, nu, K=W.K * replicas, rank_cap=W.rank_cap)
+
+
+def partition(layout, nproc):
+    """Contiguous blocks of subsets per process, balanced by m_k R_k
+    (lrfsi_partition): process p owns subsets first[p] .. first[p + 1] - 1."""
+    return lrfsi.lrfsi_partition(layout.weights(), nproc)
+
+
+class Runner:
+    """One run of Algorithm 1 over a layout on the current device."""
+
+    def __init__(self, mesh, layout, opt, target=1e-6, max_outer=40, eps_N=1e-6, newton_max_it=30,
+                 device="cuda:0"):
+        import torch
+        self.torch = torch
+        self.mesh, self.layout, self.opt = mesh, layout, opt
+        self.target, self.max_outer, self.eps_N, self.newton_max_it = target, max_outer, eps_N, newton_max_it
+        self.device = device
+        self.bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=device)
+        self.R = int(layout.caps.max()) if layout.K else 0
+        self.U = torch.zeros(max(layout.K * mesh.M * self.R, 1), dtype=torch.float64, device=device)
+        self.V = torch.zeros(max(layout.m * self.R, 1), dtype=torch.float64, device=device)
+
+    def step(self, mu=None, nu=None, opt=None):
+        """Algorithm 1 on the layout's parameters (or on host arrays ``mu``,
+        ``nu`` of the same shape).  Returns a dict: xt (K x M device tensor of
+        median solutions), ranks, relres (m), outer corrections, Newton
+        iterations and the status of the subset step."""
+        L = self.layout
+        mu = L.mu if mu is None else mu
+        nu = L.nu if nu is None else nu
+        med = L.medians
+        X = self.bD.repeat(L.K, 1)
+        it, res, _ = lrfsi.lrfsi_newton_median(self.mesh, X, mu[med], nu[med], self.eps_N, self.newton_max_it)
+        sub = lrfsi.Subsets(self.mesh, X, mu, nu, L.sizes, L.caps)
+        try:
+            ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt or self.opt, self.target, self.max_outer,
+                                                            self.U, self.R, self.V, self.R)
+        finally:
+            sub.close()
+        return dict(xt=X, ranks=ranks, relres=rel, outer=outer, newton_iters=it, status=int(st))
+
+    def factors(self, k, ranks):
+        """(U_k, V_k) views of subset k's factors (M x r_k, m_k x r_k)."""
+        L, M, R = self.layout, self.mesh.M, self.R
+        r = int(ranks[k])
+        Uk = self.U[k * M * R:(k + 1) * M * R].view(M, R)[:, :r]
+        sl = L.columns(k)
+        Vk = self.V[sl.start * R:sl.stop * R].view(int(L.sizes[k]), R)[:, :r]
+        return Uk, Vk
+
+    def dense(self, result):
+        """The dense approximation X^k = x~_k 1^T + U_k V_k^T of every subset (M x m)."""
+        cols = []
+        for k in range(self.layout.K):
+            Uk, Vk = self.factors(k, result["ranks"])
+            cols.append(result["xt"][k][:, None] + Uk @ Vk.T)
+        return self.torch.cat(cols, 1)

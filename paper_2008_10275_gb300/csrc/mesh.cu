@@ -509,6 +509,8 @@ int launch_residual(lrfsi_mesh_s* m, const double* X, int ldx, int ncol, const d
   return LRFSI_OK;
 }
 
+size_t colnorm_work_len(long M, int ncol) { return (size_t)ceil_div(M, kNormRows) * (size_t)(ncol > 0 ? ncol : 0); }
+
 int launch_colnorm2(const double* R, long M, int ncol, int ldr, double* out, double* work, size_t work_len,
                     cudaStream_t s) {
   if (ncol <= 0) return LRFSI_OK;

@@ -69,6 +69,9 @@ int launch_residual(lrfsi_mesh_s* m, const double* X, int ldx, int ncol, const d
 int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s);
 // Column squared norms of an M x ncol row-major block (ldr), accumulated in
 // fixed order: out[j] = sum_i R[i, j]^2.  work: >= ceil(M/rows_per_block) * ncol doubles.
+// Doubles of workspace launch_colnorm2 needs for M rows and ncol columns (one
+// partial sum per column per block of rows).
+size_t colnorm_work_len(long M, int ncol);
 int launch_colnorm2(const double* R, long M, int ncol, int ldr, double* out, double* work,
                     size_t work_len, cudaStream_t s);
 }  // namespace lrfsi

@@ -1,30 +1,34 @@
 // lrfsi_residual_batch_noalloc: the batched nonlinear residual and its column
 // norms without any device allocation.
 //
-// Some callers cannot let a library allocate device memory: code that records
-// its work into a CUDA graph by stream capture (a cudaMalloc issued while a
-// stream is capturing breaks the capture), and applications whose device
-// memory is owned by their own pool allocator (a framework's caching
-// allocator, a serving process with a fixed memory budget) and that must not
-// have memory taken behind that allocator's back.  lrfsi_residual_batch
-// allocates a temporary block for the per-row-block partial sums of the column
-// norms on every call; this variant keeps those partial sums in a file-scope
-// device array instead and requires the caller to pass the residual output.
+// Some callers cannot let a library allocate device memory: applications
+// whose device memory is owned by their own pool allocator (a framework's
+// caching allocator, a serving process with a fixed memory budget) must not
+// have memory taken or returned behind that allocator's back, and a
+// cudaMalloc or cudaFree in the middle of their stream work would also
+// synchronise the device.  lrfsi_residual_batch allocates a temporary block
+// for the per-row-block partial sums of the column norms on every call; this
+// variant keeps those partial sums in a file-scope device array instead and
+// requires the caller to pass the residual output.
 #include <mutex>
 
 #include "mesh.h"
 
 namespace lrfsi {
 
-// Partial sums of the column norms: ceil(M / 256) x m doubles per call.
+// Partial sums of the column norms: colnorm_work_len(M, m) = ceil(M / 256) x m
+// doubles per call.
 constexpr size_t kNoallocScratch = size_t(1) << 21;  // doubles (16 MiB per device, held until exit)
 static __device__ __align__(256) double g_norm_partials[kNoallocScratch];
 
 static std::mutex g_noalloc_mu;
 static double* g_noalloc_ptr[128] = {nullptr};
 
-// Device address of the scratch array for the current device.  Host code may
-// not use the symbol itself: on the host it names a stand-in, not device memory.
+// Device address of the scratch array for the current device, looked up once
+// per device (with that device current) and cached for the life of the
+// process.  Host code may not use the symbol itself: on the host it names a
+// stand-in, not device memory.  The cached address belongs to the device's
+// primary context, so the library must not be used across cudaDeviceReset.
 static int noalloc_scratch(double** out) {
   int dev = 0;
   LRFSI_CUDA(cudaGetDevice(&dev));
@@ -50,7 +54,7 @@ extern "C" int lrfsi_residual_batch_noalloc(lrfsi_mesh_h m, const double* X, int
   if (!m || !X || !mu || !nu || !R || ncol < 0 || ldx < ncol || ldr < ncol)
     return fail(LRFSI_EINVAL, "lrfsi_residual_batch_noalloc: bad argument (R is required, ldx, ldr >= ncol)");
   if (ncol == 0) return LRFSI_OK;
-  const size_t need = (size_t)ceil_div(m->h.M, 256) * (size_t)ncol;
+  const size_t need = colnorm_work_len(m->h.M, ncol);
   if (norm2 && need > kNoallocScratch)
     return fail(LRFSI_EINVAL, "lrfsi_residual_batch_noalloc: ceil(M/256) * ncol exceeds the 2^21-double scratch; "
                               "use lrfsi_residual_batch or fewer columns per call");

@@ -473,6 +473,9 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
                                    double eps, int max_it, int* iters_h, double* res_h, lrfsi_stream_t stream) {
   if (!m || !Xpm || !mu_h || !nu_h || K < 1 || K > kMaxGemmDescs || max_it < 0)
     return fail(LRFSI_EINVAL, "lrfsi_newton_median: bad argument (1 <= K <= 32)");
+  for (int k = 0; k < K; ++k)
+    if (!std::isfinite(mu_h[k]) || !std::isfinite(nu_h[k]))
+      return fail(LRFSI_EINVAL, "lrfsi_newton_median: parameters must be finite");
   cudaStream_t s = (cudaStream_t)stream;
   const long M = m->h.M;
   const long nnz = (long)m->h.colidx.size();
@@ -939,6 +942,9 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
     S->mmax = std::max(S->mmax, S->m[k]);
     S->Rmax = std::max(S->Rmax, S->cap[k]);
   }
+  for (int i = 0; i < S->mtot; ++i)
+    if (!std::isfinite(mu_h[i]) || !std::isfinite(nu_h[i]))
+      return fail(LRFSI_EINVAL, "lrfsi_subset_create: parameters must be finite");
   LRFSI_TRY(subset_alloc_ws(S, s));
   const long nnz = (long)mesh->h.colidx.size();
   const int ldP = S->ldP, ldR = S->ldR;

@@ -103,28 +103,18 @@ def mlp_init(sizes=(2, 128, 128, 64), seed=0):
     return np.concatenate(parts)
 
 
-def rank_strip(rank=0, world=1):
-    """Shear-modulus strip of rank ``rank`` out of ``world`` processes: the box
-    is cut into ``world`` equal strips along mu_s, so that every process solves a
-    workload of the same shape on its own parameters (weak scaling)."""
-    w = (MU_RANGE[1] - MU_RANGE[0]) / world
-    return MU_RANGE[0] + rank * w, MU_RANGE[0] + (rank + 1) * w
-
-
-def workload_parameters(W, rank=0, world=1):
-    """The parameters of workload ``W`` for process ``rank`` of ``world``, in
-    the workload's grid order (little endian: mu fastest; or nu fastest).  The
-    grid's shear moduli are mapped affinely from the full box onto the rank's
-    strip (the identity for one process).  Random workloads draw from the
-    strip with a rank-dependent seed."""
-    lo, hi = rank_strip(rank, world)
+def workload_values(W, replicas=1):
+    """The parameter values of workload ``W``, unordered: for a grid the m1
+    shear moduli and the m2 viscosities (``replicas`` > 1 refines the
+    viscosities to replicas * m2 values over the same range: a job of that
+    many copies of the workload's shape, for runs on several GPUs; in the
+    little-endian order every subset then still holds whole rows of m1 shear
+    moduli); for a random workload the n seeded draws from the box."""
     if W.seed is not None:
-        rng = np.random.default_rng(W.seed + 7919 * rank)
-        return rng.uniform(lo, hi, W.n_random), rng.uniform(*NU_RANGE, W.n_random)
-    a = (np.array(W.mu_values) - MU_RANGE[0]) / (MU_RANGE[1] - MU_RANGE[0])
-    mu_g, nu_g = lo + a * (hi - lo), np.array(W.nu_values)
-    if world == 1:
-        mu_g = np.array(W.mu_values)
-    if W.nu_fastest:
-        return np.repeat(mu_g, len(nu_g)), np.tile(nu_g, len(mu_g))
-    return np.tile(mu_g, len(nu_g)), np.repeat(nu_g, len(mu_g))
+        rng = np.random.default_rng(W.seed)
+        n = W.n_random * replicas
+        return rng.uniform(*MU_RANGE, n), rng.uniform(*NU_RANGE, n)
+    nu = np.array(W.nu_values)
+    if replicas > 1:
+        nu = np.linspace(nu[0], nu[-1], replicas * len(nu))
+    return np.array(W.mu_values), nu

@@ -103,6 +103,11 @@ def load():
         "lrfsi_learned_factors": [vp, vp, i, vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp, vp, i, vp, i, vp],
         "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
         "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
+        "lrfsi_order_grid": [i, i, vp, vp, i, vp, vp],
+        "lrfsi_order_set": [i, vp, vp, vp],
+        "lrfsi_cluster": [i, i, vp, vp, vp],
+        "lrfsi_medians": [i, vp, vp, vp],
+        "lrfsi_partition": [i, vp, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -151,6 +156,48 @@ def _stream(stream):
         import torch
         return C.c_void_p(torch.cuda.current_stream().cuda_stream)
     return C.c_void_p(int(stream))
+
+
+def lrfsi_order_grid(mu_values, nu_values, nu_fastest=False):
+    """Little-endian order of the grid (Def. 1); returns (mu, nu) of length m1 m2."""
+    a = np.ascontiguousarray(mu_values, np.float64)
+    b = np.ascontiguousarray(nu_values, np.float64)
+    mu = np.zeros(len(a) * len(b))
+    nu = np.zeros(len(a) * len(b))
+    _check(load().lrfsi_order_grid(len(a), len(b), _ptr(a), _ptr(b), int(bool(nu_fastest)), _ptr(mu), _ptr(nu)))
+    return mu, nu
+
+
+def lrfsi_order_set(mu, nu):
+    """Order of a scattered parameter set (nu_f, then mu_s); returns the permutation."""
+    a = np.ascontiguousarray(mu, np.float64)
+    b = np.ascontiguousarray(nu, np.float64)
+    perm = np.zeros(len(a), np.int32)
+    _check(load().lrfsi_order_set(len(a), _ptr(a), _ptr(b), _ptr(perm)))
+    return perm
+
+
+def lrfsi_cluster(m, K):
+    """Eq. (clustering1) subsets and upper medians: (sizes, offsets, medians)."""
+    sizes = np.zeros(max(K, 1), np.int32); offs = np.zeros(max(K, 1), np.int32); med = np.zeros(max(K, 1), np.int32)
+    _check(load().lrfsi_cluster(int(m), int(K), _ptr(sizes), _ptr(offs), _ptr(med)))
+    return sizes, offs, med
+
+
+def lrfsi_medians(sizes):
+    """Offsets and upper medians of given subset sizes: (offsets, medians)."""
+    sz = np.ascontiguousarray(sizes, np.int32)
+    offs = np.zeros(max(len(sz), 1), np.int32); med = np.zeros(max(len(sz), 1), np.int32)
+    _check(load().lrfsi_medians(len(sz), _ptr(sz), _ptr(offs), _ptr(med)))
+    return offs, med
+
+
+def lrfsi_partition(weights, nproc):
+    """Contiguous balanced split of the subsets over nproc processes: first[nproc + 1]."""
+    w = np.ascontiguousarray(weights, np.int64)
+    first = np.zeros(nproc + 1, np.int32)
+    _check(load().lrfsi_partition(len(w), _ptr(w) if len(w) else None, int(nproc), _ptr(first)))
+    return first
 
 
 def kernel_launches():

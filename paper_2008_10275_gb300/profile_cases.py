@@ -26,10 +26,11 @@ def _setup():
         raise SystemExit("profile cases need a CUDA GPU")
     build.build()
     lrfsi.load()
+    from . import algorithm1
     W = inputs.WORKLOADS["medium"]
     mesh = lrfsi.Mesh(W.nx, W.ny)
-    mus, nus = inputs.workload_parameters(W)
-    return torch, lrfsi, W, mesh, mus, nus
+    L = algorithm1.workload_layout(W)
+    return torch, lrfsi, W, mesh, L.mu, L.nu
 
 
 def _timed(torch, fn, reps=1):
@@ -115,8 +116,9 @@ def case_large():
     dev = "cuda:0"
     W = inputs.WORKLOADS["large"]
     mesh = lrfsi.Mesh(W.nx, W.ny)
-    mus, nus = inputs.workload_parameters(W)
-    mus, nus = mus[:100], nus[:100]
+    from . import algorithm1
+    L = algorithm1.workload_layout(W)
+    mus, nus = L.mu[:100], L.nu[:100]
     R, m = W.rank_cap, 100
     out = {"mesh": f"{W.nx}x{W.ny}", "M": mesh.M, "nnz": mesh.nnz, "slabs": mesh.nslab, "slab_max": mesh.nmax}
     ev = lambda: torch.cuda.Event(enable_timing=True)

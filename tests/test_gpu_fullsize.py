@@ -14,7 +14,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 from oracle import algorithm1, fsi, newton  # noqa: E402
-from paper_2008_10275_gb300 import build, inputs, lrfsi  # noqa: E402
+from paper_2008_10275_gb300 import algorithm1 as a1, build, inputs, lrfsi  # noqa: E402
 from tests.gpu_common import perm_lib_to_oracle, rel_max  # noqa: E402
 
 DEV = "cuda:0"
@@ -34,10 +34,10 @@ def fullsize():
     lm = lrfsi.Mesh(W.nx, W.ny)
     om = fsi.Mesh(fsi.Problem(W.nx, W.ny))
     perm = perm_lib_to_oracle(lm, om)
-    mus, nus = inputs.workload_parameters(W)
-    K, R, m = W.K, W.rank_cap, len(mus)
-    sizes = [m // K] * K
-    medians = [q * (m // K) + (m // K) // 2 for q in range(K)]
+    L = a1.workload_layout(W)
+    mus, nus = L.mu, L.nu
+    K, R, m = L.K, W.rank_cap, L.m
+    sizes, medians = L.sizes.tolist(), L.medians.tolist()
     bD = torch.tensor(lm.dirichlet(), device=DEV)
     X = bD.repeat(K, 1)
     it, res, st = lrfsi.lrfsi_newton_median(lm, X, mus[medians], nus[medians], 1e-8, 30)

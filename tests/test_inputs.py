@@ -1,5 +1,5 @@
 """The seeded workload descriptions and draws (paper_2008_10275_gb300/inputs.py):
-sizes, ranges, determinism and the little-endian grid order."""
+sizes, ranges and determinism (the module holds no ordering rule)."""
 import numpy as np
 
 from paper_2008_10275_gb300 import inputs
@@ -8,14 +8,16 @@ from paper_2008_10275_gb300 import inputs
 def test_box_and_grid_workloads():
     for name in ("small", "medium", "large"):
         W = inputs.WORKLOADS[name]
-        mu, nu = inputs.workload_parameters(W)
-        assert len(mu) == len(W.mu_values) * len(W.nu_values)
+        mu, nu = inputs.workload_values(W)
+        assert (len(mu), len(nu)) == (len(W.mu_values), len(W.nu_values))
         assert mu.min() == inputs.MU_RANGE[0] and mu.max() == inputs.MU_RANGE[1]
         assert nu.min() == inputs.NU_RANGE[0] and nu.max() == inputs.NU_RANGE[1]
-    W = inputs.WORKLOADS["small"]  # nu fastest: the cut into 2 subsets runs along mu_s
-    mu, nu = inputs.workload_parameters(W)
-    assert nu[1] != nu[0] and mu[1] == mu[0]
-    assert mu[: len(mu) // 2].max() < mu[len(mu) // 2:].min()
+        assert np.all(np.diff(mu) > 0) and np.all(np.diff(nu) > 0)
+    # replicas refine the viscosities over the same range
+    W = inputs.WORKLOADS["medium"]
+    mu4, nu4 = inputs.workload_values(W, replicas=4)
+    assert len(nu4) == 4 * len(W.nu_values) and np.array_equal(mu4, np.array(W.mu_values))
+    assert nu4[0] == inputs.NU_RANGE[0] and nu4[-1] == inputs.NU_RANGE[1]
 
 
 def test_batched_workload_sizes_and_caps():
@@ -30,8 +32,8 @@ def test_batched_workload_sizes_and_caps():
 def test_random_workloads_are_seeded_and_in_the_box():
     for name in ("batched", "learned"):
         W = inputs.WORKLOADS[name]
-        a = inputs.workload_parameters(W)
-        b = inputs.workload_parameters(W)
+        a = inputs.workload_values(W)
+        b = inputs.workload_values(W)
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
         assert len(a[0]) == W.n_random
         assert np.all((a[0] >= inputs.MU_RANGE[0]) & (a[0] <= inputs.MU_RANGE[1]))

@@ -1,13 +1,13 @@
 """The allocation-free residual entry point (lrfsi_residual_batch_noalloc).
 
-Callers that record work into a CUDA graph by stream capture, or whose device
-memory belongs to their own pool allocator, cannot let the library allocate.
-This file checks, through the C ABI, that the allocation-free variant returns
-the same residual block and column norms as lrfsi_residual_batch on two calls
-in a row with different inputs (the shared scratch keeps the previous call's
-partial sums, which must not leak into the next result).  It is named to be
-collected last so that a run stopping at the first failure has run every
-other test already.
+Callers whose device memory belongs to their own pool allocator or a fixed
+budget cannot let the library allocate.  This file checks, through the C ABI,
+that the allocation-free variant returns the same residual block and column
+norms as lrfsi_residual_batch on two calls in a row with different inputs
+(the shared scratch keeps the previous call's partial sums, which must not
+leak into the next result), with padded leading dimensions, and without the
+norms.  It is named to be collected last so that a run stopping at the first
+failure has run every other test already.
 """
 import numpy as np
 import pytest
@@ -28,27 +28,36 @@ def _lib():
     lrfsi.load()
 
 
-def test_noalloc_residual_matches_allocating_entry_point_twice():
+@pytest.mark.parametrize("pad_x,pad_r", [(0, 0), (3, 5)])
+def test_noalloc_residual_matches_allocating_entry_point_twice(pad_x, pad_r):
     dev = "cuda:0"
     lm = lrfsi.Mesh(20, 4)
     om = fsi.Mesh(fsi.Problem(20, 4))
     perm = perm_lib_to_oracle(lm, om)
     for call, (m, seed) in enumerate(((7, 11), (12, 23))):
         rng = np.random.default_rng(seed)
-        X = np.stack([om.bD + inputs.random_state(om.M, seed + j, nq2=om.NQ2) for j in range(m)], 1)[perm]
+        ldx, ldr = m + pad_x, m + pad_r
+        X = np.full((lm.M, ldx), 1e300)   # padding columns must never be read into a result
+        X[:, :m] = np.stack([om.bD + inputs.random_state(om.M, seed + j, nq2=om.NQ2) for j in range(m)], 1)[perm]
         Xd = torch.tensor(np.ascontiguousarray(X), device=dev)
         mu = torch.tensor(rng.uniform(*inputs.MU_RANGE, m), device=dev)
         nu = torch.tensor(rng.uniform(*inputs.NU_RANGE, m), device=dev)
-        R_ref = torch.zeros(lm.M * m, dtype=torch.float64, device=dev)
+        R_ref = torch.zeros(lm.M * ldr, dtype=torch.float64, device=dev)
         n_ref = torch.zeros(m, dtype=torch.float64, device=dev)
-        lrfsi.lrfsi_residual_batch(lm, Xd, m, m, mu, nu, R_ref, m, n_ref)
-        R = torch.full((lm.M * m,), float("nan"), dtype=torch.float64, device=dev)
+        lrfsi.lrfsi_residual_batch(lm, Xd, ldx, m, mu, nu, R_ref, ldr, n_ref)
+        R = torch.full((lm.M * ldr,), float("nan"), dtype=torch.float64, device=dev)
         n2 = torch.full((m,), float("nan"), dtype=torch.float64, device=dev)
-        lrfsi.lrfsi_residual_batch_noalloc(lm, Xd, m, m, mu, nu, R, m, n2)
+        lrfsi.lrfsi_residual_batch_noalloc(lm, Xd, ldx, m, mu, nu, R, ldr, n2)
         torch.cuda.synchronize()
-        scale = float(R_ref.abs().max())
-        assert float((R - R_ref).abs().max()) <= 1e-12 * scale, call
+        Rv, Rr = R.view(lm.M, ldr)[:, :m], R_ref.view(lm.M, ldr)[:, :m]
+        scale = float(Rr.abs().max())
+        assert float((Rv - Rr).abs().max()) <= 1e-12 * scale, call
         assert torch.allclose(n2, n_ref, rtol=1e-12, atol=0.0), call
+        # the residual alone (no norms): the scratch is not touched
+        R2 = torch.full((lm.M * ldr,), float("nan"), dtype=torch.float64, device=dev)
+        lrfsi.lrfsi_residual_batch_noalloc(lm, Xd, ldx, m, mu, nu, R2, ldr, None)
+        torch.cuda.synchronize()
+        assert float((R2.view(lm.M, ldr)[:, :m] - Rr).abs().max()) <= 1e-12 * scale, call
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch():
