@@ -348,6 +348,27 @@ int lrfsi_subset_step_init(lrfsi_subset_h sub, const lrfsi_cheb_options* opt, do
                            double* U_dev, int ldu, double* V_dev, int ldv, int* rank_host, double* relres_host,
                            int* outer_host, int* fallback_host, lrfsi_stream_t stream);
 
+/* lrfsi_graph_mode: how ChebyshevT (lrfsi_chebyshevT and the ChebyshevT
+ * solves inside lrfsi_subset_step / _init) issues its work (Algorithm 1 step
+ * 3; no counterpart in the paper: a batching choice):
+ *   0: launches sized from ranks read back to the host after every truncation;
+ *   1: a fixed launch sequence for all subsets of the handle -- widths fixed at
+ *      the rank caps (columns beyond a rank are zero), ranks and the eta test
+ *      kept on the device as flags that gate every later launch of a subset,
+ *      the optional third Cholesky-QR pass gated by the flag its first pass
+ *      writes; no host read inside a solve;
+ *   2 (default): the sequence of mode 1 captured once per handle and option set
+ *      into a CUDA graph (on a stream the handle owns, after one direct run)
+ *      and replayed with one graph launch per solve.  If the capture fails the
+ *      process falls back to mode 1 (counted by lrfsi_graph_counters).
+ * Modes 1 and 2 equal mode 0 up to rounding (zero columns change sums only
+ * by their order).  While kernel timing (lrfsi_timing) is on, mode 2 launches
+ * the sequence directly.  mode = -1 only queries.  *previous (may be NULL)
+ * receives the mode before the call.  Process-wide; set it between calls. */
+int lrfsi_graph_mode(int mode, int* previous);
+/* Graph replays, captures and capture failures since the last reset. */
+int lrfsi_graph_counters(int64_t* out3, int reset);
+
 /* lrfsi_precond_apply: Y_k = P_k^{-1} X_k with the factored mean-based
  * preconditioner of subset k (Sec. 4.2), for r_k columns.
  *   X_dev : K stacked M x ldx blocks (not modified);  Y_dev : K stacked M x ldy

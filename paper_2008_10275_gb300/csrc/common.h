@@ -55,6 +55,19 @@ inline int check_launch(const char* name) {
   return LRFSI_OK;
 }
 
+// ---- device-side run conditions ---------------------------------------------
+// A batched descriptor's work runs only if each non-null flag is nonzero: the
+// per-subset "still iterating" flag of a solve whose launch sequence is fixed
+// (and captured in a CUDA graph), and optional passes of the truncation that
+// the device decides on.  A gated-off descriptor leaves its outputs untouched.
+struct Gate {
+  const int* a = nullptr;
+  const int* b = nullptr;
+};
+#ifdef __CUDACC__
+__host__ __device__ inline bool gate_open(const Gate& g) { return (!g.a || *g.a) && (!g.b || *g.b); }
+#endif
+
 // ---- device buffers --------------------------------------------------------
 template <class T>
 struct DevBuf {

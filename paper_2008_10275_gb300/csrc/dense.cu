@@ -38,9 +38,10 @@ constexpr int GBM = 64, GBN = 64, GBK = 16;
 template <class T, int BM, int BN>
 __global__ void __launch_bounds__(256) k_gemm(GemmBatch<T> gb, int ks, T* __restrict__ part, long part_stride) {
   const int z = blockIdx.z / ks, chunk = blockIdx.z % ks;
-  const GemmDesc<T> g = gb.d[z];
+  GemmDesc<T> g = gb.d[z];
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  if (m0 >= g.m || n0 >= g.n) return;
+  if (m0 >= g.m || n0 >= g.n || !gate_open(g.gate)) return;
+  if (g.sel && *g.sel) g.A = g.A_alt;
   constexpr int RM = BM / 16, RN = BN / 16;
   __shared__ T As[GBK][BM + 1];
   __shared__ T Bs[GBK][BN + 1];
@@ -105,7 +106,7 @@ template <class T>
 __global__ void k_gemm_reduce(GemmBatch<T> gb, int ks, const T* __restrict__ part, long part_stride) {
   const GemmDesc<T> g = gb.d[blockIdx.y];
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long)g.m * g.n) return;
+  if (e >= (long)g.m * g.n || !gate_open(g.gate)) return;
   const int i = (int)(e / g.n), j = (int)(e % g.n);
   T v = 0;
   for (int c = 0; c < ks; ++c) v += part[((long)blockIdx.y * ks + c) * part_stride + e];
@@ -114,9 +115,16 @@ __global__ void k_gemm_reduce(GemmBatch<T> gb, int ks, const T* __restrict__ par
   *cp = v;
 }
 
-// process-wide split-K workspace (grown on demand, never shrunk)
+// process-wide split-K workspace (grown on demand, never shrunk) and the
+// calling thread's bound workspace, if any
 static void* g_gemm_ws = nullptr;
 static size_t g_gemm_ws_bytes = 0;
+static thread_local void* t_ws_bound = nullptr;
+static thread_local size_t t_ws_bound_bytes = 0;
+static thread_local size_t t_ws_peak = 0;
+void gemm_ws_bind(void* p, size_t bytes) { t_ws_bound = p; t_ws_bound_bytes = p ? bytes : 0; }
+size_t gemm_ws_peak() { return t_ws_peak; }
+void gemm_ws_peak_reset() { t_ws_peak = 0; }
 
 template <class T>
 int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
@@ -162,22 +170,27 @@ int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
       if (ks < 1) ks = 1;
     }
     const long pstride = (long)mm * nn;
+    void* ws = t_ws_bound ? t_ws_bound : g_gemm_ws;
     if (ks > 1) {
       const size_t need = sizeof(T) * (size_t)cnt * ks * pstride;
-      if (need > g_gemm_ws_bytes) {
+      if (need > t_ws_peak) t_ws_peak = need;
+      if (t_ws_bound) {
+        if (need > t_ws_bound_bytes) return fail(LRFSI_EINVAL, "gemm_grouped: bound split-K workspace too small");
+      } else if (need > g_gemm_ws_bytes) {
         if (g_gemm_ws) cudaFree(g_gemm_ws);
         g_gemm_ws = nullptr;
         g_gemm_ws_bytes = 0;
         LRFSI_CUDA(cudaMalloc(&g_gemm_ws, need));
         g_gemm_ws_bytes = need;
+        ws = g_gemm_ws;
       }
     }
     dim3 grid(ceil_div(nn, 32), ceil_div(mm, 32), cnt * ks);
-    k_gemm<T, 32, 32><<<grid, 256, 0, s>>>(gb, ks, (T*)g_gemm_ws, pstride);
+    k_gemm<T, 32, 32><<<grid, 256, 0, s>>>(gb, ks, (T*)ws, pstride);
     LRFSI_TRY(check_launch("k_gemm"));
     if (ks > 1) {
       dim3 g2(ceil_div(pstride, 256), cnt);
-      k_gemm_reduce<T><<<g2, 256, 0, s>>>(gb, ks, (const T*)g_gemm_ws, pstride);
+      k_gemm_reduce<T><<<g2, 256, 0, s>>>(gb, ks, (const T*)ws, pstride);
       LRFSI_TRY(check_launch("k_gemm_reduce"));
     }
     tl.end(s);
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(256) k_gram_partial(GramBatch gb, long M, int 
   const int i0 = ti * GBM, j0 = tj * GBN;
   const int split = blockIdx.y;
   double* out = work + ((size_t)blockIdx.z * nsplit + split) * (size_t)pmax * qmax;
-  if (i0 >= g.p || j0 >= g.q) return;
+  if (i0 >= g.p || j0 >= g.q || !gate_open(g.gate)) return;
   const long chunk = (M + nsplit - 1) / nsplit;
   const long r0 = split * chunk, r1 = r0 + chunk < M ? r0 + chunk : M;
   __shared__ double As[GBK][GBM + 1];
@@ -260,7 +273,7 @@ __global__ void k_gram_reduce(GramBatch gb, int nsplit, int pmax, int qmax, cons
                               int upper) {
   const GramDesc g = gb.d[blockIdx.y];
   const long idx = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long)g.p * g.q) return;
+  if (idx >= (long)g.p * g.q || !gate_open(g.gate)) return;
   int i = (int)(idx / g.q), j = (int)(idx % g.q);
   const int oi = i, oj = j;
   // symmetric products: tiles below the diagonal were not computed, read the mirror
@@ -404,6 +417,7 @@ size_t trunc_small_work(int p, int m) {
 __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs) {
   const TruncDesc d = descs[blockIdx.x];
   const int p = d.p, m = d.m;
+  if (!gate_open(d.gate)) return;
   if (p <= 0) {
     if (threadIdx.x == 0) { d.info[0] = 0; d.info[1] = 0; d.info[2] = 0; d.info[4] = 0; *d.frob2 = 0.0; }
     return;
@@ -517,9 +531,10 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
 // (the core update Y <- R Y is a GEMM after this kernel).  info[4] = 1 when the
 // basis was far from orthonormal (max |Gq_ij - delta_ij| > 0.1), so that one
 // more pass is needed before the SVD.
-__global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs) {
+__global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, int write_third) {
   const TruncDesc d = descs[blockIdx.x];
   const int p = d.p, m = d.m;
+  if (!gate_open(d.gate)) return;
   __shared__ int s_k, s_bad;
   __shared__ double s_dev;
   if (threadIdx.x == 0) { s_k = p > 0 ? d.info[0] : 0; s_bad = 0; s_dev = 0.0; }
@@ -542,16 +557,20 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs) {
   if (threadIdx.x == 0) {
     for (int i = 0; i < k; ++i)
       if (!flags[i]) s_bad = 1;
-    d.info[4] = (s_dev > 0.1) ? 1 : 0;
-    if (s_bad) d.info[2] = LRFSI_EBREAKDOWN;
+    if (write_third) d.info[4] = (s_dev > 0.1) ? 1 : 0;
+    if (s_bad) {
+      d.info[2] = LRFSI_EBREAKDOWN;
+      if (d.broke) *d.broke = 1;
+    }
   }
   __syncthreads();
   if (s_bad) return;
   upper_inverse(R, k, W.Rki, k, k);
   __syncthreads();
-  for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
-    const int a = (int)(e / k), b = (int)(e % k);
-    d.T2[(size_t)a * p + b] = W.Rki[e];
+  // T2 = R^{-1} in the leading k x k block of a zero p x p block (ld p)
+  for (long e = threadIdx.x; e < (long)p * p; e += blockDim.x) {
+    const int a = (int)(e / p), b = (int)(e % p);
+    d.T2[e] = (a < k && b < k) ? W.Rki[(size_t)a * k + b] : 0.0;
   }
   __syncthreads();
   // R (upper triangle of the k x k factor) zero-padded to p x p into Rki: the
@@ -653,12 +672,33 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   __shared__ double s_tot, s_cm;
   __shared__ int s_rot, s_r;
   // uniform across the cluster: every CTA reads the same descriptor and info
+  if (!gate_open(d.gate)) return;
   const int k = p > 0 ? d.info[0] : 0;
+  TruncWork W(d.work, p, m);
+  // outputs beyond the chosen rank are zero (up to the rank cap), so that a
+  // launch sequence of fixed widths can read rank_cap columns
+  const int wcols = d.rank_cap < p ? d.rank_cap : p;
+  auto zero_tail = [&](int r) {
+    const long stride = (long)C * kSvdThreads;
+    for (long e = (long)crank * kSvdThreads + tid; e < (long)p * wcols; e += stride) {
+      const int a = (int)(e / wcols), j = (int)(e % wcols);
+      if (a >= k || j >= r) W.Rk[(size_t)a * p + j] = 0.0;
+    }
+    const int vc = d.rank_cap - r;
+    for (long e = (long)crank * kSvdThreads + tid; e < (long)m * (vc > 0 ? vc : 0); e += stride) {
+      const int c = (int)(e / vc), j = r + (int)(e % vc);
+      d.Vout[(size_t)c * d.ldvo + j] = 0.0;
+    }
+  };
   if (k <= 0 || m <= 0 || d.info[2] != 0) {
-    if (crank == 0 && tid == 0) { d.info[1] = 0; d.info[3] = 0; *d.frob2 = 0.0; }
+    if (crank == 0 && tid == 0) {
+      d.info[1] = 0; d.info[3] = 0; *d.frob2 = 0.0;
+      if (d.rank_out) *d.rank_out = 0;
+      if (d.count) *d.count += 1;
+    }
+    if (m > 0) zero_tail(0);
     return;
   }
-  TruncWork W(d.work, p, m);
   // A = C^T whenever k <= m: the rows of the core are graded by the pivoted
   // Cholesky, and Jacobi converges in fewer sweeps on graded columns
   const bool cols_of_C = m < k;
@@ -675,7 +715,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   double* home = sm;                    // 2b columns: global columns 2 crank b + h
   double* work = sm + (size_t)2 * b * LV;  // the two blocks of a tournament round
   const int j0 = 2 * crank * b;
-  const double* core = d.core;
+  const double* core = (d.sel && *d.sel) ? d.core_alt : d.core;
   for (long e = tid; e < (long)2 * b * LV; e += kSvdThreads) {
     const int h = (int)(e / LV), i = (int)(e % LV), j = j0 + h;
     double v = 0;
@@ -814,6 +854,8 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
       d.info[3] = sweeps;
       if (sweeps < 0) d.info[2] = LRFSI_ENOCONV;
       *d.frob2 = tot;
+      if (d.rank_out) *d.rank_out = r;
+      if (d.count) *d.count += 1;
     }
   }
   __syncthreads();
@@ -833,10 +875,11 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     const int col = order[j];
     d.Vout[(size_t)c * d.ldvo + j] = cols_of_C ? W.Vm[(size_t)col * n + c] * sig[j] : W.A[(size_t)col * L + c];
   }
+  zero_tail(r);
 }
 
-int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
-  LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
+int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload) {
+  if (upload) LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
   account(KC_TRUNC, 0, 0);
   TimedLaunch tl(KC_TRUNC, s);
   k_trunc_pass1<<<n, kSmallThreads, 0, s>>>(d_dev);
@@ -845,10 +888,10 @@ int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
   return LRFSI_OK;
 }
 
-int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev) {
+int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third) {
   account(KC_TRUNC, 0, 0);
   TimedLaunch tl(KC_TRUNC, s);
-  k_trunc_qr<<<n, kSmallThreads, 0, s>>>(d_dev);
+  k_trunc_qr<<<n, kSmallThreads, 0, s>>>(d_dev, write_third);
   LRFSI_TRY(check_launch("k_trunc_qr"));
   tl.end(s);
   return LRFSI_OK;
@@ -885,9 +928,9 @@ static int svd_cluster_size(int nprob, size_t smem) {
   return 2;
 }
 
-int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev) {
+int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload) {
   if (n <= 0) return LRFSI_OK;
-  LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
+  if (upload) LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
   int nmax = 1, Lmax = 1;
   for (int i = 0; i < n; ++i) {
     const int lo = d[i].p < d[i].m ? d[i].p : d[i].m, hi = d[i].p < d[i].m ? d[i].m : d[i].p;

@@ -7,6 +7,8 @@ namespace lrfsi {
 
 // C(i,j) = alpha * sum_l A(i,l) B(l,j) + beta * C(i,j), element (i,j) of X at
 // X.p[i * X.rs + j * X.cs].  beta == 0 never reads C.
+// Optional: gate (run condition, see Gate); sel != nullptr && *sel != 0 reads
+// A_alt instead of A (same strides).
 template <class T>
 struct GemmDesc {
   int m, n, k;
@@ -14,10 +16,22 @@ struct GemmDesc {
   const T* B; long b_rs, b_cs;
   T* C; long c_rs, c_cs;
   T alpha, beta;
+  Gate gate;
+  const T* A_alt = nullptr;
+  const int* sel = nullptr;
 };
 constexpr int kMaxGemmDescs = 32;
 template <class T>
 int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s);
+// Split-K workspace of the grouped GEMM on the calling thread: by default a
+// process-wide buffer grown on demand; between gemm_ws_bind(p, bytes) and
+// gemm_ws_bind(nullptr, 0) the calls use p instead and fail (LRFSI_EINVAL)
+// rather than grow it (a launch sequence captured into a CUDA graph must not
+// see its workspace move).  gemm_ws_peak() is the largest need since the last
+// gemm_ws_peak_reset().
+void gemm_ws_bind(void* p, size_t bytes);
+size_t gemm_ws_peak();
+void gemm_ws_peak_reset();
 
 // Batched tall Gram G_b = A_b^T B_b (p_b x q_b, row-major ldg) with
 // A_b: M x p_b (row-major, lda), B_b: M x q_b (ldb); split over rows and
@@ -26,6 +40,7 @@ struct GramDesc {
   const double* A; int lda, p;
   const double* B; int ldb, q;
   double* G; int ldg;
+  Gate gate;
 };
 int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t work_len, cudaStream_t s);
 size_t gram_work_len(int nbatch, long M, int pmax, int qmax);
@@ -52,11 +67,22 @@ struct TruncDesc {
   double tol;        // relative Frobenius truncation tolerance
   int rank_cap;
   double drop;       // pass-1 pivot threshold on the unit-diagonal Gram
+  // optional (device-driven launch sequences):
+  Gate gate;                        // run condition of every kernel of this problem
+  const double* core_alt = nullptr;  // SVD core when sel != nullptr && *sel != 0
+  const int* sel = nullptr;
+  int* rank_out = nullptr;          // SVD: the chosen rank is also written here
+  int* count = nullptr;             // SVD: incremented once per truncation
+  int* broke = nullptr;             // Cholesky-QR: set to 1 on a breakdown (sticky)
 };
 size_t trunc_small_work(int p, int m);
-int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev);
-int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev);
-int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev);
+// upload = false: d_dev already holds the n descriptors (d is still read on
+// the host for launch shapes)
+int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload = true);
+// write_third = 0: a later pass that must not overwrite the "another pass"
+// flag (info[4]) of the first QR pass
+int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third = 1);
+int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload = true);
 
 // Offsets of the per-problem scratch (doubles): Dsc (p) | Rk (p*p) | Rki (p*p) |
 // Y (p*m) | C (p*m) | A (n'*n') | Vm (n'*n'), n' = max(p, m).  Rk holds the

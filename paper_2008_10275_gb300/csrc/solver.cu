@@ -82,6 +82,7 @@ struct CopyDesc {
   int mode;            // 0: copy, 1: fill alpha * rowscale, 2: alpha * identity
   const double* rowscale;
   double alpha;
+  Gate gate;
 };
 struct CopyBatch {
   CopyDesc d[kMaxGemmDescs];
@@ -90,7 +91,7 @@ struct CopyBatch {
 __global__ void k_blockcopy(CopyBatch cb) {
   const CopyDesc& d = cb.d[blockIdx.y];
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.rows * d.ncols) return;
+  if (e >= d.rows * d.ncols || !gate_open(d.gate)) return;
   const long i = e / d.ncols;
   const int j = (int)(e % d.ncols);
   double v;
@@ -128,6 +129,7 @@ struct ConvDesc {
   int ncols;
   const double* rowscale;
   double alpha;
+  Gate gate;
 };
 struct ConvBatch {
   ConvDesc d[kMaxGemmDescs];
@@ -136,7 +138,7 @@ template <class Tin, class Tout>
 __global__ void k_convert(ConvBatch cb) {
   const ConvDesc& d = cb.d[blockIdx.y];
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= d.rows * d.ncols) return;
+  if (e >= d.rows * d.ncols || !gate_open(d.gate)) return;
   const long i = e / d.ncols;
   const int j = (int)(e % d.ncols);
   double v = (double)((const Tin*)d.src)[i * d.lds + j] * d.alpha;
@@ -612,8 +614,33 @@ struct lrfsi_subset_s {
   // dense columns for the nonlinear residual (M x mtot)
   DevBuf<double> Xd;
   ResidualCtx rc;
+  // ChebyshevT as a fixed launch sequence (cheb_fixed): per-subset device
+  // state, the truncation descriptors of the sequence (host copies and device
+  // array), subset offsets/sizes, the bound split-K workspace and the graph
+  DevBuf<int> cgi, offm;
+  DevBuf<double> cgd;
+  DevBuf<TruncDesc> cgt;
+  std::vector<TruncDesc> cgt_host;
+  DevBuf<unsigned char> cgws;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t cg_graph = nullptr;
+  cudaGraphExec_t cg_exec = nullptr;
+  uint64_t cg_nodes = 0;
+  std::vector<double> cg_key;
   double* tall(DevBuf<double>& b, int k, int ld) { return b.p + (size_t)k * M * ld; }
   double* vside(DevBuf<double>& b, int k, int ld) { return b.p + (size_t)off[k] * ld; }
+  void drop_graph() {
+    if (cg_exec) cudaGraphExecDestroy(cg_exec);
+    if (cg_graph) cudaGraphDestroy(cg_graph);
+    cg_exec = nullptr;
+    cg_graph = nullptr;
+    cg_nodes = 0;
+    cg_key.clear();
+  }
+  ~lrfsi_subset_s() {
+    drop_graph();
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+  }
 };
 
 namespace lrfsi {
@@ -1277,6 +1304,460 @@ static int cheb_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<
   return LRFSI_OK;
 }
 
+// ---------------------------------------------------------------------------
+// ChebyshevT as a fixed launch sequence
+// ---------------------------------------------------------------------------
+// cheb_run above sizes every launch from ranks read back to the host (two
+// round trips per truncation).  The fixed sequence below takes no host
+// decision, so that one whole solve (cycles x iters steps of Algorithm 1 step
+// 3, for all subsets of the handle) can be captured once into a CUDA graph and
+// replayed with one launch:
+// - widths are fixed per subset: the iterate S, the direction Delta and the
+//   truncated residual have Rk = min(R_k, m_k) columns, zero beyond their
+//   rank (the SVD writes zeros there); concatenations have 2 Rk columns, the
+//   dense residual m_k.  Zero columns change nothing: the pivoted Cholesky
+//   drops them and the products add zeros;
+// - the eta test clears a per-subset device flag ("live") that gates every
+//   later launch of the subset, and the third Cholesky-QR pass is gated by
+//   the flag its first pass writes; the ranks stay on the device;
+// - every descriptor lives at a fixed device address (the truncation
+//   descriptors in S->cgt, uploaded before the first capture) or is passed by
+//   value, and the split-K workspace of the GEMMs is bound to the handle.
+// The result equals cheb_run's up to the summation order of the zero columns,
+// i.e. exactly in exact arithmetic.
+enum { CG_LIVE = 0, CG_RANK = 1, CG_STEPS = 2, CG_BROKE = 3, CG_ACT = 4, CG_NINT = 5 };
+enum { CG_NB = 0, CG_REL = 1, CG_NDBL = 2 };
+enum { TS_S = 0, TS_RES = 1, TS_D = 2, TS_NSITES = 3 };
+
+static std::atomic<int> g_graph_mode{2};  // 0 host-sized launches, 1 fixed sequence, 2 fixed sequence in a graph
+
+// ||B_k||_F from the column norms, the live flags of the solve and reset
+// counters (one thread per subset).
+__global__ void k_cheb_init(const double* __restrict__ norm2, const int* __restrict__ offm, int K, int* __restrict__ st,
+                            double* __restrict__ dd) {
+  const int k = threadIdx.x;
+  if (k >= K) return;
+  const int o = offm[2 * k], m = offm[2 * k + 1];
+  double t = 0;
+  for (int i = 0; i < m; ++i) t += norm2[o + i];
+  const double nb = sqrt(t);
+  st[CG_LIVE * K + k] = (st[CG_ACT * K + k] && nb > 0) ? 1 : 0;
+  st[CG_RANK * K + k] = 0;
+  st[CG_STEPS * K + k] = 0;
+  st[CG_BROKE * K + k] = 0;
+  dd[CG_NB * K + k] = nb;
+  dd[CG_REL * K + k] = 1.0;
+}
+
+// After a residual truncation: relative linear residual and the eta test.
+__global__ void k_cheb_eta(const double* __restrict__ frob2, int K, double eta, int* __restrict__ st,
+                           double* __restrict__ dd) {
+  const int k = threadIdx.x;
+  if (k >= K || !st[CG_LIVE * K + k]) return;
+  const double r = sqrt(frob2[k]), nb = dd[CG_NB * K + k];
+  dd[CG_REL * K + k] = nb > 0 ? r / nb : 0.0;
+  if (eta > 0 && r <= eta * nb) st[CG_LIVE * K + k] = 0;
+}
+
+static int fixed_rank(const lrfsi_subset_s* S, int k) { return std::min(S->cap[k], S->m[k]); }
+static Gate live_gate(lrfsi_subset_s* S, int k) { return Gate{S->cgi.p + CG_LIVE * S->K + k, nullptr}; }
+
+// Host copies of the truncation descriptors of the three sites of the
+// sequence (S update, residual, direction update) and of their third passes.
+static void fixed_descs(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector<TruncDesc>& out) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  out.assign((size_t)2 * TS_NSITES * K, TruncDesc{});
+  for (int site = 0; site < TS_NSITES; ++site)
+    for (int k = 0; k < K; ++k) {
+      const int Rk = fixed_rank(S, k);
+      TruncDesc& d = out[(size_t)site * K + k];
+      d.p = site == TS_RES ? S->m[k] : 2 * Rk;
+      d.m = S->m[k];
+      d.Vc = S->vside(S->Vcat, k, ldP);
+      d.ldv = ldP;
+      d.G = S->G.p + (size_t)k * ldP * ldP;
+      d.G2 = S->G2.p + (size_t)k * ldP * ldP;
+      d.T1 = S->T1.p + (size_t)k * ldP * ldP;
+      d.T2 = S->T2.p + (size_t)k * ldP * ldP;
+      double* Vout = site == TS_S ? S->vside(S->VS, k, ldR)
+                                  : (site == TS_RES ? S->vside(S->VR, k, ldR) : S->vside(S->VD, k, ldR));
+      d.Vout = Vout;
+      d.ldvo = ldR;
+      d.work = S->swork.p + S->swork_per * k;
+      d.iwork = S->iwork.p + (size_t)2 * ldP * k;
+      d.info = S->info.p + 5 * k;
+      d.sv = S->sv.p + (size_t)ldP * k;
+      d.frob2 = S->frob2.p + k;
+      d.rank_cap = Rk;
+      if (site == TS_RES && o.precision == 1) {  // FP32 residual: truncated at its noise level
+        d.tol = std::max(o.tol, 1e-6);
+        d.drop = 1e-12;
+      } else {
+        d.tol = o.tol;
+        d.drop = 1e-14;
+      }
+      d.gate = live_gate(S, k);
+      const TruncWork W(d.work, d.p, d.m);
+      d.core = W.C;
+      d.core_alt = W.Y;
+      d.sel = d.info + 4;
+      d.rank_out = site == TS_S ? S->cgi.p + CG_RANK * K + k : nullptr;
+      d.count = site == TS_S ? S->cgi.p + CG_STEPS * K + k : nullptr;
+      d.broke = S->cgi.p + CG_BROKE * K + k;
+      TruncDesc& d3 = out[(size_t)(TS_NSITES + site) * K + k];
+      d3 = d;
+      d3.gate = Gate{d.gate.a, d.info + 4};
+    }
+}
+
+// T of the concatenation in Xcat / Vcat for every subset, as a fixed sequence
+// (the launches of truncate_once with widths p, gated per subset; see the
+// header of dense.cu for the algorithm).  Outputs: the site's U buffer
+// (Rk columns, zero beyond the rank) and V buffer (written by the SVD).
+static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  const TruncDesc* hd = S->cgt_host.data() + (size_t)site * K;
+  TruncDesc* dd = S->cgt.p + (size_t)site * K;
+  TruncDesc* dd3 = S->cgt.p + (size_t)(TS_NSITES + site) * K;
+  std::vector<GramDesc> g1, g2, g3;
+  std::vector<GemmDesc<double>> q1y, c2, q2, y3, t1, uo;
+  for (int k = 0; k < K; ++k) {
+    const TruncDesc& d = hd[k];
+    const int p = d.p, m = d.m, w = d.rank_cap;
+    const TruncWork W(d.work, p, m);
+    const Gate live = d.gate, third{d.gate.a, d.info + 4};
+    double* X = S->tall(S->Xcat, k, ldP);
+    double* Q1 = S->tall(S->Q1, k, ldP);
+    double* Q2 = S->tall(S->Q2, k, ldP);
+    double* Uout = site == TS_S ? S->tall(S->US, k, ldR)
+                                : (site == TS_RES ? S->tall(S->UR, k, ldR) : S->tall(S->UD, k, ldR));
+    GramDesc g{X, ldP, p, X, ldP, p, d.G, p};
+    g.gate = live;
+    g1.push_back(g);
+    GemmDesc<double> a{(int)M, p, p, X, ldP, 1, d.T1, p, 1, Q1, ldP, 1, 1.0, 0.0};
+    a.gate = live;
+    q1y.push_back(a);
+    GemmDesc<double> b{p, m, p, W.Rk, p, 1, d.Vc, 1, d.ldv, W.Y, m, 1, 1.0, 0.0};
+    b.gate = live;
+    q1y.push_back(b);
+    g = GramDesc{Q1, ldP, p, Q1, ldP, p, d.G2, p};
+    g.gate = live;
+    g2.push_back(g);
+    GemmDesc<double> c{p, m, p, W.Rki, p, 1, W.Y, m, 1, W.C, m, 1, 1.0, 0.0};
+    c.gate = live;
+    c2.push_back(c);
+    GemmDesc<double> e{(int)M, p, p, Q1, ldP, 1, d.T2, p, 1, Q2, ldP, 1, 1.0, 0.0};
+    e.gate = third;
+    q2.push_back(e);
+    g = GramDesc{Q2, ldP, p, Q2, ldP, p, d.G2, p};
+    g.gate = third;
+    g3.push_back(g);
+    GemmDesc<double> f{p, m, p, W.Rki, p, 1, W.C, m, 1, W.Y, m, 1, 1.0, 0.0};
+    f.gate = third;
+    y3.push_back(f);
+    GemmDesc<double> t{p, w, p, d.T2, p, 1, W.Rk, p, 1, d.T1, p, 1, 1.0, 0.0};
+    t.gate = live;
+    t1.push_back(t);
+    GemmDesc<double> u{(int)M, w, p, Q1, ldP, 1, d.T1, p, 1, Uout, ldR, 1, 1.0, 0.0};
+    u.gate = live;
+    u.A_alt = Q2;
+    u.sel = d.info + 4;
+    uo.push_back(u);
+  }
+  LRFSI_TRY(gram_batched(g1.data(), K, M, S->gramwork.p, S->gramwork.n, s));
+  LRFSI_TRY(trunc_pass1(hd, K, s, dd, false));
+  LRFSI_TRY(gemm_grouped<double>(q1y.data(), (int)q1y.size(), s));
+  LRFSI_TRY(gram_batched(g2.data(), K, M, S->gramwork.p, S->gramwork.n, s));
+  LRFSI_TRY(trunc_qr(K, s, dd, 1));
+  LRFSI_TRY(gemm_grouped<double>(c2.data(), K, s));
+  LRFSI_TRY(gemm_grouped<double>(q2.data(), K, s));
+  LRFSI_TRY(gram_batched(g3.data(), K, M, S->gramwork.p, S->gramwork.n, s));
+  LRFSI_TRY(trunc_qr(K, s, dd3, 0));
+  LRFSI_TRY(gemm_grouped<double>(y3.data(), K, s));
+  LRFSI_TRY(trunc_svd(hd, K, s, dd, false));
+  LRFSI_TRY(gemm_grouped<double>(t1.data(), K, s));
+  LRFSI_TRY(gemm_grouped<double>(uo.data(), K, s));
+  return LRFSI_OK;
+}
+
+// Res = T(B - F(S)) for every live subset as a fixed sequence (lr_residual's
+// launches with S at Rk columns), then the eta test.
+static int residual_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaStream_t s) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  const long nnz = (long)S->mesh->h.colidx.size();
+  std::vector<CopyDesc> cd, cd2;
+  std::vector<SpmmDesc<double>> sd;
+  std::vector<GemmDesc<double>> gm;
+  std::vector<ConvDesc> c1, c2;
+  std::vector<SpmmDesc<float>> sdf;
+  std::vector<GemmDesc<float>> gmf;
+  for (int k = 0; k < K; ++k) {
+    const Gate live = live_gate(S, k);
+    const int m = S->m[k], r = fixed_rank(S, k);
+    double* X = S->tall(S->Xcat, k, ldP);
+    double* Vc = S->vside(S->Vcat, k, ldP);
+    const double* mu = S->mu.p + S->off[k];
+    const double* nu = S->nu.p + S->off[k];
+    const double* VS = S->vside(S->VS, k, ldR);
+    cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, X, ldP, M, m, 0, nullptr, 1.0, live});
+    cd.push_back(CopyDesc{VS, ldR, Vc, ldP, m, r, 0, nullptr, 1.0, live});
+    cd.push_back(CopyDesc{VS, ldR, Vc + r, ldP, m, r, 0, mu, 1.0, live});
+    cd.push_back(CopyDesc{VS, ldR, Vc + 2 * r, ldP, m, r, 0, nu, 1.0, live});
+    cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0, live});
+    if (o.precision == 0) {
+      SpmmDesc<double> d;
+      d.J3 = S->J3.p + (size_t)k * 3 * nnz;
+      d.U = S->tall(S->US, k, ldR);
+      d.ldu = ldR;
+      d.r = r;
+      d.Y = S->tall(S->Q1, k, ldP);
+      d.ldy = ldP;
+      d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+      d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
+      d.a1 = d.a2 = 0.0;
+      d.gate = live;
+      sd.push_back(d);
+      GemmDesc<double> g{(int)M, m, 3 * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0, 1.0};
+      g.gate = live;
+      gm.push_back(g);
+    } else {  // B - F(S) with an FP32 SpMM and GEMM, widened to FP64 for the truncation
+      float* Uf = S->USf.p + (size_t)k * M * ldR;
+      float* Yf = S->Yf.p + (size_t)k * M * ldP;
+      float* Xf = S->Xf.p + (size_t)k * M * ldP;
+      float* Vf = S->Vf.p + (size_t)S->off[k] * ldP;
+      c1.push_back(ConvDesc{S->tall(S->US, k, ldR), ldR, Uf, ldR, M, r, nullptr, 1.0, live});
+      c1.push_back(ConvDesc{X, ldP, Xf, ldP, M, m, nullptr, 1.0, live});
+      c1.push_back(ConvDesc{Vc, ldP, Vf, ldP, m, 3 * r, nullptr, 1.0, live});
+      SpmmDesc<float> d;
+      d.J3 = S->J3f.p + (size_t)k * 3 * nnz;
+      d.U = Uf; d.ldu = ldR; d.r = r; d.Y = Yf; d.ldy = ldP;
+      d.o[0] = 0; d.o[1] = r; d.o[2] = 2 * r;
+      d.sc[0] = d.sc[1] = d.sc[2] = 1.0f;
+      d.a1 = d.a2 = 0.0f;
+      d.gate = live;
+      sdf.push_back(d);
+      GemmDesc<float> g{(int)M, m, 3 * r, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f};
+      g.gate = live;
+      gmf.push_back(g);
+      c2.push_back(ConvDesc{Xf, ldP, X, ldP, M, m, nullptr, 1.0, live});
+    }
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  if (o.precision == 0) {
+    LRFSI_TRY(spmm_batched<double>(S->mesh, sd.data(), (int)sd.size(), s));
+    LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
+  } else {
+    LRFSI_TRY((convert_batched<double, float>(c1, s)));
+    LRFSI_TRY(spmm_batched<float>(S->mesh, sdf.data(), (int)sdf.size(), s));
+    LRFSI_TRY(gemm_grouped<float>(gmf.data(), (int)gmf.size(), s));
+    LRFSI_TRY((convert_batched<float, double>(c2, s)));
+  }
+  LRFSI_TRY(copy_batched(cd2, s));
+  LRFSI_TRY(trunc_fixed(S, TS_RES, s));
+  k_cheb_eta<<<1, 32, 0, s>>>(S->frob2.p, K, o.eta, S->cgi.p, S->cgd.p);
+  return check_launch("k_cheb_eta");
+}
+
+// UZ = P^{-1} UR (Rk columns) for every live subset.
+static int precond_fixed(lrfsi_subset_s* S, cudaStream_t s) {
+  const int K = S->K, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<CopyDesc> cd;
+  std::vector<double*> X(K), Y(K);
+  std::vector<int> r(K);
+  std::vector<Gate> gates(K);
+  for (int k = 0; k < K; ++k) {
+    r[k] = fixed_rank(S, k);
+    gates[k] = live_gate(S, k);
+    X[k] = S->tall(S->Ytmp, k, ldR);
+    Y[k] = S->tall(S->UZ, k, ldR);
+    cd.push_back(CopyDesc{S->tall(S->UR, k, ldR), ldR, X[k], ldR, M, r[k], 0, nullptr, 1.0, gates[k]});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  return blocklu_solve(S->lu, X.data(), Y.data(), r.data(), ldR, K, s, gates.data());
+}
+
+// [A | B] -> Xcat and [a VA | b VB] -> Vcat (Rk columns each) for every subset.
+static int concat_fixed(lrfsi_subset_s* S, DevBuf<double>& UA, DevBuf<double>& VA, double a, DevBuf<double>& UB_,
+                        DevBuf<double>& VB_, double b, cudaStream_t s) {
+  const int K = S->K, ldP = S->ldP, ldR = S->ldR;
+  const long M = S->M;
+  std::vector<CopyDesc> cd;
+  for (int k = 0; k < K; ++k) {
+    const Gate live = live_gate(S, k);
+    const int r = fixed_rank(S, k), m = S->m[k];
+    double* X = S->tall(S->Xcat, k, ldP);
+    double* Vc = S->vside(S->Vcat, k, ldP);
+    cd.push_back(CopyDesc{S->tall(UA, k, ldR), ldR, X, ldP, M, r, 0, nullptr, 1.0, live});
+    cd.push_back(CopyDesc{S->tall(UB_, k, ldR), ldR, X + r, ldP, M, r, 0, nullptr, 1.0, live});
+    cd.push_back(CopyDesc{S->vside(VA, k, ldR), ldR, Vc, ldP, m, r, 0, nullptr, a, live});
+    cd.push_back(CopyDesc{S->vside(VB_, k, ldR), ldR, Vc + r, ldP, m, r, 0, nullptr, b, live});
+  }
+  return copy_batched(cd, s);
+}
+
+// The whole ChebyshevT solve (options o) of the subsets flagged in cgi[CG_ACT]
+// as one launch sequence without host reads.  B dense in UB; result in US/VS
+// (Rk columns, zero beyond cgi[CG_RANK]).
+static int cheb_fixed_enqueue(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaStream_t s) {
+  const int K = S->K, ldR = S->ldR;
+  const long M = S->M;
+  LRFSI_CUDA(cudaMemsetAsync(S->US.p, 0, sizeof(double) * (size_t)K * M * ldR, s));
+  LRFSI_CUDA(cudaMemsetAsync(S->VS.p, 0, sizeof(double) * (size_t)S->mtot * ldR, s));
+  for (int k = 0; k < K; ++k)
+    LRFSI_TRY(launch_colnorm2(S->tall(S->UB, k, ldR), M, S->m[k], ldR, S->rc.norm2.p + S->off[k], S->rc.work.p,
+                              S->rc.work.n, s));
+  k_cheb_init<<<1, 32, 0, s>>>(S->rc.norm2.p, S->offm.p, K, S->cgi.p, S->cgd.p);
+  LRFSI_TRY(check_launch("k_cheb_init"));
+  const double sigma = o.d / o.c;
+  for (int cyc = 0; cyc < o.cycles; ++cyc) {
+    LRFSI_TRY(residual_fixed(S, o, s));
+    LRFSI_TRY(precond_fixed(S, s));
+    {  // Delta = Z / d
+      std::vector<CopyDesc> cd;
+      for (int k = 0; k < K; ++k) {
+        const Gate live = live_gate(S, k);
+        const int r = fixed_rank(S, k);
+        cd.push_back(CopyDesc{S->tall(S->UZ, k, ldR), ldR, S->tall(S->UD, k, ldR), ldR, M, r, 0, nullptr, 1.0, live});
+        cd.push_back(CopyDesc{S->vside(S->VR, k, ldR), ldR, S->vside(S->VD, k, ldR), ldR, S->m[k], r, 0, nullptr,
+                              1.0 / o.d, live});
+      }
+      LRFSI_TRY(copy_batched(cd, s));
+    }
+    double rho = 1.0 / sigma;
+    for (int j = 0; j < o.iters; ++j) {
+      LRFSI_TRY(concat_fixed(S, S->US, S->VS, 1.0, S->UD, S->VD, 1.0, s));  // S <- T(S + Delta)
+      LRFSI_TRY(trunc_fixed(S, TS_S, s));
+      if (j == o.iters - 1) break;
+      LRFSI_TRY(residual_fixed(S, o, s));
+      LRFSI_TRY(precond_fixed(S, s));
+      const double rn = 1.0 / (2.0 * sigma - rho);  // Delta <- T(rho' rho Delta + (2 rho' / c) Z)
+      LRFSI_TRY(concat_fixed(S, S->UD, S->VD, rn * rho, S->UZ, S->VR, 2.0 * rn / o.c, s));
+      LRFSI_TRY(trunc_fixed(S, TS_D, s));
+      rho = rn;
+    }
+  }
+  return LRFSI_OK;
+}
+
+// Prepared state of the fixed sequence for these options and buffers: the key
+// holds everything the descriptors and the captured launches depend on.
+static std::vector<double> fixed_key(const lrfsi_subset_s* S, const lrfsi_cheb_options& o) {
+  return {o.c, o.d, (double)o.iters, (double)o.cycles, o.tol, o.eta, (double)o.precision, (double)S->ldP,
+          (double)(uintptr_t)S->Xcat.p, (double)(uintptr_t)S->swork.p};
+}
+
+static int fixed_prepare(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaStream_t s) {
+  const int K = S->K;
+  if (!S->cgi.p) {
+    LRFSI_TRY(S->cgi.alloc((size_t)CG_NINT * K));
+    LRFSI_TRY(S->cgd.alloc((size_t)CG_NDBL * K));
+    std::vector<int> om(2 * K);
+    for (int k = 0; k < K; ++k) { om[2 * k] = S->off[k]; om[2 * k + 1] = S->m[k]; }
+    LRFSI_TRY(S->offm.upload(om, s));
+  }
+  const std::vector<double> key = fixed_key(S, o);
+  if (key != S->cg_key) {
+    S->drop_graph();
+    fixed_descs(S, o, S->cgt_host);
+    LRFSI_TRY(S->cgt.upload(S->cgt_host, s));
+    S->cg_key = key;
+  }
+  return LRFSI_OK;
+}
+
+static std::atomic<long long> g_graph_replays{0}, g_graph_captures{0}, g_graph_fallbacks{0};
+
+// ChebyshevT for the subsets in act through the fixed sequence: replayed from
+// the handle's CUDA graph (captured on first use of these options, after one
+// direct run that also sizes the split-K workspace), or launched directly
+// (graph mode 1, or while kernel timing is on).  A subset whose truncation
+// broke down is solved again by cheb_run.
+static int cheb_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std::vector<int>& act,
+                      std::vector<int>& rS, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
+  const int K = S->K;
+  LRFSI_TRY(fixed_prepare(S, o, s));
+  {
+    std::vector<int> a(K, 0);
+    for (int k : act) a[k] = 1;
+    LRFSI_CUDA(cudaMemcpyAsync(S->cgi.p + CG_ACT * K, a.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
+  }
+  const bool use_graph = g_graph_mode.load() == 2 && !g_timing;
+  if (use_graph && S->cg_exec) {
+    LRFSI_CUDA(cudaGraphLaunch(S->cg_exec, s));
+    count_launch(S->cg_nodes);
+    g_graph_replays += 1;
+  } else {
+    gemm_ws_peak_reset();
+    LRFSI_TRY(cheb_fixed_enqueue(S, o, s));
+    if (use_graph) {  // capture the same sequence on the handle's stream for the next calls
+      const size_t need = std::max<size_t>(gemm_ws_peak(), 256);
+      if (S->cgws.n < need) LRFSI_TRY(S->cgws.alloc(need));
+      if (!S->cap_stream) LRFSI_CUDA(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+      const uint64_t before = g_launches.load();
+      gemm_ws_bind(S->cgws.p, S->cgws.n);
+      cudaGraph_t graph = nullptr;
+      int st_cap = LRFSI_OK;
+      cudaError_t e = cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        st_cap = cheb_fixed_enqueue(S, o, S->cap_stream);
+        e = cudaStreamEndCapture(S->cap_stream, &graph);
+      }
+      gemm_ws_bind(nullptr, 0);
+      const uint64_t nodes = g_launches.load() - before;
+      g_launches -= nodes;  // captured, not launched
+      if (e == cudaSuccess && st_cap == LRFSI_OK && graph) {
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e == cudaSuccess) {
+          S->cg_graph = graph;
+          S->cg_exec = exec;
+          S->cg_nodes = nodes;
+          g_graph_captures += 1;
+        } else {
+          cudaGraphDestroy(graph);
+        }
+      } else if (graph) {
+        cudaGraphDestroy(graph);
+      }
+      if (!S->cg_exec) {  // capture failed: keep launching the sequence directly
+        cudaGetLastError();
+        g_graph_fallbacks += 1;
+        g_graph_mode = 1;
+      }
+    }
+  }
+  std::vector<int> hi((size_t)CG_NINT * K);
+  std::vector<double> hd((size_t)CG_NDBL * K);
+  LRFSI_CUDA(cudaMemcpyAsync(hi.data(), S->cgi.p, sizeof(int) * hi.size(), cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaMemcpyAsync(hd.data(), S->cgd.p, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  rS.assign(K, 0);
+  st.assign(K, lrfsi_cheb_stats{0, 0, 1.0, 0});
+  std::vector<int> redo;
+  for (int k : act) {
+    rS[k] = hi[CG_RANK * K + k];
+    st[k].steps = hi[CG_STEPS * K + k];
+    st[k].rank = rS[k];
+    st[k].rel_lin_res = hd[CG_REL * K + k];
+    st[k].max_concat_rank = 3 * fixed_rank(S, k);
+    if (hi[CG_BROKE * K + k]) redo.push_back(k);
+  }
+  if (!redo.empty()) {  // a Cholesky-QR breakdown: the host-sized path with its retries
+    g_tr_breakdown += (long long)redo.size();
+    std::vector<int> r2;
+    std::vector<lrfsi_cheb_stats> st2;
+    LRFSI_TRY(cheb_run(S, o, redo, r2, st2, s));
+    for (int k : redo) {
+      rS[k] = r2[k];
+      st[k] = st2[k];
+    }
+  }
+  return LRFSI_OK;
+}
+
 // Krylov basis storage of GMREST for `iters` steps per cycle: the tall
 // factors of V_j and Z_j = P^{-1} V_j (K x M x ldR each), the parameter-side
 // factors of V_j (sum m_k x ldR), the two Gram blocks of the inner products
@@ -1619,7 +2100,8 @@ static int solver_prepare(lrfsi_subset_s* S, const lrfsi_cheb_options& o) {
 // The low-rank solver the options select (0: ChebyshevT, 1: GMREST).
 static int lr_solve(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std::vector<int>& act,
                     std::vector<int>& rS, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
-  return o.solver == 1 ? gmres_run(S, o, act, rS, st, s) : cheb_run(S, o, act, rS, st, s);
+  if (o.solver == 1) return gmres_run(S, o, act, rS, st, s);
+  return g_graph_mode.load() > 0 ? cheb_fixed(S, o, act, rS, st, s) : cheb_run(S, o, act, rS, st, s);
 }
 
 static int check_opts(const lrfsi_cheb_options* o) {
@@ -1679,6 +2161,28 @@ static int lowrank_solve(lrfsi_subset_h S, const double* UB, int lduB, const dou
   }
   LRFSI_TRY(copy_batched(cd, s));
   LRFSI_CUDA(cudaStreamSynchronize(s));
+  return LRFSI_OK;
+}
+
+using namespace lrfsi;
+
+extern "C" int lrfsi_graph_mode(int mode, int* previous) {
+  if (mode < -1 || mode > 2) return fail(LRFSI_EINVAL, "lrfsi_graph_mode: mode must be 0, 1, 2 (or -1 to query)");
+  const int old = mode >= 0 ? g_graph_mode.exchange(mode) : g_graph_mode.load();
+  if (previous) *previous = old;
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_graph_counters(int64_t* out3, int reset) {
+  if (!out3) return fail(LRFSI_EINVAL, "lrfsi_graph_counters: null output");
+  out3[0] = g_graph_replays.load();
+  out3[1] = g_graph_captures.load();
+  out3[2] = g_graph_fallbacks.load();
+  if (reset) {
+    g_graph_replays = 0;
+    g_graph_captures = 0;
+    g_graph_fallbacks = 0;
+  }
   return LRFSI_OK;
 }
 

@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(256) k_spmm(SpmmBatch<T> sb, const int* __rest
   // Trip counts are made uniform over the warp (rows of one warp differ in
   // length); lanes past their row's end only skip the arithmetic.
   const SpmmDesc<T>& dref = sb.d[blockIdx.y];
+  if (!gate_open(dref.gate)) return;
   constexpr int RPB = 256 / LPR;
   const long row0 = (long)blockIdx.x * RPB + (threadIdx.x / LPR);
   const int lane = threadIdx.x % LPR;
@@ -113,6 +114,7 @@ __global__ void __launch_bounds__(256) k_spmm_win(SpmmBatch<T> sb, const int* __
   extern __shared__ __align__(16) unsigned char smraw[];
   T* Us = reinterpret_cast<T*>(smraw);
   const SpmmDesc<T>& dref = sb.d[blockIdx.y];
+  if (!gate_open(dref.gate)) return;
   const long rb0 = (long)blockIdx.x * kSpmmRowBlock;
   const int w0 = win[2 * blockIdx.x], w1 = win[2 * blockIdx.x + 1];
   const int wl = w1 - w0;
@@ -827,7 +829,8 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
   return LRFSI_OK;
 }
 
-int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r, int ld, int nprob, cudaStream_t s) {
+int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r, int ld, int nprob, cudaStream_t s,
+                  const Gate* gates) {
   TimedLaunch tl_all(KC_LUSOLVE, s);  // the whole solve is one timed region (its GEMMs are class KC_GEMM)
   const int nmax = lu.nmax;
   const size_t nb2 = (size_t)nmax * nmax;
@@ -842,6 +845,7 @@ int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r,
         double* ws = lu.ws.p + lu.per_prob * b;
         gd[b] = GemmDesc<double>{n, r[b], np, ws + lu.off_lo + nb2 * (sl - 1), nmax, 1, Y[b] + op * ld, ld, 1,
                                  X[b] + o * ld, ld, 1, -1.0, 1.0};
+        if (gates) gd[b].gate = gates[b];
       }
       LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
     }
@@ -849,6 +853,7 @@ int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r,
       double* ws = lu.ws.p + lu.per_prob * b;
       gd[b] = GemmDesc<double>{n, r[b], n, ws + lu.off_inv + nb2 * sl, nmax, 1, X[b] + o * ld, ld, 1, Y[b] + o * ld,
                                ld, 1, 1.0, 0.0};
+      if (gates) gd[b].gate = gates[b];
     }
     LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
   }
@@ -859,6 +864,7 @@ int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r,
       double* ws = lu.ws.p + lu.per_prob * b;
       gd[b] = GemmDesc<double>{n, r[b], nn, ws + lu.off_up + nb2 * sl, nmax, 1, Y[b] + on * ld, ld, 1, Y[b] + o * ld,
                                ld, 1, -1.0, 1.0};
+      if (gates) gd[b].gate = gates[b];
     }
     LRFSI_TRY(gemm_grouped<double>(gd.data(), nprob, s));
   }

@@ -17,6 +17,7 @@ struct SpmmDesc {
   int o[3];           // output column offsets (o[1] < 0: combined mode)
   T sc[3];            // output scales
   T a1, a2;           // combined-mode coefficients
+  Gate gate;          // run condition (see Gate)
 };
 template <class T>
 int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_t s);
@@ -48,8 +49,9 @@ int blocklu_factor(const lrfsi_mesh_s* m, BlockLU& lu, const double* const* J3, 
                    const double* beta, int nprob, cudaStream_t s, const double* const* b = nullptr,
                    double* const* y = nullptr, int ldb = 0);
 // Y_b = A_b^{-1} X_b for r columns; X_b is overwritten (scratch).  X, Y: M x r, ld.
+// gates (optional, nprob entries): the run condition of each problem's GEMMs.
 int blocklu_solve(BlockLU& lu, double* const* X, double* const* Y, const int* r, int ld, int nprob,
-                  cudaStream_t s);
+                  cudaStream_t s, const Gate* gates = nullptr);
 // Host copy of per-problem status (0 ok, LRFSI_ESINGULAR).
 int blocklu_status(BlockLU& lu, int nprob, std::vector<int>& out, cudaStream_t s);
 

@@ -103,6 +103,8 @@ def load():
         "lrfsi_learned_factors": [vp, vp, i, vp, vp, vp, vp, vp, i, i, vp, vp, vp, vp, vp, i, vp, i, vp],
         "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
         "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
+        "lrfsi_graph_mode": [i, vp],
+        "lrfsi_graph_counters": [vp, i],
         "lrfsi_order_grid": [i, i, vp, vp, i, vp, vp],
         "lrfsi_order_set": [i, vp, vp, vp],
         "lrfsi_cluster": [i, i, vp, vp, vp],
@@ -198,6 +200,21 @@ def lrfsi_partition(weights, nproc):
     first = np.zeros(nproc + 1, np.int32)
     _check(load().lrfsi_partition(len(w), _ptr(w) if len(w) else None, int(nproc), _ptr(first)))
     return first
+
+
+def graph_mode(mode=-1):
+    """Set the ChebyshevT launch mode (0 host-sized, 1 fixed sequence, 2 CUDA
+    graph; -1 queries); returns the previous mode."""
+    prev = C.c_int(0)
+    _check(load().lrfsi_graph_mode(int(mode), C.byref(prev)))
+    return prev.value
+
+
+def graph_counters(reset=False):
+    """(replays, captures, capture failures) of the ChebyshevT graphs."""
+    out = np.zeros(3, np.int64)
+    _check(load().lrfsi_graph_counters(_ptr(out), int(bool(reset))))
+    return dict(replays=int(out[0]), captures=int(out[1]), failures=int(out[2]))
 
 
 def kernel_launches():

@@ -1,0 +1,226 @@
+"""ChebyshevT as a fixed launch sequence and as a replayed CUDA graph
+(lrfsi_graph_mode 1 and 2) against the host-sized launches (mode 0) and the
+oracle, through the C ABI.
+
+* Three uneven subsets advancing together (the batching of Algorithm 1
+  step 3): every mode matches the oracle's ChebyshevT (1e-10 per column,
+  relative to the subset's largest column), the fixed modes match mode 0 to
+  1e-12, and the graph is captured once and then replayed (the second call
+  is a replay and gives the same result).
+* Truncation that decides the result (tol 1e-8, rank cap below m_k, eta
+  early stop on the device): the same ranks and inner step counts as mode 0,
+  the factors' product to 1e-10, and the oracle's truncated iteration to 1e-8
+  where every truncation gap is >= 1e-6.
+* The subset step (corrections until 1e-8) in mode 2, FP64 and mixed: the
+  same correction counts and relative residuals as mode 0, and the oracle's
+  residuals of the GPU's columns.
+* The launch counter adds the graph's kernel nodes on every replay.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import algorithm1, fsi, lowrank, newton, params  # noqa: E402
+from paper_2008_10275_gb300 import build, lrfsi  # noqa: E402
+from tests.gpu_common import perm_lib_to_oracle  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+    lrfsi.load()
+    prev = lrfsi.graph_mode(2)
+    yield
+    lrfsi.graph_mode(prev)
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+def _problem(sizes, seed, spread=2e5):
+    lm = lrfsi.Mesh(20, 4)
+    om = fsi.Mesh(fsi.Problem(20, 4))
+    perm = perm_lib_to_oracle(lm, om)
+    rng = np.random.default_rng(seed)
+    mus, nus, xts = [], [], []
+    for q, m in enumerate(sizes):
+        mu = np.sort(rng.uniform(6e5 + spread * q, 8e5 + spread * q, m))
+        nu = rng.uniform(2.5e-3, 3.5e-3, m)
+        xt, _, _ = newton.newton(om, mu[params.upper_median_position(m)], nu[params.upper_median_position(m)],
+                                 eps=1e-11)
+        mus.append(mu); nus.append(nu); xts.append(xt)
+    return lm, om, perm, mus, nus, xts
+
+
+def _rhs_factors(lm, om, perm, sizes, mus, nus, xts):
+    K = len(sizes)
+    UB = torch.zeros(K * lm.M * 3, dtype=torch.float64, device=DEV)
+    VB = torch.zeros(sum(sizes) * 3, dtype=torch.float64, device=DEV)
+    o = 0
+    for q, m in enumerate(sizes):
+        R0, Rmu, Rnu = fsi.affine_residual(om, xts[q])
+        UB[q * lm.M * 3:(q + 1) * lm.M * 3] = _dev(np.stack([R0, Rmu, Rnu], 1)[perm]).reshape(-1)
+        VB[o * 3:(o + m) * 3] = _dev(-np.stack([np.ones(m), mus[q], nus[q]], 1)).reshape(-1)
+        o += m
+    return UB, VB
+
+
+def _solve(sub, lm, sizes, UB, VB, opt, ld):
+    K = len(sizes)
+    U = torch.zeros(K * lm.M * ld, dtype=torch.float64, device=DEV)
+    V = torch.zeros(sum(sizes) * ld, dtype=torch.float64, device=DEV)
+    ranks, stats = lrfsi.lrfsi_chebyshevT(sub, UB, 3, VB, 3, [3] * K, opt, U, ld, V, ld)
+    Uh, Vh = U.cpu().numpy(), V.cpu().numpy()
+    out, o = [], 0
+    for q, m in enumerate(sizes):
+        r = int(ranks[q])
+        Uq = Uh[q * lm.M * ld:(q + 1) * lm.M * ld].reshape(lm.M, ld)[:, :r]
+        Vq = Vh[o * ld:(o + m) * ld].reshape(m, ld)[:, :r]
+        out.append(Uq @ Vq.T)
+        o += m
+    return ranks, stats, out
+
+
+def _oracle(om, perm, mu, nu, xt, c, d, **kw):
+    J0, Jmu, Jnu = fsi.affine_jacobian(om, xt)
+    B = lowrank.rhs(*fsi.affine_residual(om, xt), mu, nu)
+    mb, nb = params.midpoint_parameters(mu, nu)
+    return lowrank.chebyshev_T_scaled(J0, Jmu, Jnu, B, mu, nu, mb, nb, c, d, **kw)[perm]
+
+
+def test_modes_match_oracle_and_each_other_uneven_subsets():
+    sizes = [5, 12, 9]
+    lm, om, perm, mus, nus, xts = _problem(sizes, seed=17)
+    sub = lrfsi.Subsets(lm, _dev(np.stack([x[perm] for x in xts])), np.concatenate(mus), np.concatenate(nus), sizes,
+                        sizes)
+    UB, VB = _rhs_factors(lm, om, perm, sizes, mus, nus, xts)
+    c, d, ld = 0.5, 1.0, max(sizes)
+    opt = lrfsi.cheb_options(c, d, iters=6, cycles=2, rank_cap=ld, tol=1e-13)
+    res = {}
+    lrfsi.graph_counters(reset=True)
+    for mode, rep in ((0, 0), (1, 0), (2, 0), (2, 1)):
+        lrfsi.graph_mode(mode)
+        res[(mode, rep)] = _solve(sub, lm, sizes, UB, VB, opt, ld)
+    gc = lrfsi.graph_counters()
+    assert gc["captures"] == 1 and gc["replays"] == 1 and gc["failures"] == 0, gc
+    for q, m in enumerate(sizes):
+        So = _oracle(om, perm, mus[q], nus[q], xts[q], c, d, iters=6, cycles=2, tol=1e-13, rank_cap=m)
+        scale = np.linalg.norm(So, axis=0).max()
+        for key, (ranks, stats, S) in res.items():
+            err = np.linalg.norm(S[q] - So, axis=0).max() / scale
+            assert err <= 1e-10, (key, q, err)
+            assert stats[q]["steps"] == res[(0, 0)][1][q]["steps"]
+        base = res[(0, 0)][2][q]
+        for key in ((1, 0), (2, 0), (2, 1)):
+            assert np.abs(res[key][2][q] - base).max() <= 1e-12 * scale, (key, q)
+    # the replay and the direct run of the same sequence agree bit for bit
+    for q in range(len(sizes)):
+        assert np.array_equal(res[(2, 1)][2][q], res[(2, 0)][2][q])
+
+
+def _recording_truncate(gaps):
+    orig = lowrank.truncate
+
+    def T(X, tol, cap):
+        s = np.linalg.svd(X, compute_uv=False)
+        r = lowrank.truncation_rank(s, tol, cap)
+        if 0 < r < len(s) and s[r - 1] > 0:
+            gaps.append((s[r - 1] - s[r]) / s[r - 1])
+        return orig(X, tol, cap)
+    return T
+
+
+def test_truncated_eta_graph_matches_host_sized_and_oracle(monkeypatch):
+    sizes, caps = [24, 16], [10, 8]
+    lm, om, perm, mus, nus, xts = _problem(sizes, seed=11, spread=1.5e5)
+    sub = lrfsi.Subsets(lm, _dev(np.stack([x[perm] for x in xts])), np.concatenate(mus), np.concatenate(nus), sizes,
+                        caps)
+    UB, VB = _rhs_factors(lm, om, perm, sizes, mus, nus, xts)
+    c, d, ld = 0.65, 1.0, max(caps)
+    out = {}
+    for eta in (0.0, 0.05):
+        opt = lrfsi.cheb_options(c, d, iters=6, cycles=2, rank_cap=ld, tol=1e-8, eta=eta)
+        for mode in (0, 2, 2):
+            lrfsi.graph_mode(mode)
+            out[(eta, mode)] = _solve(sub, lm, sizes, UB, VB, opt, ld)
+        r0, st0, S0 = out[(eta, 0)]
+        r2, st2, S2 = out[(eta, 2)]
+        assert list(r0) == list(r2)
+        for q in range(len(sizes)):
+            assert st0[q]["steps"] == st2[q]["steps"], (eta, q)
+            scale = np.linalg.norm(S0[q], axis=0).max()
+            assert np.abs(S2[q] - S0[q]).max() <= 1e-10 * scale, (eta, q)
+    # eta stops early: fewer inner steps than the full 12
+    assert all(s["steps"] < 12 for s in out[(0.05, 2)][1])
+    # the oracle's truncated iteration, gap-checked
+    for q in range(len(sizes)):
+        gaps = []
+        monkeypatch.setattr(lowrank, "truncate", _recording_truncate(gaps))
+        So = _oracle(om, perm, mus[q], nus[q], xts[q], c, d, iters=6, cycles=2, tol=1e-8, rank_cap=caps[q])
+        monkeypatch.undo()
+        assert gaps and min(gaps) >= 1e-6, min(gaps)
+        scale = np.linalg.norm(So, axis=0).max()
+        err = np.linalg.norm(out[(0.0, 2)][2][q] - So, axis=0).max() / scale
+        assert err <= 1e-8, (q, err)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_subset_step_graph_matches_host_sized(precision):
+    sizes = [10, 14]
+    lm, om, perm, mus, nus, xts = _problem(sizes, seed=23)
+    mu, nu = np.concatenate(mus), np.concatenate(nus)
+    K, R = len(sizes), 12
+    opt = lrfsi.cheb_options(0.65, 1.0, iters=6, cycles=2, rank_cap=R, tol=1e-8, eta=0.05, precision=precision)
+    got = {}
+    for mode in (0, 2):
+        lrfsi.graph_mode(mode)
+        sub = lrfsi.Subsets(lm, _dev(np.stack([x[perm] for x in xts])), mu, nu, sizes, [R] * K)
+        U = torch.zeros(K * lm.M * R, dtype=torch.float64, device=DEV)
+        V = torch.zeros(sum(sizes) * R, dtype=torch.float64, device=DEV)
+        ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, 1e-8, 30, U, R, V, R)
+        assert st == 0 and rel.max() <= 1e-8, (mode, rel.max())
+        got[mode] = (ranks, rel, outer, U.cpu().numpy(), V.cpu().numpy())
+        sub.close()
+    assert list(got[0][2]) == list(got[2][2])           # the same correction counts
+    assert np.allclose(got[0][1], got[2][1], rtol=1e-3, atol=1e-12)
+    # the oracle's residuals of the graph path's columns
+    ranks, rel, outer, Uh, Vh = got[2]
+    inv = np.argsort(perm)
+    o = 0
+    for q, m in enumerate(sizes):
+        r = int(ranks[q])
+        X = xts[q][perm][:, None] + Uh[q * lm.M * R:(q + 1) * lm.M * R].reshape(lm.M, R)[:, :r] @ \
+            Vh[o * R:(o + m) * R].reshape(m, R)[:, :r].T
+        rr = algorithm1.relative_residuals(om, X[inv], mus[q], nus[q])
+        assert rr.max() <= 1e-8 and np.allclose(rr, rel[o:o + m], rtol=1e-6, atol=1e-14)
+        o += m
+
+
+def test_replays_count_their_kernel_nodes():
+    sizes = [6, 7]
+    lm, om, perm, mus, nus, xts = _problem(sizes, seed=5)
+    sub = lrfsi.Subsets(lm, _dev(np.stack([x[perm] for x in xts])), np.concatenate(mus), np.concatenate(nus), sizes,
+                        sizes)
+    UB, VB = _rhs_factors(lm, om, perm, sizes, mus, nus, xts)
+    opt = lrfsi.cheb_options(0.5, 1.0, iters=3, cycles=1, rank_cap=7, tol=1e-12)
+    lrfsi.graph_mode(1)
+    n0 = lrfsi.kernel_launches()
+    _solve(sub, lm, sizes, UB, VB, opt, 7)
+    direct = lrfsi.kernel_launches() - n0
+    lrfsi.graph_mode(2)
+    _solve(sub, lm, sizes, UB, VB, opt, 7)   # direct run + capture
+    deltas = []
+    for _ in range(2):
+        n0 = lrfsi.kernel_launches()
+        _solve(sub, lm, sizes, UB, VB, opt, 7)
+        deltas.append(lrfsi.kernel_launches() - n0)
+    # a replay runs the kernels of one direct sequence (plus the copy-out launches
+    # around the solve, the same in both modes)
+    assert deltas[0] == deltas[1] == direct, (deltas, direct)

@@ -3,7 +3,12 @@ truncated solvers at the benchmark's truncation settings.
 
 * lrfsi_precond_apply: P_k^{-1} X for the mean-based preconditioner
   (Sec. 4.2) vs a sparse direct solve of the oracle's P_k (scipy splu), on
-  the 20 x 4 and 80 x 16 meshes, two uneven subsets; 1e-10 per column.
+  the 20 x 4 and 80 x 16 meshes, two uneven subsets.  Two backward-stable
+  solvers agree only to about cond(P_k) eps (P_k mixes unit Dirichlet rows
+  with solid rows of size mu ~ 1e6), so the test checks the backward error of
+  the GPU solution, ||P y - x||_inf / (||P||_inf ||y||_inf + ||x||_inf) <=
+  1e-12, and the forward agreement with splu to max(1e-10, 20 cond_1(P) eps)
+  per column, cond_1 estimated with onenormest on the splu factors.
 * lrfsi_truncate: T (Sec. 5, the best rank-<= R approximation) vs the oracle's
   SVD truncation on factors with a known, well-separated spectrum; the kept
   product to 1e-12 of the largest singular value, the same rank, U
@@ -21,6 +26,7 @@ truncated solvers at the benchmark's truncation settings.
 """
 import numpy as np
 import pytest
+import scipy.sparse.linalg as spla
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -80,10 +86,19 @@ def test_precond_apply_matches_sparse_direct_solve(nx, ny):
         J0, Jmu, Jnu = fsi.affine_jacobian(om, xt_k)
         mb, nb = params.midpoint_parameters(mu_k, nu_k)
         P = lowrank.preconditioner(J0, Jmu, Jnu, mb, nb)
-        ref = P.solve(np.ascontiguousarray(Xh[k][:, :r[k]][inv]))[perm]
+        xk = np.ascontiguousarray(Xh[k][:, :r[k]][inv])
+        ref = P.solve(xk)
+        A = (J0 + mb * Jmu + nb * Jnu).tocsr()
+        Pinv = spla.LinearOperator(A.shape, matvec=P.solve, rmatvec=lambda v: P.solve(v, trans="T"))
+        cond1 = spla.norm(A, 1) * spla.onenormest(Pinv)
+        fwd_tol = max(1e-10, 20 * cond1 * np.finfo(float).eps)
+        Anorm = spla.norm(A, np.inf)
         for j in range(r[k]):
-            err = np.linalg.norm(Yh[k][:, j] - ref[:, j]) / np.linalg.norm(ref[:, j])
-            assert err <= 1e-10, (k, j, err)
+            y = Yh[k][:, j][inv]
+            back = np.abs(A @ y - xk[:, j]).max() / (Anorm * np.abs(y).max() + np.abs(xk[:, j]).max())
+            assert back <= 1e-12, (k, j, back)
+            err = np.linalg.norm(y - ref[:, j]) / np.linalg.norm(ref[:, j])
+            assert err <= fwd_tol, (k, j, err, cond1)
     sub.close()
 
 
