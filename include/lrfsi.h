@@ -213,6 +213,25 @@ int lrfsi_medians(int K, const int32_t* sizes_host, int32_t* offsets_host, int32
  * Errors: LRFSI_EINVAL for K < 0, nproc < 1, NULL arrays or negative weights. */
 int lrfsi_partition(int K, const int64_t* weights_host, int nproc, int32_t* first_host);
 
+/* lrfsi_lu_mode: the sparse LU of the Newton steps (Sec. 3.2) and of the
+ * mean-based preconditioners (Sec. 4.2; the paper factors them with a
+ * permuted sparse LU):
+ *   1 (default): nested dissection -- the node grid is bisected recursively
+ *      along vertex lines; every separator is a dense front, fronts of one
+ *      height in the separator tree are factored together (panel LU with
+ *      partial pivoting among the front's fully summed rows, explicit inverse
+ *      of its pivot block, Schur complement by GEMM, extend-add into the
+ *      parent), and a solve is two level-scheduled sweeps of GEMMs;
+ *   0: the slab-ordered block-tridiagonal LU (dense slab blocks, block Thomas).
+ * Applies to handles created (and Newton calls made) after the call.
+ * mode = -1 only queries; *previous (may be NULL) receives the old mode. */
+int lrfsi_lu_mode(int mode, int* previous);
+/* lrfsi_lu_info: host-only analysis of the nested dissection for a problem
+ * (no device work): out8 = {fronts, tree heights, largest separator, largest
+ * boundary, doubles of one factorisation, FP64 flops of one factorisation,
+ * FP64 flops of the slab block LU, doubles of the slab block LU}. */
+int lrfsi_lu_info(const lrfsi_problem* prob, int64_t* out8);
+
 /* lrfsi_newton_median: Newton iteration for K independent problems
  * (Sec. 3.2, Eq. (newton_step_indiv1)), batched: every iteration assembles
  * J(x_k; mu_k, nu_k), R(x_k; mu_k, nu_k), factors all K Jacobians with the

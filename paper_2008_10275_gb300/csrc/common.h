@@ -67,6 +67,11 @@ struct Gate {
 #ifdef __CUDACC__
 __host__ __device__ inline bool gate_open(const Gate& g) { return (!g.a || *g.a) && (!g.b || *g.b); }
 #endif
+// While kernel timing is on (lrfsi_timing), the algorithmic work of a gated
+// descriptor is counted only if its gate is open: the flags are read back
+// (synchronising the stream).  Without timing every descriptor counts.
+bool timing_enabled();
+bool gate_counts(const Gate& g, cudaStream_t s);
 
 // ---- device buffers --------------------------------------------------------
 template <class T>

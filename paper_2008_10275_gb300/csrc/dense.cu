@@ -146,6 +146,7 @@ int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
       double fl = 0, by = 0;
       for (int q = 0; q < cnt; ++q) {
         const GemmDesc<T>& g = gb.d[q];
+        if (!gate_counts(g.gate, s)) continue;
         fl += 2.0 * g.m * g.n * g.k;
         by += sizeof(T) * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != T(0) ? 2.0 : 1.0) * g.m * g.n);
       }
@@ -328,6 +329,7 @@ int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t wor
     {
       double fl = 0, by = 0;
       for (int i = 0; i < cnt; ++i) {
+        if (!gate_counts(gb.d[i].gate, s)) continue;
         // symmetric products: the algorithmic work is the upper triangle
         const bool sym = gb.d[i].A == gb.d[i].B && gb.d[i].p == gb.d[i].q;
         fl += sym ? 1.0 * M * gb.d[i].p * (gb.d[i].p + 1) : 2.0 * M * gb.d[i].p * gb.d[i].q;

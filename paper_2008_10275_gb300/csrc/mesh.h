@@ -1,6 +1,8 @@
 // Mesh, DOF layout and assembly data of the channel-with-flap FSI problem.
 #pragma once
 
+#include <memory>
+
 #include "common.h"
 
 namespace lrfsi {
@@ -37,6 +39,11 @@ struct MeshHost {
 
 }  // namespace lrfsi
 
+namespace lrfsi {
+struct NdSymbolic;
+struct NdDevice;
+}
+
 // The opaque handle.
 struct lrfsi_mesh_s {
   lrfsi::MeshHost h;
@@ -49,6 +56,9 @@ struct lrfsi_mesh_s {
   // [win[2b], win[2b+1]) its nonzeros touch; winmax = the widest window
   lrfsi::DevBuf<int> spmm_win;
   int spmm_winmax = 0;
+  // nested-dissection structure of the sparse LU (built on first use)
+  std::shared_ptr<lrfsi::NdSymbolic> nd;
+  std::shared_ptr<lrfsi::NdDevice> ndd;
 };
 
 namespace lrfsi {

@@ -14,6 +14,7 @@
 
 #include "dense.h"
 #include "mesh.h"
+#include "nd_lu.h"
 #include "sparse_lu.h"
 
 namespace lrfsi {
@@ -39,6 +40,15 @@ static lrfsi_kernel_stat g_stat[LRFSI_NUM_KERNEL_CLASSES];
 static bool g_timing = false;
 struct PendingEv { int cls; cudaEvent_t a, b; };
 static std::vector<PendingEv> g_pending;
+bool timing_enabled() { return g_timing; }
+bool gate_counts(const Gate& g, cudaStream_t s) {
+  if (!g_timing || (!g.a && !g.b)) return true;
+  int v[2] = {1, 1};
+  if (g.a && cudaMemcpyAsync(&v[0], g.a, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return true;
+  if (g.b && cudaMemcpyAsync(&v[1], g.b, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess) return true;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return true;
+  return v[0] && v[1];
+}
 void account(int cls, double flops, double bytes) {
   std::lock_guard<std::mutex> lk(g_stat_mu);
   g_stat[cls].launches += 1;
@@ -469,6 +479,70 @@ extern "C" int lrfsi_residual(lrfsi_mesh_h m, const double* xt, const double* U,
 }
 
 // ---------------------------------------------------------------------------
+// The sparse LU of the Newton steps and preconditioners: nested dissection with
+// dense fronts (default), or the slab-ordered block-tridiagonal LU
+// ---------------------------------------------------------------------------
+namespace lrfsi {
+static std::atomic<int> g_lu_mode{1};  // 0: slab block LU, 1: nested dissection
+
+struct PrecLU {
+  int kind = 1;
+  BlockLU blk;
+  NdLU nd;
+  size_t bytes() const { return blk.bytes() + nd.bytes(); }
+  int alloc(lrfsi_mesh_s* m, int nprob, int ld) {
+    kind = g_lu_mode.load();
+    return kind == 1 ? ndlu_alloc(m, nprob, ld, nd) : blocklu_alloc(m, nprob, blk);
+  }
+  int factor(lrfsi_mesh_s* m, const double* const* J3, const double* a, const double* b, int nprob, cudaStream_t s) {
+    return kind == 1 ? ndlu_factor(m, nd, J3, a, b, nprob, s) : blocklu_factor(m, blk, J3, a, b, nprob, s);
+  }
+  int status(int nprob, std::vector<int>& out, cudaStream_t s) {
+    return kind == 1 ? ndlu_status(nd, nprob, out, s) : blocklu_status(blk, nprob, out, s);
+  }
+  // Y = A^{-1} X (r_q columns, ld); the block LU overwrites X, the ND LU does not
+  int solve(double* const* X, double* const* Y, const int* r, int ld, int nprob, cudaStream_t s,
+            const Gate* gates = nullptr) {
+    if (kind == 1) return ndlu_solve(nd, X, Y, r, ld, nprob, s, gates);
+    return blocklu_solve(blk, X, Y, r, ld, nprob, s, gates);
+  }
+  int max_cols() const { return kind == 1 ? nd.ld : 1 << 30; }
+};
+}  // namespace lrfsi
+
+extern "C" int lrfsi_lu_mode(int mode, int* previous) {
+  using namespace lrfsi;
+  if (mode < -1 || mode > 1) return fail(LRFSI_EINVAL, "lrfsi_lu_mode: mode must be 0, 1 (or -1 to query)");
+  const int old = mode >= 0 ? g_lu_mode.exchange(mode) : g_lu_mode.load();
+  if (previous) *previous = old;
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_lu_info(const lrfsi_problem* prob, int64_t* out8) {
+  using namespace lrfsi;
+  if (!prob || !out8) return fail(LRFSI_EINVAL, "lrfsi_lu_info: null argument");
+  MeshHost h;
+  LRFSI_TRY(build_mesh(*prob, h));
+  NdSymbolic y;
+  LRFSI_TRY(nd_symbolic(h, y));
+  double thomas = 0;
+  for (int sl = 0; sl < h.nslab; ++sl) {
+    const double n = (double)(h.slab_off[sl + 1] - h.slab_off[sl]);
+    const double nn = sl + 1 < h.nslab ? (double)(h.slab_off[sl + 2] - h.slab_off[sl + 1]) : 0.0;
+    thomas += (2.0 / 3.0) * n * n * n + 2.0 * n * n * (nn + n) + 2.0 * nn * nn * n;
+  }
+  out8[0] = (int64_t)y.fr.size();
+  out8[1] = y.heights;
+  out8[2] = y.maxf;
+  out8[3] = y.maxb;
+  out8[4] = (int64_t)(y.ws_doubles + y.inv_doubles);
+  out8[5] = (int64_t)y.factor_flops;
+  out8[6] = (int64_t)thomas;
+  out8[7] = (int64_t)h.nslab * h.nmax * h.nmax * 4;
+  return LRFSI_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Batched Newton iteration for independent problems (median solutions)
 // ---------------------------------------------------------------------------
 extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h,
@@ -497,8 +571,8 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
   LRFSI_CUDA(cudaMemcpyAsync(nu.p, nu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
   k_transpose<<<ceil_div(M * K, 256), 256, 0, s>>>(Xpm, K, (int)M, X.p);  // (K x M) -> (M x K)
   LRFSI_TRY(check_launch("k_transpose"));
-  BlockLU lu;
-  LRFSI_TRY(blocklu_alloc(m, K, lu));
+  PrecLU lu;
+  LRFSI_TRY(lu.alloc(m, K, 1));
   auto norms = [&](const double* Xs, std::vector<double>& out) -> int {
     LRFSI_TRY(launch_residual(m, Xs, K, K, nullptr, mu.p, nu.p, Rb.p, K, s));
     LRFSI_TRY(launch_colnorm2(Rb.p, M, K, K, norm2.p, work.p, work.n, s));
@@ -545,9 +619,17 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
       bs[a] = Rb.p + act[a];
       ys[a] = dX.p + act[a];
     }
-    LRFSI_TRY(blocklu_factor(m, lu, J3p.data(), al.data(), be.data(), na, s, bs.data(), ys.data(), K));
+    if (lu.kind == 1) {
+      LRFSI_TRY(lu.factor(m, J3p.data(), al.data(), be.data(), na, s));
+      std::vector<double*> bx(na);
+      for (int a = 0; a < na; ++a) bx[a] = const_cast<double*>(bs[a]);
+      std::vector<int> one(na, 1);
+      LRFSI_TRY(lu.solve(bx.data(), ys.data(), one.data(), K, na, s));
+    } else {
+      LRFSI_TRY(blocklu_factor(m, lu.blk, J3p.data(), al.data(), be.data(), na, s, bs.data(), ys.data(), K));
+    }
     std::vector<int> lst;
-    LRFSI_TRY(blocklu_status(lu, na, lst, s));
+    LRFSI_TRY(lu.status(na, lst, s));
     for (int a = 0; a < na; ++a)
       if (lst[a] != 0) status = LRFSI_ESINGULAR;
     LRFSI_CUDA(cudaMemcpyAsync(Xold.p, X.p, sizeof(double) * M * K, cudaMemcpyDeviceToDevice, s));
@@ -600,7 +682,7 @@ struct lrfsi_subset_s {
   DevBuf<double> rsc, csc;  // K x M equilibration scales (rows, columns)
   DevBuf<double> cinv;      // K x M reciprocal column scales (allocated on first use)
   DevBuf<float> J3f, USf, Yf, Xf, Vf;  // FP32 operator copies and inner-residual buffers (mixed mode)
-  BlockLU lu;
+  PrecLU lu;
   DevBuf<double> Xcat, Q1, Q2, US, UD, UR, UZ, UB, Ytmp, UC;  // K x M x ld
   DevBuf<double> Vcat, VS, VD, VR, VB, VC;                // mtot x ld
   DevBuf<double> G, G2, T1, T2, swork, sv, frob2, gramwork;
@@ -623,23 +705,23 @@ struct lrfsi_subset_s {
   std::vector<TruncDesc> cgt_host;
   DevBuf<unsigned char> cgws;
   cudaStream_t cap_stream = nullptr;
-  cudaGraph_t cg_graph = nullptr;
-  cudaGraphExec_t cg_exec = nullptr;
-  uint64_t cg_nodes = 0;
+  std::vector<cudaGraphExec_t> cg_exec;  // one graph per phase of the sequence
+  std::vector<uint64_t> cg_nodes;        // kernel nodes per phase graph
   std::vector<double> cg_key;
+  int* live_host = nullptr;              // pinned: the live flags read after a residual
   double* tall(DevBuf<double>& b, int k, int ld) { return b.p + (size_t)k * M * ld; }
   double* vside(DevBuf<double>& b, int k, int ld) { return b.p + (size_t)off[k] * ld; }
   void drop_graph() {
-    if (cg_exec) cudaGraphExecDestroy(cg_exec);
-    if (cg_graph) cudaGraphDestroy(cg_graph);
-    cg_exec = nullptr;
-    cg_graph = nullptr;
-    cg_nodes = 0;
+    for (cudaGraphExec_t e : cg_exec)
+      if (e) cudaGraphExecDestroy(e);
+    cg_exec.clear();
+    cg_nodes.clear();
     cg_key.clear();
   }
   ~lrfsi_subset_s() {
     drop_graph();
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (live_host) cudaFreeHost(live_host);
   }
 };
 
@@ -1035,10 +1117,10 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
     LRFSI_TRY(S->Xf.alloc((size_t)K * M * ldP));
     LRFSI_TRY(S->Vf.alloc((size_t)S->mtot * ldP));
   }
-  LRFSI_TRY(blocklu_alloc(mesh, K, S->lu));
-  LRFSI_TRY(blocklu_factor(mesh, S->lu, J3p.data(), S->mubar.data(), S->nubar.data(), K, s));
+  LRFSI_TRY(S->lu.alloc(mesh, K, ldR));
+  LRFSI_TRY(S->lu.factor(mesh, J3p.data(), S->mubar.data(), S->nubar.data(), K, s));
   std::vector<int> st;
-  LRFSI_TRY(blocklu_status(S->lu, K, st, s));
+  LRFSI_TRY(S->lu.status(K, st, s));
   for (int k = 0; k < K; ++k)
     if (st[k]) return fail(LRFSI_ESINGULAR, "lrfsi_subset_create: zero pivot in a preconditioner LU");
   LRFSI_TRY(residual_bD_norms(mesh, S->rc, S->mu.p, S->nu.p, s));
@@ -1198,7 +1280,7 @@ static int lr_precond(lrfsi_subset_s* S, const std::vector<int>& L, const std::v
   }
   if (!any) return LRFSI_OK;
   LRFSI_TRY(copy_batched(cd, s));
-  return blocklu_solve(S->lu, X2.data(), Y2.data(), r2.data(), ldR, K, s);
+  return S->lu.solve(X2.data(), Y2.data(), r2.data(), ldR, K, s);
 }
 
 // Chebyshev on factors for the subsets in `act`; B given densely in UB.
@@ -1576,7 +1658,7 @@ static int precond_fixed(lrfsi_subset_s* S, cudaStream_t s) {
     cd.push_back(CopyDesc{S->tall(S->UR, k, ldR), ldR, X[k], ldR, M, r[k], 0, nullptr, 1.0, gates[k]});
   }
   LRFSI_TRY(copy_batched(cd, s));
-  return blocklu_solve(S->lu, X.data(), Y.data(), r.data(), ldR, K, s, gates.data());
+  return S->lu.solve(X.data(), Y.data(), r.data(), ldR, K, s, gates.data());
 }
 
 // [A | B] -> Xcat and [a VA | b VB] -> Vcat (Rk columns each) for every subset.
@@ -1598,24 +1680,31 @@ static int concat_fixed(lrfsi_subset_s* S, DevBuf<double>& UA, DevBuf<double>& V
   return copy_batched(cd, s);
 }
 
-// The whole ChebyshevT solve (options o) of the subsets flagged in cgi[CG_ACT]
-// as one launch sequence without host reads.  B dense in UB; result in US/VS
-// (Rk columns, zero beyond cgi[CG_RANK]).
-static int cheb_fixed_enqueue(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaStream_t s) {
+// The phases of the fixed sequence (options o) for the subsets flagged in
+// cgi[CG_ACT]; B dense in UB, result in US/VS (Rk columns, zero beyond
+// cgi[CG_RANK]).  A solve runs
+//   INIT, then per cycle: RES, Z0, and for j = 0 .. iters-1: S, then (j < iters - 1) RES, D_j,
+// and ends early once no subset is live after a RES (the one host read of a step).
+enum { PH_INIT = 0, PH_RES = 1, PH_Z0 = 2, PH_S = 3, PH_D0 = 4 };
+
+static int cheb_phase(lrfsi_subset_s* S, const lrfsi_cheb_options& o, int ph, cudaStream_t s) {
   const int K = S->K, ldR = S->ldR;
   const long M = S->M;
-  LRFSI_CUDA(cudaMemsetAsync(S->US.p, 0, sizeof(double) * (size_t)K * M * ldR, s));
-  LRFSI_CUDA(cudaMemsetAsync(S->VS.p, 0, sizeof(double) * (size_t)S->mtot * ldR, s));
-  for (int k = 0; k < K; ++k)
-    LRFSI_TRY(launch_colnorm2(S->tall(S->UB, k, ldR), M, S->m[k], ldR, S->rc.norm2.p + S->off[k], S->rc.work.p,
-                              S->rc.work.n, s));
-  k_cheb_init<<<1, 32, 0, s>>>(S->rc.norm2.p, S->offm.p, K, S->cgi.p, S->cgd.p);
-  LRFSI_TRY(check_launch("k_cheb_init"));
   const double sigma = o.d / o.c;
-  for (int cyc = 0; cyc < o.cycles; ++cyc) {
-    LRFSI_TRY(residual_fixed(S, o, s));
-    LRFSI_TRY(precond_fixed(S, s));
-    {  // Delta = Z / d
+  switch (ph) {
+    case PH_INIT: {
+      LRFSI_CUDA(cudaMemsetAsync(S->US.p, 0, sizeof(double) * (size_t)K * M * ldR, s));
+      LRFSI_CUDA(cudaMemsetAsync(S->VS.p, 0, sizeof(double) * (size_t)S->mtot * ldR, s));
+      for (int k = 0; k < K; ++k)
+        LRFSI_TRY(launch_colnorm2(S->tall(S->UB, k, ldR), M, S->m[k], ldR, S->rc.norm2.p + S->off[k], S->rc.work.p,
+                                  S->rc.work.n, s));
+      k_cheb_init<<<1, 32, 0, s>>>(S->rc.norm2.p, S->offm.p, K, S->cgi.p, S->cgd.p);
+      return check_launch("k_cheb_init");
+    }
+    case PH_RES:
+      return residual_fixed(S, o, s);
+    case PH_Z0: {  // Z = P^{-1} U_R, Delta = Z / d
+      LRFSI_TRY(precond_fixed(S, s));
       std::vector<CopyDesc> cd;
       for (int k = 0; k < K; ++k) {
         const Gate live = live_gate(S, k);
@@ -1624,22 +1713,21 @@ static int cheb_fixed_enqueue(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cu
         cd.push_back(CopyDesc{S->vside(S->VR, k, ldR), ldR, S->vside(S->VD, k, ldR), ldR, S->m[k], r, 0, nullptr,
                               1.0 / o.d, live});
       }
-      LRFSI_TRY(copy_batched(cd, s));
+      return copy_batched(cd, s);
     }
-    double rho = 1.0 / sigma;
-    for (int j = 0; j < o.iters; ++j) {
-      LRFSI_TRY(concat_fixed(S, S->US, S->VS, 1.0, S->UD, S->VD, 1.0, s));  // S <- T(S + Delta)
-      LRFSI_TRY(trunc_fixed(S, TS_S, s));
-      if (j == o.iters - 1) break;
-      LRFSI_TRY(residual_fixed(S, o, s));
+    case PH_S:  // S <- T(S + Delta)
+      LRFSI_TRY(concat_fixed(S, S->US, S->VS, 1.0, S->UD, S->VD, 1.0, s));
+      return trunc_fixed(S, TS_S, s);
+    default: {  // D_j: Z = P^{-1} U_R, Delta <- T(rho' rho Delta + (2 rho' / c) Z) with the rho of step j
+      const int j = ph - PH_D0;
+      double rho = 1.0 / sigma;
+      for (int i = 0; i < j; ++i) rho = 1.0 / (2.0 * sigma - rho);
+      const double rn = 1.0 / (2.0 * sigma - rho);
       LRFSI_TRY(precond_fixed(S, s));
-      const double rn = 1.0 / (2.0 * sigma - rho);  // Delta <- T(rho' rho Delta + (2 rho' / c) Z)
       LRFSI_TRY(concat_fixed(S, S->UD, S->VD, rn * rho, S->UZ, S->VR, 2.0 * rn / o.c, s));
-      LRFSI_TRY(trunc_fixed(S, TS_D, s));
-      rho = rn;
+      return trunc_fixed(S, TS_D, s);
     }
   }
-  return LRFSI_OK;
 }
 
 // Prepared state of the fixed sequence for these options and buffers: the key
@@ -1670,63 +1758,100 @@ static int fixed_prepare(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaStr
 
 static std::atomic<long long> g_graph_replays{0}, g_graph_captures{0}, g_graph_fallbacks{0};
 
-// ChebyshevT for the subsets in act through the fixed sequence: replayed from
-// the handle's CUDA graph (captured on first use of these options, after one
-// direct run that also sizes the split-K workspace), or launched directly
-// (graph mode 1, or while kernel timing is on).  A subset whose truncation
-// broke down is solved again by cheb_run.
+// ChebyshevT for the subsets in act through the fixed sequence.  Graph mode 2:
+// the first solve with these options runs the phases directly (which also
+// sizes the split-K workspace), then captures every phase once on the handle's
+// stream; later solves replay the phase graphs, one graph launch per phase and
+// one 4-byte-per-subset read of the live flags after each residual (the solve
+// ends when no subset is live).  Mode 1, or kernel timing on: the phases are
+// launched directly.  A subset whose truncation broke down is solved again by
+// cheb_run.
 static int cheb_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std::vector<int>& act,
                       std::vector<int>& rS, std::vector<lrfsi_cheb_stats>& st, cudaStream_t s) {
   const int K = S->K;
+  const int nph = PH_D0 + std::max(o.iters - 1, 0);
   LRFSI_TRY(fixed_prepare(S, o, s));
+  if (!S->live_host) LRFSI_CUDA(cudaMallocHost((void**)&S->live_host, sizeof(int) * CG_NINT * K));
   {
     std::vector<int> a(K, 0);
     for (int k : act) a[k] = 1;
     LRFSI_CUDA(cudaMemcpyAsync(S->cgi.p + CG_ACT * K, a.data(), sizeof(int) * K, cudaMemcpyHostToDevice, s));
   }
   const bool use_graph = g_graph_mode.load() == 2 && !g_timing;
-  if (use_graph && S->cg_exec) {
-    LRFSI_CUDA(cudaGraphLaunch(S->cg_exec, s));
-    count_launch(S->cg_nodes);
-    g_graph_replays += 1;
-  } else {
-    gemm_ws_peak_reset();
-    LRFSI_TRY(cheb_fixed_enqueue(S, o, s));
-    if (use_graph) {  // capture the same sequence on the handle's stream for the next calls
-      const size_t need = std::max<size_t>(gemm_ws_peak(), 256);
-      if (S->cgws.n < need) LRFSI_TRY(S->cgws.alloc(need));
-      if (!S->cap_stream) LRFSI_CUDA(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+  const bool replay = use_graph && (int)S->cg_exec.size() == nph;
+  if (!replay) gemm_ws_peak_reset();
+  auto run = [&](int ph) -> int {
+    if (replay) {
+      LRFSI_CUDA(cudaGraphLaunch(S->cg_exec[ph], s));
+      count_launch(S->cg_nodes[ph]);
+      g_graph_replays += 1;
+      return LRFSI_OK;
+    }
+    return cheb_phase(S, o, ph, s);
+  };
+  auto any_live = [&](bool& any) -> int {
+    LRFSI_CUDA(cudaMemcpyAsync(S->live_host, S->cgi.p + CG_LIVE * K, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    any = false;
+    for (int k = 0; k < K; ++k) any = any || S->live_host[k];
+    return LRFSI_OK;
+  };
+  LRFSI_TRY(run(PH_INIT));
+  bool any = true, done = false;
+  for (int cyc = 0; cyc < o.cycles && !done; ++cyc) {
+    LRFSI_TRY(run(PH_RES));
+    LRFSI_TRY(any_live(any));
+    if (!any) break;
+    LRFSI_TRY(run(PH_Z0));
+    for (int j = 0; j < o.iters; ++j) {
+      LRFSI_TRY(run(PH_S));
+      if (j == o.iters - 1) break;
+      LRFSI_TRY(run(PH_RES));
+      LRFSI_TRY(any_live(any));
+      if (!any) { done = true; break; }
+      LRFSI_TRY(run(PH_D0 + j));
+    }
+  }
+  if (use_graph && !replay) {  // capture every phase for the next solves
+    const size_t need = std::max<size_t>(gemm_ws_peak(), 256);
+    if (S->cgws.n < need) LRFSI_TRY(S->cgws.alloc(need));
+    if (!S->cap_stream) LRFSI_CUDA(cudaStreamCreateWithFlags(&S->cap_stream, cudaStreamNonBlocking));
+    std::vector<cudaGraphExec_t> execs;
+    std::vector<uint64_t> nodes;
+    bool ok = true;
+    gemm_ws_bind(S->cgws.p, S->cgws.n);
+    for (int ph = 0; ph < nph && ok; ++ph) {
       const uint64_t before = g_launches.load();
-      gemm_ws_bind(S->cgws.p, S->cgws.n);
       cudaGraph_t graph = nullptr;
       int st_cap = LRFSI_OK;
       cudaError_t e = cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
-        st_cap = cheb_fixed_enqueue(S, o, S->cap_stream);
+        st_cap = cheb_phase(S, o, ph, S->cap_stream);
         e = cudaStreamEndCapture(S->cap_stream, &graph);
       }
-      gemm_ws_bind(nullptr, 0);
-      const uint64_t nodes = g_launches.load() - before;
-      g_launches -= nodes;  // captured, not launched
-      if (e == cudaSuccess && st_cap == LRFSI_OK && graph) {
-        cudaGraphExec_t exec = nullptr;
-        e = cudaGraphInstantiate(&exec, graph, 0);
-        if (e == cudaSuccess) {
-          S->cg_graph = graph;
-          S->cg_exec = exec;
-          S->cg_nodes = nodes;
-          g_graph_captures += 1;
-        } else {
-          cudaGraphDestroy(graph);
-        }
-      } else if (graph) {
-        cudaGraphDestroy(graph);
+      const uint64_t n = g_launches.load() - before;
+      g_launches -= n;  // captured, not launched
+      cudaGraphExec_t exec = nullptr;
+      if (e == cudaSuccess && st_cap == LRFSI_OK && graph) e = cudaGraphInstantiate(&exec, graph, 0);
+      if (graph) cudaGraphDestroy(graph);
+      if (e != cudaSuccess || st_cap != LRFSI_OK || !exec) {
+        ok = false;
+        if (exec) cudaGraphExecDestroy(exec);
+      } else {
+        execs.push_back(exec);
+        nodes.push_back(n);
       }
-      if (!S->cg_exec) {  // capture failed: keep launching the sequence directly
-        cudaGetLastError();
-        g_graph_fallbacks += 1;
-        g_graph_mode = 1;
-      }
+    }
+    gemm_ws_bind(nullptr, 0);
+    if (ok) {
+      S->cg_exec = execs;
+      S->cg_nodes = nodes;
+      g_graph_captures += 1;
+    } else {  // capture failed: keep launching the phases directly
+      for (cudaGraphExec_t e : execs) cudaGraphExecDestroy(e);
+      cudaGetLastError();
+      g_graph_fallbacks += 1;
+      g_graph_mode = 1;
     }
   }
   std::vector<int> hi((size_t)CG_NINT * K);
@@ -2488,7 +2613,21 @@ extern "C" int lrfsi_precond_apply(lrfsi_subset_h S, const double* X, int ldx, c
     Ys[k] = S->tall(S->Q1, k, ldP);
   }
   LRFSI_TRY(copy_batched(cd, s));
-  LRFSI_TRY(blocklu_solve(S->lu, Xs.data(), Ys.data(), rr.data(), ldP, K, s));
+  {  // in chunks of at most the LU's solve width
+    const int w = S->lu.max_cols();
+    int rmax = 0;
+    for (int k = 0; k < K; ++k) rmax = std::max(rmax, rr[k]);
+    for (int c0 = 0; c0 < rmax; c0 += w) {
+      std::vector<double*> Xc(K), Yc(K);
+      std::vector<int> rc(K);
+      for (int k = 0; k < K; ++k) {
+        Xc[k] = Xs[k] + c0;
+        Yc[k] = Ys[k] + c0;
+        rc[k] = std::max(0, std::min(w, rr[k] - c0));
+      }
+      LRFSI_TRY(S->lu.solve(Xc.data(), Yc.data(), rc.data(), ldP, K, s));
+    }
+  }
   cd.clear();
   for (int k = 0; k < K; ++k)
     cd.push_back(CopyDesc{S->tall(S->Q1, k, ldP), ldP, Y + (size_t)k * M * ldy, ldy, M, rr[k], 0,

@@ -300,6 +300,7 @@ int spmm_batched(const lrfsi_mesh_s* m, const SpmmDesc<T>* d, int n, cudaStream_
       const double nnz = (double)m->h.colidx.size();
       double fl = 0, by = 0;
       for (int q = 0; q < cnt; ++q) {
+        if (!gate_counts(sb.d[q].gate, s)) continue;
         const bool comb = sb.d[q].o[1] < 0;
         fl += nnz * sb.d[q].r * (comb ? 2.0 : 6.0);
         by += nnz * (4.0 + 3.0 * sizeof(T)) + 4.0 * (M + 1) + (double)M * sb.d[q].r * sizeof(T) * (comb ? 2.0 : 4.0);

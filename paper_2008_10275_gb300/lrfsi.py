@@ -104,6 +104,8 @@ def load():
         "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
         "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
         "lrfsi_graph_mode": [i, vp],
+        "lrfsi_lu_mode": [i, vp],
+        "lrfsi_lu_info": [C.POINTER(lrfsi_problem), vp],
         "lrfsi_graph_counters": [vp, i],
         "lrfsi_order_grid": [i, i, vp, vp, i, vp, vp],
         "lrfsi_order_set": [i, vp, vp, vp],
@@ -208,6 +210,24 @@ def graph_mode(mode=-1):
     prev = C.c_int(0)
     _check(load().lrfsi_graph_mode(int(mode), C.byref(prev)))
     return prev.value
+
+
+def lu_mode(mode=-1):
+    """Set the sparse LU (1 nested dissection, 0 slab block LU; -1 queries);
+    returns the previous mode."""
+    prev = C.c_int(0)
+    _check(load().lrfsi_lu_mode(int(mode), C.byref(prev)))
+    return prev.value
+
+
+def lu_info(nx, ny, Lx=2.0, Ly=0.4, flap=(0.6, 0.7, 0.0, 0.2), rho_f=1e3, lam_s=2e6, v_mean=0.2):
+    """Host-only nested-dissection analysis of a mesh (no GPU needed)."""
+    p = lrfsi_problem(nx, ny, Lx, Ly, (C.c_double * 4)(*flap), rho_f, lam_s, v_mean)
+    out = np.zeros(8, np.int64)
+    _check(load().lrfsi_lu_info(C.byref(p), _ptr(out)))
+    keys = ("fronts", "heights", "max_separator", "max_boundary", "factor_doubles", "factor_flops",
+            "slab_lu_flops", "slab_lu_doubles")
+    return dict(zip(keys, (int(v) for v in out)))
 
 
 def graph_counters(reset=False):

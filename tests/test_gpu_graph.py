@@ -109,7 +109,7 @@ def test_modes_match_oracle_and_each_other_uneven_subsets():
         lrfsi.graph_mode(mode)
         res[(mode, rep)] = _solve(sub, lm, sizes, UB, VB, opt, ld)
     gc = lrfsi.graph_counters()
-    assert gc["captures"] == 1 and gc["replays"] == 1 and gc["failures"] == 0, gc
+    assert gc["captures"] == 1 and gc["replays"] > 0 and gc["failures"] == 0, gc
     for q, m in enumerate(sizes):
         So = _oracle(om, perm, mus[q], nus[q], xts[q], c, d, iters=6, cycles=2, tol=1e-13, rank_cap=m)
         scale = np.linalg.norm(So, axis=0).max()
@@ -176,8 +176,8 @@ def test_subset_step_graph_matches_host_sized(precision):
     sizes = [10, 14]
     lm, om, perm, mus, nus, xts = _problem(sizes, seed=23)
     mu, nu = np.concatenate(mus), np.concatenate(nus)
-    K, R = len(sizes), 12
-    opt = lrfsi.cheb_options(0.65, 1.0, iters=6, cycles=2, rank_cap=R, tol=1e-8, eta=0.05, precision=precision)
+    K, R = len(sizes), max(sizes)
+    opt = lrfsi.cheb_options(0.65, 1.0, iters=6, cycles=2, rank_cap=R, tol=1e-10, eta=0.05, precision=precision)
     got = {}
     for mode in (0, 2):
         lrfsi.graph_mode(mode)
