@@ -379,21 +379,34 @@ def main():
                              eta=args.eta)
     opt_gmres = lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=0,
                                    eta=args.eta, solver="gmres")
-    run = algorithm1.Runner(mesh, L, opt, target=args.target, max_outer=args.max_outer, eps_N=EPS_N, device=dev)
+    # subsets solved together: all of them, or groups of W.group (memory of the large mesh)
+    gsz = W.group or K
+    runs = [algorithm1.Runner(mesh, L.part(a, min(a + gsz, K)), opt, target=args.target, max_outer=args.max_outer,
+                              eps_N=EPS_N, device=dev) for a in range(0, K, gsz)]
+    run = runs[0]
     U, V = run.U, run.V
     mus, nus = L.mu, L.nu
 
     def step(mu_h, nu_h, o=None):
-        res = run.step(mu_h, nu_h, o)
+        res_all, off = [], 0
+        for rn in runs:
+            mg = rn.layout.m
+            res_all.append(rn.step(mu_h[off:off + mg], nu_h[off:off + mg], o))
+            off += mg
+        res = dict(xt=torch.cat([r["xt"] for r in res_all]), ranks=np.concatenate([r["ranks"] for r in res_all]),
+                   relres=np.concatenate([r["relres"] for r in res_all]),
+                   outer=np.concatenate([r["outer"] for r in res_all]),
+                   newton_iters=np.concatenate([r["newton_iters"] for r in res_all]),
+                   status=min(r["status"] for r in res_all))
         if dist is not None:
             packed = multi.pack(res["xt"], U, V, res["ranks"], res["relres"], mesh.M, R)
             multi.gather_results(job, first, rank, world, packed, mesh.M, R, dist, device=dev)
         return dict(newton_iters=res["newton_iters"].tolist(), ranks=res["ranks"].tolist(),
                     outer=res["outer"].tolist(), max_relres=float(res["relres"].max()) if m else 0.0,
-                    status=res["status"], xt=res["xt"])
+                    status=res["status"], xt=res["xt"], parts=res_all)
 
     def dense_solution(info):
-        return run.dense(dict(xt=info["xt"], ranks=info["ranks"]))
+        return torch.cat([rn.dense(p) for rn, p in zip(runs, info["parts"])], 1)
 
     def barrier():
         torch.cuda.synchronize()
@@ -405,7 +418,7 @@ def main():
     for _ in range(args.warmup):
         info = step(mus, nus)
     stream = torch.cuda.current_stream()
-    L0 = lrfsi.kernel_launches()
+    L0, H0 = lrfsi.kernel_launches(), lrfsi.host_launches()
     lrfsi.truncation_counters(reset=True)
     barrier()
     with Clocks(local) as clk:
@@ -418,6 +431,7 @@ def main():
         barrier()
     ms = e0.elapsed_time(e1) / args.steps
     launches = (lrfsi.kernel_launches() - L0) / args.steps
+    host_launches = (lrfsi.host_launches() - H0) / args.steps
     trunc_counts = lrfsi.truncation_counters()
     ms = multi.max_over_ranks(ms, dist, dev)
     value = job.m / (ms * 1e-3)
@@ -490,8 +504,9 @@ def main():
         mu_host = np.array(mus, copy=True)
         nu_host = np.array(nus, copy=True)
         step(mu_host, nu_host)
-        Uh = U.cpu()
-        Vh = V.cpu()
+        for rn in runs:
+            Uh = rn.U.cpu()
+            Vh = rn.V.cpu()
     e3.record(stream)
     barrier()
     ms_e2e = e2.elapsed_time(e3) / args.steps
@@ -573,10 +588,11 @@ def main():
             "e2e": {"value": job.m / (ms_e2e * 1e-3), "unit": "params/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
+            "host_launches": int(host_launches),
             "roofline": roof,
             "spmm_gbs": spmm_gbs,
             "cpu_baseline": cpu,
-            "result": {**{k: v for k, v in info.items() if k != "xt"}, "truncation": trunc_counts},
+            "result": {**{k: v for k, v in info.items() if k not in ("xt", "parts")}, "truncation": trunc_counts},
             "mixed": mixed,
             "gmrest": gmres,
         }

@@ -488,6 +488,9 @@ size_t lrfsi_mesh_bytes(lrfsi_mesh_h mesh);
 size_t lrfsi_subset_bytes(lrfsi_subset_h sub);
 
 /* Number of kernels this library has launched in the calling process. */
+/* Launch calls issued by the host since load: a direct kernel launch or a
+ * graph replay counts once (lrfsi_kernel_launches counts the replay's kernels). */
+uint64_t lrfsi_host_launches(void);
 uint64_t lrfsi_kernel_launches(void);
 
 /* Per-kernel-class accounting for roofline reports.  Classes:

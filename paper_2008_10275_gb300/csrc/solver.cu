@@ -23,7 +23,8 @@ namespace lrfsi {
 // errors and launch counting
 // ---------------------------------------------------------------------------
 static thread_local std::string g_err;
-static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_launches{0};       // kernels launched (graph replays add their kernel nodes)
+static std::atomic<uint64_t> g_host_launches{0};  // launch calls issued by the host (a graph replay is one)
 void set_error(const std::string& msg) { g_err = msg; }
 int fail(int code, const std::string& msg) {
   g_err = msg;
@@ -33,7 +34,10 @@ int cuda_fail(cudaError_t e, const char* what) {
   g_err = std::string(what) + ": " + cudaGetErrorString(e);
   return LRFSI_ECUDA;
 }
-void count_launch(uint64_t n) { g_launches += n; }
+void count_launch(uint64_t n) {
+  g_launches += n;
+  g_host_launches += 1;
+}
 
 static std::mutex g_stat_mu;
 static lrfsi_kernel_stat g_stat[LRFSI_NUM_KERNEL_CLASSES];
@@ -276,6 +280,7 @@ int lrfsi_timing(int enable) {
   return LRFSI_OK;
 }
 uint64_t lrfsi_kernel_launches(void) { return g_launches.load(); }
+uint64_t lrfsi_host_launches(void) { return g_host_launches.load(); }
 
 int lrfsi_mesh_create(const lrfsi_problem* prob, lrfsi_mesh_h* out) {
   if (!prob || !out) return fail(LRFSI_EINVAL, "lrfsi_mesh_create: null argument");
@@ -1558,6 +1563,22 @@ static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
   LRFSI_TRY(trunc_qr(K, s, dd3, 0));
   LRFSI_TRY(gemm_grouped<double>(y3.data(), K, s));
   LRFSI_TRY(trunc_svd(hd, K, s, dd, false));
+  if (timing_enabled()) {  // algorithmic work of the small kernels of the live subsets (as truncate_once)
+    std::vector<int> info((size_t)5 * K), live(K);
+    LRFSI_CUDA(cudaMemcpyAsync(info.data(), S->info.p, sizeof(int) * 5 * K, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaMemcpyAsync(live.data(), S->cgi.p + CG_LIVE * K, sizeof(int) * K, cudaMemcpyDeviceToHost, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+    double fl = 0, fj = 0;
+    for (int k = 0; k < K; ++k) {
+      if (!live[k]) continue;
+      const double P = hd[k].p, kk = info[5 * k], mm = hd[k].m;
+      const double n = std::min(kk, mm), L = std::max(kk, mm), sw = std::max(info[5 * k + 3], 1);
+      fl += 2.0 * P * P * P / 3.0 + (info[5 * k + 4] ? 2.0 : 1.0) * (2.0 * kk * kk * kk / 3.0) + kk * kk * kk / 3.0;
+      fj += sw * n * (n - 1) / 2.0 * (6.0 * L + 4.0 * (L + n));
+    }
+    account(KC_TRUNC, fl, 0);
+    account(KC_SVD, fj, 0);
+  }
   LRFSI_TRY(gemm_grouped<double>(t1.data(), K, s));
   LRFSI_TRY(gemm_grouped<double>(uo.data(), K, s));
   return LRFSI_OK;
@@ -1783,7 +1804,7 @@ static int cheb_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std:
   auto run = [&](int ph) -> int {
     if (replay) {
       LRFSI_CUDA(cudaGraphLaunch(S->cg_exec[ph], s));
-      count_launch(S->cg_nodes[ph]);
+      count_launch(S->cg_nodes[ph]);  // one host launch, cg_nodes kernels
       g_graph_replays += 1;
       return LRFSI_OK;
     }
@@ -1821,7 +1842,7 @@ static int cheb_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std:
     bool ok = true;
     gemm_ws_bind(S->cgws.p, S->cgws.n);
     for (int ph = 0; ph < nph && ok; ++ph) {
-      const uint64_t before = g_launches.load();
+      const uint64_t before = g_launches.load(), hbefore = g_host_launches.load();
       cudaGraph_t graph = nullptr;
       int st_cap = LRFSI_OK;
       cudaError_t e = cudaStreamBeginCapture(S->cap_stream, cudaStreamCaptureModeThreadLocal);
@@ -1831,6 +1852,7 @@ static int cheb_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std:
       }
       const uint64_t n = g_launches.load() - before;
       g_launches -= n;  // captured, not launched
+      g_host_launches -= g_host_launches.load() - hbefore;
       cudaGraphExec_t exec = nullptr;
       if (e == cudaSuccess && st_cap == LRFSI_OK && graph) e = cudaGraphInstantiate(&exec, graph, 0);
       if (graph) cudaGraphDestroy(graph);

@@ -32,6 +32,7 @@ class Workload:
     n_random: int = 0
     subset_sizes: tuple | None = None  # explicit uneven subset sizes (batched workload)
     rank_caps: tuple | None = None
+    group: int | None = None           # subsets solved together on one GPU (memory), None = all
 
 
 def _lin(lo_hi, n):
@@ -56,7 +57,7 @@ WORKLOADS = {
     "batched": Workload("channel80x16_random1000_16uneven", 80, 16, K=16, seed=0, n_random=1000,
                         subset_sizes=uneven_sizes(), rank_caps=tuple(int(round(60 - 40 * j / 15)) for j in range(16))),
     "large": Workload("channel320x64_2500", 320, 64, _lin(MU_RANGE, 50), _lin(NU_RANGE, 50),
-                      K=25, rank_cap=80),
+                      K=25, rank_cap=80, group=5),
     "learned": Workload("channel80x16_learned2000", 80, 16, seed=1, n_random=2000, K=20, rank_cap=40),
 }
 

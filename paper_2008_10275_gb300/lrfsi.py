@@ -119,6 +119,7 @@ def load():
         f.restype = C.c_int
     lib.lrfsi_last_error.restype = C.c_char_p
     lib.lrfsi_kernel_launches.restype = C.c_uint64
+    lib.lrfsi_host_launches.restype = C.c_uint64
     lib.lrfsi_mesh_bytes.restype = C.c_size_t
     lib.lrfsi_mesh_bytes.argtypes = [vp]
     lib.lrfsi_subset_bytes.restype = C.c_size_t
@@ -239,6 +240,10 @@ def graph_counters(reset=False):
 
 def kernel_launches():
     return int(load().lrfsi_kernel_launches())
+
+
+def host_launches():
+    return int(load().lrfsi_host_launches())
 
 
 class Mesh:

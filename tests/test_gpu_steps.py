@@ -167,7 +167,8 @@ def test_truncate_matches_svd_truncation():
     tol = 3e-2   # tails: ||s_{>=3}|| = 0.0333 > tol ||s|| = 0.0316 >= ||s_{>=4}|| = 0.0105
     lib = lrfsi.load()
     import ctypes as C
-    st = lib.lrfsi_truncate(sub.h, _dev(X.reshape(-1)).data_ptr(), ld, _dev(V).data_ptr(), ld,
+    Xd, Vd = _dev(X.reshape(-1)), _dev(V)   # kept alive across the call
+    st = lib.lrfsi_truncate(sub.h, Xd.data_ptr(), ld, Vd.data_ptr(), ld,
                             np.array(p, np.int32).ctypes.data, tol, np.array(caps, np.int32).ctypes.data,
                             U.data_ptr(), ldo, Vo.data_ptr(), ldo, ranks.ctypes.data,
                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
