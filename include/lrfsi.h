@@ -121,6 +121,26 @@ int lrfsi_residual_batch(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m,
                          const double* mu_dev, const double* nu_dev, double* R_dev, int ldr,
                          double* norm2_dev, lrfsi_stream_t stream);
 
+/* ---- the four-parameter problem (Sec. 4.4): mu_s, nu_f, lambda_s, rho_f vary;
+ * Eq. (matrix_fourpars1) with the reference values set to 0:
+ *   J = J0 + mu Jmu' + (nu rho) Jnurho' + lam Jlam' + rho Jrho',  R likewise.
+ * The mesh's own rho_f and lambda_s are not used by these entry points. */
+
+/* lrfsi_assemble_affine4: the five affine pieces at x as two interleaved
+ * triples on the CSR pattern: J3a = (J0, Jmu', Jnurho'), J3b = (Jlam', Jrho', 0)
+ * (nnz x 3 each), and R3a = (R0, Rmu, Rnurho), R3b = (Rlam, Rrho, 0) (M x 3
+ * row-major each); any output may be NULL.  The lambda and rho pieces are the
+ * differences of assemblies at (rho_f, lambda_s) = (0, 0), (1, 0), (0, 1), exact
+ * wherever no other term shares the entry and within rounding elsewhere.
+ * Synchronizes the stream (temporaries). */
+int lrfsi_assemble_affine4(lrfsi_mesh_h mesh, const double* x_dev, double* J3a_dev, double* J3b_dev,
+                           double* R3a_dev, double* R3b_dev, lrfsi_stream_t stream);
+/* lrfsi_residual_batch4: R(X_i; mu_i, nu_i, lam_i, rho_i) for m columns (as
+ * lrfsi_residual_batch with lam_dev, rho_dev per column; R_dev required). */
+int lrfsi_residual_batch4(lrfsi_mesh_h mesh, const double* X_dev, int ldx, int m, const double* mu_dev,
+                          const double* nu_dev, const double* lam_dev, const double* rho_dev, double* R_dev,
+                          int ldr, double* norm2_dev, lrfsi_stream_t stream);
+
 /* lrfsi_residual_batch_noalloc: the same residual block and column norms as
  * lrfsi_residual_batch, computed without allocating device memory.  (No
  * counterpart in the paper: an interface for callers that cannot let a library
@@ -247,6 +267,12 @@ int lrfsi_newton_median(lrfsi_mesh_h mesh, int K, double* X_dev, const double* m
                         const double* nu_host, double eps, int max_it, int* iters_host,
                         double* res_host, lrfsi_stream_t stream);
 
+/* lrfsi_newton_median4: lrfsi_newton_median for the four-parameter problem
+ * (Sec. 4.4): lam_host, rho_host (K) give lambda_s and rho_f per problem. */
+int lrfsi_newton_median4(lrfsi_mesh_h mesh, int K, double* X_dev, const double* mu_host, const double* nu_host,
+                         const double* lam_host, const double* rho_host, double eps, int max_it, int* iters_host,
+                         double* res_host, lrfsi_stream_t stream);
+
 /* Options of the low-rank solvers (truncated Chebyshev iteration and truncated GMRES). */
 typedef struct {
   double c, d;        /* half-width and centre of the spectrum of P^{-1} A (Sec. 5.1.1);
@@ -297,6 +323,16 @@ typedef struct lrfsi_subset_s* lrfsi_subset_h;
 int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt_dev, const double* mu_host,
                         const double* nu_host, const int* m_host, const int* rank_cap_host,
                         lrfsi_subset_h* out, lrfsi_stream_t stream);
+/* lrfsi_subset_create4: subsets of the four-parameter problem (Sec. 4.4,
+ * Eq. (matrix_fourpars1)): operators J0, Jmu', Jnurho', Jlam', Jrho' at xt_k,
+ * the mean-based preconditioner at the midpoints of the ranges of mu, nu rho,
+ * lambda and rho, and in every solve the five-term operator
+ *   J0 S + Jmu' S D_mu + Jnurho' S D_{nu rho} + Jlam' S D_lam + Jrho' S D_rho
+ * with the rank-5 right-hand side B^{mu,nu,lambda,rho}.  lam_host, rho_host:
+ * sum m_k values.  ChebyshevT only (GMREST returns LRFSI_EINVAL). */
+int lrfsi_subset_create4(lrfsi_mesh_h mesh, int K, const double* xt_dev, const double* mu_host,
+                         const double* nu_host, const double* lam_host, const double* rho_host, const int* m_host,
+                         const int* rank_cap_host, lrfsi_subset_h* out, lrfsi_stream_t stream);
 int lrfsi_subset_destroy(lrfsi_subset_h sub);
 
 /* lrfsi_chebyshevT: solve F_k(S_k) = B_k for every subset on the factors

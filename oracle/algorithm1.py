@@ -180,3 +180,53 @@ def algorithm1_4(mesh, mus, nus, lams, rhos, opt: Options):
             x_prev = xt
         start += size
     return X, info
+
+
+def split_subset(start, size):
+    """The two halves of the contiguous subset [start, start + size): the
+    clustering rule of Eq. (clustering1) with K = 2 applied to the subset
+    (floor(size / 2), then the remainder)."""
+    a = size // 2
+    return [(start, a), (start + a, size - a)]
+
+
+def algorithm1_adaptive(mesh, mus, nus, opt: Options, target, min_size=1, max_levels=3):
+    """Algorithm 1 with adaptively refined subsets (reading of Sec. 5,
+    "Alternative ways to cluster the parameter set": more, smaller subsets
+    lower the largest relative residual, and the paper leaves adaptive
+    refinement open).  Start from the K subsets of ``opt``; after the subset
+    step, every subset whose largest relative residual (Sec. 5.1.2) is above
+    ``target`` and that has at least 2 * min_size parameters is split into its
+    two halves, each solved again from its own upper median (Newton from b_D);
+    at most ``max_levels`` refinements.  No chord corrections here.
+    Returns (X, subsets) with subsets = [(start, size, median position)]."""
+    mus, nus = np.asarray(mus, float), np.asarray(nus, float)
+    m = len(mus)
+    X = np.zeros((mesh.M, m))
+    subsets, start = [], 0
+    for size in params.cluster_sizes(m, opt.K):
+        subsets.append((start, size))
+        start += size
+
+    def solve(start, size):
+        idx = np.arange(start, start + size)
+        med = start + params.upper_median_position(size)
+        xt, _, _ = newton.newton(mesh, mus[med], nus[med], eps=opt.eps_N)
+        X[:, idx] = subset_step(mesh, xt, mus[idx], nus[idx], opt)
+        return relative_residuals(mesh, X[:, idx], mus[idx], nus[idx]).max()
+
+    worst = {s: solve(*s) for s in subsets}
+    for _ in range(max_levels):
+        refine = [s for s in subsets if worst[s] > target and s[1] >= 2 * min_size]
+        if not refine:
+            break
+        nxt = []
+        for s in subsets:
+            if s in refine:
+                for h in split_subset(*s):
+                    worst[h] = solve(*h)
+                    nxt.append(h)
+            else:
+                nxt.append(s)
+        subsets = nxt
+    return X, [(a, n, a + params.upper_median_position(n)) for a, n in subsets]

@@ -151,3 +151,81 @@ class Runner:
             Uk, Vk = self.factors(k, result["ranks"])
             cols.append(result["xt"][k][:, None] + Uk @ Vk.T)
         return self.torch.cat(cols, 1)
+
+
+def solve_subsets(mesh, mu, nu, subsets, caps, opt, target, max_outer, eps_N=1e-6, device="cuda:0"):
+    """Algorithm 1 on the given contiguous subsets [(start, size)] of the
+    ordered parameters (mu, nu) in one batch: the upper-median Newton
+    solutions, the subset operators and preconditioners, and the subset step
+    with at most ``max_outer`` chord corrections.  Returns one dict per subset:
+    start, size, xt, U (M x r), V (size x r), relres."""
+    import torch
+    sizes = np.array([n for _, n in subsets], np.int32)
+    mu_s = np.concatenate([mu[a:a + n] for a, n in subsets])
+    nu_s = np.concatenate([nu[a:a + n] for a, n in subsets])
+    offs, med = lrfsi.lrfsi_medians(sizes)
+    K = len(subsets)
+    bD = torch.tensor(mesh.dirichlet(), dtype=torch.float64, device=device)
+    X = bD.repeat(K, 1)
+    lrfsi.lrfsi_newton_median(mesh, X, mu_s[med[:K]], nu_s[med[:K]], eps_N, 30)
+    R = int(max(caps))
+    sub = lrfsi.Subsets(mesh, X, mu_s, nu_s, sizes, caps)
+    U = torch.zeros(K * mesh.M * R, dtype=torch.float64, device=device)
+    V = torch.zeros(int(sizes.sum()) * R, dtype=torch.float64, device=device)
+    try:
+        ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, target, max_outer, U, R, V, R)
+    finally:
+        sub.close()
+    out = []
+    for k, (a, n) in enumerate(subsets):
+        r = int(ranks[k])
+        o = int(offs[k])
+        out.append(dict(start=a, size=n, xt=X[k].clone(), U=U[k * mesh.M * R:(k + 1) * mesh.M * R].view(mesh.M, R)[:, :r],
+                        V=V[o * R:(o + n) * R].view(n, R)[:, :r], relres=rel[o:o + n].copy(),
+                        outer=int(outer[k])))
+    return out
+
+
+def adaptive(mesh, layout, opt, target, min_size=1, max_levels=3, max_outer=40, eps_N=1e-6, device="cuda:0"):
+    """Algorithm 1 with adaptively refined subsets (reading of Sec. 5,
+    "Alternative ways to cluster the parameter set"): after the subset step,
+    every subset whose largest relative residual is above ``target`` and that
+    has at least 2 * min_size parameters is split into its two halves
+    (Eq. (clustering1) with K = 2 on the subset), each solved again from its
+    own upper median, for at most ``max_levels`` levels; subsets still above
+    the target then take chord corrections (at most ``max_outer``).  Returns
+    the list of per-subset results (see solve_subsets), in parameter order."""
+    cap = int(layout.caps.max())
+    subs = [(int(a), int(n)) for a, n in zip(layout.offsets, layout.sizes)]
+
+    def batch(items, outer):
+        res = []
+        for i in range(0, len(items), 32):   # at most 32 subsets per handle
+            chunk = items[i:i + 32]
+            res += solve_subsets(mesh, layout.mu, layout.nu, chunk, [min(cap, n) for _, n in chunk], opt, target,
+                                 outer, eps_N, device)
+        return res
+
+    res = {(r["start"], r["size"]): r for r in batch(subs, 0)}
+    for _ in range(max_levels):
+        refine = [s for s in subs if res[s]["relres"].max() > target and s[1] >= 2 * min_size]
+        if not refine:
+            break
+        halves = []
+        for s in refine:
+            a, n = s
+            halves += [(a, n // 2), (a + n // 2, n - n // 2)]
+        for r in batch(halves, 0):
+            res[(r["start"], r["size"])] = r
+        nxt = []
+        for s in subs:
+            if s in refine:
+                nxt += [(s[0], s[1] // 2), (s[0] + s[1] // 2, s[1] - s[1] // 2)]
+            else:
+                nxt.append(s)
+        subs = nxt
+    late = [s for s in subs if res[s]["relres"].max() > target]
+    if late and max_outer > 0:
+        for r in batch(late, max_outer):
+            res[(r["start"], r["size"])] = r
+    return [res[s] for s in subs]

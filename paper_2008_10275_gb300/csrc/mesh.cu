@@ -359,7 +359,9 @@ __global__ void __launch_bounds__(kResCols) k_residual(Tables T, const int* __re
                                                        const char* __restrict__ cell_solid, const double* __restrict__ X,
                                                        int ldx, int ncol, const double* __restrict__ c_rest,
                                                        const double* __restrict__ c_mu, const double* __restrict__ c_nu,
-                                                       double* __restrict__ R, int ldr) {
+                                                       const double* __restrict__ c_rho,
+                                                       const double* __restrict__ c_lam, double* __restrict__ R,
+                                                       int ldr) {
   const int ci = blockIdx.x;
   const int j = blockIdx.y * kResCols + threadIdx.x;
   if (ci >= ncells || j >= ncol) return;
@@ -368,6 +370,8 @@ __global__ void __launch_bounds__(kResCols) k_residual(Tables T, const int* __re
   const int* row = cell_row + (size_t)c * kLoc;
   const bool solid = cell_solid[c];
   const double cr = c_rest ? c_rest[j] : 1.0, cm = c_mu ? c_mu[j] : 0.0, cn = c_nu ? c_nu[j] : 0.0;
+  // rho_f and lambda_s of this column (Sec. 4.4 varies them per parameter)
+  const double rho = c_rho ? c_rho[j] : T.rho, lam = c_lam ? c_lam[j] : T.lam;
   // ldx == 0: every column reads the same state
   const size_t xs = ldx ? (size_t)ldx : 1, xj = ldx ? (size_t)j : 0;
   double xl[kLoc];
@@ -390,14 +394,14 @@ __global__ void __launch_bounds__(kResCols) k_residual(Tables T, const int* __re
     const double w = T.w[q];
     if (!solid) {
       // momentum: rho (v.grad)v . phi - p div phi + nu rho (grad v + grad v^T) : grad phi
-      const double c0 = T.rho * (v0 * g00 + v1 * g01), c1 = T.rho * (v0 * g10 + v1 * g11);
+      const double c0 = rho * (v0 * g00 + v1 * g01), c1 = rho * (v0 * g10 + v1 * g11);
       const double s00 = 2 * g00, s01 = g01 + g10, s11 = 2 * g11;
       const double dv = g00 + g11;
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const double n = T.N[a][q], dx = T.dN[a][q][0], dy = T.dN[a][q][1];
-        acc[4 * a + 0] += w * (cr * (c0 * n - p * dx) + cn * T.rho * (s00 * dx + s01 * dy));
-        acc[4 * a + 1] += w * (cr * (c1 * n - p * dy) + cn * T.rho * (s01 * dx + s11 * dy));
+        acc[4 * a + 0] += w * (cr * (c0 * n - p * dx) + cn * rho * (s00 * dx + s01 * dy));
+        acc[4 * a + 1] += w * (cr * (c1 * n - p * dy) + cn * rho * (s01 * dx + s11 * dy));
         acc[4 * a + 2] += w * cr * (u00 * dx + u01 * dy);  // extension
         acc[4 * a + 3] += w * cr * (u10 * dx + u11 * dy);
       }
@@ -412,8 +416,8 @@ __global__ void __launch_bounds__(kResCols) k_residual(Tables T, const int* __re
 #pragma unroll
       for (int a = 0; a < 9; ++a) {
         const double dx = T.dN[a][q][0], dy = T.dN[a][q][1];
-        acc[4 * a + 0] += w * (cm * (e00 * dx + e01 * dy) + cr * T.lam * tr * dx);
-        acc[4 * a + 1] += w * (cm * (e01 * dx + e11 * dy) + cr * T.lam * tr * dy);
+        acc[4 * a + 0] += w * (cm * (e00 * dx + e01 * dy) + cr * lam * tr * dx);
+        acc[4 * a + 1] += w * (cm * (e01 * dx + e11 * dy) + cr * lam * tr * dy);
       }
     }
   }
@@ -468,8 +472,12 @@ static Tables tables_of(const lrfsi_mesh_s* m) {
   return T;
 }
 
-int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s) {
-  const Tables T = tables_of(m);
+int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s, const double* rho_lam) {
+  Tables T = tables_of(m);
+  if (rho_lam) {
+    T.rho = rho_lam[0];
+    T.lam = rho_lam[1];
+  }
   LRFSI_CUDA(cudaMemsetAsync(J3, 0, sizeof(double) * 3 * m->h.colidx.size(), s));
   for (int col = 0; col < 4; ++col) {
     int n = m->h.color_start[col + 1] - m->h.color_start[col];
@@ -487,7 +495,8 @@ int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s
 }
 
 int launch_residual(lrfsi_mesh_s* m, const double* X, int ldx, int ncol, const double* c_rest,
-                    const double* c_mu, const double* c_nu, double* R, int ldr, cudaStream_t s) {
+                    const double* c_mu, const double* c_nu, double* R, int ldr, cudaStream_t s, const double* c_rho,
+                    const double* c_lam) {
   if (ncol <= 0) return LRFSI_OK;
   const Tables T = tables_of(m);
   LRFSI_CUDA(cudaMemsetAsync(R, 0, sizeof(double) * (size_t)m->h.M * ldr, s));
@@ -496,7 +505,8 @@ int launch_residual(lrfsi_mesh_s* m, const double* X, int ldx, int ncol, const d
     if (n == 0) continue;
     dim3 grid(n, ceil_div(ncol, kResCols));
     k_residual<<<grid, kResCols, 0, s>>>(T, m->color_cells.p + m->h.color_start[col], n, m->cell_dof.p,
-                                         m->cell_row.p, m->cell_solid.p, X, ldx, ncol, c_rest, c_mu, c_nu, R, ldr);
+                                         m->cell_row.p, m->cell_solid.p, X, ldx, ncol, c_rest, c_mu, c_nu, c_rho, c_lam,
+                                         R, ldr);
     LRFSI_TRY(check_launch("k_residual"));
   }
   long ni = (long)m->h.ident_rows.size();

@@ -73,10 +73,15 @@ int build_mesh(const lrfsi_problem& prob, MeshHost& h);
 // state), output R (M x ldr).  Column j combines the terms as
 //   c_rest[j] * (everything but the mu- and nu-terms, incl. x - b_D rows)
 //   + c_mu[j] * <G + G^T + G^T G, grad phi>_S + c_nu[j] * rho_f <grad v + grad v^T, grad phi>_F
+// c_rho, c_lam (per column, optional): rho_f and lambda_s of each column in
+// place of the mesh's constants (the four-parameter problem, Sec. 4.4); they
+// scale the convection and viscous terms (rho) and the lambda term.
 int launch_residual(lrfsi_mesh_s* m, const double* X, int ldx, int ncol, const double* c_rest,
-                    const double* c_mu, const double* c_nu, double* R, int ldr, cudaStream_t s);
-// Affine Jacobian values (nnz x 3 interleaved) at state x.
-int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s);
+                    const double* c_mu, const double* c_nu, double* R, int ldr, cudaStream_t s,
+                    const double* c_rho = nullptr, const double* c_lam = nullptr);
+// Affine Jacobian values (nnz x 3 interleaved) at state x; rho_lam (host,
+// optional): {rho_f, lambda_s} in place of the mesh's constants.
+int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s, const double* rho_lam = nullptr);
 // Column squared norms of an M x ncol row-major block (ldr), accumulated in
 // fixed order: out[j] = sum_i R[i, j]^2.  work: >= ceil(M/rows_per_block) * ncol doubles.
 // Doubles of workspace launch_colnorm2 needs for M rows and ncol columns (one

@@ -395,6 +395,109 @@ int lrfsi_assemble_affine(lrfsi_mesh_h m, const double* x, double* J3, double* R
   return LRFSI_OK;
 }
 
+}  // extern "C"
+
+namespace lrfsi {
+// J3a = (J0, Jmu', Jnurho'), J3b = (Jlam', Jrho', 0) from three assemblies at
+// (rho_f, lambda_s) = (0, 0), (1, 0), (0, 1):  the rho and lambda parts are the
+// differences of the J0 slots (they are zero at every entry the other terms fill).
+__global__ void k_five_ops(const double* __restrict__ J00, const double* __restrict__ J10,
+                           const double* __restrict__ J01, long nnz, double* __restrict__ Ja, double* __restrict__ Jb) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  const double j0 = J00[3 * e];
+  Ja[3 * e] = j0;
+  Ja[3 * e + 1] = J00[3 * e + 1];
+  Ja[3 * e + 2] = J10[3 * e + 2];
+  Jb[3 * e] = J01[3 * e] - j0;
+  Jb[3 * e + 1] = J10[3 * e] - j0;
+  Jb[3 * e + 2] = 0.0;
+}
+// R5 (M x 5: R0, Rmu, Rnurho, R0 + Rlam, R0 + Rrho) -> R3a = (R0, Rmu, Rnurho), R3b = (Rlam, Rrho, 0)
+__global__ void k_five_res(const double* __restrict__ R5, long M, double* __restrict__ Ra, double* __restrict__ Rb) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= M) return;
+  const double* r = R5 + 5 * i;
+  Ra[3 * i] = r[0];
+  Ra[3 * i + 1] = r[1];
+  Ra[3 * i + 2] = r[2];
+  Rb[3 * i] = r[3] - r[0];
+  Rb[3 * i + 1] = r[4] - r[0];
+  Rb[3 * i + 2] = 0.0;
+}
+
+// The five affine pieces of the four-parameter problem at x (Sec. 4.4,
+// Eq. (matrix_fourpars1) with the reference values set to 0):
+//   J = J0 + mu Jmu' + (nu rho) Jnurho' + lam Jlam' + rho Jrho',  R likewise.
+// J3a, J3b: nnz x 3 each (or NULL); R3a, R3b: M x 3 each (or NULL).
+static int assemble_five(lrfsi_mesh_s* m, const double* x, double* J3a, double* J3b, double* R3a, double* R3b,
+                         cudaStream_t s) {
+  const long nnz = (long)m->h.colidx.size(), M = m->h.M;
+  if (J3a || J3b) {
+    DevBuf<double> J00, J10, J01;
+    LRFSI_TRY(J00.alloc((size_t)3 * nnz));
+    LRFSI_TRY(J10.alloc((size_t)3 * nnz));
+    LRFSI_TRY(J01.alloc((size_t)3 * nnz));
+    const double rl00[2] = {0.0, 0.0}, rl10[2] = {1.0, 0.0}, rl01[2] = {0.0, 1.0};
+    LRFSI_TRY(launch_jacobian(m, x, J00.p, s, rl00));
+    LRFSI_TRY(launch_jacobian(m, x, J10.p, s, rl10));
+    LRFSI_TRY(launch_jacobian(m, x, J01.p, s, rl01));
+    DevBuf<double> ta, tb;
+    double* Ja = J3a;
+    double* Jb = J3b;
+    if (!Ja) { LRFSI_TRY(ta.alloc((size_t)3 * nnz)); Ja = ta.p; }
+    if (!Jb) { LRFSI_TRY(tb.alloc((size_t)3 * nnz)); Jb = tb.p; }
+    k_five_ops<<<ceil_div(nnz, 256), 256, 0, s>>>(J00.p, J10.p, J01.p, nnz, Ja, Jb);
+    LRFSI_TRY(check_launch("k_five_ops"));
+    LRFSI_CUDA(cudaStreamSynchronize(s));  // temporaries are freed on return
+  }
+  if (R3a || R3b) {
+    // columns (rest, mu, nu, rho, lam):
+    //   R0 (1,0,0,0,0), Rmu (0,1,0,0,0), Rnurho (0,0,1,1,0), R0 + Rlam (1,0,0,0,1), R0 + Rrho (1,0,0,1,0)
+    static const double h_coef[25] = {1, 0, 0, 1, 1,   0, 1, 0, 0, 0,   0, 0, 1, 0, 0,
+                                      0, 0, 1, 0, 1,   0, 0, 0, 1, 0};
+    DevBuf<double> coef, R5, ta, tb;
+    LRFSI_TRY(coef.alloc(25));
+    LRFSI_TRY(R5.alloc((size_t)5 * M));
+    LRFSI_CUDA(cudaMemcpyAsync(coef.p, h_coef, sizeof(h_coef), cudaMemcpyHostToDevice, s));
+    LRFSI_TRY(launch_residual(m, x, 0, 5, coef.p, coef.p + 5, coef.p + 10, R5.p, 5, s, coef.p + 15, coef.p + 20));
+    double* Ra = R3a;
+    double* Rb = R3b;
+    if (!Ra) { LRFSI_TRY(ta.alloc((size_t)3 * M)); Ra = ta.p; }
+    if (!Rb) { LRFSI_TRY(tb.alloc((size_t)3 * M)); Rb = tb.p; }
+    k_five_res<<<ceil_div(M, 256), 256, 0, s>>>(R5.p, M, Ra, Rb);
+    LRFSI_TRY(check_launch("k_five_res"));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+  }
+  return LRFSI_OK;
+}
+}  // namespace lrfsi
+
+extern "C" {
+
+int lrfsi_assemble_affine4(lrfsi_mesh_h m, const double* x, double* J3a, double* J3b, double* R3a, double* R3b,
+                           lrfsi_stream_t stream) {
+  if (!m || !x) return fail(LRFSI_EINVAL, "lrfsi_assemble_affine4: null argument");
+  return assemble_five(m, x, J3a, J3b, R3a, R3b, (cudaStream_t)stream);
+}
+
+int lrfsi_residual_batch4(lrfsi_mesh_h m, const double* X, int ldx, int ncol, const double* mu, const double* nu,
+                          const double* lam, const double* rho, double* R, int ldr, double* norm2,
+                          lrfsi_stream_t stream) {
+  if (!m || !X || !mu || !nu || !lam || !rho || !R || ncol < 0 || ldx < ncol || ldr < ncol)
+    return fail(LRFSI_EINVAL, "lrfsi_residual_batch4: bad argument");
+  if (ncol == 0) return LRFSI_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  LRFSI_TRY(launch_residual(m, X, ldx, ncol, nullptr, mu, nu, R, ldr, s, rho, lam));
+  if (norm2) {
+    DevBuf<double> work;
+    LRFSI_TRY(work.alloc(colnorm_work_len(m->h.M, ncol)));
+    LRFSI_TRY(launch_colnorm2(R, m->h.M, ncol, ldr, norm2, work.p, work.n, s));
+    LRFSI_CUDA(cudaStreamSynchronize(s));
+  }
+  return LRFSI_OK;
+}
+
 int lrfsi_residual_batch(lrfsi_mesh_h m, const double* X, int ldx, int ncol, const double* mu, const double* nu,
                          double* R, int ldr, double* norm2, lrfsi_stream_t stream) {
   if (!m || !X || !mu || !nu || ncol < 0 || ldx < ncol) return fail(LRFSI_EINVAL, "lrfsi_residual_batch: bad argument");
@@ -443,8 +546,9 @@ struct ResidualCtx {
 };
 
 // ||R(b_D; mu, nu)||^2 per column (denominator of the relative residual)
-static int residual_bD_norms(lrfsi_mesh_s* m, ResidualCtx& c, const double* mu, const double* nu, cudaStream_t s) {
-  LRFSI_TRY(launch_residual(m, m->bD.p, 0, c.ncol, nullptr, mu, nu, c.R.p, c.ncol, s));
+static int residual_bD_norms(lrfsi_mesh_s* m, ResidualCtx& c, const double* mu, const double* nu, cudaStream_t s,
+                             const double* rho = nullptr, const double* lam = nullptr) {
+  LRFSI_TRY(launch_residual(m, m->bD.p, 0, c.ncol, nullptr, mu, nu, c.R.p, c.ncol, s, rho, lam));
   return launch_colnorm2(c.R.p, m->h.M, c.ncol, c.ncol, c.norm2_bD.p, c.work.p, c.work.n, s);
 }
 
@@ -550,12 +654,16 @@ extern "C" int lrfsi_lu_info(const lrfsi_problem* prob, int64_t* out8) {
 // ---------------------------------------------------------------------------
 // Batched Newton iteration for independent problems (median solutions)
 // ---------------------------------------------------------------------------
-extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h,
-                                   double eps, int max_it, int* iters_h, double* res_h, lrfsi_stream_t stream) {
+// lam_h, rho_h (host, K each, optional): lambda_s and rho_f per problem (the
+// four-parameter problem, Sec. 4.4) in place of the mesh's constants.
+static int newton_impl(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h, const double* lam_h,
+                       const double* rho_h, double eps, int max_it, int* iters_h, double* res_h,
+                       lrfsi_stream_t stream) {
   if (!m || !Xpm || !mu_h || !nu_h || K < 1 || K > kMaxGemmDescs || max_it < 0)
     return fail(LRFSI_EINVAL, "lrfsi_newton_median: bad argument (1 <= K <= 32)");
   for (int k = 0; k < K; ++k)
-    if (!std::isfinite(mu_h[k]) || !std::isfinite(nu_h[k]))
+    if (!std::isfinite(mu_h[k]) || !std::isfinite(nu_h[k]) || (lam_h && !std::isfinite(lam_h[k])) ||
+        (rho_h && !std::isfinite(rho_h[k])))
       return fail(LRFSI_EINVAL, "lrfsi_newton_median: parameters must be finite");
   cudaStream_t s = (cudaStream_t)stream;
   const long M = m->h.M;
@@ -574,12 +682,19 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
   LRFSI_TRY(work.alloc((size_t)ceil_div(M, 256) * K));
   LRFSI_CUDA(cudaMemcpyAsync(mu.p, mu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
   LRFSI_CUDA(cudaMemcpyAsync(nu.p, nu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  DevBuf<double> lam, rho;
+  if (lam_h && rho_h) {
+    LRFSI_TRY(lam.alloc(K));
+    LRFSI_TRY(rho.alloc(K));
+    LRFSI_CUDA(cudaMemcpyAsync(lam.p, lam_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+    LRFSI_CUDA(cudaMemcpyAsync(rho.p, rho_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  }
   k_transpose<<<ceil_div(M * K, 256), 256, 0, s>>>(Xpm, K, (int)M, X.p);  // (K x M) -> (M x K)
   LRFSI_TRY(check_launch("k_transpose"));
   PrecLU lu;
   LRFSI_TRY(lu.alloc(m, K, 1));
   auto norms = [&](const double* Xs, std::vector<double>& out) -> int {
-    LRFSI_TRY(launch_residual(m, Xs, K, K, nullptr, mu.p, nu.p, Rb.p, K, s));
+    LRFSI_TRY(launch_residual(m, Xs, K, K, nullptr, mu.p, nu.p, Rb.p, K, s, rho.p, lam.p));
     LRFSI_TRY(launch_colnorm2(Rb.p, M, K, K, norm2.p, work.p, work.n, s));
     out.resize(K);
     LRFSI_CUDA(cudaMemcpyAsync(out.data(), norm2.p, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
@@ -597,14 +712,15 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
       if (!(r[k] <= eps)) act.push_back(k);
     if (act.empty()) break;
     // residual at the current iterate (Rb holds it for every column after norms())
-    LRFSI_TRY(launch_residual(m, X.p, K, K, nullptr, mu.p, nu.p, Rb.p, K, s));
+    LRFSI_TRY(launch_residual(m, X.p, K, K, nullptr, mu.p, nu.p, Rb.p, K, s, rho.p, lam.p));
     std::vector<const double*> J3p;
     std::vector<double> al, be;
     for (int k : act) {
       k_gather_col<<<ceil_div(M, 256), 256, 0, s>>>(X.p, M, K, k, xcol.p);
       LRFSI_TRY(check_launch("k_gather_col"));
       double* Jk = J3.p + (size_t)3 * nnz * J3p.size();
-      LRFSI_TRY(launch_jacobian(m, xcol.p, Jk, s));
+      const double rl[2] = {rho_h ? rho_h[k] : 0.0, lam_h ? lam_h[k] : 0.0};
+      LRFSI_TRY(launch_jacobian(m, xcol.p, Jk, s, (lam_h && rho_h) ? rl : nullptr));
       J3p.push_back(Jk);
       al.push_back(mu_h[k]);
       be.push_back(nu_h[k]);
@@ -673,6 +789,18 @@ extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const dou
   return LRFSI_OK;
 }
 
+extern "C" int lrfsi_newton_median(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h,
+                                   double eps, int max_it, int* iters_h, double* res_h, lrfsi_stream_t stream) {
+  return newton_impl(m, K, Xpm, mu_h, nu_h, nullptr, nullptr, eps, max_it, iters_h, res_h, stream);
+}
+
+extern "C" int lrfsi_newton_median4(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h,
+                                    const double* lam_h, const double* rho_h, double eps, int max_it, int* iters_h,
+                                    double* res_h, lrfsi_stream_t stream) {
+  if (!lam_h || !rho_h) return fail(LRFSI_EINVAL, "lrfsi_newton_median4: null lambda_s / rho_f");
+  return newton_impl(m, K, Xpm, mu_h, nu_h, lam_h, rho_h, eps, max_it, iters_h, res_h, stream);
+}
+
 // ---------------------------------------------------------------------------
 // Subsets
 // ---------------------------------------------------------------------------
@@ -684,6 +812,16 @@ struct lrfsi_subset_s {
   int mtot = 0, mmax = 0, Rmax = 0, ldP = 0, ldR = 0;
   std::vector<double> mu_h, nu_h, mubar, nubar;
   DevBuf<double> mu, nu, xt, J3, R3;
+  // four-parameter problem (Sec. 4.4): nu holds the affine coefficient nu rho;
+  // nu_raw, lam, rho the parameters themselves (for the nonlinear residuals);
+  // J3x = (Jlam', Jrho', 0) and R3x = (Rlam, Rrho, 0) per subset
+  bool four = false;
+  std::vector<double> lambar, rhobar;
+  DevBuf<double> nu_raw, lam, rho, J3x, R3x;
+  DevBuf<float> J3xf;
+  const double* nu_res() const { return four ? nu_raw.p : nu.p; }
+  const double* rho_res() const { return four ? rho.p : nullptr; }
+  const double* lam_res() const { return four ? lam.p : nullptr; }
   DevBuf<double> rsc, csc;  // K x M equilibration scales (rows, columns)
   DevBuf<double> cinv;      // K x M reciprocal column scales (allocated on first use)
   DevBuf<float> J3f, USf, Yf, Xf, Vf;  // FP32 operator copies and inner-residual buffers (mixed mode)
@@ -1010,8 +1148,8 @@ static int subset_alloc_ws(lrfsi_subset_s* S, cudaStream_t s) {
   const int K = S->K;
   const long M = S->M;
   // largest concatenation: residual [B | J0 U | Jmu U | Jnu U] with rank(B) <= max(R, m)
-  S->ldR = std::max(S->Rmax, S->mmax);
-  S->ldP = S->ldR + 3 * S->Rmax + 4;
+  S->ldR = std::max(std::max(S->Rmax, S->mmax), S->four ? 5 : 3);
+  S->ldP = S->ldR + (S->four ? 6 : 3) * S->Rmax + 4;
   const int ldP = S->ldP, ldR = S->ldR;
   for (DevBuf<double>* b : {&S->Xcat, &S->Q1, &S->Q2}) LRFSI_TRY(b->alloc((size_t)K * M * ldP));
   for (DevBuf<double>* b : {&S->US, &S->UD, &S->UR, &S->UZ, &S->UB, &S->Ytmp, &S->UC})
@@ -1033,8 +1171,22 @@ static int subset_alloc_ws(lrfsi_subset_s* S, cudaStream_t s) {
 }
 }  // namespace lrfsi
 
-extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
-                                   const int* m_h, const int* cap_h, lrfsi_subset_h* out, lrfsi_stream_t stream) {
+namespace lrfsi {
+// J0 slot of P's values for the four-parameter preconditioner:
+// Jeff = (J0 + lam_bar Jlam' + rho_bar Jrho', Jmu', Jnurho')
+__global__ void k_four_precond(const double* __restrict__ Ja, const double* __restrict__ Jb, long nnz, double lb,
+                               double rb, double* __restrict__ Je) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  Je[3 * e] = Ja[3 * e] + lb * Jb[3 * e] + rb * Jb[3 * e + 1];
+  Je[3 * e + 1] = Ja[3 * e + 1];
+  Je[3 * e + 2] = Ja[3 * e + 2];
+}
+}  // namespace lrfsi
+
+static int subset_create_impl(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
+                              const double* lam_h, const double* rho_h, const int* m_h, const int* cap_h,
+                              lrfsi_subset_h* out, lrfsi_stream_t stream) {
   if (!mesh || !xt || !mu_h || !nu_h || !m_h || !cap_h || !out || K < 1 || K > kMaxGemmDescs)
     return fail(LRFSI_EINVAL, "lrfsi_subset_create: bad argument (1 <= K <= 32)");
   *out = nullptr;
@@ -1057,13 +1209,24 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
     S->Rmax = std::max(S->Rmax, S->cap[k]);
   }
   for (int i = 0; i < S->mtot; ++i)
-    if (!std::isfinite(mu_h[i]) || !std::isfinite(nu_h[i]))
+    if (!std::isfinite(mu_h[i]) || !std::isfinite(nu_h[i]) || (lam_h && !std::isfinite(lam_h[i])) ||
+        (rho_h && !std::isfinite(rho_h[i])))
       return fail(LRFSI_EINVAL, "lrfsi_subset_create: parameters must be finite");
+  S->four = lam_h && rho_h;
   LRFSI_TRY(subset_alloc_ws(S, s));
   const long nnz = (long)mesh->h.colidx.size();
   const int ldP = S->ldP, ldR = S->ldR;
   S->mu_h.assign(mu_h, mu_h + S->mtot);
   S->nu_h.assign(nu_h, nu_h + S->mtot);
+  if (S->four) {  // the affine coefficient of A2 is nu rho
+    std::vector<double> lam_v(lam_h, lam_h + S->mtot), rho_v(rho_h, rho_h + S->mtot);
+    LRFSI_TRY(S->nu_raw.upload(S->nu_h, s));
+    LRFSI_TRY(S->lam.upload(lam_v, s));
+    LRFSI_TRY(S->rho.upload(rho_v, s));
+    for (int i = 0; i < S->mtot; ++i) S->nu_h[i] *= rho_h[i];
+    LRFSI_TRY(S->J3x.alloc((size_t)K * 3 * nnz));
+    LRFSI_TRY(S->R3x.alloc((size_t)K * 3 * M));
+  }
   LRFSI_TRY(S->mu.upload(S->mu_h, s));
   LRFSI_TRY(S->nu.upload(S->nu_h, s));
   LRFSI_TRY(S->xt.alloc((size_t)K * M));
@@ -1075,7 +1238,19 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
   for (int k = 0; k < K; ++k) {
     double* Jk = S->J3.p + (size_t)k * 3 * nnz;
     J3p[k] = Jk;
-    LRFSI_TRY(lrfsi_assemble_affine(mesh, S->xt.p + (size_t)k * M, Jk, S->R3.p + (size_t)k * 3 * M, stream));
+    if (S->four) {
+      LRFSI_TRY(assemble_five(mesh, S->xt.p + (size_t)k * M, Jk, S->J3x.p + (size_t)k * 3 * nnz,
+                              S->R3.p + (size_t)k * 3 * M, S->R3x.p + (size_t)k * 3 * M, s));
+      double llo = 1e300, lhi = -1e300, rlo = 1e300, rhi = -1e300;
+      for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) {
+        llo = std::min(llo, lam_h[i]); lhi = std::max(lhi, lam_h[i]);
+        rlo = std::min(rlo, rho_h[i]); rhi = std::max(rhi, rho_h[i]);
+      }
+      S->lambar.push_back(0.5 * (llo + lhi));
+      S->rhobar.push_back(0.5 * (rlo + rhi));
+    } else {
+      LRFSI_TRY(lrfsi_assemble_affine(mesh, S->xt.p + (size_t)k * M, Jk, S->R3.p + (size_t)k * 3 * M, stream));
+    }
     double mlo = 1e300, mhi = -1e300, nlo = 1e300, nhi = -1e300;
     for (int i = S->off[k]; i < S->off[k] + S->m[k]; ++i) {
       mlo = std::min(mlo, S->mu_h[i]); mhi = std::max(mhi, S->mu_h[i]);
@@ -1088,11 +1263,21 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
   // truncation run on diag(r) F(diag(c) S~) = diag(r) B
   LRFSI_TRY(S->rsc.alloc((size_t)K * M));
   LRFSI_TRY(S->csc.alloc((size_t)K * M));
+  DevBuf<double> Jeff;  // four parameters: P's values as one (J0, Jmu', Jnurho') triple per subset
+  if (S->four) {
+    LRFSI_TRY(Jeff.alloc((size_t)K * 3 * nnz));
+    for (int k = 0; k < K; ++k) {
+      k_four_precond<<<ceil_div(nnz, 256), 256, 0, s>>>(S->J3.p + (size_t)k * 3 * nnz, S->J3x.p + (size_t)k * 3 * nnz,
+                                                         nnz, S->lambar[k], S->rhobar[k], Jeff.p + (size_t)k * 3 * nnz);
+      LRFSI_TRY(check_launch("k_four_precond"));
+      J3p[k] = Jeff.p + (size_t)k * 3 * nnz;
+    }
+  }
   {
     DevBuf<unsigned long long> cmax;
     LRFSI_TRY(cmax.alloc(M));
     for (int k = 0; k < K; ++k) {
-      double* Jk = S->J3.p + (size_t)k * 3 * nnz;
+      double* Jk = const_cast<double*>(J3p[k]);
       double* rk = S->rsc.p + (size_t)k * M;
       double* ck = S->csc.p + (size_t)k * M;
       k_equil_rows<<<ceil_div(M, 256), 256, 0, s>>>(Jk, mesh->rowptr.p, M, S->mubar[k], S->nubar[k], rk);
@@ -1105,6 +1290,14 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
       LRFSI_TRY(check_launch("k_equil_cols"));
       k_scale_vals<<<ceil_div(M, 256), 256, 0, s>>>(Jk, mesh->rowptr.p, mesh->colidx.p, M, rk, ck);
       LRFSI_TRY(check_launch("k_scale_vals"));
+      if (S->four) {  // the operators themselves
+        k_scale_vals<<<ceil_div(M, 256), 256, 0, s>>>(S->J3.p + (size_t)k * 3 * nnz, mesh->rowptr.p, mesh->colidx.p, M,
+                                                       rk, ck);
+        LRFSI_TRY(check_launch("k_scale_vals"));
+        k_scale_vals<<<ceil_div(M, 256), 256, 0, s>>>(S->J3x.p + (size_t)k * 3 * nnz, mesh->rowptr.p, mesh->colidx.p,
+                                                       M, rk, ck);
+        LRFSI_TRY(check_launch("k_scale_vals"));
+      }
     }
     LRFSI_CUDA(cudaStreamSynchronize(s));
   }
@@ -1115,6 +1308,12 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
     for (int k = 0; k < K; ++k)
       cv.push_back(ConvDesc{S->J3.p + (size_t)k * 3 * nnz, 0, S->J3f.p + (size_t)k * 3 * nnz, 0, 3 * nnz, 1, nullptr,
                             1.0});
+    if (S->four) {
+      LRFSI_TRY(S->J3xf.alloc((size_t)K * 3 * nnz));
+      for (int k = 0; k < K; ++k)
+        cv.push_back(ConvDesc{S->J3x.p + (size_t)k * 3 * nnz, 0, S->J3xf.p + (size_t)k * 3 * nnz, 0, 3 * nnz, 1,
+                              nullptr, 1.0});
+    }
     for (auto& c : cv) { c.lds = 1; c.ldd = 1; }
     LRFSI_TRY((convert_batched<double, float>(cv, s)));
     LRFSI_TRY(S->USf.alloc((size_t)K * M * ldR));
@@ -1128,10 +1327,22 @@ extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, c
   LRFSI_TRY(S->lu.status(K, st, s));
   for (int k = 0; k < K; ++k)
     if (st[k]) return fail(LRFSI_ESINGULAR, "lrfsi_subset_create: zero pivot in a preconditioner LU");
-  LRFSI_TRY(residual_bD_norms(mesh, S->rc, S->mu.p, S->nu.p, s));
+  LRFSI_TRY(residual_bD_norms(mesh, S->rc, S->mu.p, S->nu_res(), s, S->rho_res(), S->lam_res()));
   LRFSI_CUDA(cudaStreamSynchronize(s));
   *out = guard.release();
   return LRFSI_OK;
+}
+
+extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
+                                   const int* m_h, const int* cap_h, lrfsi_subset_h* out, lrfsi_stream_t stream) {
+  return subset_create_impl(mesh, K, xt, mu_h, nu_h, nullptr, nullptr, m_h, cap_h, out, stream);
+}
+
+extern "C" int lrfsi_subset_create4(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
+                                    const double* lam_h, const double* rho_h, const int* m_h, const int* cap_h,
+                                    lrfsi_subset_h* out, lrfsi_stream_t stream) {
+  if (!lam_h || !rho_h) return fail(LRFSI_EINVAL, "lrfsi_subset_create4: null lambda_s / rho_f");
+  return subset_create_impl(mesh, K, xt, mu_h, nu_h, lam_h, rho_h, m_h, cap_h, out, stream);
 }
 
 namespace lrfsi {
@@ -1195,8 +1406,17 @@ static int lr_residual(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std
       d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
       d.a1 = d.a2 = 0.0;
       sd.push_back(d);
-      gm.push_back(GemmDesc<double>{(int)M, m, 3 * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0,
-                                    1.0});
+      if (S->four) {  // + Jlam' S D_lam + Jrho' S D_rho (Sec. 4.4)
+        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + 3 * r, ldP, m, r, 0, S->lam.p + S->off[k], 1.0});
+        cd.push_back(CopyDesc{S->vside(S->VS, k, ldR), ldR, Vc + 4 * r, ldP, m, r, 0, S->rho.p + S->off[k], 1.0});
+        SpmmDesc<double> d2 = d;
+        d2.J3 = S->J3x.p + (size_t)k * 3 * nnz;
+        d2.o[0] = 3 * r; d2.o[1] = 4 * r; d2.o[2] = 5 * r;
+        d2.sc[2] = 0.0;
+        sd.push_back(d2);
+      }
+      gm.push_back(GemmDesc<double>{(int)M, m, (S->four ? 5 : 3) * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X,
+                                    ldP, 1, -1.0, 1.0});
     }
     cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0});
     p[k] = m;
@@ -1214,18 +1434,20 @@ static int lr_residual(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std
     std::vector<SpmmDesc<float>> sdf;
     std::vector<GemmDesc<float>> gmf;
     for (size_t q = 0; q < sd.size(); ++q) {
+      if (S->four && sd[q].o[0] != 0) continue;  // the second operator triple is added below
       // subset of this SpMM descriptor
       int k = -1;
       for (int kk : L)
         if (S->tall(S->US, kk, ldR) == sd[q].U) k = kk;
       const int r = rS[k], m = S->m[k];
+      const int kc = (S->four ? 5 : 3) * r;
       float* Uf = S->USf.p + (size_t)k * M * ldR;
       float* Yf = S->Yf.p + (size_t)k * M * ldP;
       float* Xf = S->Xf.p + (size_t)k * M * ldP;
       float* Vf = S->Vf.p + (size_t)S->off[k] * ldP;
       c1.push_back(ConvDesc{S->tall(S->US, k, ldR), ldR, Uf, ldR, M, r, nullptr, 1.0});
       c1.push_back(ConvDesc{S->tall(S->Xcat, k, ldP), ldP, Xf, ldP, M, m, nullptr, 1.0});
-      c1.push_back(ConvDesc{S->vside(S->Vcat, k, ldP), ldP, Vf, ldP, m, 3 * r, nullptr, 1.0});
+      c1.push_back(ConvDesc{S->vside(S->Vcat, k, ldP), ldP, Vf, ldP, m, kc, nullptr, 1.0});
       SpmmDesc<float> d;
       d.J3 = S->J3f.p + (size_t)k * 3 * nnz;
       d.U = Uf; d.ldu = ldR; d.r = r; d.Y = Yf; d.ldy = ldP;
@@ -1233,7 +1455,14 @@ static int lr_residual(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std
       d.sc[0] = d.sc[1] = d.sc[2] = 1.0f;
       d.a1 = d.a2 = 0.0f;
       sdf.push_back(d);
-      gmf.push_back(GemmDesc<float>{(int)M, m, 3 * r, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f});
+      if (S->four) {
+        SpmmDesc<float> d2 = d;
+        d2.J3 = S->J3xf.p + (size_t)k * 3 * nnz;
+        d2.o[0] = 3 * r; d2.o[1] = 4 * r; d2.o[2] = 5 * r;
+        d2.sc[2] = 0.0f;
+        sdf.push_back(d2);
+      }
+      gmf.push_back(GemmDesc<float>{(int)M, m, kc, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f});
       c2.push_back(ConvDesc{Xf, ldP, S->tall(S->Xcat, k, ldP), ldP, M, m, nullptr, 1.0});
     }
     LRFSI_TRY((convert_batched<double, float>(c1, s)));
@@ -1609,6 +1838,11 @@ static int residual_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaSt
     cd.push_back(CopyDesc{VS, ldR, Vc + r, ldP, m, r, 0, mu, 1.0, live});
     cd.push_back(CopyDesc{VS, ldR, Vc + 2 * r, ldP, m, r, 0, nu, 1.0, live});
     cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0, live});
+    const int kc = (S->four ? 5 : 3) * r;
+    if (S->four) {  // + Jlam' S D_lam + Jrho' S D_rho (Sec. 4.4)
+      cd.push_back(CopyDesc{VS, ldR, Vc + 3 * r, ldP, m, r, 0, S->lam.p + S->off[k], 1.0, live});
+      cd.push_back(CopyDesc{VS, ldR, Vc + 4 * r, ldP, m, r, 0, S->rho.p + S->off[k], 1.0, live});
+    }
     if (o.precision == 0) {
       SpmmDesc<double> d;
       d.J3 = S->J3.p + (size_t)k * 3 * nnz;
@@ -1622,7 +1856,14 @@ static int residual_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaSt
       d.a1 = d.a2 = 0.0;
       d.gate = live;
       sd.push_back(d);
-      GemmDesc<double> g{(int)M, m, 3 * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0, 1.0};
+      if (S->four) {
+        SpmmDesc<double> d2 = d;
+        d2.J3 = S->J3x.p + (size_t)k * 3 * nnz;
+        d2.o[0] = 3 * r; d2.o[1] = 4 * r; d2.o[2] = 5 * r;
+        d2.sc[2] = 0.0;
+        sd.push_back(d2);
+      }
+      GemmDesc<double> g{(int)M, m, kc, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0, 1.0};
       g.gate = live;
       gm.push_back(g);
     } else {  // B - F(S) with an FP32 SpMM and GEMM, widened to FP64 for the truncation
@@ -1632,7 +1873,7 @@ static int residual_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaSt
       float* Vf = S->Vf.p + (size_t)S->off[k] * ldP;
       c1.push_back(ConvDesc{S->tall(S->US, k, ldR), ldR, Uf, ldR, M, r, nullptr, 1.0, live});
       c1.push_back(ConvDesc{X, ldP, Xf, ldP, M, m, nullptr, 1.0, live});
-      c1.push_back(ConvDesc{Vc, ldP, Vf, ldP, m, 3 * r, nullptr, 1.0, live});
+      c1.push_back(ConvDesc{Vc, ldP, Vf, ldP, m, kc, nullptr, 1.0, live});
       SpmmDesc<float> d;
       d.J3 = S->J3f.p + (size_t)k * 3 * nnz;
       d.U = Uf; d.ldu = ldR; d.r = r; d.Y = Yf; d.ldy = ldP;
@@ -1641,7 +1882,14 @@ static int residual_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaSt
       d.a1 = d.a2 = 0.0f;
       d.gate = live;
       sdf.push_back(d);
-      GemmDesc<float> g{(int)M, m, 3 * r, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f};
+      if (S->four) {
+        SpmmDesc<float> d2 = d;
+        d2.J3 = S->J3xf.p + (size_t)k * 3 * nnz;
+        d2.o[0] = 3 * r; d2.o[1] = 4 * r; d2.o[2] = 5 * r;
+        d2.sc[2] = 0.0f;
+        sdf.push_back(d2);
+      }
+      GemmDesc<float> g{(int)M, m, kc, Yf, ldP, 1, Vf, 1, ldP, Xf, ldP, 1, -1.0f, 1.0f};
       g.gate = live;
       gmf.push_back(g);
       c2.push_back(ConvDesc{Xf, ldP, X, ldP, M, m, nullptr, 1.0, live});
@@ -2240,6 +2488,7 @@ static int gmres_run(lrfsi_subset_s* S, const lrfsi_cheb_options& o, std::vector
 // takes the concatenation width (GMREST: Krylov basis, widened buffers).
 static int solver_prepare(lrfsi_subset_s* S, const lrfsi_cheb_options& o) {
   if (o.solver != 1) return LRFSI_OK;
+  if (S->four) return fail(LRFSI_EINVAL, "GMREST is not available for four-parameter subsets (use ChebyshevT)");
   LRFSI_TRY(gmres_alloc(S, o.iters));
   return widen_concat(S, (o.iters + 1) * S->Rmax);
 }
@@ -2387,7 +2636,8 @@ static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, dou
                                                               S->xt.p + (size_t)k * M, S->csc.p + (size_t)k * M, M);
       LRFSI_TRY(check_launch("k_affine_cols"));
     }
-    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->rc.R.p, S->mtot, s));
+    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu_res(), S->rc.R.p, S->mtot, s,
+                              S->rho_res(), S->lam_res()));
     LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
     std::vector<double> a(S->mtot), b(S->mtot);
     LRFSI_CUDA(cudaMemcpyAsync(a.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
@@ -2464,9 +2714,20 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
     cd.push_back(CopyDesc{nullptr, 0, vb + 2, ldR, S->m[k], 1, 1, S->nu.p + S->off[k], -1.0});
     gb.push_back(GemmDesc<double>{(int)M, S->m[k], 3, S->R3.p + (size_t)k * 3 * M, 3, 1, vb, 1, ldR,
                                   S->tall(S->UB, k, ldR), ldR, 1, 1.0, 0.0});
+    if (S->four) {  // B^{mu,nu,lambda,rho}: -(... + Rlam lam^T + Rrho rho^T) (Sec. 4.4)
+      cd.push_back(CopyDesc{nullptr, 0, vb + 3, ldR, S->m[k], 1, 1, S->lam.p + S->off[k], -1.0});
+      cd.push_back(CopyDesc{nullptr, 0, vb + 4, ldR, S->m[k], 1, 1, S->rho.p + S->off[k], -1.0});
+    }
   }
   LRFSI_TRY(copy_batched(cd, s));
   LRFSI_TRY(gemm_grouped<double>(gb.data(), (int)gb.size(), s));
+  if (S->four) {
+    std::vector<GemmDesc<double>> g2;
+    for (int k = 0; k < K; ++k)
+      g2.push_back(GemmDesc<double>{(int)M, S->m[k], 2, S->R3x.p + (size_t)k * 3 * M, 3, 1, S->vside(S->VB, k, ldR) + 3,
+                                    1, ldR, S->tall(S->UB, k, ldR), ldR, 1, 1.0, 1.0});
+    LRFSI_TRY(gemm_grouped<double>(g2.data(), (int)g2.size(), s));
+  }
   cd.clear();
   for (int k = 0; k < K; ++k)
     cd.push_back(CopyDesc{S->tall(S->UB, k, ldR), ldR, S->tall(S->UB, k, ldR), ldR, M, S->m[k], 0,
@@ -2564,7 +2825,8 @@ extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options
                                                               S->xt.p + (size_t)k * M, S->csc.p + (size_t)k * M, M);
       LRFSI_TRY(check_launch("k_affine_cols"));
     }
-    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->rc.R.p, S->mtot, s));
+    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu_res(), S->rc.R.p, S->mtot, s,
+                              S->rho_res(), S->lam_res()));
     LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
     std::vector<double> a(S->mtot), b(S->mtot);
     LRFSI_CUDA(cudaMemcpyAsync(a.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
@@ -2575,7 +2837,8 @@ extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options
                                                               S->xt.p + (size_t)k * M, S->csc.p + (size_t)k * M, M);
       LRFSI_TRY(check_launch("k_affine_cols"));
     }
-    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->rc.R.p, S->mtot, s));
+    LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu_res(), S->rc.R.p, S->mtot, s,
+                              S->rho_res(), S->lam_res()));
     LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
     LRFSI_CUDA(cudaMemcpyAsync(b.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
     LRFSI_CUDA(cudaStreamSynchronize(s));

@@ -104,6 +104,10 @@ def load():
         "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
         "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
         "lrfsi_graph_mode": [i, vp],
+        "lrfsi_assemble_affine4": [vp, vp, vp, vp, vp, vp, vp],
+        "lrfsi_residual_batch4": [vp, vp, i, i, vp, vp, vp, vp, vp, i, vp, vp],
+        "lrfsi_newton_median4": [vp, i, vp, vp, vp, vp, vp, d, i, vp, vp, vp],
+        "lrfsi_subset_create4": [vp, i, vp, vp, vp, vp, vp, vp, vp, C.POINTER(vp), vp],
         "lrfsi_lu_mode": [i, vp],
         "lrfsi_lu_info": [C.POINTER(lrfsi_problem), vp],
         "lrfsi_graph_counters": [vp, i],
@@ -328,6 +332,27 @@ def lrfsi_newton_median(mesh, X, mu, nu, eps, max_it, stream=None, allow_noconv=
     return it, res, st
 
 
+def lrfsi_newton_median4(mesh, X, mu, nu, lam, rho, eps, max_it, stream=None, allow_noconv=False):
+    """Four-parameter median Newton (Sec. 4.4); X: K x M device tensor."""
+    K = len(mu)
+    a = [np.ascontiguousarray(v, np.float64) for v in (mu, nu, lam, rho)]
+    it = np.zeros(K, np.int32); res = np.zeros(K)
+    st = load().lrfsi_newton_median4(mesh.h, K, _ptr(X), *[_ptr(v) for v in a], eps, max_it, _ptr(it), _ptr(res),
+                                     _stream(stream))
+    _check(st, (ENOCONV,) if allow_noconv else ())
+    return it, res, st
+
+
+def lrfsi_assemble_affine4(mesh, x, J3a=None, J3b=None, R3a=None, R3b=None, stream=None):
+    _check(load().lrfsi_assemble_affine4(mesh.h, _ptr(x), _ptr(J3a), _ptr(J3b), _ptr(R3a), _ptr(R3b),
+                                         _stream(stream)))
+
+
+def lrfsi_residual_batch4(mesh, X, ldx, m, mu, nu, lam, rho, R, ldr, norm2=None, stream=None):
+    _check(load().lrfsi_residual_batch4(mesh.h, _ptr(X), ldx, m, _ptr(mu), _ptr(nu), _ptr(lam), _ptr(rho), _ptr(R),
+                                        ldr, _ptr(norm2), _stream(stream)))
+
+
 SOLVERS = {"chebyshev": 0, "gmres": 1}
 
 
@@ -337,9 +362,10 @@ def cheb_options(c, d, iters=6, cycles=2, rank_cap=20, tol=1e-8, eta=0.0, precis
 
 
 class Subsets:
-    """K subsets sharing one mesh (lrfsi_subset_create)."""
+    """K subsets sharing one mesh (lrfsi_subset_create; with lam and rho the
+    four-parameter problem, lrfsi_subset_create4)."""
 
-    def __init__(self, mesh, xt, mu, nu, sizes, caps, stream=None):
+    def __init__(self, mesh, xt, mu, nu, sizes, caps, stream=None, lam=None, rho=None):
         self.mesh = mesh
         self.K = len(sizes)
         self.mu = np.ascontiguousarray(mu, np.float64)
@@ -348,8 +374,15 @@ class Subsets:
         self.caps = np.ascontiguousarray(caps, np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
         self.h = C.c_void_p()
-        _check(load().lrfsi_subset_create(mesh.h, self.K, _ptr(xt), _ptr(self.mu), _ptr(self.nu), _ptr(self.sizes),
-                                          _ptr(self.caps), C.byref(self.h), _stream(stream)))
+        if lam is not None:
+            self.lam = np.ascontiguousarray(lam, np.float64)
+            self.rho = np.ascontiguousarray(rho, np.float64)
+            _check(load().lrfsi_subset_create4(mesh.h, self.K, _ptr(xt), _ptr(self.mu), _ptr(self.nu), _ptr(self.lam),
+                                               _ptr(self.rho), _ptr(self.sizes), _ptr(self.caps), C.byref(self.h),
+                                               _stream(stream)))
+        else:
+            _check(load().lrfsi_subset_create(mesh.h, self.K, _ptr(xt), _ptr(self.mu), _ptr(self.nu),
+                                              _ptr(self.sizes), _ptr(self.caps), C.byref(self.h), _stream(stream)))
 
     def close(self):
         if self.h:

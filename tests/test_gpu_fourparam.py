@@ -1,0 +1,155 @@
+"""The four-parameter problem on the GPU (Sec. 4.4, Eq. (matrix_fourpars1):
+mu_s, nu_f, lambda_s, rho_f vary) against the oracle, through the C ABI.
+
+* lrfsi_assemble_affine4: the five operators and the five residual pieces vs
+  fsi.affine_jacobian4 / affine_residual4 (1e-12 of each piece's max-norm;
+  the lambda and rho pieces are differences of assemblies, so the bound is
+  taken against the largest entry of J0 or R0 where they share entries).
+* lrfsi_residual_batch4 vs fsi.residual4 per column (1e-12).
+* lrfsi_newton_median4 vs newton.newton4 (1e-9).
+* The subset step of a four-parameter subset: ChebyshevT with tol 1e-13 and
+  rank cap m_k vs the oracle's five-term ChebyshevT (1e-10 per column), and
+  with corrections to 1e-8 the oracle's residual4 of the GPU's columns.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import algorithm1, fsi, lowrank, newton, params  # noqa: E402
+from paper_2008_10275_gb300 import build, inputs, lrfsi  # noqa: E402
+from tests.gpu_common import lib_csr, perm_lib_to_oracle, rel_max  # noqa: E402
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    build.build()
+    lrfsi.load()
+
+
+def _dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device=DEV)
+
+
+@pytest.fixture(scope="module")
+def meshes():
+    lm = lrfsi.Mesh(20, 4)
+    om = fsi.Mesh(fsi.Problem(20, 4))
+    return lm, om, perm_lib_to_oracle(lm, om)
+
+
+def test_five_operators_and_residual_pieces(meshes):
+    lm, om, perm = meshes
+    x = om.bD + inputs.random_state(om.M, 7, nq2=om.NQ2)
+    J3a = torch.zeros(3 * lm.nnz, dtype=torch.float64, device=DEV)
+    J3b = torch.zeros(3 * lm.nnz, dtype=torch.float64, device=DEV)
+    R3a = torch.zeros(3 * lm.M, dtype=torch.float64, device=DEV)
+    R3b = torch.zeros(3 * lm.M, dtype=torch.float64, device=DEV)
+    lrfsi.lrfsi_assemble_affine4(lm, _dev(x[perm]), J3a, J3b, R3a, R3b)
+    Ja, Jb = J3a.cpu().numpy().reshape(-1, 3), J3b.cpu().numpy().reshape(-1, 3)
+    Ra, Rb = R3a.cpu().numpy().reshape(-1, 3), R3b.cpu().numpy().reshape(-1, 3)
+    oJ = fsi.affine_jacobian4(om, x)
+    oR = fsi.affine_residual4(om, x)
+    got_J = [Ja[:, 0], Ja[:, 1], Ja[:, 2], Jb[:, 0], Jb[:, 1]]
+    got_R = [Ra[:, 0], Ra[:, 1], Ra[:, 2], Rb[:, 0], Rb[:, 1]]
+    j0max = np.abs(oJ[0].toarray()).max()
+    r0max = np.abs(oR[0]).max()
+    for t in range(5):
+        A = oJ[t][perm][:, perm].toarray()
+        B = lib_csr(lm, got_J[t]).toarray()
+        scale = max(np.abs(A).max(), j0max if t >= 3 else 0.0)
+        assert np.abs(B - A).max() <= 1e-12 * scale, t
+        rs = max(np.abs(oR[t]).max(), r0max if t >= 3 else 0.0)
+        assert np.abs(got_R[t] - oR[t][perm]).max() <= 1e-12 * rs, t
+    assert np.all(Jb[:, 2] == 0) and np.all(Rb[:, 2] == 0)
+
+
+def test_residual_batch4(meshes):
+    lm, om, perm = meshes
+    rng = np.random.default_rng(3)
+    m = 5
+    X = np.stack([om.bD + inputs.random_state(om.M, 20 + j, nq2=om.NQ2) for j in range(m)], 1)
+    mu, nu = rng.uniform(5e5, 2e6, m), rng.uniform(1e-3, 5e-3, m)
+    lam, rho = rng.uniform(1.5e6, 2.5e6, m), rng.uniform(800, 1200, m)
+    R = torch.zeros(lm.M * m, dtype=torch.float64, device=DEV)
+    n2 = torch.zeros(m, dtype=torch.float64, device=DEV)
+    lrfsi.lrfsi_residual_batch4(lm, _dev(X[perm]), m, m, _dev(mu), _dev(nu), _dev(lam), _dev(rho), R, m, n2)
+    R = R.cpu().numpy().reshape(lm.M, m)
+    for j in range(m):
+        ref = fsi.residual4(om, X[:, j], mu[j], nu[j], lam[j], rho[j])
+        assert rel_max(R[:, j], ref[perm]) <= 1e-12
+        assert abs(n2[j].item() - ref @ ref) <= 1e-12 * (ref @ ref)
+
+
+def test_newton_median4(meshes):
+    lm, om, perm = meshes
+    mu, nu = np.array([6e5, 1.5e6]), np.array([2e-3, 4e-3])
+    lam, rho = np.array([1.6e6, 2.4e6]), np.array([900.0, 1150.0])
+    X = _dev(np.tile(om.bD[perm], (2, 1)))
+    it, res, st = lrfsi.lrfsi_newton_median4(lm, X, mu, nu, lam, rho, 1e-10, 30)
+    Xh = X.cpu().numpy()
+    for k in range(2):
+        xo, ito, _ = newton.newton4(om, mu[k], nu[k], lam[k], rho[k], eps=1e-10)
+        assert res[k] <= 1e-10
+        assert rel_max(Xh[k], xo[perm]) <= 1e-9
+        assert abs(int(it[k]) - ito) <= 1
+
+
+def _subset4(om, m=8, seed=5):
+    rng = np.random.default_rng(seed)
+    mu = np.sort(rng.uniform(7e5, 1e6, m))
+    nu = rng.uniform(2.8e-3, 3.4e-3, m)
+    lam = rng.uniform(1.8e6, 2.2e6, m)
+    rho = rng.uniform(0.9e3, 1.1e3, m)
+    med = params.upper_median_position(m)
+    xt, _, _ = newton.newton4(om, mu[med], nu[med], lam[med], rho[med], eps=1e-11)
+    return mu, nu, lam, rho, xt
+
+
+def test_chebyshevT_four_parameters_matches_oracle(meshes):
+    lm, om, perm = meshes
+    mu, nu, lam, rho, xt = _subset4(om)
+    m = len(mu)
+    sub = lrfsi.Subsets(lm, _dev(xt[perm]), mu, nu, [m], [m], lam=lam, rho=rho)
+    R0, Rmu, Rnr, Rlam, Rrho = fsi.affine_residual4(om, xt)
+    UB = _dev(np.stack([R0, Rmu, Rnr, Rlam, Rrho], 1)[perm])
+    VB = _dev(-np.stack([np.ones(m), mu, nu * rho, lam, rho], 1))
+    U = torch.zeros(lm.M * m, dtype=torch.float64, device=DEV)
+    V = torch.zeros(m * m, dtype=torch.float64, device=DEV)
+    c, d = 0.5, 1.0
+    opt = lrfsi.cheb_options(c, d, iters=6, cycles=3, rank_cap=m, tol=1e-13)
+    ranks, _ = lrfsi.lrfsi_chebyshevT(sub, UB, 5, VB, 5, [5], opt, U, m, V, m)
+    r = int(ranks[0])
+    S = U.cpu().numpy().reshape(lm.M, m)[:, :r] @ V.cpu().numpy().reshape(m, m)[:, :r].T
+    J0, Jmu, Jnr, Jlam, Jrho = fsi.affine_jacobian4(om, xt)
+    B = lowrank.rhs_terms(fsi.affine_residual4(om, xt), [mu, nu * rho, lam, rho])
+    mb, nrb, lb, rb = params.affine_midpoints(mu, nu * rho, lam, rho)
+    So = lowrank.chebyshev_T_scaled(J0, Jmu, Jnr, B, mu, nu * rho, mb, nrb, c, d, iters=6, cycles=3, tol=1e-13,
+                                    rank_cap=m, extra=[(Jlam, lam, lb), (Jrho, rho, rb)])[perm]
+    scale = np.linalg.norm(So, axis=0).max()
+    for j in range(m):
+        assert np.linalg.norm(S[:, j] - So[:, j]) / scale <= 1e-10, j
+    sub.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_subset_step_four_parameters_reaches_target(meshes, precision):
+    lm, om, perm = meshes
+    mu, nu, lam, rho, xt = _subset4(om, m=10, seed=9)
+    m = len(mu)
+    sub = lrfsi.Subsets(lm, _dev(xt[perm]), mu, nu, [m], [m], lam=lam, rho=rho)
+    U = torch.zeros(lm.M * m, dtype=torch.float64, device=DEV)
+    V = torch.zeros(m * m, dtype=torch.float64, device=DEV)
+    opt = lrfsi.cheb_options(0.5, 1.0, iters=6, cycles=2, rank_cap=m, tol=1e-10, eta=0.05, precision=precision)
+    ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, 1e-8, 30, U, m, V, m)
+    assert st == 0 and rel.max() <= 1e-8, rel.max()
+    r = int(ranks[0])
+    X = xt[perm][:, None] + U.cpu().numpy().reshape(lm.M, m)[:, :r] @ V.cpu().numpy().reshape(m, m)[:, :r].T
+    rr = algorithm1.relative_residuals4(om, X[np.argsort(perm)], mu, nu, lam, rho)
+    assert rr.max() <= 1e-8 and np.allclose(rr, rel, rtol=1e-6, atol=1e-14)
+    sub.close()
