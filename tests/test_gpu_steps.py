@@ -174,7 +174,7 @@ def test_truncate_matches_svd_truncation():
                             C.c_void_p(torch.cuda.current_stream().cuda_stream))
     assert st == 0, lib.lrfsi_last_error()
     Uh = U.cpu().numpy().reshape(2, lm.M, ldo)
-    Vh = Vo.cpu().numpy()
+    Vh = Vo.cpu().numpy().reshape(sum(sizes), ldo)
     for k, m in enumerate(sizes):
         P = expect[k]
         ref = lowrank.truncate(P, tol, caps[k])
