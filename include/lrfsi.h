@@ -273,6 +273,27 @@ int lrfsi_newton_median4(lrfsi_mesh_h mesh, int K, double* X_dev, const double* 
                          const double* lam_host, const double* rho_host, double eps, int max_it, int* iters_host,
                          double* res_host, lrfsi_stream_t stream);
 
+/* ---- the time-dependent problem with the theta-scheme (Sec. 4.3,
+ * Eq. (fsi_problem_time_weak1)).  One time step t_{i-1} -> t_i for parameter
+ * (mu, nu) solves
+ *   R_theta(x) = (rho_f A_t^f / dt)(x - x_prev) + theta R(x; mu, nu)
+ *                + (1 - theta) R(x_prev; mu, nu) = 0,
+ * A_t^f the fluid velocity mass <v, phi>_F in the fluid momentum rows.  The
+ * solid is quasi-static (v = 0 on the closed solid, the stationary row
+ * ownership: the weak form states no kinematic equation, so rho_s <d_t v,
+ * phi>_S vanishes); b_D does not depend on time. */
+
+/* lrfsi_mass_fluid: the values of A_t^f on the mesh's CSR pattern (nnz). */
+int lrfsi_mass_fluid(lrfsi_mesh_h mesh, double* M_dev, lrfsi_stream_t stream);
+/* lrfsi_newton_theta: Newton for one time step of K problems (Eq.
+ * (time_indiv1)): matrix rho_f A_t^f / dt + theta J(x; mu, nu), residual
+ * R_theta.  X_dev (K x M): in the start, out the solution; Xprev_dev (K x M)
+ * the previous time step.  0 < theta <= 1, dt > 0.  Other arguments and errors
+ * as lrfsi_newton_median. */
+int lrfsi_newton_theta(lrfsi_mesh_h mesh, int K, double* X_dev, const double* Xprev_dev, const double* mu_host,
+                       const double* nu_host, double theta, double dt, double eps, int max_it, int* iters_host,
+                       double* res_host, lrfsi_stream_t stream);
+
 /* Options of the low-rank solvers (truncated Chebyshev iteration and truncated GMRES). */
 typedef struct {
   double c, d;        /* half-width and centre of the spectrum of P^{-1} A (Sec. 5.1.1);
@@ -333,6 +354,13 @@ int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt_dev, const do
 int lrfsi_subset_create4(lrfsi_mesh_h mesh, int K, const double* xt_dev, const double* mu_host,
                          const double* nu_host, const double* lam_host, const double* rho_host, const int* m_host,
                          const int* rank_cap_host, lrfsi_subset_h* out, lrfsi_stream_t stream);
+/* lrfsi_subset_create_theta: subsets of one time step (Sec. 4.3, Eq.
+ * (timedep_matrix1)): at the median's time-step solutions xt_k the operators
+ * (theta J0 + rho_f A_t^f / dt, theta Jmu', theta Jnu') and the mean-based
+ * preconditioner of their affine sum; use with lrfsi_subset_step_theta. */
+int lrfsi_subset_create_theta(lrfsi_mesh_h mesh, int K, const double* xt_dev, const double* mu_host,
+                              const double* nu_host, const int* m_host, const int* rank_cap_host, double theta,
+                              double dt, lrfsi_subset_h* out, lrfsi_stream_t stream);
 int lrfsi_subset_destroy(lrfsi_subset_h sub);
 
 /* lrfsi_chebyshevT: solve F_k(S_k) = B_k for every subset on the factors
@@ -387,6 +415,19 @@ int lrfsi_subset_step(lrfsi_subset_h sub, const lrfsi_cheb_options* opt, double 
                       int max_outer, double* U_dev, int ldu, double* V_dev, int ldv,
                       int* rank_host, double* relres_host, int* outer_host,
                       lrfsi_stream_t stream);
+
+/* lrfsi_subset_step_theta: one time step on every subset of a handle from
+ * lrfsi_subset_create_theta: the Newton step of Eq. (timedep_matrix1) at
+ * X = xt_k 1^T with the right-hand side -R_theta evaluated column by column
+ * (the (***) term exactly), then chord corrections with -R_theta of the
+ * current columns, until every column's ||R_theta||_2 / ||R(b_D; mu, nu)||_2
+ * <= target or max_outer solves (>= 1).
+ *   Xprev_dev : M x (sum m_k) row-major (ldx >= sum m_k), the previous time
+ *               step's states of the columns in subset order
+ * Outputs as lrfsi_subset_step (outer counts include the Newton step). */
+int lrfsi_subset_step_theta(lrfsi_subset_h sub, const lrfsi_cheb_options* opt, const double* Xprev_dev, int ldx,
+                            double target, int max_outer, double* U_dev, int ldu, double* V_dev, int ldv,
+                            int* rank_host, double* relres_host, int* outer_host, lrfsi_stream_t stream);
 
 /* lrfsi_subset_step_init: lrfsi_subset_step from a given start instead of the
  * first Newton step: X0_k = x~_k 1^T + U0_k V0_k^T (e.g. the learned start,

@@ -347,6 +347,27 @@ __global__ void k_jacobian(Tables T, const int* __restrict__ cells, int ncells, 
   }
 }
 
+// Fluid velocity mass <v, phi>_F on the pattern (the theta-scheme's A_t^f,
+// Sec. 4.3): momentum test (a, i) x velocity trial (b, i) of fluid cells.
+__global__ void k_mass_fluid(Tables T, const int* __restrict__ cells, int ncells, const char* __restrict__ cell_solid,
+                             const int* __restrict__ slot, double* __restrict__ Mv) {
+  const int ci = blockIdx.x;
+  if (ci >= ncells) return;
+  const int c = cells[ci];
+  if (cell_solid[c]) return;
+  const int* sl = slot + (size_t)c * kLoc * kLoc;
+  for (int idx = threadIdx.x; idx < kLoc * kLoc; idx += blockDim.x) {
+    const int e = sl[idx];
+    if (e < 0) continue;
+    const int t = idx / kLoc, tt = idx % kLoc;
+    if (t >= 36 || tt >= 36 || (t & 3) >= 2 || (tt & 3) != (t & 3)) continue;
+    const int a = t >> 2, b = tt >> 2;
+    double v = 0;
+    for (int q = 0; q < kNq; ++q) v += T.w[q] * T.N[a][q] * T.N[b][q];
+    Mv[e] += v;
+  }
+}
+
 __global__ void k_ident_diag(const int* __restrict__ diag, int n, double* __restrict__ J3) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) J3[3 * (size_t)diag[i]] = 1.0;
@@ -490,6 +511,18 @@ int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s
   if (ni) {
     k_ident_diag<<<ceil_div(ni, 256), 256, 0, s>>>(m->ident_diag.p, ni, J3);
     LRFSI_TRY(check_launch("k_ident_diag"));
+  }
+  return LRFSI_OK;
+}
+
+int launch_mass_fluid(lrfsi_mesh_s* m, double* Mv, cudaStream_t s) {
+  const Tables T = tables_of(m);
+  LRFSI_CUDA(cudaMemsetAsync(Mv, 0, sizeof(double) * m->h.colidx.size(), s));
+  for (int col = 0; col < 4; ++col) {
+    int n = m->h.color_start[col + 1] - m->h.color_start[col];
+    if (n == 0) continue;
+    k_mass_fluid<<<n, 128, 0, s>>>(T, m->color_cells.p + m->h.color_start[col], n, m->cell_solid.p, m->slot.p, Mv);
+    LRFSI_TRY(check_launch("k_mass_fluid"));
   }
   return LRFSI_OK;
 }

@@ -79,6 +79,8 @@ int build_mesh(const lrfsi_problem& prob, MeshHost& h);
 int launch_residual(lrfsi_mesh_s* m, const double* X, int ldx, int ncol, const double* c_rest,
                     const double* c_mu, const double* c_nu, double* R, int ldr, cudaStream_t s,
                     const double* c_rho = nullptr, const double* c_lam = nullptr);
+// Fluid velocity mass values <v, phi>_F on the pattern (nnz; the theta-scheme's A_t^f).
+int launch_mass_fluid(lrfsi_mesh_s* m, double* Mv, cudaStream_t s);
 // Affine Jacobian values (nnz x 3 interleaved) at state x; rho_lam (host,
 // optional): {rho_f, lambda_s} in place of the mesh's constants.
 int launch_jacobian(lrfsi_mesh_s* m, const double* x, double* J3, cudaStream_t s, const double* rho_lam = nullptr);

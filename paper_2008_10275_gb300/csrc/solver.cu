@@ -654,11 +654,71 @@ extern "C" int lrfsi_lu_info(const lrfsi_problem* prob, int64_t* out8) {
 // ---------------------------------------------------------------------------
 // Batched Newton iteration for independent problems (median solutions)
 // ---------------------------------------------------------------------------
+namespace lrfsi {
+// The theta-scheme (Sec. 4.3): one time step's operators and residual.
+// J3 <- (theta J0 + cm Mv, theta Jmu', theta Jnu'), cm = rho_f / dt.
+__global__ void k_theta_ops(double* __restrict__ J3, long nnz, double theta, double cm, const double* __restrict__ Mv) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  J3[3 * e] = theta * J3[3 * e] + cm * Mv[e];
+  J3[3 * e + 1] *= theta;
+  J3[3 * e + 2] *= theta;
+}
+// D = X - Xp (M x n, ld n)
+__global__ void k_diff(const double* X, const double* Xp, long count, double* D) {  // D may be X
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) D[e] = X[e] - Xp[e];
+}
+// R <- theta R + (1 - theta) Rp + cm Y (M x n, ld n)
+__global__ void k_theta_combine(double* __restrict__ R, const double* __restrict__ Rp, const double* __restrict__ Y,
+                                long count, double theta, double cm) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < count) R[e] = theta * R[e] + (1.0 - theta) * Rp[e] + cm * Y[e];
+}
+// (Mv, 0, 0) as an operator triple for the SpMM
+__global__ void k_mass_triple(const double* __restrict__ Mv, long nnz, double* __restrict__ M3) {
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nnz) return;
+  M3[3 * e] = Mv[e];
+  M3[3 * e + 1] = 0.0;
+  M3[3 * e + 2] = 0.0;
+}
+
+// State of a time step: previous states, their residual R(X_prev), the mass
+// triple and the scheme's constants.
+struct TimeStep {
+  const double* Xprev = nullptr;  // M x n (ld n)
+  const double* Rprev = nullptr;  // M x n: R(X_prev; mu, nu)
+  const double* M3 = nullptr;     // nnz x 3 (Mv, 0, 0)
+  const double* Mv = nullptr;     // nnz
+  double theta = 1.0, cm = 0.0;   // cm = rho_f / dt
+};
+
+// R (M x n, ld n) <- R_theta(X) = theta R(X) + (1 - theta) R(X_prev) + cm Mass (X - X_prev),
+// with R(X) already in R; D, Y: M x n scratch.
+static int theta_residual_cols(lrfsi_mesh_s* m, const TimeStep& ts, const double* X, int n, double* R, double* D,
+                               double* Y, cudaStream_t s) {
+  const long M = m->h.M, cnt = M * n;
+  k_diff<<<ceil_div(cnt, 256), 256, 0, s>>>(X, ts.Xprev, cnt, D);
+  LRFSI_TRY(check_launch("k_diff"));
+  SpmmDesc<double> d;
+  d.J3 = ts.M3; d.U = D; d.ldu = n; d.r = n; d.Y = Y; d.ldy = n;
+  d.o[0] = 0; d.o[1] = -1; d.o[2] = -1;
+  d.sc[0] = d.sc[1] = d.sc[2] = 1.0;
+  d.a1 = d.a2 = 0.0;
+  LRFSI_TRY(spmm_batched<double>(m, &d, 1, s));
+  k_theta_combine<<<ceil_div(cnt, 256), 256, 0, s>>>(R, ts.Rprev, Y, cnt, ts.theta, ts.cm);
+  return check_launch("k_theta_combine");
+}
+}  // namespace lrfsi
+
 // lam_h, rho_h (host, K each, optional): lambda_s and rho_f per problem (the
 // four-parameter problem, Sec. 4.4) in place of the mesh's constants.
+// ts (optional): a theta-scheme time step (Sec. 4.3): the residual is
+// R_theta and the Jacobian rho_f Mass / dt + theta J (previous states M x K).
 static int newton_impl(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, const double* nu_h, const double* lam_h,
                        const double* rho_h, double eps, int max_it, int* iters_h, double* res_h,
-                       lrfsi_stream_t stream) {
+                       lrfsi_stream_t stream, const TimeStep* ts = nullptr) {
   if (!m || !Xpm || !mu_h || !nu_h || K < 1 || K > kMaxGemmDescs || max_it < 0)
     return fail(LRFSI_EINVAL, "lrfsi_newton_median: bad argument (1 <= K <= 32)");
   for (int k = 0; k < K; ++k)
@@ -693,8 +753,18 @@ static int newton_impl(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, c
   LRFSI_TRY(check_launch("k_transpose"));
   PrecLU lu;
   LRFSI_TRY(lu.alloc(m, K, 1));
-  auto norms = [&](const double* Xs, std::vector<double>& out) -> int {
+  DevBuf<double> tsD, tsY;
+  if (ts) {
+    LRFSI_TRY(tsD.alloc((size_t)M * K));
+    LRFSI_TRY(tsY.alloc((size_t)M * K));
+  }
+  auto resid = [&](const double* Xs) -> int {
     LRFSI_TRY(launch_residual(m, Xs, K, K, nullptr, mu.p, nu.p, Rb.p, K, s, rho.p, lam.p));
+    if (ts) LRFSI_TRY(theta_residual_cols(m, *ts, Xs, K, Rb.p, tsD.p, tsY.p, s));
+    return LRFSI_OK;
+  };
+  auto norms = [&](const double* Xs, std::vector<double>& out) -> int {
+    LRFSI_TRY(resid(Xs));
     LRFSI_TRY(launch_colnorm2(Rb.p, M, K, K, norm2.p, work.p, work.n, s));
     out.resize(K);
     LRFSI_CUDA(cudaMemcpyAsync(out.data(), norm2.p, sizeof(double) * K, cudaMemcpyDeviceToHost, s));
@@ -712,7 +782,7 @@ static int newton_impl(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, c
       if (!(r[k] <= eps)) act.push_back(k);
     if (act.empty()) break;
     // residual at the current iterate (Rb holds it for every column after norms())
-    LRFSI_TRY(launch_residual(m, X.p, K, K, nullptr, mu.p, nu.p, Rb.p, K, s, rho.p, lam.p));
+    LRFSI_TRY(resid(X.p));
     std::vector<const double*> J3p;
     std::vector<double> al, be;
     for (int k : act) {
@@ -721,6 +791,10 @@ static int newton_impl(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, c
       double* Jk = J3.p + (size_t)3 * nnz * J3p.size();
       const double rl[2] = {rho_h ? rho_h[k] : 0.0, lam_h ? lam_h[k] : 0.0};
       LRFSI_TRY(launch_jacobian(m, xcol.p, Jk, s, (lam_h && rho_h) ? rl : nullptr));
+      if (ts) {
+        k_theta_ops<<<ceil_div(nnz, 256), 256, 0, s>>>(Jk, nnz, ts->theta, ts->cm, ts->Mv);
+        LRFSI_TRY(check_launch("k_theta_ops"));
+      }
       J3p.push_back(Jk);
       al.push_back(mu_h[k]);
       be.push_back(nu_h[k]);
@@ -801,6 +875,44 @@ extern "C" int lrfsi_newton_median4(lrfsi_mesh_h m, int K, double* Xpm, const do
   return newton_impl(m, K, Xpm, mu_h, nu_h, lam_h, rho_h, eps, max_it, iters_h, res_h, stream);
 }
 
+extern "C" int lrfsi_newton_theta(lrfsi_mesh_h m, int K, double* Xpm, const double* Xprev_pm, const double* mu_h,
+                                  const double* nu_h, double theta, double dt, double eps, int max_it, int* iters_h,
+                                  double* res_h, lrfsi_stream_t stream) {
+  if (!m || !Xpm || !Xprev_pm || !mu_h || !nu_h || K < 1 || K > kMaxGemmDescs || !(theta > 0 && theta <= 1) ||
+      !(dt > 0))
+    return fail(LRFSI_EINVAL, "lrfsi_newton_theta: bad argument (0 < theta <= 1, dt > 0)");
+  cudaStream_t s = (cudaStream_t)stream;
+  const long M = m->h.M, nnz = (long)m->h.colidx.size();
+  DevBuf<double> Xp, Rp, Mv, M3, mu, nu;
+  LRFSI_TRY(Xp.alloc((size_t)M * K));
+  LRFSI_TRY(Rp.alloc((size_t)M * K));
+  LRFSI_TRY(Mv.alloc(nnz));
+  LRFSI_TRY(M3.alloc((size_t)3 * nnz));
+  LRFSI_TRY(mu.alloc(K));
+  LRFSI_TRY(nu.alloc(K));
+  LRFSI_CUDA(cudaMemcpyAsync(mu.p, mu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  LRFSI_CUDA(cudaMemcpyAsync(nu.p, nu_h, sizeof(double) * K, cudaMemcpyHostToDevice, s));
+  k_transpose<<<ceil_div(M * K, 256), 256, 0, s>>>(Xprev_pm, K, (int)M, Xp.p);  // (K x M) -> (M x K)
+  LRFSI_TRY(check_launch("k_transpose"));
+  LRFSI_TRY(launch_residual(m, Xp.p, K, K, nullptr, mu.p, nu.p, Rp.p, K, s));
+  LRFSI_TRY(launch_mass_fluid(m, Mv.p, s));
+  k_mass_triple<<<ceil_div(nnz, 256), 256, 0, s>>>(Mv.p, nnz, M3.p);
+  LRFSI_TRY(check_launch("k_mass_triple"));
+  TimeStep ts;
+  ts.Xprev = Xp.p;
+  ts.Rprev = Rp.p;
+  ts.M3 = M3.p;
+  ts.Mv = Mv.p;
+  ts.theta = theta;
+  ts.cm = m->h.prob.rho_f / dt;
+  return newton_impl(m, K, Xpm, mu_h, nu_h, nullptr, nullptr, eps, max_it, iters_h, res_h, stream, &ts);
+}
+
+extern "C" int lrfsi_mass_fluid(lrfsi_mesh_h m, double* Mv, lrfsi_stream_t stream) {
+  if (!m || !Mv) return fail(LRFSI_EINVAL, "lrfsi_mass_fluid: null argument");
+  return launch_mass_fluid(m, Mv, (cudaStream_t)stream);
+}
+
 // ---------------------------------------------------------------------------
 // Subsets
 // ---------------------------------------------------------------------------
@@ -816,6 +928,11 @@ struct lrfsi_subset_s {
   // nu_raw, lam, rho the parameters themselves (for the nonlinear residuals);
   // J3x = (Jlam', Jrho', 0) and R3x = (Rlam, Rrho, 0) per subset
   bool four = false;
+  // theta-scheme time step (Sec. 4.3): operators (theta J0 + rho_f Mass / dt,
+  // theta Jmu', theta Jnu'), previous states and their residual, mass triple
+  bool timestep = false;
+  double theta = 1.0, cm = 0.0;
+  DevBuf<double> Mv, M3, Xprev, Rprev, Yth;
   std::vector<double> lambar, rhobar;
   DevBuf<double> nu_raw, lam, rho, J3x, R3x;
   DevBuf<float> J3xf;
@@ -1186,7 +1303,7 @@ __global__ void k_four_precond(const double* __restrict__ Ja, const double* __re
 
 static int subset_create_impl(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
                               const double* lam_h, const double* rho_h, const int* m_h, const int* cap_h,
-                              lrfsi_subset_h* out, lrfsi_stream_t stream) {
+                              lrfsi_subset_h* out, lrfsi_stream_t stream, double theta = 0.0, double dt = 0.0) {
   if (!mesh || !xt || !mu_h || !nu_h || !m_h || !cap_h || !out || K < 1 || K > kMaxGemmDescs)
     return fail(LRFSI_EINVAL, "lrfsi_subset_create: bad argument (1 <= K <= 32)");
   *out = nullptr;
@@ -1258,6 +1375,23 @@ static int subset_create_impl(lrfsi_mesh_h mesh, int K, const double* xt, const 
     }
     S->mubar.push_back(0.5 * (mlo + mhi));
     S->nubar.push_back(0.5 * (nlo + nhi));
+  }
+  if (theta > 0) {  // time step: (theta J0 + rho_f Mass / dt, theta Jmu', theta Jnu')
+    S->timestep = true;
+    S->theta = theta;
+    S->cm = mesh->h.prob.rho_f / dt;
+    LRFSI_TRY(S->Mv.alloc(nnz));
+    LRFSI_TRY(S->M3.alloc((size_t)3 * nnz));
+    LRFSI_TRY(S->Xprev.alloc((size_t)M * S->mtot));
+    LRFSI_TRY(S->Rprev.alloc((size_t)M * S->mtot));
+    LRFSI_TRY(S->Yth.alloc((size_t)M * S->mtot));
+    LRFSI_TRY(launch_mass_fluid(mesh, S->Mv.p, s));
+    k_mass_triple<<<ceil_div(nnz, 256), 256, 0, s>>>(S->Mv.p, nnz, S->M3.p);
+    LRFSI_TRY(check_launch("k_mass_triple"));
+    for (int k = 0; k < K; ++k) {
+      k_theta_ops<<<ceil_div(nnz, 256), 256, 0, s>>>(S->J3.p + (size_t)k * 3 * nnz, nnz, theta, S->cm, S->Mv.p);
+      LRFSI_TRY(check_launch("k_theta_ops"));
+    }
   }
   // equilibrate P_k and scale the operator values: the iteration and the
   // truncation run on diag(r) F(diag(c) S~) = diag(r) B
@@ -1336,6 +1470,14 @@ static int subset_create_impl(lrfsi_mesh_h mesh, int K, const double* xt, const 
 extern "C" int lrfsi_subset_create(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
                                    const int* m_h, const int* cap_h, lrfsi_subset_h* out, lrfsi_stream_t stream) {
   return subset_create_impl(mesh, K, xt, mu_h, nu_h, nullptr, nullptr, m_h, cap_h, out, stream);
+}
+
+extern "C" int lrfsi_subset_create_theta(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h,
+                                         const double* nu_h, const int* m_h, const int* cap_h, double theta, double dt,
+                                         lrfsi_subset_h* out, lrfsi_stream_t stream) {
+  if (!(theta > 0 && theta <= 1) || !(dt > 0))
+    return fail(LRFSI_EINVAL, "lrfsi_subset_create_theta: need 0 < theta <= 1 and dt > 0");
+  return subset_create_impl(mesh, K, xt, mu_h, nu_h, nullptr, nullptr, m_h, cap_h, out, stream, theta, dt);
 }
 
 extern "C" int lrfsi_subset_create4(lrfsi_mesh_h mesh, int K, const double* xt, const double* mu_h, const double* nu_h,
@@ -2638,6 +2780,16 @@ static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, dou
     }
     LRFSI_TRY(launch_residual(S->mesh, S->Xd.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu_res(), S->rc.R.p, S->mtot, s,
                               S->rho_res(), S->lam_res()));
+    if (S->timestep) {  // R_theta of the time step (Sec. 4.3); Xd becomes X - X_prev
+      TimeStep ts;
+      ts.Xprev = S->Xprev.p;
+      ts.Rprev = S->Rprev.p;
+      ts.M3 = S->M3.p;
+      ts.Mv = S->Mv.p;
+      ts.theta = S->theta;
+      ts.cm = S->cm;
+      LRFSI_TRY(theta_residual_cols(S->mesh, ts, S->Xd.p, S->mtot, S->rc.R.p, S->Xd.p, S->Yth.p, s));
+    }
     LRFSI_TRY(launch_colnorm2(S->rc.R.p, M, S->mtot, S->mtot, S->rc.norm2.p, S->rc.work.p, S->rc.work.n, s));
     std::vector<double> a(S->mtot), b(S->mtot);
     LRFSI_CUDA(cudaMemcpyAsync(a.data(), S->rc.norm2.p, sizeof(double) * S->mtot, cudaMemcpyDeviceToHost, s));
@@ -2760,6 +2912,42 @@ extern "C" int lrfsi_subset_step(lrfsi_subset_h S, const lrfsi_cheb_options* opt
   LRFSI_CUDA(cudaStreamSynchronize(s));
   if (relres_h) std::memcpy(relres_h, rel.data(), sizeof(double) * S->mtot);
   if (status != LRFSI_OK) return fail(status, "lrfsi_subset_step: target not reached within max_outer corrections");
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_subset_step_theta(lrfsi_subset_h S, const lrfsi_cheb_options* opt, const double* Xprev, int ldx,
+                                       double target, int max_outer, double* U, int ldu, double* V, int ldv,
+                                       int* rank_h, double* relres_h, int* outer_h, lrfsi_stream_t stream) {
+  if (!S || !Xprev || !U || !V || !rank_h || max_outer < 1 || ldx < S->mtot)
+    return fail(LRFSI_EINVAL, "lrfsi_subset_step_theta: bad argument (max_outer >= 1, ldx >= sum m_k)");
+  if (!S->timestep) return fail(LRFSI_EINVAL, "lrfsi_subset_step_theta: handle not made by lrfsi_subset_create_theta");
+  LRFSI_TRY(check_opts(opt));
+  LRFSI_TRY(solver_prepare(S, *opt));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int K = S->K, ldR = S->ldR;
+  const long M = S->M;
+  for (int k = 0; k < K; ++k)
+    if (ldu < S->cap[k] || ldv < S->cap[k]) return fail(LRFSI_EINVAL, "lrfsi_subset_step_theta: ldu/ldv < rank cap");
+  LRFSI_CUDA(cudaMemcpy2DAsync(S->Xprev.p, sizeof(double) * S->mtot, Xprev, sizeof(double) * ldx,
+                               sizeof(double) * S->mtot, M, cudaMemcpyDeviceToDevice, s));
+  LRFSI_TRY(launch_residual(S->mesh, S->Xprev.p, S->mtot, S->mtot, nullptr, S->mu.p, S->nu.p, S->Rprev.p, S->mtot, s));
+  // from X = x~ 1^T: the first correction is the Newton step of Eq. (timedep_matrix1)
+  std::vector<int> rC(K, 0), outer(K, 0);
+  std::vector<double> rel(S->mtot, 0.0);
+  const int status = outer_corrections(S, *opt, target, max_outer, rC, outer, rel, s);
+  if (status != LRFSI_OK && status != LRFSI_ENOCONV) return status;
+  std::vector<CopyDesc> cd;
+  for (int k = 0; k < K; ++k) {
+    rank_h[k] = rC[k];
+    if (outer_h) outer_h[k] = outer[k];
+    cd.push_back(CopyDesc{S->tall(S->UC, k, ldR), ldR, U + (size_t)k * M * ldu, ldu, M, rC[k], 0,
+                          S->csc.p + (size_t)k * M, 1.0});
+    cd.push_back(CopyDesc{S->vside(S->VC, k, ldR), ldR, V + (size_t)S->off[k] * ldv, ldv, S->m[k], rC[k], 0, nullptr, 1.0});
+  }
+  LRFSI_TRY(copy_batched(cd, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  if (relres_h) std::memcpy(relres_h, rel.data(), sizeof(double) * S->mtot);
+  if (status != LRFSI_OK) return fail(status, "lrfsi_subset_step_theta: target not reached within max_outer corrections");
   return LRFSI_OK;
 }
 

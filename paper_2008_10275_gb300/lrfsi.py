@@ -104,6 +104,10 @@ def load():
         "lrfsi_precond_apply": [vp, vp, i, vp, vp, i, vp],
         "lrfsi_truncate": [vp, vp, i, vp, i, vp, d, vp, vp, i, vp, i, vp, vp],
         "lrfsi_graph_mode": [i, vp],
+        "lrfsi_mass_fluid": [vp, vp, vp],
+        "lrfsi_newton_theta": [vp, i, vp, vp, vp, vp, d, d, d, i, vp, vp, vp],
+        "lrfsi_subset_create_theta": [vp, i, vp, vp, vp, vp, vp, d, d, C.POINTER(vp), vp],
+        "lrfsi_subset_step_theta": [vp, C.POINTER(lrfsi_cheb_options), vp, i, d, i, vp, i, vp, i, vp, vp, vp, vp],
         "lrfsi_assemble_affine4": [vp, vp, vp, vp, vp, vp, vp],
         "lrfsi_residual_batch4": [vp, vp, i, i, vp, vp, vp, vp, vp, i, vp, vp],
         "lrfsi_newton_median4": [vp, i, vp, vp, vp, vp, vp, d, i, vp, vp, vp],
@@ -353,6 +357,32 @@ def lrfsi_residual_batch4(mesh, X, ldx, m, mu, nu, lam, rho, R, ldr, norm2=None,
                                         ldr, _ptr(norm2), _stream(stream)))
 
 
+def lrfsi_mass_fluid(mesh, Mv, stream=None):
+    _check(load().lrfsi_mass_fluid(mesh.h, _ptr(Mv), _stream(stream)))
+
+
+def lrfsi_newton_theta(mesh, X, Xprev, mu, nu, theta, dt, eps, max_it, stream=None, allow_noconv=False):
+    """One theta-scheme time step of K problems (Sec. 4.3); X, Xprev: K x M."""
+    K = len(mu)
+    mu = np.ascontiguousarray(mu, np.float64); nu = np.ascontiguousarray(nu, np.float64)
+    it = np.zeros(K, np.int32); res = np.zeros(K)
+    st = load().lrfsi_newton_theta(mesh.h, K, _ptr(X), _ptr(Xprev), _ptr(mu), _ptr(nu), theta, dt, eps, max_it,
+                                   _ptr(it), _ptr(res), _stream(stream))
+    _check(st, (ENOCONV,) if allow_noconv else ())
+    return it, res, st
+
+
+def lrfsi_subset_step_theta(sub, opt, Xprev, ldx, target, max_outer, U, ldu, V, ldv, stream=None,
+                            allow_noconv=True):
+    ranks = np.zeros(sub.K, np.int32)
+    rel = np.zeros(int(sub.sizes.sum()))
+    outer = np.zeros(sub.K, np.int32)
+    st = load().lrfsi_subset_step_theta(sub.h, C.byref(opt), _ptr(Xprev), ldx, target, max_outer, _ptr(U), ldu,
+                                        _ptr(V), ldv, _ptr(ranks), _ptr(rel), _ptr(outer), _stream(stream))
+    _check(st, (ENOCONV,) if allow_noconv else ())
+    return ranks, rel, outer, st
+
+
 SOLVERS = {"chebyshev": 0, "gmres": 1}
 
 
@@ -365,7 +395,7 @@ class Subsets:
     """K subsets sharing one mesh (lrfsi_subset_create; with lam and rho the
     four-parameter problem, lrfsi_subset_create4)."""
 
-    def __init__(self, mesh, xt, mu, nu, sizes, caps, stream=None, lam=None, rho=None):
+    def __init__(self, mesh, xt, mu, nu, sizes, caps, stream=None, lam=None, rho=None, theta=None, dt=None):
         self.mesh = mesh
         self.K = len(sizes)
         self.mu = np.ascontiguousarray(mu, np.float64)
@@ -374,7 +404,11 @@ class Subsets:
         self.caps = np.ascontiguousarray(caps, np.int32)
         self.offsets = np.concatenate([[0], np.cumsum(self.sizes)[:-1]]).astype(np.int64)
         self.h = C.c_void_p()
-        if lam is not None:
+        if theta is not None:
+            _check(load().lrfsi_subset_create_theta(mesh.h, self.K, _ptr(xt), _ptr(self.mu), _ptr(self.nu),
+                                                    _ptr(self.sizes), _ptr(self.caps), float(theta), float(dt),
+                                                    C.byref(self.h), _stream(stream)))
+        elif lam is not None:
             self.lam = np.ascontiguousarray(lam, np.float64)
             self.rho = np.ascontiguousarray(rho, np.float64)
             _check(load().lrfsi_subset_create4(mesh.h, self.K, _ptr(xt), _ptr(self.mu), _ptr(self.nu), _ptr(self.lam),
