@@ -288,8 +288,9 @@ int lrfsi_mass_fluid(lrfsi_mesh_h mesh, double* M_dev, lrfsi_stream_t stream);
 /* lrfsi_newton_theta: Newton for one time step of K problems (Eq.
  * (time_indiv1)): matrix rho_f A_t^f / dt + theta J(x; mu, nu), residual
  * R_theta.  X_dev (K x M): in the start, out the solution; Xprev_dev (K x M)
- * the previous time step.  0 < theta <= 1, dt > 0.  Other arguments and errors
- * as lrfsi_newton_median. */
+ * the previous time step.  0 < theta <= 1, dt > 0.  Full Newton steps (no
+ * halving: from x_prev the first step usually raises ||R_theta|| before the
+ * quadratic phase).  Other arguments and errors as lrfsi_newton_median. */
 int lrfsi_newton_theta(lrfsi_mesh_h mesh, int K, double* X_dev, const double* Xprev_dev, const double* mu_host,
                        const double* nu_host, double theta, double dt, double eps, int max_it, int* iters_host,
                        double* res_host, lrfsi_stream_t stream);

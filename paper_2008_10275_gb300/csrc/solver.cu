@@ -828,17 +828,20 @@ static int newton_impl(lrfsi_mesh_h m, int K, double* Xpm, const double* mu_h, c
     for (int a = 0; a < na; ++a)
       if (lst[a] != 0) status = LRFSI_ESINGULAR;
     LRFSI_CUDA(cudaMemcpyAsync(Xold.p, X.p, sizeof(double) * M * K, cudaMemcpyDeviceToDevice, s));
-    // step with halving while the residual grows
+    // step with halving while the residual grows (the stationary problem); a
+    // time step takes full steps: its first step from x_prev typically raises
+    // ||R_theta|| before the quadratic phase, and halving would stall it
     std::fill(t.begin(), t.end(), 0.0);
     for (int k : act) t[k] = 1.0;
-    for (int h = 0; h < 9; ++h) {
+    const int max_halve = ts ? 0 : 8;
+    for (int h = 0; h <= max_halve; ++h) {
       LRFSI_CUDA(cudaMemcpyAsync(tdev.p, t.data(), sizeof(double) * K, cudaMemcpyHostToDevice, s));
       k_newton_update<<<ceil_div(M * K, 256), 256, 0, s>>>(Xold.p, dX.p, tdev.p, M, K, X.p);
       LRFSI_TRY(check_launch("k_newton_update"));
       LRFSI_TRY(norms(X.p, rn));
       bool again = false;
       for (int k : act) {
-        if (t[k] > 0 && !(rn[k] < r[k]) && h < 8) {
+        if (t[k] > 0 && !(rn[k] < r[k]) && h < max_halve) {
           t[k] *= 0.5;
           again = true;
         }
