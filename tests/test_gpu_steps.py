@@ -163,16 +163,11 @@ def test_truncate_matches_svd_truncation():
     ldo = 9
     U = torch.zeros(2 * lm.M * ldo, dtype=torch.float64, device=DEV)
     Vo = torch.zeros(sum(sizes) * ldo, dtype=torch.float64, device=DEV)
-    ranks = np.zeros(2, np.int32)
     tol = 3e-2   # tails: ||s_{>=3}|| = 0.0333 > tol ||s|| = 0.0316 >= ||s_{>=4}|| = 0.0105
-    lib = lrfsi.load()
-    import ctypes as C
     Xd, Vd = _dev(X.reshape(-1)), _dev(V)   # kept alive across the call
-    st = lib.lrfsi_truncate(sub.h, Xd.data_ptr(), ld, Vd.data_ptr(), ld,
-                            np.array(p, np.int32).ctypes.data, tol, np.array(caps, np.int32).ctypes.data,
-                            U.data_ptr(), ldo, Vo.data_ptr(), ldo, ranks.ctypes.data,
-                            C.c_void_p(torch.cuda.current_stream().cuda_stream))
-    assert st == 0, lib.lrfsi_last_error()
+    # the binding keeps the p and cap arrays alive during the call (a bare
+    # np.array(...).ctypes.data temporary is freed before the library reads it)
+    ranks = lrfsi.lrfsi_truncate(sub, Xd, ld, Vd, ld, p, tol, caps, U, ldo, Vo, ldo)
     Uh = U.cpu().numpy().reshape(2, lm.M, ldo)
     Vh = Vo.cpu().numpy().reshape(sum(sizes), ldo)
     for k, m in enumerate(sizes):
