@@ -486,6 +486,30 @@ int lrfsi_truncate(lrfsi_subset_h sub, const double* X_dev, int ldx, const doubl
                    const int* p_host, double tol, const int* cap_host, double* U_dev, int ldu,
                    double* Vo_dev, int ldvo, int* rank_host, lrfsi_stream_t stream);
 
+/* lrfsi_gram: the Gram product G = A^T B of two tall FP64 factors (the
+ * CholeskyQR2 Gram of the truncation, Sec. 5; the Arnoldi products of
+ * GMREST), G[i][j] = sum_l A[l][i] B[l][j].
+ *   A_dev: M x p (row-major, lda >= p);  B_dev: M x q (ldb >= q); B_dev ==
+ *   A_dev with ldb == lda and q == p is the symmetric product (only its upper
+ *   tiles are computed);  G_dev: p x q (row-major, ldg >= q), written.
+ * Path as set by lrfsi_gram_path.  The call allocates its own workspace.
+ * Errors: LRFSI_EINVAL for M < 1, p or q < 1, short leading dimensions or NULL
+ * pointers; LRFSI_ENOCONV if a pipeline wait of the tensor-core path ran out
+ * (G is then wrong). */
+int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb, int q, int64_t M, double* G_dev,
+               int ldg, lrfsi_stream_t stream);
+/* lrfsi_gram_path: how every Gram product of the library is computed:
+^ *   1: on the BF16 tensor cores by error-free splitting (Ozaki,
+ *      Ogita, Oishi, Rump 2012): each column scaled by a power of two and cut
+ *      into 8 base-128 digits exact in BF16; the digit products summed over
+ *      256-row windows are exact in the FP32 accumulators (tcgen05.mma into
+ *      tensor memory) and added as integers; the 8 digit levels are combined
+ *      in FP64.  The inputs enter as 56-bit fixed point relative to their
+ *      column's largest entry: the error is that of an FP64 Gram.
+ *   0 (default): FP64 FMA kernels.
+ * mode = -1 only queries; *previous (may be NULL) receives the old path. */
+int lrfsi_gram_path(int path, int* previous);
+
 /* ---- Learned initial guess (not a method of the paper) -------------------
  * A multilayer perceptron maps the scaled parameters z = (mu_s, nu_f) in
  * [-1, 1]^2 to k coefficients of a POD basis of method-generated solutions:

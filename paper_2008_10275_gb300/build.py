@@ -17,7 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "liblrfsi.so")
-SOURCES = ["mesh.cu", "dense.cu", "sparse_lu.cu", "solver.cu", "mlp.cu", "noalloc.cu", "layout.cu", "nd_lu.cu"]
+SOURCES = ["mesh.cu", "dense.cu", "sparse_lu.cu", "solver.cu", "mlp.cu", "noalloc.cu", "layout.cu", "nd_lu.cu",
+           "ozaki.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

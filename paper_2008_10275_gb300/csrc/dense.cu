@@ -18,6 +18,7 @@
 #include <cmath>
 
 #include "dense.h"
+#include "ozaki.h"
 
 namespace lrfsi {
 
@@ -296,10 +297,13 @@ static int gram_nsplit(int nbatch, long M, int pmax, int qmax) {
 }
 
 size_t gram_work_len(int nbatch, long M, int pmax, int qmax) {
-  return (size_t)nbatch * gram_nsplit(nbatch, M, pmax, qmax) * (size_t)pmax * qmax;
+  const size_t simt = (size_t)nbatch * gram_nsplit(nbatch, M, pmax, qmax) * (size_t)pmax * qmax;
+  const size_t oz = (ozaki_work_bytes(nbatch, M, pmax, qmax) + sizeof(double) - 1) / sizeof(double);
+  return simt > oz ? simt : oz;
 }
 
 int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t work_len, cudaStream_t s) {
+  if (gram_path() == 1 && nbatch > 0) return ozaki_gram(d, nbatch, M, work, work_len * sizeof(double), s);
   for (int base = 0; base < nbatch; base += kMaxGemmDescs) {
     GramBatch gb;
     int cnt = 0, pmax = 1, qmax = 1;

@@ -1,0 +1,637 @@
+// FP64 Gram products on the BF16 tensor cores (tcgen05) by error-free
+// splitting; see ozaki.h for the method.
+//
+// Layout of the slices in the workspace (per operand of a product): the rows
+// are cut into chunks of 16 (one K step of a BF16 MMA), the columns into
+// tiles of 128.  For chunk c, column tile T and slice t the 128 x 16 block is
+// stored in the no-swizzle K-major canonical layout of tcgen05 operands:
+// core matrices of 8 columns x 8 rows (16 bytes per column), the core
+// matrix of column group g and row group k at byte g * 256 + k * 128.  The
+// 8 slices of (c, T) are contiguous (32 KB), so the A operand of a chunk is
+// one bulk copy; a B operand of 32 columns is the quarter of a block (1 KB).
+//
+// Kernels:
+//   k_oz_exp    largest biased exponent of every column (atomicMax)
+//   k_oz_split  the 8 digit slices of every entry, in the layout above
+//   k_oz_gram   one CTA per (product, 128 x 32 output tile, row split):
+//               4-stage bulk-copy pipeline, 36 MMAs per 16-row chunk into 8
+//               level accumulators (tensor memory, double buffered per
+//               256-row window), integer read-out by 8 warps
+//   k_oz_reduce sums the per-split integer levels and combines them in FP64
+#include <cuda_bf16.h>
+
+#include <atomic>
+
+#include "ozaki.h"
+
+namespace lrfsi {
+
+namespace {
+constexpr int kSl = 8;            // slices per entry
+constexpr int kLv = 8;            // levels t + u = 0 .. 7 (0-based slices)
+constexpr int kChunk = 16;        // rows per chunk (K of one MMA)
+constexpr int kWin = 256;         // rows per exact accumulation window
+constexpr int kChunksPerWin = kWin / kChunk;
+constexpr int kTA = 128;          // output rows per tile (MMA M)
+constexpr int kTB = 32;           // output columns per tile (MMA N)
+constexpr int kStages = 4;
+constexpr int kABytes = kTA * kChunk * 2 * kSl;   // 32 KB: A operand of a chunk, all slices
+constexpr int kBBytes = kTB * kChunk * 2 * kSl;   // 8 KB
+constexpr int kStageBytes = kABytes + kBBytes;
+constexpr int kGramThreads = 288;  // 8 read-out warps + 1 issuing warp
+constexpr int kMaxWinPerSplit = 128;  // int32 read-out sums stay below 2^31
+constexpr int kMaxOz = 16;        // products per launch
+
+std::atomic<int> g_gram_path{0};
+int* g_oz_err = nullptr;  // set by a pipeline wait of k_oz_gram that ran out
+
+__host__ __device__ inline long ceil_div_l(long a, long b) { return (a + b - 1) / b; }
+}  // namespace
+
+int gram_path() { return g_gram_path.load(); }
+void set_gram_path(int p) { g_gram_path.store(p ? 1 : 0); }
+
+// ---------------------------------------------------------------------------
+// PTX helpers (tcgen05, bulk copies, mbarriers)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t sm_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(sm_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(sm_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(sm_addr(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(sm_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of the given parity, at most ~2^31 clock cycles (about a
+// second); false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity))
+    if (clock64() - t0 > (1LL << 31)) return false;
+  return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   sm_addr(dst)),
+               "l"(src), "r"(bytes), "r"(sm_addr(bar))
+               : "memory");
+}
+// shared-memory matrix descriptor: no swizzle, K-major canonical layout;
+// lbo = byte distance of core matrices along K, sbo = along M / N
+__device__ __forceinline__ uint64_t sm_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+// instruction descriptor of kind::f16: BF16 A and B (K-major), FP32 D, M x N
+__host__ __device__ constexpr uint32_t mma_idesc(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(sm_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 consecutive FP32 columns of this thread's tensor-memory lane
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+      : "r"(taddr)
+      : "memory");
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Launch parameters
+// ---------------------------------------------------------------------------
+// One operand (A or B of a product): its columns, slices and exponents.
+struct OzOp {
+  const double* X;   // M x n, row-major (ld)
+  long ld;
+  int n;             // columns
+  int nt;            // 128-column tiles
+  __nv_bfloat16* sl; // slices: nchunks x nt x 8 x 2048
+  int* ex;           // nt * 128 biased exponents (max over the column; 0: zero column)
+  Gate gate;
+};
+struct OzOps {
+  OzOp op[2 * kMaxOz];
+  int cnt;
+};
+// One product for the MMA and reduction kernels.
+struct OzProd {
+  int a, b;          // operand indices (b == a: symmetric, upper tiles only)
+  int tiles;         // output tiles computed
+  int ntb;           // 32-column tiles of B
+  int first;         // first CTA (tile-major, split-minor) of this product
+  int* part;         // tiles x nsplit x kLv x kTB x kTA int32 partial level sums
+  double* G;
+  int ldg, p, q;
+  Gate gate;
+};
+struct OzProds {
+  OzProd pr[kMaxOz];
+  OzOp op[2 * kMaxOz];
+  int cnt;
+  int nsplit;        // row splits per tile
+  int wins;          // 256-row windows of the whole M
+};
+
+__device__ __forceinline__ void oz_tile_of(const OzProd& P, int t, int& ta, int& tb) {
+  // symmetric: the tiles (ta, tb) with tb * 32 + 31 >= ta * 128, row by row;
+  // otherwise all na x ntb tiles
+  if (P.a == P.b) {
+    int r = t;
+    ta = 0;
+    for (;;) {
+      const int first_tb = (ta * kTA) / kTB;
+      const int in_row = P.ntb - first_tb;
+      if (r < in_row) { tb = first_tb + r; return; }
+      r -= in_row;
+      ++ta;
+    }
+  }
+  ta = t / P.ntb;
+  tb = t % P.ntb;
+}
+
+// ---------------------------------------------------------------------------
+// Column exponents and digit slices
+// ---------------------------------------------------------------------------
+constexpr int kExpRows = 512;
+
+// ex[i] = largest biased exponent field over column i (2047 if the column
+// holds an Inf or NaN); ex must be zeroed first.
+__global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O, long M) {
+  const OzOp& op = O.op[blockIdx.y];
+  if (!gate_open(op.gate)) return;
+  const long r0 = (long)blockIdx.x * kExpRows, r1 = r0 + kExpRows < M ? r0 + kExpRows : M;
+  for (int i = threadIdx.x; i < op.n; i += blockDim.x) {
+    int mx = 0;
+    for (long l = r0; l < r1; ++l) {
+      const int be = (int)((__double_as_longlong(op.X[l * op.ld + i]) >> 52) & 0x7FF);
+      mx = be > mx ? be : mx;
+    }
+    if (mx) atomicMax(op.ex + i, mx);
+  }
+}
+
+// The 8 balanced base-128 digits of x as a 56-bit fixed-point number in units
+// of 2^(e - 56), e = bexp_max - 1022 (so |x| < 2^e): a[0] in [-128, 128],
+// a[1..7] in [-64, 63], x = sum_t a[t] 2^(e - 7 (t + 1)) up to 2^(e - 57).
+__device__ __forceinline__ void oz_digits(double x, int bexp_max, int (&a)[kSl]) {
+  const long long bits = __double_as_longlong(x);
+  const int be = (int)((bits >> 52) & 0x7FF);
+  long long v = 0;
+  if (be != 0 && be != 0x7FF && bexp_max != 0x7FF) {
+    const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
+    const int sh = be - 1019 - (bexp_max - 1022);  // v = mant 2^sh, sh <= 3
+    if (sh >= 0) v = mant << sh;
+    else if (sh > -62) v = (mant + (1LL << (-sh - 1))) >> (-sh);
+    if (bits < 0) v = -v;
+  }
+#pragma unroll
+  for (int t = kSl - 1; t >= 1; --t) {
+    const long long d = ((v + 64) & 127) - 64;
+    a[t] = (int)d;
+    v = (v - d) >> 7;
+  }
+  a[0] = (int)v;
+}
+
+// One 16-row chunk of one operand per CTA: every (column, 8-row half) item
+// writes 16 bytes (8 rows of one column) of each slice.
+__global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps O, long M) {
+  const OzOp& op = O.op[blockIdx.y];
+  if (!gate_open(op.gate)) return;
+  const long c = blockIdx.x;
+  const int items = op.nt * kTA * 2;
+  for (int it = threadIdx.x; it < items; it += blockDim.x) {
+    const int i = it % (op.nt * kTA), kg = it / (op.nt * kTA);
+    const int ti = i / kTA, il = i % kTA;
+    const int bx = i < op.n ? op.ex[i] : 0;
+    int dig[8][kSl];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const long l = c * kChunk + kg * 8 + e;
+      const double x = (i < op.n && l < M) ? op.X[l * op.ld + i] : 0.0;
+      oz_digits(x, bx, dig[e]);
+    }
+    __nv_bfloat16* base = op.sl + ((size_t)(c * op.nt + ti) * kSl) * (kTA * kChunk) + (il >> 3) * 128 + kg * 64 +
+                          (il & 7) * 8;
+#pragma unroll
+    for (int t = 0; t < kSl; ++t) {
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn((float)dig[e][t]);
+      *reinterpret_cast<uint4*>(base + (size_t)t * (kTA * kChunk)) = *reinterpret_cast<const uint4*>(v);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Slice products on the tensor cores
+// ---------------------------------------------------------------------------
+// CTA = (product, output tile of 128 rows x 32 columns, row split).  Warp 8
+// lane 0 issues the bulk copies and the MMAs; warps 0-7 read the level sums
+// out of tensor memory after every 256-row window (warp w reads lanes
+// 32 (w % 4) .. +31 and levels 4 (w / 4) .. +3) and keep them as int32.
+// Tensor memory: 2 buffers x 8 levels x 32 FP32 columns = 512 columns.
+__global__ void __launch_bounds__(kGramThreads, 1) k_oz_gram(const __grid_constant__ OzProds P, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kStages], empty[kStages], win[2], freeb[2], fin;
+  __shared__ uint32_t s_tmem;
+  const int cta = blockIdx.x;
+  int pi = 0;
+  while (pi + 1 < P.cnt && cta >= P.pr[pi + 1].first) ++pi;
+  const OzProd& pr = P.pr[pi];
+  if (!gate_open(pr.gate)) return;  // uniform over the CTA, before any barrier or allocation
+  const int local = cta - pr.first;
+  const int tile = local / P.nsplit, split = local % P.nsplit;
+  int ta, tb;
+  oz_tile_of(pr, tile, ta, tb);
+  const OzOp& A = P.op[pr.a];
+  const OzOp& B = P.op[pr.b];
+  const int w0 = (int)((long)P.wins * split / P.nsplit), w1 = (int)((long)P.wins * (split + 1) / P.nsplit);
+  const int nwin = w1 - w0, nch = nwin * kChunksPerWin;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&win[b], 1);
+      mbar_init(&freeb[b], 8);
+    }
+    mbar_init(&fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(sm_addr(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  int acc[4][32];
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+#pragma unroll
+    for (int j = 0; j < 32; ++j) acc[k][j] = 0;
+
+  if (warp == 8) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = mma_idesc(kTA, kTB);
+      const size_t cbase = (size_t)w0 * kChunksPerWin;
+      auto load = [&](int c) {
+        const int st = c % kStages;
+        unsigned char* sa = smem + (size_t)st * kStageBytes;
+        unsigned char* sb = sa + kABytes;
+        const size_t cc = cbase + c;
+        const __nv_bfloat16* ga = A.sl + (cc * A.nt + ta) * kSl * (kTA * kChunk);
+        const __nv_bfloat16* gb = B.sl + (cc * B.nt + tb / 4) * kSl * (kTA * kChunk) + (tb % 4) * (kTB * kChunk);
+        mbar_expect_tx(&full[st], kStageBytes);
+        bulk_g2s(sa, ga, kABytes, &full[st]);
+        for (int t = 0; t < kSl; ++t) bulk_g2s(sb + t * (kTB * kChunk * 2), gb + t * (kTA * kChunk), kTB * kChunk * 2, &full[st]);
+      };
+      int issued = 0, consumed = 0;
+      for (; issued < nch && issued < kStages; ++issued) load(issued);
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int st = c % kStages;
+        if (!mbar_wait(&full[st], (uint32_t)(c / kStages) & 1)) { ok = false; break; }
+        consumed = c + 1;
+        const int w = c / kChunksPerWin, buf = w & 1;
+        const bool first = (c % kChunksPerWin) == 0;
+        if (first && w >= 2 && !mbar_wait(&freeb[buf], (uint32_t)((w - 2) >> 1) & 1)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t sa = sm_addr(smem + (size_t)st * kStageBytes), sb = sa + kABytes;
+#pragma unroll 1
+        for (int lv = 0; lv < kLv; ++lv) {
+          const uint32_t dt = tmem + (uint32_t)(buf * (kLv * kTB) + lv * kTB);
+          for (int t = 0; t <= lv; ++t) {
+            const uint64_t ad = sm_desc(sa + t * (kTA * kChunk * 2), 128, 256);
+            const uint64_t bd = sm_desc(sb + (lv - t) * (kTB * kChunk * 2), 128, 256);
+            mma_bf16(dt, ad, bd, idesc, (first && t == 0) ? 0u : 1u);
+          }
+        }
+        mma_commit(&empty[st]);
+        if (c % kChunksPerWin == kChunksPerWin - 1) mma_commit(&win[buf]);
+        if (c >= 1 && issued < nch) {  // refill the stage of chunk c - 1 once its MMAs are done
+          const int ps = (c - 1) % kStages;
+          if (!mbar_wait(&empty[ps], (uint32_t)((c - 1) / kStages) & 1)) { ok = false; break; }
+          load(issued++);
+        }
+      }
+      if (!ok) atomicExch(err, 1);
+      // every MMA of this thread done, every issued copy landed, before the
+      // tensor memory and the shared memory are released
+      mma_commit(&fin);
+      mbar_wait(&fin, 0);
+      for (int c = consumed; c < issued; ++c) mbar_wait(&full[c % kStages], (uint32_t)(c / kStages) & 1);
+    }
+  } else {
+    const int q = warp & 3, h = warp >> 2;
+    for (int w = 0; w < nwin; ++w) {
+      const int buf = w & 1;
+      if (!mbar_wait(&win[buf], (uint32_t)(w >> 1) & 1)) {
+        if (lane == 0) atomicExch(err, 1);
+        break;
+      }
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        uint32_t v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * (kLv * kTB) + (4 * h + k) * kTB), v);
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[k][j] += __float2int_rn(__uint_as_float(v[j]));
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&freeb[buf]);
+    }
+    // partial level sums of this split: [tile][split][level][column][row]
+    int* out = pr.part + (size_t)(tile * P.nsplit + split) * (kLv * kTB * kTA) + 32 * q + lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+#pragma unroll
+      for (int j = 0; j < 32; ++j) out[((size_t)(4 * h + k) * kTB + j) * kTA] = acc[k][j];
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// G[i][j] from the per-split level sums: integers summed exactly (int64), the
+// 8 levels combined in FP64 with the column scales.
+__global__ void __launch_bounds__(256) k_oz_reduce(const __grid_constant__ OzProds P) {
+  const OzProd& pr = P.pr[blockIdx.y];
+  if (!gate_open(pr.gate)) return;
+  const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long)pr.p * pr.q) return;
+  const int i0 = (int)(e % pr.p), j0 = (int)(e / pr.p);
+  int i = i0, j = j0;
+  const bool sym = pr.a == pr.b;
+  if (sym && (j / kTB) * kTB + kTB - 1 < (i / kTA) * kTA) { const int t = i; i = j; j = t; }
+  const int ta = i / kTA, tb = j / kTB;
+  int tile;
+  if (sym) {
+    tile = 0;
+    for (int r = 0; r < ta; ++r) tile += pr.ntb - (r * kTA) / kTB;
+    tile += tb - (ta * kTA) / kTB;
+  } else {
+    tile = ta * pr.ntb + tb;
+  }
+  const int ea = P.op[pr.a].ex[i], eb = P.op[pr.b].ex[j];
+  double g;
+  if (ea == 0x7FF || eb == 0x7FF) {
+    g = __longlong_as_double(0x7FF8000000000000LL);
+  } else {
+    long long S[kLv];
+#pragma unroll
+    for (int lv = 0; lv < kLv; ++lv) S[lv] = 0;
+    const int* src = pr.part + (size_t)tile * P.nsplit * (kLv * kTB * kTA) + (j % kTB) * kTA + (i % kTA);
+    for (int sp = 0; sp < P.nsplit; ++sp)
+#pragma unroll
+      for (int lv = 0; lv < kLv; ++lv) S[lv] += src[((size_t)sp * kLv + lv) * (kTB * kTA)];
+    // x = sum_t a_t 2^(e - 7 (t + 1)), e = ex - 1022: level lv scales by 2^(ea + eb - 7 (lv + 2))
+    const int sc = (ea ? ea - 1022 : 0) + (eb ? eb - 1022 : 0);
+    g = 0.0;
+#pragma unroll
+    for (int lv = kLv - 1; lv >= 0; --lv) g += ldexp((double)S[lv], sc - 7 * (lv + 2));
+  }
+  pr.G[(size_t)i0 * pr.ldg + j0] = g;
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+namespace {
+struct OzPlan {
+  int nsplit = 1, wins = 0;
+  long nchunks = 0;
+  size_t ex_bytes = 0, sl_bytes = 0, part_bytes = 0;
+  size_t total() const { return ex_bytes + sl_bytes + part_bytes; }
+};
+inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+inline int sym_tiles(int p) {
+  const int nta = (int)ceil_div_l(p, kTA), ntb = (int)ceil_div_l(p, kTB);
+  int t = 0;
+  for (int r = 0; r < nta; ++r) t += ntb - (r * kTA) / kTB;
+  return t;
+}
+// the split count for T output tiles: about two CTAs per SM, windows of a
+// split at most kMaxWinPerSplit
+inline int choose_nsplit(long T, int wins) {
+  long ns = (2L * 152 + T - 1) / (T > 0 ? T : 1);
+  const long lo = (wins + kMaxWinPerSplit - 1) / kMaxWinPerSplit;
+  if (ns < lo) ns = lo;
+  if (ns > wins) ns = wins;
+  if (ns < 1) ns = 1;
+  return (int)ns;
+}
+// layout for cnt products: nops operands of nt_op tiles each and T tiles in total
+OzPlan plan_for(long M, int nops, long sum_nt, long T) {
+  OzPlan pl;
+  pl.wins = (int)ceil_div_l(M, kWin);
+  pl.nchunks = (long)pl.wins * kChunksPerWin;
+  pl.nsplit = choose_nsplit(T, pl.wins);
+  pl.ex_bytes = round256(sizeof(int) * (size_t)sum_nt * kTA);
+  pl.sl_bytes = round256((size_t)pl.nchunks * sum_nt * kSl * kTA * kChunk * 2);
+  pl.part_bytes = round256(sizeof(int) * (size_t)T * pl.nsplit * kLv * kTB * kTA);
+  (void)nops;
+  return pl;
+}
+}  // namespace
+
+// products per launch are limited by kMaxOz and by a workspace budget of
+// 1 GiB (a single product may exceed it)
+constexpr size_t kOzBudget = (size_t)1 << 30;
+
+size_t ozaki_work_bytes(int nbatch, long M, int pmax, int qmax) {
+  if (nbatch <= 0 || M <= 0) return 0;
+  const long nta = ceil_div_l(pmax, kTA), ntq = ceil_div_l(qmax, kTA), ntb = ceil_div_l(qmax, kTB);
+  // worst case per product: unsymmetric (two operands, all tiles)
+  auto need = [&](int cnt) { return plan_for(M, 2 * cnt, (long)cnt * (nta + ntq), (long)cnt * nta * ntb).total(); };
+  int cnt = nbatch < kMaxOz ? nbatch : kMaxOz;
+  while (cnt > 1 && need(cnt) > kOzBudget) --cnt;
+  return need(cnt) + 1024;
+}
+
+int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_bytes, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    LRFSI_CUDA(cudaFuncSetAttribute(k_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, kStages * kStageBytes));
+    attr = true;
+  }
+  if (!g_oz_err) {
+    LRFSI_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
+    LRFSI_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+  }
+  for (int base = 0; base < nbatch;) {
+    // the largest group of products from base that fits the workspace
+    int cnt = 0;
+    {
+      long snt = 0, tt = 0;
+      int nop = 0;
+      while (base + cnt < nbatch && cnt < kMaxOz) {
+        const GramDesc& g = d[base + cnt];
+        const bool sym = g.A == g.B && g.lda == g.ldb && g.p == g.q;
+        const long nt = ceil_div_l(g.p, kTA) + (sym ? 0 : ceil_div_l(g.q, kTA));
+        const long tl = sym ? sym_tiles(g.p) : ceil_div_l(g.p, kTA) * ceil_div_l(g.q, kTB);
+        if (cnt > 0 && plan_for(M, nop + (sym ? 1 : 2), snt + nt, tt + tl).total() > work_bytes) break;
+        snt += nt;
+        tt += tl;
+        nop += sym ? 1 : 2;
+        ++cnt;
+      }
+    }
+    OzOps ops{};
+    OzProds P{};
+    P.cnt = cnt;
+    long sum_nt = 0, T = 0;
+    for (int b = 0; b < cnt; ++b) {
+      const GramDesc& g = d[base + b];
+      const bool sym = g.A == g.B && g.lda == g.ldb && g.p == g.q;
+      OzProd& pr = P.pr[b];
+      pr.a = ops.cnt;
+      OzOp& oa = ops.op[ops.cnt++];
+      oa.X = g.A; oa.ld = g.lda; oa.n = g.p; oa.nt = (int)ceil_div_l(g.p, kTA); oa.gate = g.gate;
+      sum_nt += oa.nt;
+      if (sym) {
+        pr.b = pr.a;
+      } else {
+        pr.b = ops.cnt;
+        OzOp& ob = ops.op[ops.cnt++];
+        ob.X = g.B; ob.ld = g.ldb; ob.n = g.q; ob.nt = (int)ceil_div_l(g.q, kTA); ob.gate = g.gate;
+        sum_nt += ob.nt;
+      }
+      pr.ntb = (int)ceil_div_l(g.q, kTB);
+      pr.tiles = sym ? sym_tiles(g.p) : (int)ceil_div_l(g.p, kTA) * pr.ntb;
+      pr.G = g.G; pr.ldg = g.ldg; pr.p = g.p; pr.q = g.q; pr.gate = g.gate;
+      T += pr.tiles;
+    }
+    const OzPlan pl = plan_for(M, ops.cnt, sum_nt, T);
+    if (pl.total() > work_bytes) return fail(LRFSI_EINVAL, "tensor-core Gram: workspace too small");
+    unsigned char* w = (unsigned char*)work;
+    int* ex = (int*)w;
+    __nv_bfloat16* sl = (__nv_bfloat16*)(w + pl.ex_bytes);
+    int* part = (int*)(w + pl.ex_bytes + pl.sl_bytes);
+    size_t o_ex = 0, o_sl = 0;
+    for (int o = 0; o < ops.cnt; ++o) {
+      ops.op[o].ex = ex + o_ex;
+      ops.op[o].sl = sl + o_sl;
+      o_ex += (size_t)ops.op[o].nt * kTA;
+      o_sl += (size_t)pl.nchunks * ops.op[o].nt * kSl * kTA * kChunk;
+    }
+    size_t o_part = 0;
+    int first = 0;
+    for (int b = 0; b < cnt; ++b) {
+      P.pr[b].part = part + o_part;
+      P.pr[b].first = first;
+      o_part += (size_t)P.pr[b].tiles * pl.nsplit * kLv * kTB * kTA;
+      first += P.pr[b].tiles * pl.nsplit;
+    }
+    for (int o = 0; o < ops.cnt; ++o) P.op[o] = ops.op[o];
+    P.nsplit = pl.nsplit;
+    P.wins = pl.wins;
+    {  // algorithmic FP64 work, as the FP64 Gram kernels count it
+      double fl = 0, by = 0;
+      for (int b = 0; b < cnt; ++b) {
+        const GramDesc& g = d[base + b];
+        if (!gate_counts(g.gate, s)) continue;
+        const bool sym = P.pr[b].a == P.pr[b].b;
+        fl += sym ? 1.0 * M * g.p * (g.p + 1) : 2.0 * M * g.p * g.q;
+        by += 8.0 * M * (sym ? g.p : g.p + g.q);
+      }
+      account(KC_GRAM, fl, by);
+    }
+    TimedLaunch tl(KC_GRAM, s);
+    LRFSI_CUDA(cudaMemsetAsync(ex, 0, pl.ex_bytes, s));
+    k_oz_exp<<<dim3((unsigned)ceil_div_l(M, kExpRows), ops.cnt), 256, 0, s>>>(ops, M);
+    LRFSI_TRY(check_launch("k_oz_exp"));
+    k_oz_split<<<dim3((unsigned)pl.nchunks, ops.cnt), 256, 0, s>>>(ops, M);
+    LRFSI_TRY(check_launch("k_oz_split"));
+    if (first > 0) {
+      k_oz_gram<<<first, kGramThreads, kStages * kStageBytes, s>>>(P, g_oz_err);
+      LRFSI_TRY(check_launch("k_oz_gram"));
+    }
+    long pq = 1;
+    for (int b = 0; b < cnt; ++b) pq = std::max(pq, (long)P.pr[b].p * P.pr[b].q);
+    k_oz_reduce<<<dim3((unsigned)ceil_div_l(pq, 256), cnt), 256, 0, s>>>(P);
+    LRFSI_TRY(check_launch("k_oz_reduce"));
+    tl.end(s);
+    base += cnt;
+  }
+  return LRFSI_OK;
+}
+
+int ozaki_error(cudaStream_t s, int* flag) {
+  *flag = 0;
+  if (!g_oz_err) return LRFSI_OK;
+  LRFSI_CUDA(cudaMemcpyAsync(flag, g_oz_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  LRFSI_CUDA(cudaStreamSynchronize(s));
+  if (*flag) LRFSI_CUDA(cudaMemsetAsync(g_oz_err, 0, sizeof(int), s));
+  return LRFSI_OK;
+}
+
+}  // namespace lrfsi
+
+extern "C" int lrfsi_gram_path(int path, int* previous) {
+  using namespace lrfsi;
+  if (path < -1 || path > 1) return fail(LRFSI_EINVAL, "lrfsi_gram_path: path must be 0, 1 (or -1 to query)");
+  const int old = gram_path();
+  if (path >= 0) set_gram_path(path);
+  if (previous) *previous = old;
+  return LRFSI_OK;
+}
+
+extern "C" int lrfsi_gram(const double* A, int lda, int p, const double* B, int ldb, int q, int64_t M, double* G,
+                          int ldg, lrfsi_stream_t stream) {
+  using namespace lrfsi;
+  if (!A || !B || !G || M < 1 || p < 1 || q < 1 || lda < p || ldb < q || ldg < q)
+    return fail(LRFSI_EINVAL, "lrfsi_gram: bad argument (M, p, q >= 1, lda >= p, ldb >= q, ldg >= q)");
+  cudaStream_t s = (cudaStream_t)stream;
+  DevBuf<double> work;
+  LRFSI_TRY(work.alloc(gram_work_len(1, (long)M, p, q)));
+  GramDesc g{A, lda, p, B, ldb, q, G, ldg};
+  LRFSI_TRY(gram_batched(&g, 1, (long)M, work.p, work.n, s));
+  int flag = 0;
+  LRFSI_TRY(ozaki_error(s, &flag));
+  if (flag) return fail(LRFSI_ENOCONV, "lrfsi_gram: a pipeline wait of the tensor-core Gram ran out");
+  return LRFSI_OK;
+}

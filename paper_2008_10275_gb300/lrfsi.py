@@ -120,6 +120,8 @@ def load():
         "lrfsi_cluster": [i, i, vp, vp, vp],
         "lrfsi_medians": [i, vp, vp, vp],
         "lrfsi_partition": [i, vp, i, vp],
+        "lrfsi_gram": [vp, i, i, vp, i, i, C.c_int64, vp, i, vp],
+        "lrfsi_gram_path": [i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -219,6 +221,19 @@ def graph_mode(mode=-1):
     prev = C.c_int(0)
     _check(load().lrfsi_graph_mode(int(mode), C.byref(prev)))
     return prev.value
+
+
+def gram_path(path=-1):
+    """Set the Gram product path (1 tensor cores by error-free splitting, 0
+    FP64 FMA; -1 queries); returns the previous path."""
+    prev = C.c_int(0)
+    _check(load().lrfsi_gram_path(int(path), C.byref(prev)))
+    return prev.value
+
+
+def lrfsi_gram(A, lda, p, B, ldb, q, M, G, ldg, stream=None):
+    """G = A^T B of tall row-major device factors (M x p, M x q) into G (p x q, ldg)."""
+    _check(load().lrfsi_gram(_ptr(A), lda, p, _ptr(B), ldb, q, int(M), _ptr(G), ldg, _stream(stream)))
 
 
 def lu_mode(mode=-1):
