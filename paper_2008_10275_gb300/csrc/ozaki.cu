@@ -365,7 +365,11 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_oz_gram(const __grid_consta
     const int q = warp & 3, h = warp >> 2;
     for (int w = 0; w < nwin; ++w) {
       const int buf = w & 1;
-      if (!mbar_wait(&win[buf], (uint32_t)(w >> 1) & 1)) {
+      // one lane waits, the warp follows its result (tcgen05.ld is warp-aligned)
+      int ok = 1;
+      if (lane == 0) ok = mbar_wait(&win[buf], (uint32_t)(w >> 1) & 1) ? 1 : 0;
+      ok = __shfl_sync(0xffffffffu, ok, 0);
+      if (!ok) {
         if (lane == 0) atomicExch(err, 1);
         break;
       }
