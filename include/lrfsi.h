@@ -499,14 +499,14 @@ int lrfsi_truncate(lrfsi_subset_h sub, const double* X_dev, int ldx, const doubl
 int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb, int q, int64_t M, double* G_dev,
                int ldg, lrfsi_stream_t stream);
 /* lrfsi_gram_path: how every Gram product of the library is computed:
-^ *   1: on the BF16 tensor cores by error-free splitting (Ozaki,
+ *   1 (default): on the BF16 tensor cores by error-free splitting (Ozaki,
  *      Ogita, Oishi, Rump 2012): each column scaled by a power of two and cut
  *      into 8 base-128 digits exact in BF16; the digit products summed over
  *      256-row windows are exact in the FP32 accumulators (tcgen05.mma into
  *      tensor memory) and added as integers; the 8 digit levels are combined
  *      in FP64.  The inputs enter as 56-bit fixed point relative to their
  *      column's largest entry: the error is that of an FP64 Gram.
- *   0 (default): FP64 FMA kernels.
+ *   0: FP64 FMA kernels.
  * mode = -1 only queries; *previous (may be NULL) receives the old path. */
 int lrfsi_gram_path(int path, int* previous);
 

@@ -42,7 +42,7 @@ constexpr int kGramThreads = 288;  // 8 read-out warps + 1 issuing warp
 constexpr int kMaxWinPerSplit = 128;  // int32 read-out sums stay below 2^31
 constexpr int kMaxOz = 16;        // products per launch
 
-std::atomic<int> g_gram_path{0};
+std::atomic<int> g_gram_path{1};
 int* g_oz_err = nullptr;  // set by a pipeline wait of k_oz_gram that ran out
 
 __host__ __device__ inline long ceil_div_l(long a, long b) { return (a + b - 1) / b; }
@@ -134,8 +134,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // ---------------------------------------------------------------------------
 // One operand (A or B of a product): its columns, slices and exponents.
 struct OzOp {
-  const double* X;   // M x n, row-major (ld)
-  long ld;
+  const double* X;   // rows x n: entry (l, i) at X[l * rs + i * cs]
+  long rs, cs;
+  const double* Xalt;  // read instead of X when sel != nullptr && *sel != 0
+  const int* sel;
   int n;             // columns
   int nt;            // 128-column tiles
   __nv_bfloat16* sl; // slices: nchunks x nt x 8 x 2048
@@ -186,22 +188,23 @@ __device__ __forceinline__ void oz_tile_of(const OzProd& P, int t, int& ta, int&
 // ---------------------------------------------------------------------------
 // Column exponents and digit slices
 // ---------------------------------------------------------------------------
-constexpr int kExpRows = 512;
+constexpr int kExpRows = 64;
 
 // ex[i] = largest biased exponent field over column i (2047 if the column
 // holds an Inf or NaN); ex must be zeroed first.
 __global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O, long M) {
-  const OzOp& op = O.op[blockIdx.y];
+  const OzOp& op = O.op[blockIdx.z];
   if (!gate_open(op.gate)) return;
+  const double* X = (op.sel && *op.sel) ? op.Xalt : op.X;
   const long r0 = (long)blockIdx.x * kExpRows, r1 = r0 + kExpRows < M ? r0 + kExpRows : M;
-  for (int i = threadIdx.x; i < op.n; i += blockDim.x) {
-    int mx = 0;
-    for (long l = r0; l < r1; ++l) {
-      const int be = (int)((__double_as_longlong(op.X[l * op.ld + i]) >> 52) & 0x7FF);
-      mx = be > mx ? be : mx;
-    }
-    if (mx) atomicMax(op.ex + i, mx);
+  const int i = blockIdx.y * 256 + threadIdx.x;
+  if (i >= op.n) return;
+  int mx = 0;
+  for (long l = r0; l < r1; ++l) {
+    const int be = (int)((__double_as_longlong(X[l * op.rs + i * op.cs]) >> 52) & 0x7FF);
+    mx = be > mx ? be : mx;
   }
+  if (mx) atomicMax(op.ex + i, mx);
 }
 
 // The 8 balanced base-128 digits of x as a 56-bit fixed-point number in units
@@ -227,22 +230,25 @@ __device__ __forceinline__ void oz_digits(double x, int bexp_max, int (&a)[kSl])
   a[0] = (int)v;
 }
 
-// One 16-row chunk of one operand per CTA: every (column, 8-row half) item
-// writes 16 bytes (8 rows of one column) of each slice.
+// CTA = (16-row chunk, group of two 128-column tiles, operand): every (column,
+// 8-row half) item writes 16 bytes (8 rows of one column) of each slice.
 __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps O, long M) {
-  const OzOp& op = O.op[blockIdx.y];
+  const OzOp& op = O.op[blockIdx.z];
   if (!gate_open(op.gate)) return;
+  const double* X = (op.sel && *op.sel) ? op.Xalt : op.X;
   const long c = blockIdx.x;
-  const int items = op.nt * kTA * 2;
+  const int t0 = blockIdx.y * 2, nt = op.nt - t0 < 2 ? op.nt - t0 : 2;
+  if (nt <= 0) return;
+  const int items = nt * kTA * 2;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
-    const int i = it % (op.nt * kTA), kg = it / (op.nt * kTA);
+    const int i = t0 * kTA + it % (nt * kTA), kg = it / (nt * kTA);
     const int ti = i / kTA, il = i % kTA;
     const int bx = i < op.n ? op.ex[i] : 0;
     int dig[8][kSl];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const long l = c * kChunk + kg * 8 + e;
-      const double x = (i < op.n && l < M) ? op.X[l * op.ld + i] : 0.0;
+      const double x = (i < op.n && l < M) ? X[l * op.rs + (long)i * op.cs] : 0.0;
       oz_digits(x, bx, dig[e]);
     }
     __nv_bfloat16* base = op.sl + ((size_t)(c * op.nt + ti) * kSl) * (kTA * kChunk) + (il >> 3) * 128 + kg * 64 +
@@ -482,6 +488,20 @@ OzPlan plan_for(long M, int nops, long sum_nt, long T) {
 }
 }  // namespace
 
+// exponents and slices of every operand of a launch
+static int oz_slice(const OzOps& ops, long rows, long nchunks, cudaStream_t s) {
+  int ntmax = 1, nmax = 1;
+  for (int o = 0; o < ops.cnt; ++o) {
+    ntmax = ops.op[o].nt > ntmax ? ops.op[o].nt : ntmax;
+    nmax = ops.op[o].n > nmax ? ops.op[o].n : nmax;
+  }
+  k_oz_exp<<<dim3((unsigned)ceil_div_l(rows, kExpRows), (unsigned)ceil_div_l(nmax, 256), ops.cnt), 256, 0, s>>>(ops,
+                                                                                                          rows);
+  LRFSI_TRY(check_launch("k_oz_exp"));
+  k_oz_split<<<dim3((unsigned)nchunks, (unsigned)ceil_div_l(ntmax, 2), ops.cnt), 256, 0, s>>>(ops, rows);
+  return check_launch("k_oz_split");
+}
+
 // products per launch are limited by kMaxOz and by a workspace budget of
 // 1 GiB (a single product may exceed it)
 constexpr size_t kOzBudget = (size_t)1 << 30;
@@ -534,14 +554,14 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
       OzProd& pr = P.pr[b];
       pr.a = ops.cnt;
       OzOp& oa = ops.op[ops.cnt++];
-      oa.X = g.A; oa.ld = g.lda; oa.n = g.p; oa.nt = (int)ceil_div_l(g.p, kTA); oa.gate = g.gate;
+      oa.X = g.A; oa.rs = g.lda; oa.cs = 1; oa.n = g.p; oa.nt = (int)ceil_div_l(g.p, kTA); oa.gate = g.gate;
       sum_nt += oa.nt;
       if (sym) {
         pr.b = pr.a;
       } else {
         pr.b = ops.cnt;
         OzOp& ob = ops.op[ops.cnt++];
-        ob.X = g.B; ob.ld = g.ldb; ob.n = g.q; ob.nt = (int)ceil_div_l(g.q, kTA); ob.gate = g.gate;
+        ob.X = g.B; ob.rs = g.ldb; ob.cs = 1; ob.n = g.q; ob.nt = (int)ceil_div_l(g.q, kTA); ob.gate = g.gate;
         sum_nt += ob.nt;
       }
       pr.ntb = (int)ceil_div_l(g.q, kTB);
@@ -586,10 +606,7 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
     }
     TimedLaunch tl(KC_GRAM, s);
     LRFSI_CUDA(cudaMemsetAsync(ex, 0, pl.ex_bytes, s));
-    k_oz_exp<<<dim3((unsigned)ceil_div_l(M, kExpRows), ops.cnt), 256, 0, s>>>(ops, M);
-    LRFSI_TRY(check_launch("k_oz_exp"));
-    k_oz_split<<<dim3((unsigned)pl.nchunks, ops.cnt), 256, 0, s>>>(ops, M);
-    LRFSI_TRY(check_launch("k_oz_split"));
+    LRFSI_TRY(oz_slice(ops, M, pl.nchunks, s));
     if (first > 0) {
       k_oz_gram<<<first, kGramThreads, kStages * kStageBytes, s>>>(P, g_oz_err);
       LRFSI_TRY(check_launch("k_oz_gram"));
