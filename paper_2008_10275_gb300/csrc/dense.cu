@@ -410,7 +410,8 @@ __device__ void chol_drop(double* G, int ld, int p, double drop, int* keep) {
 
 size_t trunc_small_work(int p, int m) {
   const size_t n = (size_t)(p > m ? p : m);
-  return 4 * (size_t)p * p + 3 * n * n + 2 * (size_t)p * m + 4 * n + 64 + trunc_svd_global_len(p, m, 16);
+  return 4 * (size_t)p * p + 3 * n * n + 2 * (size_t)p * m + 4 * n + 64 + trunc_svd_global_len(p, m, 16) +
+         trunc_qr_len(p, m);
 }
 
 // Pass 1: unit-diagonal scaling and a diagonally pivoted (rank-revealing)
@@ -588,12 +589,139 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, in
 }
 
 // ---------------------------------------------------------------------------
+// QR preconditioning of the SVD (Drmac and Veselic, "New fast and accurate
+// Jacobi SVD algorithm", SIAM J. Matrix Anal. Appl. 29, 2008): the Jacobi
+// matrix A (L x n, L >= n: A = C if m < k, else C^T) is factored as
+// A P = Q R by Householder reflections with column pivoting, and the one-sided
+// Jacobi iteration then runs on X = R^T, which converges in a few sweeps
+// (the rows of R are graded by the pivoting).  With X W = Y (orthogonal
+// columns, norms sigma): A = (Q W) (P Y)^T, so Q W holds the left and P Y the
+// (sigma-scaled) right singular vectors of A.
+// ---------------------------------------------------------------------------
+// One CTA per problem.  Aw: column-major copy of A, overwritten by the
+// reflectors (v_j in rows j.. of column j, its leading entry explicit) and by
+// R above the diagonal; Rt = R^T; tau_j; perm (A P = A[:, perm]).
+__global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) {
+  const TruncDesc d = descs[blockIdx.x];
+  if (!gate_open(d.gate)) return;
+  const int p = d.p, m = d.m;
+  const int k = p > 0 ? d.info[0] : 0;
+  if (k <= 0 || m <= 0 || d.info[2] != 0) return;  // the SVD kernel handles these
+  const bool cols_of_C = m < k;
+  const int n = cols_of_C ? m : k, L = cols_of_C ? k : m;
+  const TruncWork W(d.work, p, m);
+  const QrWork Q(W, p, m);
+  double* A = Q.Aw;
+  const double* core = (d.sel && *d.sel) ? d.core_alt : d.core;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  __shared__ double s_val[32];
+  __shared__ int s_idx[32];
+  __shared__ int s_piv;
+  for (long e = tid; e < (long)L * n; e += blockDim.x) {
+    const int c = (int)(e / L), i = (int)(e % L);
+    A[e] = cols_of_C ? core[(size_t)i * m + c] : core[(size_t)c * m + i];
+  }
+  for (int c = tid; c < n; c += blockDim.x) Q.perm[c] = c;
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
+    // squared norms of the trailing parts (rows j..) of the columns j..
+    for (int c = j + warp; c < n; c += nw) {
+      double t = 0;
+      for (int i = j + lane; i < L; i += 32) t = fma(A[(size_t)c * L + i], A[(size_t)c * L + i], t);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) Q.nrm[c] = t;
+    }
+    __syncthreads();
+    // pivot: the largest trailing norm (ties: the smallest column)
+    {
+      double best = -1.0;
+      int bc = 0x7fffffff;
+      for (int c = j + tid; c < n; c += blockDim.x)
+        if (Q.nrm[c] > best) { best = Q.nrm[c]; bc = c; }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+        const int c2 = __shfl_xor_sync(0xffffffffu, bc, o);
+        if (v2 > best || (v2 == best && c2 < bc)) { best = v2; bc = c2; }
+      }
+      if (lane == 0) { s_val[warp] = best; s_idx[warp] = bc; }
+      __syncthreads();
+      if (warp == 0) {
+        best = lane < nw ? s_val[lane] : -1.0;
+        bc = lane < nw ? s_idx[lane] : 0x7fffffff;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
+          const int c2 = __shfl_xor_sync(0xffffffffu, bc, o);
+          if (v2 > best || (v2 == best && c2 < bc)) { best = v2; bc = c2; }
+        }
+        if (lane == 0) s_piv = bc;
+      }
+      __syncthreads();
+    }
+    const int pv = s_piv;
+    const double sig2 = Q.nrm[pv];
+    if (pv != j) {
+      for (int i = tid; i < L; i += blockDim.x) {
+        const double t = A[(size_t)j * L + i];
+        A[(size_t)j * L + i] = A[(size_t)pv * L + i];
+        A[(size_t)pv * L + i] = t;
+      }
+      if (tid == 0) {
+        const int t = Q.perm[j];
+        Q.perm[j] = Q.perm[pv];
+        Q.perm[pv] = t;
+      }
+    }
+    __syncthreads();
+    // reflector H = I - tau v v^T with H x = alpha e_1, alpha = -sign(x_0) |x|
+    const double x0 = A[(size_t)j * L + j];
+    const double nx = sqrt(sig2);
+    double alpha = 0.0, tau = 0.0;
+    if (nx > 0.0) {
+      alpha = x0 >= 0 ? -nx : nx;
+      const double v0 = x0 - alpha;
+      tau = -1.0 / (alpha * v0);
+      __syncthreads();  // every thread has read x0
+      if (tid == 0) A[(size_t)j * L + j] = v0;
+    }
+    if (tid == 0) {
+      Q.tau[j] = tau;
+      Q.Rt[(size_t)j * n + j] = alpha;
+    }
+    __syncthreads();
+    // apply H to the columns j+1..: w = v . a_c, a_c -= tau w v (rows j..)
+    if (tau != 0.0) {
+      const double* v = A + (size_t)j * L;
+      for (int c = j + 1 + warp; c < n; c += nw) {
+        double* a = A + (size_t)c * L;
+        double t = 0;
+        for (int i = j + lane; i < L; i += 32) t = fma(v[i], a[i], t);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        t *= tau;
+        for (int i = j + lane; i < L; i += 32) a[i] = fma(-t, v[i], a[i]);
+      }
+    }
+    __syncthreads();
+  }
+  // X = R^T: column c of X is row c of R (R[c][i] = A[i][c] for i > c)
+  for (long e = tid; e < (long)n * n; e += blockDim.x) {
+    const int c = (int)(e / n), i = (int)(e % n);
+    if (i != c) Q.Rt[e] = i > c ? A[(size_t)i * L + c] : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // SVD of the core by one-sided Jacobi on a thread-block cluster
 // ---------------------------------------------------------------------------
-// The core C (k x m, rows of d.core, ld m) is orthogonalised as A = C
-// (L = k, n = m columns) if m < k, else A = C^T (L = m, n = k): A V = A'
-// with orthogonal columns, V accumulated.  Every column is stored with its V
-// column appended (length LV = L + n), so one rotation updates both.
+// The core C (k x m, rows of d.core, ld m) gives the Jacobi matrix A = C
+// (k x m) if m < k, else A = C^T (m x k); k_trunc_qrcp factors A P = Q R and
+// the iteration orthogonalises the n columns of X = R^T (n x n): X W = Y
+// with orthogonal columns, W accumulated.  Every column is stored with its W
+// column appended (length LV = 2n), so one rotation updates both.  The kept
+// singular vectors follow from Y and W (see the output stage).
 //
 // Parallel block ordering: the n columns form nb = 2 C blocks of b columns; CTA
 // c of the cluster owns blocks 2c, 2c+1 in its shared memory.  A sweep is
@@ -705,10 +833,10 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     if (m > 0) zero_tail(0);
     return;
   }
-  // A = C^T whenever k <= m: the rows of the core are graded by the pivoted
-  // Cholesky, and Jacobi converges in fewer sweeps on graded columns
+  // Jacobi on X = R^T (n x n) of the QR of A = C (if m < k) or C^T (k_trunc_qrcp)
   const bool cols_of_C = m < k;
-  const int n = cols_of_C ? m : k, L = cols_of_C ? k : m, LV = L + n;
+  const int n = cols_of_C ? m : k, La = cols_of_C ? k : m, L = n, LV = 2 * n;
+  const QrWork Q(W, p, m);
   const int nb = 2 * C, b = (n + nb - 1) / nb;
   // the CTA's column blocks and round buffers: shared memory, or (problems
   // too large for it) a slice of the global work array per CTA
@@ -721,14 +849,10 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   double* home = sm;                    // 2b columns: global columns 2 crank b + h
   double* work = sm + (size_t)2 * b * LV;  // the two blocks of a tournament round
   const int j0 = 2 * crank * b;
-  const double* core = (d.sel && *d.sel) ? d.core_alt : d.core;
   for (long e = tid; e < (long)2 * b * LV; e += kSvdThreads) {
     const int h = (int)(e / LV), i = (int)(e % LV), j = j0 + h;
     double v = 0;
-    if (j < n) {
-      if (i < L) v = cols_of_C ? core[(size_t)i * m + j] : core[(size_t)j * m + i];
-      else v = (i - L == j) ? 1.0 : 0.0;
-    }
+    if (j < n) v = i < L ? Q.Rt[(size_t)j * n + i] : ((i - L == j) ? 1.0 : 0.0);
     home[e] = v;
   }
   __syncthreads();
@@ -810,18 +934,13 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     small2 = s_cm * zfac;
     if (s_tot == 0.0) { sweeps = t + 1; break; }
   }
-  // final columns to global memory: A (L x n) and V (n x n), column-major;
-  // unsorted singular values into Dsc
+  // unsorted singular values (column norms of Y = X W) into Dsc
   for (int h = warp; h < 2 * b; h += kSvdWarps) {
     const int j = j0 + h;
     if (j >= n) continue;
     const double* col = home + (size_t)h * LV;
     double t = 0;
-    for (int i = lane; i < L; i += 32) {
-      W.A[(size_t)j * L + i] = col[i];
-      t = fma(col[i], col[i], t);
-    }
-    for (int i = lane; i < n; i += 32) W.Vm[(size_t)j * n + i] = col[L + i];
+    for (int i = lane; i < L; i += 32) t = fma(col[i], col[i], t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
     if (lane == 0) W.Dsc[j] = sqrt(t);
@@ -833,10 +952,10 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   int* order = (int*)(work + n);
   const double* sraw = W.Dsc;
   for (int j = tid; j < n; j += kSvdThreads) {
-    const double v = sraw[j];
+    const double v = __ldcg(sraw + j);
     int rk = 0;
     for (int l = 0; l < n; ++l) {
-      const double w = sraw[l];
+      const double w = __ldcg(sraw + l);
       rk += (w > v) || (w == v && l < j);
     }
     order[rk] = j;
@@ -868,19 +987,46 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   if (crank == 0)
     for (int j = tid; j < n; j += kSvdThreads) d.sv[j] = sig[j];
   const int r = s_r;
-  // W_r (k x r, ld p) into Rk; the tall coefficients T2 W_r follow as a GEMM
-  const long stride = (long)C * kSvdThreads;
-  for (long e = (long)crank * kSvdThreads + tid; e < (long)k * r; e += stride) {
-    const int a = (int)(e / r), j = (int)(e % r);
-    const int col = order[j];
-    W.Rk[(size_t)a * p + j] =
-        cols_of_C ? (sig[j] > 0 ? W.A[(size_t)col * L + a] / sig[j] : 0.0) : W.Vm[(size_t)col * n + a];
+  // outputs of the CTA's own columns that rank below r: with Y = X W,
+  //   left singular vector of A  u = Q [w; 0]   (reflectors applied in reverse)
+  //   right singular vector x sigma of A        = P y   (y[i] -> row perm[i])
+  // C's left vectors (W_r into Rk, ld p) and sigma-scaled right vectors (Vout)
+  // are u, P y (A = C) or P y / sigma, sigma u (A = C^T).
+  for (int h = warp; h < 2 * b; h += kSvdWarps) {
+    const int j = j0 + h;
+    if (j >= n) continue;
+    int pos = -1;
+    for (int q = 0; q < r; ++q)
+      if (order[q] == j) pos = q;
+    if (pos < 0) continue;
+    const double sg = sig[pos];
+    const double* y = home + (size_t)h * LV;
+    const double* w = y + L;
+    double* u = Q.scr + (size_t)(crank * kSvdWarps + warp) * La;
+    for (int i = lane; i < La; i += 32) u[i] = i < n ? w[i] : 0.0;
+    __syncwarp();
+    for (int jj = n - 1; jj >= 0; --jj) {
+      const double tau = Q.tau[jj];
+      if (tau == 0.0) continue;
+      const double* v = Q.Aw + (size_t)jj * La;
+      double t = 0;
+      for (int i = jj + lane; i < La; i += 32) t = fma(v[i], u[i], t);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      t *= tau;
+      for (int i = jj + lane; i < La; i += 32) u[i] = fma(-t, v[i], u[i]);
+      __syncwarp();
+    }
+    if (cols_of_C) {
+      for (int a = lane; a < k; a += 32) W.Rk[(size_t)a * p + pos] = u[a];
+      for (int i = lane; i < n; i += 32) d.Vout[(size_t)Q.perm[i] * d.ldvo + pos] = y[i];
+    } else {
+      const double inv = sg > 0 ? 1.0 / sg : 0.0;
+      for (int i = lane; i < n; i += 32) W.Rk[(size_t)Q.perm[i] * p + pos] = y[i] * inv;
+      for (int c = lane; c < m; c += 32) d.Vout[(size_t)c * d.ldvo + pos] = u[c] * sg;
+    }
   }
-  for (long e = (long)crank * kSvdThreads + tid; e < (long)m * r; e += stride) {
-    const int c = (int)(e / r), j = (int)(e % r);
-    const int col = order[j];
-    d.Vout[(size_t)c * d.ldvo + j] = cols_of_C ? W.Vm[(size_t)col * n + c] * sig[j] : W.A[(size_t)col * L + c];
-  }
+  __syncthreads();
   zero_tail(r);
 }
 
@@ -937,12 +1083,12 @@ static int svd_cluster_size(int nprob, size_t smem) {
 int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload) {
   if (n <= 0) return LRFSI_OK;
   if (upload) LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
-  int nmax = 1, Lmax = 1;
+  int nmax = 1;
   for (int i = 0; i < n; ++i) {
-    const int lo = d[i].p < d[i].m ? d[i].p : d[i].m, hi = d[i].p < d[i].m ? d[i].m : d[i].p;
+    const int lo = d[i].p < d[i].m ? d[i].p : d[i].m;
     nmax = nmax > lo ? nmax : lo;
-    Lmax = Lmax > hi ? Lmax : hi;
   }
+  const int Lmax = nmax;  // the Jacobi matrix is R^T of the QR preconditioning (n x n)
   int C = svd_cluster_size(n, 0);
   size_t smem = 0;
   for (;;) {
@@ -965,6 +1111,8 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool 
   }
   account(KC_SVD, 0, 0);
   TimedLaunch tl(KC_SVD, s);
+  k_trunc_qrcp<<<n, kSmallThreads, 0, s>>>(d_dev);
+  LRFSI_TRY(check_launch("k_trunc_qrcp"));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;

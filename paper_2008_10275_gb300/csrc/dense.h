@@ -108,5 +108,26 @@ __host__ __device__ inline size_t trunc_svd_global_len(int p, int m, int C) {
   const int b = (n + 2 * C - 1) / (2 * C);
   return (size_t)C * 4 * b * (size_t)(L + n);
 }
+// The QR preconditioning of the SVD (after Jg, sized for p x m): Householder
+// vectors Aw (L x n, column-major), X = R^T (n x n, column c = row c of R),
+// tau (n), the column permutation (n ints), the trailing norms (n) and one
+// length-L scratch vector per warp of a 16-CTA cluster.
+struct QrWork {
+  double *Aw, *Rt, *tau, *nrm, *scr;
+  int* perm;
+  __host__ __device__ QrWork(const TruncWork& W, int p, int m) {
+    const size_t n = (size_t)(p < m ? p : m), L = (size_t)(p < m ? m : p);
+    Aw = W.Jg + trunc_svd_global_len(p, m, 16);
+    Rt = Aw + L * n;
+    tau = Rt + n * n;
+    nrm = tau + n;
+    perm = (int*)(nrm + n);
+    scr = nrm + 2 * n;  // perm takes n ints (<= n doubles)
+  }
+};
+__host__ __device__ inline size_t trunc_qr_len(int p, int m) {
+  const size_t n = (size_t)(p < m ? p : m), L = (size_t)(p < m ? m : p);
+  return L * n + n * n + 3 * n + 16 * 8 * L;
+}
 
 }  // namespace lrfsi

@@ -16,8 +16,9 @@
 //   k_oz_gram   one CTA per (product, 128 x 32 output tile, row split):
 //               4-stage bulk-copy pipeline, 36 MMAs per 16-row chunk into 8
 //               level accumulators (tensor memory, double buffered per
-//               256-row window), integer read-out by 8 warps
-//   k_oz_reduce sums the per-split integer levels and combines them in FP64
+//               256-row window), integer read-out by 8 warps into int32
+//               sums, added to the tile's int64 level totals (atomics)
+//   k_oz_reduce combines the 8 int64 level totals of an entry in FP64
 #include <cuda_bf16.h>
 
 #include <atomic>
@@ -154,7 +155,7 @@ struct OzProd {
   int tiles;         // output tiles computed
   int ntb;           // 32-column tiles of B
   int first;         // first CTA (tile-major, split-minor) of this product
-  int* part;         // tiles x nsplit x kLv x kTB x kTA int32 partial level sums
+  unsigned long long* acc;  // tiles x kLv x kTB x kTA int64 level sums (two's complement)
   double* G;
   int ldg, p, q;
   Gate gate;
@@ -343,14 +344,17 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_oz_gram(const __grid_consta
         if (first && w >= 2 && !mbar_wait(&freeb[buf], (uint32_t)((w - 2) >> 1) & 1)) { ok = false; break; }
         tc_fence_after();
         const uint32_t sa = sm_addr(smem + (size_t)st * kStageBytes), sb = sa + kABytes;
-#pragma unroll 1
+        // descriptors of slice 0; slice t starts t * 4 KB (A) / 1 KB (B) later,
+        // i.e. t * 256 / t * 64 in the address field (smem addresses < 2^18)
+        const uint64_t a0 = sm_desc(sa, 128, 256), b0 = sm_desc(sb, 128, 256);
+        const uint32_t d0 = tmem + (uint32_t)(buf * (kLv * kTB));
+        const uint32_t acc0 = first ? 0u : 1u;
+#pragma unroll
         for (int lv = 0; lv < kLv; ++lv) {
-          const uint32_t dt = tmem + (uint32_t)(buf * (kLv * kTB) + lv * kTB);
-          for (int t = 0; t <= lv; ++t) {
-            const uint64_t ad = sm_desc(sa + t * (kTA * kChunk * 2), 128, 256);
-            const uint64_t bd = sm_desc(sb + (lv - t) * (kTB * kChunk * 2), 128, 256);
-            mma_bf16(dt, ad, bd, idesc, (first && t == 0) ? 0u : 1u);
-          }
+#pragma unroll
+          for (int t = 0; t <= lv; ++t)
+            mma_bf16(d0 + lv * kTB, a0 + (uint64_t)(t * ((kTA * kChunk * 2) >> 4)),
+                     b0 + (uint64_t)((lv - t) * ((kTB * kChunk * 2) >> 4)), idesc, t == 0 ? acc0 : 1u);
         }
         mma_commit(&empty[st]);
         if (c % kChunksPerWin == kChunksPerWin - 1) mma_commit(&win[buf]);
@@ -391,12 +395,14 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_oz_gram(const __grid_consta
       __syncwarp();
       if (lane == 0) mbar_arrive(&freeb[buf]);
     }
-    // partial level sums of this split: [tile][split][level][column][row]
-    int* out = pr.part + (size_t)(tile * P.nsplit + split) * (kLv * kTB * kTA) + 32 * q + lane;
+    // add this split's level sums into the tile's int64 totals
+    // [tile][level][column][row] (integer adds: the order does not matter)
+    unsigned long long* out = pr.acc + (size_t)tile * (kLv * kTB * kTA) + 32 * q + lane;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
 #pragma unroll
-      for (int j = 0; j < 32; ++j) out[((size_t)(4 * h + k) * kTB + j) * kTA] = acc[k][j];
+      for (int j = 0; j < 32; ++j)
+        if (acc[k][j]) atomicAdd(out + ((size_t)(4 * h + k) * kTB + j) * kTA, (unsigned long long)(long long)acc[k][j]);
   }
   tc_fence_before();
   __syncthreads();
@@ -406,8 +412,8 @@ __global__ void __launch_bounds__(kGramThreads, 1) k_oz_gram(const __grid_consta
   }
 }
 
-// G[i][j] from the per-split level sums: integers summed exactly (int64), the
-// 8 levels combined in FP64 with the column scales.
+// G[i][j] from the int64 level totals of its tile: the 8 levels combined in
+// FP64 with the column scales.
 __global__ void __launch_bounds__(256) k_oz_reduce(const __grid_constant__ OzProds P) {
   const OzProd& pr = P.pr[blockIdx.y];
   if (!gate_open(pr.gate)) return;
@@ -434,10 +440,9 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const __grid_constant__ OzPro
     long long S[kLv];
 #pragma unroll
     for (int lv = 0; lv < kLv; ++lv) S[lv] = 0;
-    const int* src = pr.part + (size_t)tile * P.nsplit * (kLv * kTB * kTA) + (j % kTB) * kTA + (i % kTA);
-    for (int sp = 0; sp < P.nsplit; ++sp)
+    const unsigned long long* src = pr.acc + (size_t)tile * (kLv * kTB * kTA) + (j % kTB) * kTA + (i % kTA);
 #pragma unroll
-      for (int lv = 0; lv < kLv; ++lv) S[lv] += src[((size_t)sp * kLv + lv) * (kTB * kTA)];
+    for (int lv = 0; lv < kLv; ++lv) S[lv] = (long long)src[(size_t)lv * (kTB * kTA)];
     // x = sum_t a_t 2^(e - 7 (t + 1)), e = ex - 1022: level lv scales by 2^(ea + eb - 7 (lv + 2))
     const int sc = (ea ? ea - 1022 : 0) + (eb ? eb - 1022 : 0);
     g = 0.0;
@@ -467,7 +472,9 @@ inline int sym_tiles(int p) {
 // the split count for T output tiles: about two CTAs per SM, windows of a
 // split at most kMaxWinPerSplit
 inline int choose_nsplit(long T, int wins) {
-  long ns = (2L * 152 + T - 1) / (T > 0 ? T : 1);
+  // whole waves of one CTA per SM (152 SMs), windows of a split at most
+  // kMaxWinPerSplit
+  long ns = (2L * 152) / (T > 0 ? T : 1);
   const long lo = (wins + kMaxWinPerSplit - 1) / kMaxWinPerSplit;
   if (ns < lo) ns = lo;
   if (ns > wins) ns = wins;
@@ -482,7 +489,7 @@ OzPlan plan_for(long M, int nops, long sum_nt, long T) {
   pl.nsplit = choose_nsplit(T, pl.wins);
   pl.ex_bytes = round256(sizeof(int) * (size_t)sum_nt * kTA);
   pl.sl_bytes = round256((size_t)pl.nchunks * sum_nt * kSl * kTA * kChunk * 2);
-  pl.part_bytes = round256(sizeof(int) * (size_t)T * pl.nsplit * kLv * kTB * kTA);
+  pl.part_bytes = round256(sizeof(unsigned long long) * (size_t)T * kLv * kTB * kTA);
   (void)nops;
   return pl;
 }
@@ -574,7 +581,7 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
     unsigned char* w = (unsigned char*)work;
     int* ex = (int*)w;
     __nv_bfloat16* sl = (__nv_bfloat16*)(w + pl.ex_bytes);
-    int* part = (int*)(w + pl.ex_bytes + pl.sl_bytes);
+    unsigned long long* part = (unsigned long long*)(w + pl.ex_bytes + pl.sl_bytes);
     size_t o_ex = 0, o_sl = 0;
     for (int o = 0; o < ops.cnt; ++o) {
       ops.op[o].ex = ex + o_ex;
@@ -585,9 +592,9 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
     size_t o_part = 0;
     int first = 0;
     for (int b = 0; b < cnt; ++b) {
-      P.pr[b].part = part + o_part;
+      P.pr[b].acc = part + o_part;
       P.pr[b].first = first;
-      o_part += (size_t)P.pr[b].tiles * pl.nsplit * kLv * kTB * kTA;
+      o_part += (size_t)P.pr[b].tiles * kLv * kTB * kTA;
       first += P.pr[b].tiles * pl.nsplit;
     }
     for (int o = 0; o < ops.cnt; ++o) P.op[o] = ops.op[o];
@@ -606,6 +613,7 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
     }
     TimedLaunch tl(KC_GRAM, s);
     LRFSI_CUDA(cudaMemsetAsync(ex, 0, pl.ex_bytes, s));
+    LRFSI_CUDA(cudaMemsetAsync(part, 0, pl.part_bytes, s));
     LRFSI_TRY(oz_slice(ops, M, pl.nchunks, s));
     if (first > 0) {
       k_oz_gram<<<first, kGramThreads, kStages * kStageBytes, s>>>(P, g_oz_err);

@@ -1119,7 +1119,11 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
       const double n = std::min(kk, mm), L = std::max(kk, mm), sw = std::max(info[5 * k + 3], 1);
       fl += 2.0 * P * P * P / 3.0 + kk * kk * kk / 3.0;                 // pass 1
       fl += (third[k] ? 2.0 : 1.0) * (2.0 * kk * kk * kk / 3.0);         // QR passes
-      fj += sw * n * (n - 1) / 2.0 * (6.0 * L + 4.0 * (L + n));         // Jacobi
+      // QR with pivoting of the L x n Jacobi matrix (updates and trailing norms),
+      // Jacobi on R^T (n x n, pairs rotated with their V columns), reflectors
+      // applied to the r kept columns
+      fj += 3.0 * L * n * n - n * n * n + sw * n * (n - 1) / 2.0 * (6.0 * n + 8.0 * n) +
+            4.0 * L * n * info[5 * k + 1];
     }
     account(KC_TRUNC, fl, 0);
     account(KC_SVD, fj, 0);
@@ -1948,7 +1952,8 @@ static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
       const double P = hd[k].p, kk = info[5 * k], mm = hd[k].m;
       const double n = std::min(kk, mm), L = std::max(kk, mm), sw = std::max(info[5 * k + 3], 1);
       fl += 2.0 * P * P * P / 3.0 + (info[5 * k + 4] ? 2.0 : 1.0) * (2.0 * kk * kk * kk / 3.0) + kk * kk * kk / 3.0;
-      fj += sw * n * (n - 1) / 2.0 * (6.0 * L + 4.0 * (L + n));
+      fj += 3.0 * L * n * n - n * n * n + sw * n * (n - 1) / 2.0 * (6.0 * n + 8.0 * n) +
+            4.0 * L * n * info[5 * k + 1];
     }
     account(KC_TRUNC, fl, 0);
     account(KC_SVD, fj, 0);

@@ -190,12 +190,16 @@ def test_subset_step_graph_matches_host_sized(precision):
         sub.close()
     assert list(got[0][2]) == list(got[2][2])           # the same correction counts
     # FP64: the same residuals to rounding; mixed: the FP32 inner residuals round
-    # differently with the fixed widths (other split-K partitions), ~1e-7 relative,
-    # which moves the final residuals (all far below the target) by up to ~2x
+    # differently with the fixed widths (other split-K partitions), ~1e-7 relative:
+    # the last correction leaves residuals at that noise floor (1e-11 .. 5e-9,
+    # far below the target), which differ column by column by a few times; what
+    # is determined is the target and the size of the largest residual
     if precision == 0:
         assert np.allclose(got[0][1], got[2][1], rtol=1e-3, atol=1e-12)
     else:
-        assert np.all(got[2][1] <= 1e-8) and np.allclose(got[0][1], got[2][1], rtol=1.0, atol=1e-10)
+        assert np.all(got[2][1] <= 1e-8)
+        ratio = got[2][1].max() / got[0][1].max()
+        assert 0.25 <= ratio <= 4.0, ratio
     # the oracle's residuals of the graph path's columns
     ranks, rel, outer, Uh, Vh = got[2]
     inv = np.argsort(perm)
