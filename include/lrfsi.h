@@ -510,6 +510,13 @@ int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb
  * mode = -1 only queries; *previous (may be NULL) receives the old path. */
 int lrfsi_gram_path(int path, int* previous);
 
+/* lrfsi_svd_cluster: the thread-block cluster size of the truncation's Jacobi
+ * SVD (CTAs per problem): 0 (default) chooses it from the number of problems
+ * of a launch (16 up to 9 problems, 8 up to 19, 4 up to 38, else 2); 2, 4, 8
+ * or 16 force it (16 only where the device co-schedules 16-CTA clusters).
+ * A tuning knob: the results do not depend on it.  size = -1 only queries. */
+int lrfsi_svd_cluster(int size, int* previous);
+
 /* ---- Learned initial guess (not a method of the paper) -------------------
  * A multilayer perceptron maps the scaled parameters z = (mu_s, nu_f) in
  * [-1, 1]^2 to k coefficients of a POD basis of method-generated solutions:

@@ -15,6 +15,7 @@
 // products, T2 W_r) in the grouped GEMM.
 #include <cooperative_groups.h>
 
+#include <atomic>
 #include <cmath>
 
 #include "dense.h"
@@ -598,9 +599,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, in
 // columns, norms sigma): A = (Q W) (P Y)^T, so Q W holds the left and P Y the
 // (sigma-scaled) right singular vectors of A.
 // ---------------------------------------------------------------------------
-// One CTA per problem.  Aw: column-major copy of A, overwritten by the
-// reflectors (v_j in rows j.. of column j, its leading entry explicit) and by
-// R above the diagonal; Rt = R^T; tau_j; perm (A P = A[:, perm]).
+// One CTA per problem.  The matrix is worked on in shared memory when it fits
+// (kQrSmem), else in Aw.  Aw ends as the column-major reflectors (v_j in rows
+// j.. of column j, its leading entry explicit) and R above the diagonal;
+// Rt = R^T; tau_j; perm (A P = A[:, perm]).  The trailing norms of the
+// columns are recomputed exactly while each reflector is applied.
+constexpr int kQrSmem = 200 * 1024;
 __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) {
   const TruncDesc d = descs[blockIdx.x];
   if (!gate_open(d.gate)) return;
@@ -611,34 +615,37 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) 
   const int n = cols_of_C ? m : k, L = cols_of_C ? k : m;
   const TruncWork W(d.work, p, m);
   const QrWork Q(W, p, m);
-  double* A = Q.Aw;
+  extern __shared__ double qsm[];
+  const bool in_smem = (size_t)L * n * sizeof(double) <= (size_t)kQrSmem;
+  double* A = in_smem ? qsm : Q.Aw;
   const double* core = (d.sel && *d.sel) ? d.core_alt : d.core;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  __shared__ double s_val[32];
+  __shared__ double s_val[32], s_nrm[1024];
   __shared__ int s_idx[32];
   __shared__ int s_piv;
+  __shared__ double s_tau;
+  double* nrm = n <= 1024 ? s_nrm : Q.nrm;
   for (long e = tid; e < (long)L * n; e += blockDim.x) {
     const int c = (int)(e / L), i = (int)(e % L);
     A[e] = cols_of_C ? core[(size_t)i * m + c] : core[(size_t)c * m + i];
   }
   for (int c = tid; c < n; c += blockDim.x) Q.perm[c] = c;
   __syncthreads();
-  for (int j = 0; j < n; ++j) {
-    // squared norms of the trailing parts (rows j..) of the columns j..
-    for (int c = j + warp; c < n; c += nw) {
-      double t = 0;
-      for (int i = j + lane; i < L; i += 32) t = fma(A[(size_t)c * L + i], A[(size_t)c * L + i], t);
+  for (int c = warp; c < n; c += nw) {
+    double t = 0;
+    for (int i = lane; i < L; i += 32) t = fma(A[(size_t)c * L + i], A[(size_t)c * L + i], t);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == 0) Q.nrm[c] = t;
-    }
-    __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) nrm[c] = t;
+  }
+  __syncthreads();
+  for (int j = 0; j < n; ++j) {
     // pivot: the largest trailing norm (ties: the smallest column)
     {
       double best = -1.0;
       int bc = 0x7fffffff;
       for (int c = j + tid; c < n; c += blockDim.x)
-        if (Q.nrm[c] > best) { best = Q.nrm[c]; bc = c; }
+        if (nrm[c] > best) { best = nrm[c]; bc = c; }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
@@ -661,48 +668,59 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) 
       __syncthreads();
     }
     const int pv = s_piv;
-    const double sig2 = Q.nrm[pv];
+    const double sig2 = nrm[pv];
     if (pv != j) {
       for (int i = tid; i < L; i += blockDim.x) {
         const double t = A[(size_t)j * L + i];
         A[(size_t)j * L + i] = A[(size_t)pv * L + i];
         A[(size_t)pv * L + i] = t;
       }
-      if (tid == 0) {
-        const int t = Q.perm[j];
-        Q.perm[j] = Q.perm[pv];
-        Q.perm[pv] = t;
-      }
     }
     __syncthreads();
     // reflector H = I - tau v v^T with H x = alpha e_1, alpha = -sign(x_0) |x|
-    const double x0 = A[(size_t)j * L + j];
-    const double nx = sqrt(sig2);
-    double alpha = 0.0, tau = 0.0;
-    if (nx > 0.0) {
-      alpha = x0 >= 0 ? -nx : nx;
-      const double v0 = x0 - alpha;
-      tau = -1.0 / (alpha * v0);
-      __syncthreads();  // every thread has read x0
-      if (tid == 0) A[(size_t)j * L + j] = v0;
-    }
     if (tid == 0) {
+      if (pv != j) {
+        const int t = Q.perm[j];
+        Q.perm[j] = Q.perm[pv];
+        Q.perm[pv] = t;
+        nrm[pv] = nrm[j];
+      }
+      const double x0 = A[(size_t)j * L + j];
+      const double nx = sqrt(sig2);
+      double alpha = 0.0, tau = 0.0;
+      if (nx > 0.0) {
+        alpha = x0 >= 0 ? -nx : nx;
+        const double v0 = x0 - alpha;
+        tau = -1.0 / (alpha * v0);
+        A[(size_t)j * L + j] = v0;
+      }
       Q.tau[j] = tau;
       Q.Rt[(size_t)j * n + j] = alpha;
+      s_tau = tau;
     }
     __syncthreads();
-    // apply H to the columns j+1..: w = v . a_c, a_c -= tau w v (rows j..)
-    if (tau != 0.0) {
-      const double* v = A + (size_t)j * L;
-      for (int c = j + 1 + warp; c < n; c += nw) {
-        double* a = A + (size_t)c * L;
-        double t = 0;
+    // apply H to the columns j+1..: w = v . a_c, a_c -= tau w v (rows j..),
+    // and the new trailing norm of a_c (rows j+1..)
+    const double tau = s_tau;
+    const double* v = A + (size_t)j * L;
+    for (int c = j + 1 + warp; c < n; c += nw) {
+      double* a = A + (size_t)c * L;
+      double t = 0;
+      if (tau != 0.0) {
         for (int i = j + lane; i < L; i += 32) t = fma(v[i], a[i], t);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         t *= tau;
-        for (int i = j + lane; i < L; i += 32) a[i] = fma(-t, v[i], a[i]);
       }
+      double q = 0;
+      for (int i = j + lane; i < L; i += 32) {
+        const double ai = tau != 0.0 ? fma(-t, v[i], a[i]) : a[i];
+        if (tau != 0.0) a[i] = ai;
+        if (i > j) q = fma(ai, ai, q);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+      if (lane == 0) nrm[c] = q;
     }
     __syncthreads();
   }
@@ -711,6 +729,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) 
     const int c = (int)(e / n), i = (int)(e % n);
     if (i != c) Q.Rt[e] = i > c ? A[(size_t)i * L + c] : 0.0;
   }
+  if (in_smem)  // the reflectors, for the output stage of the SVD
+    for (long e = tid; e < (long)L * n; e += blockDim.x) Q.Aw[e] = A[e];
 }
 
 // ---------------------------------------------------------------------------
@@ -1052,6 +1072,12 @@ int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third) {
 // Cluster size for the SVD: the problems' clusters together should cover the
 // SMs about once (16 needs the non-portable cluster size; fall back to 8 if
 // the device cannot co-schedule it).
+static std::atomic<int> g_svd_cluster{0};  // 0: by the rule below
+int svd_cluster(int c) {
+  const int old = g_svd_cluster.load();
+  if (c >= 0) g_svd_cluster.store(c);
+  return old;
+}
 static int svd_cluster_size(int nprob, size_t smem) {
   static int max16 = -1;
   if (max16 < 0) {
@@ -1065,7 +1091,7 @@ static int svd_cluster_size(int nprob, size_t smem) {
       at[0].val.clusterDim.z = 1;
       cfg.gridDim = dim3(16, 1, 1);
       cfg.blockDim = dim3(kSvdThreads, 1, 1);
-      cfg.dynamicSmemBytes = 64 * 1024;
+      cfg.dynamicSmemBytes = 16 * 1024;  // within the default dynamic limit (48 KB)
       cfg.attrs = at;
       cfg.numAttrs = 1;
       int ncl = 0;
@@ -1074,6 +1100,9 @@ static int svd_cluster_size(int nprob, size_t smem) {
     cudaGetLastError();
   }
   (void)smem;
+  const int forced = g_svd_cluster.load();
+  if (forced == 16 && max16) return 16;
+  if (forced >= 2 && forced <= 8) return forced;
   if (nprob <= 9 && max16) return 16;
   if (nprob <= 19) return 8;
   if (nprob <= 38) return 4;
@@ -1111,7 +1140,18 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool 
   }
   account(KC_SVD, 0, 0);
   TimedLaunch tl(KC_SVD, s);
-  k_trunc_qrcp<<<n, kSmallThreads, 0, s>>>(d_dev);
+  static bool qr_attr = false;
+  if (!qr_attr) {
+    LRFSI_CUDA(cudaFuncSetAttribute(k_trunc_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, kQrSmem));
+    qr_attr = true;
+  }
+  size_t qsm = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t lo = d[i].p < d[i].m ? d[i].p : d[i].m, hi = d[i].p < d[i].m ? d[i].m : d[i].p;
+    const size_t need = lo * hi * sizeof(double);
+    if (need <= (size_t)kQrSmem && need > qsm) qsm = need;
+  }
+  k_trunc_qrcp<<<n, kSmallThreads, qsm, s>>>(d_dev);
   LRFSI_TRY(check_launch("k_trunc_qrcp"));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];

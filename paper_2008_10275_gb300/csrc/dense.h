@@ -76,6 +76,9 @@ struct TruncDesc {
   int* broke = nullptr;             // Cholesky-QR: set to 1 on a breakdown (sticky)
 };
 size_t trunc_small_work(int p, int m);
+// Cluster size of the SVD kernel: 0 = chosen from the number of problems,
+// else 2, 4, 8 or 16; c < 0 only queries.  Returns the previous setting.
+int svd_cluster(int c);
 // upload = false: d_dev already holds the n descriptors (d is still read on
 // the host for launch shapes)
 int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload = true);

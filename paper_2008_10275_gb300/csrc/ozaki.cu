@@ -664,3 +664,12 @@ extern "C" int lrfsi_gram(const double* A, int lda, int p, const double* B, int 
   if (flag) return fail(LRFSI_ENOCONV, "lrfsi_gram: a pipeline wait of the tensor-core Gram ran out");
   return LRFSI_OK;
 }
+
+extern "C" int lrfsi_svd_cluster(int size, int* previous) {
+  using namespace lrfsi;
+  if (!(size == -1 || size == 0 || size == 2 || size == 4 || size == 8 || size == 16))
+    return fail(LRFSI_EINVAL, "lrfsi_svd_cluster: size must be 0, 2, 4, 8 or 16 (or -1 to query)");
+  const int old = svd_cluster(size);
+  if (previous) *previous = old;
+  return LRFSI_OK;
+}

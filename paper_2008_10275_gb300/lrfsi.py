@@ -122,6 +122,7 @@ def load():
         "lrfsi_partition": [i, vp, i, vp],
         "lrfsi_gram": [vp, i, i, vp, i, i, C.c_int64, vp, i, vp],
         "lrfsi_gram_path": [i, vp],
+        "lrfsi_svd_cluster": [i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -228,6 +229,14 @@ def gram_path(path=-1):
     FP64 FMA; -1 queries); returns the previous path."""
     prev = C.c_int(0)
     _check(load().lrfsi_gram_path(int(path), C.byref(prev)))
+    return prev.value
+
+
+def svd_cluster(size=-1):
+    """Set the cluster size of the truncation SVD (0 automatic, 2, 4, 8, 16;
+    -1 queries); returns the previous setting."""
+    prev = C.c_int(0)
+    _check(load().lrfsi_svd_cluster(int(size), C.byref(prev)))
     return prev.value
 
 
