@@ -498,7 +498,22 @@ int lrfsi_truncate(lrfsi_subset_h sub, const double* X_dev, int ldx, const doubl
  * (G is then wrong). */
 int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb, int q, int64_t M, double* G_dev,
                int ldg, lrfsi_stream_t stream);
-/* lrfsi_gram_path: how every Gram product of the library is computed:
+/* lrfsi_gemm: C = alpha A B + beta C for row-major FP64 A (m x k, lda >= k),
+ * B (k x n, ldb >= n), C (m x n, ldc >= n); beta == 0 does not read C.  With
+ * lrfsi_gram_path 1 a tall product (m >= 2048, k <= 400) runs on the tensor
+ * cores like the Gram products: the contraction index is equilibrated (column
+ * l of A and row l of B scaled by inverse powers of two), A split by rows and
+ * B by columns into 8 BF16 digit slices, the 36 slice products of a 16-step
+ * chunk of k accumulated exactly (FP32 in tensor memory, k <= 400 keeps every
+ * level below 2^24), the 8 levels combined as two exact int64 groups and one
+ * FP64 fma; the error is below 2^-53 (|A'| |B'|) scaled by the row and column
+ * maxima, comparable to an FP64 GEMM's.  Otherwise FP64 FMA kernels.
+ * The library uses the tensor path for its tall products (the factors of the
+ * truncation, the dense residual columns).  Errors as lrfsi_gram. */
+int lrfsi_gemm(int m, int n, int k, const double* A_dev, int lda, const double* B_dev, int ldb, double* C_dev,
+               int ldc, double alpha, double beta, lrfsi_stream_t stream);
+/* lrfsi_gram_path: how every Gram product (and every tall GEMM, see lrfsi_gemm)
+ * of the library is computed:
  *   1 (default): on the BF16 tensor cores by error-free splitting (Ozaki,
  *      Ogita, Oishi, Rump 2012): each column scaled by a power of two and cut
  *      into 8 base-128 digits exact in BF16; the digit products summed over

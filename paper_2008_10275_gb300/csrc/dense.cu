@@ -16,6 +16,8 @@
 #include <cooperative_groups.h>
 
 #include <atomic>
+#include <type_traits>
+#include <vector>
 #include <cmath>
 
 #include "dense.h"
@@ -128,8 +130,60 @@ void gemm_ws_bind(void* p, size_t bytes) { t_ws_bound = p; t_ws_bound_bytes = p 
 size_t gemm_ws_peak() { return t_ws_peak; }
 void gemm_ws_peak_reset() { t_ws_peak = 0; }
 
+// workspace of a grouped-GEMM call: the bound one, else the process-wide one
+// grown on demand; records the peak need
+static int gemm_ws_get(size_t need, void** ws, size_t* bytes) {
+  if (need > t_ws_peak) t_ws_peak = need;
+  if (t_ws_bound) {
+    if (need > t_ws_bound_bytes) return fail(LRFSI_EINVAL, "gemm_grouped: bound workspace too small");
+    *ws = t_ws_bound;
+    *bytes = t_ws_bound_bytes;
+    return LRFSI_OK;
+  }
+  if (need > g_gemm_ws_bytes) {
+    if (g_gemm_ws) cudaFree(g_gemm_ws);
+    g_gemm_ws = nullptr;
+    g_gemm_ws_bytes = 0;
+    LRFSI_CUDA(cudaMalloc(&g_gemm_ws, need));
+    g_gemm_ws_bytes = need;
+  }
+  *ws = g_gemm_ws;
+  *bytes = g_gemm_ws_bytes;
+  return LRFSI_OK;
+}
+
+template <class T>
+static int gemm_grouped_simt(const GemmDesc<T>* descs, int n, cudaStream_t s);
+
 template <class T>
 int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (gram_path() == 1) {
+      std::vector<GemmDesc<double>> tcd, rest;
+      for (int i = 0; i < n; ++i) (ozaki_gemm_eligible(descs[i]) ? tcd : rest).push_back(descs[i]);
+      if (!tcd.empty()) {
+        double fl = 0, by = 0;
+        for (const GemmDesc<double>& g : tcd) {
+          if (!gate_counts(g.gate, s)) continue;
+          fl += 2.0 * g.m * g.n * g.k;
+          by += 8.0 * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != 0.0 ? 2.0 : 1.0) * g.m * g.n);
+        }
+        account(KC_GEMM, fl, by);
+        TimedLaunch tl(KC_GEMM, s);
+        void* ws = nullptr;
+        size_t wsb = 0;
+        LRFSI_TRY(gemm_ws_get(ozaki_gemm_work_bytes(tcd.data(), (int)tcd.size()), &ws, &wsb));
+        LRFSI_TRY(ozaki_gemm(tcd.data(), (int)tcd.size(), ws, wsb, s));
+        tl.end(s);
+        return rest.empty() ? LRFSI_OK : gemm_grouped_simt<double>(rest.data(), (int)rest.size(), s);
+      }
+    }
+  }
+  return gemm_grouped_simt<T>(descs, n, s);
+}
+
+template <class T>
+static int gemm_grouped_simt(const GemmDesc<T>* descs, int n, cudaStream_t s) {
   constexpr int kTarget = 2 * 152;  // enough CTAs to occupy every SM's FP64 unit twice
   for (int i = 0; i < n;) {  // chunks of up to kMaxGemmDescs non-empty products
     GemmBatch<T> gb;
@@ -173,20 +227,10 @@ int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
       if (ks < 1) ks = 1;
     }
     const long pstride = (long)mm * nn;
-    void* ws = t_ws_bound ? t_ws_bound : g_gemm_ws;
+    void* ws = nullptr;
     if (ks > 1) {
-      const size_t need = sizeof(T) * (size_t)cnt * ks * pstride;
-      if (need > t_ws_peak) t_ws_peak = need;
-      if (t_ws_bound) {
-        if (need > t_ws_bound_bytes) return fail(LRFSI_EINVAL, "gemm_grouped: bound split-K workspace too small");
-      } else if (need > g_gemm_ws_bytes) {
-        if (g_gemm_ws) cudaFree(g_gemm_ws);
-        g_gemm_ws = nullptr;
-        g_gemm_ws_bytes = 0;
-        LRFSI_CUDA(cudaMalloc(&g_gemm_ws, need));
-        g_gemm_ws_bytes = need;
-        ws = g_gemm_ws;
-      }
+      size_t wsb = 0;
+      LRFSI_TRY(gemm_ws_get(sizeof(T) * (size_t)cnt * ks * pstride, &ws, &wsb));
     }
     dim3 grid(ceil_div(nn, 32), ceil_div(mm, 32), cnt * ks);
     k_gemm<T, 32, 32><<<grid, 256, 0, s>>>(gb, ks, (T*)ws, pstride);

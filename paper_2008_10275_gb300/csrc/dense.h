@@ -19,6 +19,9 @@ struct GemmDesc {
   Gate gate;
   const T* A_alt = nullptr;
   const int* sel = nullptr;
+  // 1: a tall product (m >= 2048, k <= 400) that may run on the tensor cores
+  // (ozaki.h); set where the error bound |A| |B| is the one that matters
+  int tc = 0;
 };
 constexpr int kMaxGemmDescs = 32;
 template <class T>

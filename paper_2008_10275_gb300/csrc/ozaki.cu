@@ -137,6 +137,10 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 struct OzOp {
   const double* X;   // rows x n: entry (l, i) at X[l * rs + i * cs]
   long rs, cs;
+  long rows;         // rows (the contraction length) and
+  long nch;          // 16-row chunks of slices written (zeros beyond rows)
+  const int* lsc;    // optional per-row scale: entry (l, i) is taken times
+  int lsign;         // 2^(lsign (lsc[l] - 1022)); lsc[l] == 0: the row is zero
   const double* Xalt;  // read instead of X when sel != nullptr && *sel != 0
   const int* sel;
   int n;             // columns
@@ -197,12 +201,19 @@ __global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O,
   const OzOp& op = O.op[blockIdx.z];
   if (!gate_open(op.gate)) return;
   const double* X = (op.sel && *op.sel) ? op.Xalt : op.X;
-  const long r0 = (long)blockIdx.x * kExpRows, r1 = r0 + kExpRows < M ? r0 + kExpRows : M;
+  const long rows = op.rows;
+  (void)M;
+  const long r0 = (long)blockIdx.x * kExpRows, r1 = r0 + kExpRows < rows ? r0 + kExpRows : rows;
   const int i = blockIdx.y * 256 + threadIdx.x;
   if (i >= op.n) return;
   int mx = 0;
   for (long l = r0; l < r1; ++l) {
-    const int be = (int)((__double_as_longlong(X[l * op.rs + i * op.cs]) >> 52) & 0x7FF);
+    int be = (int)((__double_as_longlong(X[l * op.rs + i * op.cs]) >> 52) & 0x7FF);
+    if (op.lsc && be != 0 && be != 0x7FF) {
+      const int ls = op.lsc[l];
+      be = ls == 0 ? 0 : be + op.lsign * (ls - 1022);
+      be = be < 1 ? 0 : (be > 0x7FE ? 0x7FE : be);
+    }
     mx = be > mx ? be : mx;
   }
   if (mx) atomicMax(op.ex + i, mx);
@@ -211,13 +222,13 @@ __global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O,
 // The 8 balanced base-128 digits of x as a 56-bit fixed-point number in units
 // of 2^(e - 56), e = bexp_max - 1022 (so |x| < 2^e): a[0] in [-128, 128],
 // a[1..7] in [-64, 63], x = sum_t a[t] 2^(e - 7 (t + 1)) up to 2^(e - 57).
-__device__ __forceinline__ void oz_digits(double x, int bexp_max, int (&a)[kSl]) {
+__device__ __forceinline__ void oz_digits(double x, int bexp_max, int shift, int (&a)[kSl]) {
   const long long bits = __double_as_longlong(x);
   const int be = (int)((bits >> 52) & 0x7FF);
   long long v = 0;
   if (be != 0 && be != 0x7FF && bexp_max != 0x7FF) {
     const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (1LL << 52);
-    const int sh = be - 1019 - (bexp_max - 1022);  // v = mant 2^sh, sh <= 3
+    const int sh = be + shift - 1019 - (bexp_max - 1022);  // v = mant 2^sh, sh <= 3
     if (sh >= 0) v = mant << sh;
     else if (sh > -62) v = (mant + (1LL << (-sh - 1))) >> (-sh);
     if (bits < 0) v = -v;
@@ -239,7 +250,8 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps 
   const double* X = (op.sel && *op.sel) ? op.Xalt : op.X;
   const long c = blockIdx.x;
   const int t0 = blockIdx.y * 2, nt = op.nt - t0 < 2 ? op.nt - t0 : 2;
-  if (nt <= 0) return;
+  M = op.rows;
+  if (nt <= 0 || c >= op.nch) return;
   const int items = nt * kTA * 2;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int i = t0 * kTA + it % (nt * kTA), kg = it / (nt * kTA);
@@ -249,8 +261,14 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps 
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const long l = c * kChunk + kg * 8 + e;
-      const double x = (i < op.n && l < M) ? X[l * op.rs + (long)i * op.cs] : 0.0;
-      oz_digits(x, bx, dig[e]);
+      double x = (i < op.n && l < M) ? X[l * op.rs + (long)i * op.cs] : 0.0;
+      int shift = 0;
+      if (op.lsc && l < M) {
+        const int ls = op.lsc[l];
+        if (ls == 0) x = 0.0;
+        else shift = op.lsign * (ls - 1022);
+      }
+      oz_digits(x, bx, shift, dig[e]);
     }
     __nv_bfloat16* base = op.sl + ((size_t)(c * op.nt + ti) * kSl) * (kTA * kChunk) + (il >> 3) * 128 + kg * 64 +
                           (il & 7) * 8;
@@ -496,16 +514,28 @@ OzPlan plan_for(long M, int nops, long sum_nt, long T) {
 }  // namespace
 
 // exponents and slices of every operand of a launch
-static int oz_slice(const OzOps& ops, long rows, long nchunks, cudaStream_t s) {
-  int ntmax = 1, nmax = 1;
+static int oz_exp(const OzOps& ops, cudaStream_t s) {
+  int nmax = 1;
+  long rmax = 1;
+  for (int o = 0; o < ops.cnt; ++o) {
+    nmax = ops.op[o].n > nmax ? ops.op[o].n : nmax;
+    rmax = ops.op[o].rows > rmax ? ops.op[o].rows : rmax;
+  }
+  k_oz_exp<<<dim3((unsigned)ceil_div_l(rmax, kExpRows), (unsigned)ceil_div_l(nmax, 256), ops.cnt), 256, 0, s>>>(ops,
+                                                                                                          rmax);
+  return check_launch("k_oz_exp");
+}
+// exponents and slices of every operand of a launch
+static int oz_slice(const OzOps& ops, cudaStream_t s) {
+  LRFSI_TRY(oz_exp(ops, s));
+  int ntmax = 1;
+  long rmax = 1, cmax = 1;
   for (int o = 0; o < ops.cnt; ++o) {
     ntmax = ops.op[o].nt > ntmax ? ops.op[o].nt : ntmax;
-    nmax = ops.op[o].n > nmax ? ops.op[o].n : nmax;
+    rmax = ops.op[o].rows > rmax ? ops.op[o].rows : rmax;
+    cmax = ops.op[o].nch > cmax ? ops.op[o].nch : cmax;
   }
-  k_oz_exp<<<dim3((unsigned)ceil_div_l(rows, kExpRows), (unsigned)ceil_div_l(nmax, 256), ops.cnt), 256, 0, s>>>(ops,
-                                                                                                          rows);
-  LRFSI_TRY(check_launch("k_oz_exp"));
-  k_oz_split<<<dim3((unsigned)nchunks, (unsigned)ceil_div_l(ntmax, 2), ops.cnt), 256, 0, s>>>(ops, rows);
+  k_oz_split<<<dim3((unsigned)cmax, (unsigned)ceil_div_l(ntmax, 2), ops.cnt), 256, 0, s>>>(ops, rmax);
   return check_launch("k_oz_split");
 }
 
@@ -561,14 +591,14 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
       OzProd& pr = P.pr[b];
       pr.a = ops.cnt;
       OzOp& oa = ops.op[ops.cnt++];
-      oa.X = g.A; oa.rs = g.lda; oa.cs = 1; oa.n = g.p; oa.nt = (int)ceil_div_l(g.p, kTA); oa.gate = g.gate;
+      oa.X = g.A; oa.rs = g.lda; oa.cs = 1; oa.rows = M; oa.nch = (long)ceil_div_l(M, kWin) * kChunksPerWin; oa.n = g.p; oa.nt = (int)ceil_div_l(g.p, kTA); oa.gate = g.gate;
       sum_nt += oa.nt;
       if (sym) {
         pr.b = pr.a;
       } else {
         pr.b = ops.cnt;
         OzOp& ob = ops.op[ops.cnt++];
-        ob.X = g.B; ob.rs = g.ldb; ob.cs = 1; ob.n = g.q; ob.nt = (int)ceil_div_l(g.q, kTA); ob.gate = g.gate;
+        ob.X = g.B; ob.rs = g.ldb; ob.cs = 1; ob.rows = M; ob.nch = (long)ceil_div_l(M, kWin) * kChunksPerWin; ob.n = g.q; ob.nt = (int)ceil_div_l(g.q, kTA); ob.gate = g.gate;
         sum_nt += ob.nt;
       }
       pr.ntb = (int)ceil_div_l(g.q, kTB);
@@ -614,7 +644,7 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
     TimedLaunch tl(KC_GRAM, s);
     LRFSI_CUDA(cudaMemsetAsync(ex, 0, pl.ex_bytes, s));
     LRFSI_CUDA(cudaMemsetAsync(part, 0, pl.part_bytes, s));
-    LRFSI_TRY(oz_slice(ops, M, pl.nchunks, s));
+    LRFSI_TRY(oz_slice(ops, s));
     if (first > 0) {
       k_oz_gram<<<first, kGramThreads, kStages * kStageBytes, s>>>(P, g_oz_err);
       LRFSI_TRY(check_launch("k_oz_gram"));
@@ -671,5 +701,283 @@ extern "C" int lrfsi_svd_cluster(int size, int* previous) {
     return fail(LRFSI_EINVAL, "lrfsi_svd_cluster: size must be 0, 2, 4, 8 or 16 (or -1 to query)");
   const int old = svd_cluster(size);
   if (previous) *previous = old;
+  return LRFSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Tall FP64 GEMMs C = alpha A B + beta C on the tensor cores (contraction
+// K <= kOzMaxK: one exact window).  A is sliced by rows (A^T as the operand,
+// one exponent per row of A over K), B by columns; the 8 levels of an entry
+// are combined as two exact int64 groups (levels 0-3 and 4-7, each below
+// 2^45.1) and one FP64 fma.  Used for the products whose left factor has
+// orthonormal or comparable columns (the caller marks them, GemmDesc::tc):
+// there the error follows |A| |B| like that of an FP64 GEMM.
+// ---------------------------------------------------------------------------
+namespace lrfsi {
+namespace {
+constexpr int kOzMaxK = 400;      // level sums over <= 409 rows stay below 2^24
+constexpr int kGStages = 2;
+constexpr int kGThreads = 288;
+struct OzG {
+  int a, b;          // operand indices: a = A^T (rows K, columns = rows of A), b = B
+  int m, n, k;
+  int ntn;           // 32-column tiles of C
+  int first;         // first CTA (row tile major)
+  double* C;
+  long c_rs, c_cs;
+  double alpha, beta;
+  Gate gate;
+};
+struct OzGs {
+  OzG g[kMaxOz];
+  OzOp op[2 * kMaxOz];
+  int cnt;
+};
+}  // namespace
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
+               : "r"(taddr)
+               : "memory");
+}
+
+// CTA = (GEMM, 128 x 32 tile of C).  Warp 8 lane 0 issues the bulk copies and
+// the 36 MMAs per 16-row chunk of K into 8 level accumulators (256 tensor-
+// memory columns); warps 0-7 read all 8 levels of 8 columns at a time (warp w:
+// lanes 32 (w % 4) .., columns 16 (w / 4) ..) and write C.
+__global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ OzGs P, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], done, fin;
+  __shared__ uint32_t s_tmem;
+  const int cta = blockIdx.x;
+  int gi = 0;
+  while (gi + 1 < P.cnt && cta >= P.g[gi + 1].first) ++gi;
+  const OzG& G = P.g[gi];
+  if (!gate_open(G.gate)) return;
+  const int t = cta - G.first, ta = t / G.ntn, tb = t % G.ntn;
+  const OzOp& A = P.op[G.a];
+  const OzOp& B = P.op[G.b];
+  const int nch = (G.k + kChunk - 1) / kChunk;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kGStages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(&done, 1);
+    mbar_init(&fin, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 256;" ::"r"(sm_addr(&s_tmem))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = s_tmem;
+  if (warp == 8) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = mma_idesc(kTA, kTB);
+      auto load = [&](int c) {
+        const int st = c % kGStages;
+        unsigned char* sa = smem + (size_t)st * kStageBytes;
+        unsigned char* sb = sa + kABytes;
+        const __nv_bfloat16* ga = A.sl + ((size_t)c * A.nt + ta) * kSl * (kTA * kChunk);
+        const __nv_bfloat16* gb = B.sl + ((size_t)c * B.nt + tb / 4) * kSl * (kTA * kChunk) + (tb % 4) * (kTB * kChunk);
+        mbar_expect_tx(&full[st], kStageBytes);
+        bulk_g2s(sa, ga, kABytes, &full[st]);
+        for (int u = 0; u < kSl; ++u) bulk_g2s(sb + u * (kTB * kChunk * 2), gb + u * (kTA * kChunk), kTB * kChunk * 2, &full[st]);
+      };
+      int issued = 0, consumed = 0;
+      for (; issued < nch && issued < kGStages; ++issued) load(issued);
+      bool ok = true;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int st = c % kGStages;
+        if (!mbar_wait(&full[st], (uint32_t)(c / kGStages) & 1)) { ok = false; break; }
+        consumed = c + 1;
+        tc_fence_after();
+        const uint32_t sa = sm_addr(smem + (size_t)st * kStageBytes), sb = sa + kABytes;
+        const uint64_t a0 = sm_desc(sa, 128, 256), b0 = sm_desc(sb, 128, 256);
+        const uint32_t acc0 = c == 0 ? 0u : 1u;
+#pragma unroll
+        for (int lv = 0; lv < kLv; ++lv) {
+#pragma unroll
+          for (int u = 0; u <= lv; ++u)
+            mma_bf16(tmem + lv * kTB, a0 + (uint64_t)(u * ((kTA * kChunk * 2) >> 4)),
+                     b0 + (uint64_t)((lv - u) * ((kTB * kChunk * 2) >> 4)), idesc, u == 0 ? acc0 : 1u);
+        }
+        mma_commit(&empty[st]);
+        if (c == nch - 1) mma_commit(&done);
+        if (c >= 1 && issued < nch) {
+          const int ps = (c - 1) % kGStages;
+          if (!mbar_wait(&empty[ps], (uint32_t)((c - 1) / kGStages) & 1)) { ok = false; break; }
+          load(issued++);
+        }
+      }
+      if (!ok) atomicExch(err, 1);
+      mma_commit(&fin);
+      mbar_wait(&fin, 0);
+      for (int c = consumed; c < issued; ++c) mbar_wait(&full[c % kGStages], (uint32_t)(c / kGStages) & 1);
+    }
+  } else {
+    const int q = warp & 3, h = warp >> 2;
+    int ok = 1;
+    if (lane == 0) ok = mbar_wait(&done, 0) ? 1 : 0;
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    if (!ok) {
+      if (lane == 0) atomicExch(err, 1);
+    } else {
+      tc_fence_after();
+      const int i = ta * kTA + 32 * q + lane;
+      const int ea = i < G.m ? A.ex[i] : 0;
+#pragma unroll 1
+      for (int half = 0; half < 2; ++half) {
+        const int jc = 16 * h + 8 * half;  // first column of these 8 in the tile
+        uint32_t v[kLv][8];
+#pragma unroll
+        for (int lv = 0; lv < kLv; ++lv)
+          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lv * kTB + jc), v[lv]);
+        if (i < G.m) {
+#pragma unroll
+          for (int jj = 0; jj < 8; ++jj) {
+            const int j = tb * kTB + jc + jj;
+            if (j >= G.n) continue;
+            const int eb = B.ex[j];
+            double val;
+            if (ea == 0x7FF || eb == 0x7FF) {
+              val = __longlong_as_double(0x7FF8000000000000LL);
+            } else {
+              long long Hs = 0, Ls = 0;
+#pragma unroll
+              for (int lv = 0; lv < 4; ++lv) Hs = Hs * 128 + __float2int_rn(__uint_as_float(v[lv][jj]));
+#pragma unroll
+              for (int lv = 4; lv < 8; ++lv) Ls = Ls * 128 + __float2int_rn(__uint_as_float(v[lv][jj]));
+              const int sc = (ea ? ea - 1022 : 0) + (eb ? eb - 1022 : 0);
+              val = ldexp(fma((double)Ls, 0x1p-28, (double)Hs), sc - 35);
+            }
+            double* cp = G.C + (size_t)i * G.c_rs + (size_t)j * G.c_cs;
+            *cp = G.beta != 0.0 ? fma(G.alpha, val, G.beta * *cp) : G.alpha * val;
+          }
+        }
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
+  }
+}
+
+bool ozaki_gemm_eligible(const GemmDesc<double>& g) {
+  return gram_path() == 1 && g.tc && g.m >= 2048 && g.k >= 1 && g.k <= kOzMaxK && g.n >= 1;
+}
+
+namespace {
+// bytes of the operands of GEMMs d[0..cnt) (exponents + slices), 256-aligned pieces
+size_t gemm_ops_bytes(const GemmDesc<double>* d, int cnt) {
+  size_t b = 0;
+  for (int i = 0; i < cnt; ++i) {
+    const long nch = ceil_div_l(d[i].k, kChunk);
+    const long nta = ceil_div_l(d[i].m, kTA), ntb = ceil_div_l(d[i].n, kTA);
+    b += round256(sizeof(int) * ((size_t)(nta + ntb) * kTA + d[i].k));
+    b += round256((size_t)nch * nta * kSl * kTA * kChunk * 2) + round256((size_t)nch * ntb * kSl * kTA * kChunk * 2);
+  }
+  return b;
+}
+}  // namespace
+
+size_t ozaki_gemm_work_bytes(const GemmDesc<double>* d, int n) {
+  size_t mx = 0;
+  for (int base = 0; base < n; base += kMaxOz) {
+    const int cnt = n - base < kMaxOz ? n - base : kMaxOz;
+    const size_t b = gemm_ops_bytes(d + base, cnt);
+    mx = b > mx ? b : mx;
+  }
+  return mx + 1024;
+}
+
+int ozaki_gemm(const GemmDesc<double>* d, int n, void* work, size_t work_bytes, cudaStream_t s) {
+  static bool attr = false;
+  if (!attr) {
+    LRFSI_CUDA(cudaFuncSetAttribute(k_oz_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, kGStages * kStageBytes));
+    attr = true;
+  }
+  if (!g_oz_err) {
+    LRFSI_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
+    LRFSI_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+  }
+  for (int base = 0; base < n; base += kMaxOz) {
+    const int cnt = n - base < kMaxOz ? n - base : kMaxOz;
+    if (gemm_ops_bytes(d + base, cnt) > work_bytes) return fail(LRFSI_EINVAL, "tensor-core GEMM: workspace too small");
+    OzOps ops{}, eops{};
+    OzGs P{};
+    P.cnt = cnt;
+    unsigned char* w = (unsigned char*)work;
+    size_t off = 0;
+    int first = 0;
+    for (int b = 0; b < cnt; ++b) {
+      const GemmDesc<double>& g = d[base + b];
+      const long nch = ceil_div_l(g.k, kChunk);
+      // the contraction index is equilibrated: column k of A is scaled by a
+      // power of two to a largest entry in [1/2, 1), row k of B by the inverse
+      OzOp& oe = eops.op[eops.cnt++];
+      oe.X = g.A; oe.Xalt = g.A_alt; oe.sel = g.sel; oe.rs = g.a_rs; oe.cs = g.a_cs; oe.rows = g.m; oe.nch = 0;
+      oe.n = g.k; oe.nt = 0; oe.gate = g.gate;
+      OzOp& oa = ops.op[ops.cnt];
+      oa.X = g.A; oa.Xalt = g.A_alt; oa.sel = g.sel; oa.rs = g.a_cs; oa.cs = g.a_rs; oa.rows = g.k; oa.nch = nch;
+      oa.n = g.m; oa.nt = (int)ceil_div_l(g.m, kTA); oa.gate = g.gate;
+      OzOp& ob = ops.op[ops.cnt + 1];
+      ob.X = g.B; ob.rs = g.b_rs; ob.cs = g.b_cs; ob.rows = g.k; ob.nch = nch;
+      ob.n = g.n; ob.nt = (int)ceil_div_l(g.n, kTA); ob.gate = g.gate;
+      oe.ex = (int*)(w + off);
+      oa.ex = oe.ex + g.k;
+      ob.ex = oa.ex + (size_t)oa.nt * kTA;
+      oa.lsc = ob.lsc = oe.ex;
+      oa.lsign = -1;
+      ob.lsign = 1;
+      LRFSI_CUDA(cudaMemsetAsync(oe.ex, 0, sizeof(int) * ((size_t)(oa.nt + ob.nt) * kTA + g.k), s));
+      off += round256(sizeof(int) * ((size_t)(oa.nt + ob.nt) * kTA + g.k));
+      oa.sl = (__nv_bfloat16*)(w + off);
+      off += round256((size_t)nch * oa.nt * kSl * kTA * kChunk * 2);
+      ob.sl = (__nv_bfloat16*)(w + off);
+      off += round256((size_t)nch * ob.nt * kSl * kTA * kChunk * 2);
+      OzG& G = P.g[b];
+      G.a = ops.cnt; G.b = ops.cnt + 1;
+      ops.cnt += 2;
+      G.m = g.m; G.n = g.n; G.k = g.k;
+      G.ntn = (int)ceil_div_l(g.n, kTB);
+      G.first = first;
+      first += (int)ceil_div_l(g.m, kTA) * G.ntn;
+      G.C = g.C; G.c_rs = g.c_rs; G.c_cs = g.c_cs; G.alpha = g.alpha; G.beta = g.beta; G.gate = g.gate;
+    }
+    for (int o = 0; o < ops.cnt; ++o) P.op[o] = ops.op[o];
+    LRFSI_TRY(oz_exp(eops, s));   // column maxima of A (the contraction scales)
+    LRFSI_TRY(oz_slice(ops, s));
+    if (first > 0) {
+      k_oz_gemm<<<first, kGThreads, kGStages * kStageBytes, s>>>(P, g_oz_err);
+      LRFSI_TRY(check_launch("k_oz_gemm"));
+    }
+  }
+  return LRFSI_OK;
+}
+}  // namespace lrfsi
+
+extern "C" int lrfsi_gemm(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
+                          double alpha, double beta, lrfsi_stream_t stream) {
+  using namespace lrfsi;
+  if (!A || !B || !C || m < 1 || n < 1 || k < 1 || lda < k || ldb < n || ldc < n)
+    return fail(LRFSI_EINVAL, "lrfsi_gemm: bad argument (m, n, k >= 1, lda >= k, ldb >= n, ldc >= n)");
+  cudaStream_t s = (cudaStream_t)stream;
+  GemmDesc<double> g{m, n, k, A, lda, 1, B, ldb, 1, C, ldc, 1, alpha, beta};
+  g.tc = 1;
+  LRFSI_TRY(gemm_grouped<double>(&g, 1, s));
+  int flag = 0;
+  LRFSI_TRY(ozaki_error(s, &flag));
+  if (flag) return fail(LRFSI_ENOCONV, "lrfsi_gemm: a pipeline wait of the tensor-core GEMM ran out");
   return LRFSI_OK;
 }

@@ -30,6 +30,11 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
 // call (the products of that launch are wrong); synchronises the stream.
 int ozaki_error(cudaStream_t s, int* flag);
 
+// Tall GEMMs on the tensor cores (GemmDesc::tc, m >= 2048, 1 <= k <= 400).
+bool ozaki_gemm_eligible(const GemmDesc<double>& g);
+size_t ozaki_gemm_work_bytes(const GemmDesc<double>* d, int n);
+int ozaki_gemm(const GemmDesc<double>* d, int n, void* work, size_t work_bytes, cudaStream_t s);
+
 // Gram product path: 1 = tensor cores (this file), 0 = FP64 SIMT kernels.
 int gram_path();
 void set_gram_path(int p);

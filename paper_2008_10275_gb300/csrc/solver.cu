@@ -572,6 +572,7 @@ extern "C" int lrfsi_residual(lrfsi_mesh_h m, const double* xt, const double* U,
   }
   if (r > 0) {
     GemmDesc<double> g{(int)M, ncol, r, U, ldu, 1, V, 1, ldv, X.p, ncol, 1, 1.0, 1.0};
+    g.tc = 1;
     LRFSI_TRY(gemm_grouped<double>(&g, 1, s));
   }
   ResidualCtx c;
@@ -1044,6 +1045,7 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     const TruncWork W(td[a].work, p[k], S->m[k]);
     gm[a] = GemmDesc<double>{(int)M, p[k], p[k], S->tall(S->Xcat, k, ldP), ldP, 1, td[a].T1, p[k], 1,
                              S->tall(S->Q1, k, ldP), ldP, 1, 1.0, 0.0};
+    gm[a].tc = 1;
     gy.push_back(gm[a]);
     gy.push_back(GemmDesc<double>{p[k], S->m[k], p[k], W.Rk, p[k], 1, td[a].Vc, 1, td[a].ldv, W.Y, S->m[k], 1, 1.0,
                                   0.0});
@@ -1089,6 +1091,7 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
       const TruncWork W(td[a].work, p[k], S->m[k]);
       g2.push_back(GemmDesc<double>{(int)M, kk, kk, S->tall(S->Q1, k, ldP), ldP, 1, td[a].T2, p[k], 1,
                                     S->tall(S->Q2, k, ldP), ldP, 1, 1.0, 0.0});
+      g2.back().tc = 1;
       gd2.push_back(GramDesc{S->tall(S->Q2, k, ldP), ldP, kk, S->tall(S->Q2, k, ldP), ldP, kk, td[a].G2, p[k]});
       g3.push_back(GemmDesc<double>{p[k], S->m[k], p[k], W.Rki, p[k], 1, W.C, S->m[k], 1, W.Y, S->m[k], 1, 1.0, 0.0});
       td[a].core = W.Y;
@@ -1169,6 +1172,7 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     const double* Qlast = third[k] ? S->tall(S->Q2, k, ldP) : S->tall(S->Q1, k, ldP);
     gm[a] = GemmDesc<double>{(int)M, rank[k], info[5 * k], Qlast, ldP, 1, td[a].T1, p[k], 1, Uout[k], ldR, 1, 1.0,
                              0.0};
+    gm[a].tc = 1;
   }
   LRFSI_TRY(gemm_grouped<double>(gm.data(), na, s));
   return LRFSI_OK;
@@ -1566,6 +1570,7 @@ static int lr_residual(lrfsi_subset_s* S, const lrfsi_cheb_options& o, const std
       }
       gm.push_back(GemmDesc<double>{(int)M, m, (S->four ? 5 : 3) * r, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X,
                                     ldP, 1, -1.0, 1.0});
+      gm.back().tc = 1;
     }
     cd2.push_back(CopyDesc{nullptr, 0, Vc, ldP, m, m, 2, nullptr, 1.0});
     p[k] = m;
@@ -1902,6 +1907,7 @@ static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
     g1.push_back(g);
     GemmDesc<double> a{(int)M, p, p, X, ldP, 1, d.T1, p, 1, Q1, ldP, 1, 1.0, 0.0};
     a.gate = live;
+    a.tc = 1;
     q1y.push_back(a);
     GemmDesc<double> b{p, m, p, W.Rk, p, 1, d.Vc, 1, d.ldv, W.Y, m, 1, 1.0, 0.0};
     b.gate = live;
@@ -1914,6 +1920,7 @@ static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
     c2.push_back(c);
     GemmDesc<double> e{(int)M, p, p, Q1, ldP, 1, d.T2, p, 1, Q2, ldP, 1, 1.0, 0.0};
     e.gate = third;
+    e.tc = 1;
     q2.push_back(e);
     g = GramDesc{Q2, ldP, p, Q2, ldP, p, d.G2, p};
     g.gate = third;
@@ -1926,6 +1933,7 @@ static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
     t1.push_back(t);
     GemmDesc<double> u{(int)M, w, p, Q1, ldP, 1, d.T1, p, 1, Uout, ldR, 1, 1.0, 0.0};
     u.gate = live;
+    u.tc = 1;
     u.A_alt = Q2;
     u.sel = d.info + 4;
     uo.push_back(u);
@@ -2015,6 +2023,7 @@ static int residual_fixed(lrfsi_subset_s* S, const lrfsi_cheb_options& o, cudaSt
       }
       GemmDesc<double> g{(int)M, m, kc, S->tall(S->Q1, k, ldP), ldP, 1, Vc, 1, ldP, X, ldP, 1, -1.0, 1.0};
       g.gate = live;
+      g.tc = 1;
       gm.push_back(g);
     } else {  // B - F(S) with an FP32 SpMM and GEMM, widened to FP64 for the truncation
       float* Uf = S->USf.p + (size_t)k * M * ldR;
@@ -2685,6 +2694,7 @@ static int lowrank_solve(lrfsi_subset_h S, const double* UB, int lduB, const dou
     // dense B_k = UB_k VB_k^T (M x m_k)
     gm.push_back(GemmDesc<double>{(int)M, S->m[k], rB[k], UB + (size_t)k * M * lduB, lduB, 1,
                                   VB + (size_t)S->off[k] * ldvB, 1, ldvB, S->tall(S->UB, k, ldR), ldR, 1, 1.0, 0.0});
+    gm.back().tc = 1;
   }
   LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
   {
@@ -2777,6 +2787,7 @@ static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, dou
       if (rC[k] > 0)
         gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
                                       S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
+        gm.back().tc = 1;
       else
         LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
     }
@@ -3012,6 +3023,7 @@ extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options
       if (rC[k] > 0)
         gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
                                       S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
+        gm.back().tc = 1;
       else
         LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
     }

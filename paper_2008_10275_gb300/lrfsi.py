@@ -123,6 +123,7 @@ def load():
         "lrfsi_gram": [vp, i, i, vp, i, i, C.c_int64, vp, i, vp],
         "lrfsi_gram_path": [i, vp],
         "lrfsi_svd_cluster": [i, vp],
+        "lrfsi_gemm": [i, i, i, vp, i, vp, i, vp, i, d, d, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -230,6 +231,12 @@ def gram_path(path=-1):
     prev = C.c_int(0)
     _check(load().lrfsi_gram_path(int(path), C.byref(prev)))
     return prev.value
+
+
+def lrfsi_gemm(m, n, k, A, lda, B, ldb, C, ldc, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha A B + beta C for row-major device matrices (tensor cores for tall products)."""
+    _check(load().lrfsi_gemm(int(m), int(n), int(k), _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, float(alpha),
+                             float(beta), _stream(stream)))
 
 
 def svd_cluster(size=-1):
