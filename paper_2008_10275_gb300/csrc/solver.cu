@@ -2784,11 +2784,11 @@ static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, dou
     // X = xt 1^T + diag(c) U_C V_C^T (dense columns, M x mtot) and its nonlinear residual
     std::vector<GemmDesc<double>> gm;
     for (int k = 0; k < K; ++k) {
-      if (rC[k] > 0)
+      if (rC[k] > 0) {
         gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
                                       S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
         gm.back().tc = 1;
-      else
+      } else
         LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
     }
     if (!gm.empty()) LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
@@ -3020,11 +3020,11 @@ extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options
   {
     std::vector<GemmDesc<double>> gm;
     for (int k = 0; k < K; ++k) {
-      if (rC[k] > 0)
+      if (rC[k] > 0) {
         gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
                                       S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
         gm.back().tc = 1;
-      else
+      } else
         LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
     }
     if (!gm.empty()) LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
