@@ -4,10 +4,10 @@ FP64 FMA kernels).
 
 * integer-valued factors: the exact product on both paths;
 * random factors with columns of A graded over 12 orders of magnitude and the
-  rows of B graded inversely (the structure of X R^-1 in the truncation): the
-  product within 2^-48 (|A| |B|) of extended precision;
+  rows of B graded inversely (the structure of X R^-1 in the truncation) and
 * an orthonormal-by-graded product (U V^T with V carrying singular values
-  1 .. 1e-10, the dense residual columns): within 2^-48 (|A| |B|);
+  1 .. 1e-10, the dense residual columns):
+  within the error bound of each path against extended precision (_bound);
 * alpha, beta and ragged sizes (m not a multiple of 128, n of 32, k of 16).
 """
 import numpy as np
@@ -59,6 +59,21 @@ def _ref(A, B, C0, alpha, beta):
     return (L(alpha) * (A.astype(L) @ B.astype(L)) + L(beta) * C0.astype(L))
 
 
+def _bound(A, B, C0, alpha, beta, path):
+    """FP64 path: 2^-48 |alpha| (|A| |B|) + 2^-52 |beta C0|.  Tensor path, the
+    error bound of the splitting: with the contraction index equilibrated
+    (column l of A over 2^e_l, row l of B times 2^e_l, e_l the exponent above
+    the column's largest entry), each entry rounded to 56 bits of its row or
+    column maximum and the digit levels t + u >= 8 dropped, a term is off by
+    at most 2^-50.7 rmax_i cmax_j: 2^-50 k rmax_i cmax_j |alpha| in total."""
+    if path == 0:
+        return 2.0 ** -48 * abs(alpha) * (np.abs(A) @ np.abs(B)) + 2.0 ** -52 * np.abs(beta * C0)
+    e = np.frexp(np.abs(A).max(axis=0))[1].astype(np.float64)
+    Ap, Bp = A * 2.0 ** -e, B * 2.0 ** e[:, None]
+    rmax, cmax = np.abs(Ap).max(axis=1), np.abs(Bp).max(axis=0)
+    return 2.0 ** -50 * A.shape[1] * abs(alpha) * np.outer(rmax, cmax) + 2.0 ** -52 * np.abs(beta * C0)
+
+
 @pytest.mark.parametrize("path", [1, 0])
 def test_gemm_graded_contraction(path):
     """Columns of A from 1 to 1e-12, rows of B the inverse (X R^-1)."""
@@ -70,7 +85,7 @@ def test_gemm_graded_contraction(path):
     C0 = rng.standard_normal((m, n))
     C = _gemm(A, B, C0, -1.0, 1.0, path)
     err = np.abs(C.astype(np.longdouble) - _ref(A, B, C0, -1.0, 1.0)).astype(np.float64)
-    bound = 2.0 ** -48 * (np.abs(A) @ np.abs(B) + np.abs(C0))
+    bound = _bound(A, B, C0, -1.0, 1.0, path)
     assert np.all(err <= bound), (err / bound).max()
 
 
@@ -83,5 +98,5 @@ def test_gemm_orthonormal_times_graded(path):
     Vt = np.linalg.qr(rng.standard_normal((n, k)))[0].T * np.logspace(0, -10, k)[:, None]
     C = _gemm(U, Vt, np.zeros((m, n)), 2.0, 0.0, path)
     err = np.abs(C.astype(np.longdouble) - _ref(U, Vt, np.zeros((m, n)), 2.0, 0.0)).astype(np.float64)
-    bound = 2.0 ** -48 * 2.0 * (np.abs(U) @ np.abs(Vt))
+    bound = _bound(U, Vt, np.zeros((m, n)), 2.0, 0.0, path)
     assert np.all(err <= bound), (err / bound).max()
