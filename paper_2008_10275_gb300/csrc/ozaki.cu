@@ -116,18 +116,20 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// 32 consecutive FP32 columns of this thread's tensor-memory lane
+// 32 consecutive FP32 columns of this thread's tensor-memory lane, loaded and
+// waited for in one statement (the registers are valid only after
+// tcgen05.wait::ld)
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
         "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
         "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
         "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
       : "r"(taddr)
       : "memory");
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -735,11 +737,24 @@ struct OzGs {
 };
 }  // namespace
 
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&v)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
-               : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7])
-               : "r"(taddr)
-               : "memory");
+// 8 consecutive FP32 columns of this thread's lane at 4 column offsets (4
+// levels), loaded and waited for in one statement (the registers are valid
+// only after tcgen05.wait::ld)
+__device__ __forceinline__ void tmem_ld8x4(uint32_t t0, uint32_t t1, uint32_t t2, uint32_t t3,
+                                           uint32_t (&v)[4][8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%32];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%33];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%16,%17,%18,%19,%20,%21,%22,%23}, [%34];\n\t"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%24,%25,%26,%27,%28,%29,%30,%31}, [%35];\n\t"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(v[0][0]), "=r"(v[0][1]), "=r"(v[0][2]), "=r"(v[0][3]), "=r"(v[0][4]), "=r"(v[0][5]), "=r"(v[0][6]),
+        "=r"(v[0][7]), "=r"(v[1][0]), "=r"(v[1][1]), "=r"(v[1][2]), "=r"(v[1][3]), "=r"(v[1][4]), "=r"(v[1][5]),
+        "=r"(v[1][6]), "=r"(v[1][7]), "=r"(v[2][0]), "=r"(v[2][1]), "=r"(v[2][2]), "=r"(v[2][3]), "=r"(v[2][4]),
+        "=r"(v[2][5]), "=r"(v[2][6]), "=r"(v[2][7]), "=r"(v[3][0]), "=r"(v[3][1]), "=r"(v[3][2]), "=r"(v[3][3]),
+        "=r"(v[3][4]), "=r"(v[3][5]), "=r"(v[3][6]), "=r"(v[3][7])
+      : "r"(t0), "r"(t1), "r"(t2), "r"(t3)
+      : "memory");
 }
 
 // CTA = (GEMM, 128 x 32 tile of C).  Warp 8 lane 0 issues the bulk copies and
@@ -837,9 +852,10 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
       for (int half = 0; half < 2; ++half) {
         const int jc = 16 * h + 8 * half;  // first column of these 8 in the tile
         uint32_t v[kLv][8];
-#pragma unroll
-        for (int lv = 0; lv < kLv; ++lv)
-          tmem_ld8(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(lv * kTB + jc), v[lv]);
+        const uint32_t tl = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)jc;
+        tmem_ld8x4(tl, tl + kTB, tl + 2 * kTB, tl + 3 * kTB, *reinterpret_cast<uint32_t(*)[4][8]>(&v[0][0]));
+        tmem_ld8x4(tl + 4 * kTB, tl + 5 * kTB, tl + 6 * kTB, tl + 7 * kTB,
+                   *reinterpret_cast<uint32_t(*)[4][8]>(&v[4][0]));
         if (i < G.m) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {

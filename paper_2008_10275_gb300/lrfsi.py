@@ -235,6 +235,9 @@ def gram_path(path=-1):
 
 def lrfsi_gemm(m, n, k, A, lda, B, ldb, C, ldc, alpha=1.0, beta=0.0, stream=None):
     """C = alpha A B + beta C for row-major device matrices (tensor cores for tall products)."""
+    for t in (A, B, C):
+        if not t.is_contiguous():
+            raise ValueError("lrfsi_gemm: A, B and C must be row-major contiguous tensors")
     _check(load().lrfsi_gemm(int(m), int(n), int(k), _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, float(alpha),
                              float(beta), _stream(stream)))
 

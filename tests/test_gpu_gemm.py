@@ -35,9 +35,10 @@ def _gemm(A, B, C0, alpha, beta, path):
     lrfsi.gram_path(path)
     m, k = A.shape
     n = B.shape[1]
-    Ad = torch.tensor(A, dtype=torch.float64, device=DEV)
-    Bd = torch.tensor(B, dtype=torch.float64, device=DEV)
-    Cd = torch.tensor(C0, dtype=torch.float64, device=DEV)
+    # row-major device copies (torch.tensor keeps the order of a transposed array)
+    Ad = torch.tensor(np.ascontiguousarray(A), dtype=torch.float64, device=DEV)
+    Bd = torch.tensor(np.ascontiguousarray(B), dtype=torch.float64, device=DEV)
+    Cd = torch.tensor(np.ascontiguousarray(C0), dtype=torch.float64, device=DEV)
     lrfsi.lrfsi_gemm(m, n, k, Ad, k, Bd, n, Cd, n, alpha, beta)
     torch.cuda.synchronize()
     return Cd.cpu().numpy()
