@@ -508,8 +508,10 @@ int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb
  * level below 2^24), the 8 levels combined as two exact int64 groups and one
  * FP64 fma; the error is below 2^-53 (|A'| |B'|) scaled by the row and column
  * maxima, comparable to an FP64 GEMM's.  Otherwise FP64 FMA kernels.
- * The library uses the tensor path for its tall products (the factors of the
- * truncation, the dense residual columns).  Errors as lrfsi_gram. */
+ * The library uses the tensor path for the tall products inside ChebyshevT
+ * and GMREST (the truncation's bases and outputs, B - F(S), the right-hand
+ * side); the dense columns whose nonlinear residuals are reported are formed
+ * by the FP64 kernels.  Errors as lrfsi_gram. */
 int lrfsi_gemm(int m, int n, int k, const double* A_dev, int lda, const double* B_dev, int ldb, double* C_dev,
                int ldc, double alpha, double beta, lrfsi_stream_t stream);
 /* lrfsi_gram_path: how every Gram product (and every tall GEMM, see lrfsi_gemm)

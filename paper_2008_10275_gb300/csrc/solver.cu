@@ -571,8 +571,8 @@ extern "C" int lrfsi_residual(lrfsi_mesh_h m, const double* xt, const double* U,
     LRFSI_TRY(copy_batched(cd, s));
   }
   if (r > 0) {
+    // FP64 kernels: the columns whose residual is reported (no tensor path)
     GemmDesc<double> g{(int)M, ncol, r, U, ldu, 1, V, 1, ldv, X.p, ncol, 1, 1.0, 1.0};
-    g.tc = 1;
     LRFSI_TRY(gemm_grouped<double>(&g, 1, s));
   }
   ResidualCtx c;
@@ -2784,11 +2784,10 @@ static int outer_corrections(lrfsi_subset_s* S, const lrfsi_cheb_options& o, dou
     // X = xt 1^T + diag(c) U_C V_C^T (dense columns, M x mtot) and its nonlinear residual
     std::vector<GemmDesc<double>> gm;
     for (int k = 0; k < K; ++k) {
-      if (rC[k] > 0) {
+      if (rC[k] > 0)  // FP64 kernels: these columns' residuals are the reported ones
         gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
                                       S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
-        gm.back().tc = 1;
-      } else
+      else
         LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
     }
     if (!gm.empty()) LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
@@ -3020,11 +3019,10 @@ extern "C" int lrfsi_subset_step_init(lrfsi_subset_h S, const lrfsi_cheb_options
   {
     std::vector<GemmDesc<double>> gm;
     for (int k = 0; k < K; ++k) {
-      if (rC[k] > 0) {
+      if (rC[k] > 0)  // FP64 kernels: these columns' residuals are the reported ones
         gm.push_back(GemmDesc<double>{(int)M, S->m[k], rC[k], S->tall(S->UC, k, ldR), ldR, 1,
                                       S->vside(S->VC, k, ldR), 1, ldR, S->Xd.p + S->off[k], S->mtot, 1, 1.0, 0.0});
-        gm.back().tc = 1;
-      } else
+      else
         LRFSI_CUDA(cudaMemset2DAsync(S->Xd.p + S->off[k], sizeof(double) * S->mtot, 0, sizeof(double) * S->m[k], M, s));
     }
     if (!gm.empty()) LRFSI_TRY(gemm_grouped<double>(gm.data(), (int)gm.size(), s));
