@@ -547,6 +547,16 @@ def main():
     roof["per_class_frac_fp64"] = {k: round(v / peak64, 4) for k, v in roof["per_class_tflops"].items()
                                    if not k.endswith("fp32")}
     roof["per_class_launches"] = {k: int(v["launches"]) for k, v in ks.items() if v["launches"] > 0}
+    # the tensor-core slice products (k_oz_gram, k_oz_gemm): BF16 MMA FLOPs issued
+    # over their own launch time, against the measured BF16 peak
+    tc = ks.get("tc_mma")
+    if tc and tc["ms"] > 0 and tc["flops"] > 0:
+        bf = peaks.get("bf16_tflops")
+        tflops = tc["flops"] / (tc["ms"] * 1e-3) / 1e12
+        roof["tensor"] = {"bound": "tensor", "kernels": "k_oz_gram, k_oz_gemm", "achieved": round(tflops, 2),
+                          "peak": bf, "unit": "TFLOP/s", "frac": round(tflops / bf, 4) if bf else None,
+                          "ms": round(tc["ms"], 3), "launches": int(tc["launches"]),
+                          "peak_source": "of measured (bf16 burst)" if bf else None}
     spmm = ks["spmm_fp64"]
     spmm_gbs = spmm["bytes"] / (spmm["ms"] * 1e-3) / 1e9 if spmm["ms"] > 0 else None
 

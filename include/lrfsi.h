@@ -626,12 +626,15 @@ uint64_t lrfsi_kernel_launches(void);
  * per-subset factorisation kernels of the truncation, 8 LU panel kernels
  * (panel factorisation and row interchanges), 9 LU diagonal-block triangular
  * solves, 10 block-LU solves (whole region, contains class-0 launches),
- * 11 the cluster SVD of the truncation.  For every launch the library adds the algorithmic FLOPs and
+ * 11 the cluster SVD of the truncation (with its QR preconditioning), 12 the
+ * slice products of the tensor-core Gram and GEMM kernels alone (BF16 MMA
+ * FLOPs actually issued; their launches are also inside classes 0 and 2).
+ * For every launch the library adds the algorithmic FLOPs and
  * HBM bytes of the launch (from its shape) to the class counters; with timing
  * enabled it also brackets each launch with CUDA events on the launching
  * stream and accumulates the elapsed time when lrfsi_stats is called (which
  * synchronizes those events). */
-#define LRFSI_NUM_KERNEL_CLASSES 12
+#define LRFSI_NUM_KERNEL_CLASSES 13
 typedef struct {
   uint64_t launches;
   double flops;        /* algorithmic floating-point operations */

@@ -34,9 +34,9 @@ int cuda_fail(cudaError_t e, const char* what);
 // other classes (they overlap those classes); the rest time single launches.
 enum KClass {
   KC_GEMM = 0, KC_SPMM = 1, KC_GRAM = 2, KC_LU = 3, KC_FE = 4, KC_GEMM32 = 5, KC_SPMM32 = 6, KC_TRUNC = 7,
-  KC_LUPANEL = 8, KC_LUTRSM = 9, KC_LUSOLVE = 10, KC_SVD = 11
+  KC_LUPANEL = 8, KC_LUTRSM = 9, KC_LUSOLVE = 10, KC_SVD = 11, KC_TCMMA = 12
 };
-constexpr int kNumKClasses = 12;
+constexpr int kNumKClasses = 13;
 void account(int cls, double flops, double bytes);
 struct TimedLaunch {
   int cls;

@@ -648,8 +648,17 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
     LRFSI_CUDA(cudaMemsetAsync(part, 0, pl.part_bytes, s));
     LRFSI_TRY(oz_slice(ops, s));
     if (first > 0) {
+      double mf = 0, mb = 0;  // BF16 MMA work actually issued (36 slice products per chunk and tile)
+      for (int b = 0; b < cnt; ++b)
+        if (gate_counts(P.pr[b].gate, s)) {
+          mf += (double)P.pr[b].tiles * pl.wins * kChunksPerWin * 36.0 * 2.0 * kTA * kTB * kChunk;
+          mb += (double)P.pr[b].tiles * pl.wins * kChunksPerWin * kStageBytes;
+        }
+      account(KC_TCMMA, mf, mb);
+      TimedLaunch tm(KC_TCMMA, s);
       k_oz_gram<<<first, kGramThreads, kStages * kStageBytes, s>>>(P, g_oz_err);
       LRFSI_TRY(check_launch("k_oz_gram"));
+      tm.end(s);
     }
     long pq = 1;
     for (int b = 0; b < cnt; ++b) pq = std::max(pq, (long)P.pr[b].p * P.pr[b].q);
@@ -975,8 +984,19 @@ int ozaki_gemm(const GemmDesc<double>* d, int n, void* work, size_t work_bytes, 
     LRFSI_TRY(oz_exp(eops, s));   // column maxima of A (the contraction scales)
     LRFSI_TRY(oz_slice(ops, s));
     if (first > 0) {
+      double mf = 0, mb = 0;  // BF16 MMA work actually issued
+      for (int b = 0; b < cnt; ++b) {
+        const GemmDesc<double>& g = d[base + b];
+        if (!gate_counts(g.gate, s)) continue;
+        const double tiles = (double)ceil_div_l(g.m, kTA) * ceil_div_l(g.n, kTB), nch = (double)ceil_div_l(g.k, kChunk);
+        mf += tiles * nch * 36.0 * 2.0 * kTA * kTB * kChunk;
+        mb += tiles * nch * kStageBytes;
+      }
+      account(KC_TCMMA, mf, mb);
+      TimedLaunch tm(KC_TCMMA, s);
       k_oz_gemm<<<first, kGThreads, kGStages * kStageBytes, s>>>(P, g_oz_err);
       LRFSI_TRY(check_launch("k_oz_gemm"));
+      tm.end(s);
     }
   }
   return LRFSI_OK;

@@ -47,9 +47,10 @@ class lrfsi_kernel_stat(C.Structure):
 
 
 KERNEL_CLASSES = ("gemm_fp64", "spmm_fp64", "gram_fp64", "block_lu", "fe_assembly", "gemm_fp32", "spmm_fp32",
-                  "trunc_small", "lu_panel", "lu_trsm", "lu_solve", "trunc_svd")
-# classes that time whole regions containing launches of other classes
-REGION_CLASSES = ("block_lu", "lu_solve")
+                  "trunc_small", "lu_panel", "lu_trsm", "lu_solve", "trunc_svd", "tc_mma")
+# classes that time whole regions containing launches of other classes, and the
+# tensor-core slice products (inside gemm_fp64 / gram_fp64)
+REGION_CLASSES = ("block_lu", "lu_solve", "tc_mma")
 
 
 class lrfsi_cheb_stats(C.Structure):
