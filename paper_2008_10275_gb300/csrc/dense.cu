@@ -466,7 +466,14 @@ size_t trunc_small_work(int p, int m) {
 // relative remainder sqrt(drop)).  Outputs T1 (Q1 = X T1, k columns), the
 // scaled factor Rs = R1 D^{-1} (p x p in work Rk, rows >= k zero; the core
 // Y = Rs Vc^T is a GEMM after this kernel) and info[0] = k.
-__global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs) {
+// The Schur complements live in shared memory as the packed upper triangle
+// (original column order) when p (p + 1) / 2 + 2 p doubles fit the dynamic
+// shared memory of the launch (smem_doubles), else in d.G (full square).
+__device__ __forceinline__ int packed_idx(int a, int b, int p) {
+  if (a > b) { const int t = a; a = b; b = t; }
+  return a * p - (a * (a - 1)) / 2 + (b - a);
+}
+__global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs, int smem_doubles) {
   const TruncDesc d = descs[blockIdx.x];
   const int p = d.p, m = d.m;
   if (!gate_open(d.gate)) return;
@@ -487,9 +494,23 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
     perm[i] = i;
   }
   __syncthreads();
-  for (long e = threadIdx.x; e < (long)p * p; e += blockDim.x) {
-    const int a = (int)(e / p), b = (int)(e % p);
-    G[e] = (W.Dsc[a] > 0 && W.Dsc[b] > 0) ? G[e] * W.Dsc[a] * W.Dsc[b] : 0.0;
+  extern __shared__ double psm[];
+  const bool packed = (long)p * (p + 1) / 2 + 2L * p <= (long)smem_doubles;
+  double* Pk = psm;                            // packed Schur complements
+  double* rrow = psm + (size_t)p * (p + 1) / 2;  // row i of R (original order)
+  int* sperm = (int*)(rrow + p);               // the permutation (shared copy)
+  if (packed) {
+    for (long e = threadIdx.x; e < (long)p * p; e += blockDim.x) {
+      const int a = (int)(e / p), b = (int)(e % p);
+      if (b >= a) Pk[packed_idx(a, b, p)] = (W.Dsc[a] > 0 && W.Dsc[b] > 0) ? G[e] * W.Dsc[a] * W.Dsc[b] : 0.0;
+    }
+    for (int i = threadIdx.x; i < p; i += blockDim.x) sperm[i] = i;
+    perm = sperm;
+  } else {
+    for (long e = threadIdx.x; e < (long)p * p; e += blockDim.x) {
+      const int a = (int)(e / p), b = (int)(e % p);
+      G[e] = (W.Dsc[a] > 0 && W.Dsc[b] > 0) ? G[e] * W.Dsc[a] * W.Dsc[b] : 0.0;
+    }
   }
   if (threadIdx.x == 0) s_k = p;
   __syncthreads();
@@ -499,7 +520,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
     int bj = i;
     for (int j = i + threadIdx.x; j < p; j += blockDim.x) {
       const int pj = perm[j];
-      const double v = G[(size_t)pj * p + pj];
+      const double v = packed ? Pk[packed_idx(pj, pj, p)] : G[(size_t)pj * p + pj];
       if (v > best) { best = v; bj = j; }
     }
 #pragma unroll
@@ -541,17 +562,36 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
     // row i of R, indexed by ORIGINAL column (no swaps of earlier rows needed)
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
       const int pj = perm[j];
-      R[(size_t)i * p + pj] = j < i ? 0.0 : (j == i ? r : G[(size_t)pi * p + pj] / r);
+      const double gij = packed ? Pk[packed_idx(pi, pj, p)] : G[(size_t)pi * p + pj];
+      const double v = j < i ? 0.0 : (j == i ? r : gij / r);
+      R[(size_t)i * p + pj] = v;
+      if (packed) rrow[pj] = v;
     }
     __syncthreads();
     const int nt = p - i - 1;
-    for (long e = threadIdx.x; e < (long)nt * nt; e += blockDim.x) {
-      const int pa = perm[i + 1 + (int)(e / nt)], pb = perm[i + 1 + (int)(e % nt)];
-      G[(size_t)pa * p + pb] -= R[(size_t)i * p + pa] * R[(size_t)i * p + pb];
+    if (packed) {  // the upper triangle of the trailing block: a warp per row
+      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+      for (int ra = i + 1 + (threadIdx.x >> 5); ra < p; ra += nw) {
+        const int pa = perm[ra];
+        const double ua = rrow[pa];
+        for (int rb = ra + lane; rb < p; rb += 32) {
+          const int pb = perm[rb];
+          Pk[packed_idx(pa, pb, p)] -= ua * rrow[pb];
+        }
+      }
+    } else {
+      for (long e = threadIdx.x; e < (long)nt * nt; e += blockDim.x) {
+        const int pa = perm[i + 1 + (int)(e / nt)], pb = perm[i + 1 + (int)(e % nt)];
+        G[(size_t)pa * p + pb] -= R[(size_t)i * p + pa] * R[(size_t)i * p + pb];
+      }
     }
     __syncthreads();
   }
   __syncthreads();
+  if (packed) {  // the permutation for the later kernels
+    for (int i = threadIdx.x; i < p; i += blockDim.x) d.iwork[i] = sperm[i];
+    __syncthreads();
+  }
   const int k = s_k;
   if (threadIdx.x == 0) { d.info[0] = k; d.info[1] = 0; d.info[2] = 0; d.info[3] = 0; d.info[4] = 0; }
   // R_kk[a][b] = R[a][perm[b]] (upper triangular in pivot order) into T2 (ld k), inverse into Rki (ld k)
@@ -583,7 +623,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs)
 // (the core update Y <- R Y is a GEMM after this kernel).  info[4] = 1 when the
 // basis was far from orthonormal (max |Gq_ij - delta_ij| > 0.1), so that one
 // more pass is needed before the SVD.
-__global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, int write_third) {
+__global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, int write_third, int smem_doubles) {
   const TruncDesc d = descs[blockIdx.x];
   const int p = d.p, m = d.m;
   if (!gate_open(d.gate)) return;
@@ -594,7 +634,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, in
   const int k = s_k;
   if (k <= 0 || m <= 0) return;
   TruncWork W(d.work, p, m);
-  double* R = W.Rk;  // k x k (ld k)
+  extern __shared__ double qrsm[];
+  // k x k (ld k): in shared memory when it fits the launch's dynamic shared memory
+  double* R = (long)k * k <= (long)smem_doubles ? qrsm : W.Rk;
   for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
     const int a = (int)(e / k), b = (int)(e % k);
     const double g = d.G2[(size_t)a * p + b];
@@ -1094,20 +1136,41 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   zero_tail(r);
 }
 
+constexpr int kPass1Smem = 220 * 1024;
 int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload) {
   if (upload) LRFSI_CUDA(cudaMemcpyAsync(d_dev, d, sizeof(TruncDesc) * n, cudaMemcpyHostToDevice, s));
+  static bool attr = false;
+  if (!attr) {
+    LRFSI_CUDA(cudaFuncSetAttribute(k_trunc_pass1, cudaFuncAttributeMaxDynamicSharedMemorySize, kPass1Smem));
+    attr = true;
+  }
+  // packed Schur complements in shared memory when every problem of the launch fits
+  size_t need = 0;
+  for (int i = 0; i < n; ++i) {
+    const size_t p = d[i].p > 0 ? (size_t)d[i].p : 0;
+    const size_t b = sizeof(double) * (p * (p + 1) / 2 + 2 * p);
+    need = b > need ? b : need;
+  }
+  const size_t smem = need <= (size_t)kPass1Smem ? need : 0;
   account(KC_TRUNC, 0, 0);
   TimedLaunch tl(KC_TRUNC, s);
-  k_trunc_pass1<<<n, kSmallThreads, 0, s>>>(d_dev);
+  k_trunc_pass1<<<n, kSmallThreads, smem, s>>>(d_dev, (int)(smem / sizeof(double)));
   LRFSI_TRY(check_launch("k_trunc_pass1"));
   tl.end(s);
   return LRFSI_OK;
 }
 
-int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third) {
+int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third, int pmax) {
+  static bool attr = false;
+  if (!attr) {
+    LRFSI_CUDA(cudaFuncSetAttribute(k_trunc_qr, cudaFuncAttributeMaxDynamicSharedMemorySize, kPass1Smem));
+    attr = true;
+  }
+  const size_t need = sizeof(double) * (size_t)pmax * pmax;
+  const size_t smem = need <= (size_t)kPass1Smem ? need : 0;
   account(KC_TRUNC, 0, 0);
   TimedLaunch tl(KC_TRUNC, s);
-  k_trunc_qr<<<n, kSmallThreads, 0, s>>>(d_dev, write_third);
+  k_trunc_qr<<<n, kSmallThreads, smem, s>>>(d_dev, write_third, (int)(smem / sizeof(double)));
   LRFSI_TRY(check_launch("k_trunc_qr"));
   tl.end(s);
   return LRFSI_OK;

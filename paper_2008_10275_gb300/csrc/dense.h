@@ -87,7 +87,8 @@ int svd_cluster(int c);
 int trunc_pass1(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload = true);
 // write_third = 0: a later pass that must not overwrite the "another pass"
 // flag (info[4]) of the first QR pass
-int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third = 1);
+// pmax: the largest p of the n problems (sizes the shared-memory working copy)
+int trunc_qr(int n, cudaStream_t s, TruncDesc* d_dev, int write_third = 1, int pmax = 0);
 int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool upload = true);
 
 // Offsets of the per-problem scratch (doubles): Dsc (p) | Rk (p*p) | Rki (p*p) |

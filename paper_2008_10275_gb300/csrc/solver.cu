@@ -1056,7 +1056,11 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     gd[a] = GramDesc{S->tall(S->Q1, k, ldP), ldP, p[k], S->tall(S->Q1, k, ldP), ldP, p[k], td[a].G2, p[k]};
   }
   LRFSI_TRY(gram_batched(gd.data(), na, M, S->gramwork.p, S->gramwork.n, s));
-  LRFSI_TRY(trunc_qr(na, s, S->tdesc.p));
+  {
+    int pmax = 0;
+    for (int a = 0; a < na; ++a) pmax = std::max(pmax, td[a].p);
+    LRFSI_TRY(trunc_qr(na, s, S->tdesc.p, 1, pmax));
+  }
   {  // core C = R2 Y
     std::vector<GemmDesc<double>> gc;
     for (int a = 0; a < na; ++a) {
@@ -1102,7 +1106,9 @@ static int truncate_once(lrfsi_subset_s* S, const std::vector<int>& act, const s
     LRFSI_TRY(gemm_grouped<double>(g2.data(), (int)g2.size(), s));
     LRFSI_TRY(gram_batched(gd2.data(), (int)gd2.size(), M, S->gramwork.p, S->gramwork.n, s));
     LRFSI_CUDA(cudaMemcpyAsync(S->tdesc.p + S->K, td2.data(), sizeof(TruncDesc) * td2.size(), cudaMemcpyHostToDevice, s));
-    LRFSI_TRY(trunc_qr((int)td2.size(), s, S->tdesc.p + S->K));
+    int pmax2 = 0;
+    for (const TruncDesc& t : td2) pmax2 = std::max(pmax2, t.p);
+    LRFSI_TRY(trunc_qr((int)td2.size(), s, S->tdesc.p + S->K, 1, pmax2));
     LRFSI_TRY(gemm_grouped<double>(g3.data(), (int)g3.size(), s));
   }
   LRFSI_TRY(trunc_svd(td.data(), na, s, S->tdesc.p));
@@ -1942,11 +1948,13 @@ static int trunc_fixed(lrfsi_subset_s* S, int site, cudaStream_t s) {
   LRFSI_TRY(trunc_pass1(hd, K, s, dd, false));
   LRFSI_TRY(gemm_grouped<double>(q1y.data(), (int)q1y.size(), s));
   LRFSI_TRY(gram_batched(g2.data(), K, M, S->gramwork.p, S->gramwork.n, s));
-  LRFSI_TRY(trunc_qr(K, s, dd, 1));
+  int pmaxf = 0;
+  for (int k = 0; k < K; ++k) pmaxf = std::max(pmaxf, hd[k].p);
+  LRFSI_TRY(trunc_qr(K, s, dd, 1, pmaxf));
   LRFSI_TRY(gemm_grouped<double>(c2.data(), K, s));
   LRFSI_TRY(gemm_grouped<double>(q2.data(), K, s));
   LRFSI_TRY(gram_batched(g3.data(), K, M, S->gramwork.p, S->gramwork.n, s));
-  LRFSI_TRY(trunc_qr(K, s, dd3, 0));
+  LRFSI_TRY(trunc_qr(K, s, dd3, 0, pmaxf));
   LRFSI_TRY(gemm_grouped<double>(y3.data(), K, s));
   LRFSI_TRY(trunc_svd(hd, K, s, dd, false));
   if (timing_enabled()) {  // algorithmic work of the small kernels of the live subsets (as truncate_once)
