@@ -263,9 +263,12 @@ def run_learned(args, rank, world):
         cols, o = [], 0
         for q in range(K):
             r = int(ranks[q])
-            Uq = U[q * M * R:(q + 1) * M * R].view(M, R)[:, :r]
-            Vq = V[o * R:(o + sizes[q]) * R].view(sizes[q], R)[:, :r]
-            cols.append(X[q][:, None] + Uq @ Vq.T)
+            Uq = U[q * M * R:(q + 1) * M * R].view(M, R)[:, :r].contiguous()
+            Vtq = V[o * R:(o + sizes[q]) * R].view(sizes[q], R)[:, :r].T.contiguous()
+            Xq = X[q][:, None].repeat(1, sizes[q]).contiguous()
+            if r > 0:   # the library's FP64 GEMM: X_q = x~_q 1^T + U_q V_q^T
+                lrfsi.lrfsi_gemm(M, sizes[q], r, Uq, r, Vtq, sizes[q], Xq, sizes[q], 1.0, 1.0, tensor=False)
+            cols.append(Xq)
             o += sizes[q]
         return torch.cat(cols, 1), dict(newton_steps=int(it.sum()), newton_max=int(it.max()),
                                         outer=outer.tolist(), max_relres=float(rel.max()), status=int(st),

@@ -500,8 +500,8 @@ int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb
                int ldg, lrfsi_stream_t stream);
 /* lrfsi_gemm: C = alpha A B + beta C for row-major FP64 A (m x k, lda >= k),
  * B (k x n, ldb >= n), C (m x n, ldc >= n); beta == 0 does not read C.  With
- * lrfsi_gram_path 1 a tall product (m >= 2048, k <= 400) runs on the tensor
- * cores like the Gram products: the contraction index is equilibrated (column
+ * tensor != 0 and lrfsi_gram_path 1 a tall product (m >= 2048, k <= 400) runs
+ * on the tensor cores like the Gram products: the contraction index is equilibrated (column
  * l of A and row l of B scaled by inverse powers of two), A split by rows and
  * B by columns into 8 BF16 digit slices, the 36 slice products of a 16-step
  * chunk of k accumulated exactly (FP32 in tensor memory, k <= 400 keeps every
@@ -513,7 +513,7 @@ int lrfsi_gram(const double* A_dev, int lda, int p, const double* B_dev, int ldb
  * side); the dense columns whose nonlinear residuals are reported are formed
  * by the FP64 kernels.  Errors as lrfsi_gram. */
 int lrfsi_gemm(int m, int n, int k, const double* A_dev, int lda, const double* B_dev, int ldb, double* C_dev,
-               int ldc, double alpha, double beta, lrfsi_stream_t stream);
+               int ldc, double alpha, double beta, int tensor, lrfsi_stream_t stream);
 /* lrfsi_gram_path: how every Gram product (and every tall GEMM, see lrfsi_gemm)
  * of the library is computed:
  *   1 (default): on the BF16 tensor cores by error-free splitting (Ozaki,

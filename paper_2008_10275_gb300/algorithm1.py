@@ -145,12 +145,20 @@ class Runner:
         return Uk, Vk
 
     def dense(self, result):
-        """The dense approximation X^k = x~_k 1^T + U_k V_k^T of every subset (M x m)."""
+        """The dense approximation X^k = x~_k 1^T + U_k V_k^T of every subset (M x m),
+        formed by the library's FP64 GEMM."""
+        torch = self.torch
         cols = []
         for k in range(self.layout.K):
             Uk, Vk = self.factors(k, result["ranks"])
-            cols.append(result["xt"][k][:, None] + Uk @ Vk.T)
-        return self.torch.cat(cols, 1)
+            mk = int(self.layout.sizes[k])
+            Xk = result["xt"][k][:, None].repeat(1, mk).contiguous()
+            r = Uk.shape[1]
+            if r > 0:
+                Uc, Vtc = Uk.contiguous(), Vk.T.contiguous()
+                lrfsi.lrfsi_gemm(self.mesh.M, mk, r, Uc, r, Vtc, mk, Xk, mk, 1.0, 1.0, tensor=False)
+            cols.append(Xk)
+        return torch.cat(cols, 1)
 
 
 def solve_subsets(mesh, mu, nu, subsets, caps, opt, target, max_outer, eps_N=1e-6, device="cuda:0"):

@@ -1004,13 +1004,13 @@ int ozaki_gemm(const GemmDesc<double>* d, int n, void* work, size_t work_bytes, 
 }  // namespace lrfsi
 
 extern "C" int lrfsi_gemm(int m, int n, int k, const double* A, int lda, const double* B, int ldb, double* C, int ldc,
-                          double alpha, double beta, lrfsi_stream_t stream) {
+                          double alpha, double beta, int tensor, lrfsi_stream_t stream) {
   using namespace lrfsi;
   if (!A || !B || !C || m < 1 || n < 1 || k < 1 || lda < k || ldb < n || ldc < n)
     return fail(LRFSI_EINVAL, "lrfsi_gemm: bad argument (m, n, k >= 1, lda >= k, ldb >= n, ldc >= n)");
   cudaStream_t s = (cudaStream_t)stream;
   GemmDesc<double> g{m, n, k, A, lda, 1, B, ldb, 1, C, ldc, 1, alpha, beta};
-  g.tc = 1;
+  g.tc = tensor ? 1 : 0;
   LRFSI_TRY(gemm_grouped<double>(&g, 1, s));
   int flag = 0;
   LRFSI_TRY(ozaki_error(s, &flag));

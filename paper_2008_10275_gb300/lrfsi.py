@@ -124,7 +124,7 @@ def load():
         "lrfsi_gram": [vp, i, i, vp, i, i, C.c_int64, vp, i, vp],
         "lrfsi_gram_path": [i, vp],
         "lrfsi_svd_cluster": [i, vp],
-        "lrfsi_gemm": [i, i, i, vp, i, vp, i, vp, i, d, d, vp],
+        "lrfsi_gemm": [i, i, i, vp, i, vp, i, vp, i, d, d, i, vp],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -234,13 +234,14 @@ def gram_path(path=-1):
     return prev.value
 
 
-def lrfsi_gemm(m, n, k, A, lda, B, ldb, C, ldc, alpha=1.0, beta=0.0, stream=None):
-    """C = alpha A B + beta C for row-major device matrices (tensor cores for tall products)."""
+def lrfsi_gemm(m, n, k, A, lda, B, ldb, C, ldc, alpha=1.0, beta=0.0, tensor=True, stream=None):
+    """C = alpha A B + beta C for row-major device matrices (tall products on the
+    tensor cores when ``tensor`` and the tensor path is on, else FP64 kernels)."""
     for t in (A, B, C):
         if not t.is_contiguous():
             raise ValueError("lrfsi_gemm: A, B and C must be row-major contiguous tensors")
     _check(load().lrfsi_gemm(int(m), int(n), int(k), _ptr(A), lda, _ptr(B), ldb, _ptr(C), ldc, float(alpha),
-                             float(beta), _stream(stream)))
+                             float(beta), int(bool(tensor)), _stream(stream)))
 
 
 def svd_cluster(size=-1):

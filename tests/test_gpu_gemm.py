@@ -39,7 +39,7 @@ def _gemm(A, B, C0, alpha, beta, path):
     Ad = torch.tensor(np.ascontiguousarray(A), dtype=torch.float64, device=DEV)
     Bd = torch.tensor(np.ascontiguousarray(B), dtype=torch.float64, device=DEV)
     Cd = torch.tensor(np.ascontiguousarray(C0), dtype=torch.float64, device=DEV)
-    lrfsi.lrfsi_gemm(m, n, k, Ad, k, Bd, n, Cd, n, alpha, beta)
+    lrfsi.lrfsi_gemm(m, n, k, Ad, k, Bd, n, Cd, n, alpha, beta, tensor=True)
     torch.cuda.synchronize()
     return Cd.cpu().numpy()
 
