@@ -151,5 +151,8 @@ def test_subset_step_four_parameters_reaches_target(meshes, precision):
     r = int(ranks[0])
     X = xt[perm][:, None] + U.cpu().numpy().reshape(lm.M, m)[:, :r] @ V.cpu().numpy().reshape(m, m)[:, :r].T
     rr = algorithm1.relative_residuals4(om, X[np.argsort(perm)], mu, nu, lam, rho)
-    assert rr.max() <= 1e-8 and np.allclose(rr, rel, rtol=1e-6, atol=1e-14)
+    # far below the target R(x) is a cancellation of terms ~1e4 x larger, summed
+    # in another order by the oracle: the two relative residuals agree to ~1e-14
+    # absolute there, not relatively
+    assert rr.max() <= 1e-8 and np.allclose(rr, rel, rtol=1e-6, atol=1e-12)
     sub.close()
