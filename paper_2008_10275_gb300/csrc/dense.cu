@@ -847,7 +847,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) 
 // the cluster: the rotations of one problem run on C SMs.
 constexpr int kSvdThreads = 256;
 constexpr int kSvdWarps = kSvdThreads / 32;
-constexpr int kSvdInner = 4;  // passes over the 2b columns of a block round
 
 __device__ __forceinline__ bool jacobi_pair(double* __restrict__ cx, double* __restrict__ cy, int L, int LV,
                                             double small2, int lane) {
@@ -911,7 +910,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   __shared__ double s_ex[2][2];  // per sweep parity: {rotations, max column norm^2}
   __shared__ double s_tot, s_cm;
-  __shared__ int s_rot, s_r, s_pass;
+  __shared__ int s_rot, s_r;
   // uniform across the cluster: every CTA reads the same descriptor and info
   if (!gate_open(d.gate)) return;
   const int k = p > 0 ? d.info[0] : 0;
@@ -993,42 +992,40 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     if (tid == 0) s_rot = 0;
     __syncthreads();
     int nrot = 0;
-    // block rounds: every pair of blocks meets once per sweep; the 2b columns
-    // of a round are orthogonalised among themselves (tournament on 2b slots,
-    // intra- and cross-block pairs) for up to kSvdInner passes, until a pass
-    // rotates nothing -- more work per cluster barrier, fewer sweeps
-    for (int round = 0; round < nb - 1; ++round) {
+    {  // (i) all pairs inside this CTA's 2b columns: tournament on 2b slots
+      const int np = 2 * b;
+      for (int round = 0; round < np - 1; ++round) {
+        for (int q = warp; q < b; q += kSvdWarps) {
+          auto pos = [&](int u) { return u == 0 ? 0 : ((round + u - 1) % (np - 1)) + 1; };
+          int x = pos(q), y = pos(np - 1 - q);
+          if (x > y) { const int tt = x; x = y; y = tt; }
+          if (j0 + y >= n) continue;
+          if (jacobi_pair(home + (size_t)x * LV, home + (size_t)y * LV, L, LV, small2, lane)) ++nrot;
+        }
+        __syncthreads();
+      }
+    }
+    csync();
+    for (int round = 0; round < nb - 1; ++round) {  // (ii) cross pairs of the block tournament
       auto bpos = [&](int u) { return u == 0 ? 0 : ((round + u - 1) % (nb - 1)) + 1; };
       int X = bpos(crank), Y = bpos(nb - 1 - crank);
       if (X > Y) { const int tt = X; X = Y; Y = tt; }
       double* hx = owner_blocks(X >> 1) + (size_t)(X & 1) * b * LV;
       double* hy = owner_blocks(Y >> 1) + (size_t)(Y & 1) * b * LV;
-      const bool any = X * b < n;  // block X holds columns (X < Y)
+      const bool any = X * b < n && Y * b < n;
       if (any) {
         for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
           work[e] = hx[e];
           work[(size_t)b * LV + e] = hy[e];
         }
         __syncthreads();
-        const int np = 2 * b;
-        auto gcol = [&](int slot) { return slot < b ? X * b + slot : Y * b + (slot - b); };
-        for (int pass = 0; pass < kSvdInner; ++pass) {
-          if (tid == 0) s_pass = 0;
-          __syncthreads();
-          int prot = 0;
-          for (int sr = 0; sr < np - 1; ++sr) {
-            for (int q = warp; q < b; q += kSvdWarps) {
-              auto pos = [&](int u) { return u == 0 ? 0 : ((sr + u - 1) % (np - 1)) + 1; };
-              int x = pos(q), y = pos(np - 1 - q);
-              if (x > y) { const int tt = x; x = y; y = tt; }
-              if (gcol(x) >= n || gcol(y) >= n) continue;
-              if (jacobi_pair(work + (size_t)x * LV, work + (size_t)y * LV, L, LV, small2, lane)) { ++nrot; ++prot; }
-            }
-            __syncthreads();
+        for (int sr = 0; sr < b; ++sr) {
+          for (int q = warp; q < b; q += kSvdWarps) {
+            const int xi = q, yi = (q + sr) % b;
+            if (X * b + xi >= n || Y * b + yi >= n) continue;
+            if (jacobi_pair(work + (size_t)xi * LV, work + (size_t)(b + yi) * LV, L, LV, small2, lane)) ++nrot;
           }
-          if (lane == 0 && prot) atomicOr(&s_pass, 1);
           __syncthreads();
-          if (!s_pass) break;
         }
         for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
           hx[e] = work[e];
