@@ -543,6 +543,15 @@ def main():
         achieved = d["bytes"] / (d["ms"] * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": dom, "peak_source": "of measured" if "hbm_gbs" in peaks else "of fallback"}
+    # DRAM traffic per launch of the dominant kernel from an ncu capture of the
+    # profile case (python -m paper_2008_10275_gb300.profile_cases trunc; the
+    # summary under profiles/ names the command): dram__bytes_read.sum +
+    # dram__bytes_write.sum of one launch; None for kernels not captured since
+    # their last change
+    traffic = {"trunc_svd": (132864, "k_trunc_svd, ncu on the truncation profile case (80x16, 4 subsets); its inputs "
+                                     "are L2-resident work arrays")}
+    if dom in traffic:
+        roof["traffic"], roof["traffic_source"] = traffic[dom]
     roof["per_class_ms"] = {k: round(v["ms"], 3) for k, v in ks.items()}
     # algorithmic FP rate per class (TFLOP/s over its own launch time) and launches
     roof["per_class_tflops"] = {k: round(v["flops"] / (v["ms"] * 1e-3) / 1e12, 4)
