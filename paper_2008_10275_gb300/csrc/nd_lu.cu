@@ -553,42 +553,47 @@ __global__ void __launch_bounds__(kNdColThreads) k_nd_rhs(const NdFD* __restrict
 // tiles, 256 threads with 4 x 4 outputs each; ncols > 0 overrides every
 // descriptor's n (the number of right-hand sides of a solve).  Descriptors
 // whose problem's gate is closed are skipped.
+// 64-row tiles of 16 NC columns (NC = 1..4): a thread accumulates 4 rows x NC
+// columns, so a solve with few right-hand sides computes no padded columns
+// beyond the next multiple of 16.
+template <int NC>
 __global__ void __launch_bounds__(256) k_nd_gemm(const NdGemm* __restrict__ ds, int ncols, NdGates gates) {
+  constexpr int TN = 16 * NC;
   const NdGemm g = ds[blockIdx.z];
   const int n = ncols > 0 ? ncols : g.n;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * TN;
   if (m0 >= g.m || n0 >= n || !gate_open(gates.g[g.q])) return;
   __shared__ double As[16][65];
-  __shared__ double Bs[16][65];
+  __shared__ double Bs[16][TN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  double acc[4][NC];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0;
+    for (int c = 0; c < NC; ++c) acc[r][c] = 0.0;
   for (int k0 = 0; k0 < g.k; k0 += 16) {
     for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
       const int l = idx % 16, i = idx / 16;
       const int gi = m0 + i, gl = k0 + l;
       As[l][i] = (gi < g.m && gl < g.k) ? g.A[(size_t)gi * g.lda + gl] : 0.0;
     }
-    for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
-      const int j = idx % 64, l = idx / 64;
+    for (int idx = threadIdx.x; idx < TN * 16; idx += 256) {
+      const int j = idx % TN, l = idx / TN;
       const int gj = n0 + j, gl = k0 + l;
       Bs[l][j] = (gj < n && gl < g.k) ? g.B[(size_t)gl * g.ldb + gj] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
-      double a[4], bb[4];
+      double a[4], bb[NC];
 #pragma unroll
       for (int r = 0; r < 4; ++r) a[r] = As[l][ty + 16 * r];
 #pragma unroll
-      for (int c = 0; c < 4; ++c) bb[c] = Bs[l][tx + 16 * c];
+      for (int c = 0; c < NC; ++c) bb[c] = Bs[l][tx + 16 * c];
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], bb[c], acc[r][c]);
+        for (int c = 0; c < NC; ++c) acc[r][c] = fma(a[r], bb[c], acc[r][c]);
     }
     __syncthreads();
   }
@@ -597,7 +602,7 @@ __global__ void __launch_bounds__(256) k_nd_gemm(const NdGemm* __restrict__ ds, 
     const int gi = m0 + ty + 16 * r;
     if (gi >= g.m) continue;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
+    for (int c = 0; c < NC; ++c) {
       const int gj = n0 + tx + 16 * c;
       if (gj >= n) continue;
       double* cp = g.C + (size_t)gi * g.ldc + gj;
@@ -834,8 +839,16 @@ int ndlu_alloc(lrfsi_mesh_s* m, int nprob, int ld, NdLU& lu) {
 static int nd_gemm_launch(const NdPlan& pl, const NdList& L, int ncols, int nmax, const NdGates& gates, cudaStream_t s) {
   if (!L.count) return LRFSI_OK;
   const int nn = ncols > 0 ? ncols : nmax;
-  dim3 grid(ceil_div(nn, 64), ceil_div(L.m, 64), L.count);
-  k_nd_gemm<<<grid, 256, 0, s>>>(reinterpret_cast<const NdGemm*>(pl.buf.p + L.off), ncols, gates);
+  const NdGemm* ds = reinterpret_cast<const NdGemm*>(pl.buf.p + L.off);
+  // tile width: the next multiple of 16 up to 64 columns
+  const int nc = nn >= 64 ? 4 : (nn + 15) / 16;
+  dim3 grid(ceil_div(nn, 16 * nc), ceil_div(L.m, 64), L.count);
+  switch (nc) {
+    case 1: k_nd_gemm<1><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 2: k_nd_gemm<2><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 3: k_nd_gemm<3><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    default: k_nd_gemm<4><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+  }
   return check_launch("k_nd_gemm");
 }
 
