@@ -686,12 +686,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, in
 // (sigma-scaled) right singular vectors of A.
 // ---------------------------------------------------------------------------
 // One CTA per problem.  The matrix is worked on in shared memory when it fits
-// (kQrSmem), else in Aw.  Aw ends as the column-major reflectors (v_j in rows
+// the launch's dynamic shared memory (smem_bytes), else in Aw.  Aw ends as the column-major reflectors (v_j in rows
 // j.. of column j, its leading entry explicit) and R above the diagonal;
 // Rt = R^T; tau_j; perm (A P = A[:, perm]).  The trailing norms of the
 // columns are recomputed exactly while each reflector is applied.
 constexpr int kQrSmem = 200 * 1024;
-__global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) {
+__global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, int smem_bytes) {
   const TruncDesc d = descs[blockIdx.x];
   if (!gate_open(d.gate)) return;
   const int p = d.p, m = d.m;
@@ -702,7 +702,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) 
   const TruncWork W(d.work, p, m);
   const QrWork Q(W, p, m);
   extern __shared__ double qsm[];
-  const bool in_smem = (size_t)L * n * sizeof(double) <= (size_t)kQrSmem;
+  const bool in_smem = (size_t)L * n * sizeof(double) <= (size_t)smem_bytes;
   double* A = in_smem ? qsm : Q.Aw;
   const double* core = (d.sel && *d.sel) ? d.core_alt : d.core;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
@@ -753,7 +753,8 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs) 
       }
       __syncthreads();
     }
-    const int pv = s_piv;
+    // every trailing norm NaN (a non-finite core): no pivoting, tau = 0 below
+    const int pv = s_piv < n ? s_piv : j;
     const double sig2 = nrm[pv];
     if (pv != j) {
       for (int i = tid; i < L; i += blockDim.x) {
@@ -1252,13 +1253,16 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool 
     LRFSI_CUDA(cudaFuncSetAttribute(k_trunc_qrcp, cudaFuncAttributeMaxDynamicSharedMemorySize, kQrSmem));
     qr_attr = true;
   }
+  // p x m bounds the Jacobi matrix (L x n from the pass-1 rank k <= p, known
+  // only on the device): the launch gets that bound, at most kQrSmem, and the
+  // kernel works in shared memory only where its matrix fits what it got
   size_t qsm = 0;
   for (int i = 0; i < n; ++i) {
-    const size_t lo = d[i].p < d[i].m ? d[i].p : d[i].m, hi = d[i].p < d[i].m ? d[i].m : d[i].p;
-    const size_t need = lo * hi * sizeof(double);
-    if (need <= (size_t)kQrSmem && need > qsm) qsm = need;
+    const size_t need = (size_t)d[i].p * d[i].m * sizeof(double);
+    const size_t got = need < (size_t)kQrSmem ? need : (size_t)kQrSmem;
+    if (got > qsm) qsm = got;
   }
-  k_trunc_qrcp<<<n, kSmallThreads, qsm, s>>>(d_dev);
+  k_trunc_qrcp<<<n, kSmallThreads, qsm, s>>>(d_dev, (int)qsm);
   LRFSI_TRY(check_launch("k_trunc_qrcp"));
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];

@@ -139,6 +139,33 @@ def test_pod_matches_dense_svd():
     assert err == pytest.approx(np.sqrt(np.sum(s[k:] ** 2)), rel=1e-8)
 
 
+@pytest.mark.parametrize("k", [20, 40])
+def test_pod_many_snapshots_of_low_rank(k):
+    """400 snapshots of exact rank 30: the p x m bound of the Jacobi matrix
+    (400 x 400) is far beyond shared memory while the matrix of the pass-1
+    rank (30 x 400) fits it, so the QR preconditioning works in shared memory
+    sized by the launch; k = 40 asks for more than the rank (zero-filled)."""
+    mesh = lrfsi.Mesh(40, 8)
+    M, n, r = mesh.M, 400, 30
+    rng = np.random.default_rng(17)
+    Q1, _ = np.linalg.qr(rng.standard_normal((M, r)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((n, r)))
+    s = 10.0 ** (-0.1 * np.arange(r))
+    X = (Q1 * s) @ Q2.T
+    Xd = torch.as_tensor(X, device=DEV)
+    Phi = torch.zeros(M, k, dtype=torch.float64, device=DEV)
+    Cm = torch.zeros(n, k, dtype=torch.float64, device=DEV)
+    sig = lrfsi.lrfsi_pod(mesh, Xd, n, n, k, Phi, k, Cm, k)
+    kr = min(k, r)
+    assert np.allclose(sig[:kr], s[:kr], rtol=1e-10, atol=0)
+    assert np.all(sig[kr:] == 0)
+    P = Phi.cpu().numpy()
+    assert np.max(np.abs(P[:, :kr].T @ P[:, :kr] - np.eye(kr))) <= 1e-12
+    assert np.all(P[:, kr:] == 0)
+    err = np.linalg.norm(X - P @ Cm.cpu().numpy().T)
+    assert err <= 1e-9 * s[0] + 1.000001 * np.sqrt(np.sum(s[kr:] ** 2))
+
+
 def _newton(mesh, mus, nus, X0):
     """GPU Newton in chunks of <= 32 parameters; returns solutions and steps."""
     X = X0.clone()
