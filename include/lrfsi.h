@@ -628,13 +628,16 @@ uint64_t lrfsi_kernel_launches(void);
  * solves, 10 block-LU solves (whole region, contains class-0 launches),
  * 11 the cluster SVD of the truncation (with its QR preconditioning), 12 the
  * slice products of the tensor-core Gram and GEMM kernels alone (BF16 MMA
- * FLOPs actually issued; their launches are also inside classes 0 and 2).
+ * FLOPs actually issued; their launches are also inside classes 13 and 14),
+ * 13 FP64 GEMMs on the tensor cores by error-free splitting (whole pipeline;
+ * FP64 algorithmic FLOPs), 14 FP64 Gram products the same way.  Classes 0
+ * and 2 hold only the GEMMs and Gram products that run on the FP64 units.
  * For every launch the library adds the algorithmic FLOPs and
  * HBM bytes of the launch (from its shape) to the class counters; with timing
  * enabled it also brackets each launch with CUDA events on the launching
  * stream and accumulates the elapsed time when lrfsi_stats is called (which
  * synchronizes those events). */
-#define LRFSI_NUM_KERNEL_CLASSES 13
+#define LRFSI_NUM_KERNEL_CLASSES 15
 typedef struct {
   uint64_t launches;
   double flops;        /* algorithmic floating-point operations */

@@ -32,11 +32,15 @@ int cuda_fail(cudaError_t e, const char* what);
 // launch with events when timing is enabled
 // KC_LU, KC_LUSOLVE and KC_SVD time whole regions that contain launches of
 // other classes (they overlap those classes); the rest time single launches.
+// KC_GEMM_TC / KC_GRAM_TC time the whole tensor-core pipelines of FP64 GEMMs
+// and Gram products (exponents, slices, slice products, combination) and
+// count their FP64 algorithmic FLOPs; KC_TCMMA times the slice-product
+// kernels inside them and counts the BF16 MMA FLOPs they issue.
 enum KClass {
   KC_GEMM = 0, KC_SPMM = 1, KC_GRAM = 2, KC_LU = 3, KC_FE = 4, KC_GEMM32 = 5, KC_SPMM32 = 6, KC_TRUNC = 7,
-  KC_LUPANEL = 8, KC_LUTRSM = 9, KC_LUSOLVE = 10, KC_SVD = 11, KC_TCMMA = 12
+  KC_LUPANEL = 8, KC_LUTRSM = 9, KC_LUSOLVE = 10, KC_SVD = 11, KC_TCMMA = 12, KC_GEMM_TC = 13, KC_GRAM_TC = 14
 };
-constexpr int kNumKClasses = 13;
+constexpr int kNumKClasses = 15;
 void account(int cls, double flops, double bytes);
 struct TimedLaunch {
   int cls;

@@ -168,8 +168,8 @@ int gemm_grouped(const GemmDesc<T>* descs, int n, cudaStream_t s) {
           fl += 2.0 * g.m * g.n * g.k;
           by += 8.0 * ((double)g.m * g.k + (double)g.k * g.n + (g.beta != 0.0 ? 2.0 : 1.0) * g.m * g.n);
         }
-        account(KC_GEMM, fl, by);
-        TimedLaunch tl(KC_GEMM, s);
+        account(KC_GEMM_TC, fl, by);
+        TimedLaunch tl(KC_GEMM_TC, s);
         void* ws = nullptr;
         size_t wsb = 0;
         LRFSI_TRY(gemm_ws_get(ozaki_gemm_work_bytes(tcd.data(), (int)tcd.size()), &ws, &wsb));

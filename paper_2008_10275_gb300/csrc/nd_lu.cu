@@ -21,6 +21,7 @@
 #include <numeric>
 
 #include "nd_lu.h"
+#include "ozaki.h"
 
 namespace lrfsi {
 
@@ -252,9 +253,7 @@ struct NdProbs {
   const double* J3[kMaxGemmDescs];
   double alpha[kMaxGemmDescs], beta[kMaxGemmDescs];
 };
-struct NdGates {
-  Gate g[kMaxGemmDescs];
-};
+using NdGates = OzGates;
 
 __global__ void k_nd_extract(NdProbs pp, const long long* __restrict__ entry_off, long nnz) {
   const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -553,26 +552,27 @@ __global__ void __launch_bounds__(kNdColThreads) k_nd_rhs(const NdFD* __restrict
 // tiles, 256 threads with 4 x 4 outputs each; ncols > 0 overrides every
 // descriptor's n (the number of right-hand sides of a solve).  Descriptors
 // whose problem's gate is closed are skipped.
-// 64-row tiles of 16 NC columns (NC = 1..4): a thread accumulates 4 rows x NC
-// columns, so a solve with few right-hand sides computes no padded columns
-// beyond the next multiple of 16.
-template <int NC>
+// Tiles of 16 RM rows (RM = 2, 4) x 16 NC columns (NC = 1..4): a thread
+// accumulates RM rows x NC columns, so a solve with few right-hand sides
+// computes no padded columns beyond the next multiple of 16, and lists of
+// GEMMs with at most 32 rows no padded rows beyond 32.
+template <int NC, int RM>
 __global__ void __launch_bounds__(256) k_nd_gemm(const NdGemm* __restrict__ ds, int ncols, NdGates gates) {
-  constexpr int TN = 16 * NC;
+  constexpr int TN = 16 * NC, TM = 16 * RM;
   const NdGemm g = ds[blockIdx.z];
   const int n = ncols > 0 ? ncols : g.n;
-  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * TN;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   if (m0 >= g.m || n0 >= n || !gate_open(gates.g[g.q])) return;
-  __shared__ double As[16][65];
+  __shared__ double As[16][TM + 1];
   __shared__ double Bs[16][TN + 1];
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][NC];
+  double acc[RM][NC];
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int r = 0; r < RM; ++r)
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[r][c] = 0.0;
   for (int k0 = 0; k0 < g.k; k0 += 16) {
-    for (int idx = threadIdx.x; idx < 64 * 16; idx += 256) {
+    for (int idx = threadIdx.x; idx < TM * 16; idx += 256) {
       const int l = idx % 16, i = idx / 16;
       const int gi = m0 + i, gl = k0 + l;
       As[l][i] = (gi < g.m && gl < g.k) ? g.A[(size_t)gi * g.lda + gl] : 0.0;
@@ -585,20 +585,20 @@ __global__ void __launch_bounds__(256) k_nd_gemm(const NdGemm* __restrict__ ds, 
     __syncthreads();
 #pragma unroll
     for (int l = 0; l < 16; ++l) {
-      double a[4], bb[NC];
+      double a[RM], bb[NC];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = As[l][ty + 16 * r];
+      for (int r = 0; r < RM; ++r) a[r] = As[l][ty + 16 * r];
 #pragma unroll
       for (int c = 0; c < NC; ++c) bb[c] = Bs[l][tx + 16 * c];
 #pragma unroll
-      for (int r = 0; r < 4; ++r)
+      for (int r = 0; r < RM; ++r)
 #pragma unroll
         for (int c = 0; c < NC; ++c) acc[r][c] = fma(a[r], bb[c], acc[r][c]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r) {
+  for (int r = 0; r < RM; ++r) {
     const int gi = m0 + ty + 16 * r;
     if (gi >= g.m) continue;
 #pragma unroll
@@ -692,11 +692,20 @@ __global__ void k_nd_bgather(const NdBg* __restrict__ ds, int r, int ld, NdGates
 struct NdList {
   size_t off = 0;  // byte offset in the descriptor buffer
   int count = 0, m = 0, n = 0, f = 0;  // count; largest m / n (GEMMs), largest f / n (fronts), b (extends)
+  double mk = 0;   // GEMM lists: sum of m k over the GEMMs of one problem
 };
 
 struct NdPlan {
   std::vector<NdList> fd, schur, ext[2], fwd1, fwd2, vext[2], bg, bwd;  // per height
   DevBuf<unsigned char> buf;
+  // the solve GEMMs on the tensor cores (fixed left operands: the inverses,
+  // A_BF and W of the fronts, sliced after every factorisation): per height
+  // the group of each sweep list, and the FP64 lists of the GEMMs left out
+  OzFixedPlan tc;
+  bool tc_built = false;
+  int tc_sliced = 0;  // problems whose slices match their factors
+  std::vector<int> g_fwd1, g_fwd2, g_bwd;
+  std::vector<NdList> fwd1s, fwd2s, bwds;
 };
 
 int ndlu_status(NdLU& lu, int nprob, std::vector<int>& out, cudaStream_t s) {
@@ -765,8 +774,25 @@ int ndlu_alloc(lrfsi_mesh_s* m, int nprob, int ld, NdLU& lu) {
     return o;
   };
   for (auto* v : {&plan->fd, &plan->schur, &plan->ext[0], &plan->ext[1], &plan->fwd1, &plan->fwd2, &plan->vext[0],
-                  &plan->vext[1], &plan->bg, &plan->bwd})
+                  &plan->vext[1], &plan->bg, &plan->bwd, &plan->fwd1s, &plan->fwd2s, &plan->bwds})
     v->assign(H, NdList{});
+  plan->g_fwd1.assign(H, -1);
+  plan->g_fwd2.assign(H, -1);
+  plan->g_bwd.assign(H, -1);
+  // a sweep GEMM goes to the tensor cores when its left operand is large
+  // enough (ozaki_fixed_eligible); the rest stay on the FP64 kernel
+  auto split_tc = [&](const std::vector<NdGemm>& all, std::vector<NdGemm>& small, NdList& Ls,
+                      std::vector<OzFixedGemm>& tcg) {
+    for (const NdGemm& g : all) {
+      if (ozaki_fixed_eligible(g.m, g.k)) {
+        tcg.push_back(OzFixedGemm{g.A, g.lda, g.m, g.k, g.B, g.ldb, g.C, g.ldc, g.q, g.alpha, g.beta});
+      } else {
+        small.push_back(g);
+        Ls.m = std::max(Ls.m, g.m);
+        if (g.q == 0) Ls.mk += (double)g.m * g.k;
+      }
+    }
+  };
   for (int h = 0; h < H; ++h) {
     std::vector<NdFD> fd;
     std::vector<NdGemm> schur, fwd1, fwd2, bwd;
@@ -828,10 +854,36 @@ int ndlu_alloc(lrfsi_mesh_s* m, int nprob, int ld, NdLU& lu) {
     stash(plan->vext[1][h], L[7], vext[1].data(), vext[1].size(), sizeof(NdVec));
     stash(plan->bg[h], L[8], bg.data(), bg.size(), sizeof(NdBg));
     stash(plan->bwd[h], L[9], bwd.data(), bwd.size(), sizeof(NdGemm));
+    {
+      std::vector<NdGemm> s1, s2, s3;
+      std::vector<OzFixedGemm> t1, t2, t3;
+      NdList l1, l2, l3;
+      split_tc(fwd1, s1, l1, t1);
+      split_tc(fwd2, s2, l2, t2);
+      split_tc(bwd, s3, l3, t3);
+      stash(plan->fwd1s[h], l1, s1.data(), s1.size(), sizeof(NdGemm));
+      stash(plan->fwd2s[h], l2, s2.data(), s2.size(), sizeof(NdGemm));
+      stash(plan->bwds[h], l3, s3.data(), s3.size(), sizeof(NdGemm));
+      if (!t1.empty()) plan->g_fwd1[h] = plan->tc.add_group(t1);
+      if (!t2.empty()) plan->g_fwd2[h] = plan->tc.add_group(t2);
+      if (!t3.empty()) plan->g_bwd[h] = plan->tc.add_group(t3);
+    }
   }
   if (bytes.empty()) bytes.push_back(0);
   LRFSI_TRY(plan->buf.alloc(bytes.size()));
   LRFSI_CUDA(cudaMemcpy(plan->buf.p, bytes.data(), bytes.size(), cudaMemcpyHostToDevice));
+  // the tensor-core slices take about twice the bytes of the operands they
+  // replace: built only within a quarter of the free device memory
+  bool any = false;
+  for (int h = 0; h < H; ++h) any = any || plan->g_fwd1[h] >= 0 || plan->g_fwd2[h] >= 0 || plan->g_bwd[h] >= 0;
+  if (any) {
+    size_t fr = 0, tot = 0;
+    LRFSI_CUDA(cudaMemGetInfo(&fr, &tot));
+    if (plan->tc.bytes_needed(ld) <= fr / 4) {
+      LRFSI_TRY(plan->tc.build(ld, nprob));
+      plan->tc_built = true;
+    }
+  }
   lu.plan = plan;
   return LRFSI_OK;
 }
@@ -840,14 +892,20 @@ static int nd_gemm_launch(const NdPlan& pl, const NdList& L, int ncols, int nmax
   if (!L.count) return LRFSI_OK;
   const int nn = ncols > 0 ? ncols : nmax;
   const NdGemm* ds = reinterpret_cast<const NdGemm*>(pl.buf.p + L.off);
-  // tile width: the next multiple of 16 up to 64 columns
+  // tile width: the next multiple of 16 up to 64 columns; 32 rows when no
+  // GEMM of the list has more
   const int nc = nn >= 64 ? 4 : (nn + 15) / 16;
-  dim3 grid(ceil_div(nn, 16 * nc), ceil_div(L.m, 64), L.count);
-  switch (nc) {
-    case 1: k_nd_gemm<1><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
-    case 2: k_nd_gemm<2><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
-    case 3: k_nd_gemm<3><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
-    default: k_nd_gemm<4><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+  const int rm = L.m <= 32 ? 2 : 4;
+  dim3 grid(ceil_div(nn, 16 * nc), ceil_div(L.m, 16 * rm), L.count);
+  switch (nc + 4 * (rm == 2)) {
+    case 1: k_nd_gemm<1, 4><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 2: k_nd_gemm<2, 4><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 3: k_nd_gemm<3, 4><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 4: k_nd_gemm<4, 4><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 5: k_nd_gemm<1, 2><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 6: k_nd_gemm<2, 2><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    case 7: k_nd_gemm<3, 2><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
+    default: k_nd_gemm<4, 2><<<grid, 256, 0, s>>>(ds, ncols, gates); break;
   }
   return check_launch("k_nd_gemm");
 }
@@ -928,6 +986,12 @@ int ndlu_factor(const lrfsi_mesh_s* m, NdLU& lu, const double* const* J3, const 
       LRFSI_TRY(check_launch("k_nd_extend"));
     }
   }
+  NdPlan& plw = *lu.plan;
+  plw.tc_sliced = 0;
+  if (plw.tc_built && gram_path() == 1) {
+    LRFSI_TRY(plw.tc.slice(nprob, s));
+    plw.tc_sliced = nprob;
+  }
   account(KC_LU, sym.factor_flops * nprob, 0);
   tl_all.end(s);
   return LRFSI_OK;
@@ -980,14 +1044,27 @@ int ndlu_solve(NdLU& lu, double* const* X, double* const* Y, const int* r, int l
       fl += 2.0 * rmax * (f * f + 2.0 * f * b);
     }
   }
-  {
-    int live = 0;
-    for (int q = 0; q < nprob; ++q) live += (r[q] > 0 && gate_counts(g.g[q], s)) ? 1 : 0;
-    account(KC_GEMM, fl * live, 0);
-  }
+  // the sweep GEMMs: on the tensor cores where their slices are current (the
+  // rest on the FP64 kernel), else all on the FP64 kernel
+  // (a few right-hand sides: the FP64 kernel reads half the bytes)
+  const bool tc = pl.tc_built && gram_path() == 1 && nprob <= pl.tc_sliced && rmax >= 8;
+  int live = 0;
+  for (int q = 0; q < nprob; ++q) live += (r[q] > 0 && gate_counts(g.g[q], s)) ? 1 : 0;
+  if (!tc) account(KC_GEMM, fl * live, 0);
+  auto sweep = [&](const std::vector<NdList>& all, const std::vector<NdList>& small, const std::vector<int>& grp,
+                   int h) -> int {
+    const NdList L = part(tc ? small[h] : all[h]);
+    if (L.count) {
+      if (tc) account(KC_GEMM, 2.0 * rmax * small[h].mk * live, 0);
+      TimedLaunch tk(KC_GEMM, s);
+      LRFSI_TRY(nd_gemm_launch(pl, L, rmax, rmax, g, s));
+      tk.end(s);
+    }
+    return tc ? pl.tc.gemm(grp[h], rmax, nprob, g, s) : LRFSI_OK;
+  };
   for (int h = 0; h < sym.heights; ++h) {  // forward: y_F = A_FF^{-1} z_F, z_B -= A_BF y_F, z_B to the parent
-    LRFSI_TRY(nd_gemm_launch(pl, part(pl.fwd1[h]), rmax, rmax, g, s));
-    LRFSI_TRY(nd_gemm_launch(pl, part(pl.fwd2[h]), rmax, rmax, g, s));
+    LRFSI_TRY(sweep(pl.fwd1, pl.fwd1s, pl.g_fwd1, h));
+    LRFSI_TRY(sweep(pl.fwd2, pl.fwd2s, pl.g_fwd2, h));
     for (int slot = 0; slot < 2; ++slot) {
       const NdList V = part(pl.vext[slot][h]);
       if (!V.count) continue;
@@ -1003,7 +1080,7 @@ int ndlu_solve(NdLU& lu, double* const* X, double* const* Y, const int* r, int l
           reinterpret_cast<const NdBg*>(pl.buf.p + B.off), rmax, ldl, g);
       LRFSI_TRY(check_launch("k_nd_bgather"));
     }
-    LRFSI_TRY(nd_gemm_launch(pl, part(pl.bwd[h]), rmax, rmax, g, s));
+    LRFSI_TRY(sweep(pl.bwd, pl.bwds, pl.g_bwd, h));
   }
   k_nd_scatter<<<dim3(ceil_div(M * rmax, 256), nprob), 256, 0, s>>>(sp, lu.dsym->perm.p, M, rmax, ld, ldl, g);
   LRFSI_TRY(check_launch("k_nd_scatter"));

@@ -150,6 +150,7 @@ struct OzOp {
   __nv_bfloat16* sl; // slices: nchunks x nt x 8 x 2048
   int* ex;           // nt * 128 biased exponents (max over the column; 0: zero column)
   Gate gate;
+  int q;             // >= 0: the gate is the launch's gate q instead (descriptors on the device)
 };
 struct OzOps {
   OzOp op[2 * kMaxOz];
@@ -197,17 +198,14 @@ __device__ __forceinline__ void oz_tile_of(const OzProd& P, int t, int& ta, int&
 // ---------------------------------------------------------------------------
 constexpr int kExpRows = 64;
 
-// ex[i] = largest biased exponent field over column i (2047 if the column
-// holds an Inf or NaN); ex must be zeroed first.
-__global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O, long M) {
-  const OzOp& op = O.op[blockIdx.z];
-  if (!gate_open(op.gate)) return;
+// ex[i] = largest biased exponent field over column i < n (2047 if the column
+// holds an Inf or NaN); ex must be zeroed first.  CTA (row block, 256 columns).
+__device__ __forceinline__ void oz_exp_cols(const OzOp& op, int n) {
   const double* X = (op.sel && *op.sel) ? op.Xalt : op.X;
   const long rows = op.rows;
-  (void)M;
   const long r0 = (long)blockIdx.x * kExpRows, r1 = r0 + kExpRows < rows ? r0 + kExpRows : rows;
   const int i = blockIdx.y * 256 + threadIdx.x;
-  if (i >= op.n) return;
+  if (i >= n) return;
   int mx = 0;
   for (long l = r0; l < r1; ++l) {
     int be = (int)((__double_as_longlong(X[l * op.rs + i * op.cs]) >> 52) & 0x7FF);
@@ -219,6 +217,12 @@ __global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O,
     mx = be > mx ? be : mx;
   }
   if (mx) atomicMax(op.ex + i, mx);
+}
+__global__ void __launch_bounds__(256) k_oz_exp(const __grid_constant__ OzOps O, long M) {
+  const OzOp& op = O.op[blockIdx.z];
+  (void)M;
+  if (!gate_open(op.gate)) return;
+  oz_exp_cols(op, op.n);
 }
 
 // The 8 balanced base-128 digits of x as a 56-bit fixed-point number in units
@@ -244,26 +248,25 @@ __device__ __forceinline__ void oz_digits(double x, int bexp_max, int shift, int
   a[0] = (int)v;
 }
 
-// CTA = (16-row chunk, group of two 128-column tiles, operand): every (column,
-// 8-row half) item writes 16 bytes (8 rows of one column) of each slice.
-__global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps O, long M) {
-  const OzOp& op = O.op[blockIdx.z];
-  if (!gate_open(op.gate)) return;
+// CTA = (16-row chunk, group of two 128-column tiles): every (column, 8-row
+// half) item writes 16 bytes (8 rows of one column) of each slice; n columns
+// in opnt tiles of 128 (columns >= n are zero).
+__device__ __forceinline__ void oz_split_cols(const OzOp& op, int n, int opnt) {
   const double* X = (op.sel && *op.sel) ? op.Xalt : op.X;
   const long c = blockIdx.x;
-  const int t0 = blockIdx.y * 2, nt = op.nt - t0 < 2 ? op.nt - t0 : 2;
-  M = op.rows;
+  const int t0 = blockIdx.y * 2, nt = opnt - t0 < 2 ? opnt - t0 : 2;
+  const long M = op.rows;
   if (nt <= 0 || c >= op.nch) return;
   const int items = nt * kTA * 2;
   for (int it = threadIdx.x; it < items; it += blockDim.x) {
     const int i = t0 * kTA + it % (nt * kTA), kg = it / (nt * kTA);
     const int ti = i / kTA, il = i % kTA;
-    const int bx = i < op.n ? op.ex[i] : 0;
+    const int bx = i < n ? op.ex[i] : 0;
     int dig[8][kSl];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const long l = c * kChunk + kg * 8 + e;
-      double x = (i < op.n && l < M) ? X[l * op.rs + (long)i * op.cs] : 0.0;
+      double x = (i < n && l < M) ? X[l * op.rs + (long)i * op.cs] : 0.0;
       int shift = 0;
       if (op.lsc && l < M) {
         const int ls = op.lsc[l];
@@ -272,7 +275,7 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps 
       }
       oz_digits(x, bx, shift, dig[e]);
     }
-    __nv_bfloat16* base = op.sl + ((size_t)(c * op.nt + ti) * kSl) * (kTA * kChunk) + (il >> 3) * 128 + kg * 64 +
+    __nv_bfloat16* base = op.sl + ((size_t)(c * opnt + ti) * kSl) * (kTA * kChunk) + (il >> 3) * 128 + kg * 64 +
                           (il & 7) * 8;
 #pragma unroll
     for (int t = 0; t < kSl; ++t) {
@@ -282,6 +285,12 @@ __global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps 
       *reinterpret_cast<uint4*>(base + (size_t)t * (kTA * kChunk)) = *reinterpret_cast<const uint4*>(v);
     }
   }
+}
+__global__ void __launch_bounds__(256) k_oz_split(const __grid_constant__ OzOps O, long M) {
+  const OzOp& op = O.op[blockIdx.z];
+  (void)M;
+  if (!gate_open(op.gate)) return;
+  oz_split_cols(op, op.n, op.nt);
 }
 
 // ---------------------------------------------------------------------------
@@ -641,9 +650,9 @@ int ozaki_gram(const GramDesc* d, int nbatch, long M, void* work, size_t work_by
         fl += sym ? 1.0 * M * g.p * (g.p + 1) : 2.0 * M * g.p * g.q;
         by += 8.0 * M * (sym ? g.p : g.p + g.q);
       }
-      account(KC_GRAM, fl, by);
+      account(KC_GRAM_TC, fl, by);
     }
-    TimedLaunch tl(KC_GRAM, s);
+    TimedLaunch tl(KC_GRAM_TC, s);
     LRFSI_CUDA(cudaMemsetAsync(ex, 0, pl.ex_bytes, s));
     LRFSI_CUDA(cudaMemsetAsync(part, 0, pl.part_bytes, s));
     LRFSI_TRY(oz_slice(ops, s));
@@ -766,26 +775,26 @@ __device__ __forceinline__ void tmem_ld8x4(uint32_t t0, uint32_t t1, uint32_t t2
       : "memory");
 }
 
-// CTA = (GEMM, 128 x 32 tile of C).  Warp 8 lane 0 issues the bulk copies and
-// the 36 MMAs per 16-row chunk of K into 8 level accumulators (256 tensor-
-// memory columns); warps 0-7 read all 8 levels of 8 columns at a time (warp w:
-// lanes 32 (w % 4) .., columns 16 (w / 4) ..) and write C.
-__global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ OzGs P, int* err) {
+// One 128 x 32 tile (ta, tb) of C = alpha A B + beta C (m x n, contraction
+// k <= kOzMaxK) from the slices of A^T (asl: nch x ant x 8 x 2048, row
+// exponents aex) and of B (bsl: nch x bnt x 8 x 2048, column exponents bex).
+// Warp 8 lane 0 issues the bulk copies and the 36 MMAs per 16-row chunk of K
+// into 8 level accumulators (256 tensor-memory columns); warps 0-7 read all 8
+// levels of 8 columns at a time (warp w: lanes 32 (w % 4) .., columns
+// 16 (w / 4) ..) and write C.  Called by all kGThreads threads of the CTA,
+// which must not have returned before.
+template <int STAGES>
+__device__ __forceinline__ void oz_gemm_tile(const __nv_bfloat16* __restrict__ asl, int ant, const int* __restrict__ aex,
+                                             const __nv_bfloat16* __restrict__ bsl, int bnt,
+                                             const int* __restrict__ bex, int m, int n, int k, int ta, int tb,
+                                             double* C, long c_rs, long c_cs, double alpha, double beta, int* err) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[kGStages], empty[kGStages], done, fin;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done, fin;
   __shared__ uint32_t s_tmem;
-  const int cta = blockIdx.x;
-  int gi = 0;
-  while (gi + 1 < P.cnt && cta >= P.g[gi + 1].first) ++gi;
-  const OzG& G = P.g[gi];
-  if (!gate_open(G.gate)) return;
-  const int t = cta - G.first, ta = t / G.ntn, tb = t % G.ntn;
-  const OzOp& A = P.op[G.a];
-  const OzOp& B = P.op[G.b];
-  const int nch = (G.k + kChunk - 1) / kChunk;
+  const int nch = (k + kChunk - 1) / kChunk;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kGStages; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -806,21 +815,21 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
     if (lane == 0) {
       constexpr uint32_t idesc = mma_idesc(kTA, kTB);
       auto load = [&](int c) {
-        const int st = c % kGStages;
+        const int st = c % STAGES;
         unsigned char* sa = smem + (size_t)st * kStageBytes;
         unsigned char* sb = sa + kABytes;
-        const __nv_bfloat16* ga = A.sl + ((size_t)c * A.nt + ta) * kSl * (kTA * kChunk);
-        const __nv_bfloat16* gb = B.sl + ((size_t)c * B.nt + tb / 4) * kSl * (kTA * kChunk) + (tb % 4) * (kTB * kChunk);
+        const __nv_bfloat16* ga = asl + ((size_t)c * ant + ta) * kSl * (kTA * kChunk);
+        const __nv_bfloat16* gb = bsl + ((size_t)c * bnt + tb / 4) * kSl * (kTA * kChunk) + (tb % 4) * (kTB * kChunk);
         mbar_expect_tx(&full[st], kStageBytes);
         bulk_g2s(sa, ga, kABytes, &full[st]);
         for (int u = 0; u < kSl; ++u) bulk_g2s(sb + u * (kTB * kChunk * 2), gb + u * (kTA * kChunk), kTB * kChunk * 2, &full[st]);
       };
       int issued = 0, consumed = 0;
-      for (; issued < nch && issued < kGStages; ++issued) load(issued);
+      for (; issued < nch && issued < STAGES; ++issued) load(issued);
       bool ok = true;
       for (int c = 0; c < nch && ok; ++c) {
-        const int st = c % kGStages;
-        if (!mbar_wait(&full[st], (uint32_t)(c / kGStages) & 1)) { ok = false; break; }
+        const int st = c % STAGES;
+        if (!mbar_wait(&full[st], (uint32_t)(c / STAGES) & 1)) { ok = false; break; }
         consumed = c + 1;
         tc_fence_after();
         const uint32_t sa = sm_addr(smem + (size_t)st * kStageBytes), sb = sa + kABytes;
@@ -836,15 +845,15 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
         mma_commit(&empty[st]);
         if (c == nch - 1) mma_commit(&done);
         if (c >= 1 && issued < nch) {
-          const int ps = (c - 1) % kGStages;
-          if (!mbar_wait(&empty[ps], (uint32_t)((c - 1) / kGStages) & 1)) { ok = false; break; }
+          const int ps = (c - 1) % STAGES;
+          if (!mbar_wait(&empty[ps], (uint32_t)((c - 1) / STAGES) & 1)) { ok = false; break; }
           load(issued++);
         }
       }
       if (!ok) atomicExch(err, 1);
       mma_commit(&fin);
       mbar_wait(&fin, 0);
-      for (int c = consumed; c < issued; ++c) mbar_wait(&full[c % kGStages], (uint32_t)(c / kGStages) & 1);
+      for (int c = consumed; c < issued; ++c) mbar_wait(&full[c % STAGES], (uint32_t)(c / STAGES) & 1);
     }
   } else {
     const int q = warp & 3, h = warp >> 2;
@@ -856,7 +865,7 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
     } else {
       tc_fence_after();
       const int i = ta * kTA + 32 * q + lane;
-      const int ea = i < G.m ? A.ex[i] : 0;
+      const int ea = i < m ? aex[i] : 0;
 #pragma unroll 1
       for (int half = 0; half < 2; ++half) {
         const int jc = 16 * h + 8 * half;  // first column of these 8 in the tile
@@ -865,12 +874,12 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
         tmem_ld8x4(tl, tl + kTB, tl + 2 * kTB, tl + 3 * kTB, *reinterpret_cast<uint32_t(*)[4][8]>(&v[0][0]));
         tmem_ld8x4(tl + 4 * kTB, tl + 5 * kTB, tl + 6 * kTB, tl + 7 * kTB,
                    *reinterpret_cast<uint32_t(*)[4][8]>(&v[4][0]));
-        if (i < G.m) {
+        if (i < m) {
 #pragma unroll
           for (int jj = 0; jj < 8; ++jj) {
             const int j = tb * kTB + jc + jj;
-            if (j >= G.n) continue;
-            const int eb = B.ex[j];
+            if (j >= n) continue;
+            const int eb = bex[j];
             double val;
             if (ea == 0x7FF || eb == 0x7FF) {
               val = __longlong_as_double(0x7FF8000000000000LL);
@@ -883,8 +892,8 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
               const int sc = (ea ? ea - 1022 : 0) + (eb ? eb - 1022 : 0);
               val = ldexp(fma((double)Ls, 0x1p-28, (double)Hs), sc - 35);
             }
-            double* cp = G.C + (size_t)i * G.c_rs + (size_t)j * G.c_cs;
-            *cp = G.beta != 0.0 ? fma(G.alpha, val, G.beta * *cp) : G.alpha * val;
+            double* cp = C + (size_t)i * c_rs + (size_t)j * c_cs;
+            *cp = beta != 0.0 ? fma(alpha, val, beta * *cp) : alpha * val;
           }
         }
       }
@@ -896,6 +905,20 @@ __global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ O
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
   }
+}
+
+// CTA = (GEMM, 128 x 32 tile of C).
+__global__ void __launch_bounds__(kGThreads) k_oz_gemm(const __grid_constant__ OzGs P, int* err) {
+  const int cta = blockIdx.x;
+  int gi = 0;
+  while (gi + 1 < P.cnt && cta >= P.g[gi + 1].first) ++gi;
+  const OzG& G = P.g[gi];
+  if (!gate_open(G.gate)) return;  // uniform over the CTA, before any barrier or allocation
+  const int t = cta - G.first, ta = t / G.ntn, tb = t % G.ntn;
+  const OzOp& A = P.op[G.a];
+  const OzOp& B = P.op[G.b];
+  oz_gemm_tile<kGStages>(A.sl, A.nt, A.ex, B.sl, B.nt, B.ex, G.m, G.n, G.k, ta, tb, G.C, G.c_rs, G.c_cs, G.alpha,
+                         G.beta, err);
 }
 
 bool ozaki_gemm_eligible(const GemmDesc<double>& g) {
@@ -999,6 +1022,352 @@ int ozaki_gemm(const GemmDesc<double>* d, int n, void* work, size_t work_bytes, 
       tm.end(s);
     }
   }
+  return LRFSI_OK;
+}
+
+// ---------------------------------------------------------------------------
+// GEMMs with fixed left operands (OzFixedPlan)
+// ---------------------------------------------------------------------------
+namespace {
+// One GEMM of a group: the A^T operand (slices made by slice()) and the B
+// operand (sliced at every call, n = the call's columns), both with the
+// contraction scales of A.
+struct OzNdG {
+  OzOp A, B;
+  double* C;
+  long c_rs;
+  int m, k;
+  double alpha, beta;
+};
+constexpr int kGridZ = 65535;
+}  // namespace
+
+// exponents / slices of the device-resident operands ops[0 .. cnt)
+__global__ void __launch_bounds__(256) k_oz_exp_d(const OzOp* __restrict__ ops, int cnt) {
+  for (int z = blockIdx.z; z < cnt; z += gridDim.z) oz_exp_cols(ops[z], ops[z].n);
+}
+__global__ void __launch_bounds__(256) k_oz_split_d(const OzOp* __restrict__ ops, int cnt) {
+  for (int z = blockIdx.z; z < cnt; z += gridDim.z) oz_split_cols(ops[z], ops[z].n, ops[z].nt);
+}
+// The B operands of a group with ncols columns (gated per problem).  CTA =
+// (128-column tile, GEMM), 512 threads: the exponents of its columns over the
+// k rows (scaled by the contraction scales; 4 row groups reduced in shared
+// memory), then the 8 slices of the 16-row chunks, two chunks at a time (one
+// (column, 8-row half) item per thread and chunk).
+constexpr int kBsThreads = 512;
+__global__ void __launch_bounds__(kBsThreads) k_oz_bslice(const OzNdG* __restrict__ ds, int cnt, int ncols,
+                                                          const __grid_constant__ OzGates G) {
+  __shared__ int s_ex[kBsThreads / kTA][kTA];
+  constexpr int kRowGroups = kBsThreads / kTA;
+  const int ti = blockIdx.x, opnt = (int)ceil_div_l(ncols, kTA);
+  const int il = threadIdx.x & (kTA - 1), grp = threadIdx.x >> 7;
+  const int half = grp & 1, csub = grp >> 1;  // chunk phase: 8-row half, chunk of the pair
+  const int i = ti * kTA + il;
+  for (int z = blockIdx.z; z < cnt; z += gridDim.z) {
+    const OzOp& op = ds[z].B;
+    if (!gate_open(G.g[op.q])) continue;  // uniform over the CTA
+    const double* X = op.X;
+    const long k = op.rows;
+    int mx = 0;
+    if (i < ncols) {
+#pragma unroll 4
+      for (long l = grp; l < k; l += kRowGroups) {
+        int be = (int)((__double_as_longlong(X[l * op.rs + i]) >> 52) & 0x7FF);
+        if (be != 0 && be != 0x7FF) {
+          const int ls = op.lsc[l];
+          be = ls == 0 ? 0 : be + (ls - 1022);
+          be = be < 1 ? 0 : (be > 0x7FE ? 0x7FE : be);
+        }
+        mx = be > mx ? be : mx;
+      }
+    }
+    s_ex[grp][il] = mx;
+    __syncthreads();
+    int bx = 0;
+#pragma unroll
+    for (int g = 0; g < kRowGroups; ++g) bx = max(bx, s_ex[g][il]);
+    if (grp == 0 && i < ncols) op.ex[i] = bx;
+    for (long c = csub; c < op.nch; c += 2) {
+      int dig[8][kSl];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const long l = c * kChunk + half * 8 + e;
+        double x = 0.0;
+        int shift = 0;
+        if (i < ncols && l < k) {
+          const int ls = op.lsc[l];
+          if (ls != 0) {
+            x = X[l * op.rs + i];
+            shift = ls - 1022;
+          }
+        }
+        oz_digits(x, bx, shift, dig[e]);
+      }
+      __nv_bfloat16* base = op.sl + ((size_t)(c * opnt + ti) * kSl) * (kTA * kChunk) + (il >> 3) * 128 + half * 64 +
+                            (il & 7) * 8;
+#pragma unroll
+      for (int t = 0; t < kSl; ++t) {
+        __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16_rn((float)dig[e][t]);
+        *reinterpret_cast<uint4*>(base + (size_t)t * (kTA * kChunk)) = *reinterpret_cast<const uint4*>(v);
+      }
+    }
+    __syncthreads();  // s_ex is rewritten by the next GEMM of this CTA
+  }
+}
+
+// CTA = (32-column tile, 128-row tile, GEMM); STAGES pipeline stages (4 for
+// long contractions: fewer CTAs, each with more copies in flight)
+template <int STAGES>
+__global__ void __launch_bounds__(kGThreads) k_oz_ndgemm(const OzNdG* __restrict__ ds, int ncols,
+                                                         const __grid_constant__ OzGates G, int* err) {
+  const OzNdG* d = ds + blockIdx.z;
+  const int ta = blockIdx.y, tb = blockIdx.x;
+  // uniform over the CTA, before any barrier or allocation
+  if (ta >= d->A.nt || tb * kTB >= ncols || !gate_open(G.g[d->A.q])) return;
+  oz_gemm_tile<STAGES>(d->A.sl, d->A.nt, d->A.ex, d->B.sl, (int)ceil_div_l(ncols, kTA), d->B.ex, d->m, ncols, d->k, ta, tb,
+               d->C, d->c_rs, 1, d->alpha, d->beta, err);
+}
+
+bool ozaki_fixed_eligible(int m, int k) {
+  return gram_path() == 1 && k >= 16 && k <= kOzMaxK && m >= 32 && (long)m * k >= 2048;
+}
+
+int OzFixedPlan::add_group(const std::vector<OzFixedGemm>& g) {
+  Group G;
+  G.gemms = g;
+  groups_.push_back(std::move(G));
+  return (int)groups_.size() - 1;
+}
+
+namespace {
+// byte layout of an OzFixedPlan (dry run when base == nullptr)
+struct FixedLayout {
+  size_t off = 0;
+  size_t take(size_t bytes) {
+    const size_t o = off;
+    off = round256(off + bytes);
+    return o;
+  }
+};
+inline size_t a_slice_bytes(int m, int k) {
+  return (size_t)ceil_div_l(k, kChunk) * ceil_div_l(m, kTA) * kSl * kTA * kChunk * sizeof(__nv_bfloat16);
+}
+inline size_t a_exp_ints(int m, int k) { return (size_t)k + (size_t)ceil_div_l(m, kTA) * kTA; }
+}  // namespace
+
+size_t OzFixedPlan::bytes_needed(int max_cols) const {
+  const int ntb = (int)ceil_div_l(max_cols, kTA);
+  FixedLayout L;
+  size_t total = 0, bex = 0, bsl = 0, aex = 0, asl = 0;
+  for (const Group& G : groups_) {
+    L.take(sizeof(OzNdG) * G.gemms.size());
+    total += G.gemms.size();
+    size_t be = 0, bs = 0;
+    for (const OzFixedGemm& g : G.gemms) {
+      be += (size_t)ntb * kTA;
+      bs += round256((size_t)ceil_div_l(g.k, kChunk) * ntb * kSl * kTA * kChunk * sizeof(__nv_bfloat16));
+      aex += a_exp_ints(g.m, g.k);
+      asl += round256(a_slice_bytes(g.m, g.k));
+    }
+    bex = std::max(bex, be);
+    bsl = std::max(bsl, bs);
+  }
+  L.take(sizeof(OzOp) * total);
+  L.take(sizeof(OzOp) * total);
+  L.take(sizeof(int) * aex);
+  L.take(asl);
+  L.take(sizeof(int) * bex);
+  L.take(bsl);
+  return L.off;
+}
+
+int OzFixedPlan::build(int max_cols, int nprob) {
+  if (max_cols < 1 || nprob < 1 || nprob > kMaxGemmDescs) return fail(LRFSI_EINVAL, "tensor GEMM plan: bad sizes");
+  nprob_ = nprob;
+  max_cols_ = max_cols;
+  // kernel attributes and the error flag, here and not in gemm(): gemm() may
+  // run inside a stream capture
+  {
+    static bool attr = false;
+    if (!attr) {
+      LRFSI_CUDA(cudaFuncSetAttribute(k_oz_ndgemm<kGStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      kGStages * kStageBytes));
+      LRFSI_CUDA(cudaFuncSetAttribute(k_oz_ndgemm<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 4 * kStageBytes));
+      attr = true;
+    }
+    if (!g_oz_err) {
+      LRFSI_CUDA(cudaMalloc(&g_oz_err, sizeof(int)));
+      LRFSI_CUDA(cudaMemset(g_oz_err, 0, sizeof(int)));
+    }
+  }
+  const int ntb = (int)ceil_div_l(max_cols, kTA);
+  LRFSI_TRY(buf_.alloc(bytes_needed(max_cols)));
+  unsigned char* base = buf_.p;
+  FixedLayout L;
+  size_t total = 0;
+  for (Group& G : groups_) {
+    G.d_off = L.take(sizeof(OzNdG) * G.gemms.size());
+    total += G.gemms.size();
+  }
+  e_off_ = L.take(sizeof(OzOp) * total);
+  a_off_ = L.take(sizeof(OzOp) * total);
+  // slicing order: problem-major (prefixes of problems), groups in order within
+  std::vector<std::pair<int, int>> order;  // (group, index)
+  sl_prefix_.assign(nprob + 1, 0);
+  for (int q = 0; q < nprob; ++q) {
+    for (int gi = 0; gi < (int)groups_.size(); ++gi)
+      for (int i = 0; i < (int)groups_[gi].gemms.size(); ++i)
+        if (groups_[gi].gemms[i].q == q) order.push_back({gi, i});
+    sl_prefix_[q + 1] = (int)order.size();
+  }
+  if (order.size() != total) return fail(LRFSI_EINVAL, "tensor GEMM plan: a problem index outside [0, nprob)");
+  size_t aex_ints = 0, asl_bytes = 0;
+  for (auto& o : order) {
+    const OzFixedGemm& g = groups_[o.first].gemms[o.second];
+    aex_ints += a_exp_ints(g.m, g.k);
+    asl_bytes += round256(a_slice_bytes(g.m, g.k));
+  }
+  aex_off_ = L.take(sizeof(int) * aex_ints);
+  const size_t asl_off = L.take(asl_bytes);
+  size_t bex_max = 0, bsl_max = 0;
+  for (Group& G : groups_) {
+    size_t be = 0, bs = 0;
+    for (const OzFixedGemm& g : G.gemms) {
+      be += (size_t)ntb * kTA;
+      bs += round256((size_t)ceil_div_l(g.k, kChunk) * ntb * kSl * kTA * kChunk * sizeof(__nv_bfloat16));
+    }
+    G.bex_bytes = sizeof(int) * be;
+    bex_max = std::max(bex_max, be);
+    bsl_max = std::max(bsl_max, bs);
+  }
+  bex_off_ = L.take(sizeof(int) * bex_max);
+  bsl_off_ = L.take(bsl_max);
+  if (L.off > buf_.bytes()) return fail(LRFSI_EINVAL, "tensor GEMM plan: layout exceeds its buffer");
+  // A operands in slicing order
+  std::vector<OzOp> E(total), A(total);
+  std::vector<std::vector<OzOp>> Aof(groups_.size());
+  for (size_t gi = 0; gi < groups_.size(); ++gi) Aof[gi].resize(groups_[gi].gemms.size());
+  aex_prefix_.assign(nprob + 1, 0);
+  int* aex = (int*)(base + aex_off_);
+  unsigned char* asl = base + asl_off;
+  size_t ie = 0, is = 0;
+  sl_rows_max_ = sl_n_max_ = sl_nch_max_ = sl_nt_max_ = 1;
+  for (int q = 0, j = 0; q < nprob; ++q) {
+    for (; j < sl_prefix_[q + 1]; ++j) {
+      const OzFixedGemm& g = groups_[order[j].first].gemms[order[j].second];
+      OzOp e{}, a{};
+      e.X = g.A; e.rs = g.lda; e.cs = 1; e.rows = g.m; e.n = g.k; e.ex = aex + ie; e.q = -1;
+      a.X = g.A; a.rs = 1; a.cs = g.lda; a.rows = g.k; a.nch = ceil_div_l(g.k, kChunk);
+      a.lsc = aex + ie; a.lsign = -1; a.n = g.m; a.nt = (int)ceil_div_l(g.m, kTA);
+      a.ex = aex + ie + g.k; a.sl = (__nv_bfloat16*)(asl + is); a.q = -1;
+      ie += a_exp_ints(g.m, g.k);
+      is += round256(a_slice_bytes(g.m, g.k));
+      E[j] = e;
+      A[j] = a;
+      Aof[order[j].first][order[j].second] = a;
+      sl_rows_max_ = std::max(sl_rows_max_, std::max(g.m, g.k));
+      sl_n_max_ = std::max(sl_n_max_, std::max(g.m, g.k));
+      sl_nch_max_ = std::max(sl_nch_max_, (int)a.nch);
+      sl_nt_max_ = std::max(sl_nt_max_, a.nt);
+    }
+    aex_prefix_[q + 1] = sizeof(int) * ie;
+  }
+  LRFSI_CUDA(cudaMemcpy(base + e_off_, E.data(), sizeof(OzOp) * total, cudaMemcpyHostToDevice));
+  LRFSI_CUDA(cudaMemcpy(base + a_off_, A.data(), sizeof(OzOp) * total, cudaMemcpyHostToDevice));
+  // group descriptors; every group's B operands reuse the same workspace
+  for (size_t gi = 0; gi < groups_.size(); ++gi) {
+    Group& G = groups_[gi];
+    std::vector<OzNdG> d(G.gemms.size());
+    G.prefix.assign(nprob + 1, 0);
+    size_t be = 0, bs = 0;
+    for (size_t i = 0; i < G.gemms.size(); ++i) {
+      const OzFixedGemm& g = G.gemms[i];
+      if (i > 0 && g.q < G.gemms[i - 1].q) return fail(LRFSI_EINVAL, "tensor GEMM plan: a group not ordered by problem");
+      OzNdG& x = d[i];
+      x.A = Aof[gi][i];
+      x.A.q = g.q;
+      x.B = OzOp{};
+      x.B.X = g.B; x.B.rs = g.ldb; x.B.cs = 1; x.B.rows = g.k; x.B.nch = ceil_div_l(g.k, kChunk);
+      x.B.lsc = x.A.lsc; x.B.lsign = 1; x.B.n = max_cols; x.B.nt = ntb; x.B.q = g.q;
+      x.B.ex = (int*)(base + bex_off_) + be;
+      x.B.sl = (__nv_bfloat16*)(base + bsl_off_ + bs);
+      be += (size_t)ntb * kTA;
+      bs += round256((size_t)ceil_div_l(g.k, kChunk) * ntb * kSl * kTA * kChunk * sizeof(__nv_bfloat16));
+      x.C = g.C; x.c_rs = g.ldc; x.m = g.m; x.k = g.k; x.alpha = g.alpha; x.beta = g.beta;
+      G.mmax = std::max(G.mmax, g.m);
+      G.kmax = std::max(G.kmax, g.k);
+      G.ntmax = std::max(G.ntmax, x.A.nt);
+      for (int q = g.q + 1; q <= nprob; ++q) G.prefix[q] = (int)i + 1;
+    }
+    if (!d.empty()) LRFSI_CUDA(cudaMemcpy(base + G.d_off, d.data(), sizeof(OzNdG) * d.size(), cudaMemcpyHostToDevice));
+  }
+  return LRFSI_OK;
+}
+
+int OzFixedPlan::slice(int nprob, cudaStream_t s) const {
+  if (!buf_.p || nprob < 1) return LRFSI_OK;
+  if (nprob > nprob_) return fail(LRFSI_EINVAL, "tensor GEMM plan: more problems than built");
+  const int cnt = sl_prefix_[nprob];
+  if (!cnt) return LRFSI_OK;
+  const OzOp* E = (const OzOp*)(buf_.p + e_off_);
+  const OzOp* A = (const OzOp*)(buf_.p + a_off_);
+  const unsigned gz = (unsigned)std::min(cnt, kGridZ);
+  LRFSI_CUDA(cudaMemsetAsync(buf_.p + aex_off_, 0, aex_prefix_[nprob], s));
+  // contraction scales (column maxima of A), then the row exponents and slices of A^T
+  k_oz_exp_d<<<dim3((unsigned)ceil_div_l(sl_rows_max_, kExpRows), (unsigned)ceil_div_l(sl_n_max_, 256), gz), 256, 0,
+               s>>>(E, cnt);
+  LRFSI_TRY(check_launch("k_oz_exp_d"));
+  k_oz_exp_d<<<dim3((unsigned)ceil_div_l(sl_rows_max_, kExpRows), (unsigned)ceil_div_l(sl_n_max_, 256), gz), 256, 0,
+               s>>>(A, cnt);
+  LRFSI_TRY(check_launch("k_oz_exp_d"));
+  k_oz_split_d<<<dim3((unsigned)sl_nch_max_, (unsigned)ceil_div_l(sl_nt_max_, 2), gz), 256, 0, s>>>(A, cnt);
+  LRFSI_TRY(check_launch("k_oz_split_d"));
+  return LRFSI_OK;
+}
+
+int OzFixedPlan::gemm(int gi, int ncols, int nprob, const OzGates& gates, cudaStream_t s) const {
+  if (empty(gi) || ncols < 1 || nprob < 1) return LRFSI_OK;
+  if (!buf_.p || ncols > max_cols_ || nprob > nprob_ || !g_oz_err)
+    return fail(LRFSI_EINVAL, "tensor GEMM plan: call beyond its build");
+  const Group& G = groups_[gi];
+  const int cnt = G.prefix[nprob];
+  if (!cnt) return LRFSI_OK;
+  const OzNdG* d = (const OzNdG*)(buf_.p + G.d_off);
+  {  // algorithmic FP64 work and the BF16 MMA work issued, for the live problems
+    bool live[kMaxGemmDescs];
+    for (int q = 0; q < nprob; ++q) live[q] = gate_counts(gates.g[q], s);
+    double fl = 0, by = 0, mf = 0, mb = 0;
+    for (int i = 0; i < cnt; ++i) {
+      const OzFixedGemm& g = G.gemms[i];
+      if (!live[g.q]) continue;
+      fl += 2.0 * g.m * g.k * ncols;
+      by += 8.0 * ((double)g.m * g.k + (double)g.k * ncols + (g.beta != 0.0 ? 2.0 : 1.0) * g.m * ncols);
+      const double tiles = (double)ceil_div_l(g.m, kTA) * ceil_div_l(ncols, kTB), nch = (double)ceil_div_l(g.k, kChunk);
+      mf += tiles * nch * 36.0 * 2.0 * kTA * kTB * kChunk;
+      mb += tiles * nch * kStageBytes;
+    }
+    account(KC_GEMM_TC, fl, by);
+    account(KC_TCMMA, mf, mb);
+  }
+  TimedLaunch tl(KC_GEMM_TC, s);
+  const unsigned gz = (unsigned)std::min(cnt, kGridZ);
+  k_oz_bslice<<<dim3((unsigned)ceil_div_l(ncols, kTA), 1, gz), kBsThreads, 0, s>>>(d, cnt, ncols, gates);
+  LRFSI_TRY(check_launch("k_oz_bslice"));
+  TimedLaunch tm(KC_TCMMA, s);
+  const bool deep = G.kmax >= 8 * kChunk;
+  for (int z0 = 0; z0 < cnt; z0 += kGridZ) {
+    const int z = std::min(kGridZ, cnt - z0);
+    const dim3 grid((unsigned)ceil_div_l(ncols, kTB), (unsigned)G.ntmax, (unsigned)z);
+    if (deep)
+      k_oz_ndgemm<4><<<grid, kGThreads, 4 * kStageBytes, s>>>(d + z0, ncols, gates, g_oz_err);
+    else
+      k_oz_ndgemm<kGStages><<<grid, kGThreads, kGStages * kStageBytes, s>>>(d + z0, ncols, gates, g_oz_err);
+    LRFSI_TRY(check_launch("k_oz_ndgemm"));
+  }
+  tm.end(s);
+  tl.end(s);
   return LRFSI_OK;
 }
 }  // namespace lrfsi

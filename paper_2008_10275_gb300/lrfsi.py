@@ -47,10 +47,13 @@ class lrfsi_kernel_stat(C.Structure):
 
 
 KERNEL_CLASSES = ("gemm_fp64", "spmm_fp64", "gram_fp64", "block_lu", "fe_assembly", "gemm_fp32", "spmm_fp32",
-                  "trunc_small", "lu_panel", "lu_trsm", "lu_solve", "trunc_svd", "tc_mma")
+                  "trunc_small", "lu_panel", "lu_trsm", "lu_solve", "trunc_svd", "tc_mma", "gemm_tc", "gram_tc")
 # classes that time whole regions containing launches of other classes, and the
-# tensor-core slice products (inside gemm_fp64 / gram_fp64)
+# tensor-core slice products (inside gemm_tc / gram_tc)
 REGION_CLASSES = ("block_lu", "lu_solve", "tc_mma")
+# FP64 products on the tensor cores (FP64 algorithmic FLOPs over the whole
+# splitting pipeline: not FP64-unit work)
+TENSOR_CLASSES = ("gemm_tc", "gram_tc")
 
 
 class lrfsi_cheb_stats(C.Structure):

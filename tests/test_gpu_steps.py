@@ -97,7 +97,23 @@ def test_newton_median_both_lu_modes(lu_mode):
         lrfsi.lu_mode(prev)
 
 
-def _precond_case(nx, ny):
+@pytest.mark.parametrize("nx,ny", [(20, 4), (80, 16)])
+def test_precond_apply_tensor_core_sweeps(nx, ny):
+    """With >= 8 right-hand sides the sweeps of the nested-dissection solve run
+    their large GEMMs on the tensor cores (fixed factor blocks sliced once per
+    factorisation); the same handle with the FP64 sweeps (path 0) and with the
+    tensor sweeps meets the same bars against splu, and the two agree to the
+    forward bar."""
+    prev_lu, prev_path = lrfsi.lu_mode(1), lrfsi.gram_path(1)
+    try:
+        Y1 = _precond_case(nx, ny, r=(20, 13), ld=24, paths=(1, 0))
+        assert np.all(np.isfinite(Y1))
+    finally:
+        lrfsi.lu_mode(prev_lu)
+        lrfsi.gram_path(prev_path)
+
+
+def _precond_case(nx, ny, r=(5, 3), ld=6, paths=(None,)):
     lm, om, perm, subs = _two_subsets(nx, ny)
     K = len(subs)
     mu = np.concatenate([s[0] for s in subs])
@@ -105,13 +121,17 @@ def _precond_case(nx, ny):
     xt = _dev(np.stack([s[2][perm] for s in subs]))
     sizes = [len(s[0]) for s in subs]
     sub = lrfsi.Subsets(lm, xt, mu, nu, sizes, [8, 8])
-    r = [5, 3]
-    ld = 6
+    r = list(r)
     rng = np.random.default_rng(9)
     Xh = rng.standard_normal((K, lm.M, ld))
-    Y = torch.zeros(K * lm.M * ld, dtype=torch.float64, device=DEV)
-    lrfsi.lrfsi_precond_apply(sub, _dev(Xh.reshape(-1)), ld, r, Y, ld)
-    Yh = Y.cpu().numpy().reshape(K, lm.M, ld)
+    outs = []
+    for path in paths:
+        if path is not None:
+            lrfsi.gram_path(path)
+        Y = torch.zeros(K * lm.M * ld, dtype=torch.float64, device=DEV)
+        lrfsi.lrfsi_precond_apply(sub, _dev(Xh.reshape(-1)), ld, r, Y, ld)
+        outs.append(Y.cpu().numpy().reshape(K, lm.M, ld))
+    Yh = outs[0]
     inv = np.argsort(perm)
     for k, (mu_k, nu_k, xt_k) in enumerate(subs):
         J0, Jmu, Jnu = fsi.affine_jacobian(om, xt_k)
@@ -124,13 +144,19 @@ def _precond_case(nx, ny):
         cond1 = spla.norm(A, 1) * spla.onenormest(Pinv)
         fwd_tol = max(1e-10, 20 * cond1 * np.finfo(float).eps)
         Anorm = spla.norm(A, np.inf)
-        for j in range(r[k]):
-            y = Yh[k][:, j][inv]
-            back = np.abs(A @ y - xk[:, j]).max() / (Anorm * np.abs(y).max() + np.abs(xk[:, j]).max())
-            assert back <= 1e-12, (k, j, back)
-            err = np.linalg.norm(y - ref[:, j]) / np.linalg.norm(ref[:, j])
-            assert err <= fwd_tol, (k, j, err, cond1)
+        for Yo in outs:
+            for j in range(r[k]):
+                y = Yo[k][:, j][inv]
+                back = np.abs(A @ y - xk[:, j]).max() / (Anorm * np.abs(y).max() + np.abs(xk[:, j]).max())
+                assert back <= 1e-12, (k, j, back)
+                err = np.linalg.norm(y - ref[:, j]) / np.linalg.norm(ref[:, j])
+                assert err <= fwd_tol, (k, j, err, cond1)
+        for Yo in outs[1:]:
+            for j in range(r[k]):
+                d = np.linalg.norm(Yo[k][:, j] - Yh[k][:, j]) / np.linalg.norm(Yh[k][:, j])
+                assert d <= fwd_tol, (k, j, d)
     sub.close()
+    return Yh
 
 
 @pytest.mark.parametrize("tol", [3e-2, 1e-12])
