@@ -132,6 +132,14 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
       : "memory");
 }
 
+// v 2^e: within the normal exponent range one multiplication by the power of
+// two built from its IEEE-754 exponent field (exact, or rounded once where the
+// product is subnormal: the same result as ldexp); ldexp outside it
+__device__ __forceinline__ double oz_scale2(double v, int e) {
+  if (e >= -1022 && e <= 1023) return v * __longlong_as_double((long long)(e + 1023) << 52);
+  return ldexp(v, e);
+}
+
 // ---------------------------------------------------------------------------
 // Launch parameters
 // ---------------------------------------------------------------------------
@@ -476,7 +484,7 @@ __global__ void __launch_bounds__(256) k_oz_reduce(const __grid_constant__ OzPro
     const int sc = (ea ? ea - 1022 : 0) + (eb ? eb - 1022 : 0);
     g = 0.0;
 #pragma unroll
-    for (int lv = kLv - 1; lv >= 0; --lv) g += ldexp((double)S[lv], sc - 7 * (lv + 2));
+    for (int lv = kLv - 1; lv >= 0; --lv) g += oz_scale2((double)S[lv], sc - 7 * (lv + 2));
   }
   pr.G[(size_t)i0 * pr.ldg + j0] = g;
 }
@@ -890,7 +898,7 @@ __device__ __forceinline__ void oz_gemm_tile(const __nv_bfloat16* __restrict__ a
 #pragma unroll
               for (int lv = 4; lv < 8; ++lv) Ls = Ls * 128 + __float2int_rn(__uint_as_float(v[lv][jj]));
               const int sc = (ea ? ea - 1022 : 0) + (eb ? eb - 1022 : 0);
-              val = ldexp(fma((double)Ls, 0x1p-28, (double)Hs), sc - 35);
+              val = oz_scale2(fma((double)Ls, 0x1p-28, (double)Hs), sc - 35);
             }
             double* cp = C + (size_t)i * c_rs + (size_t)j * c_cs;
             *cp = beta != 0.0 ? fma(alpha, val, beta * *cp) : alpha * val;

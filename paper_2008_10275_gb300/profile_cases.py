@@ -5,6 +5,7 @@ timing outside the full step.
     python -m paper_2008_10275_gb300.profile_cases trunc    # median Newton + two correction steps (truncations)
     python -m paper_2008_10275_gb300.profile_cases spmm     # FP64 and FP32 SpMM of the affine operators
     python -m paper_2008_10275_gb300.profile_cases large    # 320 x 64 mesh: SpMM, block LU, solve, one ChebyshevT step
+    python -m paper_2008_10275_gb300.profile_cases ndsolve  # preconditioner solves, 40 right-hand sides, both paths
 
 Each case builds the 80 x 16 channel mesh (M = 22629) with the seeded
 parameters of the 400-parameter workload, runs the case twice (the first run
@@ -105,6 +106,28 @@ def case_spmm():
               f"(shape {v}, tuned ms {[round(float(t), 4) for t in tms]})")
 
 
+def case_ndsolve():
+    """The K preconditioner solves P_k^{-1} X of the medium workload (nested
+    dissection, subset operators at b_D) with 40 right-hand sides, on the
+    tensor-core sweeps (path 1) and on the FP64 sweeps (path 0)."""
+    torch, lrfsi, W, mesh, mus, nus = _setup()
+    K = W.K
+    bD = torch.tensor(mesh.dirichlet(), device="cuda:0")
+    sizes = [len(mus) // K] * K
+    sub = lrfsi.Subsets(mesh, bD.repeat(K, 1), mus, nus, sizes, [W.rank_cap] * K)
+    ld = 40
+    gen = torch.Generator(device="cuda:0").manual_seed(3)
+    X = torch.randn(K * mesh.M * ld, dtype=torch.float64, device="cuda:0", generator=gen)
+    Y = torch.zeros_like(X)
+    prev = lrfsi.gram_path()
+    for path in (1, 0):
+        lrfsi.gram_path(path)
+        ms, _ = _timed(torch, lambda: lrfsi.lrfsi_precond_apply(sub, X, ld, ld, Y, ld))
+        print(f"ndsolve path {path}: {K} problems x {ld} columns {ms:.3f} ms")
+    lrfsi.gram_path(prev)
+    sub.close()
+
+
 def case_large():
     import json
     import torch
@@ -181,4 +204,5 @@ def case_large():
 
 
 if __name__ == "__main__":
-    {"lu": case_lu, "trunc": case_trunc, "spmm": case_spmm, "large": case_large}[sys.argv[1]]()
+    {"lu": case_lu, "trunc": case_trunc, "spmm": case_spmm, "large": case_large,
+     "ndsolve": case_ndsolve}[sys.argv[1]]()
