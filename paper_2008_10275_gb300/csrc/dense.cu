@@ -404,23 +404,32 @@ int gram_batched(const GramDesc* d, int nbatch, long M, double* work, size_t wor
 constexpr int kSmallThreads = 1024;
 
 // Inverse of the k x k upper triangular R (row-major, ldr) into Ri (row-major,
-// ldi): rows from the bottom up; in row a every warp computes entries
-// Ri[a][b] = -(sum_{l=a+1..b} R[a][l] Ri[l][b]) / R[a][a] with a lane-split dot
-// product.  Must be called by the whole block.
+// ldi): the diagonal reciprocals first (in parallel), then the rows from the
+// bottom up; in row a thread b computes Ri[a][b] = -(sum_{l=a+1..b} R[a][l]
+// Ri[l][b]) Ri[a][a] with four independent partial sums (no cross-lane
+// reductions: every FP64 instruction of a warp costs the SM's FP64 pipe a
+// full warp).  Must be called by the whole block.
 __device__ void upper_inverse(const double* R, int ldr, double* Ri, int ldi, int k) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (long e = threadIdx.x; e < (long)k * k; e += blockDim.x) {
     const int i = (int)(e / k), j = (int)(e % k);
     if (j < i) Ri[(size_t)i * ldi + j] = 0.0;
+    else if (j == i) Ri[(size_t)i * ldi + i] = 1.0 / R[(size_t)i * ldr + i];
   }
-  for (int a = k - 1; a >= 0; --a) {
-    const double inv = 1.0 / R[(size_t)a * ldr + a];
-    for (int b = a + warp; b < k; b += nw) {
-      double sacc = 0;
-      for (int l = a + 1 + lane; l <= b; l += 32) sacc += R[(size_t)a * ldr + l] * Ri[(size_t)l * ldi + b];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
-      if (lane == 0) Ri[(size_t)a * ldi + b] = (b == a) ? inv : -sacc * inv;
+  __syncthreads();
+  for (int a = k - 2; a >= 0; --a) {
+    const double inv = Ri[(size_t)a * ldi + a];
+    const double* Ra = R + (size_t)a * ldr;
+    for (int b = a + 1 + threadIdx.x; b < k; b += blockDim.x) {
+      double s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+      int l = a + 1;
+      for (; l + 3 <= b; l += 4) {
+        s0 = fma(Ra[l], Ri[(size_t)l * ldi + b], s0);
+        s1 = fma(Ra[l + 1], Ri[(size_t)(l + 1) * ldi + b], s1);
+        s2 = fma(Ra[l + 2], Ri[(size_t)(l + 2) * ldi + b], s2);
+        s3 = fma(Ra[l + 3], Ri[(size_t)(l + 3) * ldi + b], s3);
+      }
+      for (; l <= b; ++l) s0 = fma(Ra[l], Ri[(size_t)l * ldi + b], s0);
+      Ri[(size_t)a * ldi + b] = -((s0 + s1) + (s2 + s3)) * inv;
     }
     __syncthreads();
   }
@@ -428,26 +437,29 @@ __device__ void upper_inverse(const double* R, int ldr, double* Ri, int ldi, int
 
 // Right-looking Cholesky G = R^T R in place (upper triangle holds R), rows with
 // pivot <= drop are marked dropped (keep[i] = 0) and do not update the rest.
+// Thread 0 takes the pivot's root and its reciprocal; in the update thread b
+// owns column b of the trailing upper triangle.
 __device__ void chol_drop(double* G, int ld, int p, double drop, int* keep) {
-  __shared__ double s_piv;
+  __shared__ double s_piv, s_rinv;
   for (int i = 0; i < p; ++i) {
     if (threadIdx.x == 0) {
       double piv = G[(size_t)i * ld + i];
       keep[i] = (piv > drop && isfinite(piv)) ? 1 : 0;
       s_piv = keep[i] ? sqrt(piv) : 0.0;
+      s_rinv = keep[i] ? 1.0 / s_piv : 0.0;
     }
     __syncthreads();
-    const double r = s_piv;
+    const double r = s_piv, rinv = s_rinv;
+    double* Gi = G + (size_t)i * ld;
     if (r > 0) {
-      for (int j = i + threadIdx.x; j < p; j += blockDim.x) G[(size_t)i * ld + j] = (j == i) ? r : G[(size_t)i * ld + j] / r;
+      for (int j = i + threadIdx.x; j < p; j += blockDim.x) Gi[j] = (j == i) ? r : Gi[j] * rinv;
       __syncthreads();
-      const int nt = p - i - 1;
-      for (long e = threadIdx.x; e < (long)nt * nt; e += blockDim.x) {
-        const int a = i + 1 + (int)(e / nt), b = i + 1 + (int)(e % nt);
-        if (b >= a) G[(size_t)a * ld + b] -= G[(size_t)i * ld + a] * G[(size_t)i * ld + b];
+      for (int b = i + 1 + threadIdx.x; b < p; b += blockDim.x) {
+        const double gib = Gi[b];
+        for (int a = i + 1; a <= b; ++a) G[(size_t)a * ld + b] = fma(-Gi[a], gib, G[(size_t)a * ld + b]);
       }
     } else {
-      for (int j = i + threadIdx.x; j < p; j += blockDim.x) G[(size_t)i * ld + j] = 0.0;
+      for (int j = i + threadIdx.x; j < p; j += blockDim.x) Gi[j] = 0.0;
     }
     __syncthreads();
   }
@@ -485,7 +497,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
   double* G = d.G;         // p x p, original column order; Schur complements in place
   double* R = W.Rk;        // k x p, R[a][b] = R1 entry for permuted columns a, b (b >= a)
   int* perm = d.iwork;
-  __shared__ double s_val[33];
+  __shared__ double s_val[33], s_root, s_rinv;
   __shared__ int s_idx[33];
   __shared__ int s_k;
   for (int i = threadIdx.x; i < p; i += blockDim.x) {
@@ -541,7 +553,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
         const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
         if (v2 > best || (v2 == best && j2 < bj)) { best = v2; bj = j2; }
       }
-      if (threadIdx.x == 0) { s_val[32] = best; s_idx[32] = bj; }
+      if (threadIdx.x == 0) {
+        s_val[32] = best;
+        s_idx[32] = bj;
+        s_root = best > 0 ? sqrt(best) : 0.0;  // the pivot's root and its reciprocal, once
+        s_rinv = s_root > 0 ? 1.0 / s_root : 0.0;
+      }
     }
     __syncthreads();
     const double piv = s_val[32];
@@ -558,12 +575,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
     }
     __syncthreads();
     const int pi = perm[i];
-    const double r = sqrt(piv);
+    const double r = s_root, rinv = s_rinv;
     // row i of R, indexed by ORIGINAL column (no swaps of earlier rows needed)
     for (int j = threadIdx.x; j < p; j += blockDim.x) {
       const int pj = perm[j];
       const double gij = packed ? Pk[packed_idx(pi, pj, p)] : G[(size_t)pi * p + pj];
-      const double v = j < i ? 0.0 : (j == i ? r : gij / r);
+      const double v = j < i ? 0.0 : (j == i ? r : gij * rinv);
       R[(size_t)i * p + pj] = v;
       if (packed) rrow[pj] = v;
     }
@@ -827,8 +844,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
 // (k x m) if m < k, else A = C^T (m x k); k_trunc_qrcp factors A P = Q R and
 // the iteration orthogonalises the n columns of X = R^T (n x n): X W = Y
 // with orthogonal columns, W accumulated.  Every column is stored with its W
-// column appended (length LV = 2n), so one rotation updates both.  The kept
-// singular vectors follow from Y and W (see the output stage).
+// column appended (length LV = 2n), so one rotation updates both, followed by
+// the squared norm of its X part (stride LS = LV + 2): a rotation refreshes
+// the norms of its two columns from the values it writes, so the test of a
+// pair needs only their inner product.  The kept singular vectors follow from
+// Y and W (see the output stage).
 //
 // Parallel block ordering: the n columns form nb = 2 C blocks of b columns; CTA
 // c of the cluster owns blocks 2c, 2c+1 in its shared memory.  A sweep is
@@ -849,49 +869,66 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
 constexpr int kSvdThreads = 256;
 constexpr int kSvdWarps = kSvdThreads / 32;
 
+// cx[LV], cy[LV]: the squared norms of the X parts (L entries), summed in the
+// order of a dot product here (lane-strided FMAs, then a butterfly), so they
+// equal the norms recomputed from the columns.
 __device__ __forceinline__ bool jacobi_pair(double* __restrict__ cx, double* __restrict__ cy, int L, int LV,
                                             double small2, int lane) {
-  double al = 0, be = 0, ga = 0;
-  for (int i = lane; i < L; i += 32) {
+  const double al = cx[LV], be = cy[LV];
+  if (!(al > small2 && be > small2)) return false;  // warp-uniform
+  double ga = 0;
+  for (int i = lane; i < L; i += 32) ga = fma(cx[i], cy[i], ga);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  // rotate when |a_x . a_y| > 2e-15 |a_x| |a_y| (squared: no square root)
+  if (!(ga * ga > 4e-30 * al * be)) return false;
+  // the rotation with t = tan theta the smaller root of t^2 + 2 zeta t - 1 = 0,
+  // zeta = (be - al) / (2 ga): with tau = be - al, g2 = 2 ga,
+  // r = sqrt(tau^2 + g2^2) and d = |tau| + r, t = sign(tau) g2 / d, so
+  // cos theta = sqrt(d / (2 r)) = d q and sin theta = sign(tau) g2 q with
+  // q = 1 / sqrt(2 r d) (no division)
+  const double tau = be - al, g2 = 2.0 * ga;
+  const double r = sqrt(fma(tau, tau, g2 * g2)), d = fabs(tau) + r;
+  const double q = rsqrt(2.0 * r * d);
+  const double c = d * q, sn = (tau >= 0 ? g2 : -g2) * q;
+  double nx = 0, ny = 0;
+  for (int i = lane; i < LV; i += 32) {
     const double u = cx[i], v = cy[i];
-    al = fma(u, u, al);
-    be = fma(v, v, be);
-    ga = fma(u, v, ga);
+    const double xu = c * u - sn * v, yv = sn * u + c * v;
+    cx[i] = xu;
+    cy[i] = yv;
+    if (i < L) {
+      nx = fma(xu, xu, nx);
+      ny = fma(yv, yv, ny);
+    }
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
-    al += __shfl_xor_sync(0xffffffffu, al, o);
-    be += __shfl_xor_sync(0xffffffffu, be, o);
-    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+    nx += __shfl_xor_sync(0xffffffffu, nx, o);
+    ny += __shfl_xor_sync(0xffffffffu, ny, o);
   }
-  // rotate when |a_x . a_y| > 2e-15 |a_x| |a_y| (squared: no square root)
-  if (!(al > small2 && be > small2 && ga * ga > 4e-30 * al * be)) return false;
-  // t = tan of the rotation angle, the smaller root of t^2 + 2 zeta t - 1 = 0
-  // with zeta = (be - al) / (2 ga), written without dividing by ga:
-  // t = sign(tau) g2 / (|tau| + sqrt(tau^2 + g2^2)), tau = be - al, g2 = 2 ga
-  const double tau = be - al, g2 = 2.0 * ga;
-  const double t = (tau >= 0 ? g2 : -g2) / (fabs(tau) + sqrt(fma(tau, tau, g2 * g2)));
-  const double c = rsqrt(fma(t, t, 1.0)), sn = c * t;
-  for (int i = lane; i < LV; i += 32) {
-    const double u = cx[i], v = cy[i];
-    cx[i] = c * u - sn * v;
-    cy[i] = sn * u + c * v;
+  if (lane == 0) {
+    cx[LV] = nx;
+    cy[LV] = ny;
   }
+  __syncwarp();
   return true;
 }
 
-// largest squared column norm (A part) of the 2b columns at cols (global
-// column index of slot 0 = j0; columns >= n are padding)
-__device__ double local_cmax(const double* cols, int nslot, int j0, int n, int L, int LV) {
+// largest squared column norm (A part) of the 2b columns at cols (stride LS;
+// global column index of slot 0 = j0; columns >= n are padding); every norm
+// is also stored at index LV of its column
+__device__ double local_cmax(double* cols, int nslot, int j0, int n, int L, int LV, int LS) {
   __shared__ double s_red[kSvdWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   double mx = 0;
   for (int h = warp; h < nslot; h += kSvdWarps) {
     if (j0 + h >= n) continue;
     double t = 0;
-    for (int i = lane; i < L; i += 32) t = fma(cols[(size_t)h * LV + i], cols[(size_t)h * LV + i], t);
+    for (int i = lane; i < L; i += 32) t = fma(cols[(size_t)h * LS + i], cols[(size_t)h * LS + i], t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) cols[(size_t)h * LS + LV] = t;
     mx = fmax(mx, t);
   }
   if (lane == 0) s_red[warp] = mx;
@@ -942,24 +979,24 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   }
   // Jacobi on X = R^T (n x n) of the QR of A = C (if m < k) or C^T (k_trunc_qrcp)
   const bool cols_of_C = m < k;
-  const int n = cols_of_C ? m : k, La = cols_of_C ? k : m, L = n, LV = 2 * n;
+  const int n = cols_of_C ? m : k, La = cols_of_C ? k : m, L = n, LV = 2 * n, LS = LV + 2;
   const QrWork Q(W, p, m);
   const int nb = 2 * C, b = (n + nb - 1) / nb;
   // the CTA's column blocks and round buffers: shared memory, or (problems
   // too large for it) a slice of the global work array per CTA
   extern __shared__ double smd[];
-  const size_t per_cta = (size_t)4 * b * LV;
+  const size_t per_cta = (size_t)4 * b * LS;
   double* sm = global_blocks ? W.Jg + (size_t)crank * per_cta : smd;
   auto owner_blocks = [&](int r) -> double* {
     return global_blocks ? W.Jg + (size_t)r * per_cta : cl.map_shared_rank(smd, r);
   };
   double* home = sm;                    // 2b columns: global columns 2 crank b + h
-  double* work = sm + (size_t)2 * b * LV;  // the two blocks of a tournament round
+  double* work = sm + (size_t)2 * b * LS;  // the two blocks of a tournament round
   const int j0 = 2 * crank * b;
-  for (long e = tid; e < (long)2 * b * LV; e += kSvdThreads) {
-    const int h = (int)(e / LV), i = (int)(e % LV), j = j0 + h;
+  for (long e = tid; e < (long)2 * b * LS; e += kSvdThreads) {
+    const int h = (int)(e / LS), i = (int)(e % LS), j = j0 + h;
     double v = 0;
-    if (j < n) v = i < L ? Q.Rt[(size_t)j * n + i] : ((i - L == j) ? 1.0 : 0.0);
+    if (j < n && i < LV) v = i < L ? Q.Rt[(size_t)j * n + i] : ((i - L == j) ? 1.0 : 0.0);
     home[e] = v;
   }
   __syncthreads();
@@ -983,7 +1020,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
     }
     __syncthreads();
   };
-  exchange(1, 0.0, local_cmax(home, 2 * b, j0, n, L, LV));
+  exchange(1, 0.0, local_cmax(home, 2 * b, j0, n, L, LV, LS));
   // columns below 1e-2 tol of the largest column norm cannot affect what the
   // truncation keeps (its tail is measured at tol): they are not rotated
   const double zfac = fmax(1e-32, (1e-2 * d.tol) * (1e-2 * d.tol));
@@ -1001,7 +1038,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
           int x = pos(q), y = pos(np - 1 - q);
           if (x > y) { const int tt = x; x = y; y = tt; }
           if (j0 + y >= n) continue;
-          if (jacobi_pair(home + (size_t)x * LV, home + (size_t)y * LV, L, LV, small2, lane)) ++nrot;
+          if (jacobi_pair(home + (size_t)x * LS, home + (size_t)y * LS, L, LV, small2, lane)) ++nrot;
         }
         __syncthreads();
       }
@@ -1011,33 +1048,33 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
       auto bpos = [&](int u) { return u == 0 ? 0 : ((round + u - 1) % (nb - 1)) + 1; };
       int X = bpos(crank), Y = bpos(nb - 1 - crank);
       if (X > Y) { const int tt = X; X = Y; Y = tt; }
-      double* hx = owner_blocks(X >> 1) + (size_t)(X & 1) * b * LV;
-      double* hy = owner_blocks(Y >> 1) + (size_t)(Y & 1) * b * LV;
+      double* hx = owner_blocks(X >> 1) + (size_t)(X & 1) * b * LS;
+      double* hy = owner_blocks(Y >> 1) + (size_t)(Y & 1) * b * LS;
       const bool any = X * b < n && Y * b < n;
       if (any) {
-        for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
+        for (long e = tid; e < (long)b * LS; e += kSvdThreads) {
           work[e] = hx[e];
-          work[(size_t)b * LV + e] = hy[e];
+          work[(size_t)b * LS + e] = hy[e];
         }
         __syncthreads();
         for (int sr = 0; sr < b; ++sr) {
           for (int q = warp; q < b; q += kSvdWarps) {
             const int xi = q, yi = (q + sr) % b;
             if (X * b + xi >= n || Y * b + yi >= n) continue;
-            if (jacobi_pair(work + (size_t)xi * LV, work + (size_t)(b + yi) * LV, L, LV, small2, lane)) ++nrot;
+            if (jacobi_pair(work + (size_t)xi * LS, work + (size_t)(b + yi) * LS, L, LV, small2, lane)) ++nrot;
           }
           __syncthreads();
         }
-        for (long e = tid; e < (long)b * LV; e += kSvdThreads) {
+        for (long e = tid; e < (long)b * LS; e += kSvdThreads) {
           hx[e] = work[e];
-          hy[e] = work[(size_t)b * LV + e];
+          hy[e] = work[(size_t)b * LS + e];
         }
       }
       csync();
     }
     if (lane == 0 && nrot) atomicAdd(&s_rot, nrot);
     __syncthreads();
-    exchange(t & 1, (double)s_rot, local_cmax(home, 2 * b, j0, n, L, LV));
+    exchange(t & 1, (double)s_rot, local_cmax(home, 2 * b, j0, n, L, LV, LS));
     small2 = s_cm * zfac;
     if (s_tot == 0.0) { sweeps = t + 1; break; }
   }
@@ -1045,7 +1082,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
   for (int h = warp; h < 2 * b; h += kSvdWarps) {
     const int j = j0 + h;
     if (j >= n) continue;
-    const double* col = home + (size_t)h * LV;
+    const double* col = home + (size_t)h * LS;
     double t = 0;
     for (int i = lane; i < L; i += 32) t = fma(col[i], col[i], t);
 #pragma unroll
@@ -1107,7 +1144,7 @@ __global__ void __launch_bounds__(kSvdThreads) k_trunc_svd(TruncDesc* descs, int
       if (order[q] == j) pos = q;
     if (pos < 0) continue;
     const double sg = sig[pos];
-    const double* y = home + (size_t)h * LV;
+    const double* y = home + (size_t)h * LS;
     const double* w = y + L;
     double* u = Q.scr + (size_t)(crank * kSvdWarps + warp) * La;
     for (int i = lane; i < La; i += 32) u[i] = i < n ? w[i] : 0.0;
@@ -1230,7 +1267,7 @@ int trunc_svd(const TruncDesc* d, int n, cudaStream_t s, TruncDesc* d_dev, bool 
   size_t smem = 0;
   for (;;) {
     const int b = (nmax + 2 * C - 1) / (2 * C);
-    smem = sizeof(double) * (size_t)4 * b * (Lmax + nmax);
+    smem = sizeof(double) * (size_t)4 * b * (Lmax + nmax + 2);
     if (smem <= 200 * 1024 || C >= 16) break;
     C *= 2;  // more CTAs per problem: smaller blocks
   }

@@ -109,11 +109,12 @@ struct TruncWork {
     Jg = Vm + n * n;  // column blocks of the cluster SVD when they exceed shared memory
   }
 };
-// Doubles of Jg per problem for a cluster of C CTAs: C x 4 b (L + n), b = ceil(n / 2C).
+// Doubles of Jg per problem for a cluster of C CTAs: C x 4 b (L + n + 2),
+// b = ceil(n / 2C) (a column: its n + n entries and its norm, padded).
 __host__ __device__ inline size_t trunc_svd_global_len(int p, int m, int C) {
   const int n = p < m ? p : m, L = p < m ? m : p;
   const int b = (n + 2 * C - 1) / (2 * C);
-  return (size_t)C * 4 * b * (size_t)(L + n);
+  return (size_t)C * 4 * b * (size_t)(L + n + 2);
 }
 // The QR preconditioning of the SVD (after Jg, sized for p x m): Householder
 // vectors Aw (L x n, column-major), X = R^T (n x n, column c = row c of R),

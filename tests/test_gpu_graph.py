@@ -189,13 +189,18 @@ def test_subset_step_graph_matches_host_sized(precision):
         got[mode] = (ranks, rel, outer, U.cpu().numpy(), V.cpu().numpy())
         sub.close()
     assert list(got[0][2]) == list(got[2][2])           # the same correction counts
-    # FP64: the same residuals to rounding; mixed: the FP32 inner residuals round
-    # differently with the fixed widths (other split-K partitions), ~1e-7 relative:
-    # the last correction leaves residuals at that noise floor (1e-11 .. 5e-9,
-    # far below the target), which differ column by column by a few times; what
-    # is determined is the target and the size of the largest residual
+    # FP64: the same residuals up to the truncation's resolution.  The fixed
+    # widths round differently (zero-padded concatenations, other split-K
+    # partitions), and the truncation with tol 1e-10 (Sec. 5: the smallest r with
+    # ||s_{>r}|| <= tol ||s||) may then keep one singular triplet more or less at
+    # the boundary, which moves an update by up to tol of its norm: residuals of
+    # 1e-9 and below may differ by ~1e-11.  Mixed: the FP32 inner residuals round
+    # differently with the fixed widths, ~1e-7 relative: the last correction
+    # leaves residuals at that noise floor (1e-11 .. 5e-9, far below the target),
+    # which differ column by column by a few times; what is determined is the
+    # target and the size of the largest residual
     if precision == 0:
-        assert np.allclose(got[0][1], got[2][1], rtol=1e-3, atol=1e-12)
+        assert np.allclose(got[0][1], got[2][1], rtol=1e-3, atol=1e-11)
     else:
         assert np.all(got[2][1] <= 1e-8)
         ratio = got[2][1].max() / got[0][1].max()
