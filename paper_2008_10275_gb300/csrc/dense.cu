@@ -525,12 +525,15 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
     }
   }
   if (threadIdx.x == 0) s_k = p;
-  __syncthreads();
-  for (int i = 0; i < p; ++i) {
-    // pivot: largest remaining diagonal (ties: smallest position)
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // per-warp pivot candidates (largest remaining diagonal; ties: the smallest
+  // position) in s_val[w], s_idx[w]: a scan here for the first pivot and on the
+  // global path; on the packed path the update of a row leaves its new diagonal
+  // with lane 0 of the row's warp, which keeps the warp's candidate
+  auto scan = [&](int from) {
     double best = -1.0;
-    int bj = i;
-    for (int j = i + threadIdx.x; j < p; j += blockDim.x) {
+    int bj = 0x7fffffff;
+    for (int j = from + threadIdx.x; j < p; j += blockDim.x) {
       const int pj = perm[j];
       const double v = packed ? Pk[packed_idx(pj, pj, p)] : G[(size_t)pj * p + pj];
       if (v > best) { best = v; bj = j; }
@@ -541,12 +544,17 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
       const int j2 = __shfl_xor_sync(0xffffffffu, bj, o);
       if (v2 > best || (v2 == best && j2 < bj)) { best = v2; bj = j2; }
     }
-    if ((threadIdx.x & 31) == 0) { s_val[threadIdx.x >> 5] = best; s_idx[threadIdx.x >> 5] = bj; }
-    __syncthreads();
+    if (lane == 0) { s_val[wp] = best; s_idx[wp] = bj; }
+  };
+  __syncthreads();
+  scan(0);
+  __syncthreads();
+  for (int i = 0; i < p; ++i) {
+    // the pivot from the warps' candidates; thread 0 takes its root and
+    // reciprocal and moves it to position i of the permutation
     if (threadIdx.x < 32) {
-      const int nw = blockDim.x >> 5;
-      best = threadIdx.x < nw ? s_val[threadIdx.x] : -1.0;
-      bj = threadIdx.x < nw ? s_idx[threadIdx.x] : 0x7fffffff;
+      double best = lane < nw ? s_val[lane] : -1.0;
+      int bj = lane < nw ? s_idx[lane] : 0x7fffffff;
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) {
         const double v2 = __shfl_xor_sync(0xffffffffu, best, o);
@@ -556,24 +564,21 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
       if (threadIdx.x == 0) {
         s_val[32] = best;
         s_idx[32] = bj;
-        s_root = best > 0 ? sqrt(best) : 0.0;  // the pivot's root and its reciprocal, once
+        s_root = best > 0 ? sqrt(best) : 0.0;
         s_rinv = s_root > 0 ? 1.0 / s_root : 0.0;
+        if (best > d.drop && isfinite(best) && bj < p) {
+          const int t = perm[i];
+          perm[i] = perm[bj];
+          perm[bj] = t;
+        }
       }
     }
     __syncthreads();
     const double piv = s_val[32];
-    const int jm = s_idx[32];
     if (!(piv > d.drop) || !isfinite(piv)) {
       if (threadIdx.x == 0) s_k = i;
-      break;  // uniform: every thread read the same s_val[0]
+      break;  // uniform: every thread read the same s_val[32]
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const int t = perm[i];
-      perm[i] = perm[jm];
-      perm[jm] = t;
-    }
-    __syncthreads();
     const int pi = perm[i];
     const double r = s_root, rinv = s_rinv;
     // row i of R, indexed by ORIGINAL column (no swaps of earlier rows needed)
@@ -587,20 +592,26 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_pass1(TruncDesc* descs,
     __syncthreads();
     const int nt = p - i - 1;
     if (packed) {  // the upper triangle of the trailing block: a warp per row
-      const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-      for (int ra = i + 1 + (threadIdx.x >> 5); ra < p; ra += nw) {
+      double best = -1.0;
+      int bj = 0x7fffffff;
+      for (int ra = i + 1 + wp; ra < p; ra += nw) {
         const int pa = perm[ra];
         const double ua = rrow[pa];
         for (int rb = ra + lane; rb < p; rb += 32) {
           const int pb = perm[rb];
-          Pk[packed_idx(pa, pb, p)] -= ua * rrow[pb];
+          const double v = Pk[packed_idx(pa, pb, p)] - ua * rrow[pb];
+          Pk[packed_idx(pa, pb, p)] = v;
+          if (rb == ra && v > best) { best = v; bj = ra; }  // lane 0: the new diagonal
         }
       }
+      if (lane == 0) { s_val[wp] = best; s_idx[wp] = bj; }
     } else {
       for (long e = threadIdx.x; e < (long)nt * nt; e += blockDim.x) {
         const int pa = perm[i + 1 + (int)(e / nt)], pb = perm[i + 1 + (int)(e % nt)];
         G[(size_t)pa * p + pb] -= R[(size_t)i * p + pa] * R[(size_t)i * p + pb];
       }
+      __syncthreads();
+      scan(i + 1);
     }
     __syncthreads();
   }
@@ -706,7 +717,11 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qr(TruncDesc* descs, in
 // the launch's dynamic shared memory (smem_bytes), else in Aw.  Aw ends as the column-major reflectors (v_j in rows
 // j.. of column j, its leading entry explicit) and R above the diagonal;
 // Rt = R^T; tau_j; perm (A P = A[:, perm]).  The trailing norms of the
-// columns are recomputed exactly while each reflector is applied.
+// columns are downdated by the squared entry that each reflector moves into
+// R, and recomputed exactly where the downdated value has lost more than a
+// sqrt(eps) fraction of the last exact one (the safeguard of Drmac and
+// Bujanovic, "On the failure of rank-revealing QR factorization software",
+// ACM TOMS 35, 2008).
 constexpr int kQrSmem = 200 * 1024;
 __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, int smem_bytes) {
   const TruncDesc d = descs[blockIdx.x];
@@ -723,11 +738,12 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
   double* A = in_smem ? qsm : Q.Aw;
   const double* core = (d.sel && *d.sel) ? d.core_alt : d.core;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-  __shared__ double s_val[32], s_nrm[1024];
+  __shared__ double s_val[32], s_nrm[1024], s_nrm0[1024];
   __shared__ int s_idx[32];
   __shared__ int s_piv;
   __shared__ double s_tau;
   double* nrm = n <= 1024 ? s_nrm : Q.nrm;
+  double* nrm0 = n <= 1024 ? s_nrm0 : Q.scr;  // the last exact value (scr is free until the SVD)
   for (long e = tid; e < (long)L * n; e += blockDim.x) {
     const int c = (int)(e / L), i = (int)(e % L);
     A[e] = cols_of_C ? core[(size_t)i * m + c] : core[(size_t)c * m + i];
@@ -739,7 +755,7 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
     for (int i = lane; i < L; i += 32) t = fma(A[(size_t)c * L + i], A[(size_t)c * L + i], t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) nrm[c] = t;
+    if (lane == 0) nrm[c] = nrm0[c] = t;
   }
   __syncthreads();
   for (int j = 0; j < n; ++j) {
@@ -772,7 +788,6 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
     }
     // every trailing norm NaN (a non-finite core): no pivoting, tau = 0 below
     const int pv = s_piv < n ? s_piv : j;
-    const double sig2 = nrm[pv];
     if (pv != j) {
       for (int i = tid; i < L; i += blockDim.x) {
         const double t = A[(size_t)j * L + i];
@@ -781,50 +796,66 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
       }
     }
     __syncthreads();
-    // reflector H = I - tau v v^T with H x = alpha e_1, alpha = -sign(x_0) |x|
-    if (tid == 0) {
-      if (pv != j) {
-        const int t = Q.perm[j];
-        Q.perm[j] = Q.perm[pv];
-        Q.perm[pv] = t;
-        nrm[pv] = nrm[j];
+    // reflector H = I - tau v v^T with H x = alpha e_1, alpha = -sign(x_0) |x|,
+    // |x| computed exactly (rows j..; the downdated norms only choose the pivot:
+    // H is orthogonal only with the exact |x|)
+    if (warp == 0) {
+      double sg = 0;
+      for (int i = j + lane; i < L; i += 32) sg = fma(A[(size_t)j * L + i], A[(size_t)j * L + i], sg);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+      if (lane == 0) {
+        if (pv != j) {
+          const int t = Q.perm[j];
+          Q.perm[j] = Q.perm[pv];
+          Q.perm[pv] = t;
+          nrm[pv] = nrm[j];
+          nrm0[pv] = nrm0[j];
+        }
+        const double x0 = A[(size_t)j * L + j];
+        const double nx = sqrt(sg);
+        double alpha = 0.0, tau = 0.0;
+        if (nx > 0.0) {
+          alpha = x0 >= 0 ? -nx : nx;
+          const double v0 = x0 - alpha;
+          tau = -1.0 / (alpha * v0);
+          A[(size_t)j * L + j] = v0;
+        }
+        Q.tau[j] = tau;
+        Q.Rt[(size_t)j * n + j] = alpha;
+        s_tau = tau;
       }
-      const double x0 = A[(size_t)j * L + j];
-      const double nx = sqrt(sig2);
-      double alpha = 0.0, tau = 0.0;
-      if (nx > 0.0) {
-        alpha = x0 >= 0 ? -nx : nx;
-        const double v0 = x0 - alpha;
-        tau = -1.0 / (alpha * v0);
-        A[(size_t)j * L + j] = v0;
-      }
-      Q.tau[j] = tau;
-      Q.Rt[(size_t)j * n + j] = alpha;
-      s_tau = tau;
     }
     __syncthreads();
-    // apply H to the columns j+1..: w = v . a_c, a_c -= tau w v (rows j..),
-    // and the new trailing norm of a_c (rows j+1..)
+    // apply H to the columns j+1..: w = v . a_c, a_c -= tau w v (rows j..);
+    // the trailing norm of a_c (rows j+1..) = that of rows j.. (H keeps it)
+    // minus the new a_c[j]^2, recomputed where that cancels
     const double tau = s_tau;
     const double* v = A + (size_t)j * L;
     for (int c = j + 1 + warp; c < n; c += nw) {
       double* a = A + (size_t)c * L;
-      double t = 0;
       if (tau != 0.0) {
+        double t = 0;
         for (int i = j + lane; i < L; i += 32) t = fma(v[i], a[i], t);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         t *= tau;
+        for (int i = j + lane; i < L; i += 32) a[i] = fma(-t, v[i], a[i]);
       }
-      double q = 0;
-      for (int i = j + lane; i < L; i += 32) {
-        const double ai = tau != 0.0 ? fma(-t, v[i], a[i]) : a[i];
-        if (tau != 0.0) a[i] = ai;
-        if (i > j) q = fma(ai, ai, q);
+      int again = 0;
+      if (lane == 0) {  // lane 0 holds row j
+        const double aj = a[j], t2 = nrm[c] - aj * aj;
+        if (t2 > 1.4901161193847656e-8 * nrm0[c]) nrm[c] = t2;
+        else again = 1;
       }
+      again = __shfl_sync(0xffffffffu, again, 0);
+      if (again) {
+        double q = 0;
+        for (int i = j + 1 + lane; i < L; i += 32) q = fma(a[i], a[i], q);
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-      if (lane == 0) nrm[c] = q;
+        for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+        if (lane == 0) nrm[c] = nrm0[c] = q;
+      }
     }
     __syncthreads();
   }
