@@ -875,11 +875,9 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
 // (k x m) if m < k, else A = C^T (m x k); k_trunc_qrcp factors A P = Q R and
 // the iteration orthogonalises the n columns of X = R^T (n x n): X W = Y
 // with orthogonal columns, W accumulated.  Every column is stored with its W
-// column appended (length LV = 2n), so one rotation updates both, followed by
-// the squared norm of its X part (stride LS = LV + 2): a rotation refreshes
-// the norms of its two columns from the values it writes, so the test of a
-// pair needs only their inner product.  The kept singular vectors follow from
-// Y and W (see the output stage).
+// column appended (length LV = 2n), so one rotation updates both (column
+// stride LS = LV + 2).  The kept singular vectors follow from Y and W (see the
+// output stage).
 //
 // Parallel block ordering: the n columns form nb = 2 C blocks of b columns; CTA
 // c of the cluster owns blocks 2c, 2c+1 in its shared memory.  A sweep is
@@ -900,19 +898,37 @@ __global__ void __launch_bounds__(kSmallThreads) k_trunc_qrcp(TruncDesc* descs, 
 constexpr int kSvdThreads = 256;
 constexpr int kSvdWarps = kSvdThreads / 32;
 
-// cx[LV], cy[LV]: the squared norms of the X parts (L entries), summed in the
-// order of a dot product here (lane-strided FMAs, then a butterfly), so they
-// equal the norms recomputed from the columns.
+// The pair test computes |a_x|^2, |a_y|^2 and a_x . a_y together (interleaved
+// chains, two partial sums each): a sub-round's time is the latency of this
+// chain, not its FP64 count.
 __device__ __forceinline__ bool jacobi_pair(double* __restrict__ cx, double* __restrict__ cy, int L, int LV,
                                             double small2, int lane) {
-  const double al = cx[LV], be = cy[LV];
-  if (!(al > small2 && be > small2)) return false;  // warp-uniform
-  double ga = 0;
-  for (int i = lane; i < L; i += 32) ga = fma(cx[i], cy[i], ga);
+  double al0 = 0, be0 = 0, ga0 = 0, al1 = 0, be1 = 0, ga1 = 0;
+  int i = lane;
+  for (; i + 32 < L; i += 64) {
+    const double u0 = cx[i], v0 = cy[i], u1 = cx[i + 32], v1 = cy[i + 32];
+    al0 = fma(u0, u0, al0);
+    be0 = fma(v0, v0, be0);
+    ga0 = fma(u0, v0, ga0);
+    al1 = fma(u1, u1, al1);
+    be1 = fma(v1, v1, be1);
+    ga1 = fma(u1, v1, ga1);
+  }
+  if (i < L) {
+    const double u0 = cx[i], v0 = cy[i];
+    al0 = fma(u0, u0, al0);
+    be0 = fma(v0, v0, be0);
+    ga0 = fma(u0, v0, ga0);
+  }
+  double al = al0 + al1, be = be0 + be1, ga = ga0 + ga1;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    al += __shfl_xor_sync(0xffffffffu, al, o);
+    be += __shfl_xor_sync(0xffffffffu, be, o);
+    ga += __shfl_xor_sync(0xffffffffu, ga, o);
+  }
   // rotate when |a_x . a_y| > 2e-15 |a_x| |a_y| (squared: no square root)
-  if (!(ga * ga > 4e-30 * al * be)) return false;
+  if (!(al > small2 && be > small2 && ga * ga > 4e-30 * al * be)) return false;
   // the rotation with t = tan theta the smaller root of t^2 + 2 zeta t - 1 = 0,
   // zeta = (be - al) / (2 ga): with tau = be - al, g2 = 2 ga,
   // r = sqrt(tau^2 + g2^2) and d = |tau| + r, t = sign(tau) g2 / d, so
@@ -922,33 +938,16 @@ __device__ __forceinline__ bool jacobi_pair(double* __restrict__ cx, double* __r
   const double r = sqrt(fma(tau, tau, g2 * g2)), d = fabs(tau) + r;
   const double q = rsqrt(2.0 * r * d);
   const double c = d * q, sn = (tau >= 0 ? g2 : -g2) * q;
-  double nx = 0, ny = 0;
-  for (int i = lane; i < LV; i += 32) {
-    const double u = cx[i], v = cy[i];
-    const double xu = c * u - sn * v, yv = sn * u + c * v;
-    cx[i] = xu;
-    cy[i] = yv;
-    if (i < L) {
-      nx = fma(xu, xu, nx);
-      ny = fma(yv, yv, ny);
-    }
+  for (int j = lane; j < LV; j += 32) {
+    const double u = cx[j], v = cy[j];
+    cx[j] = c * u - sn * v;
+    cy[j] = sn * u + c * v;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nx += __shfl_xor_sync(0xffffffffu, nx, o);
-    ny += __shfl_xor_sync(0xffffffffu, ny, o);
-  }
-  if (lane == 0) {
-    cx[LV] = nx;
-    cy[LV] = ny;
-  }
-  __syncwarp();
   return true;
 }
 
 // largest squared column norm (A part) of the 2b columns at cols (stride LS;
-// global column index of slot 0 = j0; columns >= n are padding); every norm
-// is also stored at index LV of its column
+// global column index of slot 0 = j0; columns >= n are padding)
 __device__ double local_cmax(double* cols, int nslot, int j0, int n, int L, int LV, int LS) {
   __shared__ double s_red[kSvdWarps];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -959,7 +958,7 @@ __device__ double local_cmax(double* cols, int nslot, int j0, int n, int L, int 
     for (int i = lane; i < L; i += 32) t = fma(cols[(size_t)h * LS + i], cols[(size_t)h * LS + i], t);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-    if (lane == 0) cols[(size_t)h * LS + LV] = t;
+    (void)LV;
     mx = fmax(mx, t);
   }
   if (lane == 0) s_red[warp] = mx;

@@ -1246,7 +1246,6 @@ int OzFixedPlan::build(int max_cols, int nprob) {
       be += (size_t)ntb * kTA;
       bs += round256((size_t)ceil_div_l(g.k, kChunk) * ntb * kSl * kTA * kChunk * sizeof(__nv_bfloat16));
     }
-    G.bex_bytes = sizeof(int) * be;
     bex_max = std::max(bex_max, be);
     bsl_max = std::max(bsl_max, bs);
   }

@@ -89,7 +89,6 @@ class OzFixedPlan {
     std::vector<int> prefix;   // GEMMs of the problems < q (q = 0 .. nprob)
     size_t d_off = 0;          // device descriptors (OzNdG)
     int mmax = 0, kmax = 0, ntmax = 0;
-    size_t bex_bytes = 0;      // B exponents of the group (at max_cols)
   };
   std::vector<Group> groups_;
   int nprob_ = 0, max_cols_ = 0;
