@@ -342,6 +342,8 @@ def main():
     ap.add_argument("--no-mixed", action="store_true")
     ap.add_argument("--no-gmres", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--streams", type=int, default=2,
+                    help="groups of subsets run concurrently, each on its own stream and host thread")
     args = ap.parse_args()
 
     rank, world, local = multi.rank_env()
@@ -385,7 +387,7 @@ def main():
     # subsets solved together: all of them, or groups of W.group (memory of the large mesh)
     gsz = W.group or K
     runs = [algorithm1.Runner(mesh, L.part(a, min(a + gsz, K)), opt, target=args.target, max_outer=args.max_outer,
-                              eps_N=EPS_N, device=dev) for a in range(0, K, gsz)]
+                              eps_N=EPS_N, device=dev, groups=args.streams) for a in range(0, K, gsz)]
     run = runs[0]
     U, V = run.U, run.V
     mus, nus = L.mu, L.nu
@@ -616,7 +618,8 @@ def main():
                        "target_relres": args.target, "l2": "working set (block-LU factors) larger than L2",
                        "parallelism": (f"{world} rank(s); the job's {job.K} subsets in contiguous blocks "
                                        f"balanced by m_k R_k, one gather of the results to rank 0 per step"
-                                       if world > 1 else "1 rank")},
+                                       if world > 1 else "1 rank"),
+                       "concurrent_groups": runs[0].groups},
             "clocks": clk.summary(),
             "e2e": {"value": job.m / (ms_e2e * 1e-3), "unit": "params/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -31,10 +31,14 @@
  *   values (norms, ranks, iteration counts) synchronize that stream.
  * - All arithmetic named FP64 is IEEE binary64; the mixed mode runs the inner
  *   Chebyshev correction in binary32 inside an FP64 refinement loop.
- * - Concurrency: calls on one handle must not overlap, and the library keeps
- *   process-wide scratch (the split-K GEMM workspace, the SpMM autotuner
- *   table), so calls from several host threads must be serialised by the
- *   caller.  One device per process (the current device at each call).
+ * - Concurrency: calls on one handle must not overlap.  Calls on different
+ *   handles may run at the same time from different host threads, each on its
+ *   own stream: the grouped GEMMs' workspace belongs to the calling thread
+ *   (freed when it exits), the SpMM autotuner table and a mesh's lazily built
+ *   nested-dissection structure are guarded by locks, and stream captures are
+ *   thread-local.  lrfsi_gram_path, lrfsi_lu_mode, lrfsi_graph_mode,
+ *   lrfsi_svd_cluster and lrfsi_timing are process-wide settings.  One device
+ *   per process (the current device at each call).
  */
 #ifndef LRFSI_H
 #define LRFSI_H

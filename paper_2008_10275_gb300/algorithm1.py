@@ -102,10 +102,16 @@ def partition(layout, nproc):
 
 
 class Runner:
-    """One run of Algorithm 1 over a layout on the current device."""
+    """One run of Algorithm 1 over a layout on the current device.
+
+    ``groups`` > 1 splits the K subsets into that many contiguous groups,
+    balanced by m_k R_k (``partition``), each with its own handle, CUDA stream
+    and host thread: the subsets are independent (Sec. 2), and the groups'
+    phases overlap on the GPU -- the small dense factorisations of one group's
+    truncations (a few SMs each) beside another group's solves and products."""
 
     def __init__(self, mesh, layout, opt, target=1e-6, max_outer=40, eps_N=1e-6, newton_max_it=30,
-                 device="cuda:0"):
+                 device="cuda:0", groups=1):
         import torch
         self.torch = torch
         self.mesh, self.layout, self.opt = mesh, layout, opt
@@ -115,6 +121,55 @@ class Runner:
         self.R = int(layout.caps.max()) if layout.K else 0
         self.U = torch.zeros(max(layout.K * mesh.M * self.R, 1), dtype=torch.float64, device=device)
         self.V = torch.zeros(max(layout.m * self.R, 1), dtype=torch.float64, device=device)
+        self.groups = max(1, min(int(groups), layout.K)) if layout.K else 1
+        self.first = None
+        if self.groups > 1:
+            from concurrent.futures import ThreadPoolExecutor
+            self.first = [int(x) for x in partition(layout, self.groups)]
+            self.streams = [torch.cuda.Stream(device=device) for _ in range(self.groups)]
+            # persistent threads: each keeps its own GEMM workspace in the library
+            self.pool = ThreadPoolExecutor(max_workers=self.groups)
+
+    def _subset_step(self, X, mu, nu, opt):
+        """The subset step of every subset (one handle, or one per group on its
+        own stream and thread); returns ranks, relres, outer, status."""
+        L, torch = self.layout, self.torch
+        if self.groups == 1:
+            sub = lrfsi.Subsets(self.mesh, X, mu, nu, L.sizes, L.caps)
+            try:
+                ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, self.target, self.max_outer,
+                                                                self.U, self.R, self.V, self.R)
+            finally:
+                sub.close()
+            return ranks, rel, outer, int(st)
+        M, R = self.mesh.M, self.R
+        ready = torch.cuda.Event()
+        ready.record()  # the median solutions X on the current stream
+
+        def run(g):
+            k0, k1 = self.first[g], self.first[g + 1]
+            c0, c1 = int(L.offsets[k0]), (int(L.offsets[k1]) if k1 < L.K else L.m)
+            s = self.streams[g]
+            s.wait_event(ready)
+            with torch.cuda.stream(s):
+                sub = lrfsi.Subsets(self.mesh, X[k0:k1], mu[c0:c1], nu[c0:c1], L.sizes[k0:k1], L.caps[k0:k1],
+                                    stream=s.cuda_stream)
+                try:
+                    return lrfsi.lrfsi_subset_step(sub, opt, self.target, self.max_outer,
+                                                   self.U[k0 * M * R:k1 * M * R], R, self.V[c0 * R:c1 * R], R,
+                                                   stream=s.cuda_stream)
+                finally:
+                    sub.close()
+
+        out = list(self.pool.map(run, range(self.groups)))
+        cur = torch.cuda.current_stream()
+        for s in self.streams:
+            cur.wait_stream(s)
+        ranks = np.concatenate([o[0] for o in out])
+        rel = np.concatenate([o[1] for o in out])
+        outer = np.concatenate([o[2] for o in out])
+        st = next((int(o[3]) for o in out if int(o[3]) != 0), 0)
+        return ranks, rel, outer, st
 
     def step(self, mu=None, nu=None, opt=None):
         """Algorithm 1 on the layout's parameters (or on host arrays ``mu``,
@@ -127,12 +182,7 @@ class Runner:
         med = L.medians
         X = self.bD.repeat(L.K, 1)
         it, res, _ = lrfsi.lrfsi_newton_median(self.mesh, X, mu[med], nu[med], self.eps_N, self.newton_max_it)
-        sub = lrfsi.Subsets(self.mesh, X, mu, nu, L.sizes, L.caps)
-        try:
-            ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt or self.opt, self.target, self.max_outer,
-                                                            self.U, self.R, self.V, self.R)
-        finally:
-            sub.close()
+        ranks, rel, outer, st = self._subset_step(X, mu, nu, opt or self.opt)
         return dict(xt=X, ranks=ranks, relres=rel, outer=outer, newton_iters=it, status=int(st))
 
     def factors(self, k, ranks):

@@ -119,10 +119,18 @@ __global__ void k_gemm_reduce(GemmBatch<T> gb, int ks, const T* __restrict__ par
   *cp = v;
 }
 
-// process-wide split-K workspace (grown on demand, never shrunk) and the
-// calling thread's bound workspace, if any
-static void* g_gemm_ws = nullptr;
-static size_t g_gemm_ws_bytes = 0;
+// the calling thread's workspace of the grouped GEMMs (split-K partial sums,
+// tensor-core slices; grown on demand, freed when the thread exits), so that
+// handles driven from different host threads on their own streams never share
+// it, and the thread's bound workspace, if any
+struct GemmWs {
+  void* p = nullptr;
+  size_t bytes = 0;
+  ~GemmWs() {
+    if (p) cudaFree(p);
+  }
+};
+static thread_local GemmWs t_gemm_ws;
 static thread_local void* t_ws_bound = nullptr;
 static thread_local size_t t_ws_bound_bytes = 0;
 static thread_local size_t t_ws_peak = 0;
@@ -130,7 +138,7 @@ void gemm_ws_bind(void* p, size_t bytes) { t_ws_bound = p; t_ws_bound_bytes = p 
 size_t gemm_ws_peak() { return t_ws_peak; }
 void gemm_ws_peak_reset() { t_ws_peak = 0; }
 
-// workspace of a grouped-GEMM call: the bound one, else the process-wide one
+// workspace of a grouped-GEMM call: the bound one, else the thread's one
 // grown on demand; records the peak need
 static int gemm_ws_get(size_t need, void** ws, size_t* bytes) {
   if (need > t_ws_peak) t_ws_peak = need;
@@ -140,15 +148,15 @@ static int gemm_ws_get(size_t need, void** ws, size_t* bytes) {
     *bytes = t_ws_bound_bytes;
     return LRFSI_OK;
   }
-  if (need > g_gemm_ws_bytes) {
-    if (g_gemm_ws) cudaFree(g_gemm_ws);
-    g_gemm_ws = nullptr;
-    g_gemm_ws_bytes = 0;
-    LRFSI_CUDA(cudaMalloc(&g_gemm_ws, need));
-    g_gemm_ws_bytes = need;
+  if (need > t_gemm_ws.bytes) {
+    if (t_gemm_ws.p) cudaFree(t_gemm_ws.p);
+    t_gemm_ws.p = nullptr;
+    t_gemm_ws.bytes = 0;
+    LRFSI_CUDA(cudaMalloc(&t_gemm_ws.p, need));
+    t_gemm_ws.bytes = need;
   }
-  *ws = g_gemm_ws;
-  *bytes = g_gemm_ws_bytes;
+  *ws = t_gemm_ws.p;
+  *bytes = t_gemm_ws.bytes;
   return LRFSI_OK;
 }
 

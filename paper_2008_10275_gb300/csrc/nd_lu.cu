@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <cmath>
 #include <functional>
+#include <mutex>
 #include <numeric>
 
 #include "nd_lu.h"
@@ -725,8 +726,11 @@ static int nd_attrs() {
   return LRFSI_OK;
 }
 
-// The mesh's symbolic structure and its device copies (built on first use).
+// The mesh's symbolic structure and its device copies (built on first use;
+// handles of one mesh may be created from several host threads).
+static std::mutex g_nd_mesh_mu;
 static int nd_mesh(lrfsi_mesh_s* m) {
+  std::lock_guard<std::mutex> lk(g_nd_mesh_mu);
   if (m->nd && m->ndd) return LRFSI_OK;
   auto sym = std::make_shared<NdSymbolic>();
   LRFSI_TRY(nd_symbolic(m->h, *sym));
