@@ -233,6 +233,10 @@ def run_learned(args, rank, world):
     opts = [lrfsi.cheb_options(args.c, args.d, iters=6, cycles=2, rank_cap=R, tol=W.tol, precision=pr, eta=args.eta)
             for pr in (0, 1)]
 
+    from concurrent.futures import ThreadPoolExecutor
+    streams = [torch.cuda.Stream(device=dev) for _ in range(max(1, args.streams))]
+    pool = ThreadPoolExecutor(max_workers=max(1, args.streams))
+
     def layout(mus, nus, K):
         Ly = algorithm1.set_layout(mus, nus, K=K, rank_cap=R)  # nu_f-major, mu fastest
         return Ly.mu, Ly.nu, Ly.sizes.tolist(), Ly.medians.tolist()
@@ -246,20 +250,51 @@ def run_learned(args, rank, world):
         if ls is not None:  # learned start of the median Newton iterations
             ls.start(mus[medians], nus[medians], X)
         it, res, _ = lrfsi.lrfsi_newton_median(mesh, X, mus[medians], nus[medians], EPS_N, 30)
-        sub = lrfsi.Subsets(mesh, X, mus, nus, sizes, [R] * K)
         U = torch.zeros(K * M * R, dtype=torch.float64, device=dev)
         V = torch.zeros(m * R, dtype=torch.float64, device=dev)
-        fb = np.zeros(m, np.int32)
-        if ls is None:
-            ranks, rel, outer, st = lrfsi.lrfsi_subset_step(sub, opt, args.target, args.max_outer, U, R, V, R)
-        else:
+        if ls is not None:
             k = ls.k
             U0 = torch.zeros(K * M * (k + 1), dtype=torch.float64, device=dev)
             V0 = torch.zeros(m * (k + 1), dtype=torch.float64, device=dev)
             ls.factors(sizes, mus, nus, X, U0, V0)
-            ranks, rel, outer, fb, st = lrfsi.lrfsi_subset_step_init(sub, opt, args.target, args.max_outer, U0, k + 1,
-                                                                     V0, k + 1, k + 1, U, R, V, R)
-        sub.close()
+        # the subset steps in concurrent groups (contiguous, balanced by m_k R_k),
+        # each with its own handle, stream and host thread, as Runner(groups=...)
+        G = max(1, min(args.streams, K))
+        first = [int(x) for x in lrfsi.lrfsi_partition(np.asarray(sizes, np.int64) * R, G)]
+        offs = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+        ready = torch.cuda.Event()
+        ready.record()
+
+        def run(g):
+            k0, k1 = first[g], first[g + 1]
+            c0, c1 = int(offs[k0]), int(offs[k1])
+            s = streams[g]
+            s.wait_event(ready)
+            with torch.cuda.stream(s):
+                sub = lrfsi.Subsets(mesh, X[k0:k1], mus[c0:c1], nus[c0:c1], sizes[k0:k1], [R] * (k1 - k0),
+                                    stream=s.cuda_stream)
+                try:
+                    Ug, Vg = U[k0 * M * R:k1 * M * R], V[c0 * R:c1 * R]
+                    if ls is None:
+                        rk, rl, ou, st_ = lrfsi.lrfsi_subset_step(sub, opt, args.target, args.max_outer, Ug, R, Vg, R,
+                                                                  stream=s.cuda_stream)
+                        return rk, rl, ou, np.zeros(c1 - c0, np.int32), st_
+                    kk = ls.k + 1
+                    return lrfsi.lrfsi_subset_step_init(sub, opt, args.target, args.max_outer,
+                                                        U0[k0 * M * kk:k1 * M * kk], kk, V0[c0 * kk:c1 * kk], kk, kk,
+                                                        Ug, R, Vg, R, stream=s.cuda_stream)
+                finally:
+                    sub.close()
+
+        outs = list(pool.map(run, range(G)))
+        cur = torch.cuda.current_stream()
+        for s in streams[:G]:
+            cur.wait_stream(s)
+        ranks = np.concatenate([o[0] for o in outs])
+        rel = np.concatenate([o[1] for o in outs])
+        outer = np.concatenate([o[2] for o in outs])
+        fb = np.concatenate([o[3] for o in outs])
+        st = next((int(o[4]) for o in outs if int(o[4]) != 0), 0)
         cols, o = [], 0
         for q in range(K):
             r = int(ranks[q])
@@ -310,7 +345,7 @@ def run_learned(args, rank, world):
         "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": W.name, "mesh": f"{W.nx}x{W.ny}", "M": M, "params": m, "subsets": W.K, "rank_cap": R,
                    "train": "500 method solutions at Latin-hypercube parameters", "pod_rank": k,
-                   "mlp": "2-128-128-64 GELU, BF16 weights"},
+                   "mlp": "2-128-128-64 GELU, BF16 weights", "concurrent_groups": max(1, args.streams)},
         "learned_mixed": {**st_l, "ms": ms_learn, "params_per_s": m / (ms_learn * 1e-3)},
         "learned_fp64": {**st_l64, "ms": ms_l64, "params_per_s": m / (ms_l64 * 1e-3)},
         "plain_fp64": {**st_p, "ms": ms_plain, "params_per_s": m / (ms_plain * 1e-3)},
