@@ -101,6 +101,19 @@ def partition(layout, nproc):
     return lrfsi.lrfsi_partition(layout.weights(), nproc)
 
 
+def group_bounds(layout, groups):
+    """Contiguous groups of subsets balanced by m_k R_k (``partition``): one
+    (first subset, end subset, first column, end column) per group."""
+    first = [int(x) for x in partition(layout, groups)]
+    out = []
+    for g in range(groups):
+        k0, k1 = first[g], first[g + 1]
+        c0 = int(layout.offsets[k0]) if k0 < layout.K else layout.m
+        c1 = int(layout.offsets[k1]) if k1 < layout.K else layout.m
+        out.append((k0, k1, c0, c1))
+    return out
+
+
 class Runner:
     """One run of Algorithm 1 over a layout on the current device.
 
@@ -122,10 +135,10 @@ class Runner:
         self.U = torch.zeros(max(layout.K * mesh.M * self.R, 1), dtype=torch.float64, device=device)
         self.V = torch.zeros(max(layout.m * self.R, 1), dtype=torch.float64, device=device)
         self.groups = max(1, min(int(groups), layout.K)) if layout.K else 1
-        self.first = None
+        self.bounds = None
         if self.groups > 1:
             from concurrent.futures import ThreadPoolExecutor
-            self.first = [int(x) for x in partition(layout, self.groups)]
+            self.bounds = group_bounds(layout, self.groups)
             self.streams = [torch.cuda.Stream(device=device) for _ in range(self.groups)]
             # persistent threads: each keeps its own GEMM workspace in the library
             self.pool = ThreadPoolExecutor(max_workers=self.groups)
@@ -147,8 +160,7 @@ class Runner:
         ready.record()  # the median solutions X on the current stream
 
         def run(g):
-            k0, k1 = self.first[g], self.first[g + 1]
-            c0, c1 = int(L.offsets[k0]), (int(L.offsets[k1]) if k1 < L.K else L.m)
+            k0, k1, c0, c1 = self.bounds[g]
             s = self.streams[g]
             s.wait_event(ready)
             with torch.cuda.stream(s):

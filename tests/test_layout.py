@@ -112,3 +112,25 @@ def test_layout_part_and_job_split():
     assert p1.K == 4 and p1.m == 400 and p1.offsets.tolist() == [0, 100, 200, 300]
     assert p1.medians.tolist() == [50, 150, 250, 350]
     assert np.array_equal(p1.mu, job.mu[400:]) and np.array_equal(p1.nu, job.nu[400:])
+
+
+@pytest.mark.parametrize("name,groups", [("medium", 2), ("medium", 4), ("batched", 2), ("batched", 3), ("large", 2)])
+def test_group_bounds_cover_the_layout_contiguously(name, groups):
+    """The groups that Runner(groups=G) solves concurrently: contiguous blocks of
+    whole subsets, every subset and every parameter column in exactly one group,
+    the columns of a group those of its subsets, and the heaviest group (m_k
+    R_k) within one subset of the mean."""
+    L = algorithm1.workload_layout(inputs.WORKLOADS[name])
+    b = algorithm1.group_bounds(L, groups)
+    assert len(b) == groups
+    assert b[0][0] == 0 and b[0][2] == 0 and b[-1][1] == L.K and b[-1][3] == L.m
+    for (k0, k1, c0, c1), nxt in zip(b, b[1:] + [None]):
+        assert k0 < k1  # no empty group while K >= groups
+        assert c0 == int(L.offsets[k0]) and c1 - c0 == int(L.sizes[k0:k1].sum())
+        if nxt is not None:
+            assert nxt[0] == k1 and nxt[2] == c1
+    # balance: the heaviest block of an optimal contiguous split exceeds the
+    # mean by less than one subset (a greedy fill at the mean reaches it)
+    w = L.weights()
+    heaviest = max(int(w[k0:k1].sum()) for k0, k1, _, _ in b)
+    assert heaviest <= w.sum() / groups + w.max()
